@@ -1,0 +1,30 @@
+"""Build the FP64 CPU oracle (test infrastructure) into oracle/_oracle.so.
+
+Plain gcc, IEEE arithmetic (no fast-math, no FMA contraction) so that the
+single-precision quantiser decision matches its definition exactly.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+OUT = os.path.join(HERE, "_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    hdr = os.path.join(HERE, "oracle.h")
+    if (not force and os.path.exists(OUT)
+            and os.path.getmtime(OUT) >= max(os.path.getmtime(SRC), os.path.getmtime(hdr))):
+        return OUT
+    tmp = OUT + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wextra", "-Wno-unused-parameter",
+           "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, OUT)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,897 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle of the CVC contourlet codec hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Plain loops, no blocking, no
+ * fusion, no reordering beyond what the definitions below state, so that a
+ * reader can check each function against the paper by eye.
+ *
+ * Paper: S. Katsigiannis, G. Papaioannou, D. Maroulis, "CVC: The Contourlet
+ * Video Compression algorithm for real-time applications", arXiv:1510.00561.
+ * Section references (§) are to that paper.
+ *
+ * Readings taken where the paper is silent (each one is also listed in the
+ * design notes of the repository):
+ *   - colour: the integer lifting form YCoCg-R of Table 1 (Eq. 1-6);
+ *   - chroma factor N = 4 (§4.1) read as 2x2 (4:2:0) area subsampling with
+ *     a rounded box average; decoder upsampling = bilinear (§3.1) with
+ *     centred sample siting, weights (9,3,3,1)/16;
+ *   - LP (§2.1) with the CDF 9/7 pair [18], periodic extension, synthesis by
+ *     the dual-frame rule x = d + G(c - H d);
+ *   - DFB (§2.1): iterated two-channel fan filter banks in ladder (lifting)
+ *     form with the 4-tap half-band (-1,9,9,-1)/16 prototype, resampled
+ *     (sheared) coordinates from the third stage on, wedge-ordered tree;
+ *   - lowpass normalisation (§3.4) = exact scale by 2^-L;
+ *   - quantisation and rounding (§3.5, §3.6) = round half away from zero of
+ *     c / QP, decided in single precision, int16 codes;
+ *   - K/P differencing (§3.7) in wrapping 16-bit arithmetic, zero motion;
+ *   - RLE (§3.8): per row, a non-zero value is one token, a maximal zero
+ *     run of length n is the token pair (0, n).
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int wrapi(long a, int n) {
+    long r = a % n;
+    return (int)(r < 0 ? r + n : r);
+}
+static long floordiv(long a, long b) { /* b > 0 */
+    long q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+/* ------------------------------------------------------------------ layout
+ * Coefficient layout of one plane (§3.3: the coarsest lowpass image plus the
+ * directional subbands of every scale): lowpass first, then levels 1 (finest)
+ * to L, each level's 2^k subbands in tree order.  Plane sizes must be
+ * multiples of the modulus so that every level and every DFB stage splits
+ * evenly.                                                                   */
+int or_modulus(int L, const int* k) {
+    int m = 1 << L;
+    for (int j = 1; j <= L; j++) {
+        int kj = k[j - 1];
+        int need = (1 << (j - 1)) * (kj >= 2 ? (1 << (kj - 1)) : 2);
+        if (need > m) m = need;
+    }
+    return m;
+}
+
+int or_layout_make(int H, int W, int L, const int* k, or_layout* out) {
+    if (L < 1 || L > OR_MAX_LEVELS || H <= 0 || W <= 0) return OR_EINVAL;
+    for (int j = 0; j < L; j++)
+        if (k[j] < 0 || k[j] > OR_MAX_K) return OR_EINVAL;
+    int M = or_modulus(L, k);
+    if (H % M || W % M) return OR_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->H = H; out->W = W; out->L = L;
+    for (int j = 0; j < L; j++) out->k[j] = k[j];
+    long off = 0;
+    or_subband* s = &out->sb[0];
+    s->off = 0; s->h = H >> L; s->w = W >> L; s->level = 0; s->dir = 0; s->kind = 0;
+    off += (long)s->h * s->w;
+    int n = 1;
+    for (int j = 1; j <= L; j++) {
+        int Hj = H >> (j - 1), Wj = W >> (j - 1), kj = k[j - 1];
+        int nd = 1 << kj;
+        for (int d = 0; d < nd; d++) {
+            s = &out->sb[n++];
+            s->off = off; s->level = j; s->dir = d;
+            if (kj == 0) { s->h = Hj; s->w = Wj; s->kind = 3; }
+            else if (kj == 1) { s->h = Hj; s->w = Wj / 2; s->kind = 4; }
+            else if (d < nd / 2) { s->h = Hj >> (kj - 1); s->w = Wj / 2; s->kind = 1; }
+            else { s->h = Hj / 2; s->w = Wj >> (kj - 1); s->kind = 2; }
+            off += (long)s->h * s->w;
+        }
+    }
+    out->nsub = n;
+    out->total = off;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------- CDF 9/7
+ * §2.1 cites the Cohen-Daubechies 9-7 filters [18].  They are the
+ * biorthogonal spline-variant pair obtained by splitting Daubechies'
+ * polynomial P(y) = 1 + 4y + 10y^2 + 20y^3 (y = sin^2(w/2)): the real root
+ * y0 goes to the 7-tap synthesis lowpass, the complex pair to the 9-tap
+ * analysis lowpass, each with four zeros at w = pi and DC gain sqrt(2):
+ *   H(w) = sqrt2 (1-y)^2 q(y),  G(w) = sqrt2 (1-y)^2 (1 - y/y0),
+ *   q(y) = P(y) / (1 - y/y0).
+ * Taps are computed by multiplying Laurent polynomials in z, with
+ * 1 - y = (z + 2 + 1/z)/4 and y = (-z + 2 - 1/z)/4.                        */
+static void lpoly_mul(const double* a, int ra, const double* b, int rb, double* out) {
+    /* a has taps -ra..ra at a[0..2ra]; out has taps -(ra+rb)..(ra+rb) */
+    int ro = ra + rb;
+    for (int i = 0; i <= 2 * ro; i++) out[i] = 0.0;
+    for (int i = 0; i <= 2 * ra; i++)
+        for (int j = 0; j <= 2 * rb; j++) out[i + j] += a[i] * b[j];
+}
+
+void or_cdf97(double* h, double* g) {
+    /* real root of 20y^3 + 10y^2 + 4y + 1 by Newton iteration */
+    double y0 = -0.34;
+    for (int it = 0; it < 100; it++) {
+        double f = ((20.0 * y0 + 10.0) * y0 + 4.0) * y0 + 1.0;
+        double df = (60.0 * y0 + 20.0) * y0 + 4.0;
+        y0 -= f / df;
+    }
+    double q1 = 4.0 + 1.0 / y0, q2 = 10.0 + q1 / y0;
+    double one_minus_y[3] = {0.25, 0.5, 0.25};
+    double yv[3] = {-0.25, 0.5, -0.25};
+    double sq[5], ysq[5], t5[5], t9[9], t7[7];
+    lpoly_mul(one_minus_y, 1, one_minus_y, 1, sq);        /* (1-y)^2 */
+    lpoly_mul(yv, 1, yv, 1, ysq);                          /* y^2     */
+    /* q(y) = 1 + q1 y + q2 y^2 as taps -2..2 */
+    for (int i = 0; i < 5; i++) t5[i] = q2 * ysq[i];
+    for (int i = 0; i < 3; i++) t5[i + 1] += q1 * yv[i];
+    t5[2] += 1.0;
+    lpoly_mul(sq, 2, t5, 2, t9);
+    /* r(y) = 1 - y/y0 */
+    double r3[3];
+    for (int i = 0; i < 3; i++) r3[i] = -yv[i] / y0;
+    r3[1] += 1.0;
+    lpoly_mul(sq, 2, r3, 1, t7);
+    for (int i = 0; i < 9; i++) h[i] = sqrt(2.0) * t9[i];
+    for (int i = 0; i < 7; i++) g[i] = sqrt(2.0) * t7[i];
+}
+
+static double g_h[9], g_g[7];
+static int g_taps_ready = 0;
+static void taps_init(void) {
+    if (!g_taps_ready) { or_cdf97(g_h, g_g); g_taps_ready = 1; }
+}
+
+/* --------------------------------------------------- Laplacian pyramid
+ * §2.1, Fig. 1: one LP level splits x into a lowpass c at half resolution
+ * and a detail d at full resolution.  With periodic extension:
+ *   down(x, f)[m][n] = sum_{a,b} f[a] f[b] x[2m-a][2n-b]          (filter, decimate)
+ *   up(v, f)[y][x]   = sum_{m,n} f[y-2m] f[x-2n] v[m][n]          (expand, filter)
+ * analysis:   c = down(x, h),  d = x - up(c, g)
+ * synthesis:  x = d + up(c - down(d, h), g)        (dual-frame reading)
+ * The separable sums are taken row pass first, then column pass.            */
+static void down_filter(const double* x, int H, int W, const double* f, int R, double* out) {
+    int Hh = H / 2, Wh = W / 2;
+    double* t = (double*)malloc(sizeof(double) * (size_t)H * Wh);
+    for (int r = 0; r < H; r++)
+        for (int n = 0; n < Wh; n++) {
+            double s = 0.0;
+            for (int b = -R; b <= R; b++) s += f[b + R] * x[(long)r * W + wrapi(2L * n - b, W)];
+            t[(long)r * Wh + n] = s;
+        }
+    for (int m = 0; m < Hh; m++)
+        for (int n = 0; n < Wh; n++) {
+            double s = 0.0;
+            for (int a = -R; a <= R; a++) s += f[a + R] * t[(long)wrapi(2L * m - a, H) * Wh + n];
+            out[(long)m * Wh + n] = s;
+        }
+    free(t);
+}
+
+static void up_filter(const double* v, int Hh, int Wh, const double* f, int R, double* out) {
+    int H = 2 * Hh, W = 2 * Wh;
+    double* t = (double*)malloc(sizeof(double) * (size_t)Hh * W);
+    for (int m = 0; m < Hh; m++)
+        for (int x = 0; x < W; x++) {
+            double s = 0.0;
+            for (int tt = -R; tt <= R; tt++) {
+                int u = wrapi((long)x - tt, W);
+                if ((u & 1) == 0) s += f[tt + R] * v[(long)m * Wh + u / 2];
+            }
+            t[(long)m * W + x] = s;
+        }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            double s = 0.0;
+            for (int tt = -R; tt <= R; tt++) {
+                int u = wrapi((long)y - tt, H);
+                if ((u & 1) == 0) s += f[tt + R] * t[(long)(u / 2) * W + x];
+            }
+            out[(long)y * W + x] = s;
+        }
+    free(t);
+}
+
+void or_lp_analysis(const double* x, int H, int W, double* c, double* d) {
+    taps_init();
+    long n = (long)H * W;
+    double* p = (double*)malloc(sizeof(double) * n);
+    down_filter(x, H, W, g_h, 4, c);
+    up_filter(c, H / 2, W / 2, g_g, 3, p);
+    for (long i = 0; i < n; i++) d[i] = x[i] - p[i];
+    free(p);
+}
+
+void or_lp_synthesis(const double* c, const double* d, int H, int W, double* x) {
+    taps_init();
+    long n = (long)H * W, nh = n / 4;
+    double* e = (double*)malloc(sizeof(double) * nh);
+    double* p = (double*)malloc(sizeof(double) * n);
+    down_filter(d, H, W, g_h, 4, e);
+    for (long i = 0; i < nh; i++) e[i] = c[i] - e[i];
+    up_filter(e, H / 2, W / 2, g_g, 3, p);
+    for (long i = 0; i < n; i++) x[i] = d[i] + p[i];
+    free(e); free(p);
+}
+
+/* adjoint of the analysis map x -> (c, d):  xbar = dbar + up(cbar - down(dbar, g), h)
+ * (down(., f) and up(., f) are each other's transposes for a symmetric f)    */
+void or_lp_analysis_adjoint(const double* cbar, const double* dbar, int H, int W, double* xbar) {
+    taps_init();
+    long n = (long)H * W, nh = n / 4;
+    double* e = (double*)malloc(sizeof(double) * nh);
+    double* p = (double*)malloc(sizeof(double) * n);
+    down_filter(dbar, H, W, g_g, 3, e);
+    for (long i = 0; i < nh; i++) e[i] = cbar[i] - e[i];
+    up_filter(e, H / 2, W / 2, g_h, 4, p);
+    for (long i = 0; i < n; i++) xbar[i] = dbar[i] + p[i];
+    free(e); free(p);
+}
+
+/* adjoint of the synthesis map (c, d) -> x:  cbar = down(xbar, g), dbar = xbar - up(cbar, h) */
+void or_lp_synthesis_adjoint(const double* xbar, int H, int W, double* cbar, double* dbar) {
+    taps_init();
+    long n = (long)H * W;
+    double* p = (double*)malloc(sizeof(double) * n);
+    down_filter(xbar, H, W, g_g, 3, cbar);
+    up_filter(cbar, H / 2, W / 2, g_h, 4, p);
+    for (long i = 0; i < n; i++) dbar[i] = xbar[i] - p[i];
+    free(p);
+}
+
+/* ------------------------------------------------ directional filter bank
+ * §2.1: a DFB of l stages splits the detail image into 2^l wedge-shaped
+ * subbands with perfect reconstruction.  Reading taken here:
+ *
+ * Stage building block: a two-channel fan filter bank on a channel's sample
+ * lattice, written in lifting (ladder) form.  A channel is the coset
+ * o + {b1*p1 + b2*p2} of the periodic H x W grid; in its coordinates p the
+ * even samples (p1+p2 even) and the odd samples (p1+p2 odd) are the two
+ * outputs.  With the 4-tap half-band prototype beta = (-1, 9, 9, -1)/16 at
+ * a = -3,-1,1,3 modulated to the fan (betat[a] = (-1)^((a-1)/2) beta[a],
+ * i.e. (-1, -9, 9, 1)/16) and the 16 neighbour offsets
+ *   delta(a,b) = ((a+b)/2, (a-b)/2),  weight w = betat[a] * betat[b],
+ *   predict (odd):  y = (x - sum_w x[p + delta]) / 2
+ *   update (even):  y = x + sum_w y[p + delta]
+ * (offsets in grid units: delta1*b1 + delta2*b2, wrapped periodically).
+ *
+ * Tree: stage 1 works in grid coordinates (b1=(1,0), b2=(0,1)); its even
+ * output holds the fan |w_c| > |w_r| ("F_c"), its odd output (origin (1,0))
+ * the fan |w_r| > |w_c| ("F_r").  From stage 2 on, a channel whose wedge
+ * covers slopes [i/2^m, (i+1)/2^m] (F_c: slope w_r/w_c; F_r: slope w_c/w_r)
+ * is split in the basis whose vectors are normal to the wedge's two edges,
+ * so that the split line (the wedge bisector in slope) becomes the fan
+ * diagonal:
+ *   stage 2:  F_c  b1=(1,1),  b2=(1,-1);   F_r  b1=(1,1),  b2=(-1,1)
+ *   stage s>=3, q = 2^(s-2):
+ *             F_c  b1=(q,-2i), b2=(q,-2i-2);  F_r  b1=(-2i,q), b2=(-2i-2,q)
+ * The even child takes the lower half of the slope range (index 2i), the odd
+ * child (origin o + b1) the upper half (2i+1); after stage 2 the F_c / F_r
+ * children carry i = -1, 0.  The final subbands are laid out on their
+ * rectangular lattices: F_c on 2^(k-1) x 2 (rows x columns), F_r on
+ * 2 x 2^(k-1); k = 1 keeps the two quincunx halves row-compacted.
+ * Subband order = tree order (even child first at every split).            */
+static const int DFB_A[4] = {-3, -1, 1, 3};
+static const double DFB_BT[4] = {-1.0 / 16, -9.0 / 16, 9.0 / 16, 1.0 / 16};
+
+typedef struct { int o_r, o_c, T, i; } dfb_chan; /* T: 0 = F_c, 1 = F_r */
+
+static void dfb_basis(int s, const dfb_chan* ch, int* b /* b1r b1c b2r b2c */) {
+    if (s == 1) { b[0] = 1; b[1] = 0; b[2] = 0; b[3] = 1; return; }
+    if (s == 2) {
+        if (ch->T == 0) { b[0] = 1; b[1] = 1; b[2] = 1; b[3] = -1; }
+        else { b[0] = 1; b[1] = 1; b[2] = -1; b[3] = 1; }
+        return;
+    }
+    int q = 1 << (s - 2), i = ch->i;
+    if (ch->T == 0) { b[0] = q; b[1] = -2 * i; b[2] = q; b[3] = -2 * i - 2; }
+    else { b[0] = -2 * i; b[1] = q; b[2] = -2 * i - 2; b[3] = q; }
+}
+
+static void dfb_children(int s, const dfb_chan* ch, const int* b, dfb_chan* c0, dfb_chan* c1) {
+    c0->o_r = ch->o_r; c0->o_c = ch->o_c;
+    c1->o_r = ch->o_r + b[0]; c1->o_c = ch->o_c + b[1];
+    if (s == 1) { c0->T = 0; c1->T = 1; c0->i = c1->i = 0; }
+    else if (s == 2) { c0->T = c1->T = ch->T; c0->i = -1; c1->i = 0; }
+    else { c0->T = c1->T = ch->T; c0->i = 2 * ch->i; c1->i = 2 * ch->i + 1; }
+}
+
+typedef struct {
+    int H, W, k;
+    dfb_chan* chans[OR_MAX_K + 2];  /* chans[s]: 2^(s-1) input channels of stage s; chans[k+1]: final */
+    unsigned char* par[OR_MAX_K + 1]; /* par[s][pixel]: parity in its stage-s channel */
+    int* cid[OR_MAX_K + 1];           /* cid[s][pixel]: stage-s channel index          */
+} dfb_plan;
+
+static void dfb_plan_make(dfb_plan* P, int H, int W, int k) {
+    memset(P, 0, sizeof(*P));
+    P->H = H; P->W = W; P->k = k;
+    P->chans[1] = (dfb_chan*)calloc(1, sizeof(dfb_chan));
+    for (int s = 1; s <= k; s++) {
+        int n = 1 << (s - 1);
+        P->chans[s + 1] = (dfb_chan*)calloc((size_t)2 * n, sizeof(dfb_chan));
+        for (int c = 0; c < n; c++) {
+            int b[4];
+            dfb_basis(s, &P->chans[s][c], b);
+            dfb_children(s, &P->chans[s][c], b, &P->chans[s + 1][2 * c], &P->chans[s + 1][2 * c + 1]);
+        }
+    }
+    long np = (long)H * W;
+    for (int s = 1; s <= k; s++) {
+        P->par[s] = (unsigned char*)malloc((size_t)np);
+        P->cid[s] = (int*)malloc(sizeof(int) * (size_t)np);
+    }
+    for (int r = 0; r < H; r++)
+        for (int c = 0; c < W; c++) {
+            long idx = (long)r * W + c;
+            int ch = 0;
+            for (int s = 1; s <= k; s++) {
+                const dfb_chan* C = &P->chans[s][ch];
+                int b[4];
+                dfb_basis(s, C, b);
+                long det = (long)b[0] * b[3] - (long)b[1] * b[2];
+                long dr = r - C->o_r, dc = c - C->o_c;
+                long n1 = (long)b[3] * dr - (long)b[2] * dc;
+                long n2 = -(long)b[1] * dr + (long)b[0] * dc;
+                /* the pixel lies on this channel's lattice: both divisions are exact */
+                if (n1 % det != 0 || n2 % det != 0) abort();
+                long p1 = n1 / det, p2 = n2 / det;
+                int parity = (int)(((p1 + p2) % 2 + 2) % 2);
+                P->par[s][idx] = (unsigned char)parity;
+                P->cid[s][idx] = ch;
+                ch = 2 * ch + parity;
+            }
+        }
+}
+
+static void dfb_plan_free(dfb_plan* P) {
+    for (int s = 1; s <= P->k + 1; s++) free(P->chans[s]);
+    for (int s = 1; s <= P->k; s++) { free(P->par[s]); free(P->cid[s]); }
+}
+
+/* one lifting pass of stage s: every sample of parity `target` becomes
+ * alpha * itself + gamma * (weighted sum of its 16 neighbours of the other parity) */
+static void dfb_pass(const dfb_plan* P, double* x, int s, int target, double alpha, double gamma) {
+    int H = P->H, W = P->W;
+    for (int r = 0; r < H; r++)
+        for (int c = 0; c < W; c++) {
+            long idx = (long)r * W + c;
+            if (P->par[s][idx] != target) continue;
+            int b[4];
+            dfb_basis(s, &P->chans[s][P->cid[s][idx]], b);
+            double acc = 0.0;
+            for (int ia = 0; ia < 4; ia++)
+                for (int ib = 0; ib < 4; ib++) {
+                    int a = DFB_A[ia], bb = DFB_A[ib];
+                    int d1 = (a + bb) / 2, d2 = (a - bb) / 2;
+                    int orr = d1 * b[0] + d2 * b[2], occ = d1 * b[1] + d2 * b[3];
+                    acc += DFB_BT[ia] * DFB_BT[ib] * x[(long)wrapi((long)r + orr, H) * W + wrapi((long)c + occ, W)];
+                }
+            x[idx] = alpha * x[idx] + gamma * acc;
+        }
+}
+
+/* position of element (a, b) of final subband `ci` in the detail image */
+static void dfb_leaf_pos(const dfb_plan* P, int ci, int a, int b, int* r, int* c) {
+    int k = P->k, H = P->H, W = P->W;
+    if (k == 0) { *r = a; *c = b; return; }
+    const dfb_chan* C = &P->chans[k + 1][ci];
+    if (k == 1) { *r = a; *c = 2 * b + ((a + C->o_r + C->o_c) & 1); return; }
+    int R = C->T == 0 ? (1 << (k - 1)) : 2;
+    int Cc = C->T == 0 ? 2 : (1 << (k - 1));
+    *r = wrapi((long)wrapi(C->o_r, R) + (long)R * a, H);
+    *c = wrapi((long)wrapi(C->o_c, Cc) + (long)Cc * b, W);
+}
+
+static void dfb_leaf_dims(const dfb_plan* P, int ci, int* h, int* w) {
+    int k = P->k, H = P->H, W = P->W;
+    if (k == 0) { *h = H; *w = W; return; }
+    if (k == 1) { *h = H; *w = W / 2; return; }
+    if (P->chans[k + 1][ci].T == 0) { *h = H >> (k - 1); *w = W / 2; }
+    else { *h = H / 2; *w = W >> (k - 1); }
+}
+
+int or_dfb(int mode, const double* in, int H, int W, int k, double* out) {
+    if (k < 0 || k > OR_MAX_K) return OR_EINVAL;
+    int need = k >= 2 ? (1 << (k - 1)) : 2;
+    if (k > 0 && (H % need || W % need)) return OR_EINVAL;
+    long np = (long)H * W;
+    if (k == 0) { memcpy(out, in, sizeof(double) * np); return OR_OK; }
+    dfb_plan P;
+    dfb_plan_make(&P, H, W, k);
+    double* x = (double*)malloc(sizeof(double) * np);
+    int nl = 1 << k;
+    if (mode == 0 || mode == 3) {
+        /* analysis direction, stages 1..k */
+        memcpy(x, in, sizeof(double) * np);
+        for (int s = 1; s <= k; s++) {
+            if (mode == 0) {            /* forward: predict odd, then update even */
+                dfb_pass(&P, x, s, 1, 0.5, -0.5);
+                dfb_pass(&P, x, s, 0, 1.0, 1.0);
+            } else {                    /* transpose of the inverse stage */
+                dfb_pass(&P, x, s, 0, 1.0, 1.0);
+                dfb_pass(&P, x, s, 1, 2.0, -1.0);
+            }
+        }
+        long o = 0;
+        for (int ci = 0; ci < nl; ci++) {
+            int h, w;
+            dfb_leaf_dims(&P, ci, &h, &w);
+            for (int a = 0; a < h; a++)
+                for (int b = 0; b < w; b++) {
+                    int r, c;
+                    dfb_leaf_pos(&P, ci, a, b, &r, &c);
+                    out[o++] = x[(long)r * W + c];
+                }
+        }
+    } else {
+        /* synthesis direction, stages k..1 */
+        long o = 0;
+        for (int ci = 0; ci < nl; ci++) {
+            int h, w;
+            dfb_leaf_dims(&P, ci, &h, &w);
+            for (int a = 0; a < h; a++)
+                for (int b = 0; b < w; b++) {
+                    int r, c;
+                    dfb_leaf_pos(&P, ci, a, b, &r, &c);
+                    x[(long)r * W + c] = in[o++];
+                }
+        }
+        for (int s = k; s >= 1; s--) {
+            if (mode == 1) {            /* inverse: undo update, then undo predict */
+                dfb_pass(&P, x, s, 0, 1.0, -1.0);
+                dfb_pass(&P, x, s, 1, 2.0, 1.0);
+            } else {                    /* transpose of the forward stage */
+                dfb_pass(&P, x, s, 1, 0.5, 0.5);
+                dfb_pass(&P, x, s, 0, 1.0, -1.0);
+            }
+        }
+        memcpy(out, x, sizeof(double) * np);
+    }
+    free(x);
+    dfb_plan_free(&P);
+    return OR_OK;
+}
+
+/* ------------------------------------------------- contourlet transform
+ * §2.1 / Fig. 1: the LP is iterated on the lowpass; every LP detail d_j
+ * feeds a DFB with k_j stages.  Modes: 0 forward A, 1 inverse S,
+ * 2 adjoint A^T, 3 adjoint S^T.                                             */
+int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double* out) {
+    or_layout lay;
+    int st = or_layout_make(H, W, L, k, &lay);
+    if (st) return st;
+    double* cur = (double*)malloc(sizeof(double) * (size_t)H * W);
+    double* det = (double*)malloc(sizeof(double) * (size_t)H * W);
+    double* nxt = (double*)malloc(sizeof(double) * (size_t)H * W);
+    if (mode == 0 || mode == 3) {
+        memcpy(cur, in, sizeof(double) * (size_t)H * W);
+        long off = lay.sb[0].h * (long)lay.sb[0].w;
+        for (int j = 1; j <= L; j++) {
+            int Hj = H >> (j - 1), Wj = W >> (j - 1);
+            if (mode == 0) or_lp_analysis(cur, Hj, Wj, nxt, det);
+            else or_lp_synthesis_adjoint(cur, Hj, Wj, nxt, det);
+            st = or_dfb(mode, det, Hj, Wj, k[j - 1], out + off);
+            if (st) break;
+            off += (long)Hj * Wj;
+            double* t = cur; cur = nxt; nxt = t;
+        }
+        memcpy(out, cur, sizeof(double) * lay.sb[0].h * (long)lay.sb[0].w);
+    } else {
+        memcpy(cur, in, sizeof(double) * lay.sb[0].h * (long)lay.sb[0].w);
+        long offs[OR_MAX_LEVELS + 1];
+        long off = lay.sb[0].h * (long)lay.sb[0].w;
+        for (int j = 1; j <= L; j++) { offs[j] = off; off += (long)(H >> (j - 1)) * (W >> (j - 1)); }
+        for (int j = L; j >= 1; j--) {
+            int Hj = H >> (j - 1), Wj = W >> (j - 1);
+            st = or_dfb(mode, in + offs[j], Hj, Wj, k[j - 1], det);
+            if (st) break;
+            if (mode == 1) or_lp_synthesis(cur, det, Hj, Wj, nxt);
+            else or_lp_analysis_adjoint(cur, det, Hj, Wj, nxt);
+            double* t = cur; cur = nxt; nxt = t;
+        }
+        memcpy(out, cur, sizeof(double) * (size_t)H * W);
+    }
+    free(cur); free(det); free(nxt);
+    return st;
+}
+
+/* --------------------------------------------------------------- colour
+ * Table 1 (Eq. 1-6) in its integer lifting form YCoCg-R (lossless):
+ *   Co = R - B,  t = B + floor(Co/2),  Cg = G - t,  Y = t + floor(Cg/2)
+ *   t = Y - floor(Cg/2),  G = Cg + t,  B = t - floor(Co/2),  R = B + Co
+ * Decoded values are clamped to [0, 255].                                   */
+void or_ycocgr_forward(const uint8_t* rgb, long n, int16_t* y, int16_t* co, int16_t* cg) {
+    for (long i = 0; i < n; i++) {
+        long R = rgb[3 * i], G = rgb[3 * i + 1], B = rgb[3 * i + 2];
+        long Co = R - B;
+        long t = B + floordiv(Co, 2);
+        long Cg = G - t;
+        long Y = t + floordiv(Cg, 2);
+        y[i] = (int16_t)Y; co[i] = (int16_t)Co; cg[i] = (int16_t)Cg;
+    }
+}
+
+static int clampi(long v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : (int)v); }
+
+void or_ycocgr_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, long n, uint8_t* rgb) {
+    for (long i = 0; i < n; i++) {
+        long t = (long)y[i] - floordiv(cg[i], 2);
+        long G = cg[i] + t;
+        long B = t - floordiv(co[i], 2);
+        long R = B + co[i];
+        rgb[3 * i] = (uint8_t)clampi(R, 0, 255);
+        rgb[3 * i + 1] = (uint8_t)clampi(G, 0, 255);
+        rgb[3 * i + 2] = (uint8_t)clampi(B, 0, 255);
+    }
+}
+
+/* §3.1 chroma subsampling, factor N = 4 read as 2 x 2: rounded mean of each
+ * 2x2 block, floor((s + 2) / 4); odd sizes replicate the last row / column. */
+void or_chroma_down(const int16_t* in, int H, int W, int16_t* out) {
+    int Hc = (H + 1) / 2, Wc = (W + 1) / 2;
+    for (int i = 0; i < Hc; i++)
+        for (int j = 0; j < Wc; j++) {
+            int r0 = 2 * i, r1 = 2 * i + 1 < H ? 2 * i + 1 : H - 1;
+            int c0 = 2 * j, c1 = 2 * j + 1 < W ? 2 * j + 1 : W - 1;
+            long s = (long)in[(long)r0 * W + c0] + in[(long)r0 * W + c1] + in[(long)r1 * W + c0] + in[(long)r1 * W + c1];
+            out[(long)i * Wc + j] = (int16_t)floordiv(s + 2, 4);
+        }
+}
+
+/* §3.1 decoder: bilinear interpolation from the four neighbouring chroma
+ * samples.  Centred siting: full-resolution row y sits at chroma row
+ * (y - 1/2)/2, so even rows weigh rows (i-1, i) by (1/4, 3/4) and odd rows
+ * rows (i, i+1) by (3/4, 1/4); indices clamp at the edges.  2-D weights
+ * (9,3,3,1)/16 with rounding: floor((9a + 3b + 3c + d + 8) / 16).           */
+void or_chroma_up(const int16_t* in, int Hc, int Wc, int H, int W, int16_t* out) {
+    for (int y = 0; y < H; y++) {
+        int i0 = y / 2, i1 = (y & 1) ? i0 + 1 : i0 - 1;
+        if (i1 < 0) i1 = 0;
+        if (i1 > Hc - 1) i1 = Hc - 1;
+        if (i0 > Hc - 1) i0 = Hc - 1;
+        for (int x = 0; x < W; x++) {
+            int j0 = x / 2, j1 = (x & 1) ? j0 + 1 : j0 - 1;
+            if (j1 < 0) j1 = 0;
+            if (j1 > Wc - 1) j1 = Wc - 1;
+            if (j0 > Wc - 1) j0 = Wc - 1;
+            long s = 9L * in[(long)i0 * Wc + j0] + 3L * in[(long)i1 * Wc + j0] + 3L * in[(long)i0 * Wc + j1] + in[(long)i1 * Wc + j1];
+            out[(long)y * W + x] = (int16_t)floordiv(s + 8, 16);
+        }
+    }
+}
+
+/* plane padding to the layout modulus: half-sample symmetric mirror at the
+ * bottom and right edges, x[H + i] = x[H - 1 - i] (the paper is silent).   */
+void or_pad_mirror(const double* in, int H, int W, int Hp, int Wp, double* out) {
+    for (int r = 0; r < Hp; r++) {
+        int sr = r < H ? r : 2 * H - 1 - r;
+        for (int c = 0; c < Wp; c++) {
+            int sc = c < W ? c : 2 * W - 1 - c;
+            out[(long)r * Wp + c] = in[(long)sr * W + sc];
+        }
+    }
+}
+
+/* ------------------------------------------------------------ quantiser
+ * §3.5 divide by QPH (subbands) or QPL (lowpass), §3.6 round to the nearest
+ * integer (ties away from zero).  The lowpass is first normalised (§3.4) by
+ * the exact factor 2^-L; subband coefficients below the threshold magnitude
+ * are set to zero first.  Decision in single precision; |q| > 32767 is an
+ * overflow of the int16 code.                                               */
+int or_quantize(float c, int qp, float threshold, int is_lowpass, int levels, int* ovf) {
+    float t;
+    if (is_lowpass) t = ldexpf(c, -levels);
+    else t = (fabsf(c) >= threshold) ? c : 0.0f;
+    float v = roundf(t / (float)qp);
+    if (!(fabsf(v) <= 32767.0f)) { *ovf = 1; return 0; }
+    return (int)v;
+}
+
+/* ------------------------------------------------------------------ RLE
+ * §3.8: zero runs are coded along the horizontal direction; rows are coded
+ * independently.  A non-zero value v is the token v; a maximal run of n
+ * zeros is the token pair (0, n).                                           */
+long or_rle_row(const int16_t* row, int w, int16_t* tokens) {
+    long n = 0;
+    int x = 0;
+    while (x < w) {
+        if (row[x] != 0) { tokens[n++] = row[x]; x++; continue; }
+        int run = 0;
+        while (x < w && row[x] == 0) { run++; x++; }
+        tokens[n++] = 0;
+        tokens[n++] = (int16_t)run;
+    }
+    return n;
+}
+
+int or_rle_expand(const int16_t* tokens, long ntok, int16_t* out, long n) {
+    long pos = 0, t = 0;
+    while (t < ntok) {
+        if (tokens[t] != 0) {
+            if (pos >= n) return OR_ECORRUPT;
+            out[pos++] = tokens[t++];
+            continue;
+        }
+        if (t + 1 >= ntok) return OR_ECORRUPT;
+        long run = tokens[t + 1];
+        if (run <= 0 || pos + run > n) return OR_ECORRUPT;
+        for (long i = 0; i < run; i++) out[pos++] = 0;
+        t += 2;
+    }
+    return pos == n ? OR_OK : OR_ECORRUPT;
+}
+
+/* ---------------------------------------------------------------- codec */
+struct or_codec {
+    int Wo, Ho, L, k[OR_MAX_LEVELS], qph, qpl, kint;
+    float thr;
+    int Hp, Wp, Hc, Wc, Hcp, Wcp;
+    or_layout ly, lc;
+    long ncoef;
+    int ncomp;
+    int16_t* enc_state;
+    int16_t* dec_state;
+    long enc_frame;
+    long dec_next;  /* index the next P-frame must carry; -1: a K-frame is required */
+};
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+or_codec* or_codec_create(int width, int height, int levels, const int* dirs, int qph, int qpl,
+                          float threshold, int key_interval) {
+    if (width <= 0 || height <= 0 || width > 65535 || height > 65535) return NULL;
+    if (levels < 1 || levels > OR_MAX_LEVELS) return NULL;
+    if (qph < 1 || qph > 181 || qpl < 1 || qpl > 71 || key_interval < 1) return NULL;
+    if (!(threshold >= 0.0f)) return NULL;
+    or_codec* c = (or_codec*)calloc(1, sizeof(or_codec));
+    c->Wo = width; c->Ho = height; c->L = levels; c->qph = qph; c->qpl = qpl;
+    c->thr = threshold; c->kint = key_interval;
+    for (int j = 0; j < levels; j++) c->k[j] = dirs[j];
+    int M = or_modulus(levels, c->k);
+    c->Hp = round_up(height, M); c->Wp = round_up(width, M);
+    c->Hc = (height + 1) / 2; c->Wc = (width + 1) / 2;
+    c->Hcp = round_up(c->Hc, M); c->Wcp = round_up(c->Wc, M);
+    /* the mirror reaches back at most one plane height */
+    if (c->Hp > 2 * height || c->Wp > 2 * width || c->Hcp > 2 * c->Hc || c->Wcp > 2 * c->Wc ||
+        or_layout_make(c->Hp, c->Wp, levels, c->k, &c->ly) ||
+        or_layout_make(c->Hcp, c->Wcp, levels, c->k, &c->lc)) {
+        free(c);
+        return NULL;
+    }
+    c->ncoef = c->ly.total + 2 * c->lc.total;
+    c->ncomp = c->ly.nsub + 2 * c->lc.nsub;
+    c->enc_state = (int16_t*)calloc((size_t)c->ncoef, sizeof(int16_t));
+    c->dec_state = (int16_t*)calloc((size_t)c->ncoef, sizeof(int16_t));
+    or_codec_reset(c);
+    return c;
+}
+
+void or_codec_destroy(or_codec* c) {
+    if (!c) return;
+    free(c->enc_state); free(c->dec_state); free(c);
+}
+void or_codec_reset(or_codec* c) { c->enc_frame = 0; c->dec_next = -1; }
+long or_codec_coeff_count(const or_codec* c) { return c->ncoef; }
+int or_codec_ncomp(const or_codec* c) { return c->ncomp; }
+long or_codec_max_stream(const or_codec* c) { return 32 + 4L * c->ncomp + 2L * 2L * c->ncoef; }
+void or_codec_dims(const or_codec* c, int* out) { out[0] = c->Hp; out[1] = c->Wp; out[2] = c->Hcp; out[3] = c->Wcp; }
+
+void or_codec_planes(const or_codec* c, const uint8_t* rgb, double* y, double* co, double* cg) {
+    long n = (long)c->Ho * c->Wo, nc = (long)c->Hc * c->Wc;
+    int16_t* Y = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Co = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Cg = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Co2 = (int16_t*)malloc(sizeof(int16_t) * nc);
+    int16_t* Cg2 = (int16_t*)malloc(sizeof(int16_t) * nc);
+    double* t = (double*)malloc(sizeof(double) * n);
+    or_ycocgr_forward(rgb, n, Y, Co, Cg);
+    or_chroma_down(Co, c->Ho, c->Wo, Co2);
+    or_chroma_down(Cg, c->Ho, c->Wo, Cg2);
+    for (long i = 0; i < n; i++) t[i] = Y[i];
+    or_pad_mirror(t, c->Ho, c->Wo, c->Hp, c->Wp, y);
+    for (long i = 0; i < nc; i++) t[i] = Co2[i];
+    or_pad_mirror(t, c->Hc, c->Wc, c->Hcp, c->Wcp, co);
+    for (long i = 0; i < nc; i++) t[i] = Cg2[i];
+    or_pad_mirror(t, c->Hc, c->Wc, c->Hcp, c->Wcp, cg);
+    free(Y); free(Co); free(Cg); free(Co2); free(Cg2); free(t);
+}
+
+static void put16(uint8_t* p, unsigned v) { p[0] = (uint8_t)(v & 255); p[1] = (uint8_t)((v >> 8) & 255); }
+static void put32(uint8_t* p, unsigned long v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)((v >> (8 * i)) & 255); }
+static unsigned get16(const uint8_t* p) { return (unsigned)p[0] | ((unsigned)p[1] << 8); }
+static unsigned long get32(const uint8_t* p) {
+    return (unsigned long)p[0] | ((unsigned long)p[1] << 8) | ((unsigned long)p[2] << 16) | ((unsigned long)p[3] << 24);
+}
+
+/* component j of the frame: plane index and subband */
+static const or_subband* comp_sb(const or_codec* c, int j, long* base) {
+    if (j < c->ly.nsub) { *base = 0; return &c->ly.sb[j]; }
+    j -= c->ly.nsub;
+    int p = j / c->lc.nsub;
+    *base = c->ly.total + p * c->lc.total;
+    return &c->lc.sb[j % c->lc.nsub];
+}
+
+/* §3.7: frame i (counted from the last reset) is a K-frame iff i is a
+ * multiple of the key interval.  K-frame: every lowpass column is replaced by
+ * its first difference (each element minus the element above), subbands pass
+ * unchanged.  P-frame: every component is the difference between the current
+ * and the previous frame's codes (zero motion).  Differences wrap in 16 bits;
+ * the coder state is the current frame's codes.  §3.8: K-frame lowpass is
+ * stored raw, every other component is run-length coded.                    */
+int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long cap,
+                          long* out_len, int* frame_type) {
+    int type = (c->enc_frame % c->kint) == 0 ? 0 : 1;
+    int16_t* q = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+    int16_t* r = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+    int ovf = 0;
+    for (int j = 0; j < c->ncomp; j++) {
+        long base;
+        const or_subband* s = comp_sb(c, j, &base);
+        int low = s->kind == 0;
+        for (long e = 0; e < (long)s->h * s->w; e++) {
+            long idx = base + s->off + e;
+            q[idx] = (int16_t)or_quantize(coeffs[idx], low ? c->qpl : c->qph, c->thr, low, c->L, &ovf);
+        }
+    }
+    if (ovf) { free(q); free(r); return OR_EOVERFLOW; }
+    for (int j = 0; j < c->ncomp; j++) {
+        long base;
+        const or_subband* s = comp_sb(c, j, &base);
+        for (int a = 0; a < s->h; a++)
+            for (int b = 0; b < s->w; b++) {
+                long idx = base + s->off + (long)a * s->w + b;
+                int v;
+                if (type == 1) v = q[idx] - c->enc_state[idx];
+                else if (s->kind == 0 && a > 0) v = q[idx] - q[idx - s->w];
+                else v = q[idx];
+                r[idx] = (int16_t)(uint16_t)(v & 0xFFFF);
+            }
+    }
+    /* bitstream: 32-byte header, ncomp u32 token counts, int16 tokens */
+    long need = 32 + 4L * c->ncomp;
+    int16_t* tok = (int16_t*)malloc(sizeof(int16_t) * (size_t)(2 * c->ncoef + 16));
+    long* counts = (long*)calloc((size_t)c->ncomp, sizeof(long));
+    long nt = 0;
+    for (int j = 0; j < c->ncomp; j++) {
+        long base;
+        const or_subband* s = comp_sb(c, j, &base);
+        long start = nt;
+        if (type == 0 && s->kind == 0) {
+            for (long e = 0; e < (long)s->h * s->w; e++) tok[nt++] = r[base + s->off + e];
+        } else {
+            for (int a = 0; a < s->h; a++) nt += or_rle_row(r + base + s->off + (long)a * s->w, s->w, tok + nt);
+        }
+        counts[j] = nt - start;
+    }
+    need += 2 * nt;
+    *out_len = need;
+    if (frame_type) *frame_type = type;
+    if (need > cap) { free(q); free(r); free(tok); free(counts); return OR_ECAPACITY; }
+    memset(out, 0, 32);
+    out[0] = 'C'; out[1] = 'V'; out[2] = 'C'; out[3] = '1';
+    put16(out + 4, 1);
+    out[6] = (uint8_t)type;
+    out[7] = (uint8_t)c->L;
+    put32(out + 8, (unsigned long)c->enc_frame);
+    put16(out + 12, (unsigned)c->Ho);
+    put16(out + 14, (unsigned)c->Wo);
+    for (int j = 0; j < c->L; j++) out[16 + j] = (uint8_t)c->k[j];
+    put16(out + 22, (unsigned)c->qph);
+    put16(out + 24, (unsigned)c->qpl);
+    put32(out + 28, (unsigned long)c->ncomp);
+    for (int j = 0; j < c->ncomp; j++) put32(out + 32 + 4 * j, (unsigned long)counts[j]);
+    uint8_t* tp = out + 32 + 4 * c->ncomp;
+    for (long i = 0; i < nt; i++) put16(tp + 2 * i, (unsigned)(uint16_t)tok[i]);
+    memcpy(c->enc_state, q, sizeof(int16_t) * (size_t)c->ncoef);
+    c->enc_frame += 1;
+    free(q); free(r); free(tok); free(counts);
+    return OR_OK;
+}
+
+int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out_len,
+              int* frame_type, double* coeffs_out) {
+    long ny = (long)c->Hp * c->Wp, nc = (long)c->Hcp * c->Wcp;
+    double* pl = (double*)malloc(sizeof(double) * (size_t)(ny + 2 * nc));
+    double* co = (double*)malloc(sizeof(double) * (size_t)c->ncoef);
+    or_codec_planes(c, rgb, pl, pl + ny, pl + ny + nc);
+    or_ct(0, pl, c->Hp, c->Wp, c->L, c->k, co);
+    or_ct(0, pl + ny, c->Hcp, c->Wcp, c->L, c->k, co + c->ly.total);
+    or_ct(0, pl + ny + nc, c->Hcp, c->Wcp, c->L, c->k, co + c->ly.total + c->lc.total);
+    float* cf = (float*)malloc(sizeof(float) * (size_t)c->ncoef);
+    for (long i = 0; i < c->ncoef; i++) cf[i] = (float)co[i];
+    if (coeffs_out) memcpy(coeffs_out, co, sizeof(double) * (size_t)c->ncoef);
+    int st = or_encode_from_coeffs(c, cf, out, cap, out_len, frame_type);
+    free(pl); free(co); free(cf);
+    return st;
+}
+
+/* §3.9 / decoding: undo RLE, undo the frame-type differencing, dequantise
+ * (lowpass also rescaled by 2^L), inverse CT, crop the padding, round (ties
+ * away from zero, single precision) and clamp: Y to [0,255], Co/Cg to
+ * [-255,255]; upsample the chroma and invert the colour transform.          */
+int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* planes_out) {
+    if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
+    if (get16(in + 4) != 1) return OR_ECORRUPT;
+    int type = in[6];
+    if (type > 1 || in[7] != c->L || get16(in + 12) != (unsigned)c->Ho || get16(in + 14) != (unsigned)c->Wo)
+        return OR_ECORRUPT;
+    for (int j = 0; j < c->L; j++) if (in[16 + j] != c->k[j]) return OR_ECORRUPT;
+    if (get16(in + 22) != (unsigned)c->qph || get16(in + 24) != (unsigned)c->qpl) return OR_ECORRUPT;
+    if (get32(in + 28) != (unsigned long)c->ncomp) return OR_ECORRUPT;
+    long fidx = (long)get32(in + 8);
+    if (type == 1 && fidx != c->dec_next) return OR_ESTATE;
+    if (len < 32 + 4L * c->ncomp) return OR_ECORRUPT;
+    long nt = 0;
+    for (int j = 0; j < c->ncomp; j++) nt += (long)get32(in + 32 + 4 * j);
+    if (32 + 4L * c->ncomp + 2 * nt > len) return OR_ECORRUPT;
+    const uint8_t* tp = in + 32 + 4 * c->ncomp;
+    int16_t* r = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+    int16_t* q = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+    long t0 = 0;
+    int st = OR_OK;
+    for (int j = 0; j < c->ncomp && st == OR_OK; j++) {
+        long base, cnt = (long)get32(in + 32 + 4 * j);
+        const or_subband* s = comp_sb(c, j, &base);
+        long n = (long)s->h * s->w;
+        int16_t* tk = (int16_t*)malloc(sizeof(int16_t) * (size_t)(cnt + 1));
+        for (long i = 0; i < cnt; i++) tk[i] = (int16_t)get16(tp + 2 * (t0 + i));
+        if (type == 0 && s->kind == 0) {
+            if (cnt != n) st = OR_ECORRUPT;
+            else memcpy(r + base + s->off, tk, sizeof(int16_t) * (size_t)n);
+        } else {
+            st = or_rle_expand(tk, cnt, r + base + s->off, n);
+        }
+        free(tk);
+        t0 += cnt;
+    }
+    if (st) { free(r); free(q); return st; }
+    for (int j = 0; j < c->ncomp; j++) {
+        long base;
+        const or_subband* s = comp_sb(c, j, &base);
+        for (int a = 0; a < s->h; a++)
+            for (int b = 0; b < s->w; b++) {
+                long idx = base + s->off + (long)a * s->w + b;
+                int v;
+                if (type == 1) v = r[idx] + c->dec_state[idx];
+                else if (s->kind == 0 && a > 0) v = r[idx] + q[idx - s->w];
+                else v = r[idx];
+                q[idx] = (int16_t)(uint16_t)(v & 0xFFFF);
+            }
+    }
+    double* co = (double*)malloc(sizeof(double) * (size_t)c->ncoef);
+    for (int j = 0; j < c->ncomp; j++) {
+        long base;
+        const or_subband* s = comp_sb(c, j, &base);
+        double scale = s->kind == 0 ? ldexp((double)c->qpl, c->L) : (double)c->qph;
+        for (long e = 0; e < (long)s->h * s->w; e++) co[base + s->off + e] = q[base + s->off + e] * scale;
+    }
+    long ny = (long)c->Hp * c->Wp, nc = (long)c->Hcp * c->Wcp;
+    double* pl = (double*)malloc(sizeof(double) * (size_t)(ny + 2 * nc));
+    or_ct(1, co, c->Hp, c->Wp, c->L, c->k, pl);
+    or_ct(1, co + c->ly.total, c->Hcp, c->Wcp, c->L, c->k, pl + ny);
+    or_ct(1, co + c->ly.total + c->lc.total, c->Hcp, c->Wcp, c->L, c->k, pl + ny + nc);
+    if (planes_out) memcpy(planes_out, pl, sizeof(double) * (size_t)(ny + 2 * nc));
+    long n = (long)c->Ho * c->Wo, ncs = (long)c->Hc * c->Wc;
+    int16_t* Y = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Co = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Cg = (int16_t*)malloc(sizeof(int16_t) * n);
+    int16_t* Co2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
+    int16_t* Cg2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
+    for (int y = 0; y < c->Ho; y++)
+        for (int x = 0; x < c->Wo; x++)
+            Y[(long)y * c->Wo + x] = (int16_t)clampi((long)roundf((float)pl[(long)y * c->Wp + x]), 0, 255);
+    for (int y = 0; y < c->Hc; y++)
+        for (int x = 0; x < c->Wc; x++) {
+            Co2[(long)y * c->Wc + x] = (int16_t)clampi((long)roundf((float)pl[ny + (long)y * c->Wcp + x]), -255, 255);
+            Cg2[(long)y * c->Wc + x] = (int16_t)clampi((long)roundf((float)pl[ny + nc + (long)y * c->Wcp + x]), -255, 255);
+        }
+    or_chroma_up(Co2, c->Hc, c->Wc, c->Ho, c->Wo, Co);
+    or_chroma_up(Cg2, c->Hc, c->Wc, c->Ho, c->Wo, Cg);
+    or_ycocgr_inverse(Y, Co, Cg, n, rgb);
+    memcpy(c->dec_state, q, sizeof(int16_t) * (size_t)c->ncoef);
+    c->dec_next = fidx + 1;
+    free(r); free(q); free(co); free(pl); free(Y); free(Co); free(Cg); free(Co2); free(Cg2);
+    return OR_OK;
+}

@@ -1,0 +1,112 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle of the CVC contourlet codec hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this code; only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * Every function follows one step of the method of Katsigiannis,
+ * Papaioannou and Maroulis, "CVC: The Contourlet Video Compression
+ * algorithm for real-time applications" (arXiv:1510.00561); the comment
+ * above each definition names the section / equation / table it restates
+ * and, where the paper is silent, the reading it takes.
+ *
+ * Floating point is double precision throughout, except where a float
+ * value decides an integer (the quantiser, the final pixel rounding): that
+ * decision is taken in single precision, the precision of the GPU path.
+ */
+#ifndef CVC_ORACLE_H
+#define CVC_ORACLE_H
+#include <stdint.h>
+
+#define OR_MAX_LEVELS 6
+#define OR_MAX_K 6
+#define OR_MAX_SUB (1 + OR_MAX_LEVELS * 64)
+
+/* status codes of the oracle (its own numbering) */
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_ECAPACITY 3
+#define OR_EOVERFLOW 4
+#define OR_ECORRUPT 5
+#define OR_ESTATE 9
+
+typedef struct {
+    long off;   /* element offset inside the plane's coefficient block */
+    int h, w;   /* subband rows, columns                               */
+    int level;  /* 0 = lowpass, 1 = finest LP level ... L = coarsest    */
+    int dir;    /* direction index in tree order (lowpass: 0)           */
+    int kind;   /* 0 lowpass, 1 F_c wedge, 2 F_r wedge, 3 undivided detail (k=0), 4 quincunx half (k=1) */
+} or_subband;
+
+typedef struct {
+    int H, W, L, k[OR_MAX_LEVELS];
+    int nsub;                 /* lowpass + all directional subbands */
+    or_subband sb[OR_MAX_SUB];
+    long total;               /* coefficients of one plane */
+} or_layout;
+
+int or_modulus(int L, const int* k);
+int or_layout_make(int H, int W, int L, const int* k, or_layout* out);
+
+/* CDF 9/7 lowpass pair: h[0..8] = analysis taps at -4..4, g[0..6] = synthesis taps at -3..3 */
+void or_cdf97(double* h, double* g);
+
+/* Laplacian pyramid, one level (periodic extension), and adjoints */
+void or_lp_analysis(const double* x, int H, int W, double* c, double* d);
+void or_lp_synthesis(const double* c, const double* d, int H, int W, double* x);
+void or_lp_analysis_adjoint(const double* cbar, const double* dbar, int H, int W, double* xbar);
+void or_lp_synthesis_adjoint(const double* xbar, int H, int W, double* cbar, double* dbar);
+
+/* directional filter bank with k stages on an H x W detail image.
+ * mode 0: forward (analysis), 1: inverse, 2: adjoint of forward, 3: adjoint of inverse.
+ * analysis direction (modes 0,3): plane -> subbands concatenated in tree order.
+ * synthesis direction (modes 1,2): subbands -> plane.                              */
+int or_dfb(int mode, const double* in, int H, int W, int k, double* out);
+
+/* full contourlet transform on one plane, modes as above; coefficient layout of or_layout */
+int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double* out);
+
+/* colour, chroma and padding steps */
+void or_ycocgr_forward(const uint8_t* rgb, long n, int16_t* y, int16_t* co, int16_t* cg);
+void or_ycocgr_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, long n, uint8_t* rgb);
+void or_chroma_down(const int16_t* in, int H, int W, int16_t* out);
+void or_chroma_up(const int16_t* in, int Hc, int Wc, int H, int W, int16_t* out);
+void or_pad_mirror(const double* in, int H, int W, int Hp, int Wp, double* out);
+
+/* quantiser of one value, single-precision decision (returns 0 on overflow flag set) */
+int or_quantize(float c, int qp, float threshold, int is_lowpass, int levels, int* ovf);
+
+/* run-length coding of one row; returns tokens written */
+long or_rle_row(const int16_t* row, int w, int16_t* tokens);
+/* expand one component's tokens into n elements; returns OR_OK or OR_ECORRUPT */
+int or_rle_expand(const int16_t* tokens, long ntok, int16_t* out, long n);
+
+/* ---------------------------------------------------------------- codec */
+typedef struct or_codec or_codec;
+or_codec* or_codec_create(int width, int height, int levels, const int* dirs, int qph, int qpl,
+                          float threshold, int key_interval);
+void or_codec_destroy(or_codec* c);
+void or_codec_reset(or_codec* c);
+long or_codec_coeff_count(const or_codec* c);      /* coefficients of the 3 planes */
+long or_codec_max_stream(const or_codec* c);       /* worst-case stream bytes      */
+int or_codec_ncomp(const or_codec* c);
+/* padded plane sizes: out[0..3] = Hp, Wp, Hcp, Wcp */
+void or_codec_dims(const or_codec* c, int* out);
+
+/* colour + chroma + pad of one frame: float planes Y (Hp x Wp), Co, Cg (Hcp x Wcp) */
+void or_codec_planes(const or_codec* c, const uint8_t* rgb, double* y, double* co, double* cg);
+
+/* the entropy side of the encoder from given single-precision coefficients:
+ * threshold, quantise, K/P differencing, state update, RLE, bitstream.      */
+int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long cap,
+                          long* out_len, int* frame_type);
+/* full encode: planes -> CT (FP64) -> single-precision decision -> entropy side.
+ * coeffs_out (optional, FP64, or_codec_coeff_count values) receives the CT output. */
+int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out_len,
+              int* frame_type, double* coeffs_out);
+/* full decode; planes_out (optional, FP64) receives the reconstructed padded planes */
+int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* planes_out);
+
+#endif
