@@ -1,0 +1,351 @@
+"""Benchmark: 1080p CVC encode + decode throughput on the GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: seeded synthetic 1920x1080 RGB video (12 textured moving objects on
+a smooth background, Gaussian noise sigma 3), YCoCg-R + 4:2:0, contourlet
+transform with 5 LP levels (CDF 9/7) and 32/16/16/8/8 directions, step 8
+(QPH 8, QPL 1), key frame every 10 frames, RLE bitstream.  One step encodes
+and decodes one frame of every stream this rank serves (plain path: one
+cvc_encode_frame + one cvc_decode_frame per frame, stream ordered).
+
+N > 1 (torchrun): every rank serves its own independent streams (the codec
+shards by stream; there is no exchange step), so scaling is weak.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a horizontal band of the same frames and decomposition).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_, H_, LEVELS, DIRS, QPH, QPL, KINT = 1920, 1080, 5, [5, 4, 4, 3, 3], 8, 1, 10
+METRIC = "1080p encode+decode frames/s"
+UNIT = "frames/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _gen_frames(seed, n, start=0):
+    from paper_1510_00561_b300 import synthetic as S
+    v = S.SyntheticVideo(S.spec_for(W_, H_, seed=seed))
+    return [v.frame(start + t) for t in range(n)]
+
+
+def _gen_one(args):
+    seed, t = args
+    from paper_1510_00561_b300 import synthetic as S
+    return S.SyntheticVideo(S.spec_for(W_, H_, seed=seed)).frame(t)
+
+
+def make_frames(seed, n):
+    """Frames of one stream, drawn in a spawn pool (safe before or after CUDA init)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = max(1, min(n, (os.cpu_count() or 2) - 1, 16))
+    if workers == 1:
+        return _gen_frames(seed, n)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_one, [(seed, t) for t in range(n)]))
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), source="measured")
+    except Exception:
+        return dict(hbm_gbs=6400.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def stage_bytes(codec, tokens):
+    """Algorithmic HBM bytes per frame of each stage ('Roofline')."""
+    N = W_ * H_
+    P = [(codec.Hp, codec.Wp), (codec.Hcp, codec.Wcp), (codec.Hcp, codec.Wcp)]
+    C = codec.ncoef
+    lp = 0
+    dfb = 0
+    for (h, w) in P:
+        for j in range(1, LEVELS + 1):
+            pj = (h >> (j - 1)) * (w >> (j - 1))
+            lp += 4 * (pj + pj // 4 + pj)               # read level input, write lowpass + detail
+            dfb += DIRS[j - 1] * 2 * 4 * (3 * pj // 2)  # per stage: two passes, each reads 2 and writes 1 coset
+    nplane = codec.nplane
+    return {
+        "colour_fwd": 3 * N + 4 * nplane,
+        "lp_analysis": lp,
+        "dfb_analysis": dfb,
+        "quantise_kp": 4 * C + 2 * C + 2 * C + 2 * C,
+        "rle_stream": 2 * C + 2 * C + 2 * tokens,
+        "parse_unrle": 2 * tokens + 2 * C,
+        "unquantise_kp": 2 * C + 2 * C + 2 * C + 4 * C,
+        "dfb_synthesis": dfb,
+        "lp_synthesis": lp,
+        "colour_inv": 4 * N + 2 * 4 * N // 4 + 3 * N,
+    }
+
+
+def cpu_oracle_rate(frames, band_rows=None, seconds_cap=30.0):
+    """Oracle encode+decode frames/s on host cores (single thread), on a bounded
+    sample: whole frames, or horizontal bands of band_rows rows of them."""
+    import numpy as np
+    import oracle as O
+    rows = band_rows or H_
+    cod = O.Codec(W_, rows, LEVELS, DIRS, QPH, QPL, 0.0, KINT)
+    done = 0
+    t0 = time.perf_counter()
+    for f in frames:
+        s, _ = cod.encode(np.ascontiguousarray(f[:rows]))
+        cod.decode(s)
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    dt = time.perf_counter() - t0
+    return done * rows / H_ / dt, done, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    # size the band so that the whole run takes about two minutes (one 1080p frame ~ 6 s)
+    per_step = min(6.5, 120.0 / max(1, steps + warm))
+    band = max(64, min(1088, int(per_step / 6.5 * 1088) // 64 * 64))
+    frames = _gen_frames(0, min(steps + warm, 12))
+    import numpy as np
+    import oracle as O
+    cod = O.Codec(W_, band, LEVELS, DIRS, QPH, QPL, 0.0, KINT)
+    for i in range(warm):
+        s, _ = cod.encode(np.ascontiguousarray(frames[i % len(frames)][:band]))
+        cod.decode(s)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        s, _ = cod.encode(np.ascontiguousarray(frames[(warm + i) % len(frames)][:band]))
+        cod.decode(s)
+    dt = time.perf_counter() - t0
+    value = steps * band / H_ / dt
+    sample = "oracle encode+decode of a 1920x%d band of each 1080p frame per step (%.3f frame)" % (band, band / H_)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3 / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1080p CVC encode+decode, 5-level CT 32/16/16/8/8, step 8, K every 10",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=30, help="distinct frames per stream (cycled)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    frames = make_frames(seed=rank, n=args.frames)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1510_00561_b300 import Codec, kernel_launches
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    codec = Codec(W_, H_, LEVELS, DIRS, QPH, QPL, 0.0, KINT)
+    d_frames = [torch.from_numpy(f).to(dev) for f in frames]
+    out = torch.empty(codec.max_stream, dtype=torch.uint8, device=dev)
+    rgb = torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        s, _ = codec.encode(d_frames[i % len(d_frames)], out=out)
+        codec.decode(s, out=rgb)
+        return s.numel()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    codec.set_timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    nbytes = 0
+    launches0 = kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        starts[i].record(stream)
+        nbytes += step(args.warmup + i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    stage = codec.timing()
+    codec.set_timing(False)
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot_ms = float(t.item())
+    frames_total = args.steps * world
+    value = frames_total / (tot_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), per step:
+    # H2D frame, encode, D2H bitstream, H2D bitstream, decode, D2H frame
+    h_frames = [torch.from_numpy(f).pin_memory() for f in frames[:min(len(frames), 8)]]
+    h_stream = torch.empty(codec.max_stream, dtype=torch.uint8).pin_memory()
+    h_rgb = torch.empty((H_, W_, 3), dtype=torch.uint8).pin_memory()
+    d_in = torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev)
+    d_sin = torch.empty(codec.max_stream, dtype=torch.uint8, device=dev)
+    e2e_steps = max(3, min(args.steps, 30))
+    h2d = d2h = 0
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        d_in.copy_(h_frames[i % len(h_frames)], non_blocking=True)
+        s, _ = codec.encode(d_in, out=out)
+        n = s.numel()
+        h_stream[:n].copy_(s, non_blocking=True)
+        d_sin[:n].copy_(h_stream[:n], non_blocking=True)
+        codec.decode(d_sin[:n], out=rgb)
+        h_rgb.copy_(rgb, non_blocking=True)
+        h2d += d_in.numel() + n
+        d2h += n + rgb.numel()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_steps * world / (float(t.item()) / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant stage (CUDA events in the timed region)
+    pk = peaks()
+    tokens = (nbytes / args.steps - 32 - 4 * codec.ncomp) / 2
+    sb = stage_bytes(codec, tokens)
+    dom = max(stage, key=lambda k: stage[k][0])
+    ms_dom, n_dom = stage[dom]
+    per_launch_ms = ms_dom / max(1, n_dom)
+    bytes_per_launch = sb[dom] * args.steps / max(1, n_dom)
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+            "peak_source": pk["source"], "launches": n_dom,
+            "stages_ms_per_frame": {k: v[0] / args.steps for k, v in stage.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, done, dt = cpu_oracle_rate(frames[:2], seconds_cap=25.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d full 1080p frames (K then P) encoded+decoded by the FP64 oracle in %.1f s" % (done, dt)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1080p CVC encode+decode (plain per-frame path), 1920x1080 RGB, "
+                                   "5-level CDF 9/7 LP + 32/16/16/8/8 ladder DFB, QPH 8 / QPL 1, K every 10",
+                       "streams_per_gpu": 1, "frames_cycled": len(frames),
+                       "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
+                       "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
+                       "mean_stream_bytes": nbytes / args.steps},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+                    "d2h_bytes_per_step": d2h // e2e_steps},
+            "gpu_launches": int(launches), "clocks": clk, "wall_s": t_wall}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * cvc.h -- C ABI of the B300 contourlet video codec library (libcvc.so).
+ *
+ * The library implements the data-parallel hot path of CVC, the contourlet
+ * video codec of Katsigiannis, Papaioannou and Maroulis (arXiv:1510.00561):
+ * colour conversion and chroma subsampling (§3.1), the contourlet transform
+ * (§2.1, §3.3), lowpass normalisation (§3.4), quantisation and rounding
+ * (§3.5, §3.6), K/P frame differencing (§3.7) and run-length coding (§3.8),
+ * and the inverse chain of the decoder.  Every step runs in CUDA kernels
+ * written for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never frees them and only touches them on the given stream.
+ *   - Calls are asynchronous on `stream` unless they return a host value that
+ *     needs the GPU's result (out_len / frame_type of cvc_encode_frame, the
+ *     status of cvc_decode_frame); those synchronise the stream before
+ *     returning.
+ *   - A call that fails leaves the codec state (key-frame state, frame
+ *     counter) exactly as it was.
+ *   - A context (cvc_codec, cvc_ct_plan) is not thread-safe; distinct
+ *     contexts are independent and may run concurrently on distinct streams.
+ *   - CUDA errors map to CVC_ERR_CUDA; allocation failures to CVC_ERR_NOMEM.
+ */
+#ifndef CVC_H
+#define CVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CVC_OK = 0,
+    CVC_ERR_INVALID_ARG = 1,  /* argument outside its documented range            */
+    CVC_ERR_UNSUPPORTED = 2,  /* valid but not supported by this build            */
+    CVC_ERR_CAPACITY = 3,     /* output buffer too small; *out_len = bytes needed */
+    CVC_ERR_OVERFLOW = 4,     /* a quantised code left the int16 range            */
+    CVC_ERR_CORRUPT = 5,      /* malformed or mismatched bitstream                */
+    CVC_ERR_CUDA = 6,         /* a CUDA runtime call failed                       */
+    CVC_ERR_TIMEOUT = 7,      /* a bounded device wait gave up                    */
+    CVC_ERR_NOMEM = 8,        /* device or host allocation failed                 */
+    CVC_ERR_STATE = 9         /* P-frame without its reference frame              */
+} cvc_status;
+
+/* a CUDA stream handle (the same type as cudaStream_t); NULL = legacy stream */
+typedef struct CUstream_st* cvc_stream_t;
+
+#define CVC_MAX_LEVELS 6
+#define CVC_MAX_DIRS_LOG2 6
+#define CVC_MAX_SUBBANDS (1 + CVC_MAX_LEVELS * 64)
+
+/* Human-readable name of a status code (static string). */
+const char* cvc_status_string(cvc_status s);
+
+/* ------------------------------------------------------------------ layout
+ * Coefficient layout of one plane (§3.3: the coarsest lowpass image plus
+ * the directional subbands of each scale), float elements, row-major
+ * subbands packed back to back:
+ *   [lowpass (h>>L) x (w>>L)] [level 1 (finest): 2^k1 subbands] ... [level L]
+ * Level j works on the (h>>(j-1)) x (w>>(j-1)) detail image; with k = k_j:
+ *   k = 0: one subband, the detail itself
+ *   k = 1: two quincunx halves, each (hj) x (wj/2), row-compacted
+ *   k >= 2: subbands 0 .. 2^(k-1)-1 are (hj>>(k-1)) x (wj/2) (wedges about the
+ *          horizontal-frequency axis), the rest (hj/2) x (wj>>(k-1)).
+ * Directions are in filter-bank tree order (wedge slope increasing within
+ * each half).  `kind`: 0 lowpass, 1 / 2 the two wedge families, 3 undivided
+ * detail, 4 quincunx half.
+ * Plane sizes must be multiples of cvc_modulus(levels, dirs_log2).          */
+typedef struct {
+    long long off;
+    int h, w, level, dir, kind;
+} cvc_subband;
+
+typedef struct {
+    int height, width, levels, dirs_log2[CVC_MAX_LEVELS];
+    int modulus;
+    int nsub;                             /* lowpass + directional subbands */
+    cvc_subband sub[CVC_MAX_SUBBANDS];
+    long long total;                      /* coefficients of one plane      */
+} cvc_ct_layout_t;
+
+/* Smallest size every plane dimension must be a multiple of:
+ * max(2^L, max_j 2^(j-1) * max(2^(k_j-1), 2)).  Returns 0 for bad arguments. */
+int cvc_modulus(int levels, const int* dirs_log2);
+
+/* Fill *out for an h x w plane.  INVALID_ARG unless 1 <= levels <= 6,
+ * 0 <= dirs_log2[j] <= 6 and h, w are positive multiples of the modulus.    */
+cvc_status cvc_ct_layout(int h, int w, int levels, const int* dirs_log2, cvc_ct_layout_t* out);
+
+/* ------------------------------------------------- contourlet transform
+ * §2.1: Laplacian pyramid with the CDF 9/7 pair (periodic extension) whose
+ * detail images feed directional filter banks of ladder fan filters.
+ * A plan fixes the plane size, the decomposition and a batch count, and
+ * owns the device workspace (about 1.7 plane sizes per batch entry).
+ * Data layout: d_x is `batch` dense planes of h x w floats (row-major,
+ * plane stride h*w); d_coeffs is `batch` coefficient vectors of
+ * layout.total floats.  The four maps are linear:
+ *   forward A: x -> coeffs;  inverse S: coeffs -> x  (S A = identity);
+ *   forward_adjoint A^T: coeffs -> x;  inverse_adjoint S^T: x -> coeffs.
+ * Input and output buffers must not overlap.                               */
+typedef struct cvc_ct_plan cvc_ct_plan;
+
+cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, int batch,
+                              cvc_ct_plan** out);
+cvc_status cvc_ct_plan_destroy(cvc_ct_plan* plan);
+/* total coefficients of one plane of this plan (layout.total) */
+long long cvc_ct_plan_coeffs(const cvc_ct_plan* plan);
+
+cvc_status cvc_ct_forward(cvc_ct_plan* plan, const float* d_x, float* d_coeffs, cvc_stream_t stream);
+cvc_status cvc_ct_inverse(cvc_ct_plan* plan, const float* d_coeffs, float* d_x, cvc_stream_t stream);
+cvc_status cvc_ct_forward_adjoint(cvc_ct_plan* plan, const float* d_coeffs_bar, float* d_x_bar,
+                                  cvc_stream_t stream);
+cvc_status cvc_ct_inverse_adjoint(cvc_ct_plan* plan, const float* d_x_bar, float* d_coeffs_bar,
+                                  cvc_stream_t stream);
+
+/* ---------------------------------------------------------------- codec
+ * One video stream: encoder and decoder state resident on the device.
+ *   width, height   frame size in pixels, 1..65535 (padded internally to the
+ *                   modulus by half-sample mirroring; chroma is 4:2:0)
+ *   levels          LP levels, 1..6 (§3.3)
+ *   dirs_log2[j]    DFB stages of level j+1 (finest first), 0..6
+ *   qph, qpl        quantisation steps of subbands [1,181] and lowpass [1,71] (§3.5)
+ *   subband_threshold  subband coefficients with |c| below it become 0 (>= 0)
+ *   key_interval    frame i (since create/reset) is a K-frame iff i % key_interval == 0 (§3.7)
+ *   chroma_420      must be 1                                                 */
+typedef struct {
+    int width, height;
+    int levels;
+    int dirs_log2[CVC_MAX_LEVELS];
+    int qph, qpl;
+    float subband_threshold;
+    int key_interval;
+    int chroma_420;
+} cvc_params;
+
+typedef struct {
+    int padded_height, padded_width;           /* luma plane as transformed        */
+    int chroma_height, chroma_width;           /* unpadded 4:2:0 chroma size       */
+    int padded_chroma_height, padded_chroma_width;
+    long long coeffs;                          /* coefficients of one frame (Y,Co,Cg) */
+    int components;                            /* bitstream components per frame   */
+    long long max_stream_bytes;                /* worst-case encoded frame size     */
+} cvc_codec_info_t;
+
+typedef struct cvc_codec cvc_codec;
+
+cvc_status cvc_create(const cvc_params* params, cvc_codec** out);
+cvc_status cvc_destroy(cvc_codec* codec);
+/* Next encoded frame is a K-frame; the decoder expects a K-frame next. */
+cvc_status cvc_reset(cvc_codec* codec);
+cvc_status cvc_codec_info(const cvc_codec* codec, cvc_codec_info_t* out);
+
+/* Encode one frame.
+ *   d_rgb        height rows of width*3 interleaved R,G,B bytes, row pitch pitch_bytes
+ *   d_out        receives the frame bitstream (device), capacity out_cap bytes
+ *   *out_len     (host) bytes written; on CVC_ERR_CAPACITY the bytes needed
+ *   *frame_type  (host, may be NULL) 0 = K-frame, 1 = P-frame
+ * Bitstream (little-endian): 32-byte header {"CVC1", u16 version=1, u8 type,
+ * u8 levels, u32 frame index, u16 height, u16 width, u8 dirs_log2[6],
+ * u16 qph, u16 qpl, u16 0, u32 ncomp}, then ncomp u32 token counts, then the
+ * int16 tokens of every component.  Components run Y, Co, Cg, each in the
+ * coefficient layout order.  The K-frame lowpass holds its column-differenced
+ * codes raw; every other component holds, row by row, one token per non-zero
+ * code and the pair (0, n) per maximal run of n zeros (§3.8).
+ * Synchronises `stream`.  Errors: INVALID_ARG, CAPACITY, OVERFLOW, CUDA.    */
+cvc_status cvc_encode_frame(cvc_codec* codec, const uint8_t* d_rgb, size_t pitch_bytes,
+                            uint8_t* d_out, size_t out_cap, size_t* out_len, int* frame_type,
+                            cvc_stream_t stream);
+
+/* Decode one frame produced by cvc_encode_frame of a codec with the same
+ * parameters into d_rgb (height rows of width*3 bytes, row pitch pitch_bytes).
+ * Synchronises `stream`.  Errors: INVALID_ARG, CORRUPT (malformed stream or
+ * parameter mismatch), STATE (P-frame that does not follow the last decoded
+ * frame), CUDA.                                                             */
+cvc_status cvc_decode_frame(cvc_codec* codec, const uint8_t* d_in, size_t in_len, uint8_t* d_rgb,
+                            size_t pitch_bytes, cvc_stream_t stream);
+
+/* Inspection of the last encode / decode (for parity checks): copies into
+ * d_out (device, at least cap_elems floats)
+ *   which = 0: the encoder's padded float planes Y, Co, Cg (before the transform)
+ *   which = 1: the encoder's transform coefficients (Y, Co, Cg layouts back to back)
+ *   which = 2: the decoder's reconstructed padded planes Y, Co, Cg (before rounding)
+ * Asynchronous on `stream`.  INVALID_ARG if cap_elems is too small.          */
+cvc_status cvc_codec_inspect(const cvc_codec* codec, int which, float* d_out, size_t cap_elems,
+                             cvc_stream_t stream);
+
+/* --------------------------------------------------------------- tracing
+ * Per-stage GPU time of a codec (the per-operation breakdown of §4.2),
+ * measured with CUDA events recorded on the call's stream around each stage
+ * and read back at the synchronisation that encode / decode already do.
+ * Stages (index: name): 0 colour+chroma+pad, 1 LP analysis, 2 DFB analysis,
+ * 3 quantise+K/P, 4 RLE+bitstream, 5 bitstream parse+un-RLE,
+ * 6 inverse K/P+dequantise, 7 DFB synthesis, 8 LP synthesis, 9 chroma
+ * upsampling+colour.                                                       */
+#define CVC_NUM_STAGES 10
+
+/* enable (on != 0) or disable stage timing; enabling clears the totals */
+cvc_status cvc_codec_set_timing(cvc_codec* codec, int on);
+/* accumulated milliseconds and kernel launches per stage since enabling;
+ * ms and launches each hold CVC_NUM_STAGES entries (either may be NULL)     */
+cvc_status cvc_codec_timing(const cvc_codec* codec, double* ms, long long* launches);
+
+/* Kernels this library has launched in this process (all contexts). */
+unsigned long long cvc_kernel_launches(void);
+
+/* ------------------------------------------------------------ diagnostics
+ * Host-only dump of the launch plan of a transform (no device call is
+ * made, so it works without a GPU): the job tables of every launch of
+ * `mode` (0 forward, 1 inverse, 2 adjoint of forward, 3 adjoint of inverse)
+ * for a transform plan (params == NULL; h, w, levels, dirs_log2, batch as in
+ * cvc_ct_plan_create) or for the three planes of a codec (params != NULL;
+ * the other size arguments are ignored).  Layout written to buf, little
+ * endian:
+ *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 lp_job_bytes, u32 lift_job_bytes,
+ *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
+ *   then per launch: u32 kind (0 = LP level, 1 = DFB lifting pass), u32 njobs,
+ *   and njobs job records (the library's job structures).
+ * Lets a test check, before any GPU run, that every access of every job
+ * stays inside its buffer and that the tables compute the transform.
+ * Returns CAPACITY with *used = bytes needed when cap is too small.          */
+cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int levels, const int* dirs_log2,
+                                 int batch, int mode, void* buf, size_t cap, size_t* used);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

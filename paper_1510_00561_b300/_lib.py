@@ -1,0 +1,104 @@
+"""ctypes view of libcvc.so (include/cvc.h).  Argument marshalling only.
+
+The library must have been built (``python -m paper_1510_00561_b300.build``
+or ``__graft_entry__.build()``); loading fails loudly otherwise -- there is
+no fallback implementation.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcvc.so")
+
+MAX_LEVELS = 6
+NUM_STAGES = 10
+STAGE_NAMES = ("colour_fwd", "lp_analysis", "dfb_analysis", "quantise_kp", "rle_stream",
+               "parse_unrle", "unquantise_kp", "dfb_synthesis", "lp_synthesis", "colour_inv")
+MAX_SUBBANDS = 1 + 6 * 64
+
+STATUS = {0: "CVC_OK", 1: "CVC_ERR_INVALID_ARG", 2: "CVC_ERR_UNSUPPORTED", 3: "CVC_ERR_CAPACITY",
+          4: "CVC_ERR_OVERFLOW", 5: "CVC_ERR_CORRUPT", 6: "CVC_ERR_CUDA", 7: "CVC_ERR_TIMEOUT",
+          8: "CVC_ERR_NOMEM", 9: "CVC_ERR_STATE"}
+
+
+class CvcError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        msg = _lib.cvc_status_string(status).decode() if _lib is not None else name
+        super().__init__("%s: %s (%s)" % (where, name, msg))
+
+
+class Subband(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_longlong), ("h", ctypes.c_int), ("w", ctypes.c_int),
+                ("level", ctypes.c_int), ("dir", ctypes.c_int), ("kind", ctypes.c_int)]
+
+
+class CtLayout(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("levels", ctypes.c_int),
+                ("dirs_log2", ctypes.c_int * MAX_LEVELS), ("modulus", ctypes.c_int), ("nsub", ctypes.c_int),
+                ("sub", Subband * MAX_SUBBANDS), ("total", ctypes.c_longlong)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("levels", ctypes.c_int),
+                ("dirs_log2", ctypes.c_int * MAX_LEVELS), ("qph", ctypes.c_int), ("qpl", ctypes.c_int),
+                ("subband_threshold", ctypes.c_float), ("key_interval", ctypes.c_int),
+                ("chroma_420", ctypes.c_int)]
+
+
+class CodecInfo(ctypes.Structure):
+    _fields_ = [("padded_height", ctypes.c_int), ("padded_width", ctypes.c_int),
+                ("chroma_height", ctypes.c_int), ("chroma_width", ctypes.c_int),
+                ("padded_chroma_height", ctypes.c_int), ("padded_chroma_width", ctypes.c_int),
+                ("coeffs", ctypes.c_longlong), ("components", ctypes.c_int),
+                ("max_stream_bytes", ctypes.c_longlong)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+
+def lib():
+    """Load libcvc.so once; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcvc.so is not built (%s); run `python -m paper_1510_00561_b300.build`"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.cvc_status_string.argtypes = [_I]
+        L.cvc_status_string.restype = ctypes.c_char_p
+        L.cvc_modulus.argtypes = [_I, ctypes.POINTER(_I)]
+        L.cvc_ct_layout.argtypes = [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(CtLayout)]
+        L.cvc_ct_plan_create.argtypes = [_I, _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_P)]
+        L.cvc_ct_plan_destroy.argtypes = [_P]
+        L.cvc_ct_plan_coeffs.argtypes = [_P]
+        L.cvc_ct_plan_coeffs.restype = ctypes.c_longlong
+        for name in ("cvc_ct_forward", "cvc_ct_inverse", "cvc_ct_forward_adjoint", "cvc_ct_inverse_adjoint"):
+            getattr(L, name).argtypes = [_P, _P, _P, _P]
+        L.cvc_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_P)]
+        L.cvc_destroy.argtypes = [_P]
+        L.cvc_reset.argtypes = [_P]
+        L.cvc_codec_info.argtypes = [_P, ctypes.POINTER(CodecInfo)]
+        L.cvc_encode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
+        L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
+        L.cvc_codec_inspect.argtypes = [_P, _I, _P, _SZ, _P]
+        L.cvc_codec_set_timing.argtypes = [_P, _I]
+        L.cvc_codec_timing.argtypes = [_P, _P, _P]
+        L.cvc_kernel_launches.argtypes = []
+        L.cvc_kernel_launches.restype = ctypes.c_ulonglong
+        _lib = L
+    return _lib
+
+
+def check(status, where):
+    if status != 0:
+        raise CvcError(status, where)
+
+
+def ints(seq, n=MAX_LEVELS):
+    vals = list(seq) + [0] * (n - len(seq))
+    return (_I * n)(*vals)

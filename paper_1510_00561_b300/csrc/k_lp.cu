@@ -1,0 +1,144 @@
+// k_lp.cu -- Laplacian pyramid level kernels (§2.1, Fig. 1).
+//
+// One CTA computes a 64 x 64 full-resolution tile of one pyramid level of
+// one plane, with periodic extension.  Two kernels share one body:
+//   analysis:  c = down(x, fa);           d = x - up(c, fs)
+//   synthesis: e = c - down(d, fa);       x = d + up(e, fs)
+// down(., f) filters separably with f and keeps even samples; up(., f)
+// inserts zeros and filters separably with f.  The forward transform and
+// its inverse use (fa, fs) = (h, g), the CDF 9/7 analysis / synthesis
+// lowpass pair; the adjoints swap the pair ((fa, fs) = (g, h)), because
+// down(., f) and up(., f) are transposes of each other for symmetric f.
+//
+// The tile stages everything through shared memory: the main input with
+// its halo (77 x 77), the decimated row pass, the half-resolution tile
+// with halo, and the expanded row pass; every input element is read from
+// global memory once per tile plus the halo.
+#include "cvc_internal.cuh"
+
+namespace cvc {
+
+// CDF 9/7 lowpass pair normalised to DC gain sqrt(2) (published values,
+// 12 significant digits): analysis h (taps -4..4), synthesis g (-3..3).
+__constant__ float c_h[9] = {0.037828455507f, -0.023849465020f, -0.110624404418f, 0.377402855613f,
+                             0.852698679009f,  0.377402855613f, -0.110624404418f, -0.023849465020f,
+                             0.037828455507f};
+__constant__ float c_g[7] = {-0.064538882629f, -0.040689417609f, 0.418092273222f, 0.788485616406f,
+                             0.418092273222f,  -0.040689417609f, -0.064538882629f};
+
+__device__ __forceinline__ int wrap_idx(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <int RA>
+__device__ __forceinline__ float tap_a(int t) { return RA == 4 ? c_h[t + 4] : c_g[t + 3]; }
+template <int RS>
+__device__ __forceinline__ float tap_s(int t) { return RS == 3 ? c_g[t + 3] : c_h[t + 4]; }
+
+template <int RA, int RS, bool SYNTH>
+__global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs,
+                                                  const int* __restrict__ block_job, Bases B) {
+    constexpr int T = LP_TILE;
+    constexpr int MLO = -(RS / 2);
+    constexpr int MHI = (T - 1 + RS) / 2;
+    constexpr int VN = MHI - MLO + 1;
+    constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
+    constexpr int Y0 = 2 * MLO - RA;  // main tile origin relative to the output tile origin
+    constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
+
+    __shared__ float s_main[MN * MN];
+    __shared__ float s_a[NA];        // row pass (MN x VN), later expanded rows (VN x T)
+    __shared__ float s_v[VN * VN];
+
+    const int jid = block_job[blockIdx.x];
+    const LpJob& J = jobs[jid];
+    const int tile = blockIdx.x - J.first_block;
+    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
+    const int y0 = ty * T, x0 = tx * T;
+    const int m0 = y0 / 2, n0 = x0 / 2;
+    const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
+    const float* mainp = B.p[J.main.b] + J.main.off;
+    const int mrs = J.main.rs;
+
+    for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
+        int r = i / MN, c = i - r * MN;
+        int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
+        s_main[i] = mainp[(long long)y * mrs + x];
+    }
+    __syncthreads();
+    // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]
+    for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
+        int r = i / VN, n = i - r * VN;
+        const float* row = s_main + r * MN + 2 * n + RA;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), row[-b], acc);
+        s_a[i] = acc;
+    }
+    __syncthreads();
+    // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI]
+    const float* cinp = SYNTH ? B.p[J.cin.b] + J.cin.off : nullptr;
+    for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
+        int m = i / VN, n = i - m * VN;
+        float acc = 0.f;
+#pragma unroll
+        for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), s_a[(2 * m + RA - a) * VN + n], acc);
+        if (SYNTH) {
+            int gm = wrap_idx(m0 + MLO + m, Hh), gn = wrap_idx(n0 + MLO + n, Wh);
+            acc = cinp[(long long)gm * J.cin.rs + gn] - acc;
+        }
+        s_v[i] = acc;
+    }
+    __syncthreads();
+    if (!SYNTH) {
+        // interior 32 x 32 of v is this tile's share of the lowpass output
+        float* coutp = B.p[J.cout.b] + J.cout.off;
+        for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
+            int m = i / (T / 2), n = i - m * (T / 2);
+            int gm = m0 + m, gn = n0 + n;
+            if (gm < Hh && gn < Wh) coutp[(long long)gm * J.cout.rs + gn] = s_v[(m - MLO) * VN + (n - MLO)];
+        }
+    }
+    // expanding row pass: s_a[m'][x'] = sum_t fs[t] [x'-t even] v[m'][(x'-t)/2 - MLO]
+    for (int i = threadIdx.x; i < VN * T; i += blockDim.x) {
+        int m = i / T, x = i - m * T;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if (((x - t) & 1) == 0) acc = fmaf(tap_s<RS>(t), s_v[m * VN + ((x - t) >> 1) - MLO], acc);
+        }
+        s_a[i] = acc;
+    }
+    __syncthreads();
+    // expanding column pass and the combination with the main input
+    float* outp = B.p[J.out.b] + J.out.off;
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        int y = i / T, x = i - y * T;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if (((y - t) & 1) == 0) acc = fmaf(tap_s<RS>(t), s_a[(((y - t) >> 1) - MLO) * T + x], acc);
+        }
+        int gy = y0 + y, gx = x0 + x;
+        if (gy < H && gx < W) {
+            float mv = s_main[(y - Y0) * MN + (x - Y0)];
+            outp[(long long)gy * J.out.rs + gx] = SYNTH ? mv + acc : mv - acc;
+        }
+    }
+}
+
+cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st) {
+    if (L.nblocks == 0) return cudaSuccess;
+    const bool synth = (m == INV || m == FWD_ADJ);
+    const bool swap = (m == FWD_ADJ || m == INV_ADJ);
+    dim3 grid(L.nblocks), block(256);
+    if (!synth && !swap) k_lp_level<4, 3, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else if (synth && !swap) k_lp_level<4, 3, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else if (!synth && swap) k_lp_level<3, 4, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else k_lp_level<3, 4, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    return cudaGetLastError();
+}
+
+}  // namespace cvc

@@ -1,0 +1,69 @@
+"""The launch plans of libcvc (CPU only, no GPU): every job stays inside its
+buffers, no launch has a cross-job read/write hazard, and executing the job
+tables with the kernels' semantics in double precision reproduces the
+oracle's transform.  This checks the host planner (views, strides, stencil
+offsets, pass order) independently of the GPU."""
+import numpy as np
+import pytest
+
+import oracle as O
+import plan_emulator as E
+from paper_1510_00561_b300 import _lib as L
+
+PLANS = [(64, 64, 3, [3, 2, 2], 2), (144, 176, 3, [3, 2, 2], 1), (96, 160, 4, [4, 3, 3, 2], 1),
+         (64, 96, 2, [0, 1], 1), (128, 128, 2, [6, 5], 1), (72, 88, 3, [3, 2, 2], 1), (128, 256, 5, [5, 4, 4, 3, 3], 1)]
+
+
+def _buffers(elems):
+    return {b: np.zeros(int(elems[b])) for b in range(4)}
+
+
+@pytest.mark.parametrize("H,W,Lv,k,batch", PLANS)
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_plan_tables_compute_the_transform(H, W, Lv, k, batch, mode):
+    elems, launches = E.tables(mode, h=H, w=W, levels=Lv, dirs=k, batch=batch)
+    n = O.layout(H, W, Lv, k)["total"]
+    assert elems[0] == batch * H * W and elems[1] == batch * n and elems[3] == batch * H * W
+    rng = np.random.default_rng(mode)
+    bufs = _buffers(elems)
+    in_base, out_base = {0: (0, 1), 1: (1, 3), 2: (1, 3), 3: (0, 1)}[mode]
+    x = rng.uniform(-50, 255, elems[in_base])
+    bufs[in_base][:] = x
+    E.run(mode, elems, launches, bufs)
+    for b in range(batch):
+        if mode in (0, 3):
+            xin = x[b * H * W:(b + 1) * H * W].reshape(H, W)
+            ref = O.ct(mode, xin, H, W, Lv, k)
+            got = bufs[1][b * n:(b + 1) * n]
+        else:
+            cin = x[b * n:(b + 1) * n]
+            ref = O.ct(mode, cin, H, W, Lv, k).ravel()
+            got = bufs[3][b * H * W:(b + 1) * H * W]
+        assert np.abs(got - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("w,h,Lv,k", [(176, 144, 3, [3, 2, 2]), (99, 77, 2, [2, 2]), (64, 48, 2, [1, 0])])
+def test_codec_plan_tables(w, h, Lv, k):
+    prm = L.Params(w, h, Lv, L.ints(k), 8, 1, 0.0, 8, 1)
+    elems, launches = E.tables(0, params=prm)
+    oc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 8)
+    rng = np.random.default_rng(1)
+    frame = rng.integers(0, 256, (h, w, 3), dtype=np.uint8)
+    yp, cop, cgp = oc.planes(frame)
+    bufs = _buffers(elems)
+    bufs[0][:] = np.concatenate([yp.ravel(), cop.ravel(), cgp.ravel()])
+    E.run(0, elems, launches, bufs)
+    ref = np.concatenate([O.ct(0, p, p.shape[0], p.shape[1], Lv, k) for p in (yp, cop, cgp)])
+    assert np.abs(bufs[1] - ref).max() < 1e-7
+    # and the inverse tables invert it
+    elems, launches = E.tables(1, params=prm)
+    E.run(1, elems, launches, bufs)
+    assert np.abs(bufs[3] - bufs[0]).max() < 1e-8
+
+
+def test_benchmark_codec_plan_is_in_bounds():
+    """The 1080p configuration: bounds and hazards of every forward and inverse job."""
+    prm = L.Params(1920, 1080, 5, L.ints([5, 4, 4, 3, 3]), 8, 1, 0.0, 10, 1)
+    for mode in (0, 1):
+        elems, launches = E.tables(mode, params=prm)
+        E.check_only(elems, launches, mode)
