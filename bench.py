@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=30, help="distinct frames per stream (cycled)")
+    ap.add_argument("--e2e-steps", type=int, default=30, help="steps of the host-buffer end-to-end pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     args = ap.parse_args()
@@ -279,7 +280,7 @@ def main():
     h_rgb = torch.empty((H_, W_, 3), dtype=torch.uint8).pin_memory()
     d_in = torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev)
     d_sin = torch.empty(codec.max_stream, dtype=torch.uint8, device=dev)
-    e2e_steps = max(3, min(args.steps, 30))
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     h2d = d2h = 0
     barrier()
     torch.cuda.synchronize()

@@ -480,7 +480,7 @@ cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cu
         }
     } else {
         for (const LaunchLift& L : e->lift[m]) {
-            if ((err = launch_lift(L, bases, st)) != cudaSuccess) return err;
+            if ((err = launch_lift(L, m, bases, st)) != cudaSuccess) return err;
             note_launches(L.nblocks > 0);
         }
     }

@@ -119,6 +119,6 @@ void note_launches(int n);
 
 // -------------------------------------------------------------- kernels
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st);
-cudaError_t launch_lift(const LaunchLift& L, Bases bases, cudaStream_t st);
+cudaError_t launch_lift(const LaunchLift& L, Mode m, Bases bases, cudaStream_t st);
 
 }  // namespace cvc

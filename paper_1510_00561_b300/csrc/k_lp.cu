@@ -14,6 +14,12 @@
 // its halo (77 x 77), the decimated row pass, the half-resolution tile
 // with halo, and the expanded row pass; every input element is read from
 // global memory once per tile plus the halo.
+//
+// Synthesis accumulates in float-float (error-free TwoSum / FMA-based
+// TwoProd transformations, Dekker 1971 / Knuth): the pyramid's DC gain of 2
+// per level makes coarse levels carry numbers up to 2^L * 255, and each
+// level's single-precision roundings would otherwise add ~ulp(255) to the
+// reconstruction; with compensated sums only the stored values round.
 #include "cvc_internal.cuh"
 
 namespace cvc {
@@ -129,15 +135,154 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     }
 }
 
+// ------------------------------------------------- float-float helpers
+// (hi, lo) accumulators; __fadd_rn / __fmul_rn keep the compiler from
+// contracting the error-free transformations into FMAs.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+// (hi, lo) += f * (xh + xl)
+__device__ __forceinline__ void ff_fma(float& hi, float& lo, float f, float xh, float xl) {
+    float p = __fmul_rn(f, xh);
+    float pe = fmaf(f, xh, -p);
+    ff_add(hi, lo, p);
+    lo = fmaf(f, xl, __fadd_rn(lo, pe));
+}
+__device__ __forceinline__ void ff_norm(float& hi, float& lo) {
+    float s = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
+}
+
+// Synthesis tile with float-float intermediates (dynamic shared memory):
+//   e = cin - down(main, fa);  out = main + up(e, fs)
+template <int RA, int RS>
+__global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ jobs,
+                                                     const int* __restrict__ block_job, Bases B) {
+    constexpr int T = LP_TILE;
+    constexpr int MLO = -(RS / 2);
+    constexpr int MHI = (T - 1 + RS) / 2;
+    constexpr int VN = MHI - MLO + 1;
+    constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
+    constexpr int Y0 = 2 * MLO - RA;
+    constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
+    extern __shared__ float sm[];
+    float* s_main = sm;                 // MN * MN
+    float* s_ah = s_main + MN * MN;     // NA
+    float* s_al = s_ah + NA;            // NA
+    float* s_vh = s_al + NA;            // VN * VN
+    float* s_vl = s_vh + VN * VN;       // VN * VN
+
+    const int jid = block_job[blockIdx.x];
+    const LpJob& J = jobs[jid];
+    const int tile = blockIdx.x - J.first_block;
+    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
+    const int y0 = ty * T, x0 = tx * T;
+    const int m0 = y0 / 2, n0 = x0 / 2;
+    const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
+    const float* mainp = B.p[J.main.b] + J.main.off;
+    const int mrs = J.main.rs;
+    for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
+        int r = i / MN, c = i - r * MN;
+        int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
+        s_main[i] = mainp[(long long)y * mrs + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
+        int r = i / VN, n = i - r * VN;
+        const float* row = s_main + r * MN + 2 * n + RA;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int b = -RA; b <= RA; b++) ff_fma(hi, lo, tap_a<RA>(b), row[-b], 0.f);
+        s_ah[i] = hi;
+        s_al[i] = lo;
+    }
+    __syncthreads();
+    const float* cinp = B.p[J.cin.b] + J.cin.off;
+    for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
+        int m = i / VN, n = i - m * VN;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int a = -RA; a <= RA; a++) {
+            int k = (2 * m + RA - a) * VN + n;
+            ff_fma(hi, lo, tap_a<RA>(a), s_ah[k], s_al[k]);
+        }
+        int gm = wrap_idx(m0 + MLO + m, Hh), gn = wrap_idx(n0 + MLO + n, Wh);
+        float eh = cinp[(long long)gm * J.cin.rs + gn], el = 0.f;
+        ff_add(eh, el, -hi);
+        el = __fsub_rn(el, lo);
+        ff_norm(eh, el);
+        s_vh[i] = eh;
+        s_vl[i] = el;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < VN * T; i += blockDim.x) {
+        int m = i / T, x = i - m * T;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if (((x - t) & 1) == 0) {
+                int k = m * VN + ((x - t) >> 1) - MLO;
+                ff_fma(hi, lo, tap_s<RS>(t), s_vh[k], s_vl[k]);
+            }
+        }
+        s_ah[i] = hi;
+        s_al[i] = lo;
+    }
+    __syncthreads();
+    float* outp = B.p[J.out.b] + J.out.off;
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        int y = i / T, x = i - y * T;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if (((y - t) & 1) == 0) {
+                int k = (((y - t) >> 1) - MLO) * T + x;
+                ff_fma(hi, lo, tap_s<RS>(t), s_ah[k], s_al[k]);
+            }
+        }
+        int gy = y0 + y, gx = x0 + x;
+        if (gy < H && gx < W) {
+            float mv = s_main[(y - Y0) * MN + (x - Y0)];
+            ff_add(hi, lo, mv);
+            outp[(long long)gy * J.out.rs + gx] = __fadd_rn(hi, lo);
+        }
+    }
+}
+
+template <int RA, int RS>
+constexpr size_t synth_ff_smem() {
+    constexpr int T = LP_TILE;
+    constexpr int MLO = -(RS / 2);
+    constexpr int MHI = (T - 1 + RS) / 2;
+    constexpr int VN = MHI - MLO + 1;
+    constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
+    constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
+    return sizeof(float) * (size_t)(MN * MN + 2 * NA + 2 * VN * VN);
+}
+
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st) {
     if (L.nblocks == 0) return cudaSuccess;
     const bool synth = (m == INV || m == FWD_ADJ);
     const bool swap = (m == FWD_ADJ || m == INV_ADJ);
     dim3 grid(L.nblocks), block(256);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_lp_synth_ff<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)synth_ff_smem<4, 3>());
+        cudaFuncSetAttribute(k_lp_synth_ff<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)synth_ff_smem<3, 4>());
+        attr_set = true;
+    }
     if (!synth && !swap) k_lp_level<4, 3, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
-    else if (synth && !swap) k_lp_level<4, 3, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else if (synth && !swap)
+        k_lp_synth_ff<4, 3><<<grid, block, synth_ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
     else if (!synth && swap) k_lp_level<3, 4, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
-    else k_lp_level<3, 4, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else k_lp_synth_ff<3, 4><<<grid, block, synth_ff_smem<3, 4>(), st>>>(L.d_jobs, L.d_block_job, bases);
     return cudaGetLastError();
 }
 

@@ -7,10 +7,11 @@ import torch
 
 import oracle as O
 from paper_1510_00561_b300 import CtPlan
+from tolerances import FORWARD, inverse_bound
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-4
+TOL = FORWARD
 
 CASES = [
     (64, 64, 3, [3, 2, 2]),          # one tile per level
@@ -54,10 +55,11 @@ def test_forward_and_inverse_match_oracle(H, W, L, k):
     for b in range(2):
         ref = O.ct(0, x[b].astype(np.float64), H, W, L, k)
         assert _coef_err(c_np[b], ref, H, W, L, k) < TOL
-        # inverse of the oracle's coefficients, and the GPU round trip
+        # inverse of the same coefficients in the oracle: the parity bar
         xin = O.ct(1, c_np[b].astype(np.float64), H, W, L, k)
-        assert np.abs(xr_np[b] - xin).max() < TOL
-        assert np.abs(xr_np[b] - x[b]).max() < TOL
+        assert np.abs(xr_np[b] - xin).max() < inverse_bound(L, k)
+        # GPU round trip: carries the forward's and the inverse's errors
+        assert np.abs(xr_np[b] - x[b]).max() < TOL + inverse_bound(L, k)
 
 
 @pytest.mark.parametrize("H,W,L,k", CASES[:4] + CASES[5:6])
@@ -68,8 +70,12 @@ def test_adjoints_match_oracle(H, W, L, k):
     xb = r.standard_normal((1, H, W)).astype(np.float32) * 50
     xa = plan.forward_adjoint(torch.from_numpy(cb).cuda()).cpu().numpy()[0]
     ca = plan.inverse_adjoint(torch.from_numpy(xb).cuda()).cpu().numpy()[0]
-    np.testing.assert_allclose(xa, O.ct(2, cb[0].astype(np.float64), H, W, L, k), atol=TOL * 5, rtol=0)
-    np.testing.assert_allclose(ca, O.ct(3, xb[0].astype(np.float64), H, W, L, k), atol=TOL * 5, rtol=0)
+    # adjoint outputs are gradients, not pixels: their magnitudes grow with the
+    # filter-bank depth (values in the thousands for 6 DFB stages), so the bar is
+    # relative to the output scale -- 2e-6 of the largest value, ~30 float32 ulps
+    for got, ref in ((xa, O.ct(2, cb[0].astype(np.float64), H, W, L, k)),
+                     (ca, O.ct(3, xb[0].astype(np.float64), H, W, L, k))):
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
 def test_adjoint_dot_products_on_gpu():
@@ -108,7 +114,9 @@ def test_full_size_1080p_luma():
     xr = plan.inverse(c)
     ref = O.ct(0, x[0].astype(np.float64), H, W, L, k)
     assert _coef_err(c.cpu().numpy()[0], ref, H, W, L, k) < TOL
-    assert float((xr - xt).abs().max()) < TOL
+    xin = O.ct(1, c.cpu().numpy()[0].astype(np.float64), H, W, L, k)
+    assert np.abs(xr.cpu().numpy()[0] - xin).max() < inverse_bound(L, k)
+    assert float((xr - xt).abs().max()) < TOL + inverse_bound(L, k)
 
 
 def test_constant_plane_has_zero_details():
