@@ -206,6 +206,36 @@ cvc_status cvc_codec_timing(const cvc_codec* codec, double* ms, long long* launc
 /* Kernels this library has launched in this process (all contexts). */
 unsigned long long cvc_kernel_launches(void);
 
+/* ------------------------------------------------ allocation-free pyramid
+ * The paper has no counterpart: this is a deployment variant for callers
+ * that cannot allocate device memory while they run (a fixed memory budget
+ * handed out up front, or a context where the CUDA allocator is off limits)
+ * and therefore cannot create a cvc_ct_plan.
+ *
+ * Computes exactly what cvc_ct_forward computes for a plan with
+ * dirs_log2 = {0, ..., 0}: the Laplacian pyramid of one dense h x w float
+ * plane d_x, written to d_coeffs in that plan's layout (lowpass
+ * (h>>L) x (w>>L), then the full-size detail of each level 1..L).  Both
+ * buffers belong to the caller.  It calls no allocator: its scratch (the
+ * intermediate lowpass images, one job record per level, the tile map) is a
+ * 16 MiB file-scope __device__ array that every GPU loading the library holds
+ * until the process exits.
+ *   - Limits: h and w multiples of 2^levels; the intermediate lowpass
+ *     images, sum_{j=1}^{L-1} (h>>j)(w>>j) floats (about h*w/3), must fit
+ *     the array's 4,177,536-float workspace (planes up to ~12.5 Mpixel, e.g.
+ *     4K UHD padded to 2176 x 3840), and the full-size plane may span at
+ *     most 16,384 tiles of 64 x 64.  Larger planes return
+ *     CVC_ERR_UNSUPPORTED before any device work.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other.  Calls on a
+ *     single stream are ordered and safe.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.        */
+cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int levels, float* d_coeffs,
+                                         cvc_stream_t stream);
+
 /* ------------------------------------------------------------ diagnostics
  * Host-only dump of the launch plan of a transform (no device call is
  * made, so it works without a GPU): the job tables of every launch of

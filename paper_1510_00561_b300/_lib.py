@@ -90,6 +90,7 @@ def lib():
         L.cvc_codec_timing.argtypes = [_P, _P, _P]
         L.cvc_kernel_launches.argtypes = []
         L.cvc_kernel_launches.restype = ctypes.c_ulonglong
+        L.cvc_lp_pyramid_forward_static.argtypes = [_P, _I, _I, _I, _P, _P]
         _lib = L
     return _lib
 

@@ -1,0 +1,99 @@
+// static_lp.cu -- an allocation-free entry point: the Laplacian-pyramid
+// forward transform with its scratch in a fixed device array.
+//
+// Who needs it: callers that cannot allocate device memory while they run --
+// e.g. code that owns a fixed memory budget handed out up front, or runs
+// where the CUDA allocator is off limits -- cannot create a cvc_ct_plan
+// (which cudaMallocs its workspace and job tables).  This entry point makes
+// no allocation of any kind: the intermediate lowpass images, the per-level
+// job records and the tile-to-job map live in one file-scope __device__
+// array that every GPU loading the library holds until the process exits.
+#include <cstring>
+
+#include "cvc_internal.cuh"
+
+using namespace cvc;
+
+namespace {
+
+// size of the shared scratch array: 4 Mi floats (16 MiB) in all
+constexpr long long kStaticFloats = 4LL << 20;
+// layout: [job records: one per level][tile-to-job map][lowpass workspace]
+constexpr int kJobSlotFloats = 64;  // >= sizeof(LpJob) / 4, 256-byte slots
+constexpr int kMaxTiles = 16384;    // level-1 tiles of 64 x 64 (e.g. 8192 x 8192)
+constexpr long long kWorkOffset = CVC_MAX_LEVELS * kJobSlotFloats + kMaxTiles;
+constexpr long long kWorkFloats = kStaticFloats - kWorkOffset;
+static_assert(sizeof(LpJob) <= kJobSlotFloats * 4, "job slot too small");
+
+static __device__ __align__(256) float g_lp_scratch[kStaticFloats];
+
+constexpr int kMaxDevices = 64;
+float* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int levels, float* d_coeffs,
+                                                    cvc_stream_t stream) {
+    if (!d_x || !d_coeffs || levels < 1 || levels > CVC_MAX_LEVELS || h <= 0 || w <= 0) return CVC_ERR_INVALID_ARG;
+    if (h % (1 << levels) || w % (1 << levels)) return CVC_ERR_INVALID_ARG;
+    // limits of the fixed array
+    long long need = 0;
+    for (int j = 1; j < levels; j++) need += (long long)(h >> j) * (w >> j);
+    const long long tiles1 = (long long)((h + LP_TILE - 1) / LP_TILE) * ((w + LP_TILE - 1) / LP_TILE);
+    if (need > kWorkFloats || tiles1 > kMaxTiles) return CVC_ERR_UNSUPPORTED;
+    // set-up, once per device with that device current: the device address of the array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CVC_ERR_CUDA;
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_lp_scratch) != cudaSuccess || !p) return CVC_ERR_CUDA;
+        g_scratch_ptr[dev] = static_cast<float*>(p);
+    }
+    float* base = g_scratch_ptr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    int* block_job = reinterpret_cast<int*>(base + CVC_MAX_LEVELS * kJobSlotFloats);
+    // every tile of a launch belongs to its single job: the map must read zero
+    if (cudaMemsetAsync(block_job, 0, sizeof(int) * (size_t)tiles1, st) != cudaSuccess) return CVC_ERR_CUDA;
+    Bases B;
+    memset(&B, 0, sizeof(B));
+    B.p[B_IN] = const_cast<float*>(d_x);
+    B.p[B_COEF] = d_coeffs;
+    B.p[B_WORK] = base + kWorkOffset;
+    // coefficient layout of cvc_ct_layout with dirs_log2 = 0: lowpass, then the detail of each level
+    long long coff = (long long)(h >> levels) * (w >> levels);
+    long long woff = 0, prev_woff = 0;
+    for (int j = 1; j <= levels; j++) {
+        const int hj = h >> (j - 1), wj = w >> (j - 1);
+        LpJob J;
+        memset(&J, 0, sizeof(J));
+        J.H = hj;
+        J.W = wj;
+        J.tiles_x = (wj + LP_TILE - 1) / LP_TILE;
+        J.first_block = 0;
+        J.main.b = j == 1 ? B_IN : B_WORK;
+        J.main.off = j == 1 ? 0 : prev_woff;
+        J.main.rs = wj;
+        J.main.cs = 1;
+        J.cout.b = j == levels ? B_COEF : B_WORK;
+        J.cout.off = j == levels ? 0 : woff;
+        J.cout.rs = wj / 2;
+        J.cout.cs = 1;
+        J.out.b = B_COEF;
+        J.out.off = coff;
+        J.out.rs = wj;
+        J.out.cs = 1;
+        coff += (long long)hj * wj;
+        prev_woff = woff;
+        woff += (long long)(hj / 2) * (wj / 2);
+        LpJob* slot = reinterpret_cast<LpJob*>(base + (j - 1) * kJobSlotFloats);
+        if (cudaMemcpyAsync(slot, &J, sizeof(J), cudaMemcpyHostToDevice, st) != cudaSuccess) return CVC_ERR_CUDA;
+        LaunchLp L;
+        L.njobs = 1;
+        L.nblocks = ((hj + LP_TILE - 1) / LP_TILE) * J.tiles_x;
+        L.d_jobs = slot;
+        L.d_block_job = block_job;
+        if (launch_lp(L, FWD, B, st) != cudaSuccess) return CVC_ERR_CUDA;
+        note_launches(1);
+    }
+    return CVC_OK;
+}
