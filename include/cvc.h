@@ -244,10 +244,11 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  * cvc_ct_plan_create) or for the three planes of a codec (params != NULL;
  * the other size arguments are ignored).  Layout written to buf, little
  * endian:
- *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 lp_job_bytes, u32 lift_job_bytes,
+ *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 bytes of an LP-level
+ *   job, u32 bytes of a DFB stage-1+2 job, u32 bytes of a DFB row-split job, u32 0,
  *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
- *   then per launch: u32 kind (0 = LP level, 1 = DFB lifting pass), u32 njobs,
- *   and njobs job records (the library's job structures).
+ *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage >= 3),
+ *   u32 njobs, and njobs job records (the library's job structures).
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */

@@ -614,20 +614,25 @@ cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int lev
     auto push_lp = [&]() {
         for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob)});
     };
-    auto push_lift = [&]() {
-        for (auto& v : e.h_lift[mode]) items.push_back({1, v.data(), v.size(), sizeof(LiftJob)});
+    auto push_dfb = [&]() {
+        for (size_t i = 0; i < e.dfb[mode].size(); i++) {
+            const LaunchDfb& L = e.dfb[mode][i];
+            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob);
+            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
+        }
     };
-    if (analysis) { push_lp(); push_lift(); }
-    else { push_lift(); push_lp(); }
-    size_t need = 16 + 32;
+    if (analysis) { push_lp(); push_dfb(); }
+    else { push_dfb(); push_lp(); }
+    size_t need = 24 + 32;
     for (const Item& it : items) need += 8 + it.n * it.sz;
     *used = need;
     if (!buf || cap < need) return CVC_ERR_CAPACITY;
     uint8_t* o = (uint8_t*)buf;
-    uint32_t hdr[4] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(LiftJob)};
-    memcpy(o, hdr, 16);
-    memcpy(o + 16, elems, 32);
-    size_t pos = 48;
+    uint32_t hdr[6] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
+                       (uint32_t)sizeof(DfbBJob), 0u};
+    memcpy(o, hdr, 24);
+    memcpy(o + 24, elems, 32);
+    size_t pos = 56;
     for (const Item& it : items) {
         uint32_t h2[2] = {(uint32_t)it.kind, (uint32_t)it.n};
         memcpy(o + pos, h2, 8);

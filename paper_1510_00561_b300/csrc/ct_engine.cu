@@ -23,11 +23,18 @@
 // Stage 2: family c in b1 = (1,1), b2 = (1,-1); family r in (1,1), (-1,1).
 // Stage s >= 3, for a channel covering slopes [i/2^m, (i+1)/2^m]:
 //   c: b1 = (2^(s-2), -2i), b2 = (2^(s-2), -2i-2);  r: b1 = (-2i, 2^(s-2)), b2 = (-2i-2, 2^(s-2)).
-// In the rectangular arrays the channels occupy from stage 3 on (rows
-// strided by 2^(s-2), columns by 2 for family c; transposed for r) this is
-// a split into even / odd rows (columns) with a 4 x 4 stencil whose rows
-// (columns) are sheared by -i per row step: row offset a, column offset
-// -i*a + (b-a)/2.  The even child takes the lower half of the slopes.
+// The even child takes the lower half of the slopes.
+//
+// Data flow of one level: the LP writes the detail image D; stages 1 and 2
+// run fused in k_dfb_a, whose stage-2 channels are D's four polyphase
+// classes; from stage 3 on every channel is a compact array, and a stage is a
+// split of it into even / odd rows with a 4 x 4 stencil whose columns shear by
+// -i per row (row offset a, column offset -i*a + (b-a)/2), run by k_dfb_b.
+// Family-r channels are stored transposed between stages so that the same row
+// split serves them; the last stage writes every subband into its slot of the
+// coefficient layout (family r transposed back).  Channels of a stage sit in
+// tree order, channel c at offset c * H*W / 2^(s-1) of a ping-pong pair of
+// level buffers.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -79,7 +86,7 @@ size_t workspace_elems(int H, int W, int L) {
     size_t n = 0;
     for (int j = 1; j <= L; j++) {
         size_t hj = (size_t)(H >> (j - 1)), wj = (size_t)(W >> (j - 1));
-        n += hj * wj + (hj / 2) * (wj / 2);
+        n += 2 * hj * wj + (hj / 2) * (wj / 2);   // detail D_j, its ping-pong partner Q_j, lowpass c_j
     }
     return n;
 }
@@ -90,63 +97,6 @@ CtEngine::~CtEngine() {
 
 namespace {
 
-const int A4[4] = {-3, -1, 1, 3};
-const float BT4[4] = {-1.f / 16, -9.f / 16, 9.f / 16, 1.f / 16};
-
-inline int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
-
-struct LiftSpec {     // one pass-independent description of a target coset
-    View parent;      // target coset inside the parent (in place)
-    View child;       // where the child (output coset) lives after the stage
-    int rows, cols;
-    int tsel_src;     // unused
-};
-
-// Stencil of a target coset: 16 (sel, dr, dc, w)
-struct Stencil {
-    int8_t sel[16];
-    int16_t dr[16], dc[16];
-    float w[16];
-};
-
-// stage 1 / 2 stencils on polyphase components: target component (pr, pc),
-// grid offsets (al, ga) per tap; the source component list is given.
-Stencil poly_stencil(int pr, int pc, const int (*off)[2], const int (*srcs)[2], int nsrc) {
-    Stencil S;
-    int t = 0;
-    for (int ia = 0; ia < 4; ia++)
-        for (int ib = 0; ib < 4; ib++, t++) {
-            int al = off[t][0], ga = off[t][1];
-            int qr = (pr + al) & 1, qc = (pc + ga) & 1;
-            int sel = -1;
-            for (int s = 0; s < nsrc; s++)
-                if (srcs[s][0] == qr && srcs[s][1] == qc) sel = s;
-            if (sel < 0) { fprintf(stderr, "cvc: internal stencil error\n"); abort(); }
-            S.sel[t] = (int8_t)sel;
-            S.dr[t] = (int16_t)floordiv2(pr + al);
-            S.dc[t] = (int16_t)floordiv2(pc + ga);
-            S.w[t] = BT4[ia] * BT4[ib];
-        }
-    return S;
-}
-
-// stage >= 3 stencil; fam 0: split rows, fam 1: split columns; odd target or even target
-Stencil shear_stencil(int fam, int i, bool odd_target) {
-    Stencil S;
-    int t = 0;
-    for (int ia = 0; ia < 4; ia++)
-        for (int ib = 0; ib < 4; ib++, t++) {
-            int a = A4[ia], b = A4[ib];
-            int along = odd_target ? (a + 1) / 2 : (a - 1) / 2;  // a odd: exact
-            int across = -i * a + (b - a) / 2;
-            S.sel[t] = 0;
-            if (fam == 0) { S.dr[t] = (int16_t)along; S.dc[t] = (int16_t)across; }
-            else { S.dr[t] = (int16_t)across; S.dc[t] = (int16_t)along; }
-            S.w[t] = BT4[ia] * BT4[ib];
-        }
-    return S;
-}
-
 View mk(int b, long long off, int rs, int cs) {
     View v;
     v.off = off;
@@ -156,174 +106,86 @@ View mk(int b, long long off, int rs, int cs) {
     return v;
 }
 
-// A coset target of one stage: its parent-array view, the view its child
-// occupies after the stage, its size and the stencils for both parities.
-struct Target {
-    View par, chi;
-    int rows, cols;
-    Stencil st;
-    View src_par[2], src_chi[2];  // source coset views before / after the stage
-    int nsrc;
-};
-
-// All targets of one stage of one (plane, level): odd-parity list and even-parity list
-struct StagePlan {
-    std::vector<Target> odd, even;
-};
-
-struct Chan {
-    int T, i;   // family (0 = c, 1 = r), slope index
-    View v;     // channel array view (in the detail buffer, or a coefficient slot if final)
-    int rows, cols;
-};
-
-// Build the stage plans of one DFB (plane, level): D = detail view (B_WORK,
-// pitch W), slots = coefficient offsets of the 2^k subbands (B_COEF).
-std::vector<StagePlan> dfb_stages(View D, int H, int W, int k, const std::vector<long long>& slot) {
-    std::vector<StagePlan> out(k + 1);
-    if (k == 0) return out;
-    const int Wp = D.rs;
-    auto comp = [&](int pr, int pc) { return mk(D.b, D.off + (long long)pr * Wp + pc, 2 * Wp, 2); };
+// DFB jobs of one (plane, level): detail D_j at doff, partner Q_j at qoff,
+// subband slots (coefficient offsets) in tree order.
+void dfb_jobs(int H, int W, int k, long long doff, long long qoff, const std::vector<long long>& slot,
+              std::vector<DfbAJob>& ajobs, std::vector<std::vector<DfbBJob>>& bjobs) {
+    if (k == 0) return;
     const int h2 = H / 2, w2 = W / 2;
-    // ---- stage 1: polyphase components; E = {00, 11}, O = {01, 10}
-    {
-        int off[16][2];
-        int t = 0;
-        for (int ia = 0; ia < 4; ia++)
-            for (int ib = 0; ib < 4; ib++, t++) {
-                off[t][0] = (A4[ia] + A4[ib]) / 2;
-                off[t][1] = (A4[ia] - A4[ib]) / 2;
-            }
-        const int E[2][2] = {{0, 0}, {1, 1}}, O[2][2] = {{0, 1}, {1, 0}};
-        // child views: in place, or the two row-compacted quincunx subbands when k == 1
-        auto child = [&](int pr, int pc) {
-            if (k > 1) return comp(pr, pc);
-            bool even = ((pr + pc) & 1) == 0;
-            long long base = slot[even ? 0 : 1];
-            // row-compacted subband: row r holds the coset's samples of image row r
-            return mk(B_COEF, base + (long long)pr * w2, 2 * w2, 1);
-        };
-        for (int par = 0; par < 2; par++) {
-            const int(*tg)[2] = par ? O : E;
-            const int(*sr)[2] = par ? E : O;
-            for (int c = 0; c < 2; c++) {
-                Target T;
-                T.par = comp(tg[c][0], tg[c][1]);
-                T.chi = child(tg[c][0], tg[c][1]);
-                T.rows = h2;
-                T.cols = w2;
-                T.st = poly_stencil(tg[c][0], tg[c][1], off, sr, 2);
-                T.nsrc = 2;
-                for (int s = 0; s < 2; s++) {
-                    T.src_par[s] = comp(sr[s][0], sr[s][1]);
-                    T.src_chi[s] = child(sr[s][0], sr[s][1]);
-                }
-                (par ? out[1].odd : out[1].even).push_back(T);
-            }
-        }
+    const long long hw = (long long)H * W;
+    DfbAJob A;
+    memset(&A, 0, sizeof(A));
+    A.D = mk(B_WORK, doff, W, 1);
+    A.H = H;
+    A.W = W;
+    A.nst = k == 1 ? 1 : 2;
+    A.tiles_x = (W + DFBA_TILE - 1) / DFBA_TILE;
+    // polyphase classes q = 2*pr + pc: 00, 01, 10, 11
+    if (k == 1) {
+        // stage-1 cosets are the subbands: {00, 11} row-compacted into slot 0, {01, 10} into slot 1
+        A.comp[0] = mk(B_COEF, slot[0], W, 1);
+        A.comp[3] = mk(B_COEF, slot[0] + w2, W, 1);
+        A.comp[1] = mk(B_COEF, slot[1], W, 1);
+        A.comp[2] = mk(B_COEF, slot[1] + w2, W, 1);
+    } else if (k == 2) {
+        // stage-2 channels in tree order: c(i=-1) = 00, c(i=0) = 11, r(i=-1) = 10, r(i=0) = 01
+        A.comp[0] = mk(B_COEF, slot[0], w2, 1);
+        A.comp[3] = mk(B_COEF, slot[1], w2, 1);
+        A.comp[2] = mk(B_COEF, slot[2], w2, 1);
+        A.comp[1] = mk(B_COEF, slot[3], w2, 1);
+    } else {
+        // compact channel arrays in Q_j, family r transposed ((W/2) x (H/2))
+        A.comp[0] = mk(B_WORK, qoff, w2, 1);
+        A.comp[3] = mk(B_WORK, qoff + hw / 4, w2, 1);
+        A.comp[2] = mk(B_WORK, qoff + 2 * hw / 4, 1, h2);
+        A.comp[1] = mk(B_WORK, qoff + 3 * hw / 4, 1, h2);
     }
-    if (k == 1) return out;
-    // ---- stage 2: family c on {00 (E), 11 (O)} with grid offsets (a, b);
-    //               family r on {10 (E), 01 (O)} with grid offsets (b, a)
-    std::vector<Chan> chans;
-    {
-        auto child2 = [&](int leaf, int pr, int pc) {
-            if (k > 2) return comp(pr, pc);
-            return mk(B_COEF, slot[leaf], w2, 1);
-        };
-        const int fams[2][2][2] = {{{0, 0}, {1, 1}}, {{1, 0}, {0, 1}}};  // [fam][E/O][pr,pc]
-        for (int fam = 0; fam < 2; fam++) {
-            int off[16][2];
-            int t = 0;
-            for (int ia = 0; ia < 4; ia++)
-                for (int ib = 0; ib < 4; ib++, t++) {
-                    off[t][0] = fam == 0 ? A4[ia] : A4[ib];
-                    off[t][1] = fam == 0 ? A4[ib] : A4[ia];
-                }
-            for (int par = 0; par < 2; par++) {
-                int pr = fams[fam][par][0], pc = fams[fam][par][1];
-                int qr = fams[fam][1 - par][0], qc = fams[fam][1 - par][1];
-                int srcs[1][2] = {{qr, qc}};
-                Target T;
-                T.par = comp(pr, pc);
-                T.chi = child2(2 * fam + par, pr, pc);
-                T.rows = h2;
-                T.cols = w2;
-                T.st = poly_stencil(pr, pc, off, srcs, 1);
-                T.nsrc = 1;
-                T.src_par[0] = comp(qr, qc);
-                T.src_chi[0] = child2(2 * fam + (1 - par), qr, qc);
-                T.src_par[1] = T.src_par[0];
-                T.src_chi[1] = T.src_chi[0];
-                (par ? out[2].odd : out[2].even).push_back(T);
-            }
-            chans.push_back({fam, -1, comp(fams[fam][0][0], fams[fam][0][1]), h2, w2});
-            chans.push_back({fam, 0, comp(fams[fam][1][0], fams[fam][1][1]), h2, w2});
-        }
-    }
-    // ---- stages 3..k: even / odd rows (family c) or columns (family r)
+    ajobs.push_back(A);
+    if (k <= 2) return;
+    // stages 3..k: channel list (family, slope index) in tree order
+    std::vector<std::pair<int, int>> ch = {{0, -1}, {0, 0}, {1, -1}, {1, 0}};
     for (int s = 3; s <= k; s++) {
-        std::vector<Chan> next;
         const bool fin = (s == k);
-        for (size_t ci = 0; ci < chans.size(); ci++) {
-            const Chan& C = chans[ci];
-            View pe, po;
-            int rows = C.rows, cols = C.cols;
-            if (C.T == 0) {
-                pe = mk(C.v.b, C.v.off, 2 * C.v.rs, C.v.cs);
-                po = mk(C.v.b, C.v.off + C.v.rs, 2 * C.v.rs, C.v.cs);
-                rows /= 2;
+        const long long xin = (s % 2 == 1) ? qoff : doff;    // stage 3 reads Q_j, writes D_j, ...
+        const long long yout = (s % 2 == 1) ? doff : qoff;
+        const long long csize = hw >> (s - 1);               // elements of one stage-s channel
+        std::vector<std::pair<int, int>> next;
+        for (size_t c = 0; c < ch.size(); c++) {
+            const int fam = ch[c].first, i = ch[c].second;
+            const int R = fam == 0 ? (H >> (s - 2)) : (W >> (s - 2));
+            const int C = fam == 0 ? w2 : h2;
+            const int R2 = R / 2;
+            DfbBJob J;
+            memset(&J, 0, sizeof(J));
+            const long long off = xin + (long long)c * csize;
+            J.pe = mk(B_WORK, off, 2 * C, 1);
+            J.po = mk(B_WORK, off + C, 2 * C, 1);
+            if (!fin) {
+                const long long co = yout + (long long)c * csize;
+                J.c0 = mk(B_WORK, co, C, 1);
+                J.c1 = mk(B_WORK, co + csize / 2, C, 1);
+            } else if (fam == 0) {
+                J.c0 = mk(B_COEF, slot[2 * c], C, 1);
+                J.c1 = mk(B_COEF, slot[2 * c + 1], C, 1);
             } else {
-                pe = mk(C.v.b, C.v.off, C.v.rs, 2 * C.v.cs);
-                po = mk(C.v.b, C.v.off + C.v.cs, C.v.rs, 2 * C.v.cs);
-                cols /= 2;
+                // subband (H/2) x (W >> (k-1)) is the transpose of the R2 x C child
+                J.c0 = mk(B_COEF, slot[2 * c], 1, R2);
+                J.c1 = mk(B_COEF, slot[2 * c + 1], 1, R2);
             }
-            View ce = pe, co = po;
-            if (fin) {
-                ce = mk(B_COEF, slot[2 * ci], cols, 1);
-                co = mk(B_COEF, slot[2 * ci + 1], cols, 1);
-            }
-            Target te, to;
-            te.par = pe; te.chi = ce; te.rows = rows; te.cols = cols; te.nsrc = 1;
-            te.st = shear_stencil(C.T, C.i, false);
-            te.src_par[0] = te.src_par[1] = po;
-            te.src_chi[0] = te.src_chi[1] = co;
-            to.par = po; to.chi = co; to.rows = rows; to.cols = cols; to.nsrc = 1;
-            to.st = shear_stencil(C.T, C.i, true);
-            to.src_par[0] = to.src_par[1] = pe;
-            to.src_chi[0] = to.src_chi[1] = ce;
-            out[s].even.push_back(te);
-            out[s].odd.push_back(to);
-            next.push_back({C.T, 2 * C.i, ce, rows, cols});
-            next.push_back({C.T, 2 * C.i + 1, co, rows, cols});
+            J.R2 = R2;
+            J.C = C;
+            J.i = i;
+            J.tiles_x = (C + DFBB_COLS - 1) / DFBB_COLS;
+            bjobs[s].push_back(J);
+            next.push_back({fam, 2 * i});
+            next.push_back({fam, 2 * i + 1});
         }
-        chans.swap(next);
+        ch.swap(next);
     }
-    return out;
-}
-
-LiftJob make_job(const Target& T, View out, View tin, bool src_after, float alpha, float gamma) {
-    LiftJob J;
-    memset(&J, 0, sizeof(J));
-    J.out = out;
-    J.tin = tin;
-    J.src[0] = src_after ? T.src_chi[0] : T.src_par[0];
-    J.src[1] = src_after ? T.src_chi[1] : T.src_par[1];
-    J.rows = T.rows;
-    J.cols = T.cols;
-    J.alpha = alpha;
-    J.gamma = gamma;
-    for (int t = 0; t < 16; t++) {
-        J.w[t] = T.st.w[t];
-        J.sel[t] = T.st.sel[t];
-        J.dr[t] = T.st.dr[t];
-        J.dc[t] = T.st.dc[t];
-    }
-    return J;
 }
 
 template <class Job>
-bool upload(std::vector<Job>& jobs, bool to_device, CtEngine* e, Job** d_jobs, int** d_bj, int* nblocks,
+bool upload(std::vector<Job>& jobs, bool to_device, CtEngine* e, void** d_jobs, int** d_bj, int* nblocks,
             int (*count)(const Job&)) {
     std::vector<int> bj;
     for (size_t i = 0; i < jobs.size(); i++) {
@@ -345,15 +207,18 @@ bool upload(std::vector<Job>& jobs, bool to_device, CtEngine* e, Job** d_jobs, i
     return true;
 }
 
-int count_lift(const LiftJob& J) { return (int)(((long long)J.rows * J.cols + 255) / 256); }
 int count_lp(const LpJob& J) {
     int ty = (J.H + LP_TILE - 1) / LP_TILE, tx = (J.W + LP_TILE - 1) / LP_TILE;
     return ty * tx;
 }
+int count_a(const DfbAJob& J) {
+    return ((J.H + DFBA_TILE - 1) / DFBA_TILE) * J.tiles_x;
+}
+int count_b(const DfbBJob& J) {
+    return ((J.R2 + DFBB_ROWS - 1) / DFBB_ROWS) * J.tiles_x;
+}
 
 }  // namespace
-
-static_assert(sizeof(LiftJob) % 4 == 0, "LiftJob is copied as 32-bit words");
 
 bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_device) {
     e->planes = planes_in;
@@ -372,18 +237,19 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
     for (int m = 0; m < 4; m++) {
         const bool analysis = (m == FWD || m == INV_ADJ);
         const int spatial_base = analysis ? B_IN : B_OUT;
-        // ---- LP jobs per level
         std::vector<std::vector<LpJob>> lpj(Lmax + 1);
-        // ---- lifting jobs per (stage, pass)
-        std::vector<std::vector<LiftJob>> lj1(kmax + 1), lj2(kmax + 1);
+        std::vector<DfbAJob> aj;
+        std::vector<std::vector<DfbBJob>> bj(std::max(kmax, 2) + 1);
         for (size_t p = 0; p < e->planes.size(); p++) {
             const PlaneRef& P = e->planes[p];
             const PlaneLayout& Ly = lays[p];
             long long w = P.work;
-            std::vector<long long> coff(P.L + 1), doff(P.L + 1);
+            std::vector<long long> coff(P.L + 1), doff(P.L + 1), qoff(P.L + 1);
             for (int j = 1; j <= P.L; j++) {
                 long long hj = P.H >> (j - 1), wj = P.W >> (j - 1);
                 doff[j] = w;
+                w += hj * wj;
+                qoff[j] = w;
                 w += hj * wj;
                 coff[j] = w;
                 w += (hj / 2) * (wj / 2);
@@ -413,57 +279,53 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                     J.out = spatial_prev;
                 }
                 lpj[j].push_back(J);
-                if (kj == 0) continue;
-                std::vector<StagePlan> sp = dfb_stages(mk(B_WORK, doff[j], wj, 1), hj, wj, kj, slots);
-                for (int s = 1; s <= kj; s++) {
-                    for (const Target& T : sp[s].odd) {
-                        if (m == FWD) lj1[s].push_back(make_job(T, T.chi, T.par, false, 0.5f, -0.5f));
-                        if (m == INV_ADJ) lj2[s].push_back(make_job(T, T.chi, T.par, true, 2.f, -1.f));
-                        if (m == INV) lj2[s].push_back(make_job(T, T.par, T.chi, false, 2.f, 1.f));
-                        if (m == FWD_ADJ) lj1[s].push_back(make_job(T, T.par, T.chi, true, 0.5f, 0.5f));
-                    }
-                    for (const Target& T : sp[s].even) {
-                        if (m == FWD) lj2[s].push_back(make_job(T, T.chi, T.par, true, 1.f, 1.f));
-                        if (m == INV_ADJ) lj1[s].push_back(make_job(T, T.chi, T.par, false, 1.f, 1.f));
-                        if (m == INV) lj1[s].push_back(make_job(T, T.par, T.chi, true, 1.f, -1.f));
-                        if (m == FWD_ADJ) lj2[s].push_back(make_job(T, T.par, T.chi, false, 1.f, -1.f));
-                    }
-                }
+                dfb_jobs(hj, wj, kj, doff[j], qoff[j], slots, aj, bj);
             }
         }
-        // Pass sources: in the analysis direction, pass 1 reads the parent's
-        // other coset, pass 2 the child written by pass 1.  In the synthesis
-        // direction pass 1 reads the other child, pass 2 the parent coset
-        // written by pass 1 -- make_job's src_after flag encodes exactly that
-        // (it selects the child views when true).
         e->lp[m].clear();
-        e->lift[m].clear();
+        e->dfb[m].clear();
         e->h_lp[m].clear();
-        e->h_lift[m].clear();
+        e->h_dfb[m].clear();
         auto add_lp = [&](std::vector<LpJob>& v) {
             LaunchLp L{};
-            if (!upload<LpJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_lp)) return false;
+            void* dj = nullptr;
+            if (!upload<LpJob>(v, to_device, e, &dj, &L.d_block_job, &L.nblocks, count_lp)) return false;
+            L.d_jobs = static_cast<LpJob*>(dj);
             L.njobs = (int)v.size();
             e->lp[m].push_back(L);
             e->h_lp[m].push_back(v);
             return true;
         };
-        auto add_lift = [&](std::vector<LiftJob>& v) {
-            LaunchLift L{};
-            if (!upload<LiftJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_lift)) return false;
+        auto add_a = [&](std::vector<DfbAJob>& v) {
+            LaunchDfb L{};
+            L.kind = 0;
+            if (!upload<DfbAJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_a)) return false;
             L.njobs = (int)v.size();
-            e->lift[m].push_back(L);
-            e->h_lift[m].push_back(v);
+            e->dfb[m].push_back(L);
+            e->h_dfb[m].emplace_back(reinterpret_cast<uint8_t*>(v.data()),
+                                     reinterpret_cast<uint8_t*>(v.data() + v.size()));
+            return true;
+        };
+        auto add_b = [&](std::vector<DfbBJob>& v) {
+            LaunchDfb L{};
+            L.kind = 1;
+            if (!upload<DfbBJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_b)) return false;
+            L.njobs = (int)v.size();
+            e->dfb[m].push_back(L);
+            e->h_dfb[m].emplace_back(reinterpret_cast<uint8_t*>(v.data()),
+                                     reinterpret_cast<uint8_t*>(v.data() + v.size()));
             return true;
         };
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)
                 if (!add_lp(lpj[j])) return false;
-            for (int s = 1; s <= kmax; s++)
-                if (!add_lift(lj1[s]) || !add_lift(lj2[s])) return false;
+            if (!aj.empty() && !add_a(aj)) return false;
+            for (int s = 3; s <= kmax; s++)
+                if (!bj[s].empty() && !add_b(bj[s])) return false;
         } else {
-            for (int s = kmax; s >= 1; s--)
-                if (!add_lift(lj1[s]) || !add_lift(lj2[s])) return false;
+            for (int s = kmax; s >= 3; s--)
+                if (!bj[s].empty() && !add_b(bj[s])) return false;
+            if (!aj.empty() && !add_a(aj)) return false;
             for (int j = Lmax; j >= 1; j--)
                 if (!add_lp(lpj[j])) return false;
         }
@@ -479,8 +341,8 @@ cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cu
             note_launches(L.nblocks > 0);
         }
     } else {
-        for (const LaunchLift& L : e->lift[m]) {
-            if ((err = launch_lift(L, m, bases, st)) != cudaSuccess) return err;
+        for (const LaunchDfb& L : e->dfb[m]) {
+            if ((err = launch_dfb(L, m, bases, st)) != cudaSuccess) return err;
             note_launches(L.nblocks > 0);
         }
     }
@@ -492,7 +354,7 @@ int engine_part_launches(const CtEngine* e, Mode m, int part) {
     if (part == 0)
         for (const LaunchLp& L : e->lp[m]) n += L.nblocks > 0;
     else
-        for (const LaunchLift& L : e->lift[m]) n += L.nblocks > 0;
+        for (const LaunchDfb& L : e->dfb[m]) n += L.nblocks > 0;
     return n;
 }
 

@@ -33,17 +33,44 @@ struct View {
     int rs, cs;
 };
 
-// One lifting pass of the directional filter bank on one target coset array:
-//   out(u,v) = alpha * tin(u,v) + gamma * sum_t w[t] * src_{sel[t]}((u+dr[t]) mod rows, (v+dc[t]) mod cols)
-struct LiftJob {
-    View out, tin, src[2];
-    int rows, cols;
-    float alpha, gamma;
-    float w[16];
-    int8_t sel[16];
-    int16_t dr[16], dc[16];
-    int first_block;  // first flat block of this job in the launch
+// Directional filter bank jobs.  Each DFB stage is a two-channel fan filter
+// bank in ladder form: a pass over one coset of a channel's samples (the
+// "target" parity) followed by a pass over the other, each sample becoming
+//   alpha * itself + gamma * (16-tap stencil of the other coset).
+// The mode fixes which parity goes first and the (alpha, gamma) pairs.
+struct PassParams {
+    int first_odd;      // 1: the odd coset is the first target
+    float a1, g1, a2, g2;
 };
+
+// Stages 1 and 2 of one detail image, fused in 64 x 64 tiles.  The stage-2
+// channels are the image's polyphase classes q = 2*(row & 1) + (col & 1);
+// comp[q] is where class q lives outside the image: the children in the
+// analysis direction, the inputs in the synthesis direction.  nst = 1 runs
+// stage 1 only (its cosets, classes {00, 11} and {01, 10}, are then the
+// subbands and comp[] points into them).
+struct DfbAJob {
+    View D;        // H x W detail image (rs = pitch, cs = 1)
+    View comp[4];  // (H/2) x (W/2) each, any strides
+    int H, W;
+    int nst;
+    int tiles_x, first_block;
+};
+
+// One stage s >= 3 of one channel: its array splits into even / odd rows,
+// R2 x C each, under the 4 x 4 stencil of slope index i (row offset a, column
+// offset -i*a + (b-a)/2).  Family-r channels are kept transposed so the same
+// job serves both families.
+struct DfbBJob {
+    View pe, po;   // parent's even / odd rows
+    View c0, c1;   // children (even / odd rows), any strides
+    int R2, C;
+    int i;
+    int tiles_x, first_block;
+};
+
+constexpr int DFBA_TILE = 64, DFBA_HALO = 12;
+constexpr int DFBB_ROWS = 16, DFBB_COLS = 128;
 
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)
@@ -84,9 +111,10 @@ struct LaunchLp {
     LpJob* d_jobs;
     int* d_block_job;
 };
-struct LaunchLift {
+struct LaunchDfb {
+    int kind;  // 0: DfbAJob, 1: DfbBJob
     int njobs, nblocks;
-    LiftJob* d_jobs;
+    void* d_jobs;
     int* d_block_job;
 };
 
@@ -97,10 +125,10 @@ struct CtEngine {
     long long work_elems = 0;
     // per mode: LP launches in execution order and DFB passes in execution order
     std::vector<LaunchLp> lp[4];
-    std::vector<LaunchLift> lift[4];
+    std::vector<LaunchDfb> dfb[4];
     // host copies of the job tables, launch by launch (for plan self-checks)
     std::vector<std::vector<LpJob>> h_lp[4];
-    std::vector<std::vector<LiftJob>> h_lift[4];
+    std::vector<std::vector<uint8_t>> h_dfb[4];
     std::vector<void*> allocs;
     ~CtEngine();
 };
@@ -119,6 +147,7 @@ void note_launches(int n);
 
 // -------------------------------------------------------------- kernels
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st);
-cudaError_t launch_lift(const LaunchLift& L, Mode m, Bases bases, cudaStream_t st);
+cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st);
+PassParams pass_params(Mode m);
 
 }  // namespace cvc

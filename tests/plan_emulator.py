@@ -10,8 +10,15 @@ semantics of the two kernels:
   LP level job (synthesis):  v = cin - down(main, fa);    out = main + up(v, fs)
   DFB lifting job:           out(u,v) = alpha tin(u,v) + gamma sum_t w_t src_sel(u+dr, v+dc)  (periodic)
 
+  DFB stages 1+2 job:        the fan filter bank stages 1 (and 2) on the
+                             whole periodic detail image, whose polyphase
+                             classes are the stage-2 channels (comp[q])
+  DFB row-split job:         one stage s >= 3 of a channel: even / odd rows
+                             E, O of its array, stencil row offset (a +- 1)/2,
+                             column offset -i*a + (b-a)/2 (periodic)
+
 so that a test can compare the planned computation with the oracle before
-any kernel runs on a GPU.
+any kernel runs on a GPU.  Each pass sets target = alpha*target + gamma*sum.
 """
 import ctypes
 
@@ -23,9 +30,15 @@ from paper_1510_00561_b300 import _lib as L
 VIEW = np.dtype([("off", "<i8"), ("b", "<i4"), ("rs", "<i4"), ("cs", "<i4"), ("pad", "<i4")])
 LPJOB = np.dtype([("main", VIEW), ("cin", VIEW), ("cout", VIEW), ("out", VIEW), ("H", "<i4"), ("W", "<i4"),
                   ("tiles_x", "<i4"), ("first_block", "<i4")])
-LIFTJOB = np.dtype([("out", VIEW), ("tin", VIEW), ("src", VIEW, (2,)), ("rows", "<i4"), ("cols", "<i4"),
-                    ("alpha", "<f4"), ("gamma", "<f4"), ("w", "<f4", (16,)), ("sel", "i1", (16,)),
-                    ("dr", "<i2", (16,)), ("dc", "<i2", (16,)), ("first_block", "<i4"), ("pad", "<i4")])
+AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), ("nst", "<i4"),
+                 ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
+BJOB = np.dtype([("pe", VIEW), ("po", VIEW), ("c0", VIEW), ("c1", VIEW), ("R2", "<i4"), ("C", "<i4"),
+                 ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
+BT = np.array([-1.0, -9.0, 9.0, 1.0]) / 16
+A4 = [-3, -1, 1, 3]
+# (first target is the odd coset, alpha1, gamma1, alpha2, gamma2) per mode
+PASSES = {0: (1, 0.5, -0.5, 1.0, 1.0), 3: (0, 1.0, 1.0, 2.0, -1.0),
+          1: (0, 1.0, -1.0, 2.0, 1.0), 2: (1, 0.5, 0.5, 1.0, -1.0)}
 
 
 def tables(mode, params=None, h=0, w=0, levels=0, dirs=(), batch=1):
@@ -38,20 +51,49 @@ def tables(mode, params=None, h=0, w=0, levels=0, dirs=(), batch=1):
     st = lib.cvc_debug_plan_tables(pp, h, w, levels, L.ints(dirs), batch, mode, buf, used.value, ctypes.byref(used))
     assert st == 0, st
     raw = bytes(buf)
-    magic, nl, lpb, lfb = np.frombuffer(raw[:16], "<u4")
-    assert magic == 0x43564350 and lpb == LPJOB.itemsize and lfb == LIFTJOB.itemsize
-    elems = np.frombuffer(raw[16:48], "<u8").astype(np.int64)
-    pos = 48
+    magic, nl, lpb, ab, bb, _ = np.frombuffer(raw[:24], "<u4")
+    assert magic == 0x43564350 and lpb == LPJOB.itemsize and ab == AJOB.itemsize and bb == BJOB.itemsize
+    elems = np.frombuffer(raw[24:56], "<u8").astype(np.int64)
+    pos = 56
     launches = []
     for _ in range(nl):
         kind, nj = np.frombuffer(raw[pos:pos + 8], "<u4")
         pos += 8
-        dt = LPJOB if kind == 0 else LIFTJOB
+        dt = (LPJOB, AJOB, BJOB)[kind]
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
         launches.append((int(kind), jobs))
     assert pos == len(raw)
     return elems, launches
+
+
+def _stage_a_pass(img, stage, odd, alpha, gamma):
+    """One pass of DFB stage 1 or 2 over the whole periodic image, in place."""
+    H, W = img.shape
+    r, c = np.mgrid[0:H, 0:W]
+    if stage == 1:
+        mask = ((r + c) & 1) == odd
+        offs = [((a + b) // 2, (a - b) // 2) for a in A4 for b in A4]
+        acc = sum(BT[t // 4] * BT[t % 4] * np.roll(img, (-dy, -dx), axis=(0, 1)) for t, (dy, dx) in enumerate(offs))
+    else:
+        mask = (c & 1) == odd
+        fam_c = (r & 1) == (c & 1)
+        acc_c = sum(BT[ia] * BT[ib] * np.roll(img, (-a, -b), axis=(0, 1))
+                    for ia, a in enumerate(A4) for ib, b in enumerate(A4))
+        acc_r = sum(BT[ia] * BT[ib] * np.roll(img, (-b, -a), axis=(0, 1))
+                    for ia, a in enumerate(A4) for ib, b in enumerate(A4))
+        acc = np.where(fam_c, acc_c, acc_r)
+    img[mask] = alpha * img[mask] + gamma * acc[mask]
+
+
+def _rowsplit_stencil(S, i, odd_target):
+    acc = np.zeros_like(S)
+    for ia, a in enumerate(A4):
+        for ib, b in enumerate(A4):
+            dr = (a + 1) // 2 if odd_target else (a - 1) // 2
+            dc = -i * a + (b - a) // 2
+            acc += BT[ia] * BT[ib] * np.roll(S, (-dr, -dc), axis=(0, 1))
+    return acc
 
 
 def _index(v, rows, cols):
@@ -82,66 +124,87 @@ def _up(v, f):
     return sum(f[a + R] * np.roll(z, a, axis=0) for a in range(-R, R + 1))
 
 
+def _views_of(kind, J, synth):
+    """(reads, writes): lists of (name, view, rows, cols) a job touches."""
+    if kind == 0:
+        H, W = int(J["H"]), int(J["W"])
+        if not synth:
+            return [("main", J["main"], H, W)], [("cout", J["cout"], H // 2, W // 2), ("out", J["out"], H, W)]
+        return [("main", J["main"], H, W), ("cin", J["cin"], H // 2, W // 2)], [("out", J["out"], H, W)]
+    if kind == 1:
+        H, W = int(J["H"]), int(J["W"])
+        comps = [("comp%d" % q, J["comp"][q], H // 2, W // 2) for q in range(4)]
+        D = [("D", J["D"], H, W)]
+        return (D, comps) if not synth else (comps, D)
+    R2, C = int(J["R2"]), int(J["C"])
+    par = [("pe", J["pe"], R2, C), ("po", J["po"], R2, C)]
+    chi = [("c0", J["c0"], R2, C), ("c1", J["c1"], R2, C)]
+    return (par, chi) if not synth else (chi, par)
+
+
 def run(mode, elems, launches, bufs):
     """Execute the launches on bufs (dict base id -> float64 array); checks bounds and hazards."""
     h, g = O.cdf97()
     fa, fs = (h, g) if mode in (0, 1) else (g, h)
     synth = mode in (1, 2)
+    fo, a1, g1, a2, g2 = PASSES[mode]
     for kind, jobs in launches:
-        writes, results = [], []
-        wjob, rjob = [], []
+        results, wjob, rjob = [], [], []
         for ji, J in enumerate(jobs):
+            reads, writes = _views_of(kind, J, synth)
+            rd = {}
+            for name, v, rr, cc in reads:
+                b, idx = _index(v, rr, cc)
+                _check(b, idx, elems, "read " + name)
+                rd[name] = bufs[b][idx]
+                rjob.append((ji, (b, idx)))
+            out = {}
             if kind == 0:
-                H, W = int(J["H"]), int(J["W"])
-                bm, im = _index(J["main"], H, W)
-                _check(bm, im, elems, "lp main")
-                X = bufs[bm][im]
-                rjob.append((ji, (bm, im)))
+                X = rd["main"]
                 if not synth:
-                    bc, ic = _index(J["cout"], H // 2, W // 2)
-                    _check(bc, ic, elems, "lp cout")
-                    c = _down(X, fa)
-                    results.append((bc, ic, c))
-                    writes.append((bc, ic))
-                    wjob.append((ji, bc, ic))
-                    out = X - _up(c, fs)
+                    out["cout"] = _down(X, fa)
+                    out["out"] = X - _up(out["cout"], fs)
                 else:
-                    bc, ic = _index(J["cin"], H // 2, W // 2)
-                    _check(bc, ic, elems, "lp cin")
-                    rjob.append((ji, (bc, ic)))
-                    out = X + _up(bufs[bc][ic] - _down(X, fa), fs)
-                bo, io = _index(J["out"], H, W)
-                _check(bo, io, elems, "lp out")
-                results.append((bo, io, out))
-                writes.append((bo, io))
-                wjob.append((ji, bo, io))
+                    out["out"] = X + _up(rd["cin"] - _down(X, fa), fs)
+            elif kind == 1:
+                H, W = int(J["H"]), int(J["W"])
+                nst = int(J["nst"])
+                img = np.zeros((H, W))
+                if not synth:
+                    img[:] = rd["D"]
+                else:
+                    for q in range(4):
+                        img[q >> 1::2, q & 1::2] = rd["comp%d" % q]
+                stages = list(range(1, nst + 1)) if not synth else list(range(nst, 0, -1))
+                for stg in stages:
+                    _stage_a_pass(img, stg, fo, a1, g1)
+                    _stage_a_pass(img, stg, 1 - fo, a2, g2)
+                if not synth:
+                    for q in range(4):
+                        out["comp%d" % q] = img[q >> 1::2, q & 1::2].copy()
+                else:
+                    out["D"] = img
             else:
-                R, C = int(J["rows"]), int(J["cols"])
-                bo, io = _index(J["out"], R, C)
-                bt, it = _index(J["tin"], R, C)
-                _check(bo, io, elems, "lift out")
-                _check(bt, it, elems, "lift tin")
-                srcs = []
-                for s in range(2):
-                    bs, is_ = _index(J["src"][s], R, C)
-                    _check(bs, is_, elems, "lift src")
-                    srcs.append((bs, is_))
-                acc = np.zeros((R, C))
-                used = set()
-                for t in range(16):
-                    bs, is_ = srcs[int(J["sel"][t])]
-                    used.add(int(J["sel"][t]))
-                    sh = np.roll(is_, (-int(J["dr"][t]), -int(J["dc"][t])), axis=(0, 1))
-                    acc += float(J["w"][t]) * bufs[bs][sh]
-                out = float(J["alpha"]) * bufs[bt][it] + float(J["gamma"]) * acc
-                results.append((bo, io, out))
-                writes.append((bo, io))
-                wjob.append((ji, bo, io))
-                rjob.append((ji, (bt, it)))
-                for s in used:
-                    rjob.append((ji, srcs[s]))
+                i = int(J["i"])
+                E, Od = (rd["pe"], rd["po"]) if not synth else (rd["c0"], rd["c1"])
+                E, Od = E.copy(), Od.copy()
+                if fo:
+                    Od = a1 * Od + g1 * _rowsplit_stencil(E, i, True)
+                    E = a2 * E + g2 * _rowsplit_stencil(Od, i, False)
+                else:
+                    E = a1 * E + g1 * _rowsplit_stencil(Od, i, False)
+                    Od = a2 * Od + g2 * _rowsplit_stencil(E, i, True)
+                if not synth:
+                    out["c0"], out["c1"] = E, Od
+                else:
+                    out["pe"], out["po"] = E, Od
+            for name, v, rr, cc in writes:
+                b, idx = _index(v, rr, cc)
+                _check(b, idx, elems, "write " + name)
+                results.append((b, idx, out[name]))
+                wjob.append((ji, b, idx))
         # no job writes an element that another job of the same launch reads or writes
-        for b in set(x[0] for x in writes):
+        for b in set(x[1] for x in wjob):
             w_idx = [(ji, ix.ravel()) for ji, wb, ix in wjob if wb == b]
             allw = np.concatenate([ix for _, ix in w_idx])
             owner = np.concatenate([np.full(ix.size, i) for i, ix in w_idx])
@@ -152,8 +215,7 @@ def run(mode, elems, launches, bufs):
                 if rb != b:
                     continue
                 r = ridx.ravel()
-                pos = np.searchsorted(allw, r)
-                pos = np.clip(pos, 0, allw.size - 1)
+                pos = np.clip(np.searchsorted(allw, r), 0, allw.size - 1)
                 hit = allw[pos] == r
                 assert np.all(owner[pos][hit] == i), "a job reads what another job of its launch writes"
         for b, idx, val in results:
@@ -166,17 +228,7 @@ def check_only(elems, launches, mode):
     synth = mode in (1, 2)
     for kind, jobs in launches:
         for J in jobs:
-            if kind == 0:
-                H, W = int(J["H"]), int(J["W"])
-                for name, (r, c) in (("main", (H, W)), ("out", (H, W)),
-                                     ("cin" if synth else "cout", (H // 2, W // 2))):
-                    b, idx = _index(J[name], r, c)
-                    _check(b, idx, elems, "lp " + name)
-            else:
-                R, C = int(J["rows"]), int(J["cols"])
-                for name in ("out", "tin"):
-                    b, idx = _index(J[name], R, C)
-                    _check(b, idx, elems, "lift " + name)
-                for s in set(int(x) for x in J["sel"]):
-                    b, idx = _index(J["src"][s], R, C)
-                    _check(b, idx, elems, "lift src")
+            reads, writes = _views_of(kind, J, synth)
+            for name, v, rr, cc in reads + writes:
+                b, idx = _index(v, rr, cc)
+                _check(b, idx, elems, name)
