@@ -187,6 +187,72 @@ cvc_status cvc_decode_frame(cvc_codec* codec, const uint8_t* d_in, size_t in_len
 cvc_status cvc_codec_inspect(const cvc_codec* codec, int which, float* d_out, size_t cap_elems,
                              cvc_stream_t stream);
 
+/* --------------------------------------------------------------- batches
+ * Many independent streams, each with its own cvc_params (any mix of frame
+ * sizes and decompositions), coded together: every kernel of a step covers
+ * all streams of the batch (its blocks find their stream through tables
+ * built at creation), and the step's fixed launch sequence is captured once
+ * per step kind in a CUDA graph and replayed, so a step costs one graph
+ * launch, two small copies and one synchronisation whatever the number of
+ * streams.  Each stream's bitstream, reconstruction and coder state are
+ * bit-identical to those of a cvc_codec with the same parameters fed the
+ * same frames; a stream that takes no part in a step is left untouched.    */
+typedef struct cvc_batch cvc_batch;
+
+#define CVC_STEP_ENCODE 1
+#define CVC_STEP_DECODE 2
+#define CVC_STEP_ENCODE_DECODE 3   /* encode, then decode this step's own output */
+
+typedef struct {
+    const uint8_t* d_rgb;   /* encoder input as in cvc_encode_frame; NULL: the stream does not encode */
+    size_t pitch_bytes;
+    uint8_t* d_out;         /* encoder output, 4-byte aligned, out_cap bytes */
+    size_t out_cap;
+    const uint8_t* d_in;    /* decoder input; ignored when the same step encodes the stream
+                               (CVC_STEP_ENCODE_DECODE): the decoder then reads d_out */
+    size_t in_len;
+    uint8_t* d_rgb_out;     /* decoder output as in cvc_decode_frame; NULL: the stream does not decode */
+    size_t pitch_out;
+} cvc_batch_io;
+
+typedef struct {
+    cvc_status enc_status;  /* as cvc_encode_frame (CVC_OK when the stream did not encode) */
+    cvc_status dec_status;  /* as cvc_decode_frame (CVC_OK when the stream did not decode) */
+    size_t out_len;         /* as cvc_encode_frame's *out_len; 0 when the stream did not encode */
+    int frame_type;         /* encoded frame: 0 K, 1 P, -1 none */
+    int dec_frame_type;     /* decoded frame: 0 K, 1 P, -1 none or rejected */
+    uint32_t dec_frame_index;
+} cvc_batch_result;
+
+/* n >= 1 streams with params[0..n-1].  Errors: INVALID_ARG, UNSUPPORTED
+ * (as cvc_create, or a batch whose token space exceeds 32 bits), NOMEM, CUDA. */
+cvc_status cvc_batch_create(const cvc_params* params, int n, cvc_batch** out);
+cvc_status cvc_batch_destroy(cvc_batch* batch);
+/* Device bytes cvc_batch_create would allocate for these streams (host-only,
+ * no device call): the basis of admission against a memory budget.         */
+cvc_status cvc_batch_device_bytes(const cvc_params* params, int n, size_t* bytes);
+cvc_status cvc_batch_info(const cvc_batch* batch, int i, cvc_codec_info_t* out);
+/* as cvc_reset for stream i (i < 0: every stream) */
+cvc_status cvc_batch_reset(cvc_batch* batch, int i);
+
+/* One step of kind `what` (CVC_STEP_*) over every stream: io[i] and res[i]
+ * belong to stream i.  Synchronises `stream`.  Returns INVALID_ARG (nothing
+ * was done) or CUDA for the call; otherwise the first non-OK status in res
+ * (stream order, encoder before decoder), or CVC_OK.                        */
+cvc_status cvc_batch_step(cvc_batch* batch, int what, const cvc_batch_io* io, cvc_batch_result* res,
+                          cvc_stream_t stream);
+
+/* Launch shapes (they change no result): rows per block of the run-length
+ * kernels (1..32) and blocks of the decoder's token kernels (1..65535).
+ * cvc_batch_autotune times candidate shapes on steps over `io` (the outputs
+ * of io are written; no coder state changes), keeps the fastest and returns
+ * it in shape[2] (may be NULL).  Graph replay can be switched off (on = 0)
+ * to run the same launches one by one.                                      */
+cvc_status cvc_batch_set_shape(cvc_batch* batch, int rle_rows, int tok_blocks);
+cvc_status cvc_batch_autotune(cvc_batch* batch, int what, const cvc_batch_io* io, int reps, int* shape,
+                              cvc_stream_t stream);
+cvc_status cvc_batch_set_graphs(cvc_batch* batch, int on);
+
 /* --------------------------------------------------------------- tracing
  * Per-stage GPU time of a codec (the per-operation breakdown of §4.2),
  * measured with CUDA events recorded on the call's stream around each stage
@@ -241,8 +307,9 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  * made, so it works without a GPU): the job tables of every launch of
  * `mode` (0 forward, 1 inverse, 2 adjoint of forward, 3 adjoint of inverse)
  * for a transform plan (params == NULL; h, w, levels, dirs_log2, batch as in
- * cvc_ct_plan_create) or for the three planes of a codec (params != NULL;
- * the other size arguments are ignored).  Layout written to buf, little
+ * cvc_ct_plan_create) or for the planes of the codec streams params[0 ..
+ * batch-1] (params != NULL: cvc_create for batch = 1, cvc_batch_create
+ * otherwise; h, w, levels and dirs_log2 are ignored).  Layout written to buf, little
  * endian:
  *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 bytes of an LP-level
  *   job, u32 bytes of a DFB stage-1+2 job, u32 bytes of a DFB row-split job, u32 0,

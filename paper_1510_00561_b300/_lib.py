@@ -55,6 +55,20 @@ class CodecInfo(ctypes.Structure):
                 ("max_stream_bytes", ctypes.c_longlong)]
 
 
+class BatchIo(ctypes.Structure):
+    _fields_ = [("d_rgb", ctypes.c_void_p), ("pitch_bytes", ctypes.c_size_t), ("d_out", ctypes.c_void_p),
+                ("out_cap", ctypes.c_size_t), ("d_in", ctypes.c_void_p), ("in_len", ctypes.c_size_t),
+                ("d_rgb_out", ctypes.c_void_p), ("pitch_out", ctypes.c_size_t)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("enc_status", ctypes.c_int), ("dec_status", ctypes.c_int), ("out_len", ctypes.c_size_t),
+                ("frame_type", ctypes.c_int), ("dec_frame_type", ctypes.c_int),
+                ("dec_frame_index", ctypes.c_uint32)]
+
+
+STEP_ENCODE, STEP_DECODE, STEP_ENCODE_DECODE = 1, 2, 3
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -91,8 +105,26 @@ def lib():
         L.cvc_kernel_launches.argtypes = []
         L.cvc_kernel_launches.restype = ctypes.c_ulonglong
         L.cvc_lp_pyramid_forward_static.argtypes = [_P, _I, _I, _I, _P, _P]
+        L.cvc_batch_create.argtypes = [ctypes.POINTER(Params), _I, ctypes.POINTER(_P)]
+        L.cvc_batch_destroy.argtypes = [_P]
+        L.cvc_batch_device_bytes.argtypes = [ctypes.POINTER(Params), _I, ctypes.POINTER(_SZ)]
+        L.cvc_batch_info.argtypes = [_P, _I, ctypes.POINTER(CodecInfo)]
+        L.cvc_batch_reset.argtypes = [_P, _I]
+        L.cvc_batch_step.argtypes = [_P, _I, ctypes.POINTER(BatchIo), ctypes.POINTER(BatchResult), _P]
+        L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
+        L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
+        L.cvc_batch_set_graphs.argtypes = [_P, _I]
+        L.cvc_debug_plan_tables.argtypes = [ctypes.POINTER(Params), _I, _I, _I, ctypes.POINTER(_I), _I, _I, _P,
+                                            _SZ, ctypes.POINTER(_SZ)]
         _lib = L
     return _lib
+
+
+def params(width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10):
+    """cvc_params of one stream (qpl defaults to max(1, qph // 14))."""
+    if qpl is None:
+        qpl = max(1, qph // 14)
+    return Params(width, height, levels, ints(dirs_log2), qph, qpl, threshold, key_interval, 1)
 
 
 def check(status, where):

@@ -87,11 +87,9 @@ class Codec:
     """One CVC video stream on the GPU (encoder and decoder state resident in HBM)."""
 
     def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10):
-        if qpl is None:
-            qpl = max(1, qph // 14)
+        prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval)
         self.width, self.height, self.levels, self.dirs = width, height, levels, list(dirs_log2)
-        self.qph, self.qpl, self.threshold, self.key_interval = qph, qpl, threshold, key_interval
-        prm = _L.Params(width, height, levels, _L.ints(dirs_log2), qph, qpl, threshold, key_interval, 1)
+        self.qph, self.qpl, self.threshold, self.key_interval = qph, prm.qpl, threshold, key_interval
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_create")
         self._h = p
@@ -161,3 +159,110 @@ class Codec:
         ny, nc = self.Hp * self.Wp, self.Hcp * self.Wcp
         return (flat[:ny].view(self.Hp, self.Wp), flat[ny:ny + nc].view(self.Hcp, self.Wcp),
                 flat[ny + nc:].view(self.Hcp, self.Wcp))
+
+
+def _info(fn, h, i=None):
+    info = _L.CodecInfo()
+    args = (h, i, ctypes.byref(info)) if i is not None else (h, ctypes.byref(info))
+    _L.check(fn(*args), fn.__name__)
+    return info
+
+
+class Batch:
+    """Many CVC streams coded together: one graph-replayed launch sequence per step.
+
+    streams: list of dicts with the Codec constructor's keyword arguments
+    (width, height, levels, dirs_log2, qph, qpl, threshold, key_interval).
+    Each stream's output is bit-identical to a Codec of the same parameters.
+    """
+
+    def __init__(self, streams):
+        self.streams = [dict(s) for s in streams]
+        n = len(self.streams)
+        arr = (_L.Params * n)(*[_L.params(**s) for s in self.streams])
+        self._params = arr
+        p = ctypes.c_void_p()
+        _L.check(_L.lib().cvc_batch_create(arr, n, ctypes.byref(p)), "cvc_batch_create")
+        self._h = p
+        self.n = n
+        self.info = [_info(_L.lib().cvc_batch_info, p, i) for i in range(n)]
+        self._io = (_L.BatchIo * n)()
+        self._res = (_L.BatchResult * n)()
+        self._out = [None] * n
+
+    @staticmethod
+    def device_bytes(streams):
+        """Device bytes a batch of these streams would allocate (no device call)."""
+        arr = (_L.Params * len(streams))(*[_L.params(**s) for s in streams])
+        b = ctypes.c_size_t(0)
+        _L.check(_L.lib().cvc_batch_device_bytes(arr, len(streams), ctypes.byref(b)), "cvc_batch_device_bytes")
+        return b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _L._lib is not None:
+            _L.lib().cvc_batch_destroy(h)
+            self._h = None
+
+    def reset(self, i=-1):
+        _L.check(_L.lib().cvc_batch_reset(self._h, i), "cvc_batch_reset")
+
+    def out_buffer(self, i, device="cuda"):
+        """A persistent bitstream buffer of stream i (worst-case size)."""
+        if self._out[i] is None:
+            self._out[i] = torch.empty(self.info[i].max_stream_bytes, dtype=torch.uint8, device=device)
+        return self._out[i]
+
+    def _fill(self, rgb, streams_in, rgb_out, outs):
+        for i in range(self.n):
+            io = self._io[i]
+            x = rgb[i] if rgb is not None else None
+            io.d_rgb = x.data_ptr() if x is not None else None
+            io.pitch_bytes = x.stride(0) if x is not None else 0
+            o = outs[i] if outs is not None and outs[i] is not None else (self.out_buffer(i) if x is not None
+                                                                           else None)
+            io.d_out = o.data_ptr() if o is not None else None
+            io.out_cap = o.numel() if o is not None else 0
+            b = streams_in[i] if streams_in is not None else None
+            io.d_in = b.data_ptr() if b is not None else None
+            io.in_len = b.numel() if b is not None else 0
+            y = rgb_out[i] if rgb_out is not None else None
+            io.d_rgb_out = y.data_ptr() if y is not None else None
+            io.pitch_out = y.stride(0) if y is not None else 0
+
+    def step(self, what, rgb=None, streams_in=None, rgb_out=None, outs=None, stream=None, check=True):
+        """One step over every stream (entries None take no part).
+
+        what: 1 encode, 2 decode, 3 encode + decode of the step's own output.
+        Returns a list of per-stream dicts (statuses, out_len, frame types,
+        the encoded bytes as a view of the stream's output buffer)."""
+        self._fill(rgb, streams_in, rgb_out, outs)
+        st = _L.lib().cvc_batch_step(self._h, what, self._io, self._res, _stream(stream))
+        if st in (1, 6):
+            raise _L.CvcError(st, "cvc_batch_step")
+        res = []
+        for i in range(self.n):
+            r = self._res[i]
+            d = dict(enc_status=r.enc_status, dec_status=r.dec_status, out_len=r.out_len,
+                     frame_type=r.frame_type, dec_frame_type=r.dec_frame_type, dec_frame_index=r.dec_frame_index)
+            if r.frame_type >= 0 and r.enc_status == 0:
+                o = outs[i] if outs is not None and outs[i] is not None else self._out[i]
+                d["bytes"] = o[:r.out_len]
+            res.append(d)
+        if check and st != 0:
+            raise _L.CvcError(st, "cvc_batch_step")
+        return res
+
+    def set_shape(self, rle_rows, tok_blocks):
+        _L.check(_L.lib().cvc_batch_set_shape(self._h, rle_rows, tok_blocks), "cvc_batch_set_shape")
+
+    def set_graphs(self, on):
+        _L.check(_L.lib().cvc_batch_set_graphs(self._h, int(bool(on))), "cvc_batch_set_graphs")
+
+    def autotune(self, what, rgb=None, streams_in=None, rgb_out=None, reps=5, stream=None):
+        """Time candidate launch shapes on these inputs, keep the fastest; returns (rle_rows, tok_blocks)."""
+        self._fill(rgb, streams_in, rgb_out, None)
+        shape = (ctypes.c_int * 2)()
+        _L.check(_L.lib().cvc_batch_autotune(self._h, what, self._io, reps, shape, _stream(stream)),
+                 "cvc_batch_autotune")
+        return shape[0], shape[1]

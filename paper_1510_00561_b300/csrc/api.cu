@@ -1,17 +1,19 @@
 // api.cu -- extern "C" entry points of libcvc.so (declared in include/cvc.h).
+// The plain codec is a multi-stream core of one stream; a batch is a core of
+// many.  Transform plans drive the contourlet engine directly.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "k_codec.cuh"
+#include "codec_core.cuh"
 
 using namespace cvc;
 
 namespace cvc {
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace cvc
 
 namespace {
@@ -23,58 +25,6 @@ bool dalloc(std::vector<void*>& allocs, T** p, size_t n) {
     if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) return false;
     allocs.push_back(*p);
     return true;
-}
-
-bool valid_dirs(int levels, const int* dirs) {
-    if (levels < 1 || levels > CVC_MAX_LEVELS || !dirs) return false;
-    for (int j = 0; j < levels; j++)
-        if (dirs[j] < 0 || dirs[j] > CVC_MAX_DIRS_LOG2) return false;
-    return true;
-}
-
-inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
-
-int grid_for(long long n, int block = 256) {
-    long long g = (n + block - 1) / block;
-    return (int)std::max(1LL, std::min(g, 148LL * 64));
-}
-
-// geometry shared by cvc_create and the plan dump
-bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
-    const int M = modulus(prm->levels, prm->dirs_log2);
-    g->H = prm->height;
-    g->W = prm->width;
-    g->Hp = round_up(g->H, M);
-    g->Wp = round_up(g->W, M);
-    g->Hc = (g->H + 1) / 2;
-    g->Wc = (g->W + 1) / 2;
-    g->Hcp = round_up(g->Hc, M);
-    g->Wcp = round_up(g->Wc, M);
-    // the mirror padding reaches back at most one plane size
-    return !(g->Hp > 2 * g->H || g->Wp > 2 * g->W || g->Hcp > 2 * g->Hc || g->Wcp > 2 * g->Wc);
-}
-
-std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, const FrameGeom& f) {
-    std::vector<PlaneRef> planes(3);
-    for (int p = 0; p < 3; p++) {
-        memset(&planes[p], 0, sizeof(PlaneRef));
-        planes[p].H = p == 0 ? g.Hp : g.Hcp;
-        planes[p].W = p == 0 ? g.Wp : g.Wcp;
-        planes[p].L = L;
-        for (int j = 0; j < L; j++) planes[p].k[j] = dirs[j];
-        planes[p].in.b = B_IN;
-        planes[p].in.off = p == 0 ? 0 : (long long)g.Hp * g.Wp + (long long)(p - 1) * g.Hcp * g.Wcp;
-        planes[p].in.rs = planes[p].W;
-        planes[p].in.cs = 1;
-        planes[p].coef = f.poff[p];
-    }
-    return planes;
-}
-
-bool valid_params(const cvc_params* prm) {
-    return prm && prm->width >= 1 && prm->height >= 1 && prm->width <= 65535 && prm->height <= 65535 &&
-           valid_dirs(prm->levels, prm->dirs_log2) && prm->qph >= 1 && prm->qph <= 181 && prm->qpl >= 1 &&
-           prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1;
 }
 
 std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int batch, long long total) {
@@ -96,6 +46,37 @@ std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int
     return planes;
 }
 
+void fill_info(const Core& c, int s, cvc_codec_info_t* out) {
+    const SDesc& D = c.sd[s];
+    out->padded_height = D.cg.Hp;
+    out->padded_width = D.cg.Wp;
+    out->chroma_height = D.cg.Hc;
+    out->chroma_width = D.cg.Wc;
+    out->padded_chroma_height = D.cg.Hcp;
+    out->padded_chroma_width = D.cg.Wcp;
+    out->coeffs = D.ncoef;
+    out->components = D.ncomp;
+    out->max_stream_bytes = D.hdr_bytes + 2LL * D.max_tok;
+}
+
+cvc_status make_core(Core* c, const cvc_params* params, int n) {
+    cvc_status s = core_plan(c, params, n);
+    if (s != CVC_OK) return s;
+    return core_alloc(c);
+}
+
+// enqueue, wait, collect the stage times
+cvc_status run_step(Core* c, int mode, cudaStream_t st) {
+    cvc_status s = core_enqueue(c, mode, st);
+    if (s != CVC_OK) return s;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    core_collect(c);
+    return CVC_OK;
+}
+
 }  // namespace
 
 // ====================================================================== plan
@@ -110,69 +91,12 @@ struct cvc_ct_plan {
     }
 };
 
-// ===================================================================== codec
+// ==================================================================== codecs
 struct cvc_codec {
-    cvc_params prm;
-    ColourGeom cg;
-    PlaneLayout ly, lc;
-    FrameGeom fg;
-    QuantParams qp;
-    StreamHeader hdr;
-    long long ncoef = 0;
-    int ncomp = 0;
-    long long max_stream = 0;
-    long long nplane = 0;   // floats of the three padded planes
-    CtEngine eng;
-    float *d_planes = nullptr, *d_coef = nullptr, *d_work = nullptr, *d_rplanes = nullptr, *d_dcoef = nullptr;
-    int16_t *d_est[2] = {nullptr, nullptr}, *d_dst[2] = {nullptr, nullptr}, *d_res = nullptr;
-    int ecur = 0, dcur = 0;
-    int nrows = 0;
-    long long* d_row_off = nullptr;
-    int* d_row_w = nullptr;
-    uint8_t* d_row_low = nullptr;
-    int* d_comp_row0 = nullptr;
-    uint8_t* d_comp_low = nullptr;
-    long long* d_comp_elem = nullptr;
-    uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
-    uint32_t max_tok = 0;
-    uint32_t *d_contrib = nullptr, *d_pos = nullptr, *d_comp_tok = nullptr;
-    DecInfo* d_info = nullptr;
-    uint32_t *d_err = nullptr, *d_einfo = nullptr;
-    uint32_t* h_pin = nullptr;
-    long long enc_frame = 0, dec_next = -1;
-    bool have_enc = false, have_dec = false;
-    std::vector<void*> allocs;
-    // stage timing (CVC_NUM_STAGES stages)
-    bool timing = false;
-    cudaEvent_t ev[CVC_NUM_STAGES][2] = {};
-    bool ev_used[CVC_NUM_STAGES] = {};
-    double t_ms[CVC_NUM_STAGES] = {};
-    long long t_launches[CVC_NUM_STAGES] = {};
-    ~cvc_codec() {
-        for (void* p : allocs) cudaFree(p);
-        if (h_pin) cudaFreeHost(h_pin);
-        for (int s = 0; s < CVC_NUM_STAGES; s++)
-            for (int e = 0; e < 2; e++)
-                if (ev[s][e]) cudaEventDestroy(ev[s][e]);
-    }
-    void stage_begin(int s, cudaStream_t st) {
-        if (timing) cudaEventRecord(ev[s][0], st);
-    }
-    void stage_end(int s, cudaStream_t st, int launches) {
-        note_launches(launches);
-        if (!timing) return;
-        cudaEventRecord(ev[s][1], st);
-        ev_used[s] = true;
-        t_launches[s] += launches;
-    }
-    void stage_collect() {  // after a stream synchronisation
-        for (int s = 0; s < CVC_NUM_STAGES; s++) {
-            if (!ev_used[s]) continue;
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev[s][0], ev[s][1]) == cudaSuccess) t_ms[s] += ms;
-            ev_used[s] = false;
-        }
-    }
+    Core core;
+};
+struct cvc_batch {
+    Core core;
 };
 
 extern "C" {
@@ -194,12 +118,12 @@ const char* cvc_status_string(cvc_status s) {
 }
 
 int cvc_modulus(int levels, const int* dirs_log2) {
-    if (!valid_dirs(levels, dirs_log2)) return 0;
+    if (!dirs_valid(levels, dirs_log2)) return 0;
     return modulus(levels, dirs_log2);
 }
 
 cvc_status cvc_ct_layout(int h, int w, int levels, const int* dirs_log2, cvc_ct_layout_t* out) {
-    if (!out || !valid_dirs(levels, dirs_log2)) return CVC_ERR_INVALID_ARG;
+    if (!out || !dirs_valid(levels, dirs_log2)) return CVC_ERR_INVALID_ARG;
     PlaneLayout L;
     if (!make_layout(h, w, levels, dirs_log2, &L)) return CVC_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
@@ -225,7 +149,7 @@ cvc_status cvc_ct_layout(int h, int w, int levels, const int* dirs_log2, cvc_ct_
 cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, int batch, cvc_ct_plan** out) {
     if (!out) return CVC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!valid_dirs(levels, dirs_log2) || batch < 1) return CVC_ERR_INVALID_ARG;
+    if (!dirs_valid(levels, dirs_log2) || batch < 1) return CVC_ERR_INVALID_ARG;
     cvc_ct_plan* p = new (std::nothrow) cvc_ct_plan();
     if (!p) return CVC_ERR_NOMEM;
     if (!make_layout(h, w, levels, dirs_log2, &p->lay)) {
@@ -238,7 +162,9 @@ cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, in
     p->batch = batch;
     for (int j = 0; j < levels; j++) p->k[j] = dirs_log2[j];
     std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, p->lay.total);
-    if (!engine_build(&p->eng, planes) || !dalloc(p->allocs, &p->d_work, (size_t)p->eng.work_elems)) {
+    if (!engine_build(&p->eng, planes) || !dalloc(p->allocs, &p->d_work, (size_t)p->eng.work_elems) ||
+        lp_prepare() != cudaSuccess) {
+        cudaGetLastError();
         delete p;
         return CVC_ERR_NOMEM;
     }
@@ -285,95 +211,12 @@ cvc_status cvc_ct_inverse_adjoint(cvc_ct_plan* plan, const float* d_x_bar, float
 cvc_status cvc_create(const cvc_params* prm, cvc_codec** out) {
     if (!out) return CVC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!valid_params(prm)) return CVC_ERR_INVALID_ARG;
-    if (prm->chroma_420 != 1) return CVC_ERR_UNSUPPORTED;
     cvc_codec* c = new (std::nothrow) cvc_codec();
     if (!c) return CVC_ERR_NOMEM;
-    c->prm = *prm;
-    const int L = prm->levels;
-    ColourGeom& g = c->cg;
-    if (!codec_geometry(prm, &g) || !make_layout(g.Hp, g.Wp, L, prm->dirs_log2, &c->ly) ||
-        !make_layout(g.Hcp, g.Wcp, L, prm->dirs_log2, &c->lc)) {
+    cvc_status s = make_core(&c->core, prm, 1);
+    if (s != CVC_OK) {
         delete c;
-        return CVC_ERR_UNSUPPORTED;
-    }
-    c->ncoef = c->ly.total + 2 * c->lc.total;
-    c->ncomp = (int)(c->ly.sb.size() + 2 * c->lc.sb.size());
-    c->max_stream = 32 + 4LL * c->ncomp + 2LL * 2 * c->ncoef;
-    c->nplane = (long long)g.Hp * g.Wp + 2LL * g.Hcp * g.Wcp;
-    FrameGeom& f = c->fg;
-    f.poff[0] = 0;
-    f.poff[1] = c->ly.total;
-    f.poff[2] = c->ly.total + c->lc.total;
-    f.low_n[0] = (long long)c->ly.sb[0].h * c->ly.sb[0].w;
-    f.low_n[1] = f.low_n[2] = (long long)c->lc.sb[0].h * c->lc.sb[0].w;
-    f.low_w[0] = c->ly.sb[0].w;
-    f.low_w[1] = f.low_w[2] = c->lc.sb[0].w;
-    f.total = c->ncoef;
-    c->qp.qph = (float)prm->qph;
-    c->qp.qpl = (float)prm->qpl;
-    c->qp.threshold = prm->subband_threshold;
-    c->qp.low_scale = ldexpf(1.0f, -L);
-    c->qp.qpl_denorm = ldexpf((float)prm->qpl, L);
-    StreamHeader& h = c->hdr;
-    memset(&h, 0, sizeof(h));
-    h.levels = L;
-    h.height = g.H;
-    h.width = g.W;
-    for (int j = 0; j < 6; j++) h.dirs[j] = j < L ? prm->dirs_log2[j] : 0;
-    h.qph = prm->qph;
-    h.qpl = prm->qpl;
-    // transform engine over the three planes
-    std::vector<PlaneRef> planes = codec_planes(g, L, prm->dirs_log2, f);
-    // rows of every component in stream order
-    std::vector<long long> row_off;
-    std::vector<int> row_w, comp_row0;
-    std::vector<uint8_t> row_low, comp_low;
-    std::vector<long long> comp_elem;
-    for (int p = 0; p < 3; p++) {
-        const PlaneLayout& Ly = p == 0 ? c->ly : c->lc;
-        for (const SubbandG& s : Ly.sb) {
-            comp_row0.push_back((int)row_off.size());
-            comp_low.push_back(s.kind == 0);
-            comp_elem.push_back(f.poff[p] + s.off);
-            for (int r = 0; r < s.h; r++) {
-                row_off.push_back(f.poff[p] + s.off + (long long)r * s.w);
-                row_w.push_back(s.w);
-                row_low.push_back(s.kind == 0);
-            }
-        }
-    }
-    comp_row0.push_back((int)row_off.size());
-    comp_elem.push_back(c->ncoef);
-    c->nrows = (int)row_off.size();
-    c->max_tok = (uint32_t)(2 * c->ncoef + 64);
-    bool ok = engine_build(&c->eng, planes);
-    auto& A = c->allocs;
-    ok = ok && dalloc(A, &c->d_planes, (size_t)c->nplane) && dalloc(A, &c->d_rplanes, (size_t)c->nplane) &&
-         dalloc(A, &c->d_coef, (size_t)c->ncoef) && dalloc(A, &c->d_dcoef, (size_t)c->ncoef) &&
-         dalloc(A, &c->d_work, (size_t)c->eng.work_elems) && dalloc(A, &c->d_est[0], (size_t)c->ncoef) &&
-         dalloc(A, &c->d_est[1], (size_t)c->ncoef) && dalloc(A, &c->d_dst[0], (size_t)c->ncoef) &&
-         dalloc(A, &c->d_dst[1], (size_t)c->ncoef) && dalloc(A, &c->d_res, (size_t)c->ncoef) &&
-         dalloc(A, &c->d_row_off, row_off.size()) && dalloc(A, &c->d_row_w, row_w.size()) &&
-         dalloc(A, &c->d_row_low, row_low.size()) && dalloc(A, &c->d_comp_row0, comp_row0.size()) &&
-         dalloc(A, &c->d_comp_low, comp_low.size()) && dalloc(A, &c->d_comp_elem, comp_elem.size()) &&
-         dalloc(A, &c->d_rowcnt, (size_t)c->nrows) && dalloc(A, &c->d_rowoff, (size_t)c->nrows + 1) &&
-         dalloc(A, &c->d_scan_tmp, (size_t)c->max_tok / 2048 + 8) && dalloc(A, &c->d_contrib, (size_t)c->max_tok) &&
-         dalloc(A, &c->d_pos, (size_t)c->max_tok + 1) && dalloc(A, &c->d_comp_tok, (size_t)c->ncomp + 1) &&
-         dalloc(A, &c->d_info, 1) && dalloc(A, &c->d_err, 1) && dalloc(A, &c->d_einfo, 4);
-    ok = ok && cudaMallocHost((void**)&c->h_pin, 64) == cudaSuccess;
-    ok = ok && cudaMemcpy(c->d_row_off, row_off.data(), row_off.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_row_w, row_w.data(), row_w.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_row_low, row_low.data(), row_low.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_comp_row0, comp_row0.data(), comp_row0.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_comp_low, comp_low.data(), comp_low.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_comp_elem, comp_elem.data(), comp_elem.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemset(c->d_est[0], 0, (size_t)c->ncoef * 2) == cudaSuccess &&
-         cudaMemset(c->d_dst[0], 0, (size_t)c->ncoef * 2) == cudaSuccess;
-    if (!ok) {
-        delete c;
-        cudaGetLastError();
-        return CVC_ERR_NOMEM;
+        return s;
     }
     *out = c;
     return CVC_OK;
@@ -386,226 +229,235 @@ cvc_status cvc_destroy(cvc_codec* c) {
 
 cvc_status cvc_reset(cvc_codec* c) {
     if (!c) return CVC_ERR_INVALID_ARG;
-    c->enc_frame = 0;
-    c->dec_next = -1;
+    core_reset(&c->core, -1);
     return CVC_OK;
 }
 
 cvc_status cvc_codec_info(const cvc_codec* c, cvc_codec_info_t* out) {
     if (!c || !out) return CVC_ERR_INVALID_ARG;
-    out->padded_height = c->cg.Hp;
-    out->padded_width = c->cg.Wp;
-    out->chroma_height = c->cg.Hc;
-    out->chroma_width = c->cg.Wc;
-    out->padded_chroma_height = c->cg.Hcp;
-    out->padded_chroma_width = c->cg.Wcp;
-    out->coeffs = c->ncoef;
-    out->components = c->ncomp;
-    out->max_stream_bytes = c->max_stream;
+    fill_info(c->core, 0, out);
     return CVC_OK;
 }
 
 cvc_status cvc_encode_frame(cvc_codec* c, const uint8_t* d_rgb, size_t pitch_bytes, uint8_t* d_out, size_t out_cap,
                             size_t* out_len, int* frame_type, cvc_stream_t stream) {
-    if (!c || !d_rgb || !d_out || !out_len || pitch_bytes < (size_t)c->cg.W * 3 || ((uintptr_t)d_out & 3))
-        return CVC_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int type = (c->enc_frame % c->prm.key_interval) == 0 ? 0 : 1;
-    const long long hdr_bytes = 32 + 4LL * c->ncomp;
-    const bool hdr_fits = (long long)out_cap >= hdr_bytes;
-    const long long cap_tok = hdr_fits ? ((long long)out_cap - hdr_bytes) / 2 : 0;
-    float* Yp = c->d_planes;
-    float* Cop = Yp + (long long)c->cg.Hp * c->cg.Wp;
-    float* Cgp = Cop + (long long)c->cg.Hcp * c->cg.Wcp;
-    Bases B;
-    memset(&B, 0, sizeof(B));
-    B.p[B_IN] = c->d_planes;
-    B.p[B_COEF] = c->d_coef;
-    B.p[B_WORK] = c->d_work;
-    cudaMemsetAsync(c->d_err, 0, 4, st);
-    // S1-S3: colour, 4:2:0, padding
-    c->stage_begin(0, st);
-    k_colour_fwd<<<grid_for(c->nplane), 256, 0, st>>>(d_rgb, (long long)pitch_bytes, c->cg, Yp, Cop, Cgp);
-    c->stage_end(0, st, 1);
-    // S4: LP analysis, S5: DFB analysis
-    c->stage_begin(1, st);
-    if (engine_run_part(&c->eng, FWD, 0, B, st) != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_end(1, st, 0);
-    c->stage_begin(2, st);
-    if (engine_run_part(&c->eng, FWD, 1, B, st) != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_end(2, st, 0);
-    if (c->timing) {
-        c->t_launches[1] += engine_part_launches(&c->eng, FWD, 0);
-        c->t_launches[2] += engine_part_launches(&c->eng, FWD, 1);
-    }
-    // S6-S8: normalise, threshold, quantise, K/P differencing
-    int16_t* qnew = c->d_est[1 - c->ecur];
-    c->stage_begin(3, st);
-    k_quant<<<grid_for(c->ncoef), 256, 0, st>>>(c->d_coef, c->d_est[c->ecur], c->fg, c->qp, type == 0, qnew, c->d_res,
-                                                c->d_err);
-    c->stage_end(3, st, 1);
-    // S9: RLE rows -> bitstream
-    RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->nrows};
-    const int rows_per_block = 8;
-    const int rgrid = (c->nrows + rows_per_block - 1) / rows_per_block;
-    c->stage_begin(4, st);
-    k_rle_count<<<rgrid, 32 * rows_per_block, 0, st>>>(c->d_res, rt, type == 0, c->d_rowcnt);
-    exclusive_scan(c->d_rowcnt, (uint32_t)c->nrows, c->d_rowoff, c->d_scan_tmp, st);
-    int nl = 4;
-    if (hdr_fits) {
-        k_rle_write<<<rgrid, 32 * rows_per_block, 0, st>>>(c->d_res, rt, type == 0, c->d_rowoff, d_out + hdr_bytes,
-                                                           (uint32_t)std::min<long long>(cap_tok, 0xFFFFFFFFLL),
-                                                           c->d_err);
-        StreamHeader h = c->hdr;
-        h.type = type;
-        h.frame_index = (uint32_t)c->enc_frame;
-        k_stream_header<<<(c->ncomp + 255) / 256, 256, 0, st>>>(h, c->d_rowoff, c->d_comp_row0, c->ncomp, d_out,
-                                                                c->d_einfo);
-        nl += 2;
-    } else {
-        cudaMemcpyAsync(c->d_einfo, c->d_rowoff + c->nrows, 4, cudaMemcpyDeviceToDevice, st);
-    }
-    c->stage_end(4, st, nl);
-    cudaMemcpyAsync(c->h_pin, c->d_err, 4, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(c->h_pin + 1, c->d_einfo, 4, cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_collect();
-    const uint32_t err = c->h_pin[0];
-    const long long need = hdr_bytes + 2LL * c->h_pin[1];
-    *out_len = (size_t)need;
+    if (!c || !d_rgb || !d_out || !out_len) return CVC_ERR_INVALID_ARG;
+    StreamIo io{d_rgb, pitch_bytes, d_out, out_cap, nullptr, 0, nullptr, 0};
+    if (!core_fill_call(&c->core, 0, STEP_ENC, io)) return CVC_ERR_INVALID_ARG;
+    cvc_status s = run_step(&c->core, STEP_ENC, (cudaStream_t)stream);
+    if (s != CVC_OK) return s;
+    cvc_status es;
+    int type = 0;
+    core_commit(&c->core, 0, STEP_ENC, &es, nullptr, out_len, &type, nullptr, nullptr);
     if (frame_type) *frame_type = type;
-    if (err & EF_OVERFLOW) return CVC_ERR_OVERFLOW;
-    if (!hdr_fits || need > (long long)out_cap || (err & EF_CAPACITY)) return CVC_ERR_CAPACITY;
-    c->ecur = 1 - c->ecur;
-    c->enc_frame += 1;
-    c->have_enc = true;
-    return CVC_OK;
+    return es;
 }
 
 cvc_status cvc_decode_frame(cvc_codec* c, const uint8_t* d_in, size_t in_len, uint8_t* d_rgb, size_t pitch_bytes,
                             cvc_stream_t stream) {
-    if (!c || !d_in || !d_rgb || pitch_bytes < (size_t)c->cg.W * 3) return CVC_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    const long long hdr_bytes = 32 + 4LL * c->ncomp;
-    long long avail = ((long long)in_len - hdr_bytes) / 2;
-    uint32_t max_tok = (uint32_t)std::max(0LL, std::min<long long>(avail, c->max_tok));
-    cudaMemsetAsync(c->d_err, 0, 4, st);
-    // bitstream parse and run-length expansion
-    c->stage_begin(5, st);
-    k_dec_parse<<<1, 1024, 0, st>>>(d_in, (long long)in_len, c->hdr, c->ncomp, c->dec_next, max_tok, c->d_comp_tok,
-                                    c->d_info, c->d_err);
-    const uint8_t* tok = d_in + hdr_bytes;
-    k_dec_contrib<<<grid_for(max_tok), 256, 0, st>>>(tok, c->d_comp_tok, c->ncomp, c->d_comp_low, c->d_info,
-                                                     c->d_contrib, max_tok, c->d_err);
-    exclusive_scan(c->d_contrib, max_tok, c->d_pos, c->d_scan_tmp, st);
-    k_dec_check<<<(c->ncomp + 256) / 256, 256, 0, st>>>(c->d_comp_tok, c->d_pos, c->d_comp_elem, c->ncomp, c->d_info,
-                                                        c->d_err);
-    cudaMemsetAsync(c->d_res, 0, (size_t)c->ncoef * 2, st);
-    k_dec_scatter<<<grid_for(max_tok), 256, 0, st>>>(tok, c->d_comp_tok, c->ncomp, c->d_comp_low, c->d_info, c->d_pos,
-                                                     c->ncoef, c->d_res);
-    c->stage_end(5, st, 7);
-    // inverse K/P differencing and dequantisation
-    int16_t* qnew = c->d_dst[1 - c->dcur];
-    c->stage_begin(6, st);
-    k_unquant<<<grid_for(c->ncoef), 256, 0, st>>>(c->d_res, c->d_dst[c->dcur], c->fg, c->qp, c->d_info, qnew,
-                                                  c->d_dcoef);
-    const int lowcols = c->fg.low_w[0] + 2 * c->fg.low_w[1];
-    k_unquant_keylow<<<(lowcols + 255) / 256, 256, 0, st>>>(c->d_res, c->fg, c->qp, c->d_info, qnew, c->d_dcoef);
-    c->stage_end(6, st, 2);
-    // inverse transform: DFB synthesis, then LP synthesis
-    Bases B;
-    memset(&B, 0, sizeof(B));
-    B.p[B_COEF] = c->d_dcoef;
-    B.p[B_WORK] = c->d_work;
-    B.p[B_OUT] = c->d_rplanes;
-    c->stage_begin(7, st);
-    if (engine_run_part(&c->eng, INV, 1, B, st) != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_end(7, st, 0);
-    c->stage_begin(8, st);
-    if (engine_run_part(&c->eng, INV, 0, B, st) != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_end(8, st, 0);
-    if (c->timing) {
-        c->t_launches[7] += engine_part_launches(&c->eng, INV, 1);
-        c->t_launches[8] += engine_part_launches(&c->eng, INV, 0);
-    }
-    // rounding, chroma upsampling, inverse colour transform
-    float* Yp = c->d_rplanes;
-    float* Cop = Yp + (long long)c->cg.Hp * c->cg.Wp;
-    float* Cgp = Cop + (long long)c->cg.Hcp * c->cg.Wcp;
-    c->stage_begin(9, st);
-    k_colour_inv<<<grid_for((long long)c->cg.H * c->cg.W), 256, 0, st>>>(Yp, Cop, Cgp, c->cg, d_rgb,
-                                                                         (long long)pitch_bytes);
-    c->stage_end(9, st, 1);
-    cudaMemcpyAsync(c->h_pin, c->d_err, 4, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(c->h_pin + 2, c->d_info, sizeof(DecInfo), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
-    c->stage_collect();
-    const uint32_t err = c->h_pin[0];
-    DecInfo info;
-    memcpy(&info, c->h_pin + 2, sizeof(info));
-    if (err & EF_STATE) return CVC_ERR_STATE;
-    if (err & (EF_CORRUPT | EF_MISMATCH)) return CVC_ERR_CORRUPT;
-    c->dcur = 1 - c->dcur;
-    c->dec_next = (long long)info.frame_index + 1;
-    c->have_dec = true;
-    return CVC_OK;
+    if (!c || !d_in || !d_rgb) return CVC_ERR_INVALID_ARG;
+    StreamIo io{nullptr, 0, nullptr, 0, d_in, in_len, d_rgb, pitch_bytes};
+    if (!core_fill_call(&c->core, 0, STEP_DEC, io)) return CVC_ERR_INVALID_ARG;
+    cvc_status s = run_step(&c->core, STEP_DEC, (cudaStream_t)stream);
+    if (s != CVC_OK) return s;
+    cvc_status ds;
+    core_commit(&c->core, 0, STEP_DEC, nullptr, &ds, nullptr, nullptr, nullptr, nullptr);
+    return ds;
 }
 
 cvc_status cvc_codec_set_timing(cvc_codec* c, int on) {
     if (!c) return CVC_ERR_INVALID_ARG;
-    if (on) {
-        for (int s = 0; s < CVC_NUM_STAGES; s++) {
-            for (int e = 0; e < 2; e++)
-                if (!c->ev[s][e] && cudaEventCreate(&c->ev[s][e]) != cudaSuccess) return CVC_ERR_CUDA;
-            c->t_ms[s] = 0.0;
-            c->t_launches[s] = 0;
-            c->ev_used[s] = false;
-        }
-    }
-    c->timing = on != 0;
-    return CVC_OK;
+    return core_set_timing(&c->core, on != 0);
 }
 
 cvc_status cvc_codec_timing(const cvc_codec* c, double* ms, long long* launches) {
     if (!c) return CVC_ERR_INVALID_ARG;
     for (int s = 0; s < CVC_NUM_STAGES; s++) {
-        if (ms) ms[s] = c->t_ms[s];
-        if (launches) launches[s] = c->t_launches[s];
+        if (ms) ms[s] = c->core.t_ms[s];
+        if (launches) launches[s] = c->core.t_launches[s];
     }
     return CVC_OK;
 }
 
 unsigned long long cvc_kernel_launches(void) { return g_launches.load(); }
 
+cvc_status cvc_codec_inspect(const cvc_codec* c, int which, float* d_out, size_t cap_elems, cvc_stream_t stream) {
+    if (!c || !d_out || which < 0 || which > 2) return CVC_ERR_INVALID_ARG;
+    const Core& k = c->core;
+    const float* src = which == 0 ? k.d_planes : (which == 1 ? k.d_coef : k.d_rplanes);
+    size_t n = (size_t)(which == 1 ? k.ncoef : k.nplane);
+    if (cap_elems < n) return CVC_ERR_INVALID_ARG;
+    return cudaMemcpyAsync(d_out, src, n * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) == cudaSuccess
+               ? CVC_OK
+               : CVC_ERR_CUDA;
+}
+
+// --------------------------------------------------------------- batches
+cvc_status cvc_batch_create(const cvc_params* params, int n, cvc_batch** out) {
+    if (!out) return CVC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || n < 1) return CVC_ERR_INVALID_ARG;
+    cvc_batch* b = new (std::nothrow) cvc_batch();
+    if (!b) return CVC_ERR_NOMEM;
+    cvc_status s = make_core(&b->core, params, n);
+    if (s != CVC_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_destroy(cvc_batch* b) {
+    delete b;
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_device_bytes(const cvc_params* params, int n, size_t* bytes) {
+    if (!bytes || !params || n < 1) return CVC_ERR_INVALID_ARG;
+    Core c;
+    cvc_status s = core_plan(&c, params, n);
+    if (s != CVC_OK) return s;
+    *bytes = core_device_bytes(&c);
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_info(const cvc_batch* b, int i, cvc_codec_info_t* out) {
+    if (!b || !out || i < 0 || i >= b->core.n) return CVC_ERR_INVALID_ARG;
+    fill_info(b->core, i, out);
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_reset(cvc_batch* b, int i) {
+    if (!b || i >= b->core.n) return CVC_ERR_INVALID_ARG;
+    core_reset(&b->core, i < 0 ? -1 : i);
+    return CVC_OK;
+}
+
+static bool batch_fill(Core* c, int what, const cvc_batch_io* io) {
+    for (int s = 0; s < c->n; s++) {
+        const cvc_batch_io& x = io[s];
+        StreamIo sio{x.d_rgb, x.pitch_bytes, x.d_out, x.out_cap, x.d_in, x.in_len, x.d_rgb_out, x.pitch_out};
+        if (!core_fill_call(c, s, what, sio)) return false;
+    }
+    return true;
+}
+
+cvc_status cvc_batch_step(cvc_batch* b, int what, const cvc_batch_io* io, cvc_batch_result* res,
+                          cvc_stream_t stream) {
+    if (!b || !io || !res || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
+    Core* c = &b->core;
+    if (!batch_fill(c, what, io)) return CVC_ERR_INVALID_ARG;
+    cvc_status s = run_step(c, what, (cudaStream_t)stream);
+    if (s != CVC_OK) return s;
+    cvc_status first = CVC_OK;
+    for (int i = 0; i < c->n; i++) {
+        cvc_batch_result& r = res[i];
+        unsigned didx = 0;
+        core_commit(c, i, what, &r.enc_status, &r.dec_status, &r.out_len, &r.frame_type, &r.dec_frame_type, &didx);
+        r.dec_frame_index = didx;
+        if (first == CVC_OK) first = r.enc_status != CVC_OK ? r.enc_status : r.dec_status;
+    }
+    return first;
+}
+
+cvc_status cvc_batch_set_shape(cvc_batch* b, int rle_rows, int tok_blocks) {
+    if (!b || rle_rows < 1 || rle_rows > 32 || tok_blocks < 1 || tok_blocks > 65535) return CVC_ERR_INVALID_ARG;
+    b->core.shape = LaunchShape{rle_rows, tok_blocks};
+    core_drop_graphs(&b->core);
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_set_graphs(cvc_batch* b, int on) {
+    if (!b) return CVC_ERR_INVALID_ARG;
+    b->core.use_graphs = on != 0;
+    return CVC_OK;
+}
+
+cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, int reps, int* shape,
+                              cvc_stream_t stream) {
+    if (!b || !io || reps < 1 || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
+    Core* c = &b->core;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    // time `reps` steps of one shape; the records are refilled from the
+    // uncommitted state every time, so every run codes the same frame
+    auto measure = [&](LaunchShape sh, float* ms) -> cvc_status {
+        c->shape = sh;
+        core_drop_graphs(c);
+        if (!batch_fill(c, what, io)) return CVC_ERR_INVALID_ARG;
+        cvc_status s = core_enqueue(c, what, st);   // warm-up (and graph capture)
+        if (s != CVC_OK) return s;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == CVC_OK; r++) s = core_enqueue(c, what, st);
+        cudaEventRecord(e1, st);
+        if (s != CVC_OK) return s;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            return CVC_ERR_CUDA;
+        }
+        return CVC_OK;
+    };
+    const int tok_cand[] = {148 * 2, 148 * 4, 148 * 8, 148 * 16, 148 * 32};
+    const int rle_cand[] = {2, 4, 8, 16};
+    LaunchShape best = c->shape;
+    float best_ms = 0.f;
+    cvc_status s = measure(best, &best_ms);
+    // one coordinate at a time: token grid, then RLE rows per block
+    for (int t : tok_cand) {
+        if (s != CVC_OK) break;
+        LaunchShape sh{best.rle_rows, t};
+        float ms = 0.f;
+        s = measure(sh, &ms);
+        if (s == CVC_OK && ms < best_ms) best = sh, best_ms = ms;
+    }
+    for (int r : rle_cand) {
+        if (s != CVC_OK) break;
+        LaunchShape sh{r, best.tok_blocks};
+        float ms = 0.f;
+        s = measure(sh, &ms);
+        if (s == CVC_OK && ms < best_ms) best = sh, best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape = best;
+    core_drop_graphs(c);
+    if (shape) {
+        shape[0] = best.rle_rows;
+        shape[1] = best.tok_blocks;
+    }
+    return s;
+}
+
 cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int levels, const int* dirs_log2, int batch,
                                  int mode, void* buf, size_t cap, size_t* used) {
     if (!used || mode < 0 || mode > 3) return CVC_ERR_INVALID_ARG;
-    std::vector<PlaneRef> planes;
     unsigned long long elems[4] = {0, 0, 0, 0};
+    Core core;   // host tables only: core_plan makes no device call
+    CtEngine plain;
+    const CtEngine* ep = nullptr;
     if (params) {
-        if (!valid_params(params)) return CVC_ERR_INVALID_ARG;
-        ColourGeom g;
-        PlaneLayout ly, lc;
-        if (!codec_geometry(params, &g) || !make_layout(g.Hp, g.Wp, params->levels, params->dirs_log2, &ly) ||
-            !make_layout(g.Hcp, g.Wcp, params->levels, params->dirs_log2, &lc))
-            return CVC_ERR_UNSUPPORTED;
-        FrameGeom f;
-        memset(&f, 0, sizeof(f));
-        f.poff[1] = ly.total;
-        f.poff[2] = ly.total + lc.total;
-        planes = codec_planes(g, params->levels, params->dirs_log2, f);
-        elems[0] = elems[3] = (unsigned long long)g.Hp * g.Wp + 2ULL * g.Hcp * g.Wcp;
-        elems[1] = (unsigned long long)(ly.total + 2 * lc.total);
+        cvc_status s = core_plan(&core, params, std::max(batch, 1));
+        if (s != CVC_OK) return s;
+        elems[0] = elems[3] = (unsigned long long)core.nplane;
+        elems[1] = (unsigned long long)core.ncoef;
+        ep = &core.eng;
     } else {
         PlaneLayout lay;
-        if (!valid_dirs(levels, dirs_log2) || batch < 1 || !make_layout(h, w, levels, dirs_log2, &lay))
+        if (!dirs_valid(levels, dirs_log2) || batch < 1 || !make_layout(h, w, levels, dirs_log2, &lay))
             return CVC_ERR_INVALID_ARG;
-        planes = plan_planes(h, w, levels, dirs_log2, batch, lay.total);
+        std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, lay.total);
+        if (!engine_build(&plain, planes, false)) return CVC_ERR_INVALID_ARG;
         elems[0] = elems[3] = (unsigned long long)batch * h * w;
         elems[1] = (unsigned long long)batch * lay.total;
+        ep = &plain;
     }
-    CtEngine e;
-    if (!engine_build(&e, planes, false)) return CVC_ERR_INVALID_ARG;
+    const CtEngine& e = *ep;
     elems[2] = (unsigned long long)e.work_elems;
     // launch order of the mode
     struct Item { int kind; const void* data; size_t n, sz; };
@@ -641,16 +493,6 @@ cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int lev
         pos += it.n * it.sz;
     }
     return CVC_OK;
-}
-
-cvc_status cvc_codec_inspect(const cvc_codec* c, int which, float* d_out, size_t cap_elems, cvc_stream_t stream) {
-    if (!c || !d_out || which < 0 || which > 2) return CVC_ERR_INVALID_ARG;
-    const float* src = which == 0 ? c->d_planes : (which == 1 ? c->d_coef : c->d_rplanes);
-    size_t n = (size_t)(which == 1 ? c->ncoef : c->nplane);
-    if (cap_elems < n) return CVC_ERR_INVALID_ARG;
-    return cudaMemcpyAsync(d_out, src, n * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) == cudaSuccess
-               ? CVC_OK
-               : CVC_ERR_CUDA;
 }
 
 }  // extern "C"

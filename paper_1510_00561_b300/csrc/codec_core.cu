@@ -1,0 +1,579 @@
+// codec_core.cu -- host side of the multi-stream codec core: per-stream
+// descriptors, block maps, row and component tables, one device arena, the
+// fixed launch sequence of a step and its CUDA-graph capture.
+#include <algorithm>
+#include <cstring>
+
+#include "codec_core.cuh"
+
+namespace cvc {
+
+namespace {
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+// carves one allocation into aligned sub-buffers
+struct Carve {
+    std::vector<std::pair<void**, size_t>> items;
+    size_t total = 0;
+    template <class T>
+    void add(T** p, size_t n) {
+        total = (total + 255) & ~size_t(255);
+        items.push_back({reinterpret_cast<void**>(p), total});
+        total += std::max<size_t>(n, 1) * sizeof(T);
+    }
+    void assign(char* base) {
+        for (auto& it : items) *it.first = base + it.second;
+    }
+};
+
+void carve_all(Core* c, Carve& k) {
+    const size_t n = (size_t)c->n;
+    k.add(&c->d_sd, n);
+    k.add(&c->d_sc, n);
+    k.add(&c->d_rs, n);
+    k.add(&c->d_pd, c->h_pd.size());
+    k.add(&c->d_blk_colour, c->h_blk_colour.size());
+    k.add(&c->d_blk_colour_inv, c->h_blk_colour_inv.size());
+    k.add(&c->d_blk_plane, c->h_blk_plane.size());
+    k.add(&c->d_row_off, c->h_row_off.size());
+    k.add(&c->d_row_w, c->h_row_w.size());
+    k.add(&c->d_row_stream, c->h_row_stream.size());
+    k.add(&c->d_row_low, c->h_row_low.size());
+    k.add(&c->d_comp_row0, c->h_comp_row0.size());
+    k.add(&c->d_comp_stream, c->h_comp_stream.size());
+    k.add(&c->d_comp_low, c->h_comp_low.size());
+    k.add(&c->d_comp_elem, c->h_comp_elem.size());
+    k.add(&c->d_planes, (size_t)c->nplane);
+    k.add(&c->d_rplanes, (size_t)c->nplane);
+    k.add(&c->d_coef, (size_t)c->ncoef);
+    k.add(&c->d_dcoef, (size_t)c->ncoef);
+    k.add(&c->d_work, (size_t)c->eng.work_elems);
+    for (int b = 0; b < 2; b++) {
+        k.add(&c->d_est_buf[b], (size_t)c->ncoef);
+        k.add(&c->d_dst_buf[b], (size_t)c->ncoef);
+    }
+    k.add(&c->d_res, (size_t)c->ncoef);
+    k.add(&c->d_est, 2);
+    k.add(&c->d_dst, 2);
+    k.add(&c->d_rowcnt, (size_t)c->nrows);
+    k.add(&c->d_rowoff, (size_t)c->nrows + 1);
+    k.add(&c->d_scan_tmp, (size_t)cdiv(c->nrows, 2048) + 8);
+    k.add(&c->d_comp_tok, (size_t)c->ncomp);
+    k.add(&c->d_tok_base, n + 1);
+    k.add(&c->d_contrib, (size_t)c->sum_max_tok);
+    k.add(&c->d_pos, (size_t)c->sum_max_tok + 1);
+    k.add(&c->d_scan_tmp2, 1024 + 8);
+}
+
+size_t engine_table_bytes(const CtEngine& e) {
+    size_t b = 0;
+    for (int m = 0; m < 4; m++) {
+        for (const LaunchLp& L : e.lp[m]) b += L.njobs * sizeof(LpJob) + (size_t)L.nblocks * sizeof(int) + 1024;
+        for (const LaunchDfb& L : e.dfb[m])
+            b += L.njobs * (L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob)) + (size_t)L.nblocks * sizeof(int) + 1024;
+    }
+    return b;
+}
+
+template <class T>
+bool put(T* d, const std::vector<T>& h) {
+    if (h.empty()) return true;
+    return cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+}  // namespace
+
+bool dirs_valid(int levels, const int* dirs) {
+    if (levels < 1 || levels > CVC_MAX_LEVELS || !dirs) return false;
+    for (int j = 0; j < levels; j++)
+        if (dirs[j] < 0 || dirs[j] > CVC_MAX_DIRS_LOG2) return false;
+    return true;
+}
+
+bool codec_params_valid(const cvc_params* prm) {
+    return prm && prm->width >= 1 && prm->height >= 1 && prm->width <= 65535 && prm->height <= 65535 &&
+           dirs_valid(prm->levels, prm->dirs_log2) && prm->qph >= 1 && prm->qph <= 181 && prm->qpl >= 1 &&
+           prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1;
+}
+
+bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
+    const int M = modulus(prm->levels, prm->dirs_log2);
+    g->H = prm->height;
+    g->W = prm->width;
+    g->Hp = round_up(g->H, M);
+    g->Wp = round_up(g->W, M);
+    g->Hc = (g->H + 1) / 2;
+    g->Wc = (g->W + 1) / 2;
+    g->Hcp = round_up(g->Hc, M);
+    g->Wcp = round_up(g->Wc, M);
+    // the mirror padding reaches back at most one plane size
+    return !(g->Hp > 2 * g->H || g->Wp > 2 * g->W || g->Hcp > 2 * g->Hc || g->Wcp > 2 * g->Wc);
+}
+
+std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, long long plane_off,
+                                   const long long poff[3]) {
+    std::vector<PlaneRef> planes(3);
+    for (int p = 0; p < 3; p++) {
+        memset(&planes[p], 0, sizeof(PlaneRef));
+        planes[p].H = p == 0 ? g.Hp : g.Hcp;
+        planes[p].W = p == 0 ? g.Wp : g.Wcp;
+        planes[p].L = L;
+        for (int j = 0; j < L; j++) planes[p].k[j] = dirs[j];
+        planes[p].in.b = B_IN;
+        planes[p].in.off =
+            plane_off + (p == 0 ? 0 : (long long)g.Hp * g.Wp + (long long)(p - 1) * g.Hcp * g.Wcp);
+        planes[p].in.rs = planes[p].W;
+        planes[p].in.cs = 1;
+        planes[p].coef = poff[p];
+    }
+    return planes;
+}
+
+Core::~Core() {
+    for (int m = 0; m < 4; m++)
+        if (gexec[m]) cudaGraphExecDestroy(gexec[m]);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (arena) cudaFree(arena);
+    if (h_sc) cudaFreeHost(h_sc);
+    if (h_rs) cudaFreeHost(h_rs);
+    for (int s = 0; s < CVC_NUM_STAGES; s++)
+        for (int e = 0; e < 2; e++)
+            if (ev[s][e]) cudaEventDestroy(ev[s][e]);
+}
+
+cvc_status core_plan(Core* c, const cvc_params* params, int n) {
+    if (!params || n < 1) return CVC_ERR_INVALID_ARG;
+    for (int s = 0; s < n; s++)
+        if (!codec_params_valid(&params[s])) return CVC_ERR_INVALID_ARG;
+    for (int s = 0; s < n; s++)
+        if (params[s].chroma_420 != 1) return CVC_ERR_UNSUPPORTED;
+    c->n = n;
+    c->prm.assign(params, params + n);
+    c->sd.assign(n, SDesc{});
+    c->ly.assign(n, PlaneLayout{});
+    c->lc.assign(n, PlaneLayout{});
+    std::vector<PlaneRef> planes;
+    long long plane_off = 0, coef_off = 0, sum_tok = 0;
+    for (int s = 0; s < n; s++) {
+        const cvc_params& P = params[s];
+        SDesc& D = c->sd[s];
+        memset(&D, 0, sizeof(D));
+        const int L = P.levels;
+        ColourGeom& g = D.cg;
+        if (!codec_geometry(&P, &g) || !make_layout(g.Hp, g.Wp, L, P.dirs_log2, &c->ly[s]) ||
+            !make_layout(g.Hcp, g.Wcp, L, P.dirs_log2, &c->lc[s]))
+            return CVC_ERR_UNSUPPORTED;
+        const PlaneLayout& Ly = c->ly[s];
+        const PlaneLayout& Lc = c->lc[s];
+        D.qp.qph = (float)P.qph;
+        D.qp.qpl = (float)P.qpl;
+        D.qp.threshold = P.subband_threshold;
+        D.qp.low_scale = ldexpf(1.0f, -L);
+        D.qp.qpl_denorm = ldexpf((float)P.qpl, L);
+        D.hdr.levels = L;
+        D.hdr.height = g.H;
+        D.hdr.width = g.W;
+        for (int j = 0; j < 6; j++) D.hdr.dirs[j] = j < L ? P.dirs_log2[j] : 0;
+        D.hdr.qph = P.qph;
+        D.hdr.qpl = P.qpl;
+        D.plane_off = plane_off;
+        D.nplane = (long long)g.Hp * g.Wp + 2LL * g.Hcp * g.Wcp;
+        D.coef_off = coef_off;
+        D.ncoef = Ly.total + 2 * Lc.total;
+        D.row0 = (int)c->h_row_off.size();
+        D.comp0 = (int)c->h_comp_row0.size();
+        D.ncomp = (int)(Ly.sb.size() + 2 * Lc.sb.size());
+        D.hdr_bytes = 32 + 4LL * D.ncomp;
+        D.max_tok = 2 * D.ncoef + 64;
+        D.blk_colour = (int)c->h_blk_colour.size();
+        D.blk_colour_inv = (int)c->h_blk_colour_inv.size();
+        const long long nb_col = cdiv(D.nplane, ELEM_BLOCK), nb_inv = cdiv((long long)g.H * g.W, ELEM_BLOCK);
+        if ((long long)c->h_blk_colour.size() + nb_col > (1LL << 30) ||
+            (long long)c->h_blk_colour_inv.size() + nb_inv > (1LL << 30))
+            return CVC_ERR_UNSUPPORTED;
+        c->h_blk_colour.insert(c->h_blk_colour.end(), (size_t)nb_col, s);
+        c->h_blk_colour_inv.insert(c->h_blk_colour_inv.end(), (size_t)nb_inv, s);
+        const long long poff[3] = {coef_off, coef_off + Ly.total, coef_off + Ly.total + Lc.total};
+        for (int p = 0; p < 3; p++) {
+            const PlaneLayout& Lp = p == 0 ? Ly : Lc;
+            PDesc pd;
+            memset(&pd, 0, sizeof(pd));
+            pd.coef_off = poff[p];
+            pd.total = Lp.total;
+            pd.low_n = (long long)Lp.sb[0].h * Lp.sb[0].w;
+            pd.low_w = Lp.sb[0].w;
+            pd.stream = s;
+            pd.first_block = (int)c->h_blk_plane.size();
+            const long long nb = cdiv(Lp.total, ELEM_BLOCK);
+            if ((long long)c->h_blk_plane.size() + nb > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
+            c->h_blk_plane.insert(c->h_blk_plane.end(), (size_t)nb, (int)c->h_pd.size());
+            c->h_pd.push_back(pd);
+            c->lowcols += pd.low_w;
+            // rows of every component, in stream order
+            for (const SubbandG& sb : Lp.sb) {
+                c->h_comp_row0.push_back((int)c->h_row_off.size());
+                c->h_comp_low.push_back(sb.kind == 0);
+                c->h_comp_stream.push_back(s);
+                c->h_comp_elem.push_back(poff[p] - coef_off + sb.off);
+                for (int r = 0; r < sb.h; r++) {
+                    c->h_row_off.push_back(poff[p] + sb.off + (long long)r * sb.w);
+                    c->h_row_w.push_back(sb.w);
+                    c->h_row_low.push_back(sb.kind == 0);
+                    c->h_row_stream.push_back(s);
+                }
+            }
+        }
+        D.nrows = (int)c->h_row_off.size() - D.row0;
+        std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, plane_off, poff);
+        planes.insert(planes.end(), sp.begin(), sp.end());
+        plane_off += D.nplane;
+        coef_off += D.ncoef;
+        sum_tok += D.max_tok;
+    }
+    c->h_comp_row0.push_back((int)c->h_row_off.size());   // sentinel: end of the last component
+    c->nplane = plane_off;
+    c->ncoef = coef_off;
+    c->sum_max_tok = sum_tok;
+    c->nrows = (int)c->h_row_off.size();
+    c->ncomp = (int)c->h_comp_low.size();
+    c->nplanes = (int)c->h_pd.size();
+    // token positions and element offsets are 32-bit on the device
+    if (sum_tok > 0xFFFFFF00LL || c->ncoef > 0x7FFFFFFFLL) return CVC_ERR_UNSUPPORTED;
+    if (!engine_build(&c->eng, planes, false)) return CVC_ERR_UNSUPPORTED;
+    return CVC_OK;
+}
+
+size_t core_device_bytes(const Core* c) {
+    // carve_all records where each member pointer will point; nothing is written through them here
+    Carve k;
+    carve_all(const_cast<Core*>(c), k);
+    return k.total + engine_table_bytes(c->eng);
+}
+
+cvc_status core_alloc(Core* c) {
+    // the same job tables again, now uploaded
+    const std::vector<PlaneRef> planes = c->eng.planes;
+    if (!engine_build(&c->eng, planes, true)) {
+        cudaGetLastError();
+        return CVC_ERR_NOMEM;
+    }
+    if (lp_prepare() != cudaSuccess) return CVC_ERR_CUDA;
+    Carve k;
+    carve_all(c, k);
+    c->arena_bytes = k.total;
+    if (cudaMalloc(&c->arena, k.total) != cudaSuccess) {
+        c->arena = nullptr;
+        cudaGetLastError();
+        return CVC_ERR_NOMEM;
+    }
+    k.assign(static_cast<char*>(c->arena));
+    if (cudaMallocHost((void**)&c->h_sc, sizeof(SCall) * c->n) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_rs, sizeof(SResult) * c->n) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_NOMEM;
+    }
+    memset(c->h_sc, 0, sizeof(SCall) * c->n);
+    memset(c->h_rs, 0, sizeof(SResult) * c->n);
+    int16_t* est[2] = {c->d_est_buf[0], c->d_est_buf[1]};
+    int16_t* dst[2] = {c->d_dst_buf[0], c->d_dst_buf[1]};
+    bool ok = put(c->d_sd, c->sd) && put(c->d_pd, c->h_pd) && put(c->d_blk_colour, c->h_blk_colour) &&
+              put(c->d_blk_colour_inv, c->h_blk_colour_inv) && put(c->d_blk_plane, c->h_blk_plane) &&
+              put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
+              put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
+              put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
+              put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
+              cudaMemcpy(c->d_est, est, sizeof(est), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->d_dst, dst, sizeof(dst), cudaMemcpyHostToDevice) == cudaSuccess;
+    // state buffers start at zero (no frame may read them before a K-frame)
+    for (int b = 0; b < 2 && ok; b++)
+        ok = cudaMemset(c->d_est_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess &&
+             cudaMemset(c->d_dst_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    c->enc_frame.assign(c->n, 0);
+    c->dec_next.assign(c->n, -1);
+    c->ecur.assign(c->n, 0);
+    c->dcur.assign(c->n, 0);
+    return CVC_OK;
+}
+
+void core_reset(Core* c, int s) {
+    for (int i = 0; i < c->n; i++)
+        if (s < 0 || s == i) {
+            c->enc_frame[i] = 0;
+            c->dec_next[i] = -1;
+        }
+}
+
+void core_drop_graphs(Core* c) {
+    for (int m = 0; m < 4; m++) {
+        if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
+        c->gexec[m] = nullptr;
+        c->gkernels[m] = 0;
+    }
+}
+
+namespace {
+
+struct StageClock {
+    Core* c;
+    cudaStream_t st;
+    bool on;
+    void begin(int s) {
+        if (on) cudaEventRecord(c->ev[s][0], st);
+    }
+    void end(int s, long long launches) {
+        if (!on) return;
+        cudaEventRecord(c->ev[s][1], st);
+        c->ev_used[s] = true;
+        c->t_launches[s] += launches;
+    }
+};
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+
+// the launch sequence of one step; *nl = kernels launched
+cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long long* nl) {
+    StageClock clk{c, st, timed};
+    const int n = c->n;
+    long long k = 0;
+    *nl = 0;
+    CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->d_rs, 0, sizeof(SResult) * n, st));
+    const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->nrows};
+    const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem, c->ncomp};
+    const int rpb = c->shape.rle_rows;
+    const int rgrid = (int)cdiv(c->nrows, rpb);
+    if (mode & STEP_ENC) {
+        Bases B;
+        memset(&B, 0, sizeof(B));
+        B.p[B_IN] = c->d_planes;
+        B.p[B_COEF] = c->d_coef;
+        B.p[B_WORK] = c->d_work;
+        // S1-S3: colour, 4:2:0, padding
+        clk.begin(0);
+        k_colour_fwd_b<<<(int)c->h_blk_colour.size(), ELEM_BLOCK, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour,
+                                                                           c->d_planes);
+        CK(cudaGetLastError());
+        clk.end(0, 1);
+        // S4, S5: LP analysis, DFB analysis
+        clk.begin(1);
+        CK(engine_run_part(&c->eng, FWD, 0, B, st));
+        clk.end(1, engine_part_launches(&c->eng, FWD, 0));
+        clk.begin(2);
+        CK(engine_run_part(&c->eng, FWD, 1, B, st));
+        clk.end(2, engine_part_launches(&c->eng, FWD, 1));
+        k += 1 + engine_part_launches(&c->eng, FWD, 0) + engine_part_launches(&c->eng, FWD, 1);
+        // S6-S8: normalise, threshold, quantise, K/P differencing
+        clk.begin(3);
+        k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_BLOCK, 0, st>>>(c->d_coef, c->d_est, c->d_pd, c->d_blk_plane,
+                                                                     c->d_sd, c->d_sc, c->d_res, c->d_rs);
+        CK(cudaGetLastError());
+        clk.end(3, 1);
+        // S9: RLE rows, row offsets, tokens, headers
+        clk.begin(4);
+        k_rle_count_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sc, c->d_rowcnt);
+        CK(cudaGetLastError());
+        CK(exclusive_scan(c->d_rowcnt, (uint32_t)c->nrows, c->d_rowoff, c->d_scan_tmp, st));
+        k_rle_write_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sd, c->d_sc, c->d_rowoff, c->d_rs);
+        k_stream_header_b<<<n, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rowoff, ct, c->d_rs);
+        CK(cudaGetLastError());
+        clk.end(4, 6);
+        k += 7;
+    }
+    if (mode & STEP_DEC) {
+        const int tg = c->shape.tok_blocks;
+        // parse, token -> element counts, positions, checks, scatter of non-zero codes
+        clk.begin(5);
+        k_dec_parse_b<<<n, 1024, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_comp_tok, c->d_rs);
+        k_dec_base_b<<<1, 32, 0, st>>>(c->d_sd, n, c->d_rs, c->d_tok_base);
+        k_dec_contrib_b<<<tg, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_tok_base, n, c->d_comp_tok, ct,
+                                            c->d_contrib, c->d_rs);
+        CK(cudaGetLastError());
+        CK(exclusive_scan_dev(c->d_contrib, c->d_tok_base + n, (uint32_t)c->sum_max_tok, c->d_pos, c->d_scan_tmp2,
+                              st));
+        k_dec_check_b<<<(int)cdiv(c->ncomp, 256), 256, 0, st>>>(c->d_sd, c->d_rs, c->d_tok_base, c->d_comp_tok,
+                                                                c->d_pos, ct, c->d_rs);
+        CK(cudaMemsetAsync(c->d_res, 0, (size_t)c->ncoef * 2, st));
+        k_dec_scatter_b<<<tg, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_tok_base, n, c->d_comp_tok, ct,
+                                            c->d_pos, c->d_res);
+        CK(cudaGetLastError());
+        clk.end(5, 8);
+        // inverse K/P differencing and dequantisation
+        clk.begin(6);
+        k_unquant_b<<<(int)c->h_blk_plane.size(), ELEM_BLOCK, 0, st>>>(c->d_res, c->d_dst, c->d_pd, c->d_blk_plane,
+                                                                       c->d_sd, c->d_sc, c->d_rs, c->d_dcoef);
+        k_unquant_keylow_b<<<(int)cdiv(c->lowcols, 256), 256, 0, st>>>(c->d_res, c->d_dst, c->d_pd, c->nplanes,
+                                                                       c->d_sd, c->d_sc, c->d_rs, c->d_dcoef);
+        CK(cudaGetLastError());
+        clk.end(6, 2);
+        // inverse transform: DFB synthesis, then LP synthesis
+        Bases B;
+        memset(&B, 0, sizeof(B));
+        B.p[B_COEF] = c->d_dcoef;
+        B.p[B_WORK] = c->d_work;
+        B.p[B_OUT] = c->d_rplanes;
+        clk.begin(7);
+        CK(engine_run_part(&c->eng, INV, 1, B, st));
+        clk.end(7, engine_part_launches(&c->eng, INV, 1));
+        clk.begin(8);
+        CK(engine_run_part(&c->eng, INV, 0, B, st));
+        clk.end(8, engine_part_launches(&c->eng, INV, 0));
+        // rounding, chroma upsampling, inverse colour transform
+        clk.begin(9);
+        k_colour_inv_b<<<(int)c->h_blk_colour_inv.size(), ELEM_BLOCK, 0, st>>>(
+            c->d_sd, c->d_sc, c->d_rs, c->d_blk_colour_inv, c->d_rplanes);
+        CK(cudaGetLastError());
+        clk.end(9, 1);
+        k += 8 + 2 + 1 + engine_part_launches(&c->eng, INV, 1) + engine_part_launches(&c->eng, INV, 0);
+    }
+    CK(cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(SResult) * n, cudaMemcpyDeviceToHost, st));
+    *nl = k;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cvc_status core_enqueue(Core* c, int mode, cudaStream_t st) {
+    if (mode < STEP_ENC || mode > STEP_ENCDEC) return CVC_ERR_INVALID_ARG;
+    long long nl = 0;
+    if (!c->use_graphs || c->timing) {
+        if (enqueue_direct(c, mode, st, c->timing, &nl) != cudaSuccess) {
+            cudaGetLastError();
+            return CVC_ERR_CUDA;
+        }
+        note_launches(nl);
+        return CVC_OK;
+    }
+    if (!c->gexec[mode]) {
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return CVC_ERR_CUDA;
+        }
+        cudaError_t e = enqueue_direct(c, mode, c->cap_stream, false, &nl);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[mode], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            c->gexec[mode] = nullptr;
+            cudaGetLastError();
+            return CVC_ERR_CUDA;
+        }
+        c->gkernels[mode] = nl;
+    }
+    if (cudaGraphLaunch(c->gexec[mode], st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    note_launches(c->gkernels[mode]);
+    return CVC_OK;
+}
+
+void core_collect(Core* c) {
+    for (int s = 0; s < CVC_NUM_STAGES; s++) {
+        if (!c->ev_used[s]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[s][0], c->ev[s][1]) == cudaSuccess) c->t_ms[s] += ms;
+        c->ev_used[s] = false;
+    }
+}
+
+cvc_status core_set_timing(Core* c, bool on) {
+    if (on) {
+        for (int s = 0; s < CVC_NUM_STAGES; s++) {
+            for (int e = 0; e < 2; e++)
+                if (!c->ev[s][e] && cudaEventCreate(&c->ev[s][e]) != cudaSuccess) return CVC_ERR_CUDA;
+            c->t_ms[s] = 0.0;
+            c->t_launches[s] = 0;
+            c->ev_used[s] = false;
+        }
+    }
+    c->timing = on;
+    return CVC_OK;
+}
+
+bool core_fill_call(Core* c, int s, int mode, const StreamIo& io) {
+    const SDesc& D = c->sd[s];
+    SCall& C = c->h_sc[s];
+    memset(&C, 0, sizeof(C));
+    const size_t row = (size_t)D.cg.W * 3;
+    if ((mode & STEP_ENC) && io.rgb) {
+        if (!io.out || io.pitch < row || ((uintptr_t)io.out & 3)) return false;
+        C.enc_on = 1;
+        C.rgb_in = io.rgb;
+        C.pitch_in = (long long)io.pitch;
+        C.out = io.out;
+        C.out_cap = (long long)std::min<size_t>(io.out_cap, (size_t)1 << 62);
+        C.enc_key = (c->enc_frame[s] % c->prm[s].key_interval) == 0;
+        C.enc_index = (uint32_t)c->enc_frame[s];
+    }
+    if ((mode & STEP_DEC) && io.rgb_out) {
+        if (io.pitch_out < row) return false;
+        C.dec_on = 1;
+        C.rgb_out = io.rgb_out;
+        C.pitch_out = (long long)io.pitch_out;
+        if (mode == STEP_ENCDEC && C.enc_on) {
+            C.in = C.out;   // the decoder reads this call's encoder output
+            C.in_len = -1;
+        } else {
+            if (!io.in) return false;
+            C.in = io.in;
+            C.in_len = (long long)std::min<size_t>(io.in_len, (size_t)1 << 62);
+        }
+        C.dec_expect = c->dec_next[s];
+    }
+    C.ecur = c->ecur[s];
+    C.dcur = c->dcur[s];
+    return true;
+}
+
+void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
+                 int* dec_type, unsigned* dec_index) {
+    (void)mode;
+    const SCall& C = c->h_sc[s];
+    const SResult& R = c->h_rs[s];
+    const SDesc& D = c->sd[s];
+    cvc_status es = CVC_OK, ds = CVC_OK;
+    size_t len = 0;
+    int ty = -1, dty = -1;
+    unsigned didx = 0;
+    if (C.enc_on) {
+        const long long need = D.hdr_bytes + 2LL * R.enc_tokens;
+        len = (size_t)need;
+        ty = C.enc_key ? 0 : 1;
+        if (R.enc_err & EF_OVERFLOW) es = CVC_ERR_OVERFLOW;
+        else if (need > C.out_cap || (R.enc_err & EF_CAPACITY)) es = CVC_ERR_CAPACITY;
+        if (es == CVC_OK) {
+            c->ecur[s] = 1 - c->ecur[s];
+            c->enc_frame[s] += 1;
+        }
+    }
+    if (C.dec_on) {
+        if (R.dec_err & EF_STATE) ds = CVC_ERR_STATE;
+        else if (R.dec_err & (EF_CORRUPT | EF_MISMATCH)) ds = CVC_ERR_CORRUPT;
+        if (ds == CVC_OK) {
+            dty = (int)R.dec_type;
+            didx = R.dec_index;
+            c->dcur[s] = 1 - c->dcur[s];
+            c->dec_next[s] = (long long)R.dec_index + 1;
+        }
+    }
+    if (enc) *enc = es;
+    if (dec) *dec = ds;
+    if (out_len) *out_len = len;
+    if (type) *type = ty;
+    if (dec_type) *dec_type = dty;
+    if (dec_index) *dec_index = didx;
+}
+
+}  // namespace cvc

@@ -1,0 +1,121 @@
+// codec_core.cuh -- the multi-stream codec core behind cvc_codec (one
+// stream) and cvc_batch (many streams of any sizes).
+//
+// Every launch of an encode or decode step covers all streams of the core:
+// the transform through one CtEngine over all their planes, the element-wise
+// and row-wise stages through block maps.  Per-call arguments live in SCall
+// records copied from pinned host memory at the start of the step, and the
+// per-stream results come back through one copy at its end, so a step is a
+// fixed launch sequence that is captured once in a CUDA graph and replayed
+// for every frame.
+//
+// Coder state stays consistent without host work between steps: a step
+// writes the NEXT state buffers (est[1-ecur], dst[1-dcur]) and the host flips
+// ecur / dcur only for streams whose step succeeded, so a failed or skipped
+// step leaves the stream exactly as it was.
+#pragma once
+#include <vector>
+
+#include "k_codec.cuh"
+
+namespace cvc {
+
+enum StepMode { STEP_ENC = 1, STEP_DEC = 2, STEP_ENCDEC = 3 };
+
+// launch shapes the autotuner may change (they change no result)
+struct LaunchShape {
+    int rle_rows;    // rows per block of the RLE kernels (one warp per row)
+    int tok_blocks;  // blocks of the grid-stride token kernels of the decoder
+};
+
+struct Core {
+    int n = 0;
+    std::vector<cvc_params> prm;
+    std::vector<SDesc> sd;
+    std::vector<PlaneLayout> ly, lc;
+    long long nplane = 0, ncoef = 0, sum_max_tok = 0;
+    int nrows = 0, ncomp = 0, nplanes = 0, lowcols = 0;
+    // host tables (kept for the size estimate and the upload)
+    std::vector<PDesc> h_pd;
+    std::vector<int> h_blk_colour, h_blk_colour_inv, h_blk_plane;
+    std::vector<long long> h_row_off, h_comp_elem;
+    std::vector<int> h_row_w, h_row_stream, h_comp_row0, h_comp_stream;
+    std::vector<uint8_t> h_row_low, h_comp_low;
+    CtEngine eng;
+    LaunchShape shape{8, 148 * 8};
+    // device memory: one arena for everything but the engine's job tables
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    SDesc* d_sd = nullptr;
+    SCall* d_sc = nullptr;
+    SResult* d_rs = nullptr;
+    PDesc* d_pd = nullptr;
+    int *d_blk_colour = nullptr, *d_blk_colour_inv = nullptr, *d_blk_plane = nullptr;
+    long long *d_row_off = nullptr, *d_comp_elem = nullptr;
+    int *d_row_w = nullptr, *d_row_stream = nullptr, *d_comp_row0 = nullptr, *d_comp_stream = nullptr;
+    uint8_t *d_row_low = nullptr, *d_comp_low = nullptr;
+    float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
+    int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
+    int16_t **d_est = nullptr, **d_dst = nullptr;
+    uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
+    uint32_t *d_comp_tok = nullptr, *d_tok_base = nullptr, *d_contrib = nullptr, *d_pos = nullptr,
+             *d_scan_tmp2 = nullptr;
+    // pinned per-call records
+    SCall* h_sc = nullptr;
+    SResult* h_rs = nullptr;
+    // per-stream coder state (host side)
+    std::vector<long long> enc_frame, dec_next;
+    std::vector<int> ecur, dcur;
+    // CUDA graphs of the step modes (index = StepMode)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long gkernels[4] = {0, 0, 0, 0};
+    // stage timing (direct launches only)
+    bool timing = false;
+    cudaEvent_t ev[CVC_NUM_STAGES][2] = {};
+    bool ev_used[CVC_NUM_STAGES] = {};
+    double t_ms[CVC_NUM_STAGES] = {};
+    long long t_launches[CVC_NUM_STAGES] = {};
+    ~Core();
+};
+
+bool dirs_valid(int levels, const int* dirs);
+bool codec_params_valid(const cvc_params* prm);
+bool codec_geometry(const cvc_params* prm, ColourGeom* g);
+std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, long long plane_off,
+                                   const long long poff[3]);
+
+// host tables and sizes, no device call; CVC_OK, INVALID_ARG or UNSUPPORTED
+cvc_status core_plan(Core* c, const cvc_params* params, int n);
+// device bytes core_alloc will allocate (after core_plan)
+size_t core_device_bytes(const Core* c);
+// allocate, upload, reset the state; CVC_OK or NOMEM / CUDA
+cvc_status core_alloc(Core* c);
+// reset the coder state of stream s (s < 0: all)
+void core_reset(Core* c, int s);
+// enqueue one step (the records in h_sc must be filled); no synchronisation
+cvc_status core_enqueue(Core* c, int mode, cudaStream_t st);
+// after the step completed: collect stage times
+void core_collect(Core* c);
+cvc_status core_set_timing(Core* c, bool on);
+// drop the captured graphs (after a change of launch shape)
+void core_drop_graphs(Core* c);
+
+// fill the call record of stream s for a step; returns false on bad arguments
+struct StreamIo {
+    const uint8_t* rgb;
+    size_t pitch;
+    uint8_t* out;
+    size_t out_cap;
+    const uint8_t* in;
+    size_t in_len;
+    uint8_t* rgb_out;
+    size_t pitch_out;
+};
+bool core_fill_call(Core* c, int s, int mode, const StreamIo& io);
+// statuses of stream s after the step completed; commits the state on success
+void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
+                 int* dec_type, unsigned* dec_index);
+
+}  // namespace cvc

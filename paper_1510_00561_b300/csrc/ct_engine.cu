@@ -338,12 +338,10 @@ cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cu
     if (part == 0) {
         for (const LaunchLp& L : e->lp[m]) {
             if ((err = launch_lp(L, m, bases, st)) != cudaSuccess) return err;
-            note_launches(L.nblocks > 0);
         }
     } else {
         for (const LaunchDfb& L : e->dfb[m]) {
             if ((err = launch_dfb(L, m, bases, st)) != cudaSuccess) return err;
-            note_launches(L.nblocks > 0);
         }
     }
     return err;
@@ -361,8 +359,9 @@ int engine_part_launches(const CtEngine* e, Mode m, int part) {
 cudaError_t engine_run(const CtEngine* e, Mode m, Bases bases, cudaStream_t st) {
     const bool analysis = (m == FWD || m == INV_ADJ);
     cudaError_t err = engine_run_part(e, m, analysis ? 0 : 1, bases, st);
-    if (err != cudaSuccess) return err;
-    return engine_run_part(e, m, analysis ? 1 : 0, bases, st);
+    if (err == cudaSuccess) err = engine_run_part(e, m, analysis ? 1 : 0, bases, st);
+    if (err == cudaSuccess) note_launches(engine_part_launches(e, m, 0) + engine_part_launches(e, m, 1));
+    return err;
 }
 
 }  // namespace cvc

@@ -137,16 +137,20 @@ struct CtEngine {
 // offsets are assigned by the engine; returns false on allocation failure.
 bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes, bool to_device = true);
 size_t workspace_elems(int H, int W, int L);
+// the whole transform of mode m (counted in the launch counter)
 cudaError_t engine_run(const CtEngine* e, Mode m, Bases bases, cudaStream_t st);
 // one part of a mode's launch sequence: part 0 = LP levels, part 1 = DFB passes
+// (not counted: the caller adds engine_part_launches)
 cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cudaStream_t st);
 int engine_part_launches(const CtEngine* e, Mode m, int part);
 
 // process-wide count of kernels launched by the library
-void note_launches(int n);
+void note_launches(long long n);
 
 // -------------------------------------------------------------- kernels
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st);
+// one-time kernel attributes of the LP kernels (call before any stream capture)
+cudaError_t lp_prepare();
 cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st);
 PassParams pass_params(Mode m);
 

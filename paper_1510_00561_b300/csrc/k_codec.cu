@@ -1,7 +1,13 @@
-// k_codec.cu -- the codec's element-wise and row-wise stages:
+// k_codec.cu -- the codec's element-wise and row-wise stages, each launch
+// covering every stream of a batch:
 //   colour conversion + 4:2:0 + padding (§3.1), quantisation with lowpass
 //   normalisation and thresholding (§3.4-§3.6), K/P differencing (§3.7),
-//   run-length coding of rows (§3.8), their inverses, and a device-wide scan.
+//   run-length coding of rows (§3.8), their inverses, and device-wide scans.
+// Blocks find their stream / plane through block maps built at creation, so
+// no grid depends on per-call sizes; per-call arguments (buffers, frame type,
+// state parity) come from device records refreshed by one copy per call.
+#include <algorithm>
+
 #include "k_codec.cuh"
 
 namespace cvc {
@@ -13,38 +19,45 @@ __device__ __forceinline__ int mirror_idx(int a, int n) { return a < n ? a : 2 *
 // Cg = G - t, Y = t + (Cg>>1).  Luma items write the padded Y plane, chroma
 // items the padded 2x2-averaged Co / Cg planes (rounded mean, odd edges
 // replicated); padding mirrors about the last row / column.
-__global__ void k_colour_fwd(const uint8_t* __restrict__ rgb, long long pitch, ColourGeom g, float* __restrict__ Y,
-                             float* __restrict__ Co, float* __restrict__ Cg) {
+__global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                               const int* __restrict__ blk_stream, float* __restrict__ planes) {
+    const int s = blk_stream[blockIdx.x];
+    const SCall& C = sc[s];
+    if (!C.enc_on) return;
+    const SDesc& D = sd[s];
+    const ColourGeom g = D.cg;
+    const long long i = (long long)(blockIdx.x - D.blk_colour) * ELEM_BLOCK + threadIdx.x;
     const long long nY = (long long)g.Hp * g.Wp, nC = (long long)g.Hcp * g.Wcp;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nY + nC;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (i < nY) {
-            int y = (int)(i / g.Wp), x = (int)(i - (long long)y * g.Wp);
-            int sy = mirror_idx(y, g.H), sx = mirror_idx(x, g.W);
-            const uint8_t* p = rgb + sy * pitch + 3 * sx;
-            int R = p[0], G = p[1], Bv = p[2];
-            int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-            Y[i] = (float)(t + (cg >> 1));
-        } else {
-            long long k = i - nY;
-            int cy = (int)(k / g.Wcp), cx = (int)(k - (long long)cy * g.Wcp);
-            int sy = mirror_idx(cy, g.Hc), sx = mirror_idx(cx, g.Wc);
-            int r0 = 2 * sy, r1 = min(2 * sy + 1, g.H - 1), c0 = 2 * sx, c1 = min(2 * sx + 1, g.W - 1);
-            int sco = 0, scg = 0;
-            const int rr[2] = {r0, r1}, cc[2] = {c0, c1};
+    if (i >= nY + nC) return;
+    const uint8_t* rgb = C.rgb_in;
+    const long long pitch = C.pitch_in;
+    float* Y = planes + D.plane_off;
+    if (i < nY) {
+        int y = (int)(i / g.Wp), x = (int)(i - (long long)y * g.Wp);
+        int sy = mirror_idx(y, g.H), sx = mirror_idx(x, g.W);
+        const uint8_t* p = rgb + sy * pitch + 3 * sx;
+        int R = p[0], G = p[1], Bv = p[2];
+        int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
+        Y[i] = (float)(t + (cg >> 1));
+    } else {
+        long long k = i - nY;
+        int cy = (int)(k / g.Wcp), cx = (int)(k - (long long)cy * g.Wcp);
+        int sy = mirror_idx(cy, g.Hc), sx = mirror_idx(cx, g.Wc);
+        int r0 = 2 * sy, r1 = min(2 * sy + 1, g.H - 1), c0 = 2 * sx, c1 = min(2 * sx + 1, g.W - 1);
+        int sco = 0, scg = 0;
+        const int rr[2] = {r0, r1}, cc[2] = {c0, c1};
 #pragma unroll
-            for (int a = 0; a < 2; a++)
+        for (int a = 0; a < 2; a++)
 #pragma unroll
-                for (int b = 0; b < 2; b++) {
-                    const uint8_t* p = rgb + rr[a] * pitch + 3 * cc[b];
-                    int R = p[0], G = p[1], Bv = p[2];
-                    int co = R - Bv, t = Bv + (co >> 1);
-                    sco += co;
-                    scg += G - t;
-                }
-            Co[k] = (float)((sco + 2) >> 2);
-            Cg[k] = (float)((scg + 2) >> 2);
-        }
+            for (int b = 0; b < 2; b++) {
+                const uint8_t* p = rgb + rr[a] * pitch + 3 * cc[b];
+                int R = p[0], G = p[1], Bv = p[2];
+                int co = R - Bv, t = Bv + (co >> 1);
+                sco += co;
+                scg += G - t;
+            }
+        Y[nY + k] = (float)((sco + 2) >> 2);
+        Y[nY + nC + k] = (float)((scg + 2) >> 2);
     }
 }
 
@@ -56,42 +69,47 @@ __device__ __forceinline__ int round_clamp(float v, int lo, int hi) {
 
 // Decoder end: round (ties away from zero) and clamp the reconstructed
 // planes, bilinear (9,3,3,1)/16 chroma upsampling with centred siting and
-// clamped edges, inverse YCoCg-R, clamp to [0, 255].
-__global__ void k_colour_inv(const float* __restrict__ Y, const float* __restrict__ Co, const float* __restrict__ Cg,
-                             ColourGeom g, uint8_t* __restrict__ rgb, long long pitch) {
-    const long long n = (long long)g.H * g.W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
-        int yy = round_clamp(Y[(long long)y * g.Wp + x], 0, 255);
-        int i0 = min(y >> 1, g.Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, g.Hc - 1) : max((y >> 1) - 1, 0);
-        int j0 = min(x >> 1, g.Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, g.Wc - 1) : max((x >> 1) - 1, 0);
-        int c[2];
-        const float* P[2] = {Co, Cg};
+// clamped edges, inverse YCoCg-R, clamp to [0, 255].  A stream whose
+// bitstream was rejected leaves its output untouched.
+__global__ void k_colour_inv_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                               const SResult* __restrict__ rs, const int* __restrict__ blk_stream,
+                               const float* __restrict__ planes) {
+    const int s = blk_stream[blockIdx.x];
+    const SCall& C = sc[s];
+    if (!C.dec_on || rs[s].dec_err) return;
+    const SDesc& D = sd[s];
+    const ColourGeom g = D.cg;
+    const long long i = (long long)(blockIdx.x - D.blk_colour_inv) * ELEM_BLOCK + threadIdx.x;
+    if (i >= (long long)g.H * g.W) return;
+    const float* Y = planes + D.plane_off;
+    const float* Co = Y + (long long)g.Hp * g.Wp;
+    const float* Cg = Co + (long long)g.Hcp * g.Wcp;
+    int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
+    int yy = round_clamp(Y[(long long)y * g.Wp + x], 0, 255);
+    int i0 = min(y >> 1, g.Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, g.Hc - 1) : max((y >> 1) - 1, 0);
+    int j0 = min(x >> 1, g.Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, g.Wc - 1) : max((x >> 1) - 1, 0);
+    int c[2];
+    const float* P[2] = {Co, Cg};
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
-            const float* p = P[q];
-            int a = round_clamp(p[(long long)i0 * g.Wcp + j0], -255, 255);
-            int b = round_clamp(p[(long long)i1 * g.Wcp + j0], -255, 255);
-            int d = round_clamp(p[(long long)i0 * g.Wcp + j1], -255, 255);
-            int e = round_clamp(p[(long long)i1 * g.Wcp + j1], -255, 255);
-            c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
-        }
-        int t = yy - (c[1] >> 1);
-        int G = c[1] + t;
-        int Bv = t - (c[0] >> 1);
-        int R = Bv + c[0];
-        uint8_t* o = rgb + y * pitch + 3 * x;
-        o[0] = (uint8_t)min(max(R, 0), 255);
-        o[1] = (uint8_t)min(max(G, 0), 255);
-        o[2] = (uint8_t)min(max(Bv, 0), 255);
+    for (int q = 0; q < 2; q++) {
+        const float* p = P[q];
+        int a = round_clamp(p[(long long)i0 * g.Wcp + j0], -255, 255);
+        int b = round_clamp(p[(long long)i1 * g.Wcp + j0], -255, 255);
+        int d = round_clamp(p[(long long)i0 * g.Wcp + j1], -255, 255);
+        int e = round_clamp(p[(long long)i1 * g.Wcp + j1], -255, 255);
+        c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
     }
+    int t = yy - (c[1] >> 1);
+    int G = c[1] + t;
+    int Bv = t - (c[0] >> 1);
+    int R = Bv + c[0];
+    uint8_t* o = C.rgb_out + y * C.pitch_out + 3 * x;
+    o[0] = (uint8_t)min(max(R, 0), 255);
+    o[1] = (uint8_t)min(max(G, 0), 255);
+    o[2] = (uint8_t)min(max(Bv, 0), 255);
 }
 
 // ------------------------------------------------------ quantisation + K/P
-__device__ __forceinline__ int plane_of(const FrameGeom& f, long long e) {
-    return e < f.poff[1] ? 0 : (e < f.poff[2] ? 1 : 2);
-}
-
 __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, uint32_t* err) {
     float t;
     if (low) t = c * q.low_scale;                    // exact power-of-two normalisation
@@ -104,56 +122,73 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
     return (int)v;
 }
 
-// codes q (the next coder state) and residuals r of one frame
-__global__ void k_quant(const float* __restrict__ coef, const int16_t* __restrict__ prev, FrameGeom f, QuantParams qp,
-                        int is_key, int16_t* __restrict__ q_out, int16_t* __restrict__ r_out, uint32_t* err) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < f.total;
-         e += (long long)gridDim.x * blockDim.x) {
-        int p = plane_of(f, e);
-        long long le = e - f.poff[p];
-        bool low = le < f.low_n[p];
-        int q = quant(coef[e], low, qp, err);
-        int r;
-        if (!is_key) r = q - prev[e];
-        else if (low && le >= f.low_w[p]) r = q - quant(coef[e - f.low_w[p]], true, qp, err);
-        else r = q;
-        q_out[e] = (int16_t)q;
-        r_out[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
-    }
+// codes q (the next coder state) and residuals r of one frame per stream
+__global__ void k_quant_b(const float* __restrict__ coef, int16_t* const* __restrict__ est,
+                          const PDesc* __restrict__ pd, const int* __restrict__ blk_plane,
+                          const SDesc* __restrict__ sd, const SCall* __restrict__ sc, int16_t* __restrict__ res,
+                          SResult* out) {
+    const int p = blk_plane[blockIdx.x];
+    const PDesc P = pd[p];
+    const SCall& C = sc[P.stream];
+    if (!C.enc_on) return;
+    const long long le = (long long)(blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
+    if (le >= P.total) return;
+    const long long e = P.coef_off + le;
+    const QuantParams qp = sd[P.stream].qp;
+    uint32_t* err = &out[P.stream].enc_err;
+    const bool low = le < P.low_n;
+    const int q = quant(coef[e], low, qp, err);
+    int r;
+    if (!C.enc_key) r = q - est[C.ecur][e];
+    else if (low && le >= P.low_w) r = q - quant(coef[e - P.low_w], true, qp, err);
+    else r = q;
+    est[1 - C.ecur][e] = (int16_t)q;
+    res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
 }
 
 // decoder side: codes from residuals, then dequantised coefficients
-__global__ void k_unquant(const int16_t* __restrict__ res, const int16_t* __restrict__ prev, FrameGeom f,
-                          QuantParams qp, const DecInfo* __restrict__ info, int16_t* __restrict__ q_out,
-                          float* __restrict__ coef) {
-    const int is_key = info->type == 0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < f.total;
-         e += (long long)gridDim.x * blockDim.x) {
-        int p = plane_of(f, e);
-        long long le = e - f.poff[p];
-        bool low = le < f.low_n[p];
-        if (is_key && low) continue;                  // column prefix sums: k_unquant_keylow
-        int q = is_key ? res[e] : (int16_t)(uint16_t)((res[e] + prev[e]) & 0xFFFF);
-        q_out[e] = (int16_t)q;
-        coef[e] = (float)q * (low ? qp.qpl_denorm : qp.qph);
-    }
+__global__ void k_unquant_b(const int16_t* __restrict__ res, int16_t* const* __restrict__ dst,
+                            const PDesc* __restrict__ pd, const int* __restrict__ blk_plane,
+                            const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                            const SResult* __restrict__ rs, float* __restrict__ coef) {
+    const int p = blk_plane[blockIdx.x];
+    const PDesc P = pd[p];
+    const SCall& C = sc[P.stream];
+    if (!C.dec_on || rs[P.stream].dec_err) return;
+    const long long le = (long long)(blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
+    if (le >= P.total) return;
+    const bool key = rs[P.stream].dec_type == 0;
+    const bool low = le < P.low_n;
+    if (key && low) return;                     // column running sums: k_unquant_keylow_b
+    const long long e = P.coef_off + le;
+    const QuantParams qp = sd[P.stream].qp;
+    const int q = key ? res[e] : (int16_t)(uint16_t)((res[e] + dst[C.dcur][e]) & 0xFFFF);
+    dst[1 - C.dcur][e] = (int16_t)q;
+    coef[e] = (float)q * (low ? qp.qpl_denorm : qp.qph);
 }
 
 // K-frame lowpass: undo the column first difference (running sum down each column)
-__global__ void k_unquant_keylow(const int16_t* __restrict__ res, FrameGeom f, QuantParams qp,
-                                 const DecInfo* __restrict__ info, int16_t* __restrict__ q_out,
-                                 float* __restrict__ coef) {
-    if (info->type != 0) return;
+__global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* const* __restrict__ dst,
+                                   const PDesc* __restrict__ pd, int nplanes, const SDesc* __restrict__ sd,
+                                   const SCall* __restrict__ sc, const SResult* __restrict__ rs,
+                                   float* __restrict__ coef) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int p = 0; p < 3; p++) {
-        if (t >= f.low_w[p]) { t -= f.low_w[p]; continue; }
-        long long base = f.poff[p] + t;
-        int rows = (int)(f.low_n[p] / f.low_w[p]);
+    for (int p = 0; p < nplanes; p++) {
+        const PDesc P = pd[p];
+        if (t >= P.low_w) {
+            t -= P.low_w;
+            continue;
+        }
+        const SCall& C = sc[P.stream];
+        if (!C.dec_on || rs[P.stream].dec_err || rs[P.stream].dec_type != 0) return;
+        const QuantParams qp = sd[P.stream].qp;
+        const long long base = P.coef_off + t;
+        const int rows = (int)(P.low_n / P.low_w);
         int acc = 0;
         for (int r = 0; r < rows; r++) {
-            long long e = base + (long long)r * f.low_w[p];
+            const long long e = base + (long long)r * P.low_w;
             acc = (int16_t)(uint16_t)((acc + res[e]) & 0xFFFF);
-            q_out[e] = (int16_t)acc;
+            dst[1 - C.dcur][e] = (int16_t)acc;
             coef[e] = (float)acc * qp.qpl_denorm;
         }
         return;
@@ -161,16 +196,22 @@ __global__ void k_unquant_keylow(const int16_t* __restrict__ res, FrameGeom f, Q
 }
 
 // ------------------------------------------------------------------ RLE
-// Rows of every component, in stream order.  Token count of a row: one per
-// non-zero code plus two per maximal zero run; raw rows (K-frame lowpass)
-// carry one token per code.
-__global__ void k_rle_count(const int16_t* __restrict__ res, const RowTable rt, int is_key, uint32_t* __restrict__ cnt) {
+// Rows of every component of every stream, in stream order.  Token count of
+// a row: one per non-zero code plus two per maximal zero run; raw rows
+// (K-frame lowpass) carry one token per code.
+__global__ void k_rle_count_b(const int16_t* __restrict__ res, RowTable rt, const SCall* __restrict__ sc,
+                              uint32_t* __restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= rt.nrows) return;
+    const SCall& C = sc[rt.stream[row]];
+    if (!C.enc_on) {
+        if (lane == 0) cnt[row] = 0;
+        return;
+    }
     const long long off = rt.off[row];
     const int w = rt.w[row];
-    if (is_key && rt.low[row]) {
+    if (C.enc_key && rt.low[row]) {
         if (lane == 0) cnt[row] = (uint32_t)w;
         return;
     }
@@ -182,30 +223,37 @@ __global__ void k_rle_count(const int16_t* __restrict__ res, const RowTable rt, 
         bool z = valid && res[off + x] == 0;
         unsigned zb = __ballot_sync(0xffffffffu, z);
         unsigned vb = __ballot_sync(0xffffffffu, valid);
-        unsigned prevz = (zb << 1) | (prev_zero ? 1u : 0u);
-        unsigned starts = zb & ~prevz;
+        unsigned starts = zb & ~((zb << 1) | (prev_zero ? 1u : 0u));
         n += __popc(vb & ~zb) + 2 * __popc(starts);
         prev_zero = (zb >> 31) & 1u;
     }
     if (lane == 0) cnt[row] = n;
 }
 
-__device__ __forceinline__ void put_tok(uint8_t* tok_base, uint32_t pos, uint32_t cap_tok, int16_t v, uint32_t* err) {
-    if (pos < cap_tok) reinterpret_cast<int16_t*>(tok_base)[pos] = v;
+__device__ __forceinline__ void put_tok(int16_t* tok, uint32_t pos, uint32_t cap_tok, int16_t v, uint32_t* err) {
+    if (pos < cap_tok) tok[pos] = v;
     else atomicOr(err, EF_CAPACITY);
 }
 
-__global__ void k_rle_write(const int16_t* __restrict__ res, const RowTable rt, int is_key,
-                            const uint32_t* __restrict__ tokoff, uint8_t* __restrict__ tok_base, uint32_t cap_tok,
-                            uint32_t* err) {
+__global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, const SDesc* __restrict__ sd,
+                              const SCall* __restrict__ sc, const uint32_t* __restrict__ tokoff, SResult* out) {
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= rt.nrows) return;
+    const int s = rt.stream[row];
+    const SCall& C = sc[s];
+    if (!C.enc_on) return;
+    const SDesc& D = sd[s];
+    if (C.out_cap < D.hdr_bytes) return;            // reported by the header kernel
+    int16_t* tok = reinterpret_cast<int16_t*>(C.out + D.hdr_bytes);
+    const long long capl = (C.out_cap - D.hdr_bytes) / 2;
+    const uint32_t cap_tok = (uint32_t)(capl > 0xFFFFFFFFLL ? 0xFFFFFFFFLL : capl);
+    uint32_t* err = &out[s].enc_err;
     const long long off = rt.off[row];
     const int w = rt.w[row];
-    uint32_t pos = tokoff[row];
-    if (is_key && rt.low[row]) {
-        for (int x = lane; x < w; x += 32) put_tok(tok_base, pos + x, cap_tok, res[off + x], err);
+    uint32_t pos = tokoff[row] - tokoff[D.row0];
+    if (C.enc_key && rt.low[row]) {
+        for (int x = lane; x < w; x += 32) put_tok(tok, pos + x, cap_tok, res[off + x], err);
         return;
     }
     const unsigned lt = (1u << lane) - 1u;
@@ -223,8 +271,8 @@ __global__ void k_rle_write(const int16_t* __restrict__ res, const RowTable rt, 
         unsigned nz = vb & ~zb;
         bool start = (starts >> lane) & 1u;
         uint32_t my = pos + __popc(nz & lt) + 2 * __popc(starts & lt);
-        if (valid && !z) put_tok(tok_base, my, cap_tok, v, err);
-        if (start) put_tok(tok_base, my, cap_tok, 0, err);
+        if (valid && !z) put_tok(tok, my, cap_tok, v, err);
+        if (start) put_tok(tok, my, cap_tok, 0, err);
         // the run containing this lane started at the highest start lane <= lane, or before the chunk
         unsigned le = starts & (lt | (1u << lane));
         int sl = le ? 31 - __clz(le) : -1;
@@ -235,11 +283,9 @@ __global__ void k_rle_write(const int16_t* __restrict__ res, const RowTable rt, 
         bool next_zero;
         if (lane < 31) next_zero = (zb >> (lane + 1)) & 1u;
         else next_zero = (x + 1 < w) && res[off + x + 1] == 0;
-        if (z && !next_zero) put_tok(tok_base, spos + 1, cap_tok, (int16_t)(x - sx + 1), err);
-        // carry an open run into the next chunk
-        int src31 = 31;
-        uint32_t spos31 = __shfl_sync(0xffffffffu, spos, src31);
-        int sx31 = __shfl_sync(0xffffffffu, sx, src31);
+        if (z && !next_zero) put_tok(tok, spos + 1, cap_tok, (int16_t)(x - sx + 1), err);
+        uint32_t spos31 = __shfl_sync(0xffffffffu, spos, 31);
+        int sx31 = __shfl_sync(0xffffffffu, sx, 31);
         prev_zero = (zb >> 31) & 1u;
         if (prev_zero) {
             open_pos = spos31;
@@ -249,28 +295,39 @@ __global__ void k_rle_write(const int16_t* __restrict__ res, const RowTable rt, 
     }
 }
 
-__global__ void k_stream_header(StreamHeader h, const uint32_t* __restrict__ tokoff, const int* __restrict__ comp_row0,
-                                int ncomp, uint8_t* __restrict__ out, uint32_t* __restrict__ info) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) {
-        uint8_t* o = out;
+// one block per stream: header, component token counts, capacity check
+__global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                  const uint32_t* __restrict__ tokoff, CompTable ct, SResult* out) {
+    const int s = blockIdx.x;
+    const SCall& C = sc[s];
+    if (!C.enc_on) return;
+    const SDesc& D = sd[s];
+    const uint32_t tokens = tokoff[D.row0 + D.nrows] - tokoff[D.row0];
+    const long long need = D.hdr_bytes + 2LL * tokens;
+    if (threadIdx.x == 0) {
+        out[s].enc_tokens = tokens;
+        if (need > C.out_cap) atomicOr(&out[s].enc_err, EF_CAPACITY);
+    }
+    if (C.out_cap < D.hdr_bytes) return;
+    uint8_t* o = C.out;
+    if (threadIdx.x == 0) {
+        const StreamHeader& h = D.hdr;
         o[0] = 'C'; o[1] = 'V'; o[2] = 'C'; o[3] = '1';
         o[4] = 1; o[5] = 0;
-        o[6] = (uint8_t)h.type;
+        o[6] = (uint8_t)(C.enc_key ? 0 : 1);
         o[7] = (uint8_t)h.levels;
-        for (int i = 0; i < 4; i++) o[8 + i] = (uint8_t)(h.frame_index >> (8 * i));
+        for (int i = 0; i < 4; i++) o[8 + i] = (uint8_t)(C.enc_index >> (8 * i));
         o[12] = (uint8_t)h.height; o[13] = (uint8_t)(h.height >> 8);
         o[14] = (uint8_t)h.width; o[15] = (uint8_t)(h.width >> 8);
         for (int i = 0; i < 6; i++) o[16 + i] = (uint8_t)h.dirs[i];
         o[22] = (uint8_t)h.qph; o[23] = (uint8_t)(h.qph >> 8);
         o[24] = (uint8_t)h.qpl; o[25] = (uint8_t)(h.qpl >> 8);
         o[26] = 0; o[27] = 0;
-        for (int i = 0; i < 4; i++) o[28 + i] = (uint8_t)((unsigned)ncomp >> (8 * i));
-        info[0] = tokoff[comp_row0[ncomp]];
+        for (int i = 0; i < 4; i++) o[28 + i] = (uint8_t)((unsigned)D.ncomp >> (8 * i));
     }
-    if (t < ncomp) {
-        uint32_t c = tokoff[comp_row0[t + 1]] - tokoff[comp_row0[t]];
-        reinterpret_cast<uint32_t*>(out + 32)[t] = c;
+    for (int c = threadIdx.x; c < D.ncomp; c += blockDim.x) {
+        const int g = D.comp0 + c;
+        reinterpret_cast<uint32_t*>(o + 32)[c] = tokoff[ct.row0[g + 1]] - tokoff[ct.row0[g]];
     }
 }
 
@@ -280,42 +337,56 @@ __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
 }
 __device__ __forceinline__ int16_t rd16(const uint8_t* p) { return (int16_t)(uint16_t)(p[0] | (p[1] << 8)); }
 
-// header check, component token offsets (single block)
-__global__ void k_dec_parse(const uint8_t* __restrict__ in, long long in_len, StreamHeader expect, int ncomp,
-                            long long expect_next, uint32_t max_tok, uint32_t* __restrict__ comp_tok,
-                            DecInfo* __restrict__ info, uint32_t* err) {
+__device__ __forceinline__ long long dec_in_len(const SDesc& D, const SCall& C, const SResult* enc, int s) {
+    if (C.in_len >= 0) return C.in_len;
+    return enc[s].enc_err ? 0 : D.hdr_bytes + 2LL * enc[s].enc_tokens;   // this call's encoder output
+}
+
+// one block per stream: header check, component token offsets
+__global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                              const SResult* __restrict__ enc, uint32_t* __restrict__ comp_tok, SResult* out) {
+    const int s = blockIdx.x;
+    const SCall& C = sc[s];
     __shared__ uint32_t s_carry;
     __shared__ int s_bad;
     __shared__ uint32_t s_part[1024];
+    if (!C.dec_on) {
+        if (threadIdx.x == 0) out[s].dec_tokens = 0;
+        return;
+    }
+    const SDesc& D = sd[s];
+    const uint8_t* in = C.in;
+    const long long in_len = dec_in_len(D, C, enc, s);
+    const int ncomp = D.ncomp;
     if (threadIdx.x == 0) {
         int bad = 0;
-        info->type = 0;
-        info->total = 0;
-        if (in_len < 32 + 4LL * ncomp) bad = EF_CORRUPT;
+        out[s].dec_type = 0;
+        out[s].dec_tokens = 0;
+        if (in_len < D.hdr_bytes) bad = EF_CORRUPT;
         else {
+            const StreamHeader& e = D.hdr;
             if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] != 0) bad = EF_CORRUPT;
             int type = in[6];
             if (type > 1) bad = EF_CORRUPT;
-            if (in[7] != expect.levels || (in[12] | (in[13] << 8)) != expect.height ||
-                (in[14] | (in[15] << 8)) != expect.width || (in[22] | (in[23] << 8)) != expect.qph ||
-                (in[24] | (in[25] << 8)) != expect.qpl || rd32(in + 28) != (uint32_t)ncomp)
+            if (in[7] != e.levels || (in[12] | (in[13] << 8)) != e.height || (in[14] | (in[15] << 8)) != e.width ||
+                (in[22] | (in[23] << 8)) != e.qph || (in[24] | (in[25] << 8)) != e.qpl ||
+                rd32(in + 28) != (uint32_t)ncomp)
                 bad |= EF_MISMATCH;
             for (int i = 0; i < 6; i++)
-                if (in[16 + i] != expect.dirs[i]) bad |= EF_MISMATCH;
+                if (in[16 + i] != e.dirs[i]) bad |= EF_MISMATCH;
             uint32_t fidx = rd32(in + 8);
-            if (!bad && type == 1 && (expect_next < 0 || (long long)fidx != expect_next)) bad |= EF_STATE;
-            info->type = type;
-            info->frame_index = fidx;
+            if (!bad && type == 1 && (C.dec_expect < 0 || (long long)fidx != C.dec_expect)) bad |= EF_STATE;
+            out[s].dec_type = type;
+            out[s].dec_index = fidx;
         }
         s_bad = bad;
         s_carry = 0;
     }
     __syncthreads();
     if (s_bad) {
-        if (threadIdx.x == 0) atomicOr(err, (uint32_t)s_bad);
+        if (threadIdx.x == 0) out[s].dec_err |= (uint32_t)s_bad;
         return;
     }
-    // exclusive scan of the ncomp token counts
     for (int base = 0; base < ncomp; base += blockDim.x) {
         int i = base + threadIdx.x;
         uint32_t v = i < ncomp ? rd32(in + 32 + 4 * i) : 0;
@@ -327,85 +398,126 @@ __global__ void k_dec_parse(const uint8_t* __restrict__ in, long long in_len, St
             s_part[threadIdx.x] += a;
             __syncthreads();
         }
-        if (i < ncomp) comp_tok[i] = s_carry + s_part[threadIdx.x] - v;
+        if (i < ncomp) comp_tok[D.comp0 + i] = s_carry + s_part[threadIdx.x] - v;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_carry += s_part[threadIdx.x];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        uint32_t total = s_carry;
-        comp_tok[ncomp] = total;
-        if (32 + 4LL * ncomp + 2LL * total > in_len || total > max_tok) {
-            atomicOr(err, EF_CORRUPT);
-            total = 0;
-        }
-        info->total = total;
+        const uint32_t total = s_carry;
+        // every valid frame has at least one token per component
+        if (total == 0 || D.hdr_bytes + 2LL * total > in_len || total > D.max_tok) out[s].dec_err |= EF_CORRUPT;
+        else out[s].dec_tokens = total;
     }
 }
 
-__device__ __forceinline__ int find_comp(const uint32_t* comp_tok, int ncomp, uint32_t t) {
-    int lo = 0, hi = ncomp - 1;  // largest c with comp_tok[c] <= t
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (comp_tok[mid] <= t) lo = mid;
-        else hi = mid - 1;
+// exclusive scan of the streams' token counts: the base of each stream in
+// the compact token space of this call; tok_base[n] = all tokens
+__global__ void k_dec_base_b(const SDesc* __restrict__ sd, int nstreams, const SResult* __restrict__ rs,
+                             uint32_t* __restrict__ tok_base) {
+    (void)sd;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t acc = 0;
+    for (int s = 0; s < nstreams; s++) {
+        tok_base[s] = acc;
+        acc += rs[s].dec_tokens;
+    }
+    tok_base[nstreams] = acc;
+}
+
+__device__ __forceinline__ int find_last_le(const uint32_t* a, int lo, int hi, uint32_t t) {
+    // largest i in [lo, hi) with a[i] <= t (a non-decreasing, a[lo] <= t)
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= t) lo = mid;
+        else hi = mid;
     }
     return lo;
 }
 
+// per token of the compact token space: stream, local index, component and its end
+struct TokCtx {
+    int s, c;
+    uint32_t t, c0, c1;
+};
+__device__ __forceinline__ TokCtx tok_ctx(uint32_t g, const SDesc* sd, const SResult* rs, const uint32_t* tok_base,
+                                          int nstreams, const uint32_t* comp_tok) {
+    TokCtx k;
+    // the stream whose range [tok_base[s], tok_base[s+1]) holds g (empty ranges skipped)
+    int lo = 0, hi = nstreams;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (tok_base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    k.s = lo;
+    const SDesc& D = sd[k.s];
+    k.t = g - tok_base[k.s];
+    k.c = find_last_le(comp_tok, D.comp0, D.comp0 + D.ncomp, k.t);
+    k.c0 = comp_tok[k.c];
+    k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
+    return k;
+}
+
 // elements produced by each token: value (and raw K-lowpass) tokens 1,
-// zero markers 0, run counts n.
-__global__ void k_dec_contrib(const uint8_t* __restrict__ tok, const uint32_t* __restrict__ comp_tok, int ncomp,
-                              const uint8_t* __restrict__ comp_low, const DecInfo* __restrict__ info,
-                              uint32_t* __restrict__ contrib, uint32_t max_tok, uint32_t* err) {
-    const uint32_t total = info->total;
-    const int is_key = info->type == 0;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < max_tok; t += gridDim.x * blockDim.x) {
-        if (t >= total) {
-            contrib[t] = 0;
-            continue;
-        }
-        int c = find_comp(comp_tok, ncomp, t);
-        uint32_t c0 = comp_tok[c], c1 = comp_tok[c + 1];
-        int16_t v = rd16(tok + 2LL * t);
+// zero markers 0, run counts n
+__global__ void k_dec_contrib_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                const SResult* __restrict__ rs, const uint32_t* __restrict__ tok_base, int nstreams,
+                                const uint32_t* __restrict__ comp_tok, CompTable ct, uint32_t* __restrict__ contrib,
+                                SResult* out) {
+    const uint32_t total = tok_base[nstreams];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const TokCtx k = tok_ctx(g, sd, rs, tok_base, nstreams, comp_tok);
+        const uint8_t* tok = sc[k.s].in + sd[k.s].hdr_bytes;
+        const int16_t v = rd16(tok + 2LL * k.t);
         uint32_t n;
-        if (is_key && comp_low[c]) n = 1;
-        else if (t > c0 && rd16(tok + 2LL * (t - 1)) == 0) {
+        if (rs[k.s].dec_type == 0 && ct.low[k.c]) n = 1;
+        else if (k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0) {
             n = v > 0 ? (uint32_t)v : 0;
-            if (v <= 0) atomicOr(err, EF_CORRUPT);
+            if (v <= 0) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
         } else if (v != 0) n = 1;
         else {
             n = 0;
-            if (t + 1 >= c1) atomicOr(err, EF_CORRUPT);
+            if (k.t + 1 >= k.c1) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
         }
-        contrib[t] = n;
+        contrib[g] = n;
     }
 }
 
 // every component must expand to exactly its number of codes
-__global__ void k_dec_check(const uint32_t* __restrict__ comp_tok, const uint32_t* __restrict__ pos,
-                            const long long* __restrict__ comp_elem, int ncomp, const DecInfo* __restrict__ info,
-                            uint32_t* err) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > ncomp || info->total == 0) return;
-    if ((long long)pos[comp_tok[c]] != comp_elem[c]) atomicOr(err, EF_CORRUPT);
+__global__ void k_dec_check_b(const SDesc* __restrict__ sd, const SResult* __restrict__ rs,
+                              const uint32_t* __restrict__ tok_base, const uint32_t* __restrict__ comp_tok,
+                              const uint32_t* __restrict__ pos, CompTable ct, SResult* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ct.ncomp) return;
+    const int s = ct.stream[c];
+    if (rs[s].dec_tokens == 0) return;        // not decoding, or the header was rejected
+    const SDesc& D = sd[s];
+    const uint32_t b = tok_base[s];
+    const uint32_t p0 = pos[b];
+    if ((long long)(pos[b + comp_tok[c]] - p0) != ct.elem[c]) atomicOr(&out[s].dec_err, EF_CORRUPT);
+    if (c == D.comp0 + D.ncomp - 1 && (long long)(pos[b + rs[s].dec_tokens] - p0) != D.ncoef)
+        atomicOr(&out[s].dec_err, EF_CORRUPT);
 }
 
-__global__ void k_dec_scatter(const uint8_t* __restrict__ tok, const uint32_t* __restrict__ comp_tok, int ncomp,
-                              const uint8_t* __restrict__ comp_low, const DecInfo* __restrict__ info,
-                              const uint32_t* __restrict__ pos, long long ncoef, int16_t* __restrict__ res) {
-    const uint32_t total = info->total;
-    const int is_key = info->type == 0;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        int16_t v = rd16(tok + 2LL * t);
-        int c = find_comp(comp_tok, ncomp, t);
-        bool raw = is_key && comp_low[c];
-        bool count = !raw && t > comp_tok[c] && rd16(tok + 2LL * (t - 1)) == 0;
-        if ((raw || (v != 0 && !count)) && (long long)pos[t] < ncoef) res[pos[t]] = v;
+__global__ void k_dec_scatter_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                const SResult* __restrict__ rs, const uint32_t* __restrict__ tok_base, int nstreams,
+                                const uint32_t* __restrict__ comp_tok, CompTable ct, const uint32_t* __restrict__ pos,
+                                int16_t* __restrict__ res) {
+    const uint32_t total = tok_base[nstreams];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        const TokCtx k = tok_ctx(g, sd, rs, tok_base, nstreams, comp_tok);
+        const SDesc& D = sd[k.s];
+        const uint8_t* tok = sc[k.s].in + D.hdr_bytes;
+        const int16_t v = rd16(tok + 2LL * k.t);
+        const bool raw = rs[k.s].dec_type == 0 && ct.low[k.c];
+        const bool count = !raw && k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0;
+        const long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
+        if ((raw || (v != 0 && !count)) && p >= 0 && p < D.ncoef) res[D.coef_off + p] = v;
     }
 }
 
-// ------------------------------------------------------ exclusive scan
+// ------------------------------------------------------ exclusive scans
 constexpr int SCAN_CHUNK = 2048;
 
 __device__ __forceinline__ uint32_t block_reduce(uint32_t v, uint32_t* sh) {
@@ -419,10 +531,19 @@ __device__ __forceinline__ uint32_t block_reduce(uint32_t v, uint32_t* sh) {
     return v;
 }
 
-__global__ void k_scan_reduce(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ sums) {
+// block b owns [b*chunk, min((b+1)*chunk, n)); n from the host or from device memory
+__device__ __forceinline__ uint32_t scan_chunk(uint32_t n, const uint32_t* d_n) {
+    return d_n ? ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32 : SCAN_CHUNK;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, uint32_t n_host, const uint32_t* d_n,
+                              uint32_t* __restrict__ sums) {
     __shared__ uint32_t sh[32];
-    uint32_t base = blockIdx.x * SCAN_CHUNK, v = 0;
-    for (uint32_t i = base + threadIdx.x; i < min(base + SCAN_CHUNK, n); i += blockDim.x) v += in[i];
+    const uint32_t n = d_n ? *d_n : n_host;
+    const uint32_t chunk = scan_chunk(n, d_n);
+    const uint32_t base = blockIdx.x * chunk, end = min(base + chunk, n);
+    uint32_t v = 0;
+    for (uint32_t i = base + threadIdx.x; i < end; i += blockDim.x) v += in[i];
     v = block_reduce(v, sh);
     if (threadIdx.x == 0) sums[blockIdx.x] = v;
 }
@@ -452,41 +573,50 @@ __global__ void k_scan_sums(uint32_t* sums, int nb) {
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t n, const uint32_t* __restrict__ sums,
-                             uint32_t* __restrict__ out) {
+// each block scans its range in sub-chunks of SCAN_CHUNK (8 values per thread)
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t n_host, const uint32_t* d_n,
+                             const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
     __shared__ uint32_t wsum[32];
-    uint32_t base = blockIdx.x * SCAN_CHUNK;
-    // each thread owns SCAN_CHUNK / blockDim consecutive elements
+    __shared__ uint32_t s_carry;
+    const uint32_t n = d_n ? *d_n : n_host;
+    const uint32_t chunk = scan_chunk(n, d_n);
+    const uint32_t base = blockIdx.x * chunk, end = min(base + chunk, n);
     const int per = SCAN_CHUNK / blockDim.x;
-    uint32_t loc[16];
-    uint32_t tsum = 0;
-    for (int k = 0; k < per; k++) {
-        uint32_t i = base + threadIdx.x * per + k;
-        loc[k] = i < n ? in[i] : 0;
-        tsum += loc[k];
-    }
-    // block exclusive scan of thread sums
-    uint32_t x = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) >= (unsigned)o) x += y;
-    }
-    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    if (threadIdx.x == 0) s_carry = sums[blockIdx.x];
     __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t w = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (threadIdx.x >= (unsigned)o) w += y;
+    for (uint32_t sub = base; sub < end; sub += SCAN_CHUNK) {
+        uint32_t loc[16];
+        uint32_t tsum = 0;
+        for (int k = 0; k < per; k++) {
+            uint32_t i = sub + threadIdx.x * per + k;
+            loc[k] = i < end ? in[i] : 0;
+            tsum += loc[k];
         }
-        wsum[threadIdx.x] = w;
-    }
-    __syncthreads();
-    uint32_t excl = x - tsum + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0) + sums[blockIdx.x];
-    for (int k = 0; k < per; k++) {
-        uint32_t i = base + threadIdx.x * per + k;
-        if (i < n) out[i] = excl;
-        excl += loc[k];
+        uint32_t x = tsum;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t w = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (threadIdx.x >= (unsigned)o) w += y;
+            }
+            wsum[threadIdx.x] = w;
+        }
+        __syncthreads();
+        uint32_t excl = s_carry + x - tsum + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0);
+        for (int k = 0; k < per; k++) {
+            uint32_t i = sub + threadIdx.x * per + k;
+            if (i < end) out[i] = excl;
+            excl += loc[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
 }
@@ -494,10 +624,20 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t n, const 
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* tmp, cudaStream_t st) {
     int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
     if (nb == 0) nb = 1;
-    k_scan_reduce<<<nb, 256, 0, st>>>(in, n, tmp);
+    k_scan_reduce<<<nb, 256, 0, st>>>(in, n, nullptr, tmp);
     k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, 256, 0, st>>>(in, n, tmp, out);
-    return cudaGetLastError();   // three launches, counted by the caller
+    k_scan_apply<<<nb, 256, 0, st>>>(in, n, nullptr, tmp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_dev(const uint32_t* in, const uint32_t* d_n, uint32_t n_max, uint32_t* out, uint32_t* tmp,
+                               cudaStream_t st) {
+    int nb = (int)std::min<uint32_t>(1024u, (n_max + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    if (nb < 1) nb = 1;
+    k_scan_reduce<<<nb, 256, 0, st>>>(in, 0, d_n, tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
+    k_scan_apply<<<nb, 256, 0, st>>>(in, 0, d_n, tmp, out);
+    return cudaGetLastError();
 }
 
 }  // namespace cvc

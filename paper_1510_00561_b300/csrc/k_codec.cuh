@@ -1,4 +1,5 @@
-// k_codec.cuh -- parameter blocks and kernels of the codec stages.
+// k_codec.cuh -- parameter blocks and kernels of the codec stages, for a
+// batch of independent streams (one or many) handled by every launch.
 #pragma once
 #include "cvc_internal.cuh"
 
@@ -11,14 +12,6 @@ struct ColourGeom {
     int Hcp, Wcp;  // padded chroma plane
 };
 
-// coefficient frame: planes Y, Co, Cg back to back, lowpass first in each
-struct FrameGeom {
-    long long poff[3];   // plane offsets
-    long long low_n[3];  // lowpass elements per plane
-    int low_w[3];        // lowpass row length per plane
-    long long total;
-};
-
 struct QuantParams {
     float qph, qpl;
     float threshold;
@@ -26,54 +19,113 @@ struct QuantParams {
     float qpl_denorm;   // qpl * 2^L (exact)
 };
 
-// rows of every component in stream order
-struct RowTable {
-    const long long* off;   // element offset of the row in the frame
-    const int* w;           // row length
-    const uint8_t* low;     // row belongs to a lowpass component
-    int nrows;
-};
-
 struct StreamHeader {
-    int type, levels;
-    uint32_t frame_index;
+    int levels;
     int height, width;
     int dirs[6];
     int qph, qpl;
 };
 
-struct DecInfo {
-    int type;
-    uint32_t frame_index;
-    uint32_t total;   // tokens in the stream (0 if the header is bad)
-    uint32_t pad;
+// per stream, fixed at creation
+struct SDesc {
+    ColourGeom cg;
+    QuantParams qp;
+    StreamHeader hdr;
+    long long plane_off;   // floats: padded planes Y, Co, Cg of this stream
+    long long nplane;
+    long long coef_off;    // coefficients of this stream in the frame buffers
+    long long ncoef;
+    int row0, nrows;       // its component rows in the row table
+    int comp0, ncomp;      // its components in the component table
+    long long hdr_bytes;   // 32 + 4 * ncomp
+    long long max_tok;     // largest valid token count of one frame
+    int blk_colour, blk_colour_inv;   // first block of the stream in those launches
 };
 
-__global__ void k_colour_fwd(const uint8_t* rgb, long long pitch, ColourGeom g, float* Y, float* Co, float* Cg);
-__global__ void k_colour_inv(const float* Y, const float* Co, const float* Cg, ColourGeom g, uint8_t* rgb,
-                             long long pitch);
-__global__ void k_quant(const float* coef, const int16_t* prev, FrameGeom f, QuantParams qp, int is_key,
-                        int16_t* q_out, int16_t* r_out, uint32_t* err);
-__global__ void k_unquant(const int16_t* res, const int16_t* prev, FrameGeom f, QuantParams qp, const DecInfo* info,
-                          int16_t* q_out, float* coef);
-__global__ void k_unquant_keylow(const int16_t* res, FrameGeom f, QuantParams qp, const DecInfo* info,
-                                 int16_t* q_out, float* coef);
-__global__ void k_rle_count(const int16_t* res, const RowTable rt, int is_key, uint32_t* cnt);
-__global__ void k_rle_write(const int16_t* res, const RowTable rt, int is_key, const uint32_t* tokoff,
-                            uint8_t* tok_base, uint32_t cap_tok, uint32_t* err);
-__global__ void k_stream_header(StreamHeader h, const uint32_t* tokoff, const int* comp_row0, int ncomp,
-                                uint8_t* out, uint32_t* info);
-__global__ void k_dec_parse(const uint8_t* in, long long in_len, StreamHeader expect, int ncomp, long long expect_next,
-                            uint32_t max_tok, uint32_t* comp_tok, DecInfo* info, uint32_t* err);
-__global__ void k_dec_contrib(const uint8_t* tok, const uint32_t* comp_tok, int ncomp, const uint8_t* comp_low,
-                              const DecInfo* info, uint32_t* contrib, uint32_t max_tok, uint32_t* err);
-__global__ void k_dec_check(const uint32_t* comp_tok, const uint32_t* pos, const long long* comp_elem, int ncomp,
-                            const DecInfo* info, uint32_t* err);
-__global__ void k_dec_scatter(const uint8_t* tok, const uint32_t* comp_tok, int ncomp, const uint8_t* comp_low,
-                              const DecInfo* info, const uint32_t* pos, long long ncoef, int16_t* res);
+// per stream, refreshed every call
+struct SCall {
+    const uint8_t* rgb_in;
+    long long pitch_in;
+    uint8_t* out;
+    long long out_cap;
+    const uint8_t* in;
+    long long in_len;      // < 0: the encoder's output of this call (fused encode + decode)
+    uint8_t* rgb_out;
+    long long pitch_out;
+    int enc_on, enc_key, ecur, dec_on;
+    uint32_t enc_index;
+    int dcur;
+    long long dec_expect;  // frame index a P-frame must carry; -1: a K-frame is required
+};
+
+// per stream, written by the device every call
+struct SResult {
+    uint32_t enc_err, dec_err;
+    uint32_t enc_tokens;     // tokens of the encoded frame
+    uint32_t dec_type, dec_index, dec_tokens;
+};
+
+// per plane (three per stream)
+struct PDesc {
+    long long coef_off;   // global coefficient offset of the plane
+    long long total;
+    long long low_n;      // lowpass elements
+    int low_w;            // lowpass row length
+    int stream;
+    int first_block;      // first block of the plane in element-wise launches
+    int pad;
+};
+
+struct RowTable {
+    const long long* off;   // global coefficient index of the row's first element
+    const int* w;
+    const uint8_t* low;     // row belongs to a lowpass component
+    const int* stream;
+    int nrows;
+};
+
+struct CompTable {
+    const int* row0;          // first row of the component (global)
+    const uint8_t* low;
+    const int* stream;
+    const long long* elem;    // element offset of the component inside its stream
+    int ncomp;
+};
+
+constexpr int ELEM_BLOCK = 256;   // elements per block of the element-wise kernels
+
+__global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes);
+__global__ void k_colour_inv_b(const SDesc* sd, const SCall* sc, const SResult* rs, const int* blk_stream,
+                               const float* planes);
+__global__ void k_quant_b(const float* coef, int16_t* const* est, const PDesc* pd, const int* blk_plane,
+                          const SDesc* sd, const SCall* sc, int16_t* res, SResult* out);
+__global__ void k_unquant_b(const int16_t* res, int16_t* const* dst, const PDesc* pd, const int* blk_plane,
+                            const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
+__global__ void k_unquant_keylow_b(const int16_t* res, int16_t* const* dst, const PDesc* pd, int nplanes,
+                                   const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
+__global__ void k_rle_count_b(const int16_t* res, RowTable rt, const SCall* sc, uint32_t* cnt);
+__global__ void k_rle_write_b(const int16_t* res, RowTable rt, const SDesc* sd, const SCall* sc,
+                              const uint32_t* tokoff, SResult* out);
+__global__ void k_stream_header_b(const SDesc* sd, const SCall* sc, const uint32_t* tokoff, CompTable ct,
+                                  SResult* out);
+__global__ void k_dec_parse_b(const SDesc* sd, const SCall* sc, const SResult* enc, uint32_t* comp_tok,
+                              SResult* out);
+__global__ void k_dec_base_b(const SDesc* sd, int nstreams, const SResult* rs, uint32_t* tok_base);
+__global__ void k_dec_contrib_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tok_base,
+                                int nstreams, const uint32_t* comp_tok, CompTable ct, uint32_t* contrib,
+                                SResult* out);
+__global__ void k_dec_check_b(const SDesc* sd, const SResult* rs, const uint32_t* tok_base, const uint32_t* comp_tok,
+                              const uint32_t* pos, CompTable ct, SResult* out);
+__global__ void k_dec_scatter_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tok_base,
+                                int nstreams, const uint32_t* comp_tok, CompTable ct, const uint32_t* pos,
+                                int16_t* res);
 
 // exclusive scan of n values into out[0..n] (out[n] = total); tmp holds
 // ceil(n / 2048) + 1 values.
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* tmp, cudaStream_t st);
+// the same with n read from device memory (*d_n <= n_max); a fixed grid, so
+// the launch sequence does not depend on host-side sizes
+cudaError_t exclusive_scan_dev(const uint32_t* in, const uint32_t* d_n, uint32_t n_max, uint32_t* out, uint32_t* tmp,
+                               cudaStream_t st);
 
 }  // namespace cvc

@@ -20,6 +20,8 @@
 // per level makes coarse levels carry numbers up to 2^L * 255, and each
 // level's single-precision roundings would otherwise add ~ulp(255) to the
 // reconstruction; with compensated sums only the stored values round.
+#include <mutex>
+
 #include "cvc_internal.cuh"
 
 namespace cvc {
@@ -265,19 +267,27 @@ constexpr size_t synth_ff_smem() {
     return sizeof(float) * (size_t)(MN * MN + 2 * NA + 2 * VN * VN);
 }
 
+cudaError_t lp_prepare() {
+    // the float-float synthesis kernels need more than 48 KB of dynamic shared memory
+    static std::once_flag once;
+    static cudaError_t status = cudaSuccess;
+    std::call_once(once, [] {
+        status = cudaFuncSetAttribute(k_lp_synth_ff<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)synth_ff_smem<4, 3>());
+        if (status == cudaSuccess)
+            status = cudaFuncSetAttribute(k_lp_synth_ff<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)synth_ff_smem<3, 4>());
+    });
+    return status;
+}
+
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st) {
     if (L.nblocks == 0) return cudaSuccess;
     const bool synth = (m == INV || m == FWD_ADJ);
     const bool swap = (m == FWD_ADJ || m == INV_ADJ);
     dim3 grid(L.nblocks), block(256);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_lp_synth_ff<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)synth_ff_smem<4, 3>());
-        cudaFuncSetAttribute(k_lp_synth_ff<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)synth_ff_smem<3, 4>());
-        attr_set = true;
-    }
+    cudaError_t pe = lp_prepare();
+    if (pe != cudaSuccess) return pe;
     if (!synth && !swap) k_lp_level<4, 3, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
     else if (synth && !swap)
         k_lp_synth_ff<4, 3><<<grid, block, synth_ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);

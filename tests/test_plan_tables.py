@@ -67,3 +67,46 @@ def test_benchmark_codec_plan_is_in_bounds():
     for mode in (0, 1):
         elems, launches = E.tables(mode, params=prm)
         E.check_only(elems, launches, mode)
+
+
+MIXED = [(99, 77, 2, [2, 2]), (64, 48, 3, [3, 2, 2]), (40, 30, 1, [0]), (96, 64, 2, [1, 0])]
+
+
+def test_batch_plan_tables_of_mixed_streams():
+    """A batch of streams with different sizes and decompositions shares one
+    launch sequence; its tables must compute every stream's transform (and
+    its inverse) exactly as a codec of that stream alone would."""
+    prms = (L.Params * len(MIXED))(*[L.Params(w, h, Lv, L.ints(k), 8, 1, 0.0, 8, 1) for w, h, Lv, k in MIXED])
+    elems, launches = _mixed_tables(prms, 0)
+    rng = np.random.default_rng(5)
+    planes, refs = [], []
+    for w, h, Lv, k in MIXED:
+        oc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 8)
+        yp, cop, cgp = oc.planes(rng.integers(0, 256, (h, w, 3), dtype=np.uint8))
+        planes += [yp.ravel(), cop.ravel(), cgp.ravel()]
+        refs += [O.ct(0, p, p.shape[0], p.shape[1], Lv, k) for p in (yp, cop, cgp)]
+    bufs = _buffers(elems)
+    bufs[0][:] = np.concatenate(planes)
+    E.run(0, elems, launches, bufs)
+    assert np.abs(bufs[1] - np.concatenate(refs)).max() < 1e-7
+    elems, launches = _mixed_tables(prms, 1)
+    E.run(1, elems, launches, bufs)
+    assert np.abs(bufs[3] - bufs[0]).max() < 1e-8
+
+
+def _mixed_tables(prms, mode):
+    import ctypes
+    return E.tables(mode, params=ctypes.cast(prms, ctypes.POINTER(L.Params)).contents, batch=len(MIXED))
+
+
+def test_mixed_stream_batch_of_the_streaming_workload_is_in_bounds():
+    """64 streams, 16 each of QCIF, CIF, VGA and 720p: bounds and hazards of every job."""
+    cfg = [(176, 144, 3, [3, 2, 2]), (352, 288, 3, [3, 2, 2]), (640, 480, 4, [4, 3, 3, 2]),
+           (1280, 720, 5, [5, 4, 4, 3, 3])]
+    prms = (L.Params * 64)(*[L.Params(w, h, Lv, L.ints(k), 8, 1, 0.0, 10, 1)
+                             for w, h, Lv, k in cfg for _ in range(16)])
+    import ctypes
+    first = ctypes.cast(prms, ctypes.POINTER(L.Params)).contents
+    for mode in (0, 1):
+        elems, launches = E.tables(mode, params=first, batch=64)
+        E.check_only(elems, launches, mode)
