@@ -6,8 +6,11 @@ Workload: seeded synthetic 1920x1080 RGB video (12 textured moving objects on
 a smooth background, Gaussian noise sigma 3), YCoCg-R + 4:2:0, contourlet
 transform with 5 LP levels (CDF 9/7) and 32/16/16/8/8 directions, step 8
 (QPH 8, QPL 1), key frame every 10 frames, RLE bitstream.  One step encodes
-and decodes one frame of every stream this rank serves (plain path: one
-cvc_encode_frame + one cvc_decode_frame per frame, stream ordered).
+and decodes one frame of every stream this rank serves.  The headline value
+is the batched form (--batch concurrent 1080p streams coded by one
+cvc_batch_step, i.e. one CUDA-graph launch per step); the plain per-frame
+path (one cvc_encode_frame + one cvc_decode_frame per frame) is reported
+beside it under "plain".
 
 N > 1 (torchrun): every rank serves its own independent streams (the codec
 shards by stream; there is no exchange step), so scaling is weak.
@@ -112,11 +115,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def stage_bytes(codec, tokens):
-    """Algorithmic HBM bytes per frame of each stage ('Roofline')."""
+def stage_bytes(info, tokens):
+    """Algorithmic HBM bytes per frame of each stage: every input read once and
+    every output written once at its storage width (RGB bytes, float planes
+    and coefficients, int16 codes, state and tokens)."""
     N = W_ * H_
-    P = [(codec.Hp, codec.Wp), (codec.Hcp, codec.Wcp), (codec.Hcp, codec.Wcp)]
-    C = codec.ncoef
+    Hp, Wp = info.padded_height, info.padded_width
+    Hcp, Wcp = info.padded_chroma_height, info.padded_chroma_width
+    P = [(Hp, Wp), (Hcp, Wcp), (Hcp, Wcp)]
+    C = info.coeffs
     lp = 0
     dfb = 0
     for (h, w) in P:
@@ -124,7 +131,7 @@ def stage_bytes(codec, tokens):
             pj = (h >> (j - 1)) * (w >> (j - 1))
             lp += 4 * (pj + pj // 4 + pj)               # read level input, write lowpass + detail
             dfb += DIRS[j - 1] * 2 * 4 * (3 * pj // 2)  # per stage: two passes, each reads 2 and writes 1 coset
-    nplane = codec.nplane
+    nplane = Hp * Wp + 2 * Hcp * Wcp
     return {
         "colour_fwd": 3 * N + 4 * nplane,
         "lp_analysis": lp,
@@ -199,6 +206,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30, help="steps of the host-buffer end-to-end pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--batch", type=int, default=16, help="concurrent 1080p streams per GPU in the batched form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -214,7 +222,7 @@ def main():
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_1510_00561_b300 import Codec, kernel_launches
+    from paper_1510_00561_b300 import Batch, Codec, kernel_launches
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -231,63 +239,54 @@ def main():
     rgb = torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 126 MB L2
     stream = torch.cuda.current_stream()
+    F = len(d_frames)
 
-    def step(i):
-        s, _ = codec.encode(d_frames[i % len(d_frames)], out=out)
+    def max_over_ranks(ms):
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(step, steps, flush_between=True):
+        """CUDA-event time (ms, max over ranks) of `steps` steps, L2 flushed before each."""
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            if flush_between and not args.no_flush:
+                flush.zero_()
+            starts[i].record(stream)
+            step(i)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+
+    # ---------------------------------------------------------------- plain
+    plain_bytes = [0]
+
+    def plain_step(i):
+        s, _ = codec.encode(d_frames[i % F], out=out)
         codec.decode(s, out=rgb)
-        return s.numel()
+        plain_bytes[0] += s.numel()
 
     for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    codec.set_timing(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local) if rank == 0 else None
-    if clocks:
-        clocks.start()
-    nbytes = 0
-    launches0 = kernel_launches()
-    barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    for i in range(args.steps):
-        if not args.no_flush:
-            flush.zero_()
-        starts[i].record(stream)
-        nbytes += step(args.warmup + i)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    launches = kernel_launches() - launches0
-    clk = clocks.stop() if clocks else None
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    tot_ms = sum(step_ms)
-    stage = codec.timing()
-    codec.set_timing(False)
-    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_ms = float(t.item())
-    frames_total = args.steps * world
-    value = frames_total / (tot_ms / 1e3)
+        plain_step(i)
+    plain_ms = timed(lambda i: plain_step(args.warmup + i), args.steps)
+    plain_value = args.steps * world / (plain_ms / 1e3)
 
-    # ---- end to end through the C ABI with host buffers (pinned), per step:
+    # plain end to end through the C ABI with host buffers (pinned), per step:
     # H2D frame, encode, D2H bitstream, H2D bitstream, decode, D2H frame
-    h_frames = [torch.from_numpy(f).pin_memory() for f in frames[:min(len(frames), 8)]]
+    h_frames = [torch.from_numpy(f).pin_memory() for f in frames[:min(F, 8)]]
     h_stream = torch.empty(codec.max_stream, dtype=torch.uint8).pin_memory()
     h_rgb = torch.empty((H_, W_, 3), dtype=torch.uint8).pin_memory()
     d_in = torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev)
     d_sin = torch.empty(codec.max_stream, dtype=torch.uint8, device=dev)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    h2d = d2h = 0
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(e2e_steps):
+    io_bytes = [0, 0]
+
+    def plain_e2e_step(i):
         d_in.copy_(h_frames[i % len(h_frames)], non_blocking=True)
         s, _ = codec.encode(d_in, out=out)
         n = s.numel()
@@ -295,34 +294,94 @@ def main():
         d_sin[:n].copy_(h_stream[:n], non_blocking=True)
         codec.decode(d_sin[:n], out=rgb)
         h_rgb.copy_(rgb, non_blocking=True)
-        h2d += d_in.numel() + n
-        d2h += n + rgb.numel()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_steps * world / (float(t.item()) / 1e3)
+        io_bytes[0] += d_in.numel() + n
+        io_bytes[1] += n + rgb.numel()
+
+    plain_e2e_ms = timed(plain_e2e_step, e2e_steps, flush_between=False)
+    plain = {"value": plain_value, "ms_per_step": plain_ms / args.steps, "streams_per_gpu": 1,
+             "e2e": {"value": e2e_steps * world / (plain_e2e_ms / 1e3), "unit": UNIT,
+                     "h2d_bytes_per_step": io_bytes[0] // e2e_steps, "d2h_bytes_per_step": io_bytes[1] // e2e_steps}}
+    del codec
+
+    # -------------------------------------------------------------- batched
+    # B concurrent 1080p streams; stream j shows the rank's sequence shifted by 3j frames
+    B = args.batch
+    batch = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
+                        key_interval=KINT)] * B)
+    outs_rgb = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+
+    def frames_at(i):
+        return [d_frames[(i + 3 * j) % F] for j in range(B)]
+
+    shape = batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
+    batch_bytes = [0]
+
+    def batch_step(i):
+        res = batch.step(3, rgb=frames_at(i), rgb_out=outs_rgb)
+        batch_bytes[0] += sum(r["out_len"] for r in res)
+
+    for i in range(args.warmup):
+        batch_step(i)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    launches0 = kernel_launches()
+    t_wall = time.perf_counter()
+    tot_ms = timed(lambda i: batch_step(args.warmup + i), args.steps)
+    t_wall = time.perf_counter() - t_wall
+    launches = kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    value = args.steps * B * world / (tot_ms / 1e3)
+
+    # stage breakdown of the same steps as direct launches bracketed by CUDA events
+    batch.set_timing(True)
+    stage_steps = min(args.steps, 20)
+    timed(lambda i: batch_step(args.warmup + i), stage_steps)
+    stage = batch.timing()
+    batch.set_timing(False)
+
+    # batched end to end: per step H2D of B frames from pinned memory, one batch
+    # step, D2H of the B bitstreams and the B reconstructed frames
+    d_ins = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+    h_outs = [torch.empty(batch.info[j].max_stream_bytes, dtype=torch.uint8).pin_memory() for j in range(B)]
+    h_rgbs = [torch.empty((H_, W_, 3), dtype=torch.uint8).pin_memory() for _ in range(B)]
+    io_bytes = [0, 0]
+
+    def batch_e2e_step(i):
+        for j in range(B):
+            d_ins[j].copy_(h_frames[(i + j) % len(h_frames)], non_blocking=True)
+        res = batch.step(3, rgb=d_ins, rgb_out=outs_rgb)
+        for j in range(B):
+            n = res[j]["out_len"]
+            h_outs[j][:n].copy_(res[j]["bytes"], non_blocking=True)
+            h_rgbs[j].copy_(outs_rgb[j], non_blocking=True)
+            io_bytes[0] += d_ins[j].numel()
+            io_bytes[1] += n + outs_rgb[j].numel()
+
+    e2e_ms = timed(batch_e2e_step, e2e_steps, flush_between=False)
+    e2e_value = e2e_steps * B * world / (e2e_ms / 1e3)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant stage (CUDA events in the timed region)
+    # ---- roofline of the dominant stage (per-stage CUDA events, batched steps)
     pk = peaks()
-    tokens = (nbytes / args.steps - 32 - 4 * codec.ncomp) / 2
-    sb = stage_bytes(codec, tokens)
+    frames_staged = stage_steps * B
+    mean_bytes = batch_bytes[0] / ((args.warmup + args.steps + stage_steps) * B)
+    info = batch.info[0]
+    tokens = (mean_bytes - 32 - 4 * info.components) / 2
+    sb = stage_bytes(info, tokens)
     dom = max(stage, key=lambda k: stage[k][0])
     ms_dom, n_dom = stage[dom]
     per_launch_ms = ms_dom / max(1, n_dom)
-    bytes_per_launch = sb[dom] * args.steps / max(1, n_dom)
+    bytes_per_launch = sb[dom] * frames_staged / max(1, n_dom)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
             "peak_source": pk["source"], "launches": n_dom,
-            "stages_ms_per_frame": {k: v[0] / args.steps for k, v in stage.items()}}
+            "stages_ms_per_frame": {k: v[0] / frames_staged for k, v in stage.items()}}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -333,15 +392,17 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1080p CVC encode+decode (plain per-frame path), 1920x1080 RGB, "
-                                   "5-level CDF 9/7 LP + 32/16/16/8/8 ladder DFB, QPH 8 / QPL 1, K every 10",
-                       "streams_per_gpu": 1, "frames_cycled": len(frames),
+            "config": {"workload": "1080p CVC encode+decode, %d concurrent streams per GPU in one batch "
+                                   "(one CUDA-graph launch per step), 1920x1080 RGB, 5-level CDF 9/7 LP + "
+                                   "32/16/16/8/8 ladder DFB, QPH 8 / QPL 1, K every 10" % B,
+                       "streams_per_gpu": B, "frames_cycled": F, "launch_shape": list(shape),
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
-                       "mean_stream_bytes": nbytes / args.steps},
+                       "mean_stream_bytes": mean_bytes},
+            "plain": plain,
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
-                    "d2h_bytes_per_step": d2h // e2e_steps},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
+                    "d2h_bytes_per_step": io_bytes[1] // e2e_steps},
             "gpu_launches": int(launches), "clocks": clk, "wall_s": t_wall}
     print(json.dumps(line), flush=True)
     if world > 1:

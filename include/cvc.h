@@ -252,6 +252,11 @@ cvc_status cvc_batch_set_shape(cvc_batch* batch, int rle_rows, int tok_blocks);
 cvc_status cvc_batch_autotune(cvc_batch* batch, int what, const cvc_batch_io* io, int reps, int* shape,
                               cvc_stream_t stream);
 cvc_status cvc_batch_set_graphs(cvc_batch* batch, int on);
+/* Stage timing of a batch, as cvc_codec_set_timing / cvc_codec_timing (each
+ * stage's events bracket that stage's launches over all streams).  While
+ * timing is on, steps run as direct launches instead of graph replays.     */
+cvc_status cvc_batch_set_timing(cvc_batch* batch, int on);
+cvc_status cvc_batch_timing(const cvc_batch* batch, double* ms, long long* launches);
 
 /* --------------------------------------------------------------- tracing
  * Per-stage GPU time of a codec (the per-operation breakdown of §4.2),

@@ -114,6 +114,8 @@ def lib():
         L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
         L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
         L.cvc_batch_set_graphs.argtypes = [_P, _I]
+        L.cvc_batch_set_timing.argtypes = [_P, _I]
+        L.cvc_batch_timing.argtypes = [_P, _P, _P]
         L.cvc_debug_plan_tables.argtypes = [ctypes.POINTER(Params), _I, _I, _I, ctypes.POINTER(_I), _I, _I, _P,
                                             _SZ, ctypes.POINTER(_SZ)]
         _lib = L

@@ -259,6 +259,16 @@ class Batch:
     def set_graphs(self, on):
         _L.check(_L.lib().cvc_batch_set_graphs(self._h, int(bool(on))), "cvc_batch_set_graphs")
 
+    def set_timing(self, on=True):
+        _L.check(_L.lib().cvc_batch_set_timing(self._h, int(bool(on))), "cvc_batch_set_timing")
+
+    def timing(self):
+        """dict stage -> (milliseconds, kernel launches) accumulated since set_timing(True)."""
+        ms = (ctypes.c_double * _L.NUM_STAGES)()
+        n = (ctypes.c_longlong * _L.NUM_STAGES)()
+        _L.check(_L.lib().cvc_batch_timing(self._h, ms, n), "cvc_batch_timing")
+        return {name: (ms[i], n[i]) for i, name in enumerate(_L.STAGE_NAMES)}
+
     def autotune(self, what, rgb=None, streams_in=None, rgb_out=None, reps=5, stream=None):
         """Time candidate launch shapes on these inputs, keep the fastest; returns (rle_rows, tok_blocks)."""
         self._fill(rgb, streams_in, rgb_out, None)

@@ -374,6 +374,20 @@ cvc_status cvc_batch_set_graphs(cvc_batch* b, int on) {
     return CVC_OK;
 }
 
+cvc_status cvc_batch_set_timing(cvc_batch* b, int on) {
+    if (!b) return CVC_ERR_INVALID_ARG;
+    return core_set_timing(&b->core, on != 0);
+}
+
+cvc_status cvc_batch_timing(const cvc_batch* b, double* ms, long long* launches) {
+    if (!b) return CVC_ERR_INVALID_ARG;
+    for (int s = 0; s < CVC_NUM_STAGES; s++) {
+        if (ms) ms[s] = b->core.t_ms[s];
+        if (launches) launches[s] = b->core.t_launches[s];
+    }
+    return CVC_OK;
+}
+
 cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, int reps, int* shape,
                               cvc_stream_t stream) {
     if (!b || !io || reps < 1 || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
