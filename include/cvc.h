@@ -116,6 +116,27 @@ cvc_status cvc_ct_forward_adjoint(cvc_ct_plan* plan, const float* d_coeffs_bar, 
 cvc_status cvc_ct_inverse_adjoint(cvc_ct_plan* plan, const float* d_x_bar, float* d_coeffs_bar,
                                   cvc_stream_t stream);
 
+/* Soft thresholding of a plan's coefficients with one threshold per
+ * directional subband, for gradient-based tuning of the thresholds (a
+ * differentiable stand-in for the hard subband threshold of §3.5):
+ *   y = sign(c) * max(|c| - T[s], 0) in directional subband s (layout order,
+ *   s = 0 .. cvc_ct_plan_subbands - 1, shared by every batch entry); the
+ *   lowpass is copied unchanged.
+ * The backward pass takes dL/dy and returns
+ *   dL/dc = dL/dy * [|c| > T[s]] (lowpass: dL/dy) and
+ *   dL/dT[s] = -sum over subband s of every batch entry of dL/dy * sign(c) * [|c| > T[s]],
+ * the latter summed in a fixed order (repeatable bit for bit).
+ * d_thresholds and d_grad_thresholds hold cvc_ct_plan_subbands floats;
+ * coefficient buffers are `batch` vectors of layout.total floats.  d_out may
+ * equal d_coeffs and d_grad_coeffs may equal d_grad_out; no other overlap.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.                    */
+int cvc_ct_plan_subbands(const cvc_ct_plan* plan);
+cvc_status cvc_ct_soft_threshold(cvc_ct_plan* plan, const float* d_coeffs, const float* d_thresholds,
+                                 float* d_out, cvc_stream_t stream);
+cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* plan, const float* d_coeffs, const float* d_thresholds,
+                                          const float* d_grad_out, float* d_grad_coeffs,
+                                          float* d_grad_thresholds, cvc_stream_t stream);
+
 /* ---------------------------------------------------------------- codec
  * One video stream: encoder and decoder state resident on the device.
  *   width, height   frame size in pixels, 1..65535 (padded internally to the

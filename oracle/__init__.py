@@ -58,6 +58,8 @@ def lib():
         L.or_lp_analysis_adjoint.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, _D]
         L.or_lp_synthesis_adjoint.argtypes = [_D, ctypes.c_int, ctypes.c_int, _D, _D]
         L.or_dfb.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.or_soft_threshold.argtypes = [_D, ctypes.POINTER(_Layout), ctypes.c_int, _D, _D]
+        L.or_soft_threshold_vjp.argtypes = [_D, ctypes.POINTER(_Layout), ctypes.c_int, _D, _D, _D, _D]
         L.or_ct.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, _D]
         L.or_ycocgr_forward.argtypes = [_U8, ctypes.c_long, _I16, _I16, _I16]
         L.or_ycocgr_inverse.argtypes = [_I16, _I16, _I16, ctypes.c_long, _U8]
@@ -174,6 +176,55 @@ def ct(mode, x, H, W, L, k):
     if st:
         raise ValueError("ct: invalid arguments")
     return out if mode in (0, 3) else out.reshape(H, W)
+
+
+def _layout_struct(H, W, L, k):
+    lay = _Layout()
+    if lib().or_layout_make(H, W, L, _ints(k), ctypes.byref(lay)):
+        raise ValueError("layout: invalid arguments")
+    return lay
+
+
+def soft_threshold(c, H, W, L, k, T):
+    """Per-subband soft threshold of coefficient vectors c (batch, total) or (total,)."""
+    lay = _layout_struct(H, W, L, k)
+    c = _f64(c)
+    batch = c.size // lay.total
+    y = np.zeros(c.size)
+    lib().or_soft_threshold(c.ravel(), ctypes.byref(lay), batch, _f64(T).ravel(), y)
+    return y.reshape(c.shape)
+
+
+def soft_threshold_vjp(c, H, W, L, k, T, g):
+    """(dL/dc, dL/dT) of the soft threshold for upstream gradient g = dL/dy."""
+    lay = _layout_struct(H, W, L, k)
+    c = _f64(c)
+    batch = c.size // lay.total
+    gc = np.zeros(c.size)
+    gT = np.zeros(lay.nsub - 1)
+    lib().or_soft_threshold_vjp(c.ravel(), ctypes.byref(lay), batch, _f64(T).ravel(), _f64(g).ravel(), gc, gT)
+    return gc.reshape(c.shape), gT
+
+
+def threshold_loss(x, L, k, T, want_grad=True):
+    """Loss of thresholded reconstruction, mean over all pixels of
+    (S(soft_T(A x)) - x)^2 for planes x (batch, H, W), and its gradients
+    (dL/dT, dL/dx) by the chain rule through the adjoint transforms:
+    r = S y - x;  dL/dy = S^T (2 r / N);  (dL/dc, dL/dT) = vjp;  dL/dx = A^T dL/dc - 2 r / N."""
+    x = _f64(x)
+    B, H, W = x.shape
+    N = x.size
+    c = np.stack([ct(MODE_FORWARD, x[b], H, W, L, k) for b in range(B)])
+    y = soft_threshold(c, H, W, L, k, T)
+    r = np.stack([ct(MODE_INVERSE, y[b], H, W, L, k) for b in range(B)]) - x
+    loss = float(np.sum(r * r) / N)
+    if not want_grad:
+        return loss
+    gxh = 2.0 * r / N
+    gy = np.stack([ct(MODE_INVERSE_ADJOINT, gxh[b], H, W, L, k) for b in range(B)])
+    gc, gT = soft_threshold_vjp(c, H, W, L, k, T, gy)
+    gx = np.stack([ct(MODE_FORWARD_ADJOINT, gc[b], H, W, L, k) for b in range(B)]) - gxh
+    return loss, gT, gx
 
 
 def ycocgr_forward(rgb):

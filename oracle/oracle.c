@@ -588,6 +588,42 @@ int or_quantize(float c, int qp, float threshold, int is_lowpass, int levels, in
     return (int)v;
 }
 
+/* ---------------------------------------------------- soft thresholding */
+static double or_sign(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
+
+void or_soft_threshold(const double* c, const or_layout* lay, int batch, const double* T, double* y) {
+    for (int b = 0; b < batch; b++) {
+        const double* cb = c + (long)b * lay->total;
+        double* yb = y + (long)b * lay->total;
+        for (int s = 0; s < lay->nsub; s++) {
+            const or_subband* sb = &lay->sb[s];
+            for (long e = 0; e < (long)sb->h * sb->w; e++) {
+                double v = cb[sb->off + e];
+                if (s == 0) yb[sb->off + e] = v;
+                else yb[sb->off + e] = or_sign(v) * fmax(fabs(v) - T[s - 1], 0.0);
+            }
+        }
+    }
+}
+
+void or_soft_threshold_vjp(const double* c, const or_layout* lay, int batch, const double* T, const double* g,
+                           double* gc, double* gT) {
+    for (int s = 0; s + 1 < lay->nsub; s++) gT[s] = 0.0;
+    for (int b = 0; b < batch; b++) {
+        long base = (long)b * lay->total;
+        for (int s = 0; s < lay->nsub; s++) {
+            const or_subband* sb = &lay->sb[s];
+            for (long e = 0; e < (long)sb->h * sb->w; e++) {
+                long i = base + sb->off + e;
+                if (s == 0) { gc[i] = g[i]; continue; }
+                int on = fabs(c[i]) > T[s - 1];
+                gc[i] = on ? g[i] : 0.0;
+                if (on) gT[s - 1] -= g[i] * or_sign(c[i]);
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ RLE
  * §3.8: zero runs are coded along the horizontal direction; rows are coded
  * independently.  A non-zero value v is the token v; a maximal run of n

@@ -83,6 +83,18 @@ long or_rle_row(const int16_t* row, int w, int16_t* tokens);
 /* expand one component's tokens into n elements; returns OR_OK or OR_ECORRUPT */
 int or_rle_expand(const int16_t* tokens, long ntok, int16_t* out, long n);
 
+/* ------------------------------------------------- soft thresholding
+ * Differentiable stand-in for the hard subband threshold of §3.5, used to
+ * tune the thresholds by gradient descent: in directional subband s (layout
+ * order, s = 0 .. nsub-2) y = sign(c) max(|c| - T[s], 0); the lowpass is
+ * copied.  The vector-Jacobian product takes dL/dy and gives
+ * dL/dc = dL/dy [|c| > T[s]] (lowpass: dL/dy) and
+ * dL/dT[s] = -sum_{i in s} dL/dy_i sign(c_i) [|c_i| > T[s]], over `batch`
+ * coefficient vectors of the layout.                                        */
+void or_soft_threshold(const double* c, const or_layout* lay, int batch, const double* T, double* y);
+void or_soft_threshold_vjp(const double* c, const or_layout* lay, int batch, const double* T, const double* g,
+                           double* gc, double* gT);
+
 /* ---------------------------------------------------------------- codec */
 typedef struct or_codec or_codec;
 or_codec* or_codec_create(int width, int height, int levels, const int* dirs, int qph, int qpl,

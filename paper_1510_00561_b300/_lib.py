@@ -93,6 +93,9 @@ def lib():
         L.cvc_ct_plan_coeffs.restype = ctypes.c_longlong
         for name in ("cvc_ct_forward", "cvc_ct_inverse", "cvc_ct_forward_adjoint", "cvc_ct_inverse_adjoint"):
             getattr(L, name).argtypes = [_P, _P, _P, _P]
+        L.cvc_ct_plan_subbands.argtypes = [_P]
+        L.cvc_ct_soft_threshold.argtypes = [_P, _P, _P, _P, _P]
+        L.cvc_ct_soft_threshold_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         L.cvc_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_P)]
         L.cvc_destroy.argtypes = [_P]
         L.cvc_reset.argtypes = [_P]

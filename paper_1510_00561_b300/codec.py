@@ -82,6 +82,41 @@ class CtPlan:
     def inverse_adjoint(self, xbar, out=None):
         return self._run("cvc_ct_inverse_adjoint", xbar, (self.batch, self.h, self.w), (self.batch, self.total), out)
 
+    @property
+    def subbands(self):
+        """Number of directional subbands (one soft threshold each)."""
+        return _L.lib().cvc_ct_plan_subbands(self._h)
+
+    def _check_coeffs(self, t):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and tuple(t.shape) == (self.batch, self.total)):
+            raise ValueError("expected contiguous float32 CUDA coefficients of shape %s" % ((self.batch, self.total),))
+
+    def _check_thresholds(self, T):
+        if not (T.is_cuda and T.dtype == torch.float32 and T.is_contiguous() and T.numel() == self.subbands):
+            raise ValueError("expected %d contiguous float32 CUDA thresholds" % self.subbands)
+
+    def soft_threshold(self, c, T, out=None):
+        """sign(c) max(|c| - T[s], 0) per directional subband s; lowpass unchanged."""
+        self._check_coeffs(c)
+        self._check_thresholds(T)
+        if out is None:
+            out = torch.empty_like(c)
+        _L.check(_L.lib().cvc_ct_soft_threshold(self._h, _ptr(c), _ptr(T), _ptr(out), _stream()),
+                 "cvc_ct_soft_threshold")
+        return out
+
+    def soft_threshold_backward(self, c, T, grad_out):
+        """(dL/dc, dL/dT) of soft_threshold for the upstream gradient dL/dy."""
+        self._check_coeffs(c)
+        self._check_coeffs(grad_out)
+        self._check_thresholds(T)
+        gc = torch.empty_like(c)
+        gT = torch.empty_like(T)
+        _L.check(_L.lib().cvc_ct_soft_threshold_backward(self._h, _ptr(c), _ptr(T), _ptr(grad_out), _ptr(gc),
+                                                         _ptr(gT), _stream()), "cvc_ct_soft_threshold_backward")
+        return gc, gT
+
 
 class Codec:
     """One CVC video stream on the GPU (encoder and decoder state resident in HBM)."""

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "codec_core.cuh"
+#include "k_soft.cuh"
 
 using namespace cvc;
 
@@ -85,6 +86,11 @@ struct cvc_ct_plan {
     PlaneLayout lay;
     CtEngine eng;
     float* d_work = nullptr;
+    // soft thresholding: chunk jobs, first job of each directional subband, partial sums
+    SoftJob* d_soft = nullptr;
+    int* d_soft_first = nullptr;
+    float* d_soft_partial = nullptr;
+    int nsoft = 0, nsub = 0;
     std::vector<void*> allocs;
     ~cvc_ct_plan() {
         for (void* p : allocs) cudaFree(p);
@@ -162,7 +168,16 @@ cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, in
     p->batch = batch;
     for (int j = 0; j < levels; j++) p->k[j] = dirs_log2[j];
     std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, p->lay.total);
+    std::vector<SoftJob> sj;
+    std::vector<int> sf;
+    soft_jobs(p->lay, batch, &sj, &sf);
+    p->nsoft = (int)sj.size();
+    p->nsub = (int)sf.size() - 1;
     if (!engine_build(&p->eng, planes) || !dalloc(p->allocs, &p->d_work, (size_t)p->eng.work_elems) ||
+        !dalloc(p->allocs, &p->d_soft, sj.size()) || !dalloc(p->allocs, &p->d_soft_first, sf.size()) ||
+        !dalloc(p->allocs, &p->d_soft_partial, sj.size()) ||
+        cudaMemcpy(p->d_soft, sj.data(), sj.size() * sizeof(SoftJob), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_soft_first, sf.data(), sf.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         lp_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -205,6 +220,33 @@ cvc_status cvc_ct_forward_adjoint(cvc_ct_plan* plan, const float* d_coeffs_bar, 
 }
 cvc_status cvc_ct_inverse_adjoint(cvc_ct_plan* plan, const float* d_x_bar, float* d_coeffs_bar, cvc_stream_t stream) {
     return ct_run(plan, INV_ADJ, d_x_bar, d_coeffs_bar, stream);
+}
+
+int cvc_ct_plan_subbands(const cvc_ct_plan* plan) { return plan ? plan->nsub : 0; }
+
+cvc_status cvc_ct_soft_threshold(cvc_ct_plan* p, const float* d_coeffs, const float* d_thresholds, float* d_out,
+                                 cvc_stream_t stream) {
+    if (!p || !d_coeffs || !d_thresholds || !d_out) return CVC_ERR_INVALID_ARG;
+    if (launch_soft_fwd(p->d_soft, p->nsoft, d_coeffs, d_thresholds, d_out, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    note_launches(p->nsoft > 0);
+    return CVC_OK;
+}
+
+cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* p, const float* d_coeffs, const float* d_thresholds,
+                                          const float* d_grad_out, float* d_grad_coeffs, float* d_grad_thresholds,
+                                          cvc_stream_t stream) {
+    if (!p || !d_coeffs || !d_thresholds || !d_grad_out || !d_grad_coeffs || !d_grad_thresholds)
+        return CVC_ERR_INVALID_ARG;
+    if (launch_soft_bwd(p->d_soft, p->nsoft, p->d_soft_first, p->nsub, d_coeffs, d_thresholds, d_grad_out,
+                        d_grad_coeffs, d_grad_thresholds, p->d_soft_partial, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    note_launches((p->nsoft > 0) + (p->nsoft > 0 && p->nsub > 0));
+    return CVC_OK;
 }
 
 // ----------------------------------------------------------------- codec

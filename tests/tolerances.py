@@ -17,3 +17,19 @@ FORWARD = 1e-4
 
 def inverse_bound(levels, dirs_log2=None):
     return levels * FORWARD
+
+# Gradients of the threshold-tuning loss mean((S soft_T(A x) - x)^2).  The
+# residual r = S y - x carries the forward and inverse errors (at most
+# FORWARD + inverse_bound(L) = (L + 1) * 1e-4 absolute on the 0-255 scale),
+# and every gradient entry is a sum of the adjoint image of 2r/N weighted by
+# +-1 masks, so its relative error is about that absolute error over the
+# typical residual size (a few units at thresholds of a few units):
+# (L + 1) * 1e-4 / 3 = 2e-4 at L = 5.  Coefficients within the forward error
+# of their threshold may flip their mask; each flip moves one term of a sum
+# over a whole subband.  The bar leaves a factor five:
+GRAD_REL = 1e-3
+
+# Fixed-order single-precision sums of n terms (block partials of up to 4096
+# terms, then a double-precision sum of the partials): error below
+# (log2(4096) + 2) * 2^-24 * sum |terms| = 8.3e-7 * sum |terms|.
+SUM_REL = 1e-5
