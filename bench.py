@@ -165,6 +165,102 @@ def cpu_oracle_rate(frames, band_rows=None, seconds_cap=30.0):
     return done * rows / H_ / dt, done, dt
 
 
+SERVE_CLASSES = [  # (width, height, levels, dirs_log2, weight)
+    (176, 144, 3, [3, 2, 2], 0.20), (352, 288, 3, [3, 2, 2], 0.30), (640, 480, 4, [4, 3, 3, 2], 0.30),
+    (1280, 720, 5, [5, 4, 4, 3, 3], 0.15), (1920, 1080, 5, [5, 4, 4, 3, 3], 0.05)]
+
+
+def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, budget=120 << 30, slots=16,
+               ring=4, seed=0):
+    """Continuous-batching run: n_streams sessions with resolutions drawn by
+    the class weights, Poisson frame arrivals at fps * load per session, each
+    arrival an encode + decode request.  Frames are crops of the 1080p
+    sequence.  A session holds `ring` request buffers; an arrival that finds
+    them all in flight waits on the host (its latency counts from arrival)."""
+    import collections
+    import numpy as np
+    import torch
+    from paper_1510_00561_b300 import Codec, Server
+    rng = np.random.default_rng(seed)
+    cls = rng.choice(len(SERVE_CLASSES), n_streams, p=[c[4] for c in SERVE_CLASSES])
+    srv = Server(budget, slots_per_shard=slots)
+    sess = []
+    max_stream = {}
+    for i in range(n_streams):
+        w, h, L, k, _ = SERVE_CLASSES[cls[i]]
+        cfg = dict(width=w, height=h, levels=L, dirs_log2=k, qph=QPH, qpl=QPL, key_interval=KINT)
+        if (w, h) not in max_stream:
+            max_stream[(w, h)] = Codec(**cfg).max_stream
+        bufs = [(torch.empty(max_stream[(w, h)], dtype=torch.uint8, device=dev),
+                 torch.empty((h, w, 3), dtype=torch.uint8, device=dev)) for _ in range(ring)]
+        sess.append(dict(id=srv.open(**cfg), w=w, h=h, bufs=bufs, free=list(range(ring)),
+                         arrivals=collections.deque(), t=0))
+    setup = srv.stats()
+    # arrival times (seconds from start) of every session
+    events = []
+    for i in range(n_streams):
+        t = rng.exponential(1.0 / (fps * load))
+        while t < seconds:
+            events.append((t, i))
+            t += rng.exponential(1.0 / (fps * load))
+    events.sort()
+    lat, inflight = [], {}
+    tag = 0
+    t0 = Server.now_ns()
+    ev_i = 0
+    done = 0
+    deadline = t0 + int(seconds * 4e9)
+    pending = set()        # sessions with arrivals not yet submitted
+
+    def pump():
+        nonlocal tag
+        for i in list(pending):
+            S = sess[i]
+            while S["arrivals"] and S["free"]:
+                arr = S["arrivals"].popleft()
+                b = S["free"].pop()
+                out, rgb_out = S["bufs"][b]
+                f = d_frames[S["t"] % len(d_frames)][:S["h"], :S["w"]]
+                S["t"] += 1
+                srv.submit(S["id"], 3, rgb=f, out=out, rgb_out=rgb_out, tag=tag)
+                inflight[tag] = (i, b, arr)
+                tag += 1
+            if not S["arrivals"]:
+                pending.discard(i)
+
+    while True:
+        now = Server.now_ns()
+        while ev_i < len(events) and t0 + int(events[ev_i][0] * 1e9) <= now:
+            t_arr, i = events[ev_i]
+            sess[i]["arrivals"].append(t0 + int(t_arr * 1e9))
+            pending.add(i)
+            ev_i += 1
+        pump()
+        for c in srv.poll(wait_us=200):
+            i, b, arr = inflight.pop(c["tag"])
+            sess[i]["free"].append(b)
+            if c["enc_status"] == 0 and c["dec_status"] == 0:
+                lat.append((c["t_done_ns"] - arr) / 1e6)
+                done += 1
+            if sess[i]["arrivals"]:
+                pending.add(i)
+        if ev_i == len(events) and not inflight and not pending:
+            break
+        if now > deadline:
+            break
+    t_end = Server.now_ns()
+    st = srv.stats()
+    wall = (t_end - t0) / 1e9
+    lat_sorted = sorted(lat)
+    q = lambda p: lat_sorted[min(len(lat_sorted) - 1, int(p * len(lat_sorted)))] if lat_sorted else None
+    return {"streams": n_streams, "load": load, "offered_fps": len(events) / seconds,
+            "completed": done, "requests": len(events), "frames_per_s": done / wall, "wall_s": wall,
+            "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat_sorted[-1] if lat_sorted else None,
+            "shards": setup["shards"], "admitted": setup["active_sessions"], "waiting": setup["waiting_sessions"],
+            "peak_bytes": st["peak_used_bytes"], "budget_bytes": budget, "steps": st["steps"],
+            "requests_per_step": st["requests_done"] / max(1, st["steps"])}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -207,6 +303,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="concurrent 1080p streams per GPU in the batched form")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served run (0: skip)")
+    ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -314,6 +412,7 @@ def main():
         return [d_frames[(i + 3 * j) % F] for j in range(B)]
 
     shape = batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
+    info0 = batch.info[0]
     batch_bytes = [0]
 
     def batch_step(i):
@@ -360,6 +459,16 @@ def main():
 
     e2e_ms = timed(batch_e2e_step, e2e_steps, flush_between=False)
     e2e_value = e2e_steps * B * world / (e2e_ms / 1e3)
+    del batch, outs_rgb, d_ins
+
+    # served form: continuous batching of concurrent streams under a memory budget
+    served = None
+    if args.serve_seconds > 0:
+        torch.cuda.synchronize()
+        served = served_run(d_frames, dev, seconds=args.serve_seconds, seed=rank)
+        if args.serve_sweep:
+            served["sweep"] = [served_run(d_frames, dev, seconds=args.serve_seconds, load=float(m), seed=rank)
+                               for m in args.serve_sweep.split(",")]
 
     if rank != 0:
         if world > 1:
@@ -370,7 +479,7 @@ def main():
     pk = peaks()
     frames_staged = stage_steps * B
     mean_bytes = batch_bytes[0] / ((args.warmup + args.steps + stage_steps) * B)
-    info = batch.info[0]
+    info = info0
     tokens = (mean_bytes - 32 - 4 * info.components) / 2
     sb = stage_bytes(info, tokens)
     dom = max(stage, key=lambda k: stage[k][0])
@@ -399,7 +508,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain,
+            "plain": plain, "served": served,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},

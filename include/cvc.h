@@ -279,6 +279,70 @@ cvc_status cvc_batch_set_graphs(cvc_batch* batch, int on);
 cvc_status cvc_batch_set_timing(cvc_batch* batch, int on);
 cvc_status cvc_batch_timing(const cvc_batch* batch, double* ms, long long* launches);
 
+/* ---------------------------------------------------------------- server
+ * A continuous-batching request loop over many concurrent streams (the
+ * deployment form of the codec for conferencing: §4's real-time claim, many
+ * streams per GPU).  Streams ("sessions") open and close at any time;
+ * frames are submitted as they arrive and complete asynchronously.
+ *   - Admission by memory: a session is admitted when a slot for its
+ *     parameters is free or a new shard fits the budget (the exact device
+ *     bytes of cvc_batch_device_bytes); until then it waits (first fit, in
+ *     opening order) and its submitted frames queue.
+ *   - Shards: sessions with identical parameters share a shard of
+ *     slots_per_shard slots; one step of a shard codes the next queued
+ *     request of each of its sessions (one CUDA-graph launch).  Every shard
+ *     runs on its own CUDA stream, so shards overlap on the device; requests
+ *     that arrive while a shard's step runs go into its next step.
+ *   - Coder state stays resident in the shard; a session's requests run in
+ *     submission order.  Each result is bit-identical to a cvc_codec of the
+ *     same parameters fed the same requests, whatever else is in flight.
+ *   - An empty shard is freed, which may admit waiting sessions.
+ * The caller drives the loop with cvc_server_poll (no hidden threads).
+ * Buffers in a request are the caller's and must stay valid until its
+ * completion is returned.                                                   */
+typedef struct cvc_server cvc_server;
+
+typedef struct {
+    size_t budget_bytes;   /* device bytes the server may hold (shards' state and workspace) */
+    int slots_per_shard;   /* 1..256 */
+} cvc_server_config;
+
+typedef struct {
+    uint64_t tag;                /* the caller's tag of the request */
+    int session;
+    int kind;                    /* CVC_STEP_* of the request */
+    cvc_status enc_status, dec_status;
+    size_t out_len;
+    int frame_type, dec_frame_type;
+    int64_t t_submit_ns, t_launch_ns, t_done_ns;   /* cvc_server_now_ns clock */
+} cvc_server_completion;
+
+typedef struct {
+    size_t budget_bytes, used_bytes, peak_used_bytes;
+    int shards, active_sessions, waiting_sessions;
+    long long steps, requests_done, requests_queued;
+} cvc_server_stats;
+
+/* host steady clock (CLOCK_MONOTONIC) in nanoseconds */
+int64_t cvc_server_now_ns(void);
+cvc_status cvc_server_create(const cvc_server_config* config, cvc_server** out);
+/* waits for in-flight steps, frees everything */
+cvc_status cvc_server_destroy(cvc_server* server);
+/* open a session; NOMEM if one shard of its parameters exceeds the whole budget */
+cvc_status cvc_server_open(cvc_server* server, const cvc_params* params, int* session);
+/* no further submits; the slot is freed after the session's last completion */
+cvc_status cvc_server_close(cvc_server* server, int session);
+/* queue one request (io as for cvc_batch_step; `kind` CVC_STEP_*).
+ * INVALID_ARG (nothing queued) for a closed session or buffers that do not
+ * fit the session's frame size.                                             */
+cvc_status cvc_server_submit(cvc_server* server, int session, int kind, const cvc_batch_io* io, uint64_t tag);
+/* Run the loop once: collect finished steps, free and admit, launch steps
+ * for idle shards with queued requests; then, if no completion is ready,
+ * wait up to wait_us microseconds for one.  Copies up to max_out
+ * completions to out (*n_out of them); the rest stay for the next poll.    */
+cvc_status cvc_server_poll(cvc_server* server, int wait_us, cvc_server_completion* out, int max_out, int* n_out);
+cvc_status cvc_server_get_stats(const cvc_server* server, cvc_server_stats* out);
+
 /* --------------------------------------------------------------- tracing
  * Per-stage GPU time of a codec (the per-operation breakdown of §4.2),
  * measured with CUDA events recorded on the call's stream around each stage

@@ -67,6 +67,24 @@ class BatchResult(ctypes.Structure):
                 ("dec_frame_index", ctypes.c_uint32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("slots_per_shard", ctypes.c_int)]
+
+
+class ServerCompletion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("session", ctypes.c_int), ("kind", ctypes.c_int),
+                ("enc_status", ctypes.c_int), ("dec_status", ctypes.c_int), ("out_len", ctypes.c_size_t),
+                ("frame_type", ctypes.c_int), ("dec_frame_type", ctypes.c_int),
+                ("t_submit_ns", ctypes.c_int64), ("t_launch_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_used_bytes", ctypes.c_size_t), ("shards", ctypes.c_int), ("active_sessions", ctypes.c_int),
+                ("waiting_sessions", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("requests_done", ctypes.c_longlong), ("requests_queued", ctypes.c_longlong)]
+
+
 STEP_ENCODE, STEP_DECODE, STEP_ENCODE_DECODE = 1, 2, 3
 
 _lib = None
@@ -119,6 +137,15 @@ def lib():
         L.cvc_batch_set_graphs.argtypes = [_P, _I]
         L.cvc_batch_set_timing.argtypes = [_P, _I]
         L.cvc_batch_timing.argtypes = [_P, _P, _P]
+        L.cvc_server_now_ns.argtypes = []
+        L.cvc_server_now_ns.restype = ctypes.c_int64
+        L.cvc_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
+        L.cvc_server_destroy.argtypes = [_P]
+        L.cvc_server_open.argtypes = [_P, ctypes.POINTER(Params), ctypes.POINTER(_I)]
+        L.cvc_server_close.argtypes = [_P, _I]
+        L.cvc_server_submit.argtypes = [_P, _I, _I, ctypes.POINTER(BatchIo), ctypes.c_uint64]
+        L.cvc_server_poll.argtypes = [_P, _I, ctypes.POINTER(ServerCompletion), _I, ctypes.POINTER(_I)]
+        L.cvc_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
         L.cvc_debug_plan_tables.argtypes = [ctypes.POINTER(Params), _I, _I, _I, ctypes.POINTER(_I), _I, _I, _P,
                                             _SZ, ctypes.POINTER(_SZ)]
         _lib = L

@@ -311,3 +311,73 @@ class Batch:
         _L.check(_L.lib().cvc_batch_autotune(self._h, what, self._io, reps, shape, _stream(stream)),
                  "cvc_batch_autotune")
         return shape[0], shape[1]
+
+
+class Server:
+    """Continuous-batching request loop over many streams (cvc_server_*).
+
+    open(**codec kwargs) -> session id (admitted now or when memory frees);
+    submit(session, kind, rgb=..., out=..., stream_in=..., rgb_out=..., tag=...)
+    queues a request (kind 1 encode, 2 decode, 3 encode + decode of its own
+    output); poll() runs the loop and returns completions as dicts.  Request
+    buffers must stay alive until their completion is returned.
+    """
+
+    def __init__(self, budget_bytes, slots_per_shard=8):
+        cfg = _L.ServerConfig(int(budget_bytes), int(slots_per_shard))
+        p = ctypes.c_void_p()
+        _L.check(_L.lib().cvc_server_create(ctypes.byref(cfg), ctypes.byref(p)), "cvc_server_create")
+        self._h = p
+        self._cpl = (_L.ServerCompletion * 4096)()
+        self._keep = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _L._lib is not None:
+            _L.lib().cvc_server_destroy(h)
+            self._h = None
+
+    @staticmethod
+    def now_ns():
+        return int(_L.lib().cvc_server_now_ns())
+
+    def open(self, **stream):
+        prm = _L.params(**stream)
+        sid = ctypes.c_int(-1)
+        _L.check(_L.lib().cvc_server_open(self._h, ctypes.byref(prm), ctypes.byref(sid)), "cvc_server_open")
+        return sid.value
+
+    def close(self, session):
+        _L.check(_L.lib().cvc_server_close(self._h, session), "cvc_server_close")
+
+    def submit(self, session, kind, rgb=None, out=None, stream_in=None, rgb_out=None, tag=0):
+        io = _L.BatchIo()
+        if rgb is not None:
+            io.d_rgb, io.pitch_bytes = rgb.data_ptr(), rgb.stride(0)
+        if out is not None:
+            io.d_out, io.out_cap = out.data_ptr(), out.numel()
+        if stream_in is not None:
+            io.d_in, io.in_len = stream_in.data_ptr(), stream_in.numel()
+        if rgb_out is not None:
+            io.d_rgb_out, io.pitch_out = rgb_out.data_ptr(), rgb_out.stride(0)
+        _L.check(_L.lib().cvc_server_submit(self._h, session, kind, ctypes.byref(io), int(tag)), "cvc_server_submit")
+        self._keep[int(tag)] = (rgb, out, stream_in, rgb_out)   # alive until completion
+
+    def poll(self, wait_us=0):
+        n = ctypes.c_int(0)
+        _L.check(_L.lib().cvc_server_poll(self._h, int(wait_us), self._cpl, len(self._cpl), ctypes.byref(n)),
+                 "cvc_server_poll")
+        res = []
+        for i in range(n.value):
+            c = self._cpl[i]
+            self._keep.pop(int(c.tag), None)
+            res.append(dict(tag=c.tag, session=c.session, kind=c.kind, enc_status=c.enc_status,
+                            dec_status=c.dec_status, out_len=c.out_len, frame_type=c.frame_type,
+                            dec_frame_type=c.dec_frame_type, t_submit_ns=c.t_submit_ns,
+                            t_launch_ns=c.t_launch_ns, t_done_ns=c.t_done_ns))
+        return res
+
+    def stats(self):
+        st = _L.ServerStats()
+        _L.check(_L.lib().cvc_server_get_stats(self._h, ctypes.byref(st)), "cvc_server_get_stats")
+        return {f: getattr(st, f) for f, _ in _L.ServerStats._fields_}

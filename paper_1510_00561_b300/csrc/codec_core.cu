@@ -443,10 +443,32 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
 
 }  // namespace
 
+cvc_status core_capture(Core* c, int mode) {
+    if (mode < STEP_ENC || mode > STEP_ENCDEC) return CVC_ERR_INVALID_ARG;
+    if (c->gexec[mode]) return CVC_OK;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    long long nl = 0;
+    cudaError_t e = enqueue_direct(c, mode, c->cap_stream, false, &nl);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[mode], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        c->gexec[mode] = nullptr;
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    c->gkernels[mode] = nl;
+    return CVC_OK;
+}
+
 cvc_status core_enqueue(Core* c, int mode, cudaStream_t st) {
     if (mode < STEP_ENC || mode > STEP_ENCDEC) return CVC_ERR_INVALID_ARG;
-    long long nl = 0;
     if (!c->use_graphs || c->timing) {
+        long long nl = 0;
         if (enqueue_direct(c, mode, st, c->timing, &nl) != cudaSuccess) {
             cudaGetLastError();
             return CVC_ERR_CUDA;
@@ -454,23 +476,8 @@ cvc_status core_enqueue(Core* c, int mode, cudaStream_t st) {
         note_launches(nl);
         return CVC_OK;
     }
-    if (!c->gexec[mode]) {
-        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            cudaGetLastError();
-            return CVC_ERR_CUDA;
-        }
-        cudaError_t e = enqueue_direct(c, mode, c->cap_stream, false, &nl);
-        cudaGraph_t g = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[mode], g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            c->gexec[mode] = nullptr;
-            cudaGetLastError();
-            return CVC_ERR_CUDA;
-        }
-        c->gkernels[mode] = nl;
-    }
+    cvc_status s = core_capture(c, mode);
+    if (s != CVC_OK) return s;
     if (cudaGraphLaunch(c->gexec[mode], st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;

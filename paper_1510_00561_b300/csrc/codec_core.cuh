@@ -96,6 +96,8 @@ cvc_status core_alloc(Core* c);
 void core_reset(Core* c, int s);
 // enqueue one step (the records in h_sc must be filled); no synchronisation
 cvc_status core_enqueue(Core* c, int mode, cudaStream_t st);
+// capture the graph of a step mode ahead of its first use (no launch)
+cvc_status core_capture(Core* c, int mode);
 // after the step completed: collect stage times
 void core_collect(Core* c);
 cvc_status core_set_timing(Core* c, bool on);
