@@ -303,6 +303,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="concurrent 1080p streams per GPU in the batched form")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served run (0: skip)")
     ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
     args = ap.parse_args()
@@ -411,7 +412,7 @@ def main():
     def frames_at(i):
         return [d_frames[(i + 3 * j) % F] for j in range(B)]
 
-    shape = batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
+    shape = (8, 148 * 8) if args.no_autotune else batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
     info0 = batch.info[0]
     batch_bytes = [0]
 

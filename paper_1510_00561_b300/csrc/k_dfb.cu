@@ -32,66 +32,180 @@ __device__ __forceinline__ int wrapd(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-__constant__ float c_bt[4] = {-1.f / 16, -9.f / 16, 9.f / 16, 1.f / 16};
+// the dyadic taps betat = (-1, -9, 9, 1) / 16 as immediates
+constexpr float BT0 = -0.0625f, BT1 = -0.5625f, BT2 = 0.5625f, BT3 = 0.0625f;
+
+// 4-byte asynchronous global -> shared copies: a thread issues all of its
+// staging loads before waiting, so a tile's whole halo is in flight at once
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 // ============================================================ k_dfb_a
 constexpr int SA = DFBA_TILE + 2 * DFBA_HALO;  // 88: tile + halo, image samples
 constexpr int PA = SA / 2;                     // 44: polyphase plane side
 constexpr int PAS = PA + 1;                    // padded plane row stride
 
-// tap t = 4*ia + ib, a = 2ia-3, b = 2ib-3; image offset of the tap for a
-// target of class (pr, pc) at stage 1 / 2
-__host__ __device__ constexpr int tap_dy(int stage, int pr, int pc, int t) {
-    return stage == 1 ? ((2 * (t >> 2) - 3) + (2 * (t & 3) - 3)) / 2
-                      : (pr == pc ? (2 * (t >> 2) - 3) : (2 * (t & 3) - 3));
-}
-__host__ __device__ constexpr int tap_dx(int stage, int pr, int pc, int t) {
-    return stage == 1 ? ((2 * (t >> 2) - 3) - (2 * (t & 3) - 3)) / 2
-                      : (pr == pc ? (2 * (t & 3) - 3) : (2 * (t >> 2) - 3));
-}
 __host__ __device__ constexpr int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+// plane rows (or columns) of parity p whose image index lies in [lo, hi)
+__host__ __device__ constexpr int pl0(int lo, int p) { return (lo - p + 1) / 2; }
+__host__ __device__ constexpr int pl1(int hi, int p) { return (hi - 1 - p) / 2 + 1; }
 
-// one pass over target class (PR, PC): plane rows / columns [u0, u1) x [v0, v1)
-template <int STAGE, int PR, int PC>
-__device__ __forceinline__ void dfba_class_pass(float* planes, int n, float alpha, float gamma) {
-    const int lo = 3 * n, hi = SA - 3 * n;
-    const int u0 = (lo - PR + 1) / 2, u1 = (hi - 1 - PR) / 2 + 1;
-    const int v0 = (lo - PC + 1) / 2, v1 = (hi - 1 - PC) / 2 + 1;
-    const int nu = u1 - u0, nv = v1 - v0;
-    float* T = planes + (2 * PR + PC) * PA * PAS;
-    for (int k = threadIdx.x; k < nu * nv; k += blockDim.x) {
-        const int u = u0 + k / nv, v = v0 + k % nv;
-        float acc = 0.f;
+// Both stages evaluate their 16-tap stencils separably.
+//   Stage 1 (quincunx, taps at ((a+b)/2, (a-b)/2)): the anti-diagonal sums
+//     D[p] = sum_m betat[m] x[p + (m, -m)] at the source coset's points, then
+//     acc(t) = sum_n betat[n] D[t + (n - 3, n)].
+//   Stage 2 (taps at (a, b) in both families): row sums along the target's
+//     source plane, then sums down its columns.
+// A pass over image-local [lo, hi)^2, lo = 3n, reads the region the previous
+// pass left valid, [lo - 3, hi + 3)^2.  Warps take plane rows, lanes columns.
+
+template <int N, bool ODD>
+__device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alpha, float gamma) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones; D of class
+    // (sr, sc) goes to tmp plane sr
 #pragma unroll
-        for (int t = 0; t < 16; t++) {
-            const int dy = tap_dy(STAGE, PR, PC, t), dx = tap_dx(STAGE, PR, PC, t);
-            const int sr = PR + dy, sc = PC + dx;
-            const int q = ((sr & 1) << 1) | (sc & 1);
-            const float* S = planes + q * PA * PAS;
-            acc = fmaf(c_bt[t >> 2] * c_bt[t & 3], S[(u + fdiv2(sr)) * PAS + v + fdiv2(sc)], acc);
+    for (int k = 0; k < 2; k++) {
+        const int sr = k, sc = ODD ? k : 1 - k;
+        // D at image rows [lo-3, hi), columns [lo, hi+3)
+        const int u0 = pl0(lo - 3, sr), u1 = pl1(hi, sr), v0 = pl0(lo, sc), v1 = pl1(hi + 3, sc);
+        const float* Pm[4];
+        int du[4], dv[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            Pm[m] = planes + (2 * ((sr + m) & 1) + ((sc - m) & 1)) * PA * PAS;
+            du[m] = fdiv2(sr + m);
+            dv[m] = fdiv2(sc - m);
         }
-        T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
-    }
-}
-
-template <int STAGE>
-__device__ __forceinline__ void dfba_pass(float* planes, int n, int odd, float alpha, float gamma) {
-    if (STAGE == 1) {
-        // stage 1: odd coset = classes 01, 10; even = 00, 11
-        if (odd) { dfba_class_pass<1, 0, 1>(planes, n, alpha, gamma); dfba_class_pass<1, 1, 0>(planes, n, alpha, gamma); }
-        else { dfba_class_pass<1, 0, 0>(planes, n, alpha, gamma); dfba_class_pass<1, 1, 1>(planes, n, alpha, gamma); }
-    } else {
-        // stage 2: odd coset = classes 11 (family c), 01 (family r); even = 00 (c), 10 (r)
-        if (odd) { dfba_class_pass<2, 1, 1>(planes, n, alpha, gamma); dfba_class_pass<2, 0, 1>(planes, n, alpha, gamma); }
-        else { dfba_class_pass<2, 0, 0>(planes, n, alpha, gamma); dfba_class_pass<2, 1, 0>(planes, n, alpha, gamma); }
+        float* D = tmp + sr * PA * PAS;
+        for (int u = u0 + warp; u < u1; u += 8) {
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int v = v0 + lane + 32 * j;
+                if (v < v1) {
+                    float acc = BT0 * Pm[0][(u + du[0]) * PAS + v + dv[0]];
+                    acc = fmaf(BT1, Pm[1][(u + du[1]) * PAS + v + dv[1]], acc);
+                    acc = fmaf(BT2, Pm[2][(u + du[2]) * PAS + v + dv[2]], acc);
+                    D[u * PAS + v] = fmaf(BT3, Pm[3][(u + du[3]) * PAS + v + dv[3]], acc);
+                }
+            }
+        }
     }
     __syncthreads();
+    // targets: {01, 10} (odd) or {00, 11}
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int tr = k, tc = ODD ? 1 - k : k;
+        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
+        float* T = planes + (2 * tr + tc) * PA * PAS;
+        const float* Dn[4];
+        int du[4], dv[4];
+#pragma unroll
+        for (int n = 0; n < 4; n++) {
+            Dn[n] = tmp + ((tr + n + 1) & 1) * PA * PAS;
+            du[n] = fdiv2(tr + n - 3);
+            dv[n] = fdiv2(tc + n);
+        }
+        for (int u = u0 + warp; u < u1; u += 8) {
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int v = v0 + lane + 32 * j;
+                if (v < v1) {
+                    float acc = BT0 * Dn[0][(u + du[0]) * PAS + v + dv[0]];
+                    acc = fmaf(BT1, Dn[1][(u + du[1]) * PAS + v + dv[1]], acc);
+                    acc = fmaf(BT2, Dn[2][(u + du[2]) * PAS + v + dv[2]], acc);
+                    acc = fmaf(BT3, Dn[3][(u + du[3]) * PAS + v + dv[3]], acc);
+                    T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, bool ODD>
+__device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alpha, float gamma) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // targets: {11, 01} (odd) or {00, 10}; target (tr, tc) reads class (1-tr, 1-tc)
+    // at plane (u + ky + tr - 2, v + kx + tc - 2); row sums go to tmp plane tr
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int tr = k, tc = ODD ? 1 : 0;
+        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
+        const float* Sp = planes + (2 * (1 - tr) + (1 - tc)) * PA * PAS + (tc - 2);
+        float* Rs = tmp + tr * PA * PAS;
+        for (int u = u0 + tr - 2 + warp; u < u1 + tr + 1; u += 8) {
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int v = v0 + lane + 32 * j;
+                if (v < v1) {
+                    const float* src = Sp + u * PAS + v;
+                    float acc = BT0 * src[0];
+                    acc = fmaf(BT1, src[1], acc);
+                    acc = fmaf(BT2, src[2], acc);
+                    Rs[u * PAS + v] = fmaf(BT3, src[3], acc);
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int tr = k, tc = ODD ? 1 : 0;
+        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
+        float* T = planes + (2 * tr + tc) * PA * PAS;
+        const float* Rs = tmp + tr * PA * PAS + (tr - 2) * PAS;
+        for (int u = u0 + warp; u < u1; u += 8) {
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int v = v0 + lane + 32 * j;
+                if (v < v1) {
+                    const float* h = Rs + u * PAS + v;
+                    float acc = BT0 * h[0];
+                    acc = fmaf(BT1, h[PAS], acc);
+                    acc = fmaf(BT2, h[2 * PAS], acc);
+                    acc = fmaf(BT3, h[3 * PAS], acc);
+                    T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// the passes of one tile: analysis runs stage 1 then 2, synthesis stage 2 then 1
+template <bool SYN, bool FO>
+__device__ __forceinline__ void dfba_passes(float* planes, float* tmp, int nst, const PassParams& pp) {
+    if (!SYN) {
+        dfba_stage1<1, FO>(planes, tmp, pp.a1, pp.g1);
+        dfba_stage1<2, !FO>(planes, tmp, pp.a2, pp.g2);
+        if (nst == 2) {
+            dfba_stage2<3, FO>(planes, tmp, pp.a1, pp.g1);
+            dfba_stage2<4, !FO>(planes, tmp, pp.a2, pp.g2);
+        }
+    } else if (nst == 2) {
+        dfba_stage2<1, FO>(planes, tmp, pp.a1, pp.g1);
+        dfba_stage2<2, !FO>(planes, tmp, pp.a2, pp.g2);
+        dfba_stage1<3, FO>(planes, tmp, pp.a1, pp.g1);
+        dfba_stage1<4, !FO>(planes, tmp, pp.a2, pp.g2);
+    } else {
+        dfba_stage1<1, FO>(planes, tmp, pp.a1, pp.g1);
+        dfba_stage1<2, !FO>(planes, tmp, pp.a2, pp.g2);
+    }
 }
 
 template <bool SYN>
 __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     __shared__ float planes[4 * PA * PAS];
+    __shared__ float tmp[2 * PA * PAS];
     const DfbAJob& J = jobs[block_job[blockIdx.x]];
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
@@ -105,7 +219,8 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
         for (int k = threadIdx.x; k < SA * SA; k += blockDim.x) {
             int r = k / SA, c = k - r * SA;
             int y = wrapd(y0 - DFBA_HALO + r, H), x = wrapd(x0 - DFBA_HALO + c, W);
-            planes[(2 * (r & 1) + (c & 1)) * PA * PAS + (r >> 1) * PAS + (c >> 1)] = Dp[(long long)y * J.D.rs + x];
+            cp_async4(&planes[(2 * (r & 1) + (c & 1)) * PA * PAS + (r >> 1) * PAS + (c >> 1)],
+                      Dp + (long long)y * J.D.rs + x);
         }
     } else {
         for (int q = 0; q < 4; q++) {
@@ -116,28 +231,14 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
                 int a = k / PA, b = k - a * PA;
                 int u = trans ? b : a, v = trans ? a : b;
                 int cu = wrapd(cu0 + u, H2), cv = wrapd(cv0 + v, W2);
-                planes[q * PA * PAS + u * PAS + v] = P[(long long)cu * V.rs + (long long)cv * V.cs];
+                cp_async4(&planes[q * PA * PAS + u * PAS + v], P + (long long)cu * V.rs + (long long)cv * V.cs);
             }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
-    // analysis runs stage 1 then 2, synthesis stage 2 then 1
-    if (!SYN) {
-        dfba_pass<1>(planes, 1, pp.first_odd, pp.a1, pp.g1);
-        dfba_pass<1>(planes, 2, !pp.first_odd, pp.a2, pp.g2);
-        if (J.nst == 2) {
-            dfba_pass<2>(planes, 3, pp.first_odd, pp.a1, pp.g1);
-            dfba_pass<2>(planes, 4, !pp.first_odd, pp.a2, pp.g2);
-        }
-    } else {
-        int n = 1;
-        if (J.nst == 2) {
-            dfba_pass<2>(planes, n++, pp.first_odd, pp.a1, pp.g1);
-            dfba_pass<2>(planes, n++, !pp.first_odd, pp.a2, pp.g2);
-        }
-        dfba_pass<1>(planes, n++, pp.first_odd, pp.a1, pp.g1);
-        dfba_pass<1>(planes, n++, !pp.first_odd, pp.a2, pp.g2);
-    }
+    if (pp.first_odd) dfba_passes<SYN, true>(planes, tmp, J.nst, pp);
+    else dfba_passes<SYN, false>(planes, tmp, J.nst, pp);
     // store the 64 x 64 tile: plane-local rows / columns [6, 38)
     constexpr int T2 = DFBA_TILE / 2, H6 = DFBA_HALO / 2;
     if (!SYN) {
@@ -169,35 +270,48 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 // ============================================================ k_dfb_b
 constexpr int RB = DFBB_ROWS + 6, CB = DFBB_COLS + 12;
 
-// separable 4 x 4 pass in the sheared frame: target rows [r0, r1) x cols [x0, x1)
+// separable 4 x 4 pass in the sheared frame: target rows [R0, R1) x cols [X0, X1)
 // of array T, sources in array S (rows r + (a + dr)/2 with dr = +1 for odd
-// targets, -1 for even ones; columns x + (b - a)/2).
-__device__ __forceinline__ void dfbb_pass(float* T, const float* S, float* Hs, int r0, int r1, int x0, int x1,
-                                          int odd_target, float alpha, float gamma) {
-    const int sr0 = r0 + (odd_target ? -1 : -2), sr1 = r1 + (odd_target ? 2 : 1);
-    const int hx0 = x0 - 3, hw = x1 - hx0;
+// targets, -1 for even ones; columns x + (b - a)/2).  Warps take rows, lanes
+// take columns (five 32-column groups cover the 140-column frame).
+template <int R0, int R1, int X0, int X1, bool ODD>
+__device__ __forceinline__ void dfbb_pass(float* T, const float* S, float* Hs, float alpha, float gamma) {
+    constexpr int SR0 = R0 + (ODD ? -1 : -2), SR1 = R1 + (ODD ? 2 : 1);
+    constexpr int HX0 = X0 - 3;
+    static_assert(SR0 >= 0 && SR1 <= RB && HX0 >= 0 && X1 + 3 <= CB, "pass window outside the tile");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // row sums h[rr][x'] = sum_b betat[b] * S[rr][x' + (b+3)/2]
-    for (int k = threadIdx.x; k < (sr1 - sr0) * hw; k += blockDim.x) {
-        const int rr = sr0 + k / hw, xx = hx0 + k % hw;
-        const float* src = S + rr * CB + xx;
-        float acc = c_bt[0] * src[0];
-        acc = fmaf(c_bt[1], src[1], acc);
-        acc = fmaf(c_bt[2], src[2], acc);
-        Hs[rr * CB + xx] = fmaf(c_bt[3], src[3], acc);
+    for (int rr = SR0 + warp; rr < SR1; rr += 8) {
+        const float* src = S + rr * CB;
+        float* dst = Hs + rr * CB;
+#pragma unroll
+        for (int j = 0; j < (X1 - HX0 + 31) / 32; j++) {
+            const int xx = HX0 + lane + 32 * j;
+            if (xx < X1) {
+                float acc = BT0 * src[xx];
+                acc = fmaf(BT1, src[xx + 1], acc);
+                acc = fmaf(BT2, src[xx + 2], acc);
+                dst[xx] = fmaf(BT3, src[xx + 3], acc);
+            }
+        }
     }
     __syncthreads();
-    const int w = x1 - x0;
     // tap a (ia = 0..3, a = 2ia - 3): row r + (a + (odd ? 1 : -1))/2 = rb + ia, column x - (a+3)/2 = x - ia
-    const int db = odd_target ? -1 : -2;
-    for (int k = threadIdx.x; k < (r1 - r0) * w; k += blockDim.x) {
-        const int r = r0 + k / w, x = x0 + k % w;
-        const float* h = Hs + (r + db) * CB + x;
-        float acc = c_bt[0] * h[0];
-        acc = fmaf(c_bt[1], h[CB - 1], acc);
-        acc = fmaf(c_bt[2], h[2 * CB - 2], acc);
-        acc = fmaf(c_bt[3], h[3 * CB - 3], acc);
-        float* t = T + r * CB + x;
-        *t = fmaf(alpha, *t, gamma * acc);
+    constexpr int DB = ODD ? -1 : -2;
+    for (int r = R0 + warp; r < R1; r += 8) {
+        const float* h = Hs + (r + DB) * CB;
+        float* t = T + r * CB;
+#pragma unroll
+        for (int j = 0; j < (X1 - X0 + 31) / 32; j++) {
+            const int x = X0 + lane + 32 * j;
+            if (x < X1) {
+                float acc = BT0 * h[x];
+                acc = fmaf(BT1, h[CB + x - 1], acc);
+                acc = fmaf(BT2, h[2 * CB + x - 2], acc);
+                acc = fmaf(BT3, h[3 * CB + x - 3], acc);
+                t[x] = fmaf(alpha, t[x], gamma * acc);
+            }
+        }
     }
     __syncthreads();
 }
@@ -231,24 +345,33 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 const int tu = t0 - 3 + r;
                 const float* row = P + (long long)wrapd(tu, R2) * V.rs;
                 const int vs = wrapd(c0 - 6 - i * (2 * tu + par), C);
-                for (int x = lane; x < CB; x += 32) S[r * CB + x] = row[wrap_fast(vs + x, C)];
+                for (int x = lane; x < CB; x += 32) cp_async4(&S[r * CB + x], row + wrap_fast(vs + x, C));
             }
         } else {
-            for (int k = threadIdx.x; k < RB * CB; k += blockDim.x) {
-                const int x = k / RB, r = k - x * RB;
-                const int tu = t0 - 3 + r;
-                const int v = wrapd(c0 - 6 + x - i * (2 * tu + par), C);
-                S[r * CB + x] = P[(long long)wrapd(tu, R2) * V.rs + (long long)v * V.cs];
+            // transposed array (rows contiguous in memory along t): walk the sheared
+            // tile along memory order; for offset w every row r shares the array
+            // column v, at tile column x = w + 2*i*r
+            const int wlo = i > 0 ? -2 * i * (RB - 1) : 0, whi = CB + (i < 0 ? -2 * i * (RB - 1) : 0);
+            const int vbase = c0 - 6 - i * (2 * (t0 - 3) + par);
+            for (int k = threadIdx.x; k < (whi - wlo) * RB; k += blockDim.x) {
+                const int w = wlo + k / RB, r = k - (k / RB) * RB;
+                const int x = w + 2 * i * r;
+                if (x < 0 || x >= CB) continue;
+                const int v = wrapd(vbase + w, C);
+                cp_async4(&S[r * CB + x], P + (long long)wrapd(t0 - 3 + r, R2) * V.rs + (long long)v * V.cs);
             }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     // pass 1 covers what pass 2 needs; pass 2 covers the tile [3, 3+ROWS) x [6, 6+COLS)
-    const int fo = pp.first_odd;
-    if (fo) dfbb_pass(sO, sE, sH, 1, DFBB_ROWS + 4, 3, DFBB_COLS + 9, 1, pp.a1, pp.g1);
-    else dfbb_pass(sE, sO, sH, 2, DFBB_ROWS + 5, 3, DFBB_COLS + 9, 0, pp.a1, pp.g1);
-    if (fo) dfbb_pass(sE, sO, sH, 3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, 0, pp.a2, pp.g2);
-    else dfbb_pass(sO, sE, sH, 3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, 1, pp.a2, pp.g2);
+    if (pp.first_odd) {
+        dfbb_pass<1, DFBB_ROWS + 4, 3, DFBB_COLS + 9, true>(sO, sE, sH, pp.a1, pp.g1);
+        dfbb_pass<3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, false>(sE, sO, sH, pp.a2, pp.g2);
+    } else {
+        dfbb_pass<2, DFBB_ROWS + 5, 3, DFBB_COLS + 9, false>(sE, sO, sH, pp.a1, pp.g1);
+        dfbb_pass<3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, true>(sO, sE, sH, pp.a2, pp.g2);
+    }
     // outputs: analysis writes the children, synthesis the parent's cosets
     const int ncol = min(DFBB_COLS, C - c0);
     for (int par = 0; par < 2; par++) {
@@ -264,11 +387,16 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast(vs + xx, C)] = S[(3 + rr) * CB + 6 + xx];
             }
         } else {
-            for (int k = threadIdx.x; k < DFBB_ROWS * DFBB_COLS; k += blockDim.x) {
-                const int xx = k / DFBB_ROWS, rr = k - xx * DFBB_ROWS;
+            // transposed subband: walk along memory order as in the load
+            const int wlo = i > 0 ? -2 * i * (DFBB_ROWS - 1) : 0;
+            const int whi = DFBB_COLS + (i < 0 ? -2 * i * (DFBB_ROWS - 1) : 0);
+            const int vbase = c0 - i * (2 * t0 + par);
+            for (int k = threadIdx.x; k < (whi - wlo) * DFBB_ROWS; k += blockDim.x) {
+                const int w = wlo + k / DFBB_ROWS, rr = k - (k / DFBB_ROWS) * DFBB_ROWS;
+                const int xx = w + 2 * i * rr;
                 const int t = t0 + rr;
-                if (t >= R2 || xx >= ncol) continue;
-                const int v = wrapd(c0 + xx - i * (2 * t + par), C);
+                if (xx < 0 || xx >= ncol || t >= R2) continue;
+                const int v = wrapd(vbase + w, C);
                 P[(long long)t * V.rs + (long long)v * V.cs] = S[(3 + rr) * CB + 6 + xx];
             }
         }
