@@ -55,8 +55,6 @@ void carve_all(Core* c, Carve& k) {
         k.add(&c->d_dst_buf[b], (size_t)c->ncoef);
     }
     k.add(&c->d_res, (size_t)c->ncoef);
-    k.add(&c->d_est, 2);
-    k.add(&c->d_dst, 2);
     k.add(&c->d_rowcnt, (size_t)c->nrows);
     k.add(&c->d_rowoff, (size_t)c->nrows + 1);
     k.add(&c->d_scan_tmp, (size_t)cdiv(c->nrows, 2048) + 8);
@@ -189,7 +187,9 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.max_tok = 2 * D.ncoef + 64;
         D.blk_colour = (int)c->h_blk_colour.size();
         D.blk_colour_inv = (int)c->h_blk_colour_inv.size();
-        const long long nb_col = cdiv(D.nplane, ELEM_BLOCK), nb_inv = cdiv((long long)g.H * g.W, ELEM_BLOCK);
+        // colour kernels: one block per padded luma row and per padded chroma row (forward),
+        // one per frame row (inverse)
+        const long long nb_col = (long long)g.Hp + g.Hcp, nb_inv = g.H;
         if ((long long)c->h_blk_colour.size() + nb_col > (1LL << 30) ||
             (long long)c->h_blk_colour_inv.size() + nb_inv > (1LL << 30))
             return CVC_ERR_UNSUPPORTED;
@@ -276,16 +276,12 @@ cvc_status core_alloc(Core* c) {
     }
     memset(c->h_sc, 0, sizeof(SCall) * c->n);
     memset(c->h_rs, 0, sizeof(SResult) * c->n);
-    int16_t* est[2] = {c->d_est_buf[0], c->d_est_buf[1]};
-    int16_t* dst[2] = {c->d_dst_buf[0], c->d_dst_buf[1]};
     bool ok = put(c->d_sd, c->sd) && put(c->d_pd, c->h_pd) && put(c->d_blk_colour, c->h_blk_colour) &&
               put(c->d_blk_colour_inv, c->h_blk_colour_inv) && put(c->d_blk_plane, c->h_blk_plane) &&
               put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
               put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
               put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
-              put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
-              cudaMemcpy(c->d_est, est, sizeof(est), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(c->d_dst, dst, sizeof(dst), cudaMemcpyHostToDevice) == cudaSuccess;
+              put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem);
     // state buffers start at zero (no frame may read them before a K-frame)
     for (int b = 0; b < 2 && ok; b++)
         ok = cudaMemset(c->d_est_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess &&
@@ -361,8 +357,7 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
         B.p[B_WORK] = c->d_work;
         // S1-S3: colour, 4:2:0, padding
         clk.begin(0);
-        k_colour_fwd_b<<<(int)c->h_blk_colour.size(), ELEM_BLOCK, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour,
-                                                                           c->d_planes);
+        k_colour_fwd_b<<<(int)c->h_blk_colour.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour, c->d_planes);
         CK(cudaGetLastError());
         clk.end(0, 1);
         // S4, S5: LP analysis, DFB analysis
@@ -375,8 +370,8 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
         k += 1 + engine_part_launches(&c->eng, FWD, 0) + engine_part_launches(&c->eng, FWD, 1);
         // S6-S8: normalise, threshold, quantise, K/P differencing
         clk.begin(3);
-        k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_BLOCK, 0, st>>>(c->d_coef, c->d_est, c->d_pd, c->d_blk_plane,
-                                                                     c->d_sd, c->d_sc, c->d_res, c->d_rs);
+        k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_THREADS, 0, st>>>(
+            c->d_coef, c->d_est_buf[0], c->d_est_buf[1], c->d_pd, c->d_blk_plane, c->d_sd, c->d_sc, c->d_res, c->d_rs);
         CK(cudaGetLastError());
         clk.end(3, 1);
         // S9: RLE rows, row offsets, tokens, headers
@@ -410,10 +405,11 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
         clk.end(5, 8);
         // inverse K/P differencing and dequantisation
         clk.begin(6);
-        k_unquant_b<<<(int)c->h_blk_plane.size(), ELEM_BLOCK, 0, st>>>(c->d_res, c->d_dst, c->d_pd, c->d_blk_plane,
-                                                                       c->d_sd, c->d_sc, c->d_rs, c->d_dcoef);
-        k_unquant_keylow_b<<<(int)cdiv(c->lowcols, 256), 256, 0, st>>>(c->d_res, c->d_dst, c->d_pd, c->nplanes,
-                                                                       c->d_sd, c->d_sc, c->d_rs, c->d_dcoef);
+        k_unquant_b<<<(int)c->h_blk_plane.size(), ELEM_THREADS, 0, st>>>(
+            c->d_res, c->d_dst_buf[0], c->d_dst_buf[1], c->d_pd, c->d_blk_plane, c->d_sd, c->d_sc, c->d_rs, c->d_dcoef);
+        k_unquant_keylow_b<<<(int)cdiv(c->lowcols, 256), 256, 0, st>>>(c->d_res, c->d_dst_buf[0], c->d_dst_buf[1],
+                                                                       c->d_pd, c->nplanes, c->d_sd, c->d_sc, c->d_rs,
+                                                                       c->d_dcoef);
         CK(cudaGetLastError());
         clk.end(6, 2);
         // inverse transform: DFB synthesis, then LP synthesis
@@ -430,7 +426,7 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
         clk.end(8, engine_part_launches(&c->eng, INV, 0));
         // rounding, chroma upsampling, inverse colour transform
         clk.begin(9);
-        k_colour_inv_b<<<(int)c->h_blk_colour_inv.size(), ELEM_BLOCK, 0, st>>>(
+        k_colour_inv_b<<<(int)c->h_blk_colour_inv.size(), 256, 0, st>>>(
             c->d_sd, c->d_sc, c->d_rs, c->d_blk_colour_inv, c->d_rplanes);
         CK(cudaGetLastError());
         clk.end(9, 1);

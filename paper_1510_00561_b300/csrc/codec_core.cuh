@@ -56,7 +56,6 @@ struct Core {
     uint8_t *d_row_low = nullptr, *d_comp_low = nullptr;
     float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
     int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
-    int16_t **d_est = nullptr, **d_dst = nullptr;
     uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
     uint32_t *d_comp_tok = nullptr, *d_tok_base = nullptr, *d_contrib = nullptr, *d_pos = nullptr,
              *d_scan_tmp2 = nullptr;

@@ -16,9 +16,10 @@ __device__ __forceinline__ int mirror_idx(int a, int n) { return a < n ? a : 2 *
 
 // ------------------------------------------------------------- colour
 // YCoCg-R lifting (integer form of Table 1): Co = R-B, t = B + (Co>>1),
-// Cg = G - t, Y = t + (Cg>>1).  Luma items write the padded Y plane, chroma
-// items the padded 2x2-averaged Co / Cg planes (rounded mean, odd edges
-// replicated); padding mirrors about the last row / column.
+// Cg = G - t, Y = t + (Cg>>1).  One block per padded output row: rows
+// [0, Hp) are luma rows, rows [Hp, Hp + Hcp) chroma rows (each writes its Co
+// and Cg row; 2x2 rounded mean, odd edges replicated); padding mirrors about
+// the last row / column.
 __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                const int* __restrict__ blk_stream, float* __restrict__ planes) {
     const int s = blk_stream[blockIdx.x];
@@ -26,38 +27,41 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
     if (!C.enc_on) return;
     const SDesc& D = sd[s];
     const ColourGeom g = D.cg;
-    const long long i = (long long)(blockIdx.x - D.blk_colour) * ELEM_BLOCK + threadIdx.x;
-    const long long nY = (long long)g.Hp * g.Wp, nC = (long long)g.Hcp * g.Wcp;
-    if (i >= nY + nC) return;
+    const int row = blockIdx.x - D.blk_colour;
     const uint8_t* rgb = C.rgb_in;
     const long long pitch = C.pitch_in;
     float* Y = planes + D.plane_off;
-    if (i < nY) {
-        int y = (int)(i / g.Wp), x = (int)(i - (long long)y * g.Wp);
-        int sy = mirror_idx(y, g.H), sx = mirror_idx(x, g.W);
-        const uint8_t* p = rgb + sy * pitch + 3 * sx;
-        int R = p[0], G = p[1], Bv = p[2];
-        int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-        Y[i] = (float)(t + (cg >> 1));
+    if (row < g.Hp) {
+        const uint8_t* src = rgb + (long long)mirror_idx(row, g.H) * pitch;
+        float* out = Y + (long long)row * g.Wp;
+        for (int x = threadIdx.x; x < g.Wp; x += blockDim.x) {
+            const uint8_t* p = src + 3 * mirror_idx(x, g.W);
+            const int R = p[0], G = p[1], Bv = p[2];
+            const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
+            out[x] = (float)(t + (cg >> 1));
+        }
     } else {
-        long long k = i - nY;
-        int cy = (int)(k / g.Wcp), cx = (int)(k - (long long)cy * g.Wcp);
-        int sy = mirror_idx(cy, g.Hc), sx = mirror_idx(cx, g.Wc);
-        int r0 = 2 * sy, r1 = min(2 * sy + 1, g.H - 1), c0 = 2 * sx, c1 = min(2 * sx + 1, g.W - 1);
-        int sco = 0, scg = 0;
-        const int rr[2] = {r0, r1}, cc[2] = {c0, c1};
+        const int cy = row - g.Hp;
+        const int sy = mirror_idx(cy, g.Hc);
+        const uint8_t* r0 = rgb + (long long)(2 * sy) * pitch;
+        const uint8_t* r1 = rgb + (long long)min(2 * sy + 1, g.H - 1) * pitch;
+        float* oco = Y + (long long)g.Hp * g.Wp + (long long)cy * g.Wcp;
+        float* ocg = oco + (long long)g.Hcp * g.Wcp;
+        for (int cx = threadIdx.x; cx < g.Wcp; cx += blockDim.x) {
+            const int sx = mirror_idx(cx, g.Wc);
+            const int c0 = 3 * (2 * sx), c1 = 3 * min(2 * sx + 1, g.W - 1);
+            int sco = 0, scg = 0;
+            const uint8_t* q[4] = {r0 + c0, r0 + c1, r1 + c0, r1 + c1};
 #pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int b = 0; b < 2; b++) {
-                const uint8_t* p = rgb + rr[a] * pitch + 3 * cc[b];
-                int R = p[0], G = p[1], Bv = p[2];
-                int co = R - Bv, t = Bv + (co >> 1);
+            for (int k = 0; k < 4; k++) {
+                const int R = q[k][0], G = q[k][1], Bv = q[k][2];
+                const int co = R - Bv, t = Bv + (co >> 1);
                 sco += co;
                 scg += G - t;
             }
-        Y[nY + k] = (float)((sco + 2) >> 2);
-        Y[nY + nC + k] = (float)((scg + 2) >> 2);
+            oco[cx] = (float)((sco + 2) >> 2);
+            ocg[cx] = (float)((scg + 2) >> 2);
+        }
     }
 }
 
@@ -69,8 +73,8 @@ __device__ __forceinline__ int round_clamp(float v, int lo, int hi) {
 
 // Decoder end: round (ties away from zero) and clamp the reconstructed
 // planes, bilinear (9,3,3,1)/16 chroma upsampling with centred siting and
-// clamped edges, inverse YCoCg-R, clamp to [0, 255].  A stream whose
-// bitstream was rejected leaves its output untouched.
+// clamped edges, inverse YCoCg-R, clamp to [0, 255].  One block per output
+// row.  A stream whose bitstream was rejected leaves its output untouched.
 __global__ void k_colour_inv_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                const SResult* __restrict__ rs, const int* __restrict__ blk_stream,
                                const float* __restrict__ planes) {
@@ -79,34 +83,35 @@ __global__ void k_colour_inv_b(const SDesc* __restrict__ sd, const SCall* __rest
     if (!C.dec_on || rs[s].dec_err) return;
     const SDesc& D = sd[s];
     const ColourGeom g = D.cg;
-    const long long i = (long long)(blockIdx.x - D.blk_colour_inv) * ELEM_BLOCK + threadIdx.x;
-    if (i >= (long long)g.H * g.W) return;
-    const float* Y = planes + D.plane_off;
-    const float* Co = Y + (long long)g.Hp * g.Wp;
+    const int y = blockIdx.x - D.blk_colour_inv;
+    const float* Yrow = planes + D.plane_off + (long long)y * g.Wp;
+    const float* Co = planes + D.plane_off + (long long)g.Hp * g.Wp;
     const float* Cg = Co + (long long)g.Hcp * g.Wcp;
-    int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
-    int yy = round_clamp(Y[(long long)y * g.Wp + x], 0, 255);
-    int i0 = min(y >> 1, g.Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, g.Hc - 1) : max((y >> 1) - 1, 0);
-    int j0 = min(x >> 1, g.Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, g.Wc - 1) : max((x >> 1) - 1, 0);
-    int c[2];
-    const float* P[2] = {Co, Cg};
+    const int i0 = min(y >> 1, g.Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, g.Hc - 1) : max((y >> 1) - 1, 0);
+    const float* P[2][2] = {{Co + (long long)i0 * g.Wcp, Co + (long long)i1 * g.Wcp},
+                            {Cg + (long long)i0 * g.Wcp, Cg + (long long)i1 * g.Wcp}};
+    uint8_t* orow = C.rgb_out + (long long)y * C.pitch_out;
+    for (int x = threadIdx.x; x < g.W; x += blockDim.x) {
+        const int yy = round_clamp(Yrow[x], 0, 255);
+        const int j0 = min(x >> 1, g.Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, g.Wc - 1) : max((x >> 1) - 1, 0);
+        int c[2];
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-        const float* p = P[q];
-        int a = round_clamp(p[(long long)i0 * g.Wcp + j0], -255, 255);
-        int b = round_clamp(p[(long long)i1 * g.Wcp + j0], -255, 255);
-        int d = round_clamp(p[(long long)i0 * g.Wcp + j1], -255, 255);
-        int e = round_clamp(p[(long long)i1 * g.Wcp + j1], -255, 255);
-        c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
+        for (int q = 0; q < 2; q++) {
+            const int a = round_clamp(P[q][0][j0], -255, 255);
+            const int b = round_clamp(P[q][1][j0], -255, 255);
+            const int d = round_clamp(P[q][0][j1], -255, 255);
+            const int e = round_clamp(P[q][1][j1], -255, 255);
+            c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
+        }
+        const int t = yy - (c[1] >> 1);
+        const int G = c[1] + t;
+        const int Bv = t - (c[0] >> 1);
+        const int R = Bv + c[0];
+        uint8_t* o = orow + 3 * x;
+        o[0] = (uint8_t)min(max(R, 0), 255);
+        o[1] = (uint8_t)min(max(G, 0), 255);
+        o[2] = (uint8_t)min(max(Bv, 0), 255);
     }
-    int t = yy - (c[1] >> 1);
-    int G = c[1] + t;
-    int Bv = t - (c[0] >> 1);
-    int R = Bv + c[0];
-    uint8_t* o = C.rgb_out + y * C.pitch_out + 3 * x;
-    o[0] = (uint8_t)min(max(R, 0), 255);
-    o[1] = (uint8_t)min(max(G, 0), 255);
-    o[2] = (uint8_t)min(max(Bv, 0), 255);
 }
 
 // ------------------------------------------------------ quantisation + K/P
@@ -122,53 +127,72 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
     return (int)v;
 }
 
-// codes q (the next coder state) and residuals r of one frame per stream
-__global__ void k_quant_b(const float* __restrict__ coef, int16_t* const* __restrict__ est,
-                          const PDesc* __restrict__ pd, const int* __restrict__ blk_plane,
-                          const SDesc* __restrict__ sd, const SCall* __restrict__ sc, int16_t* __restrict__ res,
-                          SResult* out) {
-    const int p = blk_plane[blockIdx.x];
-    const PDesc P = pd[p];
+// codes q (the next coder state) and residuals r of one frame per stream;
+// a block covers ELEM_BLOCK elements of one plane, ELEM_PER_THREAD per thread
+__global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restrict__ coef, int16_t* est0,
+                                                          int16_t* est1, const PDesc* __restrict__ pd,
+                                                          const int* __restrict__ blk_plane,
+                                                          const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                                          int16_t* __restrict__ res, SResult* out) {
+    const PDesc P = pd[blk_plane[blockIdx.x]];
     const SCall& C = sc[P.stream];
     if (!C.enc_on) return;
-    const long long le = (long long)(blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
-    if (le >= P.total) return;
-    const long long e = P.coef_off + le;
+    const int key = C.enc_key;
+    const int16_t* cur = C.ecur ? est1 : est0;
+    int16_t* nxt = C.ecur ? est0 : est1;
     const QuantParams qp = sd[P.stream].qp;
     uint32_t* err = &out[P.stream].enc_err;
-    const bool low = le < P.low_n;
-    const int q = quant(coef[e], low, qp, err);
-    int r;
-    if (!C.enc_key) r = q - est[C.ecur][e];
-    else if (low && le >= P.low_w) r = q - quant(coef[e - P.low_w], true, qp, err);
-    else r = q;
-    est[1 - C.ecur][e] = (int16_t)q;
-    res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
+    const int total = (int)P.total, low_n = (int)P.low_n, low_w = P.low_w;
+    const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
+    const float* cp = coef + P.coef_off;
+#pragma unroll
+    for (int k = 0; k < ELEM_PER_THREAD; k++) {
+        const int le = base + k * ELEM_THREADS;
+        if (le >= total) break;
+        const long long e = P.coef_off + le;
+        const bool low = le < low_n;
+        const int q = quant(cp[le], low, qp, err);
+        int r;
+        if (!key) r = q - cur[e];
+        else if (low && le >= low_w) r = q - quant(cp[le - low_w], true, qp, err);
+        else r = q;
+        nxt[e] = (int16_t)q;
+        res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
+    }
 }
 
 // decoder side: codes from residuals, then dequantised coefficients
-__global__ void k_unquant_b(const int16_t* __restrict__ res, int16_t* const* __restrict__ dst,
-                            const PDesc* __restrict__ pd, const int* __restrict__ blk_plane,
-                            const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                            const SResult* __restrict__ rs, float* __restrict__ coef) {
-    const int p = blk_plane[blockIdx.x];
-    const PDesc P = pd[p];
+__global__ void __launch_bounds__(ELEM_THREADS) k_unquant_b(const int16_t* __restrict__ res, int16_t* dst0,
+                                                            int16_t* dst1, const PDesc* __restrict__ pd,
+                                                            const int* __restrict__ blk_plane,
+                                                            const SDesc* __restrict__ sd,
+                                                            const SCall* __restrict__ sc,
+                                                            const SResult* __restrict__ rs,
+                                                            float* __restrict__ coef) {
+    const PDesc P = pd[blk_plane[blockIdx.x]];
     const SCall& C = sc[P.stream];
     if (!C.dec_on || rs[P.stream].dec_err) return;
-    const long long le = (long long)(blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
-    if (le >= P.total) return;
     const bool key = rs[P.stream].dec_type == 0;
-    const bool low = le < P.low_n;
-    if (key && low) return;                     // column running sums: k_unquant_keylow_b
-    const long long e = P.coef_off + le;
+    const int16_t* cur = C.dcur ? dst1 : dst0;
+    int16_t* nxt = C.dcur ? dst0 : dst1;
     const QuantParams qp = sd[P.stream].qp;
-    const int q = key ? res[e] : (int16_t)(uint16_t)((res[e] + dst[C.dcur][e]) & 0xFFFF);
-    dst[1 - C.dcur][e] = (int16_t)q;
-    coef[e] = (float)q * (low ? qp.qpl_denorm : qp.qph);
+    const int total = (int)P.total, low_n = (int)P.low_n;
+    const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < ELEM_PER_THREAD; k++) {
+        const int le = base + k * ELEM_THREADS;
+        if (le >= total) break;
+        const bool low = le < low_n;
+        if (key && low) continue;                   // column running sums: k_unquant_keylow_b
+        const long long e = P.coef_off + le;
+        const int q = key ? res[e] : (int16_t)(uint16_t)((res[e] + cur[e]) & 0xFFFF);
+        nxt[e] = (int16_t)q;
+        coef[e] = (float)q * (low ? qp.qpl_denorm : qp.qph);
+    }
 }
 
 // K-frame lowpass: undo the column first difference (running sum down each column)
-__global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* const* __restrict__ dst,
+__global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* dst0, int16_t* dst1,
                                    const PDesc* __restrict__ pd, int nplanes, const SDesc* __restrict__ sd,
                                    const SCall* __restrict__ sc, const SResult* __restrict__ rs,
                                    float* __restrict__ coef) {
@@ -188,7 +212,7 @@ __global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* con
         for (int r = 0; r < rows; r++) {
             const long long e = base + (long long)r * P.low_w;
             acc = (int16_t)(uint16_t)((acc + res[e]) & 0xFFFF);
-            dst[1 - C.dcur][e] = (int16_t)acc;
+            (C.dcur ? dst0 : dst1)[e] = (int16_t)acc;
             coef[e] = (float)acc * qp.qpl_denorm;
         }
         return;

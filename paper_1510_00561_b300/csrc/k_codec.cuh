@@ -92,16 +92,17 @@ struct CompTable {
     int ncomp;
 };
 
-constexpr int ELEM_BLOCK = 256;   // elements per block of the element-wise kernels
+// element-wise kernels: ELEM_THREADS threads, ELEM_PER_THREAD elements each
+constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS * ELEM_PER_THREAD;
 
 __global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes);
 __global__ void k_colour_inv_b(const SDesc* sd, const SCall* sc, const SResult* rs, const int* blk_stream,
                                const float* planes);
-__global__ void k_quant_b(const float* coef, int16_t* const* est, const PDesc* pd, const int* blk_plane,
+__global__ void k_quant_b(const float* coef, int16_t* est0, int16_t* est1, const PDesc* pd, const int* blk_plane,
                           const SDesc* sd, const SCall* sc, int16_t* res, SResult* out);
-__global__ void k_unquant_b(const int16_t* res, int16_t* const* dst, const PDesc* pd, const int* blk_plane,
+__global__ void k_unquant_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, const int* blk_plane,
                             const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
-__global__ void k_unquant_keylow_b(const int16_t* res, int16_t* const* dst, const PDesc* pd, int nplanes,
+__global__ void k_unquant_keylow_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, int nplanes,
                                    const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
 __global__ void k_rle_count_b(const int16_t* res, RowTable rt, const SCall* sc, uint32_t* cnt);
 __global__ void k_rle_write_b(const int16_t* res, RowTable rt, const SDesc* sd, const SCall* sc,
