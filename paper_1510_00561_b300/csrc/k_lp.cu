@@ -40,6 +40,15 @@ __device__ __forceinline__ int wrap_idx(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
+// 4-byte asynchronous global -> shared copies (all of a tile's staging in flight at once)
+__device__ __forceinline__ void lp_cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void lp_cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int RA>
 __device__ __forceinline__ float tap_a(int t) { return RA == 4 ? c_h[t + 4] : c_g[t + 3]; }
 template <int RS>
@@ -73,8 +82,9 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
         int r = i / MN, c = i - r * MN;
         int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
-        s_main[i] = mainp[(long long)y * mrs + x];
+        lp_cp_async4(&s_main[i], mainp + (long long)y * mrs + x);
     }
+    lp_cp_async_wait_all();
     __syncthreads();
     // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]
     for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
@@ -109,30 +119,41 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
             if (gm < Hh && gn < Wh) coutp[(long long)gm * J.cout.rs + gn] = s_v[(m - MLO) * VN + (n - MLO)];
         }
     }
-    // expanding row pass: s_a[m'][x'] = sum_t fs[t] [x'-t even] v[m'][(x'-t)/2 - MLO]
-    for (int i = threadIdx.x; i < VN * T; i += blockDim.x) {
-        int m = i / T, x = i - m * T;
-        float acc = 0.f;
+    // expanding row pass, by output pairs (x = 2p, 2p + 1):
+    //   s_a[m][x] = sum_{t : x - t even} fs[t] v[m][(x - t)/2 - MLO]
+    for (int i = threadIdx.x; i < VN * (T / 2); i += blockDim.x) {
+        const int m = i / (T / 2), p = i - m * (T / 2);
+        const float* vr = s_v + m * VN + p - MLO;
+        float ev = 0.f, od = 0.f;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
-            if (((x - t) & 1) == 0) acc = fmaf(tap_s<RS>(t), s_v[m * VN + ((x - t) >> 1) - MLO], acc);
+            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), vr[-(t / 2)], ev);               // x = 2p
+            else od = fmaf(tap_s<RS>(t), vr[(1 - t) / 2], od);                           // x = 2p + 1
         }
-        s_a[i] = acc;
+        s_a[m * T + 2 * p] = ev;
+        s_a[m * T + 2 * p + 1] = od;
     }
     __syncthreads();
-    // expanding column pass and the combination with the main input
+    // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main input
     float* outp = B.p[J.out.b] + J.out.off;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        int y = i / T, x = i - y * T;
-        float acc = 0.f;
+    for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
+        const int p = i / T, x = i - p * T;
+        const float* ar = s_a + (p - MLO) * T + x;
+        float ev = 0.f, od = 0.f;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
-            if (((y - t) & 1) == 0) acc = fmaf(tap_s<RS>(t), s_a[(((y - t) >> 1) - MLO) * T + x], acc);
+            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), ar[-(t / 2) * T], ev);
+            else od = fmaf(tap_s<RS>(t), ar[((1 - t) / 2) * T], od);
         }
-        int gy = y0 + y, gx = x0 + x;
-        if (gy < H && gx < W) {
-            float mv = s_main[(y - Y0) * MN + (x - Y0)];
-            outp[(long long)gy * J.out.rs + gx] = SYNTH ? mv + acc : mv - acc;
+        const int gx = x0 + x;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int y = 2 * p + h, gy = y0 + y;
+            if (gy < H && gx < W) {
+                const float acc = h ? od : ev;
+                const float mv = s_main[(y - Y0) * MN + (x - Y0)];
+                outp[(long long)gy * J.out.rs + gx] = SYNTH ? mv + acc : mv - acc;
+            }
         }
     }
 }
@@ -191,8 +212,9 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
         int r = i / MN, c = i - r * MN;
         int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
-        s_main[i] = mainp[(long long)y * mrs + x];
+        lp_cp_async4(&s_main[i], mainp + (long long)y * mrs + x);
     }
+    lp_cp_async_wait_all();
     __syncthreads();
     for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
         int r = i / VN, n = i - r * VN;
@@ -222,36 +244,53 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         s_vl[i] = el;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < VN * T; i += blockDim.x) {
-        int m = i / T, x = i - m * T;
-        float hi = 0.f, lo = 0.f;
+    // expanding row pass by output pairs (x = 2p, 2p + 1)
+    for (int i = threadIdx.x; i < VN * (T / 2); i += blockDim.x) {
+        const int m = i / (T / 2), p = i - m * (T / 2);
+        const int kb = m * VN + p - MLO;
+        float eh = 0.f, el = 0.f, oh = 0.f, ol = 0.f;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
-            if (((x - t) & 1) == 0) {
-                int k = m * VN + ((x - t) >> 1) - MLO;
-                ff_fma(hi, lo, tap_s<RS>(t), s_vh[k], s_vl[k]);
+            if ((t & 1) == 0) {
+                const int k = kb - t / 2;
+                ff_fma(eh, el, tap_s<RS>(t), s_vh[k], s_vl[k]);
+            } else {
+                const int k = kb + (1 - t) / 2;
+                ff_fma(oh, ol, tap_s<RS>(t), s_vh[k], s_vl[k]);
             }
         }
-        s_ah[i] = hi;
-        s_al[i] = lo;
+        s_ah[m * T + 2 * p] = eh;
+        s_al[m * T + 2 * p] = el;
+        s_ah[m * T + 2 * p + 1] = oh;
+        s_al[m * T + 2 * p + 1] = ol;
     }
     __syncthreads();
+    // expanding column pass by output pairs (y = 2p, 2p + 1), plus the main input
     float* outp = B.p[J.out.b] + J.out.off;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        int y = i / T, x = i - y * T;
-        float hi = 0.f, lo = 0.f;
+    for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
+        const int p = i / T, x = i - p * T;
+        const int kb = (p - MLO) * T + x;
+        float eh = 0.f, el = 0.f, oh = 0.f, ol = 0.f;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
-            if (((y - t) & 1) == 0) {
-                int k = (((y - t) >> 1) - MLO) * T + x;
-                ff_fma(hi, lo, tap_s<RS>(t), s_ah[k], s_al[k]);
+            if ((t & 1) == 0) {
+                const int k = kb - (t / 2) * T;
+                ff_fma(eh, el, tap_s<RS>(t), s_ah[k], s_al[k]);
+            } else {
+                const int k = kb + ((1 - t) / 2) * T;
+                ff_fma(oh, ol, tap_s<RS>(t), s_ah[k], s_al[k]);
             }
         }
-        int gy = y0 + y, gx = x0 + x;
-        if (gy < H && gx < W) {
-            float mv = s_main[(y - Y0) * MN + (x - Y0)];
-            ff_add(hi, lo, mv);
-            outp[(long long)gy * J.out.rs + gx] = __fadd_rn(hi, lo);
+        const int gx = x0 + x;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int y = 2 * p + h, gy = y0 + y;
+            if (gy < H && gx < W) {
+                float hi = h ? oh : eh, lo = h ? ol : el;
+                const float mv = s_main[(y - Y0) * MN + (x - Y0)];
+                ff_add(hi, lo, mv);
+                outp[(long long)gy * J.out.rs + gx] = __fadd_rn(hi, lo);
+            }
         }
     }
 }
