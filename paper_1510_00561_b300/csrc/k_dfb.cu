@@ -62,12 +62,12 @@ __host__ __device__ constexpr int pl1(int hi, int p) { return (hi - 1 - p) / 2 +
 //   Stage 2 (taps at (a, b) in both families): row sums along the target's
 //     source plane, then sums down its columns.
 // A pass over image-local [lo, hi)^2, lo = 3n, reads the region the previous
-// pass left valid, [lo - 3, hi + 3)^2.  Warps take plane rows, lanes columns.
+// pass left valid, [lo - 3, hi + 3)^2.  Consecutive threads take consecutive
+// elements of a region row.
 
 template <int N, bool ODD>
 __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alpha, float gamma) {
     constexpr int lo = 3 * N, hi = SA - 3 * N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones; D of class
     // (sr, sc) goes to tmp plane sr
 #pragma unroll
@@ -84,17 +84,13 @@ __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alp
             dv[m] = fdiv2(sc - m);
         }
         float* D = tmp + sr * PA * PAS;
-        for (int u = u0 + warp; u < u1; u += 8) {
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const int v = v0 + lane + 32 * j;
-                if (v < v1) {
-                    float acc = BT0 * Pm[0][(u + du[0]) * PAS + v + dv[0]];
-                    acc = fmaf(BT1, Pm[1][(u + du[1]) * PAS + v + dv[1]], acc);
-                    acc = fmaf(BT2, Pm[2][(u + du[2]) * PAS + v + dv[2]], acc);
-                    D[u * PAS + v] = fmaf(BT3, Pm[3][(u + du[3]) * PAS + v + dv[3]], acc);
-                }
-            }
+        const int nv = v1 - v0;
+        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
+            const int u = u0 + idx / nv, v = v0 + idx % nv;
+            float acc = BT0 * Pm[0][(u + du[0]) * PAS + v + dv[0]];
+            acc = fmaf(BT1, Pm[1][(u + du[1]) * PAS + v + dv[1]], acc);
+            acc = fmaf(BT2, Pm[2][(u + du[2]) * PAS + v + dv[2]], acc);
+            D[u * PAS + v] = fmaf(BT3, Pm[3][(u + du[3]) * PAS + v + dv[3]], acc);
         }
     }
     __syncthreads();
@@ -112,18 +108,14 @@ __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alp
             du[n] = fdiv2(tr + n - 3);
             dv[n] = fdiv2(tc + n);
         }
-        for (int u = u0 + warp; u < u1; u += 8) {
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const int v = v0 + lane + 32 * j;
-                if (v < v1) {
-                    float acc = BT0 * Dn[0][(u + du[0]) * PAS + v + dv[0]];
-                    acc = fmaf(BT1, Dn[1][(u + du[1]) * PAS + v + dv[1]], acc);
-                    acc = fmaf(BT2, Dn[2][(u + du[2]) * PAS + v + dv[2]], acc);
-                    acc = fmaf(BT3, Dn[3][(u + du[3]) * PAS + v + dv[3]], acc);
-                    T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
-                }
-            }
+        const int nv = v1 - v0;
+        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
+            const int u = u0 + idx / nv, v = v0 + idx % nv;
+            float acc = BT0 * Dn[0][(u + du[0]) * PAS + v + dv[0]];
+            acc = fmaf(BT1, Dn[1][(u + du[1]) * PAS + v + dv[1]], acc);
+            acc = fmaf(BT2, Dn[2][(u + du[2]) * PAS + v + dv[2]], acc);
+            acc = fmaf(BT3, Dn[3][(u + du[3]) * PAS + v + dv[3]], acc);
+            T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
         }
     }
     __syncthreads();
@@ -132,7 +124,6 @@ __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alp
 template <int N, bool ODD>
 __device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alpha, float gamma) {
     constexpr int lo = 3 * N, hi = SA - 3 * N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // targets: {11, 01} (odd) or {00, 10}; target (tr, tc) reads class (1-tr, 1-tc)
     // at plane (u + ky + tr - 2, v + kx + tc - 2); row sums go to tmp plane tr
 #pragma unroll
@@ -141,18 +132,14 @@ __device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alp
         const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
         const float* Sp = planes + (2 * (1 - tr) + (1 - tc)) * PA * PAS + (tc - 2);
         float* Rs = tmp + tr * PA * PAS;
-        for (int u = u0 + tr - 2 + warp; u < u1 + tr + 1; u += 8) {
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const int v = v0 + lane + 32 * j;
-                if (v < v1) {
-                    const float* src = Sp + u * PAS + v;
-                    float acc = BT0 * src[0];
-                    acc = fmaf(BT1, src[1], acc);
-                    acc = fmaf(BT2, src[2], acc);
-                    Rs[u * PAS + v] = fmaf(BT3, src[3], acc);
-                }
-            }
+        const int nv = v1 - v0, ur0 = u0 + tr - 2;
+        for (int idx = threadIdx.x; idx < (u1 - u0 + 3) * nv; idx += blockDim.x) {
+            const int u = ur0 + idx / nv, v = v0 + idx % nv;
+            const float* src = Sp + u * PAS + v;
+            float acc = BT0 * src[0];
+            acc = fmaf(BT1, src[1], acc);
+            acc = fmaf(BT2, src[2], acc);
+            Rs[u * PAS + v] = fmaf(BT3, src[3], acc);
         }
     }
     __syncthreads();
@@ -162,19 +149,15 @@ __device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alp
         const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
         float* T = planes + (2 * tr + tc) * PA * PAS;
         const float* Rs = tmp + tr * PA * PAS + (tr - 2) * PAS;
-        for (int u = u0 + warp; u < u1; u += 8) {
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const int v = v0 + lane + 32 * j;
-                if (v < v1) {
-                    const float* h = Rs + u * PAS + v;
-                    float acc = BT0 * h[0];
-                    acc = fmaf(BT1, h[PAS], acc);
-                    acc = fmaf(BT2, h[2 * PAS], acc);
-                    acc = fmaf(BT3, h[3 * PAS], acc);
-                    T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
-                }
-            }
+        const int nv = v1 - v0;
+        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
+            const int u = u0 + idx / nv, v = v0 + idx % nv;
+            const float* h = Rs + u * PAS + v;
+            float acc = BT0 * h[0];
+            acc = fmaf(BT1, h[PAS], acc);
+            acc = fmaf(BT2, h[2 * PAS], acc);
+            acc = fmaf(BT3, h[3 * PAS], acc);
+            T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
         }
     }
     __syncthreads();
