@@ -65,101 +65,114 @@ __host__ __device__ constexpr int pl1(int hi, int p) { return (hi - 1 - p) / 2 +
 // pass left valid, [lo - 3, hi + 3)^2.  Consecutive threads take consecutive
 // elements of a region row.
 
+// element offset of plane class (r, c) at plane-local (u, v)
+__host__ __device__ constexpr int pofs(int r, int c, int u, int v) { return (2 * r + c) * PA * PAS + u * PAS + v; }
+
+// Visit every (u, v) of [U0, U1) x [V0, V1) with the element offset u*PAS + v:
+// thread t owns column V0 + t % NV and walks down rows U0 + t / NV, stepping
+// by the number of row chunks, so an access is one running offset plus a
+// compile-time displacement.
+template <int U0, int U1, int V0, int V1, class F>
+__device__ __forceinline__ void region_walk(F&& f) {
+    constexpr int NV = V1 - V0, CH = 256 / NV;
+    static_assert(NV >= 1 && NV <= 256 && U1 > U0, "region");
+    const int t = threadIdx.x;
+    if (t >= CH * NV) return;
+    const int v = V0 + t % NV;
+    int off = (U0 + t / NV) * PAS + v;
+    for (int u = U0 + t / NV; u < U1; u += CH, off += CH * PAS) f(off);
+}
+
+// stage 1, source class (sr, sc): D[p] = sum_m betat[m] x[p + (m, -m)] over image rows
+// [lo-3, hi) and columns [lo, hi+3) of the class, into tmp plane sr
+template <int N, bool ODD, int K>
+__device__ __forceinline__ void s1_dsum(const float* planes, float* tmp) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    constexpr int sr = K, sc = ODD ? K : 1 - K;
+    constexpr int o0 = pofs((sr + 0) & 1, (sc - 0) & 1, fdiv2(sr + 0), fdiv2(sc - 0));
+    constexpr int o1 = pofs((sr + 1) & 1, (sc - 1) & 1, fdiv2(sr + 1), fdiv2(sc - 1));
+    constexpr int o2 = pofs((sr + 2) & 1, (sc - 2) & 1, fdiv2(sr + 2), fdiv2(sc - 2));
+    constexpr int o3 = pofs((sr + 3) & 1, (sc - 3) & 1, fdiv2(sr + 3), fdiv2(sc - 3));
+    float* D = tmp + sr * PA * PAS;
+    region_walk<pl0(lo - 3, sr), pl1(hi, sr), pl0(lo, sc), pl1(hi + 3, sc)>([&](int off) {
+        float acc = BT0 * planes[off + o0];
+        acc = fmaf(BT1, planes[off + o1], acc);
+        acc = fmaf(BT2, planes[off + o2], acc);
+        D[off] = fmaf(BT3, planes[off + o3], acc);
+    });
+}
+
+// stage 1, target class (tr, tc): acc(t) = sum_n betat[n] D[t + (n - 3, n)]
+template <int N, bool ODD, int K>
+__device__ __forceinline__ void s1_target(float* planes, const float* tmp, float alpha, float gamma) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    constexpr int tr = K, tc = ODD ? 1 - K : K;
+    constexpr int o0 = ((tr + 1) & 1) * PA * PAS + fdiv2(tr - 3) * PAS + fdiv2(tc + 0);
+    constexpr int o1 = ((tr + 2) & 1) * PA * PAS + fdiv2(tr - 2) * PAS + fdiv2(tc + 1);
+    constexpr int o2 = ((tr + 3) & 1) * PA * PAS + fdiv2(tr - 1) * PAS + fdiv2(tc + 2);
+    constexpr int o3 = ((tr + 4) & 1) * PA * PAS + fdiv2(tr + 0) * PAS + fdiv2(tc + 3);
+    float* T = planes + (2 * tr + tc) * PA * PAS;
+    region_walk<pl0(lo, tr), pl1(hi, tr), pl0(lo, tc), pl1(hi, tc)>([&](int off) {
+        float acc = BT0 * tmp[off + o0];
+        acc = fmaf(BT1, tmp[off + o1], acc);
+        acc = fmaf(BT2, tmp[off + o2], acc);
+        acc = fmaf(BT3, tmp[off + o3], acc);
+        T[off] = fmaf(alpha, T[off], gamma * acc);
+    });
+}
+
+// stage 2, target class (tr, tc) reads class (1-tr, 1-tc) at (u + ky + tr - 2, v + kx + tc - 2):
+// row sums into tmp plane tr, then sums down the columns
+template <int N, bool ODD, int K>
+__device__ __forceinline__ void s2_rowsum(const float* planes, float* tmp) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    constexpr int tr = K, tc = ODD ? 1 : 0;
+    constexpr int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
+    constexpr int os = (2 * (1 - tr) + (1 - tc)) * PA * PAS + (tc - 2);
+    float* Rs = tmp + tr * PA * PAS;
+    region_walk<u0 + tr - 2, u1 + tr + 1, v0, v1>([&](int off) {
+        float acc = BT0 * planes[off + os];
+        acc = fmaf(BT1, planes[off + os + 1], acc);
+        acc = fmaf(BT2, planes[off + os + 2], acc);
+        Rs[off] = fmaf(BT3, planes[off + os + 3], acc);
+    });
+}
+
+template <int N, bool ODD, int K>
+__device__ __forceinline__ void s2_target(float* planes, const float* tmp, float alpha, float gamma) {
+    constexpr int lo = 3 * N, hi = SA - 3 * N;
+    constexpr int tr = K, tc = ODD ? 1 : 0;
+    constexpr int oh = tr * PA * PAS + (tr - 2) * PAS;
+    float* T = planes + (2 * tr + tc) * PA * PAS;
+    region_walk<pl0(lo, tr), pl1(hi, tr), pl0(lo, tc), pl1(hi, tc)>([&](int off) {
+        float acc = BT0 * tmp[off + oh];
+        acc = fmaf(BT1, tmp[off + oh + PAS], acc);
+        acc = fmaf(BT2, tmp[off + oh + 2 * PAS], acc);
+        acc = fmaf(BT3, tmp[off + oh + 3 * PAS], acc);
+        T[off] = fmaf(alpha, T[off], gamma * acc);
+    });
+}
+
 template <int N, bool ODD>
 __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alpha, float gamma) {
-    constexpr int lo = 3 * N, hi = SA - 3 * N;
-    // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones; D of class
-    // (sr, sc) goes to tmp plane sr
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int sr = k, sc = ODD ? k : 1 - k;
-        // D at image rows [lo-3, hi), columns [lo, hi+3)
-        const int u0 = pl0(lo - 3, sr), u1 = pl1(hi, sr), v0 = pl0(lo, sc), v1 = pl1(hi + 3, sc);
-        const float* Pm[4];
-        int du[4], dv[4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            Pm[m] = planes + (2 * ((sr + m) & 1) + ((sc - m) & 1)) * PA * PAS;
-            du[m] = fdiv2(sr + m);
-            dv[m] = fdiv2(sc - m);
-        }
-        float* D = tmp + sr * PA * PAS;
-        const int nv = v1 - v0;
-        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
-            const int u = u0 + idx / nv, v = v0 + idx % nv;
-            float acc = BT0 * Pm[0][(u + du[0]) * PAS + v + dv[0]];
-            acc = fmaf(BT1, Pm[1][(u + du[1]) * PAS + v + dv[1]], acc);
-            acc = fmaf(BT2, Pm[2][(u + du[2]) * PAS + v + dv[2]], acc);
-            D[u * PAS + v] = fmaf(BT3, Pm[3][(u + du[3]) * PAS + v + dv[3]], acc);
-        }
-    }
+    // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones
+    s1_dsum<N, ODD, 0>(planes, tmp);
+    s1_dsum<N, ODD, 1>(planes, tmp);
     __syncthreads();
     // targets: {01, 10} (odd) or {00, 11}
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int tr = k, tc = ODD ? 1 - k : k;
-        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
-        float* T = planes + (2 * tr + tc) * PA * PAS;
-        const float* Dn[4];
-        int du[4], dv[4];
-#pragma unroll
-        for (int n = 0; n < 4; n++) {
-            Dn[n] = tmp + ((tr + n + 1) & 1) * PA * PAS;
-            du[n] = fdiv2(tr + n - 3);
-            dv[n] = fdiv2(tc + n);
-        }
-        const int nv = v1 - v0;
-        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
-            const int u = u0 + idx / nv, v = v0 + idx % nv;
-            float acc = BT0 * Dn[0][(u + du[0]) * PAS + v + dv[0]];
-            acc = fmaf(BT1, Dn[1][(u + du[1]) * PAS + v + dv[1]], acc);
-            acc = fmaf(BT2, Dn[2][(u + du[2]) * PAS + v + dv[2]], acc);
-            acc = fmaf(BT3, Dn[3][(u + du[3]) * PAS + v + dv[3]], acc);
-            T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
-        }
-    }
+    s1_target<N, ODD, 0>(planes, tmp, alpha, gamma);
+    s1_target<N, ODD, 1>(planes, tmp, alpha, gamma);
     __syncthreads();
 }
 
 template <int N, bool ODD>
 __device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alpha, float gamma) {
-    constexpr int lo = 3 * N, hi = SA - 3 * N;
-    // targets: {11, 01} (odd) or {00, 10}; target (tr, tc) reads class (1-tr, 1-tc)
-    // at plane (u + ky + tr - 2, v + kx + tc - 2); row sums go to tmp plane tr
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int tr = k, tc = ODD ? 1 : 0;
-        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
-        const float* Sp = planes + (2 * (1 - tr) + (1 - tc)) * PA * PAS + (tc - 2);
-        float* Rs = tmp + tr * PA * PAS;
-        const int nv = v1 - v0, ur0 = u0 + tr - 2;
-        for (int idx = threadIdx.x; idx < (u1 - u0 + 3) * nv; idx += blockDim.x) {
-            const int u = ur0 + idx / nv, v = v0 + idx % nv;
-            const float* src = Sp + u * PAS + v;
-            float acc = BT0 * src[0];
-            acc = fmaf(BT1, src[1], acc);
-            acc = fmaf(BT2, src[2], acc);
-            Rs[u * PAS + v] = fmaf(BT3, src[3], acc);
-        }
-    }
+    // targets: {11, 01} (odd) or {00, 10}
+    s2_rowsum<N, ODD, 0>(planes, tmp);
+    s2_rowsum<N, ODD, 1>(planes, tmp);
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int tr = k, tc = ODD ? 1 : 0;
-        const int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
-        float* T = planes + (2 * tr + tc) * PA * PAS;
-        const float* Rs = tmp + tr * PA * PAS + (tr - 2) * PAS;
-        const int nv = v1 - v0;
-        for (int idx = threadIdx.x; idx < (u1 - u0) * nv; idx += blockDim.x) {
-            const int u = u0 + idx / nv, v = v0 + idx % nv;
-            const float* h = Rs + u * PAS + v;
-            float acc = BT0 * h[0];
-            acc = fmaf(BT1, h[PAS], acc);
-            acc = fmaf(BT2, h[2 * PAS], acc);
-            acc = fmaf(BT3, h[3 * PAS], acc);
-            T[u * PAS + v] = fmaf(alpha, T[u * PAS + v], gamma * acc);
-        }
-    }
+    s2_target<N, ODD, 0>(planes, tmp, alpha, gamma);
+    s2_target<N, ODD, 1>(planes, tmp, alpha, gamma);
     __syncthreads();
 }
 
