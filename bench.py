@@ -129,8 +129,12 @@ def stage_bytes(info, tokens):
     for (h, w) in P:
         for j in range(1, LEVELS + 1):
             pj = (h >> (j - 1)) * (w >> (j - 1))
+            k = DIRS[j - 1]
             lp += 4 * (pj + pj // 4 + pj)               # read level input, write lowpass + detail
-            dfb += DIRS[j - 1] * 2 * 4 * (3 * pj // 2)  # per stage: two passes, each reads 2 and writes 1 coset
+            # DFB launches touching level j: one for stages 1-2 (fused), one per stage >= 3;
+            # each reads and writes every sample of the level once
+            launches = 0 if k == 0 else 1 + max(0, k - 2)
+            dfb += launches * 8 * pj
     nplane = Hp * Wp + 2 * Hcp * Wcp
     return {
         "colour_fwd": 3 * N + 4 * nplane,
@@ -267,7 +271,7 @@ def run_reference(args, rank):
     steps, warm = args.steps, args.warmup
     # size the band so that the whole run takes about two minutes (one 1080p frame ~ 6 s)
     per_step = min(6.5, 120.0 / max(1, steps + warm))
-    band = max(64, min(1088, int(per_step / 6.5 * 1088) // 64 * 64))
+    band = max(64, min(H_, int(per_step / 6.5 * H_) // 64 * 64))   # rows of the frame actually coded
     frames = _gen_frames(0, min(steps + warm, 12))
     import numpy as np
     import oracle as O
