@@ -34,6 +34,12 @@ W_, H_, LEVELS, DIRS, QPH, QPL, KINT = 1920, 1080, 5, [5, 4, 4, 3, 3], 8, 1, 10
 METRIC = "1080p encode+decode frames/s"
 UNIT = "frames/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes per 1080p frame of the transform stages (dram__bytes_read.sum +
+# dram__bytes_write.sum over the stage's launches), from one ncu capture of a
+# batched step of 8 streams (profiles/dfb_lp_traffic_batched_1080p.md); set to
+# None when those kernels change
+DRAM_PER_FRAME = {"lp_analysis": 28.1e6, "dfb_analysis": 106.9e6, "dfb_synthesis": 107.2e6,
+                  "lp_synthesis": 29.4e6}
 
 
 def _gen_frames(seed, n, start=0):
@@ -492,8 +498,11 @@ def main():
     per_launch_ms = ms_dom / max(1, n_dom)
     bytes_per_launch = sb[dom] * frames_staged / max(1, n_dom)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    if dom in DRAM_PER_FRAME:
+        traffic = DRAM_PER_FRAME[dom] * frames_staged / max(1, n_dom)
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": dom,
             "peak_source": pk["source"], "launches": n_dom,
             "stages_ms_per_frame": {k: v[0] / frames_staged for k, v in stage.items()}}
 
