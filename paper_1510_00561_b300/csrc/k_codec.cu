@@ -241,10 +241,13 @@ __global__ void k_rle_count_b(const int16_t* __restrict__ res, RowTable rt, cons
     }
     uint32_t n = 0;
     bool prev_zero = false;
+    int16_t vn = lane < w ? res[off + lane] : (int16_t)1;     // the next chunk, loaded one chunk ahead
     for (int x0 = 0; x0 < w; x0 += 32) {
         int x = x0 + lane;
         bool valid = x < w;
-        bool z = valid && res[off + x] == 0;
+        const int16_t v = vn;
+        if (x + 32 < w) vn = res[off + x + 32];
+        bool z = valid && v == 0;
         unsigned zb = __ballot_sync(0xffffffffu, z);
         unsigned vb = __ballot_sync(0xffffffffu, valid);
         unsigned starts = zb & ~((zb << 1) | (prev_zero ? 1u : 0u));
@@ -284,10 +287,12 @@ __global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, cons
     bool prev_zero = false;
     uint32_t open_pos = 0;   // token position of the marker of a run left open by the previous chunk
     int open_x = 0;
+    int16_t vn = lane < w ? res[off + lane] : (int16_t)1;     // the next chunk, loaded one chunk ahead
     for (int x0 = 0; x0 < w; x0 += 32) {
         int x = x0 + lane;
         bool valid = x < w;
-        int16_t v = valid ? res[off + x] : (int16_t)1;
+        const int16_t v = valid ? vn : (int16_t)1;
+        if (x + 32 < w) vn = res[off + x + 32];
         bool z = valid && v == 0;
         unsigned zb = __ballot_sync(0xffffffffu, z);
         unsigned vb = __ballot_sync(0xffffffffu, valid);
@@ -484,27 +489,54 @@ __device__ __forceinline__ TokCtx tok_ctx(uint32_t g, const SDesc* sd, const SRe
 }
 
 // elements produced by each token: value (and raw K-lowpass) tokens 1,
-// zero markers 0, run counts n
+// zero markers 0, run counts n.  A thread takes TOK_GROUP consecutive tokens:
+// one search for the first token's stream and component, then a forward walk.
+constexpr int TOK_GROUP = 8;
+
+__device__ __forceinline__ void tok_advance(TokCtx& k, uint32_t g, const SDesc* sd, const SResult* rs,
+                                            const uint32_t* tok_base, int nstreams, const uint32_t* comp_tok) {
+    // move k (valid for some g' < g) forward to token g
+    while (k.s + 1 < nstreams && g >= tok_base[k.s + 1]) {
+        k.s++;
+        k.c = sd[k.s].comp0;
+        k.c0 = comp_tok[k.c];
+        const SDesc& D = sd[k.s];
+        k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
+    }
+    k.t = g - tok_base[k.s];
+    const SDesc& D = sd[k.s];
+    while (k.t >= k.c1 && k.c + 1 < D.comp0 + D.ncomp) {
+        k.c++;
+        k.c0 = k.c1;
+        k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
+    }
+}
+
 __global__ void k_dec_contrib_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                 const SResult* __restrict__ rs, const uint32_t* __restrict__ tok_base, int nstreams,
                                 const uint32_t* __restrict__ comp_tok, CompTable ct, uint32_t* __restrict__ contrib,
                                 SResult* out) {
     const uint32_t total = tok_base[nstreams];
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const TokCtx k = tok_ctx(g, sd, rs, tok_base, nstreams, comp_tok);
-        const uint8_t* tok = sc[k.s].in + sd[k.s].hdr_bytes;
-        const int16_t v = rd16(tok + 2LL * k.t);
-        uint32_t n;
-        if (rs[k.s].dec_type == 0 && ct.low[k.c]) n = 1;
-        else if (k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0) {
-            n = v > 0 ? (uint32_t)v : 0;
-            if (v <= 0) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
-        } else if (v != 0) n = 1;
-        else {
-            n = 0;
-            if (k.t + 1 >= k.c1) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
+    const uint32_t stride = gridDim.x * blockDim.x * TOK_GROUP;
+    for (uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) * TOK_GROUP; g0 < total; g0 += stride) {
+        TokCtx k = tok_ctx(g0, sd, rs, tok_base, nstreams, comp_tok);
+        const uint32_t g1 = min(total, g0 + TOK_GROUP);
+        for (uint32_t g = g0; g < g1; g++) {
+            if (g > g0) tok_advance(k, g, sd, rs, tok_base, nstreams, comp_tok);
+            const uint8_t* tok = sc[k.s].in + sd[k.s].hdr_bytes;
+            const int16_t v = rd16(tok + 2LL * k.t);
+            uint32_t n;
+            if (rs[k.s].dec_type == 0 && ct.low[k.c]) n = 1;
+            else if (k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0) {
+                n = v > 0 ? (uint32_t)v : 0;
+                if (v <= 0) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
+            } else if (v != 0) n = 1;
+            else {
+                n = 0;
+                if (k.t + 1 >= k.c1) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
+            }
+            contrib[g] = n;
         }
-        contrib[g] = n;
     }
 }
 
@@ -529,15 +561,20 @@ __global__ void k_dec_scatter_b(const SDesc* __restrict__ sd, const SCall* __res
                                 const uint32_t* __restrict__ comp_tok, CompTable ct, const uint32_t* __restrict__ pos,
                                 int16_t* __restrict__ res) {
     const uint32_t total = tok_base[nstreams];
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const TokCtx k = tok_ctx(g, sd, rs, tok_base, nstreams, comp_tok);
-        const SDesc& D = sd[k.s];
-        const uint8_t* tok = sc[k.s].in + D.hdr_bytes;
-        const int16_t v = rd16(tok + 2LL * k.t);
-        const bool raw = rs[k.s].dec_type == 0 && ct.low[k.c];
-        const bool count = !raw && k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0;
-        const long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
-        if ((raw || (v != 0 && !count)) && p >= 0 && p < D.ncoef) res[D.coef_off + p] = v;
+    const uint32_t stride = gridDim.x * blockDim.x * TOK_GROUP;
+    for (uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) * TOK_GROUP; g0 < total; g0 += stride) {
+        TokCtx k = tok_ctx(g0, sd, rs, tok_base, nstreams, comp_tok);
+        const uint32_t g1 = min(total, g0 + TOK_GROUP);
+        for (uint32_t g = g0; g < g1; g++) {
+            if (g > g0) tok_advance(k, g, sd, rs, tok_base, nstreams, comp_tok);
+            const SDesc& D = sd[k.s];
+            const uint8_t* tok = sc[k.s].in + D.hdr_bytes;
+            const int16_t v = rd16(tok + 2LL * k.t);
+            const bool raw = rs[k.s].dec_type == 0 && ct.low[k.c];
+            const bool count = !raw && k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0;
+            const long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
+            if ((raw || (v != 0 && !count)) && p >= 0 && p < D.ncoef) res[D.coef_off + p] = v;
+        }
     }
 }
 
