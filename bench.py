@@ -64,6 +64,21 @@ def make_frames(seed, n):
         return list(ex.map(_gen_one, [(seed, t) for t in range(n)]))
 
 
+def combine_ranks(local_ms, local_units, dist=None, device=None):
+    """Whole-job throughput of independent replicas: units summed over ranks,
+    divided by the slowest rank's time (max over ranks).  Returns
+    (value per second, max ms, total units).  No data moves between ranks
+    besides these two numbers."""
+    import torch
+    ms = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    units = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    max_ms, total = float(ms.item()), float(units.item())
+    return total / (max_ms / 1e3), max_ms, total
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -349,14 +364,8 @@ def main():
     stream = torch.cuda.current_stream()
     F = len(d_frames)
 
-    def max_over_ranks(ms):
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed(step, steps, flush_between=True):
-        """CUDA-event time (ms, max over ranks) of `steps` steps, L2 flushed before each."""
+        """CUDA-event time (ms, this rank) of `steps` steps, L2 flushed before each."""
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         barrier()
@@ -369,7 +378,7 @@ def main():
             ends[i].record(stream)
         torch.cuda.synchronize()
         barrier()
-        return max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
     # ---------------------------------------------------------------- plain
     plain_bytes = [0]
@@ -381,8 +390,8 @@ def main():
 
     for i in range(args.warmup):
         plain_step(i)
-    plain_ms = timed(lambda i: plain_step(args.warmup + i), args.steps)
-    plain_value = args.steps * world / (plain_ms / 1e3)
+    plain_value, plain_ms, _ = combine_ranks(timed(lambda i: plain_step(args.warmup + i), args.steps), args.steps,
+                                             dist, dev)
 
     # plain end to end through the C ABI with host buffers (pinned), per step:
     # H2D frame, encode, D2H bitstream, H2D bitstream, decode, D2H frame
@@ -405,9 +414,9 @@ def main():
         io_bytes[0] += d_in.numel() + n
         io_bytes[1] += n + rgb.numel()
 
-    plain_e2e_ms = timed(plain_e2e_step, e2e_steps, flush_between=False)
+    plain_e2e_value = combine_ranks(timed(plain_e2e_step, e2e_steps, flush_between=False), e2e_steps, dist, dev)[0]
     plain = {"value": plain_value, "ms_per_step": plain_ms / args.steps, "streams_per_gpu": 1,
-             "e2e": {"value": e2e_steps * world / (plain_e2e_ms / 1e3), "unit": UNIT,
+             "e2e": {"value": plain_e2e_value, "unit": UNIT,
                      "h2d_bytes_per_step": io_bytes[0] // e2e_steps, "d2h_bytes_per_step": io_bytes[1] // e2e_steps}}
     del codec
 
@@ -436,11 +445,11 @@ def main():
         clocks.start()
     launches0 = kernel_launches()
     t_wall = time.perf_counter()
-    tot_ms = timed(lambda i: batch_step(args.warmup + i), args.steps)
+    value, tot_ms, _ = combine_ranks(timed(lambda i: batch_step(args.warmup + i), args.steps), args.steps * B,
+                                     dist, dev)
     t_wall = time.perf_counter() - t_wall
     launches = kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
-    value = args.steps * B * world / (tot_ms / 1e3)
 
     # stage breakdown of the same steps as direct launches bracketed by CUDA events
     batch.set_timing(True)
@@ -467,8 +476,7 @@ def main():
             io_bytes[0] += d_ins[j].numel()
             io_bytes[1] += n + outs_rgb[j].numel()
 
-    e2e_ms = timed(batch_e2e_step, e2e_steps, flush_between=False)
-    e2e_value = e2e_steps * B * world / (e2e_ms / 1e3)
+    e2e_value = combine_ranks(timed(batch_e2e_step, e2e_steps, flush_between=False), e2e_steps * B, dist, dev)[0]
     del batch, outs_rgb, d_ins
 
     # served form: continuous batching of concurrent streams under a memory budget

@@ -309,9 +309,11 @@ __global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, cons
         int sx = sl < 0 ? open_x : x0 + sl;
         if (sl < 0) spos = open_pos;
         // this lane ends its run if it is zero and the next element is not (or the row ends)
+        // the element after lane 31 is the first of the next chunk (lane 0's prefetched value)
+        const int16_t after = __shfl_sync(0xffffffffu, vn, 0);
         bool next_zero;
         if (lane < 31) next_zero = (zb >> (lane + 1)) & 1u;
-        else next_zero = (x + 1 < w) && res[off + x + 1] == 0;
+        else next_zero = (x + 1 < w) && after == 0;
         if (z && !next_zero) put_tok(tok, spos + 1, cap_tok, (int16_t)(x - sx + 1), err);
         uint32_t spos31 = __shfl_sync(0xffffffffu, spos, 31);
         int sx31 = __shfl_sync(0xffffffffu, sx, 31);
