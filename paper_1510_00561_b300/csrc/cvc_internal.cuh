@@ -70,7 +70,7 @@ struct DfbBJob {
 };
 
 constexpr int DFBA_TILE = 64, DFBA_HALO = 12;
-constexpr int DFBB_ROWS = 16, DFBB_COLS = 128;
+constexpr int DFBB_ROWS = 16, DFBB_COLS = 116;
 
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)

@@ -264,52 +264,64 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 }
 
 // ============================================================ k_dfb_b
-constexpr int RB = DFBB_ROWS + 6, CB = DFBB_COLS + 12;
+// Tile frame: RB = 16 + 6 rows (3-row halo) by CB = 116 + 12 columns (6-column
+// halo), rows stored with stride CBS = CB + 4.  The coset updated first (F)
+// and the second pass's row sums are stored one float to the right of their
+// array base, so that every column-pair window below is 8-byte aligned.  A
+// thread owns one column pair and one of four interleaved row chunks and walks
+// its rows with constant pointer steps; pairs of lanes compute with paired
+// FP32 instructions, rounding each lane exactly as the scalar sequence would.
+constexpr int RB = DFBB_ROWS + 6, CB = DFBB_COLS + 12, CBS = CB + 4;
+constexpr int NPAIR = 64, NCHUNK = 4;   // 256 threads
+constexpr int SMB = RB * CBS + 2;       // floats per tile array (room for the shift)
+static_assert(CB / 2 <= NPAIR, "one column pair per thread");
 
-// separable 4 x 4 pass in the sheared frame: target rows [R0, R1) x cols [X0, X1)
-// of array T, sources in array S (rows r + (a + dr)/2 with dr = +1 for odd
-// targets, -1 for even ones; columns x + (b - a)/2).  Warps take rows, lanes
-// take columns (five 32-column groups cover the 140-column frame).
-template <int R0, int R1, int X0, int X1, bool ODD>
-__device__ __forceinline__ void dfbb_pass(float* T, const float* S, float* Hs, float alpha, float gamma) {
-    constexpr int SR0 = R0 + (ODD ? -1 : -2), SR1 = R1 + (ODD ? 2 : 1);
-    constexpr int HX0 = X0 - 3;
-    static_assert(SR0 >= 0 && SR1 <= RB && HX0 >= 0 && X1 + 3 <= CB, "pass window outside the tile");
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // row sums h[rr][x'] = sum_b betat[b] * S[rr][x' + (b+3)/2]
-    for (int rr = SR0 + warp; rr < SR1; rr += 8) {
-        const float* src = S + rr * CB;
-        float* dst = Hs + rr * CB;
-#pragma unroll
-        for (int j = 0; j < (X1 - HX0 + 31) / 32; j++) {
-            const int xx = HX0 + lane + 32 * j;
-            if (xx < X1) {
-                float acc = BT0 * src[xx];
-                acc = fmaf(BT1, src[xx + 1], acc);
-                acc = fmaf(BT2, src[xx + 2], acc);
-                dst[xx] = fmaf(BT3, src[xx + 3], acc);
-            }
-        }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// row sums h[rr][x] = sum_b betat[b] S[rr][x + b], rows [SR0, SR1), pairs x = X0 + 2p, p < NP
+template <int SR0, int SR1, int X0, int NP>
+__device__ __forceinline__ void rowsum_pairs(const float* S, float* H) {
+    static_assert(SR0 >= 0 && SR1 <= RB && X0 >= 0 && X0 + 2 * NP + 3 <= CBS, "row-sum window");
+    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
+    if (p >= NP) return;
+    const float* s = S + (SR0 + c) * CBS + X0 + 2 * p;
+    float* h = H + (SR0 + c) * CBS + X0 + 2 * p;
+    for (int rr = SR0 + c; rr < SR1; rr += NCHUNK, s += NCHUNK * CBS, h += NCHUNK * CBS) {
+        const float2 a = *reinterpret_cast<const float2*>(s);
+        const float2 b = *reinterpret_cast<const float2*>(s + 2);
+        const float e = s[4];
+        float2 acc = __fmul2_rn(f2(BT0, BT0), a);
+        acc = __ffma2_rn(f2(BT1, BT1), f2(a.y, b.x), acc);
+        acc = __ffma2_rn(f2(BT2, BT2), b, acc);
+        acc = __ffma2_rn(f2(BT3, BT3), f2(b.y, e), acc);
+        *reinterpret_cast<float2*>(h) = acc;
     }
-    __syncthreads();
-    // tap a (ia = 0..3, a = 2ia - 3): row r + (a + (odd ? 1 : -1))/2 = rb + ia, column x - (a+3)/2 = x - ia
+}
+
+// targets t[r][x] = alpha t + gamma sum_ia betat[ia] h[r + DB + ia][x - ia], rows [R0, R1),
+// pairs x = X0 + 2p, p < NP.  The layout makes the ia-odd pairs 8-byte aligned.
+template <int R0, int R1, int X0, int NP, bool ODD>
+__device__ __forceinline__ void target_pairs(float* T, const float* H, float alpha, float gamma) {
     constexpr int DB = ODD ? -1 : -2;
-    for (int r = R0 + warp; r < R1; r += 8) {
-        const float* h = Hs + (r + DB) * CB;
-        float* t = T + r * CB;
-#pragma unroll
-        for (int j = 0; j < (X1 - X0 + 31) / 32; j++) {
-            const int x = X0 + lane + 32 * j;
-            if (x < X1) {
-                float acc = BT0 * h[x];
-                acc = fmaf(BT1, h[CB + x - 1], acc);
-                acc = fmaf(BT2, h[2 * CB + x - 2], acc);
-                acc = fmaf(BT3, h[3 * CB + x - 3], acc);
-                t[x] = fmaf(alpha, t[x], gamma * acc);
-            }
-        }
+    static_assert(R0 + DB >= 0 && R1 + DB + 3 <= RB && X0 >= 3 && X0 + 2 * NP <= CB, "target window");
+    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
+    if (p >= NP) return;
+    const float* h = H + (R0 + c + DB) * CBS + X0 + 2 * p;
+    float* t = T + (R0 + c) * CBS + X0 + 2 * p;
+    const float2 al = f2(alpha, alpha), ga = f2(gamma, gamma);
+    for (int r = R0 + c; r < R1; r += NCHUNK, h += NCHUNK * CBS, t += NCHUNK * CBS) {
+        const float a0 = h[0], a1 = h[1];                                      // ia = 0: x, x+1
+        const float2 b = *reinterpret_cast<const float2*>(h + CBS - 1);        // ia = 1: x-1, x
+        const float c0 = h[2 * CBS - 2], c1 = h[2 * CBS - 1];                  // ia = 2: x-2, x-1
+        const float2 d = *reinterpret_cast<const float2*>(h + 3 * CBS - 3);    // ia = 3: x-3, x-2
+        float2 acc = __fmul2_rn(f2(BT0, BT0), f2(a0, a1));
+        acc = __ffma2_rn(f2(BT1, BT1), b, acc);
+        acc = __ffma2_rn(f2(BT2, BT2), f2(c0, c1), acc);
+        acc = __ffma2_rn(f2(BT3, BT3), d, acc);
+        float2 tv = *reinterpret_cast<const float2*>(t);
+        tv = __ffma2_rn(al, tv, __fmul2_rn(ga, acc));
+        *reinterpret_cast<float2*>(t) = tv;
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ int wrap_fast(int v, int C) {
@@ -320,28 +332,31 @@ __device__ __forceinline__ int wrap_fast(int v, int C) {
 template <bool SYN>
 __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
-    __shared__ float sE[RB * CB];
-    __shared__ float sO[RB * CB];
-    __shared__ float sH[RB * CB];
+    __shared__ __align__(16) float sE[SMB];
+    __shared__ __align__(16) float sO[SMB];
+    __shared__ __align__(16) float sH[SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * DFBB_COLS;
     const int R2 = J.R2, C = J.C, i = J.i;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int fo = pp.first_odd;
+    // the first-updated coset (odd if fo) sits one float to the right
+    float* arr[2] = {sE + (fo ? 0 : 1), sO + (fo ? 1 : 0)};
     // inputs: analysis reads the parent's cosets, synthesis the children.
     // Smem row r <-> coset row t0 - 3 + r; smem column x <-> sheared column c0 - 6 + x,
     // i.e. array column (c0 - 6 + x - i*q) mod C for parent row q = 2*(t0 - 3 + r) + parity
     for (int par = 0; par < 2; par++) {
         const View V = par ? (SYN ? J.c1 : J.po) : (SYN ? J.c0 : J.pe);
         const float* P = B.p[V.b] + V.off;
-        float* S = par ? sO : sE;
+        float* S = arr[par];
         if (V.cs == 1) {
             for (int r = warp; r < RB; r += nwarp) {
                 const int tu = t0 - 3 + r;
                 const float* row = P + (long long)wrapd(tu, R2) * V.rs;
                 const int vs = wrapd(c0 - 6 - i * (2 * tu + par), C);
-                for (int x = lane; x < CB; x += 32) cp_async4(&S[r * CB + x], row + wrap_fast(vs + x, C));
+                for (int x = lane; x < CB; x += 32) cp_async4(&S[r * CBS + x], row + wrap_fast(vs + x, C));
             }
         } else {
             // transposed array (rows contiguous in memory along t): walk the sheared
@@ -354,33 +369,50 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 const int x = w + 2 * i * r;
                 if (x < 0 || x >= CB) continue;
                 const int v = wrapd(vbase + w, C);
-                cp_async4(&S[r * CB + x], P + (long long)wrapd(t0 - 3 + r, R2) * V.rs + (long long)v * V.cs);
+                cp_async4(&S[r * CBS + x], P + (long long)wrapd(t0 - 3 + r, R2) * V.rs + (long long)v * V.cs);
             }
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    // pass 1 covers what pass 2 needs; pass 2 covers the tile [3, 3+ROWS) x [6, 6+COLS)
-    if (pp.first_odd) {
-        dfbb_pass<1, DFBB_ROWS + 4, 3, DFBB_COLS + 9, true>(sO, sE, sH, pp.a1, pp.g1);
-        dfbb_pass<3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, false>(sE, sO, sH, pp.a2, pp.g2);
+    // pass 1 updates F on columns [3, 125), which covers what pass 2 reads; pass 2
+    // updates S on the tile [3, 3 + ROWS) x [6, 122).  Pass-1 row sums sit at the
+    // base of sH, pass-2 row sums one float to the right.
+    float* F = arr[fo ? 1 : 0];
+    float* Sx = arr[fo ? 0 : 1];
+    constexpr int NP1 = 61, NH1 = 63, NP2 = 58, NH2 = 60;
+    static_assert(3 + 2 * NP1 == CB - 3 && 6 + 2 * NP2 == CB - 6, "pass windows");
+    if (fo) {
+        rowsum_pairs<0, RB, 0, NH1>(Sx, sH);
+        __syncthreads();
+        target_pairs<1, DFBB_ROWS + 4, 3, NP1, true>(F, sH, pp.a1, pp.g1);
+        __syncthreads();
+        rowsum_pairs<1, DFBB_ROWS + 4, 3, NH2>(F, sH + 1);
+        __syncthreads();
+        target_pairs<3, DFBB_ROWS + 3, 6, NP2, false>(Sx, sH + 1, pp.a2, pp.g2);
     } else {
-        dfbb_pass<2, DFBB_ROWS + 5, 3, DFBB_COLS + 9, false>(sE, sO, sH, pp.a1, pp.g1);
-        dfbb_pass<3, DFBB_ROWS + 3, 6, DFBB_COLS + 6, true>(sO, sE, sH, pp.a2, pp.g2);
+        rowsum_pairs<0, RB, 0, NH1>(Sx, sH);
+        __syncthreads();
+        target_pairs<2, DFBB_ROWS + 5, 3, NP1, false>(F, sH, pp.a1, pp.g1);
+        __syncthreads();
+        rowsum_pairs<2, DFBB_ROWS + 5, 3, NH2>(F, sH + 1);
+        __syncthreads();
+        target_pairs<3, DFBB_ROWS + 3, 6, NP2, true>(Sx, sH + 1, pp.a2, pp.g2);
     }
+    __syncthreads();
     // outputs: analysis writes the children, synthesis the parent's cosets
     const int ncol = min(DFBB_COLS, C - c0);
     for (int par = 0; par < 2; par++) {
         const View V = par ? (SYN ? J.po : J.c1) : (SYN ? J.pe : J.c0);
         float* P = B.p[V.b] + V.off;
-        const float* S = par ? sO : sE;
+        const float* S = arr[par];
         if (V.cs == 1) {
             for (int rr = warp; rr < DFBB_ROWS; rr += nwarp) {
                 const int t = t0 + rr;
                 if (t >= R2) break;
                 float* row = P + (long long)t * V.rs;
                 const int vs = wrapd(c0 - i * (2 * t + par), C);
-                for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast(vs + xx, C)] = S[(3 + rr) * CB + 6 + xx];
+                for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast(vs + xx, C)] = S[(3 + rr) * CBS + 6 + xx];
             }
         } else {
             // transposed subband: walk along memory order as in the load
@@ -393,7 +425,7 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 const int t = t0 + rr;
                 if (xx < 0 || xx >= ncol || t >= R2) continue;
                 const int v = wrapd(vbase + w, C);
-                P[(long long)t * V.rs + (long long)v * V.cs] = S[(3 + rr) * CB + 6 + xx];
+                P[(long long)t * V.rs + (long long)v * V.cs] = S[(3 + rr) * CBS + 6 + xx];
             }
         }
     }
