@@ -41,6 +41,10 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async4s(unsigned dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ unsigned smem_addr(const float* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -210,24 +214,39 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     // plane-local (u, v) of class (pr, pc) <-> image (y0 - 12 + 2u + pr, x0 - 12 + 2v + pc);
     // class-array index ((y0 - 12)/2 + u, (x0 - 12)/2 + v), periodic in (H/2, W/2)
     const int cu0 = (y0 - DFBA_HALO) / 2, cv0 = (x0 - DFBA_HALO) / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!SYN) {
         const float* Dp = B.p[J.D.b] + J.D.off;
-        for (int k = threadIdx.x; k < SA * SA; k += blockDim.x) {
-            int r = k / SA, c = k - r * SA;
-            int y = wrapd(y0 - DFBA_HALO + r, H), x = wrapd(x0 - DFBA_HALO + c, W);
-            cp_async4(&planes[(2 * (r & 1) + (c & 1)) * PA * PAS + (r >> 1) * PAS + (c >> 1)],
-                      Dp + (long long)y * J.D.rs + x);
+        const bool inner = x0 - DFBA_HALO >= 0 && x0 - DFBA_HALO + SA <= W;   // no column wrap in this tile
+        for (int r = warp; r < SA; r += 8) {
+            const float* row = Dp + (long long)wrapd(y0 - DFBA_HALO + r, H) * J.D.rs;
+            // image column c of the tile -> plane (r & 1, c & 1), plane column c >> 1
+            const unsigned sb = smem_addr(planes + 2 * (r & 1) * PA * PAS + (r >> 1) * PAS);
+            for (int c = lane; c < SA; c += 32) {
+                const int x = inner ? x0 - DFBA_HALO + c : wrapd(x0 - DFBA_HALO + c, W);
+                cp_async4s(sb + 4u * ((c & 1) * PA * PAS + (c >> 1)), row + x);
+            }
         }
     } else {
         for (int q = 0; q < 4; q++) {
             const View& V = J.comp[q];
             const float* P = B.p[V.b] + V.off;
-            const bool trans = V.cs != 1;
-            for (int k = threadIdx.x; k < PA * PA; k += blockDim.x) {
-                int a = k / PA, b = k - a * PA;
-                int u = trans ? b : a, v = trans ? a : b;
-                int cu = wrapd(cu0 + u, H2), cv = wrapd(cv0 + v, W2);
-                cp_async4(&planes[q * PA * PAS + u * PAS + v], P + (long long)cu * V.rs + (long long)cv * V.cs);
+            if (V.cs == 1) {
+                // row-major channel: plane row u is a run of array row cu
+                const bool inner = cv0 >= 0 && cv0 + PA <= W2;
+                for (int u = warp; u < PA; u += 8) {
+                    const float* row = P + (long long)wrapd(cu0 + u, H2) * V.rs;
+                    const unsigned sb = smem_addr(planes + q * PA * PAS + u * PAS);
+                    for (int v = lane; v < PA; v += 32)
+                        cp_async4s(sb + 4u * v, row + (inner ? cv0 + v : wrapd(cv0 + v, W2)));
+                }
+            } else {
+                // transposed channel (rs = 1): walk along its memory rows, plane column v
+                for (int v = warp; v < PA; v += 8) {
+                    const float* col = P + (long long)wrapd(cv0 + v, W2) * V.cs;
+                    for (int u = lane; u < PA; u += 32)
+                        cp_async4s(smem_addr(planes + q * PA * PAS + u * PAS + v), col + wrapd(cu0 + u, H2) * V.rs);
+                }
             }
         }
     }
@@ -356,7 +375,13 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 const int tu = t0 - 3 + r;
                 const float* row = P + (long long)wrapd(tu, R2) * V.rs;
                 const int vs = wrapd(c0 - 6 - i * (2 * tu + par), C);
-                for (int x = lane; x < CB; x += 32) cp_async4(&S[r * CBS + x], row + wrap_fast(vs + x, C));
+                const unsigned sb = smem_addr(S + r * CBS);
+                if (vs + CB <= C) {                  // the sheared window does not wrap: no per-element checks
+                    const float* src = row + vs;
+                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
+                } else {
+                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast(vs + x, C));
+                }
             }
         } else {
             // transposed array (rows contiguous in memory along t): walk the sheared
@@ -412,7 +437,13 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
                 if (t >= R2) break;
                 float* row = P + (long long)t * V.rs;
                 const int vs = wrapd(c0 - i * (2 * t + par), C);
-                for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast(vs + xx, C)] = S[(3 + rr) * CBS + 6 + xx];
+                const float* srow = S + (3 + rr) * CBS + 6;
+                if (vs + ncol <= C) {
+                    float* dst = row + vs;
+                    for (int xx = lane; xx < ncol; xx += 32) dst[xx] = srow[xx];
+                } else {
+                    for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast(vs + xx, C)] = srow[xx];
+                }
             }
         } else {
             // transposed subband: walk along memory order as in the load
