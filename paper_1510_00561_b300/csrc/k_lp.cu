@@ -181,6 +181,24 @@ __device__ __forceinline__ void ff_norm(float& hi, float& lo) {
     hi = s;
 }
 
+// The same transformations on two independent lanes at once (paired FP32
+// instructions; each lane rounds exactly as the scalar sequence above).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void ff2_add(float2& hi, float2& lo, float2 x) {
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bb = __fadd2_rn(s, neg2(hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(x, neg2(bb)));
+    hi = s;
+    lo = __fadd2_rn(lo, e);
+}
+__device__ __forceinline__ void ff2_fma(float2& hi, float2& lo, float f, float2 xh, float2 xl) {
+    const float2 ff = make_float2(f, f);
+    const float2 p = __fmul2_rn(ff, xh);
+    const float2 pe = __ffma2_rn(ff, xh, neg2(p));
+    ff2_add(hi, lo, p);
+    lo = __ffma2_rn(ff, xl, __fadd2_rn(lo, pe));
+}
+
 // Synthesis tile with float-float intermediates (dynamic shared memory):
 //   e = cin - down(main, fa);  out = main + up(e, fs)
 template <int RA, int RS>
@@ -216,81 +234,104 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     }
     lp_cp_async_wait_all();
     __syncthreads();
-    for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
-        int r = i / VN, n = i - r * VN;
-        const float* row = s_main + r * MN + 2 * n + RA;
-        float hi = 0.f, lo = 0.f;
+    // Every pass computes two outputs per thread with paired instructions.
+    // decimating row pass, column pairs (na, nb); an odd last column pairs with itself
+    constexpr int NQ = (VN + 1) / 2;
+    const float2 zero2 = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < MN * NQ; i += blockDim.x) {
+        const int r = i / NQ, q = i - r * NQ;
+        const int na = 2 * q, nb = min(2 * q + 1, VN - 1);
+        const float* row = s_main + r * MN + RA;
+        float2 hi = zero2, lo = zero2;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++) ff_fma(hi, lo, tap_a<RA>(b), row[-b], 0.f);
-        s_ah[i] = hi;
-        s_al[i] = lo;
+        for (int b = -RA; b <= RA; b++)
+            ff2_fma(hi, lo, tap_a<RA>(b), make_float2(row[2 * na - b], row[2 * nb - b]), zero2);
+        s_ah[r * VN + na] = hi.x;
+        s_al[r * VN + na] = lo.x;
+        if (nb != na) {
+            s_ah[r * VN + nb] = hi.y;
+            s_al[r * VN + nb] = lo.y;
+        }
     }
     __syncthreads();
+    // decimating column pass, then e = cin - down(main) (normalised float-float)
     const float* cinp = B.p[J.cin.b] + J.cin.off;
-    for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
-        int m = i / VN, n = i - m * VN;
-        float hi = 0.f, lo = 0.f;
+    for (int i = threadIdx.x; i < VN * NQ; i += blockDim.x) {
+        const int m = i / NQ, q = i - m * NQ;
+        const int na = 2 * q, nb = min(2 * q + 1, VN - 1);
+        float2 hi = zero2, lo = zero2;
 #pragma unroll
         for (int a = -RA; a <= RA; a++) {
-            int k = (2 * m + RA - a) * VN + n;
-            ff_fma(hi, lo, tap_a<RA>(a), s_ah[k], s_al[k]);
+            const int k = (2 * m + RA - a) * VN;
+            ff2_fma(hi, lo, tap_a<RA>(a), make_float2(s_ah[k + na], s_ah[k + nb]),
+                    make_float2(s_al[k + na], s_al[k + nb]));
         }
-        int gm = wrap_idx(m0 + MLO + m, Hh), gn = wrap_idx(n0 + MLO + n, Wh);
-        float eh = cinp[(long long)gm * J.cin.rs + gn], el = 0.f;
-        ff_add(eh, el, -hi);
-        el = __fsub_rn(el, lo);
-        ff_norm(eh, el);
-        s_vh[i] = eh;
-        s_vl[i] = el;
+        const float* crow = cinp + (long long)wrap_idx(m0 + MLO + m, Hh) * J.cin.rs;
+        float2 eh = make_float2(crow[wrap_idx(n0 + MLO + na, Wh)], crow[wrap_idx(n0 + MLO + nb, Wh)]);
+        float2 el = zero2;
+        ff2_add(eh, el, neg2(hi));
+        el = __fadd2_rn(el, neg2(lo));
+        const float2 sn = __fadd2_rn(eh, el);
+        el = __fadd2_rn(el, neg2(__fadd2_rn(sn, neg2(eh))));
+        eh = sn;
+        s_vh[m * VN + na] = eh.x;
+        s_vl[m * VN + na] = el.x;
+        if (nb != na) {
+            s_vh[m * VN + nb] = eh.y;
+            s_vl[m * VN + nb] = el.y;
+        }
     }
     __syncthreads();
-    // expanding row pass by output pairs (x = 2p, 2p + 1)
-    for (int i = threadIdx.x; i < VN * (T / 2); i += blockDim.x) {
-        const int m = i / (T / 2), p = i - m * (T / 2);
-        const int kb = m * VN + p - MLO;
-        float eh = 0.f, el = 0.f, oh = 0.f, ol = 0.f;
+    // expanding row pass: output pairs x = 2p, 2p + 1 for p = 2w and 2w + 1
+    for (int i = threadIdx.x; i < VN * (T / 4); i += blockDim.x) {
+        const int m = i / (T / 4), w = i - m * (T / 4);
+        const int kb = m * VN + 2 * w - MLO;
+        float2 eh = zero2, el = zero2, oh = zero2, ol = zero2;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - t / 2;
-                ff_fma(eh, el, tap_s<RS>(t), s_vh[k], s_vl[k]);
+                ff2_fma(eh, el, tap_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]), make_float2(s_vl[k], s_vl[k + 1]));
             } else {
                 const int k = kb + (1 - t) / 2;
-                ff_fma(oh, ol, tap_s<RS>(t), s_vh[k], s_vl[k]);
+                ff2_fma(oh, ol, tap_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]), make_float2(s_vl[k], s_vl[k + 1]));
             }
         }
-        s_ah[m * T + 2 * p] = eh;
-        s_al[m * T + 2 * p] = el;
-        s_ah[m * T + 2 * p + 1] = oh;
-        s_al[m * T + 2 * p + 1] = ol;
+        float* ah = s_ah + m * T + 4 * w;
+        float* al = s_al + m * T + 4 * w;
+        ah[0] = eh.x; ah[1] = oh.x; ah[2] = eh.y; ah[3] = oh.y;
+        al[0] = el.x; al[1] = ol.x; al[2] = el.y; al[3] = ol.y;
     }
     __syncthreads();
-    // expanding column pass by output pairs (y = 2p, 2p + 1), plus the main input
+    // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input
     float* outp = B.p[J.out.b] + J.out.off;
-    for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
-        const int p = i / T, x = i - p * T;
+    for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
+        const int p = i / (T / 2), w = i - p * (T / 2);
+        const int x = 2 * w;
         const int kb = (p - MLO) * T + x;
-        float eh = 0.f, el = 0.f, oh = 0.f, ol = 0.f;
+        float2 eh = zero2, el = zero2, oh = zero2, ol = zero2;
 #pragma unroll
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - (t / 2) * T;
-                ff_fma(eh, el, tap_s<RS>(t), s_ah[k], s_al[k]);
+                ff2_fma(eh, el, tap_s<RS>(t), make_float2(s_ah[k], s_ah[k + 1]), make_float2(s_al[k], s_al[k + 1]));
             } else {
                 const int k = kb + ((1 - t) / 2) * T;
-                ff_fma(oh, ol, tap_s<RS>(t), s_ah[k], s_al[k]);
+                ff2_fma(oh, ol, tap_s<RS>(t), make_float2(s_ah[k], s_ah[k + 1]), make_float2(s_al[k], s_al[k + 1]));
             }
         }
         const int gx = x0 + x;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int y = 2 * p + h, gy = y0 + y;
-            if (gy < H && gx < W) {
-                float hi = h ? oh : eh, lo = h ? ol : el;
-                const float mv = s_main[(y - Y0) * MN + (x - Y0)];
-                ff_add(hi, lo, mv);
-                outp[(long long)gy * J.out.rs + gx] = __fadd_rn(hi, lo);
-            }
+            if (gy >= H) continue;
+            float2 hi = h ? oh : eh, lo = h ? ol : el;
+            const float* mrow = s_main + (y - Y0) * MN + (x - Y0);
+            ff2_add(hi, lo, make_float2(mrow[0], mrow[1]));
+            const float2 o = __fadd2_rn(hi, lo);
+            float* orow = outp + (long long)gy * J.out.rs;
+            if (gx < W) orow[gx] = o.x;
+            if (gx + 1 < W) orow[gx + 1] = o.y;
         }
     }
 }
