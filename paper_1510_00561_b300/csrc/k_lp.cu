@@ -235,50 +235,51 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     lp_cp_async_wait_all();
     __syncthreads();
     // Every pass computes two outputs per thread with paired instructions.
-    // decimating row pass, column pairs (na, nb); an odd last column pairs with itself
-    constexpr int NQ = (VN + 1) / 2;
+    // decimating row pass, row pairs (ra, rb) (an odd last row pairs with itself), so that
+    // consecutive threads read consecutive columns as in a scalar pass
+    constexpr int NR = (MN + 1) / 2, NM = (VN + 1) / 2;
     const float2 zero2 = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < MN * NQ; i += blockDim.x) {
-        const int r = i / NQ, q = i - r * NQ;
-        const int na = 2 * q, nb = min(2 * q + 1, VN - 1);
-        const float* row = s_main + r * MN + RA;
+    for (int i = threadIdx.x; i < NR * VN; i += blockDim.x) {
+        const int q = i / VN, n = i - q * VN;
+        const int ra = 2 * q, rb = min(2 * q + 1, MN - 1);
+        const float* rowa = s_main + ra * MN + 2 * n + RA;
+        const float* rowb = s_main + rb * MN + 2 * n + RA;
         float2 hi = zero2, lo = zero2;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++)
-            ff2_fma(hi, lo, tap_a<RA>(b), make_float2(row[2 * na - b], row[2 * nb - b]), zero2);
-        s_ah[r * VN + na] = hi.x;
-        s_al[r * VN + na] = lo.x;
-        if (nb != na) {
-            s_ah[r * VN + nb] = hi.y;
-            s_al[r * VN + nb] = lo.y;
+        for (int b = -RA; b <= RA; b++) ff2_fma(hi, lo, tap_a<RA>(b), make_float2(rowa[-b], rowb[-b]), zero2);
+        s_ah[ra * VN + n] = hi.x;
+        s_al[ra * VN + n] = lo.x;
+        if (rb != ra) {
+            s_ah[rb * VN + n] = hi.y;
+            s_al[rb * VN + n] = lo.y;
         }
     }
     __syncthreads();
-    // decimating column pass, then e = cin - down(main) (normalised float-float)
+    // decimating column pass over row pairs (ma, mb), then e = cin - down(main) (normalised float-float)
     const float* cinp = B.p[J.cin.b] + J.cin.off;
-    for (int i = threadIdx.x; i < VN * NQ; i += blockDim.x) {
-        const int m = i / NQ, q = i - m * NQ;
-        const int na = 2 * q, nb = min(2 * q + 1, VN - 1);
+    for (int i = threadIdx.x; i < NM * VN; i += blockDim.x) {
+        const int q = i / VN, n = i - q * VN;
+        const int ma = 2 * q, mb = min(2 * q + 1, VN - 1);
         float2 hi = zero2, lo = zero2;
 #pragma unroll
         for (int a = -RA; a <= RA; a++) {
-            const int k = (2 * m + RA - a) * VN;
-            ff2_fma(hi, lo, tap_a<RA>(a), make_float2(s_ah[k + na], s_ah[k + nb]),
-                    make_float2(s_al[k + na], s_al[k + nb]));
+            const int ka = (2 * ma + RA - a) * VN + n, kb = (2 * mb + RA - a) * VN + n;
+            ff2_fma(hi, lo, tap_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
         }
-        const float* crow = cinp + (long long)wrap_idx(m0 + MLO + m, Hh) * J.cin.rs;
-        float2 eh = make_float2(crow[wrap_idx(n0 + MLO + na, Wh)], crow[wrap_idx(n0 + MLO + nb, Wh)]);
+        const int gn = wrap_idx(n0 + MLO + n, Wh);
+        float2 eh = make_float2(cinp[(long long)wrap_idx(m0 + MLO + ma, Hh) * J.cin.rs + gn],
+                                cinp[(long long)wrap_idx(m0 + MLO + mb, Hh) * J.cin.rs + gn]);
         float2 el = zero2;
         ff2_add(eh, el, neg2(hi));
         el = __fadd2_rn(el, neg2(lo));
         const float2 sn = __fadd2_rn(eh, el);
         el = __fadd2_rn(el, neg2(__fadd2_rn(sn, neg2(eh))));
         eh = sn;
-        s_vh[m * VN + na] = eh.x;
-        s_vl[m * VN + na] = el.x;
-        if (nb != na) {
-            s_vh[m * VN + nb] = eh.y;
-            s_vl[m * VN + nb] = el.y;
+        s_vh[ma * VN + n] = eh.x;
+        s_vl[ma * VN + n] = el.x;
+        if (mb != ma) {
+            s_vh[mb * VN + n] = eh.y;
+            s_vl[mb * VN + n] = el.y;
         }
     }
     __syncthreads();
