@@ -211,3 +211,20 @@ def test_device_bytes_estimate_matches_allocation():
     assert b.n == len(streams)
     slack = 64 << 20
     assert est - slack <= used <= est + est // 20 + slack, (est, used)
+
+
+def test_1080p_batch_matches_plain():
+    """The benchmark's configuration: concurrent 1080p streams, 5 levels, 32/16/16/8/8."""
+    cfg = dict(width=1920, height=1080, levels=5, dirs_log2=[5, 4, 4, 3, 3], qph=8, qpl=1, key_interval=10)
+    v = S.SyntheticVideo(S.spec_for(1920, 1080, seed=7))
+    frames = [torch.from_numpy(f).cuda() for f in v.frames(6)]
+    b = Batch([cfg] * 4)
+    plain = [Codec(**cfg) for _ in range(4)]
+    outs = _rgb_buffers([cfg] * 4)
+    for t in range(3):
+        inp = [frames[t + j] for j in range(4)]          # stream j is the sequence shifted by j frames
+        res = b.step(3, rgb=inp, rgb_out=outs)
+        for j, c in enumerate(plain):
+            ref, ft = c.encode(inp[j])
+            assert res[j]["frame_type"] == ft and torch.equal(res[j]["bytes"], ref)
+            assert torch.equal(outs[j], c.decode(ref.clone()))
