@@ -87,6 +87,7 @@ def lib():
         L.or_encode.argtypes = [ctypes.c_void_p, _U8, _U8, ctypes.c_long, ctypes.POINTER(ctypes.c_long),
                                 _IP, ctypes.c_void_p]
         L.or_decode.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, _U8, ctypes.c_void_p]
+        L.or_decode_scaled.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -354,17 +355,22 @@ class Codec:
             raise RuntimeError("oracle encode failed: status %d" % st)
         return out[:n.value].copy(), ft.value
 
-    def decode(self, stream, want_planes=False):
+    def decode(self, stream, want_planes=False, scale=0):
+        """Decode one frame; scale s > 0 reconstructs the level-s approximation (§3.3) as
+        ceil(H/2^s) x ceil(W/2^s) RGB from the lowpass and levels s+1..L."""
         s = np.ascontiguousarray(stream, dtype=np.uint8)
-        rgb = np.zeros((self.height, self.width, 3), np.uint8)
-        pl = np.zeros(self.Hp * self.Wp + 2 * self.Hcp * self.Wcp) if want_planes else None
-        st = lib().or_decode(self._h, s, s.size, rgb.reshape(-1), pl.ctypes.data if pl is not None else None)
+        f = 1 << scale
+        h, w = (self.height + f - 1) // f, (self.width + f - 1) // f
+        Hp, Wp, Hcp, Wcp = self.Hp >> scale, self.Wp >> scale, self.Hcp >> scale, self.Wcp >> scale
+        rgb = np.zeros((h, w, 3), np.uint8)
+        pl = np.zeros(Hp * Wp + 2 * Hcp * Wcp) if want_planes else None
+        st = lib().or_decode_scaled(self._h, s, s.size, scale, rgb.reshape(-1),
+                                    pl.ctypes.data if pl is not None else None)
         if st:
             raise RuntimeError("oracle decode failed: status %d" % st)
         if want_planes:
-            ny, nc = self.Hp * self.Wp, self.Hcp * self.Wcp
-            return rgb, (pl[:ny].reshape(self.Hp, self.Wp), pl[ny:ny + nc].reshape(self.Hcp, self.Wcp),
-                         pl[ny + nc:].reshape(self.Hcp, self.Wcp))
+            ny, nc = Hp * Wp, Hcp * Wcp
+            return rgb, (pl[:ny].reshape(Hp, Wp), pl[ny:ny + nc].reshape(Hcp, Wcp), pl[ny + nc:].reshape(Hcp, Wcp))
         return rgb
 
     def decode_status(self, stream):

@@ -848,6 +848,12 @@ int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out
  * away from zero, single precision) and clamp: Y to [0,255], Co/Cg to
  * [-255,255]; upsample the chroma and invert the colour transform.          */
 int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* planes_out) {
+    return or_decode_scaled(c, in, len, 0, rgb, planes_out);
+}
+
+/* the same at scale s in [0, L] (§3.3; see oracle.h) */
+int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_t* rgb, double* planes_out) {
+    if (scale < 0 || scale > c->L) return OR_EINVAL;
     if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
     if (get16(in + 4) != 1) return OR_ECORRUPT;
     int type = in[6];
@@ -903,28 +909,55 @@ int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* pl
         double scale = s->kind == 0 ? ldexp((double)c->qpl, c->L) : (double)c->qph;
         for (long e = 0; e < (long)s->h * s->w; e++) co[base + s->off + e] = q[base + s->off + e] * scale;
     }
-    long ny = (long)c->Hp * c->Wp, nc = (long)c->Hcp * c->Wcp;
+    /* §3.3 scalability: scale s keeps the lowpass and levels s+1..L, which form the
+     * sub-pyramid of the (Hp >> s) x (Wp >> s) level-s lowpass image; its inverse is
+     * c_s, normalised by the DC gain 2^-s of s levels. */
+    const int s = scale;
+    const int Hps = c->Hp >> s, Wps = c->Wp >> s, Hcps = c->Hcp >> s, Wcps = c->Wcp >> s;
+    const int Hos = (c->Ho + (1 << s) - 1) >> s, Wos = (c->Wo + (1 << s) - 1) >> s;
+    const int Hcs = (c->Hc + (1 << s) - 1) >> s, Wcs = (c->Wc + (1 << s) - 1) >> s;
+    long ny = (long)Hps * Wps, nc = (long)Hcps * Wcps;
     double* pl = (double*)malloc(sizeof(double) * (size_t)(ny + 2 * nc));
-    or_ct(1, co, c->Hp, c->Wp, c->L, c->k, pl);
-    or_ct(1, co + c->ly.total, c->Hcp, c->Wcp, c->L, c->k, pl + ny);
-    or_ct(1, co + c->ly.total + c->lc.total, c->Hcp, c->Wcp, c->L, c->k, pl + ny + nc);
+    const or_layout* lays[3] = {&c->ly, &c->lc, &c->lc};
+    const long poff[3] = {0, c->ly.total, c->ly.total + c->lc.total};
+    const long ploff[3] = {0, ny, ny + nc};
+    const int ph[3] = {Hps, Hcps, Hcps}, pw[3] = {Wps, Wcps, Wcps};
+    for (int p = 0; p < 3; p++) {
+        const or_layout* ly = lays[p];
+        const double* cp = co + poff[p];
+        long nlow = (long)ly->sb[0].h * ly->sb[0].w;
+        if (s == c->L) {
+            memcpy(pl + ploff[p], cp, sizeof(double) * (size_t)nlow);
+        } else {
+            /* first subband of level s+1 */
+            int first = 1;
+            for (int j = 0; j < s; j++) first += 1 << c->k[j];
+            long tail = ly->total - ly->sb[first].off;
+            double* sub = (double*)malloc(sizeof(double) * (size_t)(nlow + tail));
+            memcpy(sub, cp, sizeof(double) * (size_t)nlow);
+            memcpy(sub + nlow, cp + ly->sb[first].off, sizeof(double) * (size_t)tail);
+            or_ct(1, sub, ph[p], pw[p], c->L - s, c->k + s, pl + ploff[p]);
+            free(sub);
+        }
+        for (long e = 0; e < (long)ph[p] * pw[p]; e++) pl[ploff[p] + e] = ldexp(pl[ploff[p] + e], -s);
+    }
     if (planes_out) memcpy(planes_out, pl, sizeof(double) * (size_t)(ny + 2 * nc));
-    long n = (long)c->Ho * c->Wo, ncs = (long)c->Hc * c->Wc;
+    long n = (long)Hos * Wos, ncs = (long)Hcs * Wcs;
     int16_t* Y = (int16_t*)malloc(sizeof(int16_t) * n);
     int16_t* Co = (int16_t*)malloc(sizeof(int16_t) * n);
     int16_t* Cg = (int16_t*)malloc(sizeof(int16_t) * n);
     int16_t* Co2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
     int16_t* Cg2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
-    for (int y = 0; y < c->Ho; y++)
-        for (int x = 0; x < c->Wo; x++)
-            Y[(long)y * c->Wo + x] = (int16_t)clampi((long)roundf((float)pl[(long)y * c->Wp + x]), 0, 255);
-    for (int y = 0; y < c->Hc; y++)
-        for (int x = 0; x < c->Wc; x++) {
-            Co2[(long)y * c->Wc + x] = (int16_t)clampi((long)roundf((float)pl[ny + (long)y * c->Wcp + x]), -255, 255);
-            Cg2[(long)y * c->Wc + x] = (int16_t)clampi((long)roundf((float)pl[ny + nc + (long)y * c->Wcp + x]), -255, 255);
+    for (int y = 0; y < Hos; y++)
+        for (int x = 0; x < Wos; x++)
+            Y[(long)y * Wos + x] = (int16_t)clampi((long)roundf((float)pl[(long)y * Wps + x]), 0, 255);
+    for (int y = 0; y < Hcs; y++)
+        for (int x = 0; x < Wcs; x++) {
+            Co2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + (long)y * Wcps + x]), -255, 255);
+            Cg2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + nc + (long)y * Wcps + x]), -255, 255);
         }
-    or_chroma_up(Co2, c->Hc, c->Wc, c->Ho, c->Wo, Co);
-    or_chroma_up(Cg2, c->Hc, c->Wc, c->Ho, c->Wo, Cg);
+    or_chroma_up(Co2, Hcs, Wcs, Hos, Wos, Co);
+    or_chroma_up(Cg2, Hcs, Wcs, Hos, Wos, Cg);
     or_ycocgr_inverse(Y, Co, Cg, n, rgb);
     memcpy(c->dec_state, q, sizeof(int16_t) * (size_t)c->ncoef);
     c->dec_next = fidx + 1;

@@ -120,5 +120,11 @@ int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out
               int* frame_type, double* coeffs_out);
 /* full decode; planes_out (optional, FP64) receives the reconstructed padded planes */
 int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* planes_out);
+/* decode at scale s in [0, L] (§3.3): the decoder state advances for every
+ * component as in or_decode, and the frame is reconstructed from the lowpass
+ * and levels s+1..L only: the level-s approximation, normalised by 2^-s, as
+ * ceil(H/2^s) x ceil(W/2^s) RGB.  planes_out receives the three normalised
+ * (Hp>>s) x (Wp>>s), (Hcp>>s) x (Wcp>>s) planes. */
+int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_t* rgb, double* planes_out);
 
 #endif
