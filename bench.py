@@ -329,6 +329,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served run (0: skip)")
     ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
+    ap.add_argument("--no-scalable", action="store_true", help="skip the per-scale decode pass")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -512,7 +513,41 @@ def main():
     e2e_run(2)                                   # warm-up of the copy path
     io_bytes[0] = io_bytes[1] = 0
     e2e_value = combine_ranks(e2e_run(e2e_steps), e2e_steps * B, dist, dev)[0]
-    del batch, outs_rgb, d_ins, d_outs, d_rgbs
+    del d_ins, d_outs, d_rgbs
+
+    # scalable decoding (§3.3): the same B streams decoded alone at every pyramid
+    # scale; one K-frame period of bitstreams is encoded once and decoded in order
+    scalable = None
+    if not args.no_scalable:
+        batch.reset()
+        kstreams = []
+        for t in range(KINT):
+            res = batch.step(1, rgb=frames_at(t))
+            kstreams.append([r["bytes"].clone() for r in res])
+        del batch, outs_rgb
+        dbatch = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
+                             key_interval=KINT)] * B)
+        dbatch.set_shape(*shape)
+        sc_steps = max(KINT, min(args.steps, 2 * KINT))
+        scales = []
+        for sc in range(LEVELS + 1):
+            hs, ws = dbatch.scaled_size(0, sc)
+            souts = [torch.empty((hs, ws, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+
+            def dec_step(i, sc=sc, souts=souts):
+                dbatch.step(2, streams_in=kstreams[i % KINT], rgb_out=souts, scale=sc)
+
+            dbatch.reset()
+            for i in range(KINT):                # warm-up: one whole K-frame period
+                dec_step(i)
+            v, ms, _ = combine_ranks(timed(dec_step, sc_steps), sc_steps * B, dist, dev)
+            scales.append({"scale": sc, "size": [hs, ws], "value": v, "ms_per_step": ms / sc_steps})
+        scalable = {"workload": "decode only of %d 1080p streams, each at pyramid scale s (ceil(1080/2^s) x "
+                                "ceil(1920/2^s) output), K-frame period decoded in order" % B,
+                    "unit": UNIT, "steps": sc_steps, "scales": scales}
+        del dbatch, kstreams
+    else:
+        del batch, outs_rgb
 
     # served form: continuous batching of concurrent streams under a memory budget
     served = None
@@ -564,7 +599,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served,
+            "plain": plain, "served": served, "scalable": scalable,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},

@@ -199,6 +199,22 @@ cvc_status cvc_encode_frame(cvc_codec* codec, const uint8_t* d_rgb, size_t pitch
 cvc_status cvc_decode_frame(cvc_codec* codec, const uint8_t* d_in, size_t in_len, uint8_t* d_rgb,
                             size_t pitch_bytes, cvc_stream_t stream);
 
+/* Scalable decoding (§3.3: each LP scale of a frame can be decoded on its
+ * own).  As cvc_decode_frame, but the output is the frame at pyramid scale
+ * `scale` (0 <= scale <= levels): ceil(height / 2^scale) rows of
+ * ceil(width / 2^scale) * 3 bytes at row pitch pitch_bytes.  Scale s
+ * inverts only the lowpass and levels s+1..L of each plane, i.e. the
+ * coefficients of its level-s lowpass image under an (L - s)-level
+ * transform, and divides the result by the DC gain 2^s of s levels; scale L
+ * shows the lowpass band itself.  The whole bitstream is still parsed and
+ * the decoder state (the P-frame reference) updated in full, so the scale
+ * may change from frame to frame, and a later full-scale decode is the same
+ * as if every frame had been decoded at full scale.  Scale 0 is
+ * cvc_decode_frame.  Errors: as cvc_decode_frame; INVALID_ARG also for a
+ * scale outside [0, levels].                                                */
+cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t in_len, int scale,
+                                   uint8_t* d_rgb, size_t pitch_bytes, cvc_stream_t stream);
+
 /* Inspection of the last encode / decode (for parity checks): copies into
  * d_out (device, at least cap_elems floats)
  *   which = 0: the encoder's padded float planes Y, Co, Cg (before the transform)
@@ -262,6 +278,13 @@ cvc_status cvc_batch_reset(cvc_batch* batch, int i);
  * (stream order, encoder before decoder), or CVC_OK.                        */
 cvc_status cvc_batch_step(cvc_batch* batch, int what, const cvc_batch_io* io, cvc_batch_result* res,
                           cvc_stream_t stream);
+
+/* The same with every decoding stream of the step output at pyramid scale
+ * `scale` (as cvc_decode_frame_scaled; each d_rgb_out sized for that scale).
+ * INVALID_ARG if a decoding stream has fewer than `scale` levels.  Each
+ * scale replays its own captured graph.                                     */
+cvc_status cvc_batch_step_scaled(cvc_batch* batch, int what, const cvc_batch_io* io, int scale,
+                                 cvc_batch_result* res, cvc_stream_t stream);
 
 /* Launch shapes (they change no result): rows per block of the run-length
  * kernels (1..32) and blocks of the decoder's token kernels (1..65535).
@@ -411,6 +434,18 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */
 cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int levels, const int* dirs_log2,
                                  int batch, int mode, void* buf, size_t cap, size_t* used);
+
+/* The decoder back end at pyramid scale `scale` of the codec streams
+ * params[0 .. n-1] (host only, no device call): the inverse transform's
+ * launches over their sub-pyramids, in the format above with the header's
+ * last u32 = bytes of one output record, followed by n output records
+ *   {i32 H, W, Hc, Wc, rs_y, rs_c, src, blk0; i64 off[3]; f32 norm; i32 0}
+ * (output frame and chroma size at the scale, plane row pitches, source
+ * buffer 0 = reconstructed planes / 1 = decoded coefficients, first block,
+ * Y/Co/Cg offsets, normalisation).  elems[] are those of the full decoder.
+ * INVALID_ARG for a scale outside [0, max levels]; CAPACITY as above.       */
+cvc_status cvc_debug_scale_tables(const cvc_params* params, int n, int scale, void* buf, size_t cap,
+                                  size_t* used);
 
 #ifdef __cplusplus
 }

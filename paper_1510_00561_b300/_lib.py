@@ -120,6 +120,7 @@ def lib():
         L.cvc_codec_info.argtypes = [_P, ctypes.POINTER(CodecInfo)]
         L.cvc_encode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
+        L.cvc_decode_frame_scaled.argtypes = [_P, _P, _SZ, _I, _P, _SZ, _P]
         L.cvc_codec_inspect.argtypes = [_P, _I, _P, _SZ, _P]
         L.cvc_codec_set_timing.argtypes = [_P, _I]
         L.cvc_codec_timing.argtypes = [_P, _P, _P]
@@ -132,6 +133,7 @@ def lib():
         L.cvc_batch_info.argtypes = [_P, _I, ctypes.POINTER(CodecInfo)]
         L.cvc_batch_reset.argtypes = [_P, _I]
         L.cvc_batch_step.argtypes = [_P, _I, ctypes.POINTER(BatchIo), ctypes.POINTER(BatchResult), _P]
+        L.cvc_batch_step_scaled.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(BatchResult), _P]
         L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
         L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
         L.cvc_batch_set_graphs.argtypes = [_P, _I]
@@ -148,6 +150,7 @@ def lib():
         L.cvc_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
         L.cvc_debug_plan_tables.argtypes = [ctypes.POINTER(Params), _I, _I, _I, ctypes.POINTER(_I), _I, _I, _P,
                                             _SZ, ctypes.POINTER(_SZ)]
+        L.cvc_debug_scale_tables.argtypes = [ctypes.POINTER(Params), _I, _I, _P, _SZ, ctypes.POINTER(_SZ)]
         _lib = L
     return _lib
 

@@ -162,14 +162,23 @@ class Codec:
             raise err
         return out[:n.value], ft.value
 
-    def decode(self, stream_bytes, out=None, stream=None):
-        """stream_bytes: uint8 CUDA tensor holding one encoded frame.  Returns (H, W, 3) uint8."""
+    def scaled_size(self, scale):
+        """(height, width) of the decoder's output at pyramid scale `scale`."""
+        f = 1 << scale
+        return (self.height + f - 1) // f, (self.width + f - 1) // f
+
+    def decode(self, stream_bytes, out=None, stream=None, scale=0):
+        """stream_bytes: uint8 CUDA tensor holding one encoded frame.  Returns (H, W, 3) uint8,
+        or the frame at pyramid scale `scale` (ceil(H / 2^scale) x ceil(W / 2^scale),
+        cvc_decode_frame_scaled)."""
         if not (stream_bytes.is_cuda and stream_bytes.dtype == torch.uint8 and stream_bytes.is_contiguous()):
             raise ValueError("expected a contiguous uint8 CUDA tensor")
         if out is None:
-            out = torch.empty((self.height, self.width, 3), dtype=torch.uint8, device=stream_bytes.device)
-        _L.check(_L.lib().cvc_decode_frame(self._h, _ptr(stream_bytes), stream_bytes.numel(), _ptr(out),
-                                           out.stride(0), _stream(stream)), "cvc_decode_frame")
+            h, w = self.scaled_size(scale) if 0 <= scale <= self.levels else (1, 1)
+            out = torch.empty((h, w, 3), dtype=torch.uint8, device=stream_bytes.device)
+        _L.check(_L.lib().cvc_decode_frame_scaled(self._h, _ptr(stream_bytes), stream_bytes.numel(), int(scale),
+                                                  _ptr(out), out.stride(0), _stream(stream)),
+                 "cvc_decode_frame_scaled")
         return out
 
     def inspect(self, which):
@@ -265,14 +274,21 @@ class Batch:
             io.d_rgb_out = y.data_ptr() if y is not None else None
             io.pitch_out = y.stride(0) if y is not None else 0
 
-    def step(self, what, rgb=None, streams_in=None, rgb_out=None, outs=None, stream=None, check=True):
+    def scaled_size(self, i, scale):
+        """(height, width) of stream i's decoder output at pyramid scale `scale`."""
+        f = 1 << scale
+        s = self.streams[i]
+        return (s["height"] + f - 1) // f, (s["width"] + f - 1) // f
+
+    def step(self, what, rgb=None, streams_in=None, rgb_out=None, outs=None, stream=None, check=True, scale=0):
         """One step over every stream (entries None take no part).
 
         what: 1 encode, 2 decode, 3 encode + decode of the step's own output.
+        scale: pyramid scale of every decoder output (cvc_batch_step_scaled).
         Returns a list of per-stream dicts (statuses, out_len, frame types,
         the encoded bytes as a view of the stream's output buffer)."""
         self._fill(rgb, streams_in, rgb_out, outs)
-        st = _L.lib().cvc_batch_step(self._h, what, self._io, self._res, _stream(stream))
+        st = _L.lib().cvc_batch_step_scaled(self._h, what, self._io, int(scale), self._res, _stream(stream))
         if st in (1, 6):
             raise _L.CvcError(st, "cvc_batch_step")
         res = []

@@ -33,6 +33,7 @@ std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int
     for (int b = 0; b < batch; b++) {
         PlaneRef r;
         memset(&r, 0, sizeof(r));
+        r.low_coef = -1;
         r.H = h;
         r.W = w;
         r.L = levels;
@@ -67,8 +68,8 @@ cvc_status make_core(Core* c, const cvc_params* params, int n) {
 }
 
 // enqueue, wait, collect the stage times
-cvc_status run_step(Core* c, int mode, cudaStream_t st) {
-    cvc_status s = core_enqueue(c, mode, st);
+cvc_status run_step(Core* c, int mode, cudaStream_t st, int scale = 0) {
+    cvc_status s = core_enqueue(c, mode, st, scale);
     if (s != CVC_OK) return s;
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
@@ -297,10 +298,15 @@ cvc_status cvc_encode_frame(cvc_codec* c, const uint8_t* d_rgb, size_t pitch_byt
 
 cvc_status cvc_decode_frame(cvc_codec* c, const uint8_t* d_in, size_t in_len, uint8_t* d_rgb, size_t pitch_bytes,
                             cvc_stream_t stream) {
+    return cvc_decode_frame_scaled(c, d_in, in_len, 0, d_rgb, pitch_bytes, stream);
+}
+
+cvc_status cvc_decode_frame_scaled(cvc_codec* c, const uint8_t* d_in, size_t in_len, int scale, uint8_t* d_rgb,
+                                   size_t pitch_bytes, cvc_stream_t stream) {
     if (!c || !d_in || !d_rgb) return CVC_ERR_INVALID_ARG;
     StreamIo io{nullptr, 0, nullptr, 0, d_in, in_len, d_rgb, pitch_bytes};
-    if (!core_fill_call(&c->core, 0, STEP_DEC, io)) return CVC_ERR_INVALID_ARG;
-    cvc_status s = run_step(&c->core, STEP_DEC, (cudaStream_t)stream);
+    if (!core_fill_call(&c->core, 0, STEP_DEC, io, scale)) return CVC_ERR_INVALID_ARG;
+    cvc_status s = run_step(&c->core, STEP_DEC, (cudaStream_t)stream, scale);
     if (s != CVC_OK) return s;
     cvc_status ds;
     core_commit(&c->core, 0, STEP_DEC, nullptr, &ds, nullptr, nullptr, nullptr, nullptr);
@@ -376,21 +382,26 @@ cvc_status cvc_batch_reset(cvc_batch* b, int i) {
     return CVC_OK;
 }
 
-static bool batch_fill(Core* c, int what, const cvc_batch_io* io) {
+static bool batch_fill(Core* c, int what, const cvc_batch_io* io, int scale = 0) {
     for (int s = 0; s < c->n; s++) {
         const cvc_batch_io& x = io[s];
         StreamIo sio{x.d_rgb, x.pitch_bytes, x.d_out, x.out_cap, x.d_in, x.in_len, x.d_rgb_out, x.pitch_out};
-        if (!core_fill_call(c, s, what, sio)) return false;
+        if (!core_fill_call(c, s, what, sio, scale)) return false;
     }
     return true;
 }
 
 cvc_status cvc_batch_step(cvc_batch* b, int what, const cvc_batch_io* io, cvc_batch_result* res,
                           cvc_stream_t stream) {
+    return cvc_batch_step_scaled(b, what, io, 0, res, stream);
+}
+
+cvc_status cvc_batch_step_scaled(cvc_batch* b, int what, const cvc_batch_io* io, int scale, cvc_batch_result* res,
+                                 cvc_stream_t stream) {
     if (!b || !io || !res || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
     Core* c = &b->core;
-    if (!batch_fill(c, what, io)) return CVC_ERR_INVALID_ARG;
-    cvc_status s = run_step(c, what, (cudaStream_t)stream);
+    if (!batch_fill(c, what, io, scale)) return CVC_ERR_INVALID_ARG;
+    cvc_status s = run_step(c, what, (cudaStream_t)stream, scale);
     if (s != CVC_OK) return s;
     cvc_status first = CVC_OK;
     for (int i = 0; i < c->n; i++) {
@@ -490,6 +501,48 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
     return s;
 }
 
+// the launches of one direction of an engine (and optional trailing
+// records), in the cvc_debug_plan_tables format
+static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long long elems_in[4], const void* tail,
+                              size_t tail_n, size_t tail_sz, void* buf, size_t cap, size_t* used) {
+    unsigned long long elems[4] = {elems_in[0], elems_in[1], elems_in[2], elems_in[3]};
+    elems[2] = std::max(elems[2], (unsigned long long)e.work_elems);
+    struct Item { int kind; const void* data; size_t n, sz; };
+    std::vector<Item> items;
+    const bool analysis = (mode == FWD || mode == INV_ADJ);
+    auto push_lp = [&]() {
+        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob)});
+    };
+    auto push_dfb = [&]() {
+        for (size_t i = 0; i < e.dfb[mode].size(); i++) {
+            const LaunchDfb& L = e.dfb[mode][i];
+            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob);
+            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
+        }
+    };
+    if (analysis) { push_lp(); push_dfb(); }
+    else { push_dfb(); push_lp(); }
+    size_t need = 24 + 32 + tail_n * tail_sz;
+    for (const Item& it : items) need += 8 + it.n * it.sz;
+    *used = need;
+    if (!buf || cap < need) return CVC_ERR_CAPACITY;
+    uint8_t* o = (uint8_t*)buf;
+    uint32_t hdr[6] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
+                       (uint32_t)sizeof(DfbBJob), (uint32_t)(tail_n ? tail_sz : 0)};
+    memcpy(o, hdr, 24);
+    memcpy(o + 24, elems, 32);
+    size_t pos = 56;
+    for (const Item& it : items) {
+        uint32_t h2[2] = {(uint32_t)it.kind, (uint32_t)it.n};
+        memcpy(o + pos, h2, 8);
+        pos += 8;
+        memcpy(o + pos, it.data, it.n * it.sz);
+        pos += it.n * it.sz;
+    }
+    if (tail_n) memcpy(o + pos, tail, tail_n * tail_sz);
+    return CVC_OK;
+}
+
 cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int levels, const int* dirs_log2, int batch,
                                  int mode, void* buf, size_t cap, size_t* used) {
     if (!used || mode < 0 || mode > 3) return CVC_ERR_INVALID_ARG;
@@ -513,42 +566,22 @@ cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int lev
         elems[1] = (unsigned long long)batch * lay.total;
         ep = &plain;
     }
-    const CtEngine& e = *ep;
-    elems[2] = (unsigned long long)e.work_elems;
-    // launch order of the mode
-    struct Item { int kind; const void* data; size_t n, sz; };
-    std::vector<Item> items;
-    const bool analysis = (mode == FWD || mode == INV_ADJ);
-    auto push_lp = [&]() {
-        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob)});
-    };
-    auto push_dfb = [&]() {
-        for (size_t i = 0; i < e.dfb[mode].size(); i++) {
-            const LaunchDfb& L = e.dfb[mode][i];
-            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob);
-            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
-        }
-    };
-    if (analysis) { push_lp(); push_dfb(); }
-    else { push_dfb(); push_lp(); }
-    size_t need = 24 + 32;
-    for (const Item& it : items) need += 8 + it.n * it.sz;
-    *used = need;
-    if (!buf || cap < need) return CVC_ERR_CAPACITY;
-    uint8_t* o = (uint8_t*)buf;
-    uint32_t hdr[6] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
-                       (uint32_t)sizeof(DfbBJob), 0u};
-    memcpy(o, hdr, 24);
-    memcpy(o + 24, elems, 32);
-    size_t pos = 56;
-    for (const Item& it : items) {
-        uint32_t h2[2] = {(uint32_t)it.kind, (uint32_t)it.n};
-        memcpy(o + pos, h2, 8);
-        pos += 8;
-        memcpy(o + pos, it.data, it.n * it.sz);
-        pos += it.n * it.sz;
-    }
-    return CVC_OK;
+    elems[2] = (unsigned long long)ep->work_elems;
+    return dump_tables(*ep, mode, elems, nullptr, 0, 0, buf, cap, used);
+}
+
+cvc_status cvc_debug_scale_tables(const cvc_params* params, int n, int scale, void* buf, size_t cap,
+                                  size_t* used) {
+    if (!used || !params || n < 1) return CVC_ERR_INVALID_ARG;
+    Core core;
+    cvc_status s = core_plan(&core, params, n);
+    if (s != CVC_OK) return s;
+    if (scale < 0 || scale > core.max_levels) return CVC_ERR_INVALID_ARG;
+    const ScalePlan& sp = *core.scale[scale];
+    const unsigned long long elems[4] = {(unsigned long long)core.nplane, (unsigned long long)core.ncoef,
+                                         (unsigned long long)core.eng.work_elems, (unsigned long long)core.nplane};
+    return dump_tables(scale == 0 ? core.eng : sp.eng, INV, elems, sp.h_desc.data(), sp.h_desc.size(),
+                       sizeof(ScaleDesc), buf, cap, used);
 }
 
 }  // extern "C"

@@ -35,7 +35,6 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_rs, n);
     k.add(&c->d_pd, c->h_pd.size());
     k.add(&c->d_blk_colour, c->h_blk_colour.size());
-    k.add(&c->d_blk_colour_inv, c->h_blk_colour_inv.size());
     k.add(&c->d_blk_plane, c->h_blk_plane.size());
     k.add(&c->d_row_off, c->h_row_off.size());
     k.add(&c->d_row_w, c->h_row_w.size());
@@ -49,7 +48,14 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_rplanes, (size_t)c->nplane);
     k.add(&c->d_coef, (size_t)c->ncoef);
     k.add(&c->d_dcoef, (size_t)c->ncoef);
-    k.add(&c->d_work, (size_t)c->eng.work_elems);
+    // the sub-pyramids of every decoding scale fit in the full transform's workspace
+    long long work = c->eng.work_elems;
+    for (const auto& sp : c->scale) work = std::max(work, sp->eng.work_elems);
+    k.add(&c->d_work, (size_t)work);
+    for (const auto& sp : c->scale) {
+        k.add(&sp->d_desc, n);
+        k.add(&sp->d_blk, sp->h_blk.size());
+    }
     for (int b = 0; b < 2; b++) {
         k.add(&c->d_est_buf[b], (size_t)c->ncoef);
         k.add(&c->d_dst_buf[b], (size_t)c->ncoef);
@@ -65,7 +71,7 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_scan_tmp2, 1024 + 8);
 }
 
-size_t engine_table_bytes(const CtEngine& e) {
+size_t engine_table_bytes_of(const CtEngine& e) {
     size_t b = 0;
     for (int m = 0; m < 4; m++) {
         for (const LaunchLp& L : e.lp[m]) b += L.njobs * sizeof(LpJob) + (size_t)L.nblocks * sizeof(int) + 1024;
@@ -73,6 +79,83 @@ size_t engine_table_bytes(const CtEngine& e) {
             b += L.njobs * (L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob)) + (size_t)L.nblocks * sizeof(int) + 1024;
     }
     return b;
+}
+
+size_t engine_table_bytes(const Core* c) {
+    size_t b = engine_table_bytes_of(c->eng);
+    for (const auto& sp : c->scale) b += engine_table_bytes_of(sp->eng);
+    return b;
+}
+
+// the decoder back end of every scale 0 .. max_levels (host tables; see ScalePlan)
+cvc_status plan_scales(Core* c) {
+    c->scale.clear();
+    for (int sc = 0; sc <= c->max_levels; sc++) {
+        std::unique_ptr<ScalePlan> sp(new ScalePlan());
+        sp->h_desc.assign((size_t)c->n, ScaleDesc{});
+        std::vector<PlaneRef> sub;
+        for (int s = 0; s < c->n; s++) {
+            const cvc_params& P = c->prm[s];
+            if (P.levels < sc) continue;
+            const SDesc& D = c->sd[s];
+            const ColourGeom& g = D.cg;
+            const int f = 1 << sc;
+            ScaleDesc& Q = sp->h_desc[s];
+            Q.H = (g.H + f - 1) >> sc;
+            Q.W = (g.W + f - 1) >> sc;
+            Q.Hc = (g.Hc + f - 1) >> sc;
+            Q.Wc = (g.Wc + f - 1) >> sc;
+            Q.norm = ldexpf(1.0f, -sc);
+            Q.blk0 = (int)sp->h_blk.size();
+            // padded planes are multiples of 2^L, so these sizes are exact
+            const int hs[3] = {g.Hp >> sc, g.Hcp >> sc, g.Hcp >> sc}, ws[3] = {g.Wp >> sc, g.Wcp >> sc, g.Wcp >> sc};
+            Q.rs_y = ws[0];
+            Q.rs_c = ws[1];
+            const PlaneLayout* lays[3] = {&c->ly[s], &c->lc[s], &c->lc[s]};
+            const long long poff[3] = {D.coef_off, D.coef_off + c->ly[s].total,
+                                       D.coef_off + c->ly[s].total + c->lc[s].total};
+            if (sc == P.levels) {
+                // no level left: the lowpass bands ((H >> L) x (W >> L), dequantised) are the planes
+                Q.src = 1;
+                for (int p = 0; p < 3; p++) Q.off[p] = poff[p] + lays[p]->sb[0].off;
+            } else {
+                Q.src = 0;
+                Q.off[0] = D.plane_off;
+                Q.off[1] = Q.off[0] + (long long)hs[0] * ws[0];
+                Q.off[2] = Q.off[1] + (long long)hs[1] * ws[1];
+            }
+            if (sc > 0 && sc < P.levels) {
+                // subbands of levels sc+1..L sit in the layout in the order of the
+                // sub-pyramid's own layout, right after the lowpass: shifting the
+                // coefficient base by (first subband of level sc+1) - (lowpass size)
+                // lines them up; the lowpass keeps its own offset
+                int first = 1;
+                for (int j = 0; j < sc; j++) first += 1 << P.dirs_log2[j];
+                for (int p = 0; p < 3; p++) {
+                    const PlaneLayout& Lp = *lays[p];
+                    const long long nlow = (long long)Lp.sb[0].h * Lp.sb[0].w;
+                    PlaneRef r;
+                    memset(&r, 0, sizeof(r));
+                    r.H = hs[p];
+                    r.W = ws[p];
+                    r.L = P.levels - sc;
+                    for (int j = 0; j < r.L; j++) r.k[j] = P.dirs_log2[sc + j];
+                    r.in.b = B_OUT;
+                    r.in.off = Q.off[p];
+                    r.in.rs = ws[p];
+                    r.in.cs = 1;
+                    r.coef = poff[p] + Lp.sb[first].off - nlow;
+                    r.low_coef = poff[p] + Lp.sb[0].off;
+                    sub.push_back(r);
+                }
+            }
+            if ((long long)sp->h_blk.size() + Q.H > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
+            sp->h_blk.insert(sp->h_blk.end(), (size_t)Q.H, s);
+        }
+        if (sc > 0 && !engine_build(&sp->eng, sub, false)) return CVC_ERR_UNSUPPORTED;
+        c->scale.push_back(std::move(sp));
+    }
+    return CVC_OK;
 }
 
 template <class T>
@@ -115,6 +198,7 @@ std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, 
     std::vector<PlaneRef> planes(3);
     for (int p = 0; p < 3; p++) {
         memset(&planes[p], 0, sizeof(PlaneRef));
+        planes[p].low_coef = -1;
         planes[p].H = p == 0 ? g.Hp : g.Hcp;
         planes[p].W = p == 0 ? g.Wp : g.Wcp;
         planes[p].L = L;
@@ -129,9 +213,13 @@ std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, 
     return planes;
 }
 
-Core::~Core() {
+ScalePlan::~ScalePlan() {
     for (int m = 0; m < 4; m++)
         if (gexec[m]) cudaGraphExecDestroy(gexec[m]);
+}
+
+Core::~Core() {
+    scale.clear();   // graphs first
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (arena) cudaFree(arena);
     if (h_sc) cudaFreeHost(h_sc);
@@ -186,15 +274,11 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.hdr_bytes = 32 + 4LL * D.ncomp;
         D.max_tok = 2 * D.ncoef + 64;
         D.blk_colour = (int)c->h_blk_colour.size();
-        D.blk_colour_inv = (int)c->h_blk_colour_inv.size();
-        // colour kernels: one block per padded luma row and per padded chroma row (forward),
-        // one per frame row (inverse)
-        const long long nb_col = (long long)g.Hp + g.Hcp, nb_inv = g.H;
-        if ((long long)c->h_blk_colour.size() + nb_col > (1LL << 30) ||
-            (long long)c->h_blk_colour_inv.size() + nb_inv > (1LL << 30))
-            return CVC_ERR_UNSUPPORTED;
+        // forward colour kernel: one block per padded luma row and per padded chroma row
+        // (the inverse one, per output row, is planned per decoding scale)
+        const long long nb_col = (long long)g.Hp + g.Hcp;
+        if ((long long)c->h_blk_colour.size() + nb_col > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
         c->h_blk_colour.insert(c->h_blk_colour.end(), (size_t)nb_col, s);
-        c->h_blk_colour_inv.insert(c->h_blk_colour_inv.end(), (size_t)nb_inv, s);
         const long long poff[3] = {coef_off, coef_off + Ly.total, coef_off + Ly.total + Lc.total};
         for (int p = 0; p < 3; p++) {
             const PlaneLayout& Lp = p == 0 ? Ly : Lc;
@@ -242,14 +326,16 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
     // token positions and element offsets are 32-bit on the device
     if (sum_tok > 0xFFFFFF00LL || c->ncoef > 0x7FFFFFFFLL) return CVC_ERR_UNSUPPORTED;
     if (!engine_build(&c->eng, planes, false)) return CVC_ERR_UNSUPPORTED;
-    return CVC_OK;
+    c->max_levels = 0;
+    for (int s = 0; s < n; s++) c->max_levels = std::max(c->max_levels, params[s].levels);
+    return plan_scales(c);
 }
 
 size_t core_device_bytes(const Core* c) {
     // carve_all records where each member pointer will point; nothing is written through them here
     Carve k;
     carve_all(const_cast<Core*>(c), k);
-    return k.total + engine_table_bytes(c->eng);
+    return k.total + engine_table_bytes(c);
 }
 
 cvc_status core_alloc(Core* c) {
@@ -258,6 +344,14 @@ cvc_status core_alloc(Core* c) {
     if (!engine_build(&c->eng, planes, true)) {
         cudaGetLastError();
         return CVC_ERR_NOMEM;
+    }
+    for (size_t sc = 1; sc < c->scale.size(); sc++) {
+        CtEngine& e = c->scale[sc]->eng;
+        const std::vector<PlaneRef> sub = e.planes;
+        if (!engine_build(&e, sub, true)) {
+            cudaGetLastError();
+            return CVC_ERR_NOMEM;
+        }
     }
     if (lp_prepare() != cudaSuccess) return CVC_ERR_CUDA;
     Carve k;
@@ -277,11 +371,12 @@ cvc_status core_alloc(Core* c) {
     memset(c->h_sc, 0, sizeof(SCall) * c->n);
     memset(c->h_rs, 0, sizeof(SResult) * c->n);
     bool ok = put(c->d_sd, c->sd) && put(c->d_pd, c->h_pd) && put(c->d_blk_colour, c->h_blk_colour) &&
-              put(c->d_blk_colour_inv, c->h_blk_colour_inv) && put(c->d_blk_plane, c->h_blk_plane) &&
+              put(c->d_blk_plane, c->h_blk_plane) &&
               put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
               put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
               put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
               put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem);
+    for (const auto& sp : c->scale) ok = ok && put(sp->d_desc, sp->h_desc) && put(sp->d_blk, sp->h_blk);
     // state buffers start at zero (no frame may read them before a K-frame)
     for (int b = 0; b < 2 && ok; b++)
         ok = cudaMemset(c->d_est_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess &&
@@ -307,11 +402,19 @@ void core_reset(Core* c, int s) {
 }
 
 void core_drop_graphs(Core* c) {
-    for (int m = 0; m < 4; m++) {
-        if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
-        c->gexec[m] = nullptr;
-        c->gkernels[m] = 0;
-    }
+    for (auto& sp : c->scale)
+        for (int m = 0; m < 4; m++) {
+            if (sp->gexec[m]) cudaGraphExecDestroy(sp->gexec[m]);
+            sp->gexec[m] = nullptr;
+            sp->gkernels[m] = 0;
+        }
+}
+
+void core_scaled_size(const Core* c, int s, int scale, int* h, int* w) {
+    const ColourGeom& g = c->sd[s].cg;
+    const int f = 1 << scale;
+    *h = (g.H + f - 1) >> scale;
+    *w = (g.W + f - 1) >> scale;
 }
 
 namespace {
@@ -338,7 +441,7 @@ struct StageClock {
     } while (0)
 
 // the launch sequence of one step; *nl = kernels launched
-cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long long* nl) {
+cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool timed, long long* nl) {
     StageClock clk{c, st, timed};
     const int n = c->n;
     long long k = 0;
@@ -412,25 +515,31 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
                                                                        c->d_dcoef);
         CK(cudaGetLastError());
         clk.end(6, 2);
-        // inverse transform: DFB synthesis, then LP synthesis
+        // inverse transform of the scale: DFB synthesis, then LP synthesis
+        const ScalePlan& sp = *c->scale[scale];
+        const CtEngine* ie = scale == 0 ? &c->eng : &sp.eng;
         Bases B;
         memset(&B, 0, sizeof(B));
         B.p[B_COEF] = c->d_dcoef;
         B.p[B_WORK] = c->d_work;
         B.p[B_OUT] = c->d_rplanes;
         clk.begin(7);
-        CK(engine_run_part(&c->eng, INV, 1, B, st));
-        clk.end(7, engine_part_launches(&c->eng, INV, 1));
+        CK(engine_run_part(ie, INV, 1, B, st));
+        clk.end(7, engine_part_launches(ie, INV, 1));
         clk.begin(8);
-        CK(engine_run_part(&c->eng, INV, 0, B, st));
-        clk.end(8, engine_part_launches(&c->eng, INV, 0));
-        // rounding, chroma upsampling, inverse colour transform
+        CK(engine_run_part(ie, INV, 0, B, st));
+        clk.end(8, engine_part_launches(ie, INV, 0));
+        // normalisation, rounding, chroma upsampling, inverse colour transform
         clk.begin(9);
-        k_colour_inv_b<<<(int)c->h_blk_colour_inv.size(), 256, 0, st>>>(
-            c->d_sd, c->d_sc, c->d_rs, c->d_blk_colour_inv, c->d_rplanes);
-        CK(cudaGetLastError());
-        clk.end(9, 1);
-        k += 8 + 2 + 1 + engine_part_launches(&c->eng, INV, 1) + engine_part_launches(&c->eng, INV, 0);
+        int ncol = 0;
+        if (!sp.h_blk.empty()) {
+            k_colour_inv_b<<<(int)sp.h_blk.size(), 256, 0, st>>>(sp.d_desc, c->d_sc, c->d_rs, sp.d_blk,
+                                                                 c->d_rplanes, c->d_dcoef);
+            CK(cudaGetLastError());
+            ncol = 1;
+        }
+        clk.end(9, ncol);
+        k += 8 + 2 + ncol + engine_part_launches(ie, INV, 1) + engine_part_launches(ie, INV, 0);
     }
     CK(cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(SResult) * n, cudaMemcpyDeviceToHost, st));
     *nl = k;
@@ -439,46 +548,53 @@ cudaError_t enqueue_direct(Core* c, int mode, cudaStream_t st, bool timed, long 
 
 }  // namespace
 
-cvc_status core_capture(Core* c, int mode) {
-    if (mode < STEP_ENC || mode > STEP_ENCDEC) return CVC_ERR_INVALID_ARG;
-    if (c->gexec[mode]) return CVC_OK;
+cvc_status core_capture(Core* c, int mode, int scale) {
+    if (mode < STEP_ENC || mode > STEP_ENCDEC || scale < 0 || scale > c->max_levels) return CVC_ERR_INVALID_ARG;
+    if (mode == STEP_ENC) scale = 0;   // no decoder in the step
+    ScalePlan& sp = *c->scale[scale];
+    if (sp.gexec[mode]) return CVC_OK;
     if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
     long long nl = 0;
-    cudaError_t e = enqueue_direct(c, mode, c->cap_stream, false, &nl);
+    cudaError_t e = enqueue_direct(c, mode, scale, c->cap_stream, false, &nl);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
-    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[mode], g, 0);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&sp.gexec[mode], g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
-        c->gexec[mode] = nullptr;
+        sp.gexec[mode] = nullptr;
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    c->gkernels[mode] = nl;
+    sp.gkernels[mode] = nl;
     return CVC_OK;
 }
 
-cvc_status core_enqueue(Core* c, int mode, cudaStream_t st) {
-    if (mode < STEP_ENC || mode > STEP_ENCDEC) return CVC_ERR_INVALID_ARG;
+cvc_status core_enqueue(Core* c, int mode, cudaStream_t st, int scale) {
+    if (mode < STEP_ENC || mode > STEP_ENCDEC || scale < 0 || scale > c->max_levels) return CVC_ERR_INVALID_ARG;
+    if (mode == STEP_ENC) scale = 0;
+    // every decoder output buffer was checked for the scale the step writes
+    for (int i = 0; i < c->n; i++)
+        if (c->h_sc[i].dec_on && c->h_sc[i].dec_scale != scale) return CVC_ERR_INVALID_ARG;
     if (!c->use_graphs || c->timing) {
         long long nl = 0;
-        if (enqueue_direct(c, mode, st, c->timing, &nl) != cudaSuccess) {
+        if (enqueue_direct(c, mode, scale, st, c->timing, &nl) != cudaSuccess) {
             cudaGetLastError();
             return CVC_ERR_CUDA;
         }
         note_launches(nl);
         return CVC_OK;
     }
-    cvc_status s = core_capture(c, mode);
+    cvc_status s = core_capture(c, mode, scale);
     if (s != CVC_OK) return s;
-    if (cudaGraphLaunch(c->gexec[mode], st) != cudaSuccess) {
+    const ScalePlan& sp = *c->scale[scale];
+    if (cudaGraphLaunch(sp.gexec[mode], st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    note_launches(c->gkernels[mode]);
+    note_launches(sp.gkernels[mode]);
     return CVC_OK;
 }
 
@@ -505,7 +621,7 @@ cvc_status core_set_timing(Core* c, bool on) {
     return CVC_OK;
 }
 
-bool core_fill_call(Core* c, int s, int mode, const StreamIo& io) {
+bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale) {
     const SDesc& D = c->sd[s];
     SCall& C = c->h_sc[s];
     memset(&C, 0, sizeof(C));
@@ -521,7 +637,10 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io) {
         C.enc_index = (uint32_t)c->enc_frame[s];
     }
     if ((mode & STEP_DEC) && io.rgb_out) {
-        if (io.pitch_out < row) return false;
+        if (scale < 0 || scale > c->prm[s].levels) return false;
+        int hs = 0, ws = 0;
+        core_scaled_size(c, s, scale, &hs, &ws);
+        if (io.pitch_out < (size_t)ws * 3) return false;
         C.dec_on = 1;
         C.rgb_out = io.rgb_out;
         C.pitch_out = (long long)io.pitch_out;
@@ -534,6 +653,7 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io) {
             C.in_len = (long long)std::min<size_t>(io.in_len, (size_t)1 << 62);
         }
         C.dec_expect = c->dec_next[s];
+        C.dec_scale = scale;
     }
     C.ecur = c->ecur[s];
     C.dcur = c->dcur[s];

@@ -14,6 +14,7 @@
 // ecur / dcur only for streams whose step succeeded, so a failed or skipped
 // step leaves the stream exactly as it was.
 #pragma once
+#include <memory>
 #include <vector>
 
 #include "k_codec.cuh"
@@ -28,6 +29,27 @@ struct LaunchShape {
     int tok_blocks;  // blocks of the grid-stride token kernels of the decoder
 };
 
+// The decoder's back end at one pyramid scale s (§3.3: every LP scale can
+// be decoded on its own).  Scale s keeps the lowpass and levels s+1..L of
+// each plane, which are the coefficients of the (Hp >> s) x (Wp >> s)
+// level-s lowpass image under an (L - s)-level transform; their inverse,
+// normalised by 2^-s, is the output at ceil(H / 2^s) x ceil(W / 2^s).  A
+// stream with L = s has no transform left: its lowpass bands are the planes.
+// Scale 0 is the full decode (the core's own engine); every scale has its
+// inverse colour table and its own step graphs.  Parsing, dequantisation
+// and the decoder state cover every coefficient at every scale, so a stream
+// may change scale from frame to frame.
+struct ScalePlan {
+    CtEngine eng;                    // s > 0: sub-pyramids of the streams with L > s
+    std::vector<ScaleDesc> h_desc;   // one per stream (streams with L < s: unused)
+    std::vector<int> h_blk;          // inverse colour launch: block -> stream
+    ScaleDesc* d_desc = nullptr;     // in the core's arena
+    int* d_blk = nullptr;
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};   // index = StepMode
+    long long gkernels[4] = {0, 0, 0, 0};
+    ~ScalePlan();
+};
+
 struct Core {
     int n = 0;
     std::vector<cvc_params> prm;
@@ -37,11 +59,13 @@ struct Core {
     int nrows = 0, ncomp = 0, nplanes = 0, lowcols = 0;
     // host tables (kept for the size estimate and the upload)
     std::vector<PDesc> h_pd;
-    std::vector<int> h_blk_colour, h_blk_colour_inv, h_blk_plane;
+    std::vector<int> h_blk_colour, h_blk_plane;
     std::vector<long long> h_row_off, h_comp_elem;
     std::vector<int> h_row_w, h_row_stream, h_comp_row0, h_comp_stream;
     std::vector<uint8_t> h_row_low, h_comp_low;
     CtEngine eng;
+    int max_levels = 0;
+    std::vector<std::unique_ptr<ScalePlan>> scale;   // index = scale, 0 .. max_levels
     LaunchShape shape{8, 148 * 8};
     // device memory: one arena for everything but the engine's job tables
     void* arena = nullptr;
@@ -50,7 +74,7 @@ struct Core {
     SCall* d_sc = nullptr;
     SResult* d_rs = nullptr;
     PDesc* d_pd = nullptr;
-    int *d_blk_colour = nullptr, *d_blk_colour_inv = nullptr, *d_blk_plane = nullptr;
+    int *d_blk_colour = nullptr, *d_blk_plane = nullptr;
     long long *d_row_off = nullptr, *d_comp_elem = nullptr;
     int *d_row_w = nullptr, *d_row_stream = nullptr, *d_comp_row0 = nullptr, *d_comp_stream = nullptr;
     uint8_t *d_row_low = nullptr, *d_comp_low = nullptr;
@@ -65,11 +89,9 @@ struct Core {
     // per-stream coder state (host side)
     std::vector<long long> enc_frame, dec_next;
     std::vector<int> ecur, dcur;
-    // CUDA graphs of the step modes (index = StepMode)
+    // CUDA graphs of the step modes: one set per decoding scale (in ScalePlan)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-    long long gkernels[4] = {0, 0, 0, 0};
     // stage timing (direct launches only)
     bool timing = false;
     cudaEvent_t ev[CVC_NUM_STAGES][2] = {};
@@ -93,10 +115,11 @@ size_t core_device_bytes(const Core* c);
 cvc_status core_alloc(Core* c);
 // reset the coder state of stream s (s < 0: all)
 void core_reset(Core* c, int s);
-// enqueue one step (the records in h_sc must be filled); no synchronisation
-cvc_status core_enqueue(Core* c, int mode, cudaStream_t st);
+// enqueue one step whose decoders output pyramid scale `scale` (the records
+// in h_sc must be filled for that scale); no synchronisation
+cvc_status core_enqueue(Core* c, int mode, cudaStream_t st, int scale = 0);
 // capture the graph of a step mode ahead of its first use (no launch)
-cvc_status core_capture(Core* c, int mode);
+cvc_status core_capture(Core* c, int mode, int scale = 0);
 // after the step completed: collect stage times
 void core_collect(Core* c);
 cvc_status core_set_timing(Core* c, bool on);
@@ -114,7 +137,10 @@ struct StreamIo {
     uint8_t* rgb_out;
     size_t pitch_out;
 };
-bool core_fill_call(Core* c, int s, int mode, const StreamIo& io);
+// (the decoder's output at pyramid scale `scale`, 0 <= scale <= the stream's levels)
+bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale = 0);
+// output size of stream s at a decoding scale
+void core_scaled_size(const Core* c, int s, int scale, int* h, int* w);
 // statuses of stream s after the step completed; commits the state on success
 void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
                  int* dec_type, unsigned* dec_index);

@@ -262,7 +262,8 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 sbi += (size_t)1 << kj;
                 View spatial_prev = (j == 1) ? mk(spatial_base, P.in.off, P.in.rs, 1)
                                              : mk(B_WORK, coff[j - 1], wj, 1);
-                View low = (j == P.L) ? mk(B_COEF, P.coef + Ly.sb[0].off, wj / 2, 1) : mk(B_WORK, coff[j], wj / 2, 1);
+                const long long low_at = P.low_coef >= 0 ? P.low_coef : P.coef + Ly.sb[0].off;
+                View low = (j == P.L) ? mk(B_COEF, low_at, wj / 2, 1) : mk(B_WORK, coff[j], wj / 2, 1);
                 View det = (kj == 0) ? mk(B_COEF, slots[0], wj, 1) : mk(B_WORK, doff[j], wj, 1);
                 LpJob J;
                 memset(&J, 0, sizeof(J));

@@ -104,6 +104,8 @@ struct PlaneRef {
     View in;          // plane for forward / inverse-adjoint input (rs = pitch), or output for inverse
     long long coef;   // coefficient block offset in B_COEF
     long long work;   // workspace offset in B_WORK
+    long long low_coef;   // >= 0: the lowpass lives here instead of at coef (a sub-pyramid of a
+                          // larger layout keeps its lowpass apart from its subbands)
 };
 
 struct LaunchLp {

@@ -71,36 +71,39 @@ __device__ __forceinline__ int round_clamp(float v, int lo, int hi) {
     return (int)r;
 }
 
-// Decoder end: round (ties away from zero) and clamp the reconstructed
-// planes, bilinear (9,3,3,1)/16 chroma upsampling with centred siting and
-// clamped edges, inverse YCoCg-R, clamp to [0, 255].  One block per output
-// row.  A stream whose bitstream was rejected leaves its output untouched.
-__global__ void k_colour_inv_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+// Decoder end: normalise by the scale's DC gain, round (ties away from zero)
+// and clamp the reconstructed planes, bilinear (9,3,3,1)/16 chroma
+// upsampling with centred siting and clamped edges, inverse YCoCg-R, clamp to
+// [0, 255].  One block per output row.  A stream whose bitstream was
+// rejected leaves its output untouched.
+__global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall* __restrict__ sc,
                                const SResult* __restrict__ rs, const int* __restrict__ blk_stream,
-                               const float* __restrict__ planes) {
+                               const float* __restrict__ rplanes, const float* __restrict__ dcoef) {
     const int s = blk_stream[blockIdx.x];
     const SCall& C = sc[s];
     if (!C.dec_on || rs[s].dec_err) return;
-    const SDesc& D = sd[s];
-    const ColourGeom g = D.cg;
-    const int y = blockIdx.x - D.blk_colour_inv;
-    const float* Yrow = planes + D.plane_off + (long long)y * g.Wp;
-    const float* Co = planes + D.plane_off + (long long)g.Hp * g.Wp;
-    const float* Cg = Co + (long long)g.Hcp * g.Wcp;
-    const int i0 = min(y >> 1, g.Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, g.Hc - 1) : max((y >> 1) - 1, 0);
-    const float* P[2][2] = {{Co + (long long)i0 * g.Wcp, Co + (long long)i1 * g.Wcp},
-                            {Cg + (long long)i0 * g.Wcp, Cg + (long long)i1 * g.Wcp}};
+    const ScaleDesc& D = sdesc[s];
+    const float* base = D.src ? dcoef : rplanes;
+    const float norm = D.norm;
+    const int y = blockIdx.x - D.blk0;
+    const float* Yrow = base + D.off[0] + (long long)y * D.rs_y;
+    const float* Co = base + D.off[1];
+    const float* Cg = base + D.off[2];
+    const int Hc = D.Hc, Wc = D.Wc;
+    const int i0 = min(y >> 1, Hc - 1), i1 = (y & 1) ? min((y >> 1) + 1, Hc - 1) : max((y >> 1) - 1, 0);
+    const float* P[2][2] = {{Co + (long long)i0 * D.rs_c, Co + (long long)i1 * D.rs_c},
+                            {Cg + (long long)i0 * D.rs_c, Cg + (long long)i1 * D.rs_c}};
     uint8_t* orow = C.rgb_out + (long long)y * C.pitch_out;
-    for (int x = threadIdx.x; x < g.W; x += blockDim.x) {
-        const int yy = round_clamp(Yrow[x], 0, 255);
-        const int j0 = min(x >> 1, g.Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, g.Wc - 1) : max((x >> 1) - 1, 0);
+    for (int x = threadIdx.x; x < D.W; x += blockDim.x) {
+        const int yy = round_clamp(Yrow[x] * norm, 0, 255);
+        const int j0 = min(x >> 1, Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, Wc - 1) : max((x >> 1) - 1, 0);
         int c[2];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
-            const int a = round_clamp(P[q][0][j0], -255, 255);
-            const int b = round_clamp(P[q][1][j0], -255, 255);
-            const int d = round_clamp(P[q][0][j1], -255, 255);
-            const int e = round_clamp(P[q][1][j1], -255, 255);
+            const int a = round_clamp(P[q][0][j0] * norm, -255, 255);
+            const int b = round_clamp(P[q][1][j0] * norm, -255, 255);
+            const int d = round_clamp(P[q][0][j1] * norm, -255, 255);
+            const int e = round_clamp(P[q][1][j1] * norm, -255, 255);
             c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
         }
         const int t = yy - (c[1] >> 1);

@@ -39,7 +39,21 @@ struct SDesc {
     int comp0, ncomp;      // its components in the component table
     long long hdr_bytes;   // 32 + 4 * ncomp
     long long max_tok;     // largest valid token count of one frame
-    int blk_colour, blk_colour_inv;   // first block of the stream in those launches
+    int blk_colour;        // first block of the stream in the forward colour launch
+};
+
+// the decoder's output stage of one stream at pyramid scale s (s = 0: full
+// resolution).  Scale s reconstructs the level-s lowpass image of every
+// plane: the frame and its 4:2:0 chroma shrink to ceil(n / 2^s).
+struct ScaleDesc {
+    int H, W;              // output frame at this scale
+    int Hc, Wc;            // its 4:2:0 chroma
+    int rs_y, rs_c;        // row pitch of the luma / chroma planes read
+    int src;               // 0: reconstructed planes; 1: the decoded lowpass bands themselves (s = L)
+    int blk0;              // first block (output row) of the stream
+    long long off[3];      // Y, Co, Cg in that buffer
+    float norm;            // 2^-s: the DC gain of s pyramid levels (exact)
+    int pad;
 };
 
 // per stream, refreshed every call
@@ -56,6 +70,8 @@ struct SCall {
     uint32_t enc_index;
     int dcur;
     long long dec_expect;  // frame index a P-frame must carry; -1: a K-frame is required
+    int dec_scale;         // pyramid scale of the decoder's output (its buffer was checked for it)
+    int pad;
 };
 
 // per stream, written by the device every call
@@ -96,8 +112,8 @@ struct CompTable {
 constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS * ELEM_PER_THREAD;
 
 __global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes);
-__global__ void k_colour_inv_b(const SDesc* sd, const SCall* sc, const SResult* rs, const int* blk_stream,
-                               const float* planes);
+__global__ void k_colour_inv_b(const ScaleDesc* sdesc, const SCall* sc, const SResult* rs, const int* blk_stream,
+                               const float* rplanes, const float* dcoef);
 __global__ void k_quant_b(const float* coef, int16_t* est0, int16_t* est1, const PDesc* pd, const int* blk_plane,
                           const SDesc* sd, const SCall* sc, int16_t* res, SResult* out);
 __global__ void k_unquant_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, const int* blk_plane,

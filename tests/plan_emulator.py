@@ -41,17 +41,42 @@ PASSES = {0: (1, 0.5, -0.5, 1.0, 1.0), 3: (0, 1.0, 1.0, 2.0, -1.0),
           1: (0, 1.0, -1.0, 2.0, 1.0), 2: (1, 0.5, 0.5, 1.0, -1.0)}
 
 
-def tables(mode, params=None, h=0, w=0, levels=0, dirs=(), batch=1):
-    lib = L.lib()
+# decoder output stage of one stream at one pyramid scale
+SCALEDESC = np.dtype([("H", "<i4"), ("W", "<i4"), ("Hc", "<i4"), ("Wc", "<i4"), ("rs_y", "<i4"), ("rs_c", "<i4"),
+                      ("src", "<i4"), ("blk0", "<i4"), ("off", "<i8", (3,)), ("norm", "<f4"), ("pad", "<i4")])
+
+
+def _dump(call):
     used = ctypes.c_size_t(0)
-    pp = ctypes.byref(params) if params is not None else None
-    st = lib.cvc_debug_plan_tables(pp, h, w, levels, L.ints(dirs), batch, mode, None, 0, ctypes.byref(used))
+    st = call(None, 0, ctypes.byref(used))
     assert st == 3, st
     buf = (ctypes.c_uint8 * used.value)()
-    st = lib.cvc_debug_plan_tables(pp, h, w, levels, L.ints(dirs), batch, mode, buf, used.value, ctypes.byref(used))
+    st = call(buf, used.value, ctypes.byref(used))
     assert st == 0, st
-    raw = bytes(buf)
-    magic, nl, lpb, ab, bb, _ = np.frombuffer(raw[:24], "<u4")
+    return bytes(buf)
+
+
+def tables(mode, params=None, h=0, w=0, levels=0, dirs=(), batch=1):
+    lib = L.lib()
+    pp = ctypes.byref(params) if params is not None else None
+    raw = _dump(lambda buf, cap, used: lib.cvc_debug_plan_tables(pp, h, w, levels, L.ints(dirs), batch, mode,
+                                                                 buf, cap, used))
+    elems, launches, tail = _parse(raw)
+    assert len(tail) == 0
+    return elems, launches
+
+
+def scale_tables(params, n, scale):
+    """(elems, inverse launches, output records) of the decoder at pyramid scale `scale`."""
+    lib = L.lib()
+    raw = _dump(lambda buf, cap, used: lib.cvc_debug_scale_tables(params, n, scale, buf, cap, used))
+    elems, launches, tail = _parse(raw)
+    return elems, launches, np.frombuffer(tail, SCALEDESC)
+
+
+def _parse(raw):
+    magic, nl, lpb, ab, bb, tail_sz = np.frombuffer(raw[:24], "<u4")
+    assert tail_sz in (0, SCALEDESC.itemsize)
     assert magic == 0x43564350 and lpb == LPJOB.itemsize and ab == AJOB.itemsize and bb == BJOB.itemsize
     elems = np.frombuffer(raw[24:56], "<u8").astype(np.int64)
     pos = 56
@@ -63,8 +88,7 @@ def tables(mode, params=None, h=0, w=0, levels=0, dirs=(), batch=1):
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
         launches.append((int(kind), jobs))
-    assert pos == len(raw)
-    return elems, launches
+    return elems, launches, raw[pos:]
 
 
 def _stage_a_pass(img, stage, odd, alpha, gamma):

@@ -110,3 +110,74 @@ def test_mixed_stream_batch_of_the_streaming_workload_is_in_bounds():
     for mode in (0, 1):
         elems, launches = E.tables(mode, params=first, batch=64)
         E.check_only(elems, launches, mode)
+
+
+SCALED = [(99, 77, 2, [2, 2]), (64, 48, 3, [3, 2, 2]), (40, 30, 1, [0]), (176, 144, 3, [3, 0, 2]),
+          (96, 64, 2, [1, 0])]
+
+
+@pytest.mark.parametrize("scale", [0, 1, 2, 3])
+def test_scaled_decoder_tables(scale):
+    """The decoder back end at pyramid scale s (§3.3) over a batch of mixed
+    streams: the inverse-transform tables of the sub-pyramids stay in bounds
+    and, executed on random coefficients, give every stream's level-s lowpass
+    planes (the oracle's inverse of the lowpass and levels s+1..L, over 2^s);
+    the output records address those planes (or, at s = L, the lowpass band
+    itself) with the right sizes and block offsets."""
+    import ctypes
+    prms = (L.Params * len(SCALED))(*[L.Params(w, h, Lv, L.ints(k), 8, 1, 0.0, 8, 1) for w, h, Lv, k in SCALED])
+    elems, launches, desc = E.scale_tables(ctypes.cast(prms, ctypes.POINTER(L.Params)), len(SCALED), scale)
+    assert len(desc) == len(SCALED)
+    rng = np.random.default_rng(scale)
+    bufs = _buffers(elems)
+    bufs[1][:] = rng.uniform(-60, 60, elems[1])
+    E.run(1, elems, launches, bufs)
+    coef_off = plane_off = blk = 0
+    for i, (w, h, Lv, k) in enumerate(SCALED):
+        oc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 8)
+        dims = [(oc.Hp, oc.Wp), (oc.Hcp, oc.Wcp), (oc.Hcp, oc.Wcp)]
+        lays = [O.layout(H, W, Lv, k) for H, W in dims]
+        if Lv >= scale:
+            Q = desc[i]
+            f = 1 << scale
+            hc, wc = (h + 1) // 2, (w + 1) // 2
+            assert (Q["H"], Q["W"], Q["Hc"], Q["Wc"]) == ((h + f - 1) // f, (w + f - 1) // f,
+                                                          (hc + f - 1) // f, (wc + f - 1) // f)
+            assert Q["blk0"] == blk and Q["norm"] == 2.0 ** -scale
+            blk += Q["H"]
+            src = bufs[1] if Q["src"] else bufs[3]
+            assert Q["src"] == (scale == Lv)
+            poff = coef_off
+            for p, ((H, W), lay) in enumerate(zip(dims, lays)):
+                cp = bufs[1][poff:poff + lay["total"]]
+                sb = lay["subbands"]
+                nlow = sb[0]["h"] * sb[0]["w"]
+                if scale == Lv:
+                    ref = cp[:nlow].reshape(sb[0]["h"], sb[0]["w"])
+                else:
+                    first = 1 + sum(1 << k[j] for j in range(scale))
+                    sub = np.concatenate([cp[:nlow], cp[sb[first]["off"]:]])
+                    ref = O.ct(1, sub, H >> scale, W >> scale, Lv - scale, k[scale:]).reshape(H >> scale, W >> scale)
+                ref = ref * 2.0 ** -scale
+                rows, cols = (Q["H"], Q["W"]) if p == 0 else (Q["Hc"], Q["Wc"])
+                rs = Q["rs_y"] if p == 0 else Q["rs_c"]
+                assert rs == ref.shape[1] and rows <= ref.shape[0] and cols <= ref.shape[1]
+                idx = Q["off"][p] + np.arange(ref.shape[0])[:, None] * rs + np.arange(ref.shape[1])[None, :]
+                assert idx.min() >= 0 and idx.max() < len(src)
+                got = src[idx] * float(Q["norm"])
+                assert np.abs(got - ref).max() < 1e-8 * max(1.0, np.abs(ref).max()), (i, p)
+                poff += lay["total"]
+        coef_off += sum(l["total"] for l in lays)
+        plane_off += sum(H * W for H, W in dims)
+    assert elems[1] == coef_off and elems[3] == plane_off
+
+
+def test_scale_tables_refuse_a_scale_beyond_every_stream():
+    import ctypes
+    prms = (L.Params * 2)(L.Params(99, 77, 2, L.ints([2, 2]), 8, 1, 0.0, 8, 1),
+                          L.Params(40, 30, 1, L.ints([0]), 8, 1, 0.0, 8, 1))
+    used = ctypes.c_size_t(0)
+    lib = L.lib()
+    assert lib.cvc_debug_scale_tables(prms, 2, 3, None, 0, ctypes.byref(used)) == 1
+    assert lib.cvc_debug_scale_tables(prms, 2, -1, None, 0, ctypes.byref(used)) == 1
+    assert lib.cvc_debug_scale_tables(prms, 2, 2, None, 0, ctypes.byref(used)) == 3
