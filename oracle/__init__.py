@@ -88,6 +88,8 @@ def lib():
                                 _IP, ctypes.c_void_p]
         L.or_decode.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, _U8, ctypes.c_void_p]
         L.or_decode_scaled.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_void_p]
+        L.or_stream_drop.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_long,
+                                     ctypes.POINTER(ctypes.c_long)]
         _lib = L
     return _lib
 
@@ -372,6 +374,16 @@ class Codec:
             ny, nc = Hp * Wp, Hcp * Wcp
             return rgb, (pl[:ny].reshape(Hp, Wp), pl[ny:ny + nc].reshape(Hcp, Wcp), pl[ny + nc:].reshape(Hcp, Wcp))
         return rgb
+
+    def drop_levels(self, stream, drop):
+        """The frame without its finest `drop` levels (§3.3); raises on a bad stream or drop."""
+        s = np.ascontiguousarray(stream, dtype=np.uint8)
+        out = np.zeros(max(1, s.size), np.uint8)
+        n = ctypes.c_long(0)
+        st = lib().or_stream_drop(self._h, s, s.size, drop, out, out.size, ctypes.byref(n))
+        if st:
+            raise RuntimeError("oracle stream drop failed: status %d" % st)
+        return out[:n.value].copy()
 
     def decode_status(self, stream):
         s = np.ascontiguousarray(stream, dtype=np.uint8)

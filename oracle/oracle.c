@@ -670,6 +670,7 @@ struct or_codec {
     int16_t* dec_state;
     long enc_frame;
     long dec_next;  /* index the next P-frame must carry; -1: a K-frame is required */
+    int dec_floor;  /* finest levels 1..dec_floor of the decoder state are missing */
 };
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -707,7 +708,7 @@ void or_codec_destroy(or_codec* c) {
     if (!c) return;
     free(c->enc_state); free(c->dec_state); free(c);
 }
-void or_codec_reset(or_codec* c) { c->enc_frame = 0; c->dec_next = -1; }
+void or_codec_reset(or_codec* c) { c->enc_frame = 0; c->dec_next = -1; c->dec_floor = 0; }
 long or_codec_coeff_count(const or_codec* c) { return c->ncoef; }
 int or_codec_ncomp(const or_codec* c) { return c->ncomp; }
 long or_codec_max_stream(const or_codec* c) { return 32 + 4L * c->ncomp + 2L * 2L * c->ncoef; }
@@ -864,6 +865,11 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
     if (get32(in + 28) != (unsigned long)c->ncomp) return OR_ECORRUPT;
     long fidx = (long)get32(in + 8);
     if (type == 1 && fidx != c->dec_next) return OR_ESTATE;
+    /* §3.3: a stream may arrive without its finest `drop` levels; it then serves
+     * scales >= drop only, and a P-frame needs the state of levels > scale */
+    int drop = (int)get16(in + 26);
+    if (drop > c->L) return OR_ECORRUPT;
+    if (drop > scale || (type == 1 && c->dec_floor > scale)) return OR_ESTATE;
     if (len < 32 + 4L * c->ncomp) return OR_ECORRUPT;
     long nt = 0;
     for (int j = 0; j < c->ncomp; j++) nt += (long)get32(in + 32 + 4 * j);
@@ -879,7 +885,11 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
         long n = (long)s->h * s->w;
         int16_t* tk = (int16_t*)malloc(sizeof(int16_t) * (size_t)(cnt + 1));
         for (long i = 0; i < cnt; i++) tk[i] = (int16_t)get16(tp + 2 * (t0 + i));
-        if (type == 0 && s->kind == 0) {
+        if (s->kind != 0 && s->level <= drop) {
+            /* dropped component: no tokens; its residual is zero */
+            if (cnt != 0) st = OR_ECORRUPT;
+            else memset(r + base + s->off, 0, sizeof(int16_t) * (size_t)n);
+        } else if (type == 0 && s->kind == 0) {
             if (cnt != n) st = OR_ECORRUPT;
             else memcpy(r + base + s->off, tk, sizeof(int16_t) * (size_t)n);
         } else {
@@ -961,6 +971,46 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
     or_ycocgr_inverse(Y, Co, Cg, n, rgb);
     memcpy(c->dec_state, q, sizeof(int16_t) * (size_t)c->ncoef);
     c->dec_next = fidx + 1;
+    c->dec_floor = type == 0 ? drop : (drop > c->dec_floor ? drop : c->dec_floor);
     free(r); free(q); free(co); free(pl); free(Y); free(Co); free(Cg); free(Co2); free(Cg2);
+    return OR_OK;
+}
+
+/* §3.3, §3.9: a receiver that wants scale s needs only the lowpass and levels
+ * s+1..L, so the finest `drop` levels can be left out of a frame without
+ * re-encoding: their token counts become 0, their tokens go, and header bytes
+ * 26-27 record `drop`.  A stream already missing d0 levels can only lose more. */
+int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uint8_t* out, long cap,
+                   long* out_len) {
+    if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
+    if (in[7] != c->L || get32(in + 28) != (unsigned long)c->ncomp) return OR_ECORRUPT;
+    if (len < 32 + 4L * c->ncomp) return OR_ECORRUPT;
+    int d0 = (int)get16(in + 26);
+    if (drop < d0 || drop > c->L) return OR_EINVAL;
+    long ntot = 0, nkeep = 0;
+    for (int j = 0; j < c->ncomp; j++) {
+        long base, cnt = (long)get32(in + 32 + 4 * j);
+        const or_subband* s = comp_sb(c, j, &base);
+        ntot += cnt;
+        if (!(s->kind != 0 && s->level <= drop)) nkeep += cnt;
+    }
+    long hdr = 32 + 4L * c->ncomp;
+    if (hdr + 2 * ntot > len) return OR_ECORRUPT;
+    *out_len = hdr + 2 * nkeep;
+    if (*out_len > cap) return OR_ECAPACITY;
+    memcpy(out, in, 32);
+    put16(out + 26, (unsigned)drop);
+    long src = hdr, dst = hdr;
+    for (int j = 0; j < c->ncomp; j++) {
+        long base, cnt = (long)get32(in + 32 + 4 * j);
+        const or_subband* s = comp_sb(c, j, &base);
+        int keep = !(s->kind != 0 && s->level <= drop);
+        put32(out + 32 + 4 * j, keep ? (unsigned long)cnt : 0UL);
+        if (keep) {
+            memcpy(out + dst, in + src, (size_t)(2 * cnt));
+            dst += 2 * cnt;
+        }
+        src += 2 * cnt;
+    }
     return OR_OK;
 }

@@ -126,5 +126,15 @@ int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* pl
  * ceil(H/2^s) x ceil(W/2^s) RGB.  planes_out receives the three normalised
  * (Hp>>s) x (Wp>>s), (Hcp>>s) x (Wcp>>s) planes. */
 int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_t* rgb, double* planes_out);
+/* a frame without its finest `drop` levels (§3.3: a receiver drops what refers
+ * to resolutions above the one it wants): those components keep a zero token
+ * count and lose their tokens, header bytes 26-27 hold `drop`.  Such a frame
+ * decodes at scales >= drop only; after it the decoder state of levels
+ * 1..drop is missing (a K-frame sets the missing levels to exactly its own
+ * drop), and a P-frame decodes only at scales >= that floor.
+ * Returns OR_OK, OR_EINVAL (drop < the frame's own drop or > L), OR_ECORRUPT,
+ * OR_ECAPACITY (*out_len = bytes needed). */
+int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uint8_t* out, long cap,
+                   long* out_len);
 
 #endif

@@ -83,3 +83,82 @@ def test_invalid_scale_is_refused():
     s, _ = _codec(w, h, L, k).encode(frame)
     with pytest.raises(Exception):
         _codec(w, h, L, k).decode(s, scale=3)
+
+
+def _sequence(w, h, L, k, n, seed, kint=3):
+    frames = S.SyntheticVideo(S.spec_for(w, h, seed=seed)).frames(n)
+    enc = _codec(w, h, L, k, kint=kint)
+    return [enc.encode(f)[0] for f in frames]
+
+
+def _dropped_token_bytes(stream, w, h, L, k, drop):
+    """bytes of the tokens of components of levels 1..drop (from the count table)"""
+    c = _codec(w, h, L, k)
+    lays = [O.layout(c.Hp, c.Wp, L, k)] + [O.layout(c.Hcp, c.Wcp, L, k)] * 2
+    counts = np.frombuffer(bytes(stream[32:32 + 4 * c.ncomp]), "<u4")
+    j = n = 0
+    for lay in lays:
+        for sb in lay["subbands"]:
+            if sb["kind"] != 0 and sb["level"] <= drop:
+                n += 2 * int(counts[j])
+            j += 1
+    return n
+
+
+@pytest.mark.parametrize("w,h,L,k", [(176, 144, 3, [3, 2, 2]), (99, 77, 2, [2, 0])])
+def test_dropping_fine_levels_leaves_every_coarser_scale_unchanged(w, h, L, k):
+    """§3.3: a receiver at scale s can be sent the stream without levels 1..s.
+    Decoding a K/P sequence with levels 1..d dropped gives, at every scale
+    s >= d, exactly the frames of the complete sequence at that scale; the
+    dropped stream is shorter by exactly the dropped components' tokens."""
+    seq = _sequence(w, h, L, k, 5, seed=11)
+    for d in range(L + 1):
+        dropped = [_codec(w, h, L, k).drop_levels(s, d) for s in seq]
+        for s, t in zip(seq, dropped):
+            assert t.size == s.size - _dropped_token_bytes(s, w, h, L, k, d)
+            assert t[26] | (t[27] << 8) == d
+            if d == 0:
+                assert np.array_equal(s, t)
+        for sc in range(d, L + 1):
+            full, part = _codec(w, h, L, k), _codec(w, h, L, k)
+            for s, t in zip(seq, dropped):
+                assert np.array_equal(full.decode(s, scale=sc), part.decode(t, scale=sc)), (d, sc)
+
+
+def test_dropped_levels_bound_the_decodable_scales():
+    w, h, L, k = 176, 144, 3, [3, 2, 2]
+    seq = _sequence(w, h, L, k, 5, seed=12)          # K P P K P
+    c = _codec(w, h, L, k)
+    d2 = [c.drop_levels(s, 2) for s in seq]
+    dec = _codec(w, h, L, k)
+    with pytest.raises(RuntimeError, match="status 9"):
+        dec.decode(d2[0], scale=1)                   # the stream lacks level 2
+    dec.decode(d2[0], scale=2)                       # K-frame without levels 1-2
+    with pytest.raises(RuntimeError, match="status 9"):
+        dec.decode(seq[1], scale=0)                  # complete P-frame, but no state for levels 1-2
+    dec.decode(seq[1], scale=2)
+    dec.decode(seq[2], scale=3)
+    ref = _codec(w, h, L, k)
+    for s in seq:
+        r = ref.decode(s)
+    # a complete K-frame restores every level: full-scale decoding resumes
+    assert np.array_equal(dec.decode(seq[3]), _codec(w, h, L, k).decode(seq[3]))
+    assert np.array_equal(dec.decode(seq[4]), r)
+
+
+def test_stream_drop_only_removes():
+    w, h, L, k = 99, 77, 2, [2, 2]
+    s = _sequence(w, h, L, k, 1, seed=13)[0]
+    c = _codec(w, h, L, k)
+    d1 = c.drop_levels(s, 1)
+    assert np.array_equal(c.drop_levels(d1, 2), c.drop_levels(s, 2))
+    assert np.array_equal(c.drop_levels(d1, 1), d1)
+    with pytest.raises(RuntimeError, match="status 1"):
+        c.drop_levels(d1, 0)
+    with pytest.raises(RuntimeError, match="status 1"):
+        c.drop_levels(s, 3)
+    # the lowpass components always stay; everything of level 1 is gone
+    counts = np.frombuffer(bytes(d1[32:32 + 4 * c.ncomp]), "<u4")
+    lay = O.layout(c.Hp, c.Wp, L, k)
+    for j, sb in enumerate(lay["subbands"]):
+        assert (counts[j] == 0) == (sb["level"] == 1)
