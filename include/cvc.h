@@ -215,6 +215,24 @@ cvc_status cvc_decode_frame(cvc_codec* codec, const uint8_t* d_in, size_t in_len
 cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t in_len, int scale,
                                    uint8_t* d_rgb, size_t pitch_bytes, cvc_stream_t stream);
 
+/* Transmission-side scalability (§3.3: a receiver's resolution is served by
+ * dropping what refers to higher resolutions, without re-encoding).  Copies
+ * the frame `in` (HOST memory, in_len bytes, from a codec with `params`)
+ * into `out` (HOST memory) without the components of its finest `drop`
+ * levels: their token counts become 0, their tokens are left out, and
+ * header bytes 26-27 (0 in a complete frame) hold `drop`.  A frame that
+ * already left out d0 levels can only lose more (drop >= d0).  `out` may be
+ * `in` (the tokens only move forward).  Host work only, no device call.
+ * A decoder accepts such a frame at scales >= drop (cvc_decode_frame_scaled;
+ * STATE below that).  Afterwards the decoder state of levels 1..drop is
+ * missing: a P-frame then decodes only at scales >= the largest drop since
+ * the last K-frame (STATE otherwise), and a K-frame resets that floor to its
+ * own drop.  Errors: INVALID_ARG (bad params, drop outside [d0, levels]),
+ * CORRUPT (not a frame of these params), CAPACITY (*out_len = bytes needed),
+ * UNSUPPORTED.                                                               */
+cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, size_t in_len, int drop,
+                                  uint8_t* out, size_t out_cap, size_t* out_len);
+
 /* Inspection of the last encode / decode (for parity checks): copies into
  * d_out (device, at least cap_elems floats)
  *   which = 0: the encoder's padded float planes Y, Co, Cg (before the transform)

@@ -121,6 +121,7 @@ def lib():
         L.cvc_encode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
         L.cvc_decode_frame_scaled.argtypes = [_P, _P, _SZ, _I, _P, _SZ, _P]
+        L.cvc_stream_drop_levels.argtypes = [ctypes.POINTER(Params), _P, _SZ, _I, _P, _SZ, ctypes.POINTER(_SZ)]
         L.cvc_codec_inspect.argtypes = [_P, _I, _P, _SZ, _P]
         L.cvc_codec_set_timing.argtypes = [_P, _I]
         L.cvc_codec_timing.argtypes = [_P, _P, _P]

@@ -5,6 +5,7 @@ of the codec runs in the library's CUDA kernels (see include/cvc.h).
 """
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib as _L
@@ -125,6 +126,7 @@ class Codec:
         prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval)
         self.width, self.height, self.levels, self.dirs = width, height, levels, list(dirs_log2)
         self.qph, self.qpl, self.threshold, self.key_interval = qph, prm.qpl, threshold, key_interval
+        self._prm = prm
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_create")
         self._h = p
@@ -181,6 +183,12 @@ class Codec:
                  "cvc_decode_frame_scaled")
         return out
 
+    def drop_levels(self, stream_bytes, drop):
+        """The frame without its finest `drop` levels (cvc_stream_drop_levels, host memory):
+        stream_bytes is a host uint8 array or CPU tensor; returns a numpy uint8 array that
+        decodes at scales >= drop."""
+        return drop_levels(self._prm, stream_bytes, drop)
+
     def inspect(self, which):
         """0: encoder padded planes, 1: encoder coefficients, 2: decoder reconstructed planes (float32)."""
         n = self.ncoef if which == 1 else self.nplane
@@ -203,6 +211,22 @@ class Codec:
         ny, nc = self.Hp * self.Wp, self.Hcp * self.Wcp
         return (flat[:ny].view(self.Hp, self.Wp), flat[ny:ny + nc].view(self.Hcp, self.Wcp),
                 flat[ny + nc:].view(self.Hcp, self.Wcp))
+
+
+def drop_levels(params, stream_bytes, drop):
+    """cvc_stream_drop_levels for a frame of a stream with `params` (a cvc_params or a dict of
+    Codec keyword arguments); host bytes in, numpy uint8 out."""
+    if isinstance(params, dict):
+        params = _L.params(**params)
+    if isinstance(stream_bytes, torch.Tensor):
+        stream_bytes = stream_bytes.cpu().numpy()
+    src = np.ascontiguousarray(stream_bytes, dtype=np.uint8)
+    out = np.empty(max(1, src.size), np.uint8)
+    n = ctypes.c_size_t(0)
+    _L.check(_L.lib().cvc_stream_drop_levels(ctypes.byref(params), src.ctypes.data, src.size, int(drop),
+                                             out.ctypes.data, out.size, ctypes.byref(n)),
+             "cvc_stream_drop_levels")
+    return out[:n.value].copy()
 
 
 def _info(fn, h, i=None):

@@ -313,6 +313,54 @@ cvc_status cvc_decode_frame_scaled(cvc_codec* c, const uint8_t* d_in, size_t in_
     return ds;
 }
 
+cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, size_t in_len, int drop,
+                                  uint8_t* out, size_t out_cap, size_t* out_len) {
+    if (!params || !in || !out_len || !codec_params_valid(params)) return CVC_ERR_INVALID_ARG;
+    ColourGeom g;
+    PlaneLayout ly, lc;
+    if (!codec_geometry(params, &g) || !make_layout(g.Hp, g.Wp, params->levels, params->dirs_log2, &ly) ||
+        !make_layout(g.Hcp, g.Wcp, params->levels, params->dirs_log2, &lc))
+        return CVC_ERR_UNSUPPORTED;
+    // pyramid level of each component, in stream order (Y, Co, Cg; layout order)
+    std::vector<int> level;
+    for (int p = 0; p < 3; p++)
+        for (const SubbandG& sb : (p == 0 ? ly : lc).sb) level.push_back(sb.kind == 0 ? 0 : sb.level);
+    const size_t ncomp = level.size(), hdr = 32 + 4 * ncomp;
+    auto rd32 = [&](size_t at) {
+        return (uint32_t)in[at] | ((uint32_t)in[at + 1] << 8) | ((uint32_t)in[at + 2] << 16) |
+               ((uint32_t)in[at + 3] << 24);
+    };
+    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[7] != params->levels || rd32(28) != ncomp)
+        return CVC_ERR_CORRUPT;
+    const int d0 = in[26] | (in[27] << 8);
+    if (drop < d0 || drop > params->levels) return CVC_ERR_INVALID_ARG;
+    unsigned long long all = 0, keep = 0;
+    for (size_t j = 0; j < ncomp; j++) {
+        const uint32_t n = rd32(32 + 4 * j);
+        all += n;
+        if (level[j] == 0 || level[j] > drop) keep += n;
+    }
+    if (hdr + 2 * all > in_len) return CVC_ERR_CORRUPT;
+    *out_len = hdr + 2 * keep;
+    if (!out || out_cap < *out_len) return CVC_ERR_CAPACITY;
+    memmove(out, in, 32);
+    out[26] = (uint8_t)(drop & 255);
+    out[27] = (uint8_t)(drop >> 8);
+    size_t src = hdr, dst = hdr;
+    for (size_t j = 0; j < ncomp; j++) {
+        const uint32_t n = rd32(32 + 4 * j);
+        const bool kept = level[j] == 0 || level[j] > drop;
+        const uint32_t w = kept ? n : 0;
+        memcpy(out + 32 + 4 * j, &w, 4);   // little-endian host
+        if (kept) {
+            memmove(out + dst, in + src, 2 * (size_t)n);
+            dst += 2 * (size_t)n;
+        }
+        src += 2 * (size_t)n;
+    }
+    return CVC_OK;
+}
+
 cvc_status cvc_codec_set_timing(cvc_codec* c, int on) {
     if (!c) return CVC_ERR_INVALID_ARG;
     return core_set_timing(&c->core, on != 0);

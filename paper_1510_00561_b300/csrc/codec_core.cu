@@ -43,6 +43,8 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_comp_row0, c->h_comp_row0.size());
     k.add(&c->d_comp_stream, c->h_comp_stream.size());
     k.add(&c->d_comp_low, c->h_comp_low.size());
+    k.add(&c->d_comp_level, c->h_comp_level.size());
+    k.add(&c->d_comp_plane, c->h_comp_plane.size());
     k.add(&c->d_comp_elem, c->h_comp_elem.size());
     k.add(&c->d_planes, (size_t)c->nplane);
     k.add(&c->d_rplanes, (size_t)c->nplane);
@@ -282,6 +284,15 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         const long long poff[3] = {coef_off, coef_off + Ly.total, coef_off + Ly.total + Lc.total};
         for (int p = 0; p < 3; p++) {
             const PlaneLayout& Lp = p == 0 ? Ly : Lc;
+            // levels 1..d follow the lowpass in the layout
+            D.pstart[p] = poff[p] - coef_off;
+            D.nlow[p] = (long long)Lp.sb[0].h * Lp.sb[0].w;
+            for (int d = 0; d <= CVC_MAX_LEVELS; d++) {
+                long long a = 0;
+                for (const SubbandG& sb : Lp.sb)
+                    if (sb.kind != 0 && sb.level <= d) a += (long long)sb.h * sb.w;
+                D.absent[d][p] = a;
+            }
             PDesc pd;
             memset(&pd, 0, sizeof(pd));
             pd.coef_off = poff[p];
@@ -299,6 +310,8 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             for (const SubbandG& sb : Lp.sb) {
                 c->h_comp_row0.push_back((int)c->h_row_off.size());
                 c->h_comp_low.push_back(sb.kind == 0);
+                c->h_comp_level.push_back((uint8_t)sb.level);
+                c->h_comp_plane.push_back((uint8_t)p);
                 c->h_comp_stream.push_back(s);
                 c->h_comp_elem.push_back(poff[p] - coef_off + sb.off);
                 for (int r = 0; r < sb.h; r++) {
@@ -375,7 +388,8 @@ cvc_status core_alloc(Core* c) {
               put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
               put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
               put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
-              put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem);
+              put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
+              put(c->d_comp_level, c->h_comp_level) && put(c->d_comp_plane, c->h_comp_plane);
     for (const auto& sp : c->scale) ok = ok && put(sp->d_desc, sp->h_desc) && put(sp->d_blk, sp->h_blk);
     // state buffers start at zero (no frame may read them before a K-frame)
     for (int b = 0; b < 2 && ok; b++)
@@ -390,6 +404,7 @@ cvc_status core_alloc(Core* c) {
     c->dec_next.assign(c->n, -1);
     c->ecur.assign(c->n, 0);
     c->dcur.assign(c->n, 0);
+    c->dec_floor.assign(c->n, 0);
     return CVC_OK;
 }
 
@@ -398,6 +413,7 @@ void core_reset(Core* c, int s) {
         if (s < 0 || s == i) {
             c->enc_frame[i] = 0;
             c->dec_next[i] = -1;
+            c->dec_floor[i] = 0;
         }
 }
 
@@ -449,7 +465,8 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
     CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->d_rs, 0, sizeof(SResult) * n, st));
     const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->nrows};
-    const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem, c->ncomp};
+    const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
+                       c->d_comp_level, c->d_comp_plane, c->ncomp};
     const int rpb = c->shape.rle_rows;
     const int rgrid = (int)cdiv(c->nrows, rpb);
     if (mode & STEP_ENC) {
@@ -492,7 +509,7 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         const int tg = c->shape.tok_blocks;
         // parse, token -> element counts, positions, checks, scatter of non-zero codes
         clk.begin(5);
-        k_dec_parse_b<<<n, 1024, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_comp_tok, c->d_rs);
+        k_dec_parse_b<<<n, 1024, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, ct, c->d_comp_tok, c->d_rs);
         k_dec_base_b<<<1, 32, 0, st>>>(c->d_sd, n, c->d_rs, c->d_tok_base);
         k_dec_contrib_b<<<tg, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_tok_base, n, c->d_comp_tok, ct,
                                             c->d_contrib, c->d_rs);
@@ -654,6 +671,7 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale) {
         }
         C.dec_expect = c->dec_next[s];
         C.dec_scale = scale;
+        C.dec_floor = c->dec_floor[s];
     }
     C.ecur = c->ecur[s];
     C.dcur = c->dcur[s];
@@ -689,6 +707,8 @@ void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, siz
             didx = R.dec_index;
             c->dcur[s] = 1 - c->dcur[s];
             c->dec_next[s] = (long long)R.dec_index + 1;
+            const int drop = (int)R.dec_drop;
+            c->dec_floor[s] = R.dec_type == 0 ? drop : std::max(c->dec_floor[s], drop);
         }
     }
     if (enc) *enc = es;

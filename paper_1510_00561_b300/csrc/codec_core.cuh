@@ -62,7 +62,7 @@ struct Core {
     std::vector<int> h_blk_colour, h_blk_plane;
     std::vector<long long> h_row_off, h_comp_elem;
     std::vector<int> h_row_w, h_row_stream, h_comp_row0, h_comp_stream;
-    std::vector<uint8_t> h_row_low, h_comp_low;
+    std::vector<uint8_t> h_row_low, h_comp_low, h_comp_level, h_comp_plane;
     CtEngine eng;
     int max_levels = 0;
     std::vector<std::unique_ptr<ScalePlan>> scale;   // index = scale, 0 .. max_levels
@@ -77,7 +77,7 @@ struct Core {
     int *d_blk_colour = nullptr, *d_blk_plane = nullptr;
     long long *d_row_off = nullptr, *d_comp_elem = nullptr;
     int *d_row_w = nullptr, *d_row_stream = nullptr, *d_comp_row0 = nullptr, *d_comp_stream = nullptr;
-    uint8_t *d_row_low = nullptr, *d_comp_low = nullptr;
+    uint8_t *d_row_low = nullptr, *d_comp_low = nullptr, *d_comp_level = nullptr, *d_comp_plane = nullptr;
     float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
     int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
     uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
@@ -89,6 +89,7 @@ struct Core {
     // per-stream coder state (host side)
     std::vector<long long> enc_frame, dec_next;
     std::vector<int> ecur, dcur;
+    std::vector<int> dec_floor;   // finest levels whose decoder state is missing (dropped in transmission)
     // CUDA graphs of the step modes: one set per decoding scale (in ScalePlan)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;

@@ -378,11 +378,12 @@ __device__ __forceinline__ long long dec_in_len(const SDesc& D, const SCall& C, 
 
 // one block per stream: header check, component token offsets
 __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                              const SResult* __restrict__ enc, uint32_t* __restrict__ comp_tok, SResult* out) {
+                              const SResult* __restrict__ enc, CompTable ct, uint32_t* __restrict__ comp_tok,
+                              SResult* out) {
     const int s = blockIdx.x;
     const SCall& C = sc[s];
     __shared__ uint32_t s_carry;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_drop;
     __shared__ uint32_t s_part[1024];
     if (!C.dec_on) {
         if (threadIdx.x == 0) out[s].dec_tokens = 0;
@@ -410,8 +411,15 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
                 if (in[16 + i] != e.dirs[i]) bad |= EF_MISMATCH;
             uint32_t fidx = rd32(in + 8);
             if (!bad && type == 1 && (C.dec_expect < 0 || (long long)fidx != C.dec_expect)) bad |= EF_STATE;
+            // a frame without its finest `drop` levels serves scales >= drop; a P-frame
+            // also needs the decoder state of the levels above the scale
+            const int drop = in[26] | (in[27] << 8);
+            if (drop > e.levels) bad |= EF_CORRUPT;
+            if (!bad && (drop > C.dec_scale || (type == 1 && C.dec_floor > C.dec_scale))) bad |= EF_STATE;
             out[s].dec_type = type;
             out[s].dec_index = fidx;
+            out[s].dec_drop = bad ? 0 : (uint32_t)drop;
+            s_drop = drop;
         }
         s_bad = bad;
         s_carry = 0;
@@ -421,9 +429,14 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
         if (threadIdx.x == 0) out[s].dec_err |= (uint32_t)s_bad;
         return;
     }
+    const int drop = s_drop;
     for (int base = 0; base < ncomp; base += blockDim.x) {
         int i = base + threadIdx.x;
         uint32_t v = i < ncomp ? rd32(in + 32 + 4 * i) : 0;
+        if (v != 0 && i < ncomp) {
+            const int lv = ct.level[D.comp0 + i];
+            if (lv >= 1 && lv <= drop) atomicOr(&out[s].dec_err, EF_CORRUPT);   // dropped components hold no tokens
+        }
         s_part[threadIdx.x] = v;
         __syncthreads();
         for (int d = 1; d < (int)blockDim.x; d <<= 1) {
@@ -545,7 +558,23 @@ __global__ void k_dec_contrib_b(const SDesc* __restrict__ sd, const SCall* __res
     }
 }
 
-// every component must expand to exactly its number of codes
+// The decoded codes of a frame that dropped its finest d levels are dense:
+// each plane's lowpass, then its levels d+1..L.  Element offsets inside the
+// stream: layout -> dense (for a component's first element) and back.
+__device__ __forceinline__ long long absent_before(const SDesc& D, int d, int q) {
+    long long a = 0;
+    for (int i = 0; i < q; i++) a += D.absent[d][i];
+    return a;
+}
+__device__ __forceinline__ long long dense_to_layout(const SDesc& D, int d, long long p) {
+    const long long ds1 = D.pstart[1] - D.absent[d][0];
+    const long long ds2 = D.pstart[2] - D.absent[d][0] - D.absent[d][1];
+    const int q = p >= ds2 ? 2 : (p >= ds1 ? 1 : 0);
+    const long long u = p - (q == 2 ? ds2 : (q == 1 ? ds1 : 0));
+    return D.pstart[q] + (u < D.nlow[q] ? u : u + D.absent[d][q]);
+}
+
+// every component must expand to exactly its number of codes (none if dropped)
 __global__ void k_dec_check_b(const SDesc* __restrict__ sd, const SResult* __restrict__ rs,
                               const uint32_t* __restrict__ tok_base, const uint32_t* __restrict__ comp_tok,
                               const uint32_t* __restrict__ pos, CompTable ct, SResult* out) {
@@ -554,10 +583,16 @@ __global__ void k_dec_check_b(const SDesc* __restrict__ sd, const SResult* __res
     const int s = ct.stream[c];
     if (rs[s].dec_tokens == 0) return;        // not decoding, or the header was rejected
     const SDesc& D = sd[s];
+    const int d = min((int)rs[s].dec_drop, CVC_MAX_LEVELS);
+    const int q = ct.plane[c], lv = ct.level[c];
+    long long before = absent_before(D, d, q);
+    if (lv >= 1 && lv <= d) before += ct.elem[c] - D.pstart[q] - D.nlow[q];
+    else if (lv > d) before += D.absent[d][q];
     const uint32_t b = tok_base[s];
     const uint32_t p0 = pos[b];
-    if ((long long)(pos[b + comp_tok[c]] - p0) != ct.elem[c]) atomicOr(&out[s].dec_err, EF_CORRUPT);
-    if (c == D.comp0 + D.ncomp - 1 && (long long)(pos[b + rs[s].dec_tokens] - p0) != D.ncoef)
+    if ((long long)(pos[b + comp_tok[c]] - p0) != ct.elem[c] - before) atomicOr(&out[s].dec_err, EF_CORRUPT);
+    if (c == D.comp0 + D.ncomp - 1 &&
+        (long long)(pos[b + rs[s].dec_tokens] - p0) != D.ncoef - absent_before(D, d, 3))
         atomicOr(&out[s].dec_err, EF_CORRUPT);
 }
 
@@ -577,7 +612,9 @@ __global__ void k_dec_scatter_b(const SDesc* __restrict__ sd, const SCall* __res
             const int16_t v = rd16(tok + 2LL * k.t);
             const bool raw = rs[k.s].dec_type == 0 && ct.low[k.c];
             const bool count = !raw && k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0;
-            const long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
+            long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
+            const int d = min((int)rs[k.s].dec_drop, CVC_MAX_LEVELS);
+            if (d > 0) p = dense_to_layout(D, d, p);
             if ((raw || (v != 0 && !count)) && p >= 0 && p < D.ncoef) res[D.coef_off + p] = v;
         }
     }

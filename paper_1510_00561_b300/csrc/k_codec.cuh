@@ -40,6 +40,11 @@ struct SDesc {
     long long hdr_bytes;   // 32 + 4 * ncomp
     long long max_tok;     // largest valid token count of one frame
     int blk_colour;        // first block of the stream in the forward colour launch
+    // planes Y, Co, Cg inside the stream's coefficients: start, lowpass size, and
+    // the elements of levels 1..d (absent from a frame that dropped d levels)
+    long long pstart[3];
+    long long nlow[3];
+    long long absent[CVC_MAX_LEVELS + 1][3];
 };
 
 // the decoder's output stage of one stream at pyramid scale s (s = 0: full
@@ -71,7 +76,7 @@ struct SCall {
     int dcur;
     long long dec_expect;  // frame index a P-frame must carry; -1: a K-frame is required
     int dec_scale;         // pyramid scale of the decoder's output (its buffer was checked for it)
-    int pad;
+    int dec_floor;         // finest levels 1..dec_floor of the decoder state are missing
 };
 
 // per stream, written by the device every call
@@ -79,6 +84,8 @@ struct SResult {
     uint32_t enc_err, dec_err;
     uint32_t enc_tokens;     // tokens of the encoded frame
     uint32_t dec_type, dec_index, dec_tokens;
+    uint32_t dec_drop;       // finest levels the decoded frame left out
+    uint32_t pad;
 };
 
 // per plane (three per stream)
@@ -105,6 +112,8 @@ struct CompTable {
     const uint8_t* low;
     const int* stream;
     const long long* elem;    // element offset of the component inside its stream
+    const uint8_t* level;     // 0 lowpass, j = pyramid level j (1 finest)
+    const uint8_t* plane;     // 0 Y, 1 Co, 2 Cg
     int ncomp;
 };
 
@@ -125,8 +134,8 @@ __global__ void k_rle_write_b(const int16_t* res, RowTable rt, const SDesc* sd, 
                               const uint32_t* tokoff, SResult* out);
 __global__ void k_stream_header_b(const SDesc* sd, const SCall* sc, const uint32_t* tokoff, CompTable ct,
                                   SResult* out);
-__global__ void k_dec_parse_b(const SDesc* sd, const SCall* sc, const SResult* enc, uint32_t* comp_tok,
-                              SResult* out);
+__global__ void k_dec_parse_b(const SDesc* sd, const SCall* sc, const SResult* enc, CompTable ct,
+                              uint32_t* comp_tok, SResult* out);
 __global__ void k_dec_base_b(const SDesc* sd, int nstreams, const SResult* rs, uint32_t* tok_base);
 __global__ void k_dec_contrib_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tok_base,
                                 int nstreams, const uint32_t* comp_tok, CompTable ct, uint32_t* contrib,

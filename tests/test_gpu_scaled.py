@@ -206,3 +206,86 @@ def test_invalid_scales_are_refused():
     # nothing was decoded: the stream still needs its K-frame and decodes normally
     out = g.decode(s.clone(), scale=1)
     assert out.shape == (39, 50, 3)
+
+
+def _host(s):
+    return s.cpu().numpy()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("kw", [QCIF, VGA], ids=["qcif", "vga"])
+def test_dropped_levels_decode_like_complete_frames(kw):
+    """§3.3: frames without their finest d levels (cvc_stream_drop_levels)
+    decode at every scale s >= d exactly as the complete frames do, and
+    match the oracle's decode of the same dropped frames."""
+    frames = _frames(kw, 5, seed=25)
+    kw = dict(kw, key_interval=3)                     # K P P K P
+    streams = _encode_all(kw, frames)
+    L = kw["levels"]
+    g = _gpu(kw)
+    for d in range(1, L + 1):
+        dropped = [g.drop_levels(_host(s), d) for s in streams]
+        for s, t in zip(streams, dropped):
+            assert t.size < s.numel()
+        for sc in range(d, L + 1):
+            full, part, og = _gpu(kw), _gpu(kw), _oracle(kw)
+            for t, (s, x) in enumerate(zip(streams, dropped)):
+                a = full.decode(s.clone(), scale=sc)
+                b = part.decode(_dev(x), scale=sc)
+                assert torch.equal(a, b), (d, sc, t)
+                if sc == d:
+                    _check_frame(part, b.cpu().numpy(), sc, og, x, kw)
+                else:
+                    og.decode(x, scale=sc)
+
+
+def test_dropped_levels_bound_the_decodable_scales():
+    kw = dict(QCIF, key_interval=3)
+    streams = _encode_all(kw, _frames(kw, 5, seed=26))      # K P P K P
+    g = _gpu(kw)
+    d2 = [_dev(g.drop_levels(_host(s), 2)) for s in streams]
+    dec = _gpu(kw)
+    with pytest.raises(CvcError) as e:
+        dec.decode(d2[0], scale=1)                           # the frame lacks level 2
+    assert e.value.status == 9
+    dec.decode(d2[0], scale=2)
+    with pytest.raises(CvcError) as e:
+        dec.decode(streams[1].clone(), scale=0)              # no state for levels 1-2
+    assert e.value.status == 9
+    dec.decode(streams[1].clone(), scale=2)
+    dec.decode(streams[2].clone(), scale=3)
+    ref = _gpu(kw)
+    for s in streams:
+        last = ref.decode(s.clone()).clone()
+    # a complete K-frame restores every level
+    assert torch.equal(dec.decode(streams[3].clone()), _gpu(kw).decode(streams[3].clone()))
+    assert torch.equal(dec.decode(streams[4].clone()), last)
+    # a corrupt drop count is refused
+    bad = streams[0].clone()
+    bad[26] = 7
+    with pytest.raises(CvcError) as e:
+        _gpu(kw).decode(bad, scale=3)
+    assert e.value.status == 5
+
+
+def test_batch_with_different_drops_per_stream():
+    cfgs = [QCIF, VGA, QCIF, VGA]
+    drops = [0, 1, 2, 2]
+    T = 3
+    frames = [_frames(kw, T, seed=40 + i) for i, kw in enumerate(cfgs)]
+    streams = [_encode_all(kw, fr) for kw, fr in zip(cfgs, frames)]
+    g = [_gpu(kw) for kw in cfgs]
+    for scale in (2, 3):
+        b = Batch(cfgs)
+        plain = [_gpu(kw) for kw in cfgs]
+        for t in range(T):
+            ins = [_dev(g[i].drop_levels(_host(streams[i][t]), drops[i])) for i in range(len(cfgs))]
+            outs = [torch.zeros(b.scaled_size(i, scale) + (3,), dtype=torch.uint8, device="cuda")
+                    for i in range(len(cfgs))]
+            res = b.step(2, streams_in=ins, rgb_out=outs, scale=scale)
+            for i in range(len(cfgs)):
+                assert res[i]["dec_status"] == 0
+                assert torch.equal(outs[i], plain[i].decode(streams[i][t].clone(), scale=scale)), (scale, t, i)
