@@ -88,6 +88,11 @@ def lib():
                                 _IP, ctypes.c_void_p]
         L.or_decode.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, _U8, ctypes.c_void_p]
         L.or_decode_scaled.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_void_p]
+        L.or_codec_set_motion.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_motion_search.argtypes = [_U8, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")]
+        L.or_encode_from_coeffs_luma.argtypes = [ctypes.c_void_p, _F, _U8, _U8, ctypes.c_long,
+                                                 ctypes.POINTER(ctypes.c_long), _IP]
         L.or_stream_drop.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_long,
                                      ctypes.POINTER(ctypes.c_long)]
         _lib = L
@@ -97,6 +102,18 @@ def lib():
 def _ints(seq):
     arr = (ctypes.c_int * max(6, len(seq)))(*seq)
     return arr
+
+
+def motion_search(cur, prev, range_):
+    """§3.2 full-search block matching of two luma planes (uint8, same shape); returns
+    the (nby, nbx, 2) int8 field of (dy, dx)."""
+    cur = np.ascontiguousarray(cur, dtype=np.uint8)
+    prev = np.ascontiguousarray(prev, dtype=np.uint8)
+    H, W = cur.shape
+    nby, nbx = (H + 15) // 16, (W + 15) // 16
+    mv = np.zeros(nby * nbx * 2, np.int8)
+    lib().or_motion_search(cur.ravel(), prev.ravel(), H, W, range_, mv)
+    return mv.reshape(nby, nbx, 2)
 
 
 def cdf97():
@@ -299,16 +316,20 @@ def rle_expand(tokens, n):
 class Codec:
     """The oracle codec: one video stream, encoder and decoder state."""
 
-    def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10):
+    def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10,
+                 motion_range=0):
         if qpl is None:
             qpl = max(1, qph // 14)
         self.width, self.height, self.levels = width, height, levels
         self.dirs = list(dirs_log2)
         self.qph, self.qpl, self.threshold, self.key_interval = qph, qpl, threshold, key_interval
+        self.motion_range = motion_range
         self._h = lib().or_codec_create(width, height, levels, _ints(self.dirs), qph, qpl,
                                         ctypes.c_float(threshold), key_interval)
         if not self._h:
             raise ValueError("oracle codec: invalid parameters")
+        if lib().or_codec_set_motion(self._h, motion_range):
+            raise ValueError("oracle codec: invalid motion range")
         self.ncoef = lib().or_codec_coeff_count(self._h)
         self.ncomp = lib().or_codec_ncomp(self._h)
         self.max_stream = lib().or_codec_max_stream(self._h)
@@ -346,13 +367,20 @@ class Codec:
         res = (out[:n.value].copy(), ft.value)
         return res + (co,) if want_coeffs else res
 
-    def encode_from_coeffs(self, coeffs_f32):
+    def encode_from_coeffs(self, coeffs_f32, luma=None):
+        """The entropy side from given coefficients; `luma` (the frame's padded luma plane,
+        Hp x Wp, values 0..255) is needed by a codec with a motion range."""
         cf = np.ascontiguousarray(coeffs_f32, dtype=np.float32).ravel()
         assert cf.size == self.ncoef
         out = np.zeros(self.max_stream, np.uint8)
         n = ctypes.c_long(0)
         ft = ctypes.c_int(0)
-        st = lib().or_encode_from_coeffs(self._h, cf, out, out.size, ctypes.byref(n), ctypes.byref(ft))
+        if luma is not None:
+            lu = np.ascontiguousarray(luma, dtype=np.uint8).ravel()
+            assert lu.size == self.Hp * self.Wp
+            st = lib().or_encode_from_coeffs_luma(self._h, cf, lu, out, out.size, ctypes.byref(n), ctypes.byref(ft))
+        else:
+            st = lib().or_encode_from_coeffs(self._h, cf, out, out.size, ctypes.byref(n), ctypes.byref(ft))
         if st:
             raise RuntimeError("oracle encode failed: status %d" % st)
         return out[:n.value].copy(), ft.value

@@ -671,6 +671,9 @@ struct or_codec {
     long enc_frame;
     long dec_next;  /* index the next P-frame must carry; -1: a K-frame is required */
     int dec_floor;  /* finest levels 1..dec_floor of the decoder state are missing */
+    int range;      /* motion search range W (0: zero-motion P-frames) */
+    int nby, nbx;   /* 16 x 16 luma blocks */
+    uint8_t* enc_luma;   /* the previous frame's padded luma (encoder) */
 };
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -706,12 +709,55 @@ or_codec* or_codec_create(int width, int height, int levels, const int* dirs, in
 
 void or_codec_destroy(or_codec* c) {
     if (!c) return;
-    free(c->enc_state); free(c->dec_state); free(c);
+    free(c->enc_state); free(c->dec_state); free(c->enc_luma); free(c);
+}
+
+int or_codec_set_motion(or_codec* c, int range) {
+    if (range < 0 || range > OR_MAX_RANGE) return OR_EINVAL;
+    c->range = range;
+    c->nby = (c->Hp + 15) / 16;
+    c->nbx = (c->Wp + 15) / 16;
+    free(c->enc_luma);
+    c->enc_luma = range ? (uint8_t*)calloc((size_t)c->Hp * c->Wp, 1) : NULL;
+    return OR_OK;
+}
+
+/* §3.2: full-search block matching on luma (see oracle.h) */
+void or_motion_search(const uint8_t* cur, const uint8_t* prev, int H, int W, int range, int8_t* mv) {
+    int nby = (H + 15) / 16, nbx = (W + 15) / 16;
+    for (int by = 0; by < nby; by++)
+        for (int bx = 0; bx < nbx; bx++) {
+            int y0 = 16 * by, x0 = 16 * bx;
+            int bh = H - y0 < 16 ? H - y0 : 16, bw = W - x0 < 16 ? W - x0 : 16;
+            long best = -1;
+            int bdy = 0, bdx = 0;
+            for (int dy = -range; dy <= range; dy++)
+                for (int dx = -range; dx <= range; dx++) {
+                    if (y0 + dy < 0 || y0 + dy + bh > H || x0 + dx < 0 || x0 + dx + bw > W) continue;
+                    long sse = 0;
+                    for (int y = 0; y < bh; y++)
+                        for (int x = 0; x < bw; x++) {
+                            long d = (long)cur[(long)(y0 + y) * W + x0 + x] -
+                                     (long)prev[(long)(y0 + dy + y) * W + x0 + dx + x];
+                            sse += d * d;
+                        }
+                    int better = best < 0 || sse < best;
+                    if (!better && sse == best) {
+                        int m = abs(dy) + abs(dx), bm = abs(bdy) + abs(bdx);
+                        better = m < bm;   /* equal norms: the earlier candidate stays */
+                    }
+                    if (better) { best = sse; bdy = dy; bdx = dx; }
+                }
+            mv[2 * (by * nbx + bx)] = (int8_t)bdy;
+            mv[2 * (by * nbx + bx) + 1] = (int8_t)bdx;
+        }
 }
 void or_codec_reset(or_codec* c) { c->enc_frame = 0; c->dec_next = -1; c->dec_floor = 0; }
 long or_codec_coeff_count(const or_codec* c) { return c->ncoef; }
 int or_codec_ncomp(const or_codec* c) { return c->ncomp; }
-long or_codec_max_stream(const or_codec* c) { return 32 + 4L * c->ncomp + 2L * 2L * c->ncoef; }
+long or_codec_max_stream(const or_codec* c) {
+    return 32 + 4L * c->ncomp + 2L * 2L * c->ncoef + (c->range ? 2L * c->nby * c->nbx : 0);
+}
 void or_codec_dims(const or_codec* c, int* out) { out[0] = c->Hp; out[1] = c->Wp; out[2] = c->Hcp; out[3] = c->Wcp; }
 
 void or_codec_planes(const or_codec* c, const uint8_t* rgb, double* y, double* co, double* cg) {
@@ -750,6 +796,42 @@ static const or_subband* comp_sb(const or_codec* c, int j, long* base) {
     return &c->lc.sb[j % c->lc.nsub];
 }
 
+static int ilog2(long v) { int e = 0; while ((1L << e) < v) e++; return e; }
+
+/* §3.7: the motion-compensated prediction of component j from the previous
+ * frame's codes `prev` (whole-frame array).  One element of the component
+ * stands for 2^ey x 2^ex luma samples (its plane's size over its own, times 2
+ * for chroma); element (i, j) takes the vector of the luma block holding its
+ * first luma sample (i 2^ey, j 2^ex), scaled to the component by 2^-ey, 2^-ex
+ * and rounded half away from zero, and reads prev at the displaced element,
+ * clamped to the component. */
+static long rshift_round(long v, int e) {
+    if (e == 0) return v;
+    long a = v < 0 ? -v : v;
+    a = (a + (1L << (e - 1))) >> e;
+    return v < 0 ? -a : a;
+}
+static void mc_predict(const or_codec* c, int j, const int16_t* prev, const int8_t* mv, int16_t* pred) {
+    long base;
+    const or_subband* s = comp_sb(c, j, &base);
+    int chroma = j >= c->ly.nsub;
+    int ey = ilog2((chroma ? c->Hcp : c->Hp) / s->h) + chroma;
+    int ex = ilog2((chroma ? c->Wcp : c->Wp) / s->w) + chroma;
+    const int16_t* P = prev + base + s->off;
+    int16_t* Q = pred + base + s->off;
+    for (int i = 0; i < s->h; i++)
+        for (int k = 0; k < s->w; k++) {
+            long by = ((long)i << ey) >> 4, bx = ((long)k << ex) >> 4;
+            if (by > c->nby - 1) by = c->nby - 1;
+            if (bx > c->nbx - 1) bx = c->nbx - 1;
+            const int8_t* v = mv + 2 * (by * c->nbx + bx);
+            long si = i + rshift_round(v[0], ey), sk = k + rshift_round(v[1], ex);
+            si = si < 0 ? 0 : (si > s->h - 1 ? s->h - 1 : si);
+            sk = sk < 0 ? 0 : (sk > s->w - 1 ? s->w - 1 : sk);
+            Q[(long)i * s->w + k] = P[si * s->w + sk];
+        }
+}
+
 /* §3.7: frame i (counted from the last reset) is a K-frame iff i is a
  * multiple of the key interval.  K-frame: every lowpass column is replaced by
  * its first difference (each element minus the element above), subbands pass
@@ -759,7 +841,14 @@ static const or_subband* comp_sb(const or_codec* c, int j, long* base) {
  * stored raw, every other component is run-length coded.                    */
 int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long cap,
                           long* out_len, int* frame_type) {
-    int type = (c->enc_frame % c->kint) == 0 ? 0 : 1;
+    if (c->range) return OR_EINVAL;   /* motion search needs the frame's luma */
+    return or_encode_from_coeffs_luma(c, coeffs, NULL, out, cap, out_len, frame_type);
+}
+
+int or_encode_from_coeffs_luma(or_codec* c, const float* coeffs, const uint8_t* luma, uint8_t* out, long cap,
+                               long* out_len, int* frame_type) {
+    if (c->range && !luma) return OR_EINVAL;
+    int type = (c->enc_frame % c->kint) == 0 ? 0 : (c->range ? 2 : 1);
     int16_t* q = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
     int16_t* r = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
     int ovf = 0;
@@ -773,6 +862,16 @@ int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long c
         }
     }
     if (ovf) { free(q); free(r); return OR_EOVERFLOW; }
+    /* P-frame with motion: the prediction of every component (§3.2, §3.7) */
+    long nmv = (long)c->nby * c->nbx;
+    int8_t* mv = NULL;
+    int16_t* pred = NULL;
+    if (type == 2) {
+        mv = (int8_t*)malloc((size_t)(2 * nmv));
+        pred = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+        or_motion_search(luma, c->enc_luma, c->Hp, c->Wp, c->range, mv);
+        for (int j = 0; j < c->ncomp; j++) mc_predict(c, j, c->enc_state, mv, pred);
+    }
     for (int j = 0; j < c->ncomp; j++) {
         long base;
         const or_subband* s = comp_sb(c, j, &base);
@@ -780,7 +879,8 @@ int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long c
             for (int b = 0; b < s->w; b++) {
                 long idx = base + s->off + (long)a * s->w + b;
                 int v;
-                if (type == 1) v = q[idx] - c->enc_state[idx];
+                if (type == 2) v = q[idx] - pred[idx];
+                else if (type == 1) v = q[idx] - c->enc_state[idx];
                 else if (s->kind == 0 && a > 0) v = q[idx] - q[idx - s->w];
                 else v = q[idx];
                 r[idx] = (int16_t)(uint16_t)(v & 0xFFFF);
@@ -789,7 +889,7 @@ int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long c
     /* bitstream: 32-byte header, ncomp u32 token counts, int16 tokens */
     long need = 32 + 4L * c->ncomp;
     int16_t* tok = (int16_t*)malloc(sizeof(int16_t) * (size_t)(2 * c->ncoef + 16));
-    long* counts = (long*)calloc((size_t)c->ncomp, sizeof(long));
+    long* counts = (long*)calloc((size_t)(unsigned)c->ncomp, sizeof(long));
     long nt = 0;
     for (int j = 0; j < c->ncomp; j++) {
         long base;
@@ -803,9 +903,10 @@ int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long c
         counts[j] = nt - start;
     }
     need += 2 * nt;
+    if (type == 2) need += 2 * nmv;   /* the motion vectors follow the tokens */
     *out_len = need;
     if (frame_type) *frame_type = type;
-    if (need > cap) { free(q); free(r); free(tok); free(counts); return OR_ECAPACITY; }
+    if (need > cap) { free(q); free(r); free(tok); free(counts); free(mv); free(pred); return OR_ECAPACITY; }
     memset(out, 0, 32);
     out[0] = 'C'; out[1] = 'V'; out[2] = 'C'; out[3] = '1';
     put16(out + 4, 1);
@@ -821,9 +922,11 @@ int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long c
     for (int j = 0; j < c->ncomp; j++) put32(out + 32 + 4 * j, (unsigned long)counts[j]);
     uint8_t* tp = out + 32 + 4 * c->ncomp;
     for (long i = 0; i < nt; i++) put16(tp + 2 * i, (unsigned)(uint16_t)tok[i]);
+    if (type == 2) memcpy(tp + 2 * nt, mv, (size_t)(2 * nmv));
     memcpy(c->enc_state, q, sizeof(int16_t) * (size_t)c->ncoef);
+    if (c->range) memcpy(c->enc_luma, luma, (size_t)c->Hp * c->Wp);
     c->enc_frame += 1;
-    free(q); free(r); free(tok); free(counts);
+    free(q); free(r); free(tok); free(counts); free(mv); free(pred);
     return OR_OK;
 }
 
@@ -839,8 +942,11 @@ int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out
     float* cf = (float*)malloc(sizeof(float) * (size_t)c->ncoef);
     for (long i = 0; i < c->ncoef; i++) cf[i] = (float)co[i];
     if (coeffs_out) memcpy(coeffs_out, co, sizeof(double) * (size_t)c->ncoef);
-    int st = or_encode_from_coeffs(c, cf, out, cap, out_len, frame_type);
-    free(pl); free(co); free(cf);
+    /* the padded luma plane holds integers in [0, 255] */
+    uint8_t* luma = (uint8_t*)malloc((size_t)ny);
+    for (long i = 0; i < ny; i++) luma[i] = (uint8_t)pl[i];
+    int st = or_encode_from_coeffs_luma(c, cf, luma, out, cap, out_len, frame_type);
+    free(pl); free(co); free(cf); free(luma);
     return st;
 }
 
@@ -858,23 +964,27 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
     if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
     if (get16(in + 4) != 1) return OR_ECORRUPT;
     int type = in[6];
-    if (type > 1 || in[7] != c->L || get16(in + 12) != (unsigned)c->Ho || get16(in + 14) != (unsigned)c->Wo)
+    if (type > 2 || (type == 2 && !c->range) || in[7] != c->L || get16(in + 12) != (unsigned)c->Ho || get16(in + 14) != (unsigned)c->Wo)
         return OR_ECORRUPT;
     for (int j = 0; j < c->L; j++) if (in[16 + j] != c->k[j]) return OR_ECORRUPT;
     if (get16(in + 22) != (unsigned)c->qph || get16(in + 24) != (unsigned)c->qpl) return OR_ECORRUPT;
     if (get32(in + 28) != (unsigned long)c->ncomp) return OR_ECORRUPT;
     long fidx = (long)get32(in + 8);
-    if (type == 1 && fidx != c->dec_next) return OR_ESTATE;
+    if (type >= 1 && fidx != c->dec_next) return OR_ESTATE;
     /* §3.3: a stream may arrive without its finest `drop` levels; it then serves
      * scales >= drop only, and a P-frame needs the state of levels > scale */
     int drop = (int)get16(in + 26);
     if (drop > c->L) return OR_ECORRUPT;
-    if (drop > scale || (type == 1 && c->dec_floor > scale)) return OR_ESTATE;
+    if (drop > scale || (type >= 1 && c->dec_floor > scale)) return OR_ESTATE;
     if (len < 32 + 4L * c->ncomp) return OR_ECORRUPT;
     long nt = 0;
     for (int j = 0; j < c->ncomp; j++) nt += (long)get32(in + 32 + 4 * j);
-    if (32 + 4L * c->ncomp + 2 * nt > len) return OR_ECORRUPT;
+    long nmv = type == 2 ? (long)c->nby * c->nbx : 0;
+    if (32 + 4L * c->ncomp + 2 * nt + 2 * nmv > len) return OR_ECORRUPT;
     const uint8_t* tp = in + 32 + 4 * c->ncomp;
+    const int8_t* mv = (const int8_t*)(tp + 2 * nt);
+    for (long b = 0; b < 2 * nmv; b++)
+        if (mv[b] < -c->range || mv[b] > c->range) return OR_ECORRUPT;
     int16_t* r = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
     int16_t* q = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
     long t0 = 0;
@@ -899,6 +1009,11 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
         t0 += cnt;
     }
     if (st) { free(r); free(q); return st; }
+    int16_t* pred = NULL;
+    if (type == 2) {
+        pred = (int16_t*)malloc(sizeof(int16_t) * (size_t)c->ncoef);
+        for (int j = 0; j < c->ncomp; j++) mc_predict(c, j, c->dec_state, mv, pred);
+    }
     for (int j = 0; j < c->ncomp; j++) {
         long base;
         const or_subband* s = comp_sb(c, j, &base);
@@ -906,12 +1021,14 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
             for (int b = 0; b < s->w; b++) {
                 long idx = base + s->off + (long)a * s->w + b;
                 int v;
-                if (type == 1) v = r[idx] + c->dec_state[idx];
+                if (type == 2) v = r[idx] + pred[idx];
+                else if (type == 1) v = r[idx] + c->dec_state[idx];
                 else if (s->kind == 0 && a > 0) v = r[idx] + q[idx - s->w];
                 else v = r[idx];
                 q[idx] = (int16_t)(uint16_t)(v & 0xFFFF);
             }
     }
+    free(pred);
     double* co = (double*)malloc(sizeof(double) * (size_t)c->ncoef);
     for (int j = 0; j < c->ncomp; j++) {
         long base;
@@ -996,7 +1113,8 @@ int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uin
     }
     long hdr = 32 + 4L * c->ncomp;
     if (hdr + 2 * ntot > len) return OR_ECORRUPT;
-    *out_len = hdr + 2 * nkeep;
+    long tail = len - (hdr + 2 * ntot);   /* the motion vectors of a P-frame with motion */
+    *out_len = hdr + 2 * nkeep + tail;
     if (*out_len > cap) return OR_ECAPACITY;
     memcpy(out, in, 32);
     put16(out + 26, (unsigned)drop);
@@ -1012,5 +1130,6 @@ int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uin
         }
         src += 2 * cnt;
     }
+    memcpy(out + dst, in + src, (size_t)tail);
     return OR_OK;
 }

@@ -31,6 +31,7 @@
 #define OR_EOVERFLOW 4
 #define OR_ECORRUPT 5
 #define OR_ESTATE 9
+#define OR_MAX_RANGE 64
 
 typedef struct {
     long off;   /* element offset inside the plane's coefficient block */
@@ -110,10 +111,35 @@ void or_codec_dims(const or_codec* c, int* out);
 /* colour + chroma + pad of one frame: float planes Y (Hp x Wp), Co, Cg (Hcp x Wcp) */
 void or_codec_planes(const or_codec* c, const uint8_t* rgb, double* y, double* co, double* cg);
 
+/* §3.2 motion estimation between the current and the previous frame's padded
+ * luma planes (H x W, values 0..255): 16 x 16 blocks in raster order (the last
+ * block row and column clipped to the plane); every displacement (dy, dx) in
+ * [-range, range]^2 whose displaced block lies inside the plane is a
+ * candidate; the smallest sum of squared differences wins (the MSE of the
+ * block, whose size is the same for all its candidates); ties go to the
+ * smaller |dy| + |dx|, then to the first candidate in raster order (dy, then
+ * dx, ascending).  mv[2b] = dy, mv[2b + 1] = dx of block b.               */
+void or_motion_search(const uint8_t* cur, const uint8_t* prev, int H, int W, int range, int8_t* mv);
+/* P-frames with motion (§3.2, §3.7): range W in [0, OR_MAX_RANGE]; 0 keeps
+ * zero-motion P-frames.  With W > 0 a P-frame (type byte 2) carries the
+ * vectors of the luma blocks of its padded luma plane after its tokens (int8
+ * dy, dx per block, raster order), and every component's residual is taken
+ * against the motion-compensated prediction of the previous codes: element
+ * (i, j) of a component whose element covers 2^ey x 2^ex luma samples uses
+ * the vector of the block holding luma sample (i 2^ey, j 2^ex) (the last
+ * block row / column for positions past the plane), scaled by 2^-ey, 2^-ex
+ * with rounding half away from zero, and reads the previous code at the
+ * displaced position clamped to the component.                              */
+int or_codec_set_motion(or_codec* c, int range);
+
 /* the entropy side of the encoder from given single-precision coefficients:
  * threshold, quantise, K/P differencing, state update, RLE, bitstream.      */
 int or_encode_from_coeffs(or_codec* c, const float* coeffs, uint8_t* out, long cap,
                           long* out_len, int* frame_type);
+/* the same with the frame's padded luma plane (Hp x Wp bytes), which motion
+ * estimation needs (required when the codec has a motion range)            */
+int or_encode_from_coeffs_luma(or_codec* c, const float* coeffs, const uint8_t* luma, uint8_t* out, long cap,
+                               long* out_len, int* frame_type);
 /* full encode: planes -> CT (FP64) -> single-precision decision -> entropy side.
  * coeffs_out (optional, FP64, or_codec_coeff_count values) receives the CT output. */
 int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out_len,
