@@ -146,7 +146,26 @@ cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* plan, const float* d_coef
  *   qph, qpl        quantisation steps of subbands [1,181] and lowpass [1,71] (§3.5)
  *   subband_threshold  subband coefficients with |c| below it become 0 (>= 0)
  *   key_interval    frame i (since create/reset) is a K-frame iff i % key_interval == 0 (§3.7)
- *   chroma_420      must be 1                                                 */
+ *   chroma_420      must be 1
+ *   motion_range    W in 0..CVC_MAX_MOTION_RANGE.  0: P-frames predict every
+ *                   component from the previous frame's codes at the same
+ *                   position (type byte 1).  W > 0 (§3.2, §3.7): full-search
+ *                   block matching of each 16x16 block of the padded luma
+ *                   plane against the previous frame's, over every
+ *                   displacement in [-W, W]^2 that keeps the block inside the
+ *                   plane, by smallest sum of squared differences (ties: the
+ *                   smaller |dy| + |dx|, then the first in raster order, dy
+ *                   then dx ascending); P-frames (type byte 2) then carry one
+ *                   int8 (dy, dx) per block, raster order, after their tokens,
+ *                   and each component is predicted through the vector of the
+ *                   block under each element: an element standing for 2^ey x
+ *                   2^ex luma samples (its plane's size over the component's,
+ *                   doubled for chroma) uses the block of luma sample
+ *                   (i 2^ey, j 2^ex) (the last block row / column past the
+ *                   plane) and reads the previous code at (i + dy/2^ey,
+ *                   j + dx/2^ex), each quotient rounded half away from zero,
+ *                   clamped to the component.                               */
+#define CVC_MAX_MOTION_RANGE 64
 typedef struct {
     int width, height;
     int levels;
@@ -155,6 +174,7 @@ typedef struct {
     float subband_threshold;
     int key_interval;
     int chroma_420;
+    int motion_range;
 } cvc_params;
 
 typedef struct {
@@ -220,7 +240,8 @@ cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t
  * the frame `in` (HOST memory, in_len bytes, from a codec with `params`)
  * into `out` (HOST memory) without the components of its finest `drop`
  * levels: their token counts become 0, their tokens are left out, and
- * header bytes 26-27 (0 in a complete frame) hold `drop`.  A frame that
+ * header bytes 26-27 (0 in a complete frame) hold `drop`; the motion
+ * vectors of a P-frame with motion stay after the tokens.  A frame that
  * already left out d0 levels can only lose more (drop >= d0).  `out` may be
  * `in` (the tokens only move forward).  Host work only, no device call.
  * A decoder accepts such a frame at scales >= drop (cvc_decode_frame_scaled;

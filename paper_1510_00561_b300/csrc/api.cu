@@ -58,7 +58,7 @@ void fill_info(const Core& c, int s, cvc_codec_info_t* out) {
     out->padded_chroma_width = D.cg.Wcp;
     out->coeffs = D.ncoef;
     out->components = D.ncomp;
-    out->max_stream_bytes = D.hdr_bytes + 2LL * D.max_tok;
+    out->max_stream_bytes = D.hdr_bytes + 2LL * D.max_tok + D.mv_bytes;
 }
 
 cvc_status make_core(Core* c, const cvc_params* params, int n) {
@@ -340,8 +340,14 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         all += n;
         if (level[j] == 0 || level[j] > drop) keep += n;
     }
-    if (hdr + 2 * all > in_len) return CVC_ERR_CORRUPT;
-    *out_len = hdr + 2 * keep;
+    // a P-frame with motion carries its vectors after the tokens; they stay
+    unsigned long long mvb = 0;
+    if (in[6] == 2) {
+        if (params->motion_range == 0) return CVC_ERR_CORRUPT;
+        mvb = 2ULL * ((g.Hp + 15) / 16) * ((g.Wp + 15) / 16);
+    }
+    if (hdr + 2 * all + mvb > in_len) return CVC_ERR_CORRUPT;
+    *out_len = hdr + 2 * keep + mvb;
     if (!out || out_cap < *out_len) return CVC_ERR_CAPACITY;
     memmove(out, in, 32);
     out[26] = (uint8_t)(drop & 255);
@@ -358,6 +364,7 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         }
         src += 2 * (size_t)n;
     }
+    memmove(out + dst, in + src, (size_t)mvb);
     return CVC_OK;
 }
 

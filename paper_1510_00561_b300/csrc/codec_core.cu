@@ -39,12 +39,19 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_row_off, c->h_row_off.size());
     k.add(&c->d_row_w, c->h_row_w.size());
     k.add(&c->d_row_stream, c->h_row_stream.size());
+    k.add(&c->d_row_comp, c->h_row_comp.size());
     k.add(&c->d_row_low, c->h_row_low.size());
     k.add(&c->d_comp_row0, c->h_comp_row0.size());
     k.add(&c->d_comp_stream, c->h_comp_stream.size());
     k.add(&c->d_comp_low, c->h_comp_low.size());
     k.add(&c->d_comp_level, c->h_comp_level.size());
     k.add(&c->d_comp_plane, c->h_comp_plane.size());
+    k.add(&c->d_comp_ey, c->h_comp_ey.size());
+    k.add(&c->d_comp_ex, c->h_comp_ex.size());
+    k.add(&c->d_blk_motion, c->h_blk_motion.size());
+    k.add(&c->d_luma[0], (size_t)c->luma_total);
+    k.add(&c->d_luma[1], (size_t)c->luma_total);
+    k.add(&c->d_mv, 2 * (size_t)c->mv_pairs);
     k.add(&c->d_comp_elem, c->h_comp_elem.size());
     k.add(&c->d_planes, (size_t)c->nplane);
     k.add(&c->d_rplanes, (size_t)c->nplane);
@@ -178,7 +185,8 @@ bool dirs_valid(int levels, const int* dirs) {
 bool codec_params_valid(const cvc_params* prm) {
     return prm && prm->width >= 1 && prm->height >= 1 && prm->width <= 65535 && prm->height <= 65535 &&
            dirs_valid(prm->levels, prm->dirs_log2) && prm->qph >= 1 && prm->qph <= 181 && prm->qpl >= 1 &&
-           prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1;
+           prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1 && prm->motion_range >= 0 &&
+           prm->motion_range <= CVC_MAX_MOTION_RANGE;
 }
 
 bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
@@ -275,6 +283,20 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.ncomp = (int)(Ly.sb.size() + 2 * Lc.sb.size());
         D.hdr_bytes = 32 + 4LL * D.ncomp;
         D.max_tok = 2 * D.ncoef + 64;
+        D.mv_range = P.motion_range;
+        if (P.motion_range > 0) {
+            // 16 x 16 blocks of the padded luma plane, one motion search block each
+            D.nby = (g.Hp + 15) / 16;
+            D.nbx = (g.Wp + 15) / 16;
+            D.mv_bytes = 2LL * D.nby * D.nbx;
+            D.mv_off = c->mv_pairs;
+            D.luma_off = c->luma_total;
+            D.blk_motion = (int)c->h_blk_motion.size();
+            c->mv_pairs += (long long)D.nby * D.nbx;
+            c->luma_total += (long long)g.Hp * g.Wp;
+            if ((long long)c->h_blk_motion.size() + D.nby * D.nbx > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
+            c->h_blk_motion.insert(c->h_blk_motion.end(), (size_t)D.nby * D.nbx, s);
+        }
         D.blk_colour = (int)c->h_blk_colour.size();
         // forward colour kernel: one block per padded luma row and per padded chroma row
         // (the inverse one, per output row, is planned per decoding scale)
@@ -308,10 +330,17 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             c->lowcols += pd.low_w;
             // rows of every component, in stream order
             for (const SubbandG& sb : Lp.sb) {
+                const int comp = (int)c->h_comp_low.size();
                 c->h_comp_row0.push_back((int)c->h_row_off.size());
                 c->h_comp_low.push_back(sb.kind == 0);
                 c->h_comp_level.push_back((uint8_t)sb.level);
                 c->h_comp_plane.push_back((uint8_t)p);
+                // luma samples per element: the plane's size over the component's, doubled for chroma
+                int ey = p > 0, ex = p > 0;
+                while (((p == 0 ? g.Hp : g.Hcp) >> (ey - (p > 0))) > sb.h) ey++;
+                while (((p == 0 ? g.Wp : g.Wcp) >> (ex - (p > 0))) > sb.w) ex++;
+                c->h_comp_ey.push_back((uint8_t)ey);
+                c->h_comp_ex.push_back((uint8_t)ex);
                 c->h_comp_stream.push_back(s);
                 c->h_comp_elem.push_back(poff[p] - coef_off + sb.off);
                 for (int r = 0; r < sb.h; r++) {
@@ -319,6 +348,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
                     c->h_row_w.push_back(sb.w);
                     c->h_row_low.push_back(sb.kind == 0);
                     c->h_row_stream.push_back(s);
+                    c->h_row_comp.push_back(comp);
                 }
             }
         }
@@ -389,7 +419,9 @@ cvc_status core_alloc(Core* c) {
               put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
               put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
               put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
-              put(c->d_comp_level, c->h_comp_level) && put(c->d_comp_plane, c->h_comp_plane);
+              put(c->d_comp_level, c->h_comp_level) && put(c->d_comp_plane, c->h_comp_plane) &&
+              put(c->d_row_comp, c->h_row_comp) && put(c->d_comp_ey, c->h_comp_ey) &&
+              put(c->d_comp_ex, c->h_comp_ex) && put(c->d_blk_motion, c->h_blk_motion);
     for (const auto& sp : c->scale) ok = ok && put(sp->d_desc, sp->h_desc) && put(sp->d_blk, sp->h_blk);
     // state buffers start at zero (no frame may read them before a K-frame)
     for (int b = 0; b < 2 && ok; b++)
@@ -464,9 +496,10 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
     *nl = 0;
     CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->d_rs, 0, sizeof(SResult) * n, st));
-    const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->nrows};
+    const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->d_row_comp, c->nrows};
     const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
-                       c->d_comp_level, c->d_comp_plane, c->ncomp};
+                       c->d_comp_level, c->d_comp_plane, c->d_comp_ey, c->d_comp_ex, c->ncomp};
+    const bool motion = !c->h_blk_motion.empty();
     const int rpb = c->shape.rle_rows;
     const int rgrid = (int)cdiv(c->nrows, rpb);
     if (mode & STEP_ENC) {
@@ -477,7 +510,8 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         B.p[B_WORK] = c->d_work;
         // S1-S3: colour, 4:2:0, padding
         clk.begin(0);
-        k_colour_fwd_b<<<(int)c->h_blk_colour.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour, c->d_planes);
+        k_colour_fwd_b<<<(int)c->h_blk_colour.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour, c->d_planes,
+                                                                    c->d_luma[0], c->d_luma[1]);
         CK(cudaGetLastError());
         clk.end(0, 1);
         // S4, S5: LP analysis, DFB analysis
@@ -493,14 +527,23 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_THREADS, 0, st>>>(
             c->d_coef, c->d_est_buf[0], c->d_est_buf[1], c->d_pd, c->d_blk_plane, c->d_sd, c->d_sc, c->d_res, c->d_rs);
         CK(cudaGetLastError());
-        clk.end(3, 1);
+        if (motion) {
+            // §3.2 motion search, then the residuals of the motion-compensated P-frames
+            k_motion_b<<<(int)c->h_blk_motion.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_motion, c->d_luma[0],
+                                                                    c->d_luma[1], c->d_mv);
+            k_mc_resid_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_est_buf[0], c->d_est_buf[1], rt, ct, c->d_sd, c->d_sc,
+                                                     c->d_mv, c->d_res);
+            CK(cudaGetLastError());
+            k += 2;
+        }
+        clk.end(3, motion ? 3 : 1);
         // S9: RLE rows, row offsets, tokens, headers
         clk.begin(4);
         k_rle_count_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sc, c->d_rowcnt);
         CK(cudaGetLastError());
         CK(exclusive_scan(c->d_rowcnt, (uint32_t)c->nrows, c->d_rowoff, c->d_scan_tmp, st));
         k_rle_write_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sd, c->d_sc, c->d_rowoff, c->d_rs);
-        k_stream_header_b<<<n, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rowoff, ct, c->d_rs);
+        k_stream_header_b<<<n, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rowoff, ct, c->d_mv, c->d_rs);
         CK(cudaGetLastError());
         clk.end(4, 6);
         k += 7;
@@ -531,7 +574,13 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
                                                                        c->d_pd, c->nplanes, c->d_sd, c->d_sc, c->d_rs,
                                                                        c->d_dcoef);
         CK(cudaGetLastError());
-        clk.end(6, 2);
+        if (motion) {
+            k_mc_recon_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, c->d_dst_buf[0], c->d_dst_buf[1], rt, ct, c->d_sd,
+                                                     c->d_sc, c->d_rs, c->d_dcoef);
+            CK(cudaGetLastError());
+            k += 1;
+        }
+        clk.end(6, motion ? 3 : 2);
         // inverse transform of the scale: DFB synthesis, then LP synthesis
         const ScalePlan& sp = *c->scale[scale];
         const CtEngine* ie = scale == 0 ? &c->eng : &sp.eng;
@@ -689,9 +738,10 @@ void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, siz
     int ty = -1, dty = -1;
     unsigned didx = 0;
     if (C.enc_on) {
-        const long long need = D.hdr_bytes + 2LL * R.enc_tokens;
+        const bool mc = !C.enc_key && D.mv_range > 0;
+        const long long need = D.hdr_bytes + 2LL * R.enc_tokens + (mc ? D.mv_bytes : 0);
         len = (size_t)need;
-        ty = C.enc_key ? 0 : 1;
+        ty = C.enc_key ? 0 : (mc ? 2 : 1);
         if (R.enc_err & EF_OVERFLOW) es = CVC_ERR_OVERFLOW;
         else if (need > C.out_cap || (R.enc_err & EF_CAPACITY)) es = CVC_ERR_CAPACITY;
         if (es == CVC_OK) {

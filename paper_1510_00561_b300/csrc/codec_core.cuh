@@ -59,10 +59,11 @@ struct Core {
     int nrows = 0, ncomp = 0, nplanes = 0, lowcols = 0;
     // host tables (kept for the size estimate and the upload)
     std::vector<PDesc> h_pd;
-    std::vector<int> h_blk_colour, h_blk_plane;
+    std::vector<int> h_blk_colour, h_blk_plane, h_blk_motion;
     std::vector<long long> h_row_off, h_comp_elem;
-    std::vector<int> h_row_w, h_row_stream, h_comp_row0, h_comp_stream;
-    std::vector<uint8_t> h_row_low, h_comp_low, h_comp_level, h_comp_plane;
+    std::vector<int> h_row_w, h_row_stream, h_row_comp, h_comp_row0, h_comp_stream;
+    std::vector<uint8_t> h_row_low, h_comp_low, h_comp_level, h_comp_plane, h_comp_ey, h_comp_ex;
+    long long luma_total = 0, mv_pairs = 0;   // motion: luma bytes per buffer, vector pairs
     CtEngine eng;
     int max_levels = 0;
     std::vector<std::unique_ptr<ScalePlan>> scale;   // index = scale, 0 .. max_levels
@@ -74,10 +75,14 @@ struct Core {
     SCall* d_sc = nullptr;
     SResult* d_rs = nullptr;
     PDesc* d_pd = nullptr;
-    int *d_blk_colour = nullptr, *d_blk_plane = nullptr;
+    int *d_blk_colour = nullptr, *d_blk_plane = nullptr, *d_blk_motion = nullptr;
     long long *d_row_off = nullptr, *d_comp_elem = nullptr;
-    int *d_row_w = nullptr, *d_row_stream = nullptr, *d_comp_row0 = nullptr, *d_comp_stream = nullptr;
-    uint8_t *d_row_low = nullptr, *d_comp_low = nullptr, *d_comp_level = nullptr, *d_comp_plane = nullptr;
+    int *d_row_w = nullptr, *d_row_stream = nullptr, *d_row_comp = nullptr, *d_comp_row0 = nullptr,
+        *d_comp_stream = nullptr;
+    uint8_t *d_row_low = nullptr, *d_comp_low = nullptr, *d_comp_level = nullptr, *d_comp_plane = nullptr,
+            *d_comp_ey = nullptr, *d_comp_ex = nullptr;
+    uint8_t* d_luma[2] = {nullptr, nullptr};   // previous / current padded luma of streams with motion
+    int8_t* d_mv = nullptr;                    // the encoder's motion vectors
     float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
     int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
     uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;

@@ -21,7 +21,8 @@ __device__ __forceinline__ int mirror_idx(int a, int n) { return a < n ? a : 2 *
 // and Cg row; 2x2 rounded mean, odd edges replicated); padding mirrors about
 // the last row / column.
 __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                               const int* __restrict__ blk_stream, float* __restrict__ planes) {
+                               const int* __restrict__ blk_stream, float* __restrict__ planes,
+                               uint8_t* __restrict__ luma0, uint8_t* __restrict__ luma1) {
     const int s = blk_stream[blockIdx.x];
     const SCall& C = sc[s];
     if (!C.enc_on) return;
@@ -34,11 +35,15 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
     if (row < g.Hp) {
         const uint8_t* src = rgb + (long long)mirror_idx(row, g.H) * pitch;
         float* out = Y + (long long)row * g.Wp;
+        // streams with motion also keep the padded luma as bytes (Y is in [0, 255]) for the search
+        uint8_t* lum = D.mv_range ? (C.ecur ? luma0 : luma1) + D.luma_off + (long long)row * g.Wp : nullptr;
         for (int x = threadIdx.x; x < g.Wp; x += blockDim.x) {
             const uint8_t* p = src + 3 * mirror_idx(x, g.W);
             const int R = p[0], G = p[1], Bv = p[2];
             const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-            out[x] = (float)(t + (cg >> 1));
+            const int yv = t + (cg >> 1);
+            out[x] = (float)yv;
+            if (lum) lum[x] = (uint8_t)yv;
         }
     } else {
         const int cy = row - g.Hp;
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
     const SCall& C = sc[P.stream];
     if (!C.enc_on) return;
     const int key = C.enc_key;
+    const bool mc = !key && sd[P.stream].mv_range > 0;   // residuals by k_mc_resid_b
     const int16_t* cur = C.ecur ? est1 : est0;
     int16_t* nxt = C.ecur ? est0 : est1;
     const QuantParams qp = sd[P.stream].qp;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
         else if (low && le >= low_w) r = q - quant(cp[le - low_w], true, qp, err);
         else r = q;
         nxt[e] = (int16_t)q;
-        res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
+        if (!mc) res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
     }
 }
 
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_unquant_b(const int16_t* __res
                                                             float* __restrict__ coef) {
     const PDesc P = pd[blk_plane[blockIdx.x]];
     const SCall& C = sc[P.stream];
-    if (!C.dec_on || rs[P.stream].dec_err) return;
+    if (!C.dec_on || rs[P.stream].dec_err || rs[P.stream].dec_type == 2) return;   // type 2: k_mc_recon_b
     const bool key = rs[P.stream].dec_type == 0;
     const int16_t* cur = C.dcur ? dst1 : dst0;
     int16_t* nxt = C.dcur ? dst0 : dst1;
@@ -219,6 +225,186 @@ __global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* dst
             coef[e] = (float)acc * qp.qpl_denorm;
         }
         return;
+    }
+}
+
+// ------------------------------------------------------------- motion
+// §3.2: full-search block matching of the padded luma plane in 16 x 16
+// blocks against the previous frame's, over every displacement in
+// [-W, W]^2 that keeps the block inside the plane.  The criterion is the sum
+// of squared differences sum (c - p)^2 = sum c^2 + (sum p^2 - 2 sum c p); the
+// first term is the same for every candidate of a block, so the search ranks
+// the exact integer sum p^2 - 2 sum c p, with the same order and the same
+// ties.  Ties go to the smaller |dy| + |dx|, then to the first candidate in
+// raster order.  Full blocks use four-byte dot products of packed rows.
+constexpr int ME_MAXR = CVC_MAX_MOTION_RANGE;
+constexpr int ME_WIN = 16 + 2 * ME_MAXR;    // window rows / columns
+constexpr int ME_WS = ME_WIN + 4;           // row stride (bytes): room for the last packed word
+
+__global__ void __launch_bounds__(256) k_motion_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                                  const int* __restrict__ blk_stream,
+                                                  const uint8_t* __restrict__ luma0,
+                                                  const uint8_t* __restrict__ luma1, int8_t* __restrict__ mv) {
+    __shared__ __align__(16) uint8_t s_win[ME_WIN * ME_WS];
+    __shared__ uint32_t s_cur[16 * 4];
+    __shared__ unsigned long long s_best[8];
+    const int s = blk_stream[blockIdx.x];
+    const SCall& C = sc[s];
+    if (!C.enc_on || C.enc_key) return;
+    const SDesc& D = sd[s];
+    const int R = D.mv_range, Hp = D.cg.Hp, Wp = D.cg.Wp;
+    const int b = blockIdx.x - D.blk_motion;
+    const int by = b / D.nbx, bx = b - by * D.nbx;
+    const int y0 = 16 * by, x0 = 16 * bx;
+    const int bh = min(16, Hp - y0), bw = min(16, Wp - x0);
+    const uint8_t* cur = (C.ecur ? luma0 : luma1) + D.luma_off;    // this frame (written by the colour kernel)
+    const uint8_t* prev = (C.ecur ? luma1 : luma0) + D.luma_off;
+    // the window: previous-frame rows [y0 - R, y0 + bh + R), columns [x0 - R, x0 + bw + R),
+    // in-plane bytes only (a valid candidate never reads the others)
+    const int nr = bh + 2 * R, nc = bw + 2 * R;
+    for (int i = threadIdx.x; i < nr * nc; i += blockDim.x) {
+        const int r = i / nc, c = i - r * nc;
+        const int gy = y0 - R + r, gx = x0 - R + c;
+        s_win[r * ME_WS + c] = (gy >= 0 && gy < Hp && gx >= 0 && gx < Wp) ? prev[(long long)gy * Wp + gx] : 0;
+    }
+    if (threadIdx.x < 64) {
+        const int r = threadIdx.x >> 2, w = threadIdx.x & 3;
+        uint32_t v = 0;
+        for (int k = 0; k < 4; k++) {
+            const int x = 4 * w + k;
+            const uint32_t byte = (r < bh && x < bw) ? cur[(long long)(y0 + r) * Wp + x0 + x] : 0u;
+            v |= byte << (8 * k);
+        }
+        s_cur[threadIdx.x] = v;
+    }
+    __syncthreads();
+    const int side = 2 * R + 1, ncand = side * side;
+    unsigned long long best = ~0ull;
+    for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+        const int dy = k / side - R, dx = k - (k / side) * side - R;
+        if (y0 + dy < 0 || y0 + dy + bh > Hp || x0 + dx < 0 || x0 + dx + bw > Wp) continue;
+        unsigned cp = 0, pp = 0;                   // bytes are unsigned: the unsigned dot products
+        const uint8_t* w0 = s_win + (dy + R) * ME_WS + (dx + R);
+        if (bw == 16) {
+            const int sh = 8 * ((dx + R) & 3);
+            for (int r = 0; r < bh; r++) {
+                const uint32_t* wr = reinterpret_cast<const uint32_t*>(s_win + (dy + R + r) * ME_WS + ((dx + R) & ~3));
+                uint32_t w[5];
+#pragma unroll
+                for (int q = 0; q < 5; q++) w[q] = wr[q];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t pw = __funnelshift_r(w[q], w[q + 1], sh);
+                    cp = __dp4a(s_cur[4 * r + q], pw, cp);
+                    pp = __dp4a(pw, pw, pp);
+                }
+            }
+        } else {
+            for (int r = 0; r < bh; r++)
+                for (int x = 0; x < bw; x++) {
+                    const unsigned p = w0[r * ME_WS + x];
+                    const unsigned c = (s_cur[4 * r + (x >> 2)] >> (8 * (x & 3))) & 255u;
+                    cp += c * p;
+                    pp += p * p;
+                }
+        }
+        // key = (pp - 2 cp) + 2^26 (27 bits), then |dy| + |dx| (8 bits), then the raster index (15 bits)
+        const unsigned long long key = ((unsigned long long)(unsigned)((int)pp - 2 * (int)cp + (1 << 26)) << 23) |
+                                       ((unsigned long long)(abs(dy) + abs(dx)) << 15) | (unsigned long long)k;
+        best = key < best ? key : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) best = s_best[w] < best ? s_best[w] : best;
+        best = s_best[0] < best ? s_best[0] : best;
+        const int k = (int)(best & 0x7FFF);
+        mv[2 * (D.mv_off + b)] = (int8_t)(k / side - R);
+        mv[2 * (D.mv_off + b) + 1] = (int8_t)(k - (k / side) * side - R);
+    }
+}
+
+// §3.7: the prediction of element (i, j) of a component from the previous
+// codes: the vector of the luma block under luma sample (i 2^ey, j 2^ex),
+// scaled by 2^-ey, 2^-ex (rounded half away from zero), clamped to the
+// component
+__device__ __forceinline__ int shift_round(int v, int e) {
+    if (e == 0) return v;
+    const int a = (abs(v) + (1 << (e - 1))) >> e;
+    return v < 0 ? -a : a;
+}
+
+struct McRow {
+    const int8_t* mvrow;   // the vectors of the block row under this component row
+    long long base;        // global index of the component's first element
+    int i, h, w, ey, ex, nbx;
+};
+__device__ __forceinline__ McRow mc_row(int row, const RowTable& rt, const CompTable& ct, const SDesc& D,
+                                        const int8_t* mv) {
+    McRow m;
+    const int c = rt.comp[row];
+    const int r0 = ct.row0[c];
+    m.i = row - r0;
+    m.h = ct.row0[c + 1] - r0;
+    m.w = rt.w[row];
+    m.base = rt.off[r0];
+    m.ey = ct.ey[c];
+    m.ex = ct.ex[c];
+    m.nbx = D.nbx;
+    const int by = min((m.i << m.ey) >> 4, D.nby - 1);
+    m.mvrow = mv + 2LL * by * D.nbx;
+    return m;
+}
+__device__ __forceinline__ long long mc_src(const McRow& m, int x) {
+    const int bx = min((x << m.ex) >> 4, m.nbx - 1);
+    const int si = min(max(m.i + shift_round(m.mvrow[2 * bx], m.ey), 0), m.h - 1);
+    const int sj = min(max(x + shift_round(m.mvrow[2 * bx + 1], m.ex), 0), m.w - 1);
+    return m.base + (long long)si * m.w + sj;
+}
+
+// one warp per component row of the motion-compensated P-frames
+__global__ void k_mc_resid_b(const int16_t* __restrict__ est0, const int16_t* __restrict__ est1, RowTable rt,
+                             CompTable ct, const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                             const int8_t* __restrict__ mv, int16_t* __restrict__ res) {
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= rt.nrows) return;
+    const int s = rt.stream[row];
+    const SCall& C = sc[s];
+    const SDesc& D = sd[s];
+    if (!C.enc_on || C.enc_key || D.mv_range == 0) return;
+    const int16_t* prev = C.ecur ? est1 : est0;
+    const int16_t* q = C.ecur ? est0 : est1;       // this frame's codes (k_quant_b)
+    const McRow m = mc_row(row, rt, ct, D, mv + 2 * D.mv_off);
+    const long long off = rt.off[row];
+    for (int x = lane; x < m.w; x += 32)
+        res[off + x] = (int16_t)(uint16_t)((q[off + x] - prev[mc_src(m, x)]) & 0xFFFF);
+}
+
+__global__ void k_mc_recon_b(const int16_t* __restrict__ res, int16_t* dst0, int16_t* dst1, RowTable rt,
+                             CompTable ct, const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                             const SResult* __restrict__ rs, float* __restrict__ coef) {
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= rt.nrows) return;
+    const int s = rt.stream[row];
+    const SCall& C = sc[s];
+    if (!C.dec_on || rs[s].dec_err || rs[s].dec_type != 2) return;
+    const SDesc& D = sd[s];
+    const int16_t* prev = C.dcur ? dst1 : dst0;
+    int16_t* nxt = C.dcur ? dst0 : dst1;
+    const int8_t* v = reinterpret_cast<const int8_t*>(C.in + D.hdr_bytes + 2LL * rs[s].dec_tokens);
+    const McRow m = mc_row(row, rt, ct, D, v);
+    const long long off = rt.off[row];
+    const float scale = rt.low[row] ? D.qp.qpl_denorm : D.qp.qph;
+    for (int x = lane; x < m.w; x += 32) {
+        const int16_t qv = (int16_t)(uint16_t)((res[off + x] + prev[mc_src(m, x)]) & 0xFFFF);
+        nxt[off + x] = qv;
+        coef[off + x] = (float)qv * scale;
     }
 }
 
@@ -329,15 +515,17 @@ __global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, cons
     }
 }
 
-// one block per stream: header, component token counts, capacity check
+// one block per stream: header, component token counts, motion vectors, capacity check
 __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                                  const uint32_t* __restrict__ tokoff, CompTable ct, SResult* out) {
+                                  const uint32_t* __restrict__ tokoff, CompTable ct, const int8_t* __restrict__ mv,
+                                  SResult* out) {
     const int s = blockIdx.x;
     const SCall& C = sc[s];
     if (!C.enc_on) return;
     const SDesc& D = sd[s];
     const uint32_t tokens = tokoff[D.row0 + D.nrows] - tokoff[D.row0];
-    const long long need = D.hdr_bytes + 2LL * tokens;
+    const bool mc = !C.enc_key && D.mv_range > 0;
+    const long long need = D.hdr_bytes + 2LL * tokens + (mc ? D.mv_bytes : 0);
     if (threadIdx.x == 0) {
         out[s].enc_tokens = tokens;
         if (need > C.out_cap) atomicOr(&out[s].enc_err, EF_CAPACITY);
@@ -348,7 +536,7 @@ __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __r
         const StreamHeader& h = D.hdr;
         o[0] = 'C'; o[1] = 'V'; o[2] = 'C'; o[3] = '1';
         o[4] = 1; o[5] = 0;
-        o[6] = (uint8_t)(C.enc_key ? 0 : 1);
+        o[6] = (uint8_t)(C.enc_key ? 0 : (mc ? 2 : 1));
         o[7] = (uint8_t)h.levels;
         for (int i = 0; i < 4; i++) o[8 + i] = (uint8_t)(C.enc_index >> (8 * i));
         o[12] = (uint8_t)h.height; o[13] = (uint8_t)(h.height >> 8);
@@ -363,6 +551,12 @@ __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __r
         const int g = D.comp0 + c;
         reinterpret_cast<uint32_t*>(o + 32)[c] = tokoff[ct.row0[g + 1]] - tokoff[ct.row0[g]];
     }
+    // the vectors follow the tokens
+    if (mc && need <= C.out_cap) {
+        uint8_t* v = o + D.hdr_bytes + 2LL * tokens;
+        const int8_t* m = mv + 2 * D.mv_off;
+        for (long long i = threadIdx.x; i < D.mv_bytes; i += blockDim.x) v[i] = (uint8_t)m[i];
+    }
 }
 
 // ------------------------------------------------------------ decoding
@@ -373,7 +567,9 @@ __device__ __forceinline__ int16_t rd16(const uint8_t* p) { return (int16_t)(uin
 
 __device__ __forceinline__ long long dec_in_len(const SDesc& D, const SCall& C, const SResult* enc, int s) {
     if (C.in_len >= 0) return C.in_len;
-    return enc[s].enc_err ? 0 : D.hdr_bytes + 2LL * enc[s].enc_tokens;   // this call's encoder output
+    if (enc[s].enc_err) return 0;
+    // this call's encoder output
+    return D.hdr_bytes + 2LL * enc[s].enc_tokens + (!C.enc_key && D.mv_range > 0 ? D.mv_bytes : 0);
 }
 
 // one block per stream: header check, component token offsets
@@ -402,7 +598,8 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
             const StreamHeader& e = D.hdr;
             if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] != 0) bad = EF_CORRUPT;
             int type = in[6];
-            if (type > 1) bad = EF_CORRUPT;
+            if (type > 2) bad = EF_CORRUPT;
+            if (type == 2 && D.mv_range == 0) bad |= EF_MISMATCH;   // vectors for a decoder without motion
             if (in[7] != e.levels || (in[12] | (in[13] << 8)) != e.height || (in[14] | (in[15] << 8)) != e.width ||
                 (in[22] | (in[23] << 8)) != e.qph || (in[24] | (in[25] << 8)) != e.qpl ||
                 rd32(in + 28) != (uint32_t)ncomp)
@@ -410,12 +607,12 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
             for (int i = 0; i < 6; i++)
                 if (in[16 + i] != e.dirs[i]) bad |= EF_MISMATCH;
             uint32_t fidx = rd32(in + 8);
-            if (!bad && type == 1 && (C.dec_expect < 0 || (long long)fidx != C.dec_expect)) bad |= EF_STATE;
+            if (!bad && type >= 1 && (C.dec_expect < 0 || (long long)fidx != C.dec_expect)) bad |= EF_STATE;
             // a frame without its finest `drop` levels serves scales >= drop; a P-frame
             // also needs the decoder state of the levels above the scale
             const int drop = in[26] | (in[27] << 8);
             if (drop > e.levels) bad |= EF_CORRUPT;
-            if (!bad && (drop > C.dec_scale || (type == 1 && C.dec_floor > C.dec_scale))) bad |= EF_STATE;
+            if (!bad && (drop > C.dec_scale || (type >= 1 && C.dec_floor > C.dec_scale))) bad |= EF_STATE;
             out[s].dec_type = type;
             out[s].dec_index = fidx;
             out[s].dec_drop = bad ? 0 : (uint32_t)drop;
@@ -450,11 +647,23 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
         if (threadIdx.x == blockDim.x - 1) s_carry += s_part[threadIdx.x];
         __syncthreads();
     }
+    const uint32_t total = s_carry;
+    const bool mc = out[s].dec_type == 2;
+    const long long need = D.hdr_bytes + 2LL * total + (mc ? D.mv_bytes : 0);
+    const bool ok = total != 0 && need <= in_len && total <= D.max_tok;   // a frame has tokens in its lowpass
     if (threadIdx.x == 0) {
-        const uint32_t total = s_carry;
-        // every valid frame has at least one token per component
-        if (total == 0 || D.hdr_bytes + 2LL * total > in_len || total > D.max_tok) out[s].dec_err |= EF_CORRUPT;
+        if (!ok) out[s].dec_err |= EF_CORRUPT;
         else out[s].dec_tokens = total;
+    }
+    // the vectors of a P-frame with motion lie within the search range
+    if (ok && mc) {
+        const int8_t* v = reinterpret_cast<const int8_t*>(in + D.hdr_bytes + 2LL * total);
+        bool bad = false;
+        for (long long i = threadIdx.x; i < D.mv_bytes; i += blockDim.x) bad |= v[i] < -D.mv_range || v[i] > D.mv_range;
+        if (__syncthreads_or(bad) && threadIdx.x == 0) {
+            out[s].dec_err |= EF_CORRUPT;
+            out[s].dec_tokens = 0;
+        }
     }
 }
 

@@ -45,6 +45,13 @@ struct SDesc {
     long long pstart[3];
     long long nlow[3];
     long long absent[CVC_MAX_LEVELS + 1][3];
+    // motion (§3.2): search range (0: zero-motion P-frames), 16 x 16 luma blocks,
+    // the stream's vectors in the vector buffer, its luma planes in the luma buffers,
+    // its first block in the motion search launch
+    int mv_range, nby, nbx, blk_motion;
+    long long mv_off;      // first block's (dy, dx) pair
+    long long luma_off;    // bytes
+    long long mv_bytes;    // 2 * nby * nbx
 };
 
 // the decoder's output stage of one stream at pyramid scale s (s = 0: full
@@ -104,6 +111,7 @@ struct RowTable {
     const int* w;
     const uint8_t* low;     // row belongs to a lowpass component
     const int* stream;
+    const int* comp;        // global component index
     int nrows;
 };
 
@@ -114,13 +122,25 @@ struct CompTable {
     const long long* elem;    // element offset of the component inside its stream
     const uint8_t* level;     // 0 lowpass, j = pyramid level j (1 finest)
     const uint8_t* plane;     // 0 Y, 1 Co, 2 Cg
+    const uint8_t* ey;        // one element stands for 2^ey x 2^ex luma samples
+    const uint8_t* ex;
     int ncomp;
 };
 
 // element-wise kernels: ELEM_THREADS threads, ELEM_PER_THREAD elements each
 constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS * ELEM_PER_THREAD;
 
-__global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes);
+__global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes,
+                               uint8_t* luma0, uint8_t* luma1);
+// motion search of the P-frames of streams with a motion range: one block per 16 x 16 luma block
+__global__ void k_motion_b(const SDesc* sd, const SCall* sc, const int* blk_stream, const uint8_t* luma0,
+                           const uint8_t* luma1, int8_t* mv);
+// residuals of motion-compensated P-frames (after k_quant_b wrote their codes)
+__global__ void k_mc_resid_b(const int16_t* est0, const int16_t* est1, RowTable rt, CompTable ct,
+                             const SDesc* sd, const SCall* sc, const int8_t* mv, int16_t* res);
+// decoder: codes and coefficients of motion-compensated P-frames
+__global__ void k_mc_recon_b(const int16_t* res, int16_t* dst0, int16_t* dst1, RowTable rt, CompTable ct,
+                             const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
 __global__ void k_colour_inv_b(const ScaleDesc* sdesc, const SCall* sc, const SResult* rs, const int* blk_stream,
                                const float* rplanes, const float* dcoef);
 __global__ void k_quant_b(const float* coef, int16_t* est0, int16_t* est1, const PDesc* pd, const int* blk_plane,
@@ -133,7 +153,7 @@ __global__ void k_rle_count_b(const int16_t* res, RowTable rt, const SCall* sc, 
 __global__ void k_rle_write_b(const int16_t* res, RowTable rt, const SDesc* sd, const SCall* sc,
                               const uint32_t* tokoff, SResult* out);
 __global__ void k_stream_header_b(const SDesc* sd, const SCall* sc, const uint32_t* tokoff, CompTable ct,
-                                  SResult* out);
+                                  const int8_t* mv, SResult* out);
 __global__ void k_dec_parse_b(const SDesc* sd, const SCall* sc, const SResult* enc, CompTable ct,
                               uint32_t* comp_tok, SResult* out);
 __global__ void k_dec_base_b(const SDesc* sd, int nstreams, const SResult* rs, uint32_t* tok_base);

@@ -58,3 +58,19 @@ def test_drop_refusals():
     assert _drop(prm, s[:40], 1)[0] == 5      # truncated count table
     other = L.params(w, h, 2, [2, 1], 8, 1, 0.0, 3)
     assert _drop(other, s, 1)[0] == 5         # another decomposition: component count differs
+
+
+def test_drop_keeps_the_motion_vectors():
+    w, h, Lv, k = 176, 144, 3, [3, 2, 2]
+    prm = L.params(w, h, Lv, k, 8, 1, 0.0, 4, motion_range=8)
+    enc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 4, motion_range=8)
+    frames = S.SyntheticVideo(S.spec_for(w, h, seed=9)).frames(2)
+    enc.encode(frames[0])
+    s, t = enc.encode(frames[1])
+    assert t == 2
+    for d in range(Lv + 1):
+        st, got, _ = _drop(prm, s, d)
+        assert st == 0 and np.array_equal(got, enc.drop_levels(s, d))
+        assert np.array_equal(got[-2 * 99:], s[-2 * 99:])     # 9 x 11 blocks of (dy, dx)
+    # the vectors of a frame are no use to a stream without motion
+    assert _drop(L.params(w, h, Lv, k, 8, 1, 0.0, 4), s, 1)[0] == 5
