@@ -330,6 +330,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served run (0: skip)")
     ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
     ap.add_argument("--no-scalable", action="store_true", help="skip the per-scale decode pass")
+    ap.add_argument("--motion-range", type=int, default=8, help="search range of the motion pass (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -549,6 +550,38 @@ def main():
     else:
         del batch, outs_rgb
 
+    # motion-compensated P-frames (§3.2, §3.7): the same batched encode+decode with a
+    # full search of +-8 pixels, against the zero-motion rate and stream size above
+    motion = None
+    if args.motion_range > 0:
+        mb = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
+                         key_interval=KINT, motion_range=args.motion_range)] * B)
+        mb.set_shape(*shape)
+        m_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+        m_bytes = [0, 0]
+
+        def motion_step(i):
+            res = mb.step(3, rgb=frames_at(i), rgb_out=m_outs)
+            m_bytes[0] += sum(r["out_len"] for r in res)
+            m_bytes[1] += B
+
+        for i in range(args.warmup):
+            motion_step(i)
+        m_bytes[0] = m_bytes[1] = 0
+        m_steps = max(KINT, min(args.steps, 2 * KINT))
+        mv_value, m_ms, _ = combine_ranks(timed(lambda i: motion_step(args.warmup + i), m_steps), m_steps * B,
+                                          dist, dev)
+        mb.set_timing(True)
+        timed(lambda i: motion_step(args.warmup + m_steps + i), KINT)
+        m_stage = mb.timing()
+        mb.set_timing(False)
+        motion = {"workload": "%d 1080p streams batched, encode+decode, full search +-%d pixels on 16x16 luma "
+                              "blocks, motion-compensated P-frames" % (B, args.motion_range),
+                  "value": mv_value, "unit": UNIT, "ms_per_step": m_ms / m_steps, "steps": m_steps,
+                  "mean_stream_bytes": m_bytes[0] / max(1, m_bytes[1]),
+                  "stages_ms_per_frame": {k: v[0] / (KINT * B) for k, v in m_stage.items()}}
+        del mb, m_outs
+
     # served form: continuous batching of concurrent streams under a memory budget
     served = None
     if args.serve_seconds > 0:
@@ -599,7 +632,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served, "scalable": scalable,
+            "plain": plain, "served": served, "scalable": scalable, "motion": motion,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},

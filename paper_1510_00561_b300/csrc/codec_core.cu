@@ -296,6 +296,9 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             c->luma_total += (long long)g.Hp * g.Wp;
             if ((long long)c->h_blk_motion.size() + D.nby * D.nbx > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
             c->h_blk_motion.insert(c->h_blk_motion.end(), (size_t)D.nby * D.nbx, s);
+            // one thread per candidate of the widest search, in whole warps
+            const int ncand = (2 * P.motion_range + 1) * (2 * P.motion_range + 1);
+            c->motion_threads = std::max(c->motion_threads, std::min(1024, (ncand + 31) / 32 * 32));
         }
         D.blk_colour = (int)c->h_blk_colour.size();
         // forward colour kernel: one block per padded luma row and per padded chroma row
@@ -529,7 +532,7 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         CK(cudaGetLastError());
         if (motion) {
             // §3.2 motion search, then the residuals of the motion-compensated P-frames
-            k_motion_b<<<(int)c->h_blk_motion.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_motion, c->d_luma[0],
+            k_motion_b<<<(int)c->h_blk_motion.size(), c->motion_threads, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_motion, c->d_luma[0],
                                                                     c->d_luma[1], c->d_mv);
             k_mc_resid_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_est_buf[0], c->d_est_buf[1], rt, ct, c->d_sd, c->d_sc,
                                                      c->d_mv, c->d_res);

@@ -241,13 +241,13 @@ constexpr int ME_MAXR = CVC_MAX_MOTION_RANGE;
 constexpr int ME_WIN = 16 + 2 * ME_MAXR;    // window rows / columns
 constexpr int ME_WS = ME_WIN + 4;           // row stride (bytes): room for the last packed word
 
-__global__ void __launch_bounds__(256) k_motion_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+__global__ void __launch_bounds__(1024) k_motion_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                                   const int* __restrict__ blk_stream,
                                                   const uint8_t* __restrict__ luma0,
                                                   const uint8_t* __restrict__ luma1, int8_t* __restrict__ mv) {
     __shared__ __align__(16) uint8_t s_win[ME_WIN * ME_WS];
     __shared__ uint32_t s_cur[16 * 4];
-    __shared__ unsigned long long s_best[8];
+    __shared__ unsigned long long s_best[32];
     const int s = blk_stream[blockIdx.x];
     const SCall& C = sc[s];
     if (!C.enc_on || C.enc_key) return;
@@ -267,15 +267,15 @@ __global__ void __launch_bounds__(256) k_motion_b(const SDesc* __restrict__ sd, 
         const int gy = y0 - R + r, gx = x0 - R + c;
         s_win[r * ME_WS + c] = (gy >= 0 && gy < Hp && gx >= 0 && gx < Wp) ? prev[(long long)gy * Wp + gx] : 0;
     }
-    if (threadIdx.x < 64) {
-        const int r = threadIdx.x >> 2, w = threadIdx.x & 3;
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        const int r = t >> 2, w = t & 3;
         uint32_t v = 0;
         for (int k = 0; k < 4; k++) {
             const int x = 4 * w + k;
             const uint32_t byte = (r < bh && x < bw) ? cur[(long long)(y0 + r) * Wp + x0 + x] : 0u;
             v |= byte << (8 * k);
         }
-        s_cur[threadIdx.x] = v;
+        s_cur[t] = v;
     }
     __syncthreads();
     const int side = 2 * R + 1, ncand = side * side;
