@@ -263,6 +263,39 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
 cvc_status cvc_codec_inspect(const cvc_codec* codec, int which, float* d_out, size_t cap_elems,
                              cvc_stream_t stream);
 
+/* --------------------------------------------------------------- DEFLATE
+ * The last stage of CVC (§3.9), in its scalable mode: the tokens of every
+ * component become a raw DEFLATE stream (RFC 1951) of their own, so that any
+ * subset of components can be sent or dropped.  Each stream is one final
+ * block with dynamic Huffman codes (at most 15 bits) over the token bytes
+ * taken as literals, without LZ77 matches, which lets both directions run
+ * as data-parallel kernels.  Container ("deflated frame"): the 32-byte CVC
+ * header with version byte 2, the ncomp u32 token counts, ncomp u32 stream
+ * byte lengths (0 for a component without tokens), for every 256-byte
+ * segment of every component's token bytes (in component order) the u16 bit
+ * length of its literals, zero padding to 4 bytes, the streams back to back
+ * (each byte-aligned, its header, literals and end-of-block code), then the
+ * motion vectors of a type-2 frame.  Any inflater decodes each stream alone;
+ * the segment lengths are the entry points of the parallel inflate.
+ * A context holds device scratch for frames of one parameter set.          */
+typedef struct cvc_deflate_ctx cvc_deflate_ctx;
+cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out);
+cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx);
+/* d_in: one frame of cvc_encode_frame (version byte 1, possibly without some
+ * levels, cvc_stream_drop_levels) in device memory; d_out (device, 4-byte
+ * aligned, out_cap bytes) receives the deflated frame; *out_len (host) its
+ * length, or the bytes needed on CAPACITY.  Synchronises `stream`.
+ * Errors: INVALID_ARG, CORRUPT, CAPACITY, CUDA.                              */
+cvc_status cvc_deflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t in_len, uint8_t* d_out,
+                             size_t out_cap, size_t* out_len, cvc_stream_t stream);
+/* the inverse: a deflated frame of this context's parameters back to the
+ * frame cvc_decode_frame reads (device memory both).  CORRUPT for anything
+ * but the container above (a stream must decode to exactly its token bytes,
+ * each segment to its recorded bit length, and end with the end-of-block
+ * code).  Synchronises `stream`.                                            */
+cvc_status cvc_inflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t in_len, uint8_t* d_out,
+                             size_t out_cap, size_t* out_len, cvc_stream_t stream);
+
 /* --------------------------------------------------------------- batches
  * Many independent streams, each with its own cvc_params (any mix of frame
  * sizes and decompositions), coded together: every kernel of a step covers

@@ -93,6 +93,11 @@ def lib():
                                        np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")]
         L.or_encode_from_coeffs_luma.argtypes = [ctypes.c_void_p, _F, _U8, _U8, ctypes.c_long,
                                                  ctypes.POINTER(ctypes.c_long), _IP]
+        L.or_huffman_cost.argtypes = [np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS"), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]
+        L.or_huffman_cost.restype = ctypes.c_ulonglong
+        L.or_inflate_container.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, _U8, ctypes.c_long,
+                                           ctypes.POINTER(ctypes.c_long)]
         L.or_stream_drop.argtypes = [ctypes.c_void_p, _U8, ctypes.c_long, ctypes.c_int, _U8, ctypes.c_long,
                                      ctypes.POINTER(ctypes.c_long)]
         _lib = L
@@ -114,6 +119,14 @@ def motion_search(cur, prev, range_):
     mv = np.zeros(nby * nbx * 2, np.int8)
     lib().or_motion_search(cur.ravel(), prev.ravel(), H, W, range_, mv)
     return mv.reshape(nby, nbx, 2)
+
+
+def huffman_cost(freq):
+    """(cost, longest code) of an optimal prefix code for the frequencies (§3.9)."""
+    f = np.ascontiguousarray(freq, dtype=np.uint64)
+    d = ctypes.c_int(0)
+    cost = lib().or_huffman_cost(f, f.size, ctypes.byref(d))
+    return int(cost), d.value
 
 
 def cdf97():
@@ -411,6 +424,17 @@ class Codec:
         st = lib().or_stream_drop(self._h, s, s.size, drop, out, out.size, ctypes.byref(n))
         if st:
             raise RuntimeError("oracle stream drop failed: status %d" % st)
+        return out[:n.value].copy()
+
+    def inflate_container(self, packed):
+        """The frame inside a deflated frame, inflated stream by stream with zlib."""
+        s = np.ascontiguousarray(packed, dtype=np.uint8)
+        cap = max(1, self.max_stream)
+        out = np.zeros(cap, np.uint8)
+        n = ctypes.c_long(0)
+        st = lib().or_inflate_container(self._h, s, s.size, out, cap, ctypes.byref(n))
+        if st:
+            raise RuntimeError("oracle inflate failed: status %d" % st)
         return out[:n.value].copy()
 
     def decode_status(self, stream):

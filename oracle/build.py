@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
     tmp = OUT + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-Wall", "-Wextra", "-Wno-unused-parameter",
-           "-o", tmp, SRC, "-lm"]
+           "-o", tmp, SRC, "-lm", "-lz"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)
     return OUT

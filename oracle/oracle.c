@@ -31,6 +31,7 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <zlib.h>
 
 static int wrapi(long a, int n) {
     long r = a % n;
@@ -1131,5 +1132,85 @@ int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uin
         src += 2 * cnt;
     }
     memcpy(out + dst, in + src, (size_t)tail);
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------- DEFLATE */
+/* cost (sum of frequency x code length) of an optimal prefix code: the sum of
+ * the weights of the internal nodes Huffman's pairing creates (§3.9's DEFLATE
+ * codes are Huffman codes); *depth receives the longest code length */
+unsigned long long or_huffman_cost(const unsigned long* freq, int n, int* depth) {
+    unsigned long long w[2 * 300];
+    int dep[2 * 300], alive[2 * 300], m = 0;
+    for (int i = 0; i < n; i++)
+        if (freq[i]) { w[m] = freq[i]; dep[m] = 0; alive[m] = 1; m++; }
+    *depth = m == 1 ? 1 : 0;
+    if (m < 2) return m == 1 ? (unsigned long long)w[0] : 0;
+    /* leaves under each node: track the deepest leaf below every node */
+    unsigned long long cost = 0;
+    int left = m;
+    while (left > 1) {
+        int a = -1, b = -1;
+        for (int i = 0; i < m; i++) {
+            if (!alive[i]) continue;
+            if (a < 0 || w[i] < w[a]) { b = a; a = i; }
+            else if (b < 0 || w[i] < w[b]) b = i;
+        }
+        alive[a] = alive[b] = 0;
+        w[m] = w[a] + w[b];
+        dep[m] = (dep[a] > dep[b] ? dep[a] : dep[b]) + 1;
+        alive[m] = 1;
+        cost += w[m];
+        m++;
+        left--;
+    }
+    *depth = dep[m - 1];
+    return cost;
+}
+
+static unsigned long rd32u(const uint8_t* p) { return get32(p); }
+
+/* inflate a deflated frame (the container of cvc_deflate_frame) with zlib,
+ * each component's raw DEFLATE stream on its own; the segment table is only
+ * checked for its size */
+int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len) {
+    long hdr = 32 + 4L * c->ncomp;
+    if (len < hdr + 4L * c->ncomp || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 2 ||
+        in[5] != 0 || get32(in + 28) != (unsigned long)c->ncomp)
+        return OR_ECORRUPT;
+    long ntok = 0, nseg = 0;
+    for (int j = 0; j < c->ncomp; j++) {
+        long n = (long)rd32u(in + 32 + 4 * j);
+        ntok += n;
+        nseg += (2 * n + 255) / 256;
+    }
+    long mvb = in[6] == 2 ? 2L * ((c->Hp + 15) / 16) * ((c->Wp + 15) / 16) : 0;
+    *out_len = hdr + 2 * ntok + mvb;
+    if (*out_len > cap) return OR_ECAPACITY;
+    long pos = hdr + 4L * c->ncomp + ((2 * nseg + 3) & ~3L);
+    memcpy(out, in, (size_t)hdr);
+    out[4] = 1;
+    long o = hdr;
+    for (int j = 0; j < c->ncomp; j++) {
+        long n = (long)rd32u(in + 32 + 4 * j), nb = (long)rd32u(in + hdr + 4 * j);
+        if ((n == 0) != (nb == 0) || pos + nb > len) return OR_ECORRUPT;
+        if (n) {
+            z_stream z;
+            memset(&z, 0, sizeof(z));
+            if (inflateInit2(&z, -15) != Z_OK) return OR_ECORRUPT;
+            z.next_in = (Bytef*)(in + pos);
+            z.avail_in = (uInt)nb;
+            z.next_out = out + o;
+            z.avail_out = (uInt)(2 * n);
+            int r = inflate(&z, Z_FINISH);
+            long got = (long)(2 * n) - (long)z.avail_out;
+            inflateEnd(&z);
+            if (r != Z_STREAM_END || got != 2 * n) return OR_ECORRUPT;
+        }
+        pos += nb;
+        o += 2 * n;
+    }
+    if (pos + mvb > len) return OR_ECORRUPT;
+    memcpy(out + o, in + pos, (size_t)mvb);
     return OR_OK;
 }

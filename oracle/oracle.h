@@ -163,4 +163,12 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
 int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uint8_t* out, long cap,
                    long* out_len);
 
+/* §3.9 DEFLATE: the cost (sum freq x length) of an optimal prefix code of n
+ * symbols (Huffman's pairing); *depth = its longest code */
+unsigned long long or_huffman_cost(const unsigned long* freq, int n, int* depth);
+/* the frame inside a deflated frame (per-component raw DEFLATE streams after
+ * the header, token counts, stream lengths and segment table), inflated with
+ * zlib; OR_ECORRUPT unless every stream inflates to exactly its tokens */
+int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len);
+
 #endif

@@ -5,7 +5,7 @@ include/cvc.h; this package marshals torch tensors into it.
 """
 from ._lib import CvcError  # noqa: F401
 
-_LAZY = ("Codec", "Batch", "Server", "CtPlan", "ct_layout", "modulus", "kernel_launches", "drop_levels")
+_LAZY = ("Codec", "Batch", "Server", "CtPlan", "ct_layout", "modulus", "kernel_launches", "drop_levels", "Deflater")
 
 
 def __getattr__(name):

@@ -121,6 +121,10 @@ def lib():
         L.cvc_encode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
         L.cvc_decode_frame_scaled.argtypes = [_P, _P, _SZ, _I, _P, _SZ, _P]
+        L.cvc_deflate_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_P)]
+        L.cvc_deflate_destroy.argtypes = [_P]
+        L.cvc_deflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]
+        L.cvc_inflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]
         L.cvc_stream_drop_levels.argtypes = [ctypes.POINTER(Params), _P, _SZ, _I, _P, _SZ, ctypes.POINTER(_SZ)]
         L.cvc_codec_inspect.argtypes = [_P, _I, _P, _SZ, _P]
         L.cvc_codec_set_timing.argtypes = [_P, _I]

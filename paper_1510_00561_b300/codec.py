@@ -231,6 +231,47 @@ def drop_levels(params, stream_bytes, drop):
     return out[:n.value].copy()
 
 
+class Deflater:
+    """The DEFLATE stage (§3.9, scalable mode) for frames of one parameter set:
+    per-component Huffman-only DEFLATE streams on the GPU (cvc_deflate_*)."""
+
+    def __init__(self, **stream):
+        prm = _L.params(**stream)
+        p = ctypes.c_void_p()
+        _L.check(_L.lib().cvc_deflate_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_deflate_create")
+        self._h = p
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _L._lib is not None:
+            _L.lib().cvc_deflate_destroy(h)
+            self._h = None
+
+    def _run(self, fn, name, src, out, guess, stream):
+        if not (src.is_cuda and src.dtype == torch.uint8 and src.is_contiguous()):
+            raise ValueError("expected a contiguous uint8 CUDA tensor")
+        n = ctypes.c_size_t(0)
+        for _ in range(2):
+            o = out if out is not None else torch.empty(max(16, guess), dtype=torch.uint8, device=src.device)
+            st = fn(self._h, _ptr(src), src.numel(), _ptr(o), o.numel(), ctypes.byref(n), _stream(stream))
+            if st == 3 and out is None:          # too small: once more with the size needed
+                guess = n.value
+                continue
+            _L.check(st, name)
+            return o[:n.value]
+        _L.check(st, name)
+
+    def deflate(self, frame, out=None, stream=None):
+        """frame: uint8 CUDA tensor of one encoded frame; returns the deflated frame (a view of out)."""
+        return self._run(_L.lib().cvc_deflate_frame, "cvc_deflate_frame", frame, out,
+                         frame.numel() + frame.numel() // 4 + 65536, stream)
+
+    def inflate(self, packed, out=None, stream=None):
+        """the frame inside a deflated frame (uint8 CUDA tensors)."""
+        return self._run(_L.lib().cvc_inflate_frame, "cvc_inflate_frame", packed, out, 8 * packed.numel() + 65536,
+                         stream)
+
+
 def _info(fn, h, i=None):
     info = _L.CodecInfo()
     args = (h, i, ctypes.byref(info)) if i is not None else (h, ctypes.byref(info))

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "codec_core.cuh"
+#include "k_deflate.cuh"
 #include "k_soft.cuh"
 
 using namespace cvc;
@@ -393,6 +394,151 @@ cvc_status cvc_codec_inspect(const cvc_codec* c, int which, float* d_out, size_t
     return cudaMemcpyAsync(d_out, src, n * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) == cudaSuccess
                ? CVC_OK
                : CVC_ERR_CUDA;
+}
+
+// --------------------------------------------------------------- DEFLATE
+struct cvc_deflate_ctx {
+    int ncomp = 0, max_seg = 0;
+    long long hdr_bytes = 0, mv_bytes = 0;
+    void* arena = nullptr;
+    DflScratch* d_S = nullptr;
+    DflScratch ptrs;             // host copy of the device pointers
+    DflScratch* h_S = nullptr;   // pinned: the scalars come back through it
+    ~cvc_deflate_ctx() {
+        if (arena) cudaFree(arena);
+        if (h_S) cudaFreeHost(h_S);
+    }
+};
+
+cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
+    if (!out) return CVC_ERR_INVALID_ARG;
+    *out = nullptr;
+    Core core;   // the stream's layout: component count, token bound (host only)
+    cvc_status s = core_plan(&core, params, 1);
+    if (s != CVC_OK) return s;
+    const SDesc& D = core.sd[0];
+    cvc_deflate_ctx* x = new (std::nothrow) cvc_deflate_ctx();
+    if (!x) return CVC_ERR_NOMEM;
+    x->ncomp = D.ncomp;
+    x->hdr_bytes = D.hdr_bytes;
+    x->mv_bytes = D.mv_bytes;
+    const long long segs = (2 * D.max_tok + DFL_SEG - 1) / DFL_SEG + D.ncomp;
+    if (segs > (1LL << 30)) {
+        delete x;
+        return CVC_ERR_UNSUPPORTED;
+    }
+    x->max_seg = (int)segs;
+    const size_t n = (size_t)x->ncomp, m = (size_t)x->max_seg;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        const size_t at = off;
+        off += std::max<size_t>(bytes, 1);
+        return at;
+    };
+    const size_t o_S = take(sizeof(DflScratch)), o_comp = take((n + 1) * sizeof(DflComp)),
+                 o_hist = take(n * DFL_NLIT * 4), o_len = take(n * DFL_NLIT), o_code = take(n * DFL_NLIT * 2),
+                 o_hdr = take(n * DFL_HDR_BYTES), o_dc = take(n * 16 * 2), o_ds = take(n * DFL_NSYM * 2),
+                 o_sb = take((m + 1) * 4), o_so = take((m + 1) * 4), o_sc = take(m * 4),
+                 o_tmp = take(((m + 2047) / 2048 + 8) * 4);
+    if (cudaMalloc(&x->arena, off) != cudaSuccess ||
+        cudaMallocHost((void**)&x->h_S, sizeof(DflScratch)) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return CVC_ERR_NOMEM;
+    }
+    char* b = static_cast<char*>(x->arena);
+    DflScratch S;
+    memset(&S, 0, sizeof(S));
+    S.comp = reinterpret_cast<DflComp*>(b + o_comp);
+    S.hist = reinterpret_cast<uint32_t*>(b + o_hist);
+    S.len = reinterpret_cast<uint8_t*>(b + o_len);
+    S.code = reinterpret_cast<uint16_t*>(b + o_code);
+    S.hdr = reinterpret_cast<uint8_t*>(b + o_hdr);
+    S.dcount = reinterpret_cast<uint16_t*>(b + o_dc);
+    S.dsym = reinterpret_cast<uint16_t*>(b + o_ds);
+    S.segbits = reinterpret_cast<uint32_t*>(b + o_sb);
+    S.segoff = reinterpret_cast<uint32_t*>(b + o_so);
+    S.segcomp = reinterpret_cast<int*>(b + o_sc);
+    S.scan_tmp = reinterpret_cast<uint32_t*>(b + o_tmp);
+    x->d_S = reinterpret_cast<DflScratch*>(b + o_S);
+    x->ptrs = S;
+    if (cudaMemcpy(x->d_S, &S, sizeof(S), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return CVC_ERR_CUDA;
+    }
+    *out = x;
+    return CVC_OK;
+}
+
+cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx) {
+    delete ctx;
+    return CVC_OK;
+}
+
+static cvc_status dfl_finish(cvc_deflate_ctx* x, cudaStream_t st, size_t* out_len, long long launches) {
+    if (cudaMemcpyAsync(x->h_S, x->d_S, sizeof(DflScratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    note_launches(launches);
+    const DflScratch& S = *x->h_S;
+    *out_len = (size_t)S.total;
+    if (S.err & DFL_INTERNAL) return CVC_ERR_CUDA;
+    if (S.err & DFL_CORRUPT) return CVC_ERR_CORRUPT;
+    if (S.err & DFL_CAPACITY) return CVC_ERR_CAPACITY;
+    return CVC_OK;
+}
+
+cvc_status cvc_deflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_len, uint8_t* d_out, size_t out_cap,
+                             size_t* out_len, cvc_stream_t stream) {
+    if (!x || !d_in || !d_out || !out_len || ((uintptr_t)d_out & 3)) return CVC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // whole words only: the streams are OR-ed in 32-bit words
+    const DflArgs a{d_in, (long long)std::min<size_t>(in_len, (size_t)1 << 62), d_out,
+                    (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
+                    x->ncomp, x->max_seg, x->d_S};
+    const int sg = (x->max_seg + 255) / 256;
+    k_dfl_plan<<<1, 32, 0, st>>>(a);
+    k_dfl_hist<<<x->ncomp, 256, 0, st>>>(a);
+    k_dfl_code<<<(x->ncomp + 63) / 64, 64, 0, st>>>(a);
+    k_dfl_layout<<<1, 32, 0, st>>>(a);
+    k_dfl_seglen<<<sg, 256, 0, st>>>(a);
+    const DflScratch& S = x->ptrs;
+    if (exclusive_scan(S.segbits, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    k_dfl_zero<<<148 * 4, 256, 0, st>>>(a);
+    k_dfl_write<<<(x->max_seg + 127) / 128, 128, 0, st>>>(a);
+    k_dfl_tables<<<64, 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
+    return dfl_finish(x, st, out_len, 11);
+}
+
+cvc_status cvc_inflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_len, uint8_t* d_out, size_t out_cap,
+                             size_t* out_len, cvc_stream_t stream) {
+    if (!x || !d_in || !d_out || !out_len) return CVC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // whole words only: the streams are OR-ed in 32-bit words
+    const DflArgs a{d_in, (long long)std::min<size_t>(in_len, (size_t)1 << 62), d_out,
+                    (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
+                    x->ncomp, x->max_seg, x->d_S};
+    const int sg = (x->max_seg + 255) / 256;
+    k_ifl_plan<<<1, 32, 0, st>>>(a);
+    k_ifl_seglen<<<sg, 256, 0, st>>>(a);
+    const DflScratch& S = x->ptrs;
+    if (exclusive_scan(S.segbits, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    k_ifl_tables<<<(x->ncomp + 63) / 64, 64, 0, st>>>(a);
+    k_ifl_decode<<<(x->max_seg + 127) / 128, 128, 0, st>>>(a);
+    k_ifl_finish<<<64, 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
+    return dfl_finish(x, st, out_len, 8);
 }
 
 // --------------------------------------------------------------- batches
