@@ -241,7 +241,11 @@ cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t
  * into `out` (HOST memory) without the components of its finest `drop`
  * levels: their token counts become 0, their tokens are left out, and
  * header bytes 26-27 (0 in a complete frame) hold `drop`; the motion
- * vectors of a P-frame with motion stay after the tokens.  A frame that
+ * vectors of a P-frame with motion stay after the tokens.  A deflated frame
+ * (version byte 2, cvc_deflate_frame) loses the DEFLATE streams and segment
+ * entries of those components the same way (its stream lengths become 0),
+ * and is byte-identical to deflating the frame with the levels dropped.  A
+ * frame that
  * already left out d0 levels can only lose more (drop >= d0).  `out` may be
  * `in` (the tokens only move forward).  Host work only, no device call.
  * A decoder accepts such a frame at scales >= drop (cvc_decode_frame_scaled;

@@ -331,39 +331,94 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         return (uint32_t)in[at] | ((uint32_t)in[at + 1] << 8) | ((uint32_t)in[at + 2] << 16) |
                ((uint32_t)in[at + 3] << 24);
     };
-    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[7] != params->levels || rd32(28) != ncomp)
+    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || (in[4] != 1 && in[4] != 2) || in[5] != 0 ||
+        in[7] != params->levels || rd32(28) != ncomp)
         return CVC_ERR_CORRUPT;
+    const bool deflated = in[4] == 2;   // per-component DEFLATE streams (cvc_deflate_frame)
     const int d0 = in[26] | (in[27] << 8);
     if (drop < d0 || drop > params->levels) return CVC_ERR_INVALID_ARG;
-    unsigned long long all = 0, keep = 0;
+    if (deflated && in_len < hdr + 4 * ncomp) return CVC_ERR_CORRUPT;
+    // pass 1 (reads only): the sizes of what stays
+    unsigned long long all = 0, keep = 0, nseg = 0, kseg = 0, sbytes = 0, kbytes = 0;
     for (size_t j = 0; j < ncomp; j++) {
         const uint32_t n = rd32(32 + 4 * j);
+        const bool kept = level[j] == 0 || level[j] > drop;
+        const unsigned long long segs = (2ULL * n + 255) / 256;
         all += n;
-        if (level[j] == 0 || level[j] > drop) keep += n;
+        nseg += segs;
+        if (kept) {
+            keep += n;
+            kseg += segs;
+        }
+        if (deflated) {
+            const uint32_t nb = rd32(hdr + 4 * j);
+            sbytes += nb;
+            if (kept) kbytes += nb;
+        }
     }
-    // a P-frame with motion carries its vectors after the tokens; they stay
+    // a P-frame with motion carries its vectors after the tokens (or streams); they stay
     unsigned long long mvb = 0;
     if (in[6] == 2) {
         if (params->motion_range == 0) return CVC_ERR_CORRUPT;
         mvb = 2ULL * ((g.Hp + 15) / 16) * ((g.Wp + 15) / 16);
     }
-    if (hdr + 2 * all + mvb > in_len) return CVC_ERR_CORRUPT;
-    *out_len = hdr + 2 * keep + mvb;
+    auto pad4 = [](unsigned long long v) { return (v + 3) & ~3ULL; };
+    const unsigned long long body_in = deflated ? 4ULL * ncomp + pad4(2 * nseg) + sbytes : 2 * all;
+    const unsigned long long body_out = deflated ? 4ULL * ncomp + pad4(2 * kseg) + kbytes : 2 * keep;
+    if (hdr + body_in + mvb > in_len) return CVC_ERR_CORRUPT;
+    *out_len = hdr + body_out + mvb;
     if (!out || out_cap < *out_len) return CVC_ERR_CAPACITY;
+    // pass 2: every section moves forward (or stays), so `out` may be `in`
     memmove(out, in, 32);
     out[26] = (uint8_t)(drop & 255);
     out[27] = (uint8_t)(drop >> 8);
-    size_t src = hdr, dst = hdr;
-    for (size_t j = 0; j < ncomp; j++) {
-        const uint32_t n = rd32(32 + 4 * j);
-        const bool kept = level[j] == 0 || level[j] > drop;
-        const uint32_t w = kept ? n : 0;
-        memcpy(out + 32 + 4 * j, &w, 4);   // little-endian host
-        if (kept) {
-            memmove(out + dst, in + src, 2 * (size_t)n);
-            dst += 2 * (size_t)n;
+    if (!deflated) {
+        size_t src = hdr, dst = hdr;
+        for (size_t j = 0; j < ncomp; j++) {
+            const uint32_t n = rd32(32 + 4 * j);
+            const bool kept = level[j] == 0 || level[j] > drop;
+            const uint32_t w = kept ? n : 0;
+            memcpy(out + 32 + 4 * j, &w, 4);   // little-endian host
+            if (kept) {
+                memmove(out + dst, in + src, 2 * (size_t)n);
+                dst += 2 * (size_t)n;
+            }
+            src += 2 * (size_t)n;
         }
-        src += 2 * (size_t)n;
+        memmove(out + dst, in + src, (size_t)mvb);
+        return CVC_OK;
+    }
+    // deflated frame: counts and stream lengths of dropped components become 0, their
+    // segment entries and streams go
+    std::vector<uint32_t> cnt(ncomp), nbs(ncomp);
+    for (size_t j = 0; j < ncomp; j++) {
+        cnt[j] = rd32(32 + 4 * j);
+        nbs[j] = rd32(hdr + 4 * j);
+    }
+    const size_t seg_in = hdr + 4 * ncomp, str_in = seg_in + (size_t)pad4(2 * nseg);
+    const size_t seg_out = seg_in, str_out = seg_out + (size_t)pad4(2 * kseg);
+    size_t si = seg_in, so = seg_out;
+    for (size_t j = 0; j < ncomp; j++) {
+        const bool kept = level[j] == 0 || level[j] > drop;
+        const uint32_t w = kept ? cnt[j] : 0, b = kept ? nbs[j] : 0;
+        memcpy(out + 32 + 4 * j, &w, 4);
+        memcpy(out + hdr + 4 * j, &b, 4);
+        const size_t segb = 2 * (size_t)((2ULL * cnt[j] + 255) / 256);
+        if (kept) {
+            memmove(out + so, in + si, segb);
+            so += segb;
+        }
+        si += segb;
+    }
+    for (; so < str_out; so++) out[so] = 0;
+    size_t src = str_in, dst = str_out;
+    for (size_t j = 0; j < ncomp; j++) {
+        const bool kept = level[j] == 0 || level[j] > drop;
+        if (kept) {
+            memmove(out + dst, in + src, nbs[j]);
+            dst += nbs[j];
+        }
+        src += nbs[j];
     }
     memmove(out + dst, in + src, (size_t)mvb);
     return CVC_OK;

@@ -169,3 +169,22 @@ def test_corrupt_and_short_buffers_are_refused():
     with pytest.raises(CvcError) as e:
         dfl.deflate(packed)                           # already deflated
     assert e.value.status == 5
+
+
+def test_dropping_levels_of_deflated_frames():
+    """§3.3 + §3.9: a deflated frame loses whole component streams; that equals
+    deflating the frame without those levels, and decodes at the coarser scales."""
+    kw = dict(QCIF, motion_range=8)
+    g = _codec(kw)
+    dfl = Deflater(**kw)
+    frames = S.SyntheticVideo(S.spec_for(176, 144, seed=74)).frames(3)
+    streams = [g.encode(torch.from_numpy(f).cuda())[0].clone() for f in frames]
+    for d in range(kw["levels"] + 1):
+        full, part = _codec(kw), _codec(kw)
+        for s in streams:
+            packed = dfl.deflate(s).clone()
+            thin = g.drop_levels(packed.cpu(), d)
+            ref = dfl.deflate(torch.from_numpy(g.drop_levels(s.cpu(), d)).cuda()).cpu().numpy()
+            assert np.array_equal(thin, ref)
+            back = dfl.inflate(torch.from_numpy(thin).cuda()).clone()
+            assert torch.equal(part.decode(back, scale=d), full.decode(s.clone(), scale=d))

@@ -74,3 +74,40 @@ def test_drop_keeps_the_motion_vectors():
         assert np.array_equal(got[-2 * 99:], s[-2 * 99:])     # 9 x 11 blocks of (dy, dx)
     # the vectors of a frame are no use to a stream without motion
     assert _drop(L.params(w, h, Lv, k, 8, 1, 0.0, 4), s, 1)[0] == 5
+
+
+def _deflate_like_the_container(frame, ncomp):
+    """a deflated frame of the container layout with zlib streams (the dropper only moves bytes)"""
+    import zlib
+    hdr = 32 + 4 * ncomp
+    counts = np.frombuffer(bytes(frame[32:hdr]), "<u4")
+    streams, segs, pos = [], [], hdr
+    for n in counts:
+        tok = bytes(frame[pos:pos + 2 * int(n)])
+        pos += 2 * int(n)
+        streams.append(zlib.compress(tok, 6)[2:-4] if n else b"")
+        segs += [(len(tok[k:k + 256]) * 7) & 0xFFFF for k in range(0, len(tok), 256)]
+    head = bytearray(frame[:hdr])
+    head[4] = 2
+    seg = np.array(segs, "<u2").tobytes()
+    seg += bytes(((len(seg) + 3) // 4) * 4 - len(seg))
+    lens = np.array([len(x) for x in streams], "<u4").tobytes()
+    return np.frombuffer(bytes(head) + lens + seg + b"".join(streams) + bytes(frame[pos:]), np.uint8)
+
+
+@pytest.mark.parametrize("motion", [0, 8])
+def test_drop_of_deflated_frames_equals_deflating_the_dropped_frame(motion):
+    w, h, Lv, k = 176, 144, 3, [3, 2, 2]
+    prm = L.params(w, h, Lv, k, 8, 1, 0.0, 4, motion_range=motion)
+    enc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 4, motion_range=motion)
+    for f in S.SyntheticVideo(S.spec_for(w, h, seed=10)).frames(2):
+        s, _ = enc.encode(f)
+        box = _deflate_like_the_container(s, enc.ncomp)
+        for d in range(Lv + 1):
+            st, got, _ = _drop(prm, box, d)
+            assert st == 0
+            assert np.array_equal(got, _deflate_like_the_container(enc.drop_levels(s, d), enc.ncomp)), d
+            st, got2, _ = _drop(prm, box, d, inplace=True)
+            assert st == 0 and np.array_equal(got2, got)
+            # and the oracle inflates what remains to the dropped frame
+            assert np.array_equal(enc.inflate_container(got), enc.drop_levels(s, d))
