@@ -284,6 +284,60 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
             "requests_per_step": st["requests_done"] / max(1, st["steps"])}
 
 
+def deflate_run(kstreams, dev, reps=3):
+    """§3.9 DEFLATE of one K-frame period of encoded 1080p frames (stream 0 of the batch):
+    GPU deflate and inflate time per frame (synchronous calls, CUDA events), sizes,
+    and zlib's Huffman-only and default sizes of the same token bytes for reference."""
+    import zlib
+    import numpy as np
+    import torch
+    from paper_1510_00561_b300 import Deflater
+    dfl = Deflater(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL, key_interval=KINT)
+    frames = [ks[0] for ks in kstreams]
+    packed = [dfl.deflate(f).clone() for f in frames]          # warm-up, and the outputs
+    outs = [torch.empty(f.numel() + (1 << 16), dtype=torch.uint8, device=dev) for f in frames]
+    pouts = [torch.empty(p.numel() + (1 << 16), dtype=torch.uint8, device=dev) for p in packed]
+    st = torch.cuda.current_stream()
+    times = {}
+    for name, fn in (("deflate", lambda i: dfl.deflate(frames[i], out=pouts[i])),
+                     ("inflate", lambda i: dfl.inflate(packed[i], out=outs[i]))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            for i in range(len(frames)):
+                fn(i)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / (reps * len(frames))
+    raw = sum(f.numel() for f in frames)
+    out = sum(p.numel() for p in packed)
+    tok = zh = zd = 0
+    for f in frames:
+        b = bytes(f.cpu().numpy())
+        ncomp = int(np.frombuffer(b[28:32], "<u4")[0])
+        counts = np.frombuffer(b[32:32 + 4 * ncomp], "<u4")
+        tok += 2 * int(counts.sum())
+        pos = 32 + 4 * ncomp
+        for n in counts:
+            t = b[pos:pos + 2 * int(n)]
+            pos += 2 * int(n)
+            for strat, acc in ((zlib.Z_HUFFMAN_ONLY, "h"), (zlib.Z_DEFAULT_STRATEGY, "d")):
+                z = zlib.compressobj(6, zlib.DEFLATED, -15, 8, strat)
+                k = len(z.compress(t) + z.flush())
+                if acc == "h":
+                    zh += k
+                else:
+                    zd += k
+    return {"workload": "DEFLATE (scalable mode, per-component Huffman-only streams) of %d encoded 1080p frames "
+                        "(one K-frame period)" % len(frames),
+            "deflate_ms_per_frame": times["deflate"], "inflate_ms_per_frame": times["inflate"],
+            "deflate_frames_per_s": 1e3 / times["deflate"], "inflate_frames_per_s": 1e3 / times["inflate"],
+            "mean_frame_bytes": raw / len(frames), "mean_deflated_bytes": out / len(frames),
+            "ratio": out / raw, "token_bytes_ratio_zlib_huffman_only": zh / tok,
+            "token_bytes_ratio_zlib_default": zd / tok, "note": "calls synchronise; one frame per call"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -518,7 +572,7 @@ def main():
 
     # scalable decoding (§3.3): the same B streams decoded alone at every pyramid
     # scale; one K-frame period of bitstreams is encoded once and decoded in order
-    scalable = None
+    scalable = deflate = None
     if not args.no_scalable:
         batch.reset()
         kstreams = []
@@ -546,6 +600,7 @@ def main():
         scalable = {"workload": "decode only of %d 1080p streams, each at pyramid scale s (ceil(1080/2^s) x "
                                 "ceil(1920/2^s) output), K-frame period decoded in order" % B,
                     "unit": UNIT, "steps": sc_steps, "scales": scales}
+        deflate = deflate_run(kstreams, dev)
         del dbatch, kstreams
     else:
         del batch, outs_rgb
@@ -632,7 +687,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served, "scalable": scalable, "motion": motion,
+            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "deflate": deflate,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},

@@ -133,7 +133,7 @@ constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS
 __global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes,
                                uint8_t* luma0, uint8_t* luma1);
 // motion search of the P-frames of streams with a motion range: one block per 16 x 16 luma block,
-// 32..1024 threads (a multiple of 32; one candidate each when they cover (2W + 1)^2)
+// any multiple of 32 threads up to 1024 walking the (2W + 1)^2 candidates
 __global__ void k_motion_b(const SDesc* sd, const SCall* sc, const int* blk_stream, const uint8_t* luma0,
                            const uint8_t* luma1, int8_t* mv);
 // residuals of motion-compensated P-frames (after k_quant_b wrote their codes)
