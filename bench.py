@@ -338,6 +338,44 @@ def deflate_run(kstreams, dev, reps=3):
             "token_bytes_ratio_zlib_default": zd / tok, "note": "calls synchronise; one frame per call"}
 
 
+def rd_run(dev, n_frames=30):
+    """Rate-distortion analogues of the paper's QCIF experiments (§4.1, Figs 3, 4, 6-8) on the
+    synthetic QCIF sequence: mean Y-PSNR of the decoded frames, and mean deflated bits per frame
+    (scalable DEFLATE stage).  rd: the whole QPH range with QPL = max(1, QPH // 14), motion
+    search +-8, K every 10; qph: QPH with QPL = 1 (Fig. 3); qpl: QPL with QPH = 1 (Fig. 4)."""
+    import numpy as np
+    import torch
+    from paper_1510_00561_b300 import Codec, Deflater
+    from paper_1510_00561_b300 import synthetic as S
+    w, h, L, k = 176, 144, 3, [3, 2, 2]
+    src = S.SyntheticVideo(S.spec_for(w, h, seed=0)).frames(n_frames)
+    d_src = [torch.from_numpy(f).to(dev) for f in src]
+
+    def luma(x):
+        x = x.float()
+        return (x[..., 0] + 2 * x[..., 1] + x[..., 2]) / 4
+
+    y_src = [luma(f) for f in d_src]
+
+    def point(qph, qpl, motion):
+        kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=qph, qpl=qpl, key_interval=10, motion_range=motion)
+        enc, dec, dfl = Codec(**kw), Codec(**kw), Deflater(**kw)
+        mse, bits = 0.0, 0
+        for f, ys in zip(d_src, y_src):
+            s, _ = enc.encode(f)
+            bits += 8 * dfl.deflate(s).numel()
+            mse += float(((luma(dec.decode(s.clone())) - ys) ** 2).mean())
+        mse /= len(d_src)
+        return {"qph": qph, "qpl": qpl, "y_psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-12)),
+                "kbit_per_frame": bits / len(d_src) / 1e3}
+
+    qphs = [1, 2, 4, 8, 16, 32, 64, 128, 181]
+    return {"workload": "synthetic QCIF, %d frames, 3 levels 8/4/4 directions, 4:2:0" % n_frames,
+            "rd": [point(q, max(1, q // 14), 8) for q in qphs],
+            "qph": [point(q, 1, 0) for q in qphs],
+            "qpl": [point(1, q, 0) for q in [1, 2, 4, 8, 16, 32, 48, 71]]}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -385,6 +423,7 @@ def main():
     ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
     ap.add_argument("--no-scalable", action="store_true", help="skip the per-scale decode pass")
     ap.add_argument("--motion-range", type=int, default=8, help="search range of the motion pass (0: skip)")
+    ap.add_argument("--no-rd", action="store_true", help="skip the QCIF rate-distortion sweeps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -637,6 +676,8 @@ def main():
                   "stages_ms_per_frame": {k: v[0] / (KINT * B) for k, v in m_stage.items()}}
         del mb, m_outs
 
+    rd = rd_run(dev) if not args.no_rd else None
+
     # served form: continuous batching of concurrent streams under a memory budget
     served = None
     if args.serve_seconds > 0:
@@ -687,7 +728,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "deflate": deflate,
+            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "deflate": deflate, "rd": rd,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},
