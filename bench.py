@@ -676,7 +676,7 @@ def main():
                   "stages_ms_per_frame": {k: v[0] / (KINT * B) for k, v in m_stage.items()}}
         del mb, m_outs
 
-    rd = rd_run(dev) if not args.no_rd else None
+    rd = rd_run(dev) if (not args.no_rd and rank == 0) else None
 
     # served form: continuous batching of concurrent streams under a memory budget
     served = None
