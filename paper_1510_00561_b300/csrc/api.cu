@@ -494,6 +494,7 @@ cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
     const size_t o_S = take(sizeof(DflScratch)), o_comp = take((n + 1) * sizeof(DflComp)),
                  o_hist = take(n * DFL_NLIT * 4), o_len = take(n * DFL_NLIT), o_code = take(n * DFL_NLIT * 2),
                  o_hdr = take(n * DFL_HDR_BYTES), o_dc = take(n * 16 * 2), o_ds = take(n * DFL_NSYM * 2),
+                 o_dt = take(n * (1 << DFL_LUT) * 2),
                  o_sb = take((m + 1) * 4), o_so = take((m + 1) * 4), o_sc = take(m * 4),
                  o_tmp = take(((m + 2047) / 2048 + 8) * 4);
     if (cudaMalloc(&x->arena, off) != cudaSuccess ||
@@ -512,6 +513,7 @@ cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
     S.hdr = reinterpret_cast<uint8_t*>(b + o_hdr);
     S.dcount = reinterpret_cast<uint16_t*>(b + o_dc);
     S.dsym = reinterpret_cast<uint16_t*>(b + o_ds);
+    S.dtab = reinterpret_cast<uint16_t*>(b + o_dt);
     S.segbits = reinterpret_cast<uint32_t*>(b + o_sb);
     S.segoff = reinterpret_cast<uint32_t*>(b + o_so);
     S.segcomp = reinterpret_cast<int*>(b + o_sc);
@@ -555,19 +557,18 @@ cvc_status cvc_deflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_
     const DflArgs a{d_in, (long long)std::min<size_t>(in_len, (size_t)1 << 62), d_out,
                     (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
                     x->ncomp, x->max_seg, x->d_S};
-    const int sg = (x->max_seg + 255) / 256;
-    k_dfl_plan<<<1, 32, 0, st>>>(a);
+    k_dfl_plan<<<1, 256, 0, st>>>(a);
     k_dfl_hist<<<x->ncomp, 256, 0, st>>>(a);
-    k_dfl_code<<<(x->ncomp + 63) / 64, 64, 0, st>>>(a);
-    k_dfl_layout<<<1, 32, 0, st>>>(a);
-    k_dfl_seglen<<<sg, 256, 0, st>>>(a);
+    k_dfl_code<<<x->ncomp, 256, 0, st>>>(a);
+    k_dfl_layout<<<1, 256, 0, st>>>(a);
+    k_dfl_seglen<<<x->ncomp, 256, 0, st>>>(a);
     const DflScratch& S = x->ptrs;
-    if (exclusive_scan(S.segbits, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
+    if (exclusive_scan_dev(S.segbits, &x->d_S->nseg, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
     k_dfl_zero<<<148 * 4, 256, 0, st>>>(a);
-    k_dfl_write<<<(x->max_seg + 127) / 128, 128, 0, st>>>(a);
+    k_dfl_write<<<x->ncomp, 256, 0, st>>>(a);
     k_dfl_tables<<<64, 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
     return dfl_finish(x, st, out_len, 11);
@@ -582,15 +583,15 @@ cvc_status cvc_inflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_
                     (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
                     x->ncomp, x->max_seg, x->d_S};
     const int sg = (x->max_seg + 255) / 256;
-    k_ifl_plan<<<1, 32, 0, st>>>(a);
+    k_ifl_plan<<<1, 256, 0, st>>>(a);
     k_ifl_seglen<<<sg, 256, 0, st>>>(a);
     const DflScratch& S = x->ptrs;
     if (exclusive_scan(S.segbits, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    k_ifl_tables<<<(x->ncomp + 63) / 64, 64, 0, st>>>(a);
-    k_ifl_decode<<<(x->max_seg + 127) / 128, 128, 0, st>>>(a);
+    k_ifl_tables<<<x->ncomp, 128, 0, st>>>(a);
+    k_ifl_decode<<<x->ncomp, 256, 0, st>>>(a);
     k_ifl_finish<<<64, 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
     return dfl_finish(x, st, out_len, 8);

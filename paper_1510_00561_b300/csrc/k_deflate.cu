@@ -121,14 +121,25 @@ __device__ void canonical_codes(const uint8_t* len, int n, uint16_t* code) {
 // sequential bit writer into a byte buffer (zeroed by the caller)
 struct BitOut {
     uint8_t* p;
-    uint32_t pos, cap;
+    uint32_t pos, cap;     // bits written, bit capacity
     bool over;
+    unsigned long long acc = 0;   // the nacc bits after the last stored byte
+    int nacc = 0;
     __device__ void put(uint32_t v, int n) {
-        for (int i = 0; i < n; i++) {
-            if (pos >= cap) { over = true; return; }
-            if ((v >> i) & 1u) p[pos >> 3] |= (uint8_t)(1u << (pos & 7));
-            pos++;
+        if (pos + n > cap) { over = true; return; }
+        acc |= (unsigned long long)(v & ((n < 32) ? ((1u << n) - 1u) : 0xFFFFFFFFu)) << nacc;
+        nacc += n;
+        pos += n;
+        while (nacc >= 8) {
+            p[(pos - nacc) >> 3] = (uint8_t)acc;
+            acc >>= 8;
+            nacc -= 8;
         }
+    }
+    __device__ void flush() {
+        if (nacc > 0) p[(pos - nacc) >> 3] = (uint8_t)acc;
+        acc = 0;
+        nacc = 0;
     }
 };
 
@@ -185,41 +196,121 @@ __device__ __noinline__ bool build_decoder(const uint8_t* len, int n, uint16_t* 
     return true;
 }
 
+// exclusive scan of one value per thread over a block of 256 threads; *total = the sum
+__device__ unsigned long long block_scan(unsigned long long v, unsigned long long* sh, unsigned long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = lane < 8 ? sh[lane] : 0;
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < 8) sh[lane] = t;
+    }
+    __syncthreads();
+    const unsigned long long r = (warp ? sh[warp - 1] : 0) + x - v;
+    *total = sh[7];
+    __syncthreads();
+    return r;
+}
+
+// Huffman lengths of the (at most 19) code-length symbols, limited to maxlen:
+// leaves sorted by (weight, symbol), two queues, halving the weights while too deep
+__device__ void small_huffman(const uint32_t* f, int n, int maxlen, uint8_t* len) {
+    uint32_t w[40];
+    uint8_t ord[20], q[20], parent[40];
+    for (int i = 0; i < n; i++) w[i] = f[i];
+    for (;;) {
+        int nu = 0;
+        for (int i = 0; i < n; i++) {
+            len[i] = 0;
+            if (!w[i]) continue;
+            int k = nu++;
+            while (k > 0 && (w[ord[k - 1]] > w[i])) { ord[k] = ord[k - 1]; k--; }
+            ord[k] = (uint8_t)i;
+        }
+        if (nu < 2) {                      // a lone symbol: one bit (the caller completes the code)
+            for (int i = 0; i < n; i++) len[i] = w[i] ? 1 : 0;
+            return;
+        }
+        int li = 0, qh = 0, qt = 0, m = n;
+        auto take = [&]() -> int {
+            if (li < nu && (qh >= qt || w[ord[li]] <= w[q[qh]])) return ord[li++];
+            return q[qh++];
+        };
+        for (int k = 0; k < nu - 1; k++) {
+            const int x = take(), y = take();
+            w[m] = w[x] + w[y];
+            parent[x] = parent[y] = (uint8_t)m;
+            q[qt++] = (uint8_t)m;
+            m++;
+        }
+        const int root = m - 1;
+        int deep = 0;
+        for (int i = 0; i < n; i++) {
+            if (!w[i]) continue;
+            int d = 0;
+            for (int x = i; x != root; x = parent[x]) d++;
+            len[i] = (uint8_t)d;
+            deep = max(deep, d);
+        }
+        if (deep <= maxlen) return;
+        for (int i = 0; i < n; i++) w[i] = w[i] ? (w[i] + 1) >> 1 : 0;
+    }
+}
+
 }  // namespace
 
 // -------------------------------------------------------------- deflate
-// one thread: component byte offsets of the input tokens and the segments
-__global__ void k_dfl_plan(DflArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// component byte offsets of the input tokens and the segments (one block)
+__global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
     DflScratch& S = *a.S;
-    S.err = 0;
-    S.total = 0;
+    __shared__ unsigned long long sh[8];
+    __shared__ int s_bad;
     const uint8_t* in = a.in;
-    if (a.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] != 0 ||
-        rd32(in + 28) != (uint32_t)a.ncomp) {
-        S.err = DFL_CORRUPT;
-        return;
+    if (threadIdx.x == 0) {
+        S.err = 0;
+        S.total = 0;
+        s_bad = a.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] != 0 ||
+                rd32(in + 28) != (uint32_t)a.ncomp;
+        if (s_bad) S.err = DFL_CORRUPT;
     }
-    unsigned long long tok = 0;
-    uint32_t seg = 0;
-    for (int c = 0; c < a.ncomp; c++) {
-        const uint32_t n = rd32(in + 32 + 4 * c);
-        S.comp[c].in_off = a.hdr_bytes + 2 * tok;
-        S.comp[c].bytes = 2 * n;
-        S.comp[c].seg0 = seg;
-        tok += n;
-        seg += (2 * n + DFL_SEG - 1) / DFL_SEG;
+    __syncthreads();
+    if (s_bad) return;
+    unsigned long long tok = 0, seg = 0, tt, ts;
+    for (int b = 0; b < a.ncomp; b += blockDim.x) {
+        const int c = b + threadIdx.x;
+        const uint32_t n = c < a.ncomp ? rd32(in + 32 + 4 * c) : 0;
+        const unsigned long long segs = (2ULL * n + DFL_SEG - 1) / DFL_SEG;
+        const unsigned long long pt = block_scan(n, sh, &tt), ps = block_scan(segs, sh, &ts);
+        if (c < a.ncomp) {
+            S.comp[c].in_off = a.hdr_bytes + 2 * (tok + pt);
+            S.comp[c].bytes = 2ULL * n;
+            S.comp[c].seg0 = (uint32_t)(seg + ps);
+        }
+        tok += tt;
+        seg += ts;
     }
-    S.comp[a.ncomp].seg0 = seg;
-    const int type = in[6];
-    const long long mvb = type == 2 ? a.mv_bytes : 0;
-    if ((type == 2 && a.mv_bytes == 0) || seg > (uint32_t)a.max_seg || a.hdr_bytes + 2 * tok + mvb > (unsigned long long)a.in_len) {
-        S.err = DFL_CORRUPT;
-        return;
+    if (threadIdx.x == 0) {
+        S.comp[a.ncomp].seg0 = (uint32_t)seg;
+        const int type = in[6];
+        const long long mvb = type == 2 ? a.mv_bytes : 0;
+        if ((type == 2 && a.mv_bytes == 0) || seg > (unsigned long long)a.max_seg ||
+            a.hdr_bytes + 2 * tok + mvb > (unsigned long long)a.in_len) {
+            S.err = DFL_CORRUPT;
+            return;
+        }
+        S.nseg = (uint32_t)seg;
+        S.tok_bytes = 2 * tok;
+        S.tail = mvb;
     }
-    S.nseg = seg;
-    S.tok_bytes = 2 * tok;
-    S.tail = mvb;
 }
 
 // byte histogram of each component: one block per component
@@ -227,156 +318,267 @@ __global__ void __launch_bounds__(256) k_dfl_hist(DflArgs a) {
     DflScratch& S = *a.S;
     if (S.err) return;
     const int c = blockIdx.x;
-    __shared__ uint32_t h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __shared__ uint32_t h[8][256];     // one per warp: the few common bytes collide less
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i >> 8][i & 255] = 0;
     __syncthreads();
     const uint8_t* p = a.in + S.comp[c].in_off;
     const unsigned long long n = S.comp[c].bytes;
-    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&h[p[i]], 1u);
+    uint32_t* hw = h[(threadIdx.x >> 5) & 7];
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hw[p[i]], 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) S.hist[c * DFL_NLIT + i] = h[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        uint32_t t = 0;
+        for (int k = 0; k < 8; k++) t += h[k][i];
+        S.hist[c * DFL_NLIT + i] = t;
+    }
     if (threadIdx.x == 0) S.hist[c * DFL_NLIT + 256] = 1;   // end of block
 }
 
-// code of each component (one thread per component): literal/length code
-// lengths and codes, the run-length coded header, its bit length
-__global__ void k_dfl_code(DflArgs a) {
+// code of each component (one block each): literal/length code lengths (two
+// queues over the leaves sorted by (weight, symbol), in shared memory; the
+// weights halved while a code would be longer than 15 bits), canonical codes,
+// the run-length coded block header and its bit length
+__global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
     DflScratch& S = *a.S;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S.err || c >= a.ncomp) return;
+    const int c = blockIdx.x, tid = threadIdx.x;
+    if (S.err) return;
     DflComp& C = S.comp[c];
     if (C.bytes == 0) {
-        C.hdr_bits = 0;
-        C.data_bits = 0;
+        if (tid == 0) C.hdr_bits = 0, C.data_bits = 0;
         return;
     }
-    uint32_t w[2 * DFL_NLIT];
-    uint16_t parent[2 * DFL_NLIT], heap[DFL_NLIT];
-    uint8_t* len = S.len + c * DFL_NLIT;
-    huffman_lengths(S.hist + c * DFL_NLIT, DFL_NLIT, 15, len, w, parent, heap);
-    canonical_codes(len, DFL_NLIT, S.code + c * DFL_NLIT);
-    // code lengths of the 257 literal/length codes and of two (unused) distance
-    // codes of one bit, run-length coded with the code-length alphabet
-    uint8_t seq[DFL_NLIT + 2];
-    for (int i = 0; i < DFL_NLIT; i++) seq[i] = len[i];
-    seq[DFL_NLIT] = seq[DFL_NLIT + 1] = 1;
-    const int N = DFL_NLIT + 2;
-    uint8_t rs[DFL_NLIT + 2], rx[DFL_NLIT + 2];   // code-length symbols, their extra values
-    int nr = 0;
-    for (int i = 0; i < N;) {
-        const int v = seq[i];
-        int run = 1;
-        while (i + run < N && seq[i + run] == v) run++;
-        if (v == 0) {
-            int r = run;
-            while (r >= 11) {
-                const int k = min(r, 138);
-                rs[nr] = 18; rx[nr++] = (uint8_t)(k - 11);
-                r -= k;
-            }
-            if (r >= 3) {
-                rs[nr] = 17; rx[nr++] = (uint8_t)(r - 3);
-                r = 0;
-            }
-            while (r-- > 0) { rs[nr] = 0; rx[nr++] = 0; }
-        } else {
-            rs[nr] = (uint8_t)v; rx[nr++] = 0;
-            int r = run - 1;
-            while (r >= 3) {
-                const int k = min(r, 6);
-                rs[nr] = 16; rx[nr++] = (uint8_t)(k - 3);
-                r -= k;
-            }
-            while (r-- > 0) { rs[nr] = (uint8_t)v; rx[nr++] = 0; }
+    __shared__ uint32_t w[2 * DFL_NLIT];
+    __shared__ uint16_t parent[2 * DFL_NLIT], order[DFL_NLIT], q[DFL_NLIT], scode[DFL_NLIT];
+    __shared__ uint8_t len[DFL_NLIT];
+    __shared__ int s_n, s_root, s_deep;
+    __shared__ uint16_t nextc[16];
+    __shared__ uint8_t hbuf[DFL_HDR_BYTES];
+    __shared__ unsigned long long sh[8];
+    const uint32_t* hist = S.hist + c * DFL_NLIT;
+    for (int i = tid; i < DFL_NLIT; i += blockDim.x) w[i] = hist[i];
+    for (int round = 0; round < 40; round++) {
+        if (tid == 0) s_n = 0, s_deep = 0;
+        __syncthreads();
+        // rank of each used leaf by (weight, symbol)
+        for (int i = tid; i < DFL_NLIT; i += blockDim.x) {
+            if (!w[i]) continue;
+            int r = 0;
+            for (int j = 0; j < DFL_NLIT; j++) r += w[j] && (w[j] < w[i] || (w[j] == w[i] && j < i));
+            order[r] = (uint16_t)i;
+            atomicAdd(&s_n, 1);
         }
-        i += run;
+        __syncthreads();
+        if (tid == 0) {
+            const int n = s_n;
+            int li = 0, qh = 0, qt = 0, m = DFL_NLIT;
+            for (int k = 0; k < n - 1; k++) {
+                int x[2];
+                for (int e = 0; e < 2; e++) {
+                    if (li < n && (qh >= qt || w[order[li]] <= w[q[qh]])) x[e] = order[li++];
+                    else x[e] = q[qh++];
+                }
+                w[m] = w[x[0]] + w[x[1]];
+                parent[x[0]] = parent[x[1]] = (uint16_t)m;
+                q[qt++] = (uint16_t)m;
+                m++;
+            }
+            s_root = m - 1;
+        }
+        __syncthreads();
+        for (int i = tid; i < DFL_NLIT; i += blockDim.x) {
+            int d = 0;
+            if (hist[i]) {
+                for (int x = i; x != s_root; x = parent[x]) d++;
+            }
+            len[i] = (uint8_t)d;
+            atomicMax(&s_deep, d);
+        }
+        __syncthreads();
+        if (s_deep <= 15) break;
+        if (round == 0) {
+            // too deep: clamp to 15 bits and rebalance Kraft's sum by moving leaves one
+            // level down from the deepest level below 15 (the overflow repair of zlib's
+            // trees.c); the least frequent leaves then take the longest lengths
+            if (tid == 0) {
+                int cnt[16] = {0}, overflow = 0;
+                for (int i = 0; i < DFL_NLIT; i++) {
+                    if (!hist[i]) continue;
+                    if (len[i] > 15) overflow++;
+                    cnt[min((int)len[i], 15)]++;
+                }
+                while (overflow > 0) {
+                    int b = 14;
+                    while (b > 0 && cnt[b] == 0) b--;
+                    if (b == 0) break;
+                    cnt[b]--;
+                    cnt[b + 1] += 2;
+                    cnt[15]--;
+                    overflow -= 2;
+                }
+                long long kraft = 0;
+                for (int b = 1; b <= 15; b++) kraft += (long long)cnt[b] << (15 - b);
+                int k = 0;
+                for (int b = 15; b >= 1; b--)
+                    for (int m = cnt[b]; m > 0; m--) len[order[k++]] = (uint8_t)b;
+                s_deep = (kraft == (1LL << 15) && k == s_n) ? 15 : 99;
+            }
+            __syncthreads();
+            if (s_deep <= 15) break;
+        }
+        for (int i = tid; i < DFL_NLIT; i += blockDim.x) w[i] = w[i] ? (w[i] + 1) >> 1 : 0;
+        __syncthreads();
     }
-    uint32_t cf[19] = {0};
-    for (int i = 0; i < nr; i++) cf[rs[i]]++;
-    uint8_t cl[19];
-    uint16_t cc[19];
-    {
-        uint32_t w2[38];
-        uint16_t p2[38], h2[19];
-        huffman_lengths(cf, 19, 7, cl, w2, p2, h2);
+    // canonical codes (RFC 1951, 3.2.2): the codes of one length are consecutive in symbol order
+    if (tid == 0) {
+        uint16_t cnt[16] = {0};
+        for (int i = 0; i < DFL_NLIT; i++) cnt[len[i]]++;
+        cnt[0] = 0;
+        uint16_t cc = 0;
+        for (int b = 1; b < 16; b++) {
+            cc = (uint16_t)((cc + cnt[b - 1]) << 1);
+            nextc[b] = cc;
+        }
     }
-    // a single used code-length symbol still needs a complete prefix code: give it a one-bit partner
-    int used = 0, only = 0;
-    for (int i = 0; i < 19; i++)
-        if (cf[i]) { used++; only = i; }
-    if (used == 1) {
-        cl[only] = 1;
-        cl[only == 0 ? 1 : 0] = 1;
-    }
-    canonical_codes(cl, 19, cc);
-    int hclen = 19;
-    while (hclen > 4 && cl[CL_ORDER[hclen - 1]] == 0) hclen--;
-    // the header bits
-    uint8_t* hb = S.hdr + (size_t)c * DFL_HDR_BYTES;
-    for (int i = 0; i < DFL_HDR_BYTES; i++) hb[i] = 0;
-    BitOut o{hb, 0, DFL_HDR_BYTES * 8, false};
-    o.put(1, 1);                   // BFINAL
-    o.put(2, 2);                   // BTYPE = dynamic Huffman
-    o.put(DFL_NLIT - 257, 5);      // HLIT
-    o.put(1, 5);                   // HDIST: two distance codes
-    o.put(hclen - 4, 4);           // HCLEN
-    for (int i = 0; i < hclen; i++) o.put(cl[CL_ORDER[i]], 3);
-    for (int i = 0; i < nr; i++) {
-        o.put(cc[rs[i]], cl[rs[i]]);
-        if (rs[i] == 16) o.put(rx[i], 2);
-        else if (rs[i] == 17) o.put(rx[i], 3);
-        else if (rs[i] == 18) o.put(rx[i], 7);
-    }
-    if (o.over) S.err = DFL_INTERNAL;
-    C.hdr_bits = o.pos;
+    __syncthreads();
     unsigned long long bits = 0;
-    for (int i = 0; i < DFL_NLIT; i++) bits += (unsigned long long)S.hist[c * DFL_NLIT + i] * len[i];
-    C.data_bits = bits;            // the literals and the end-of-block code
+    for (int i = tid; i < DFL_NLIT; i += blockDim.x) {
+        const int l = len[i];
+        uint16_t v = 0;
+        if (l) {
+            int r = 0;
+            for (int j = 0; j < i; j++) r += len[j] == l;
+            v = (uint16_t)bit_reverse(nextc[l] + r, l);
+        }
+        scode[i] = v;
+        S.code[c * DFL_NLIT + i] = v;
+        S.len[c * DFL_NLIT + i] = (uint8_t)l;
+        bits += (unsigned long long)hist[i] * l;
+    }
+    unsigned long long total_bits;
+    block_scan(bits, sh, &total_bits);
+    // the block header (one thread): code lengths of the 257 literal/length codes and
+    // two unused one-bit distance codes, run-length coded with the code-length alphabet
+    if (tid == 0) {
+        uint8_t rs[DFL_NLIT + 2], rx[DFL_NLIT + 2];
+        const int N = DFL_NLIT + 2;
+        auto seq = [&](int k) -> int { return k < DFL_NLIT ? len[k] : 1; };
+        int nr = 0;
+        for (int i = 0; i < N;) {
+            const int v = seq(i);
+            int run = 1;
+            while (i + run < N && seq(i + run) == v) run++;
+            if (v == 0) {
+                int r = run;
+                while (r >= 11) {
+                    const int k = min(r, 138);
+                    rs[nr] = 18; rx[nr++] = (uint8_t)(k - 11);
+                    r -= k;
+                }
+                if (r >= 3) {
+                    rs[nr] = 17; rx[nr++] = (uint8_t)(r - 3);
+                    r = 0;
+                }
+                while (r-- > 0) { rs[nr] = 0; rx[nr++] = 0; }
+            } else {
+                rs[nr] = (uint8_t)v; rx[nr++] = 0;
+                int r = run - 1;
+                while (r >= 3) {
+                    const int k = min(r, 6);
+                    rs[nr] = 16; rx[nr++] = (uint8_t)(k - 3);
+                    r -= k;
+                }
+                while (r-- > 0) { rs[nr] = (uint8_t)v; rx[nr++] = 0; }
+            }
+            i += run;
+        }
+        uint32_t cf[19] = {0};
+        for (int i = 0; i < nr; i++) cf[rs[i]]++;
+        uint8_t cl[19];
+        uint16_t cc[19];
+        small_huffman(cf, 19, 7, cl);
+        int used = 0, only = 0;
+        for (int i = 0; i < 19; i++)
+            if (cf[i]) { used++; only = i; }
+        if (used == 1) {
+            cl[only] = 1;
+            cl[only == 0 ? 1 : 0] = 1;
+        }
+        canonical_codes(cl, 19, cc);
+        int hclen = 19;
+        while (hclen > 4 && cl[CL_ORDER[hclen - 1]] == 0) hclen--;
+        for (int i = 0; i < DFL_HDR_BYTES; i++) hbuf[i] = 0;
+        BitOut o{hbuf, 0, DFL_HDR_BYTES * 8, false};
+        o.put(1, 1);                   // BFINAL
+        o.put(2, 2);                   // BTYPE = dynamic Huffman
+        o.put(DFL_NLIT - 257, 5);      // HLIT
+        o.put(1, 5);                   // HDIST: two distance codes
+        o.put(hclen - 4, 4);           // HCLEN
+        for (int i = 0; i < hclen; i++) o.put(cl[CL_ORDER[i]], 3);
+        for (int i = 0; i < nr; i++) {
+            o.put(cc[rs[i]], cl[rs[i]]);
+            if (rs[i] == 16) o.put(rx[i], 2);
+            else if (rs[i] == 17) o.put(rx[i], 3);
+            else if (rs[i] == 18) o.put(rx[i], 7);
+        }
+        o.flush();
+        if (o.over) S.err = DFL_INTERNAL;
+        C.hdr_bits = o.pos;
+        C.data_bits = total_bits;      // the literals and the end-of-block code
+    }
+    __syncthreads();
+    uint8_t* hb = S.hdr + (size_t)c * DFL_HDR_BYTES;
+    for (int i = tid; i < DFL_HDR_BYTES; i += blockDim.x) hb[i] = hbuf[i];
 }
 
-// one thread: stream offsets, container layout, the size check
-__global__ void k_dfl_layout(DflArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// stream offsets, container layout, the size check (one block)
+__global__ void __launch_bounds__(256) k_dfl_layout(DflArgs a) {
     DflScratch& S = *a.S;
+    __shared__ unsigned long long sh[8];
     if (S.err) return;
     const unsigned long long tables = a.hdr_bytes + 4ULL * a.ncomp + ((2ULL * S.nseg + 3) & ~3ULL);
-    unsigned long long off = tables;
-    for (int c = 0; c < a.ncomp; c++) {
-        DflComp& C = S.comp[c];
-        C.out_off = off;
-        C.out_bytes = C.bytes ? (C.hdr_bits + C.data_bits + 7) >> 3 : 0;
-        off += C.out_bytes;
+    unsigned long long off = tables, tt;
+    for (int b = 0; b < a.ncomp; b += blockDim.x) {
+        const int c = b + threadIdx.x;
+        unsigned long long nb = 0;
+        if (c < a.ncomp) {
+            const DflComp& C = S.comp[c];
+            nb = C.bytes ? (C.hdr_bits + C.data_bits + 7) >> 3 : 0;
+        }
+        const unsigned long long p = block_scan(nb, sh, &tt);
+        if (c < a.ncomp) {
+            S.comp[c].out_off = off + p;
+            S.comp[c].out_bytes = nb;
+        }
+        off += tt;
     }
-    S.streams = tables;
-    S.total = off + S.tail;
-    if (S.total > (unsigned long long)a.out_cap) S.err = DFL_CAPACITY;
+    if (threadIdx.x == 0) {
+        S.streams = tables;
+        S.total = off + S.tail;
+        if (S.total > (unsigned long long)a.out_cap) S.err = DFL_CAPACITY;
+    }
 }
 
-// bit length of every segment (one thread per segment)
-__global__ void k_dfl_seglen(DflArgs a) {
+// bit length of every segment: one block per component, its code lengths in
+// shared memory, one thread per segment at a time
+__global__ void __launch_bounds__(256) k_dfl_seglen(DflArgs a) {
     DflScratch& S = *a.S;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S.err || s >= (uint32_t)a.max_seg) return;
-    if (s >= S.nseg) {
-        S.segbits[s] = 0;
-        return;
-    }
-    int lo = 0, hi = a.ncomp;             // the component with seg0 <= s < seg0 of the next
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (S.comp[mid].seg0 <= s) lo = mid;
-        else hi = mid;
-    }
-    while (lo + 1 < a.ncomp && S.comp[lo + 1].seg0 <= s) lo++;
-    const DflComp& C = S.comp[lo];
-    const unsigned long long b0 = (unsigned long long)(s - C.seg0) * DFL_SEG;
-    const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+    const int c = blockIdx.x;
+    if (S.err) return;
+    const DflComp& C = S.comp[c];
+    if (C.bytes == 0) return;
+    __shared__ uint8_t len[DFL_NLIT];
+    for (int i = threadIdx.x; i < DFL_NLIT; i += blockDim.x) len[i] = S.len[c * DFL_NLIT + i];
+    __syncthreads();
     const uint8_t* p = a.in + C.in_off;
-    const uint8_t* len = S.len + lo * DFL_NLIT;
-    uint32_t bits = 0;
-    for (unsigned long long i = b0; i < b1; i++) bits += len[p[i]];
-    S.segbits[s] = bits;
-    S.segcomp[s] = lo;
+    const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
+    for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
+        const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
+        const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+        uint32_t bits = 0;
+        for (unsigned long long i = b0; i < b1; i++) bits += len[p[i]];
+        S.segbits[C.seg0 + k] = bits;
+        S.segcomp[C.seg0 + k] = c;
+    }
 }
 
 // zero the words of the stream region (the streams are OR-ed in)
@@ -397,43 +599,53 @@ __device__ __forceinline__ void or_bits(uint32_t* w, unsigned long long ab, uint
     if ((int)(ab & 31) + n > 32) atomicOr(&w[(ab >> 5) + 1], (uint32_t)(x >> 32));
 }
 
-// the data of every segment (one thread each), the header of every component
-// (the thread of its first segment), the end-of-block code (its last)
-__global__ void k_dfl_write(DflArgs a) {
+// the data of every segment: one block per component, its codes in shared
+// memory, one thread per segment at a time; thread 0 adds the header, the
+// thread of the last segment the end-of-block code
+__global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
     DflScratch& S = *a.S;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S.err || s >= S.nseg) return;
-    const int c = S.segcomp[s];
+    const int c = blockIdx.x;
+    if (S.err) return;
     const DflComp& C = S.comp[c];
+    if (C.bytes == 0) return;
+    __shared__ uint8_t len[DFL_NLIT];
+    __shared__ uint16_t code[DFL_NLIT];
+    for (int i = threadIdx.x; i < DFL_NLIT; i += blockDim.x) {
+        len[i] = S.len[c * DFL_NLIT + i];
+        code[i] = S.code[c * DFL_NLIT + i];
+    }
+    __syncthreads();
     uint32_t* w = reinterpret_cast<uint32_t*>(a.out);
     const unsigned long long base = 8ULL * C.out_off;
-    const uint8_t* len = S.len + c * DFL_NLIT;
-    const uint16_t* code = S.code + c * DFL_NLIT;
-    if (s == C.seg0) {
+    if (threadIdx.x == 0) {
         const uint8_t* hb = S.hdr + (size_t)c * DFL_HDR_BYTES;
         for (uint32_t b = 0; b < C.hdr_bits; b += 8) or_bits(w, base + b, hb[b >> 3], (int)min(8u, C.hdr_bits - b));
     }
-    // segment bit offset inside the stream: the header, then the earlier segments
-    unsigned long long ab = base + C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
-    const unsigned long long b0 = (unsigned long long)(s - C.seg0) * DFL_SEG;
-    const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
     const uint8_t* p = a.in + C.in_off;
-    // accumulate into whole words, OR-ed at the word grid
-    unsigned long long acc = 0;
-    int nacc = (int)(ab & 31);
-    unsigned long long wi = ab >> 5;
-    auto emit = [&](uint32_t v, int n) {
-        acc |= (unsigned long long)v << nacc;
-        nacc += n;
-        if (nacc >= 32) {
-            atomicOr(&w[wi++], (uint32_t)acc);
-            acc >>= 32;
-            nacc -= 32;
-        }
-    };
-    for (unsigned long long i = b0; i < b1; i++) emit(code[p[i]], len[p[i]]);
-    if (s + 1 == S.comp[c + 1].seg0 || s + 1 == S.nseg) emit(code[256], len[256]);
-    if (nacc > 0) atomicOr(&w[wi], (uint32_t)acc);
+    const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
+    for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
+        const uint32_t s = C.seg0 + k;
+        // segment bit offset inside the stream: the header, then the earlier segments
+        const unsigned long long ab = base + C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
+        const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
+        const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+        // accumulate into whole words, OR-ed at the word grid
+        unsigned long long acc = 0;
+        int nacc = (int)(ab & 31);
+        unsigned long long wi = ab >> 5;
+        auto emit = [&](uint32_t v, int n) {
+            acc |= (unsigned long long)v << nacc;
+            nacc += n;
+            if (nacc >= 32) {
+                atomicOr(&w[wi++], (uint32_t)acc);
+                acc >>= 32;
+                nacc -= 32;
+            }
+        };
+        for (unsigned long long i = b0; i < b1; i++) emit(code[p[i]], len[p[i]]);
+        if (k + 1 == nseg) emit(code[256], len[256]);
+        if (nacc > 0) atomicOr(&w[wi], (uint32_t)acc);
+    }
 }
 
 // container tables and the motion vectors (after the streams are written)
@@ -455,50 +667,59 @@ __global__ void k_dfl_tables(DflArgs a) {
 }
 
 // -------------------------------------------------------------- inflate
-__global__ void k_ifl_plan(DflArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// the container's tables: token offsets, segments, stream offsets (one block)
+__global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
     DflScratch& S = *a.S;
-    S.err = 0;
-    S.total = 0;
+    __shared__ unsigned long long sh[8];
+    __shared__ int s_bad;
     const uint8_t* in = a.in;
     const unsigned long long tabs = a.hdr_bytes + 4ULL * a.ncomp;
-    if (a.in_len < (long long)tabs || rd32(in) != 0x31435643u || in[4] != 2 || in[5] != 0 ||
-        rd32(in + 28) != (uint32_t)a.ncomp) {
-        S.err = DFL_CORRUPT;
-        return;
+    if (threadIdx.x == 0) {
+        S.err = 0;
+        S.total = 0;
+        s_bad = a.in_len < (long long)tabs || rd32(in) != 0x31435643u || in[4] != 2 || in[5] != 0 ||
+                rd32(in + 28) != (uint32_t)a.ncomp;
+        if (s_bad) S.err = DFL_CORRUPT;
     }
-    unsigned long long tok = 0;
-    uint32_t seg = 0;
-    for (int c = 0; c < a.ncomp; c++) {
-        const uint32_t n = rd32(in + 32 + 4 * c);
-        S.comp[c].bytes = 2ULL * n;
-        S.comp[c].in_off = a.hdr_bytes + 2 * tok;   // in the inflated frame
-        S.comp[c].seg0 = seg;
-        tok += n;
-        seg += (2 * n + DFL_SEG - 1) / DFL_SEG;
+    __syncthreads();
+    if (s_bad) return;
+    unsigned long long tok = 0, seg = 0, sb = 0, tt, ts, tb;
+    for (int b = 0; b < a.ncomp; b += blockDim.x) {
+        const int c = b + threadIdx.x;
+        const uint32_t n = c < a.ncomp ? rd32(in + 32 + 4 * c) : 0;
+        const uint32_t nb = c < a.ncomp ? rd32(in + a.hdr_bytes + 4 * c) : 0;
+        const unsigned long long segs = (2ULL * n + DFL_SEG - 1) / DFL_SEG;
+        const unsigned long long pt = block_scan(n, sh, &tt), ps = block_scan(segs, sh, &ts),
+                                 pb = block_scan(nb, sh, &tb);
+        if (c < a.ncomp) {
+            S.comp[c].bytes = 2ULL * n;
+            S.comp[c].in_off = a.hdr_bytes + 2 * (tok + pt);   // in the inflated frame
+            S.comp[c].seg0 = (uint32_t)(seg + ps);
+            S.comp[c].out_off = sb + pb;                     // relative to the streams, fixed below
+            S.comp[c].out_bytes = nb;
+            if ((nb == 0) != (n == 0)) atomicOr(&S.err, DFL_CORRUPT);
+        }
+        tok += tt;
+        seg += ts;
+        sb += tb;
     }
-    S.comp[a.ncomp].seg0 = seg;
-    if (seg > (uint32_t)a.max_seg) {
-        S.err = DFL_CORRUPT;
-        return;
-    }
+    __syncthreads();
     const unsigned long long streams = tabs + ((2ULL * seg + 3) & ~3ULL);
-    unsigned long long off = streams;
-    for (int c = 0; c < a.ncomp; c++) {
-        const uint32_t nb = rd32(in + a.hdr_bytes + 4 * c);
-        S.comp[c].out_off = off;                  // the stream in the container
-        S.comp[c].out_bytes = nb;
-        if ((nb == 0) != (S.comp[c].bytes == 0)) S.err = DFL_CORRUPT;
-        off += nb;
+    if (seg <= (unsigned long long)a.max_seg)
+        for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) S.comp[c].out_off += streams;
+    if (threadIdx.x == 0) {
+        S.comp[a.ncomp].seg0 = (uint32_t)seg;
+        const long long mvb = in[6] == 2 ? a.mv_bytes : 0;
+        if (seg > (unsigned long long)a.max_seg || (in[6] == 2 && a.mv_bytes == 0) ||
+            streams + sb + mvb > (unsigned long long)a.in_len)
+            atomicOr(&S.err, DFL_CORRUPT);
+        S.nseg = (uint32_t)seg;
+        S.tok_bytes = 2 * tok;
+        S.tail = mvb;
+        S.streams = streams + sb;                  // where the motion vectors start
+        S.total = a.hdr_bytes + 2 * tok + mvb;
+        if (S.total > (unsigned long long)a.out_cap) atomicOr(&S.err, DFL_CAPACITY);
     }
-    const long long mvb = in[6] == 2 ? a.mv_bytes : 0;
-    if ((in[6] == 2 && a.mv_bytes == 0) || off + mvb > (unsigned long long)a.in_len) S.err = DFL_CORRUPT;
-    S.nseg = seg;
-    S.tok_bytes = 2 * tok;
-    S.tail = mvb;
-    S.streams = off;                              // where the motion vectors start
-    S.total = a.hdr_bytes + 2 * tok + mvb;
-    if (!S.err && S.total > (unsigned long long)a.out_cap) S.err = DFL_CAPACITY;
 }
 
 // segment bit lengths from the container, with their component
@@ -522,74 +743,211 @@ __global__ void k_ifl_seglen(DflArgs a) {
     S.segcomp[s] = lo;
 }
 
-// block header of each component -> canonical decoding tables
-__global__ void k_ifl_tables(DflArgs a) {
+// block header of each component -> decoding tables (one block per
+// component): the header is read by one thread; the canonical code then
+// fills a 2^DFL_LUT-entry table indexed by the next DFL_LUT bits of the
+// stream (symbol | length << 9; 0 for longer codes, which take the
+// bit-serial canonical decoder)
+__global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
     DflScratch& S = *a.S;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S.err || c >= a.ncomp) return;
+    const int c = blockIdx.x, tid = threadIdx.x;
+    if (S.err) return;
     DflComp& C = S.comp[c];
     if (C.bytes == 0) return;
-    BitIn in{a.in + C.out_off, 0, 8ULL * C.out_bytes, false};
-    const uint32_t bfinal = in.get(1), btype = in.get(2);
-    const int hlit = (int)in.get(5) + 257, hdist = (int)in.get(5) + 1, hclen = (int)in.get(4) + 4;
-    bool ok = bfinal == 1 && btype == 2 && hlit <= 286 && hdist <= 30;
-    uint8_t cl[19] = {0};
-    for (int i = 0; i < hclen; i++) cl[CL_ORDER[i]] = (uint8_t)in.get(3);
-    uint16_t ccount[16], csym[19];
-    ok = ok && build_decoder(cl, 19, ccount, csym);
-    uint8_t lens[286 + 30];
-    const int n = hlit + hdist;
-    for (int i = 0; ok && i < n;) {
-        const int sym = decode_sym(in, ccount, csym);
-        if (in.bad || sym < 0) { ok = false; break; }
-        if (sym < 16) {
-            lens[i++] = (uint8_t)sym;
-            continue;
+    __shared__ uint8_t lens[286 + 30];
+    __shared__ int s_ok, s_hlit;
+    __shared__ uint16_t nextc[16];
+    __shared__ uint8_t head[DFL_HDR_BYTES];     // a valid block header fits
+    const unsigned long long nh = min((unsigned long long)DFL_HDR_BYTES, C.out_bytes);
+    for (unsigned long long i = tid; i < nh; i += blockDim.x) head[i] = a.in[C.out_off + i];
+    __syncthreads();
+    if (tid == 0) {
+        // bits of the header, LSB first, from shared memory through a 64-bit buffer
+        unsigned long long buf = 0, bp = 0, pos = 0;
+        const unsigned long long hbits = 8ULL * nh;
+        int nb = 0;
+        bool bad = false;
+        auto get = [&](int n) -> uint32_t {
+            while (nb < n) {
+                buf |= (unsigned long long)(bp < nh ? head[bp] : 0) << nb;
+                bp++;
+                nb += 8;
+            }
+            const uint32_t v = (uint32_t)(buf & ((1ull << n) - 1));
+            buf >>= n;
+            nb -= n;
+            pos += n;
+            if (pos > hbits) bad = true;
+            return v;
+        };
+        const uint32_t bfinal = get(1), btype = get(2);
+        const int hlit = (int)get(5) + 257, hdist = (int)get(5) + 1, hclen = (int)get(4) + 4;
+        bool ok = bfinal == 1 && btype == 2 && hlit <= 286 && hdist <= 30;
+        uint8_t cl[19] = {0};
+        for (int i = 0; i < hclen; i++) cl[CL_ORDER[i]] = (uint8_t)get(3);
+        // code-length code: 7-bit lookup table, symbol | length << 5 (0: no code)
+        uint16_t lut[128];
+        for (int i = 0; i < 128; i++) lut[i] = 0;
+        {
+            int cnt[8] = {0}, left = 1;
+            for (int i = 0; i < 19; i++) cnt[cl[i]]++;
+            cnt[0] = 0;
+            for (int b = 1; b < 8; b++) {
+                left = (left << 1) - cnt[b];
+                if (left < 0) ok = false;
+            }
+            int nc[8], cc = 0;
+            for (int b = 1; b < 8; b++) {
+                cc = (cc + cnt[b - 1]) << 1;
+                nc[b] = cc;
+            }
+            for (int i = 0; ok && i < 19; i++) {
+                const int l = cl[i];
+                if (!l) continue;
+                const uint32_t rc = bit_reverse((uint32_t)nc[l]++, l);
+                for (uint32_t k = 0; k < (1u << (7 - l)); k++) lut[rc | (k << l)] = (uint16_t)(i | (l << 5));
+            }
         }
-        int rep, val = 0;
-        if (sym == 16) {
-            if (i == 0) { ok = false; break; }
-            val = lens[i - 1];
-            rep = 3 + (int)in.get(2);
-        } else if (sym == 17) {
-            rep = 3 + (int)in.get(3);
+        const int n = hlit + hdist;
+        for (int i = 0; ok && i < n;) {
+            while (nb < 7) {
+                buf |= (unsigned long long)(bp < nh ? head[bp] : 0) << nb;
+                bp++;
+                nb += 8;
+            }
+            const uint16_t e = lut[buf & 127];
+            if (!e) { ok = false; break; }
+            const int sym = e & 31, l = e >> 5;
+            buf >>= l;
+            nb -= l;
+            pos += l;
+            if (pos > hbits) { ok = false; break; }
+            if (sym < 16) {
+                lens[i++] = (uint8_t)sym;
+                continue;
+            }
+            int rep, val = 0;
+            if (sym == 16) {
+                if (i == 0) { ok = false; break; }
+                val = lens[i - 1];
+                rep = 3 + (int)get(2);
+            } else if (sym == 17) {
+                rep = 3 + (int)get(3);
+            } else {
+                rep = 11 + (int)get(7);
+            }
+            if (i + rep > n) { ok = false; break; }
+            while (rep-- > 0) lens[i++] = (uint8_t)val;
+        }
+        ok = ok && !bad;
+        uint8_t ll[286];
+        for (int i = 0; ok && i < hlit; i++) ll[i] = lens[i];
+        ok = ok && lens[256] != 0 && build_decoder(ll, hlit, S.dcount + c * 16, S.dsym + c * DFL_NSYM);
+        if (ok) {
+            uint16_t cnt[16] = {0};
+            for (int i = 0; i < hlit; i++) cnt[lens[i]]++;
+            cnt[0] = 0;
+            uint16_t cc = 0;
+            for (int b = 1; b < 16; b++) {
+                cc = (uint16_t)((cc + cnt[b - 1]) << 1);
+                nextc[b] = cc;
+            }
+            C.hdr_bits = (uint32_t)pos;
         } else {
-            rep = 11 + (int)in.get(7);
+            atomicOr(&S.err, DFL_CORRUPT);
         }
-        if (i + rep > n) { ok = false; break; }
-        while (rep-- > 0) lens[i++] = (uint8_t)val;
+        s_ok = ok;
+        s_hlit = hlit;
     }
-    ok = ok && !in.bad && lens[256] != 0 &&
-         build_decoder(lens, hlit, S.dcount + c * 16, S.dsym + c * DFL_NSYM);
-    if (!ok) {
-        atomicOr(&S.err, DFL_CORRUPT);
-        return;
+    __syncthreads();
+    if (!s_ok) return;
+    uint16_t* tab = S.dtab + (size_t)c * (1 << DFL_LUT);
+    for (int i = tid; i < (1 << DFL_LUT); i += blockDim.x) tab[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < s_hlit; i += blockDim.x) {
+        const int l = lens[i];
+        if (l == 0 || l > DFL_LUT) continue;
+        int r = 0;
+        for (int j = 0; j < i; j++) r += lens[j] == l;
+        const uint32_t rc = bit_reverse(nextc[l] + r, l);
+        for (uint32_t k = 0; k < (1u << (DFL_LUT - l)); k++) tab[rc | (k << l)] = (uint16_t)(i | (l << 9));
     }
-    C.hdr_bits = in.pos;
 }
 
-// one thread per segment: its literals, and the end-of-block code after the last one
-__global__ void k_ifl_decode(DflArgs a) {
+// the literals of every segment: one block per component, its decoding tables
+// in shared memory, one thread per segment at a time (lookup table, longer codes
+// bit by bit); each segment must take exactly its recorded bits, and the
+// component's last one must be followed by the end-of-block code
+__global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
     DflScratch& S = *a.S;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S.err || s >= S.nseg) return;
-    const int c = S.segcomp[s];
+    const int c = blockIdx.x;
+    if (S.err) return;
     const DflComp& C = S.comp[c];
-    BitIn in{a.in + C.out_off, C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]), 8ULL * C.out_bytes, false};
-    const unsigned long long end_of_seg = in.pos + S.segbits[s];
-    const uint16_t* count = S.dcount + c * 16;
-    const uint16_t* sym = S.dsym + c * DFL_NSYM;
-    const unsigned long long b0 = (unsigned long long)(s - C.seg0) * DFL_SEG;
-    const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+    if (C.bytes == 0) return;
+    __shared__ uint16_t tab[1 << DFL_LUT];
+    __shared__ uint16_t count[16], sym[DFL_NSYM];
+    for (int i = threadIdx.x; i < (1 << DFL_LUT); i += blockDim.x) tab[i] = S.dtab[(size_t)c * (1 << DFL_LUT) + i];
+    for (int i = threadIdx.x; i < DFL_NSYM; i += blockDim.x) sym[i] = S.dsym[c * DFL_NSYM + i];
+    if (threadIdx.x < 16) count[threadIdx.x] = S.dcount[c * 16 + threadIdx.x];
+    __syncthreads();
+    const uint8_t* p = a.in + C.out_off;
+    const unsigned long long nbytes = C.out_bytes, end = 8ULL * nbytes;
     uint8_t* o = a.out + C.in_off;
+    const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
     bool ok = true;
-    for (unsigned long long i = b0; i < b1; i++) {
-        const int v = decode_sym(in, count, sym);
-        if (in.bad || v < 0 || v > 255) { ok = false; break; }
-        o[i] = (uint8_t)v;
+    for (uint32_t k = threadIdx.x; ok && k < nseg; k += blockDim.x) {
+        const uint32_t s = C.seg0 + k;
+        const unsigned long long start = C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
+        const unsigned long long stop = start + S.segbits[s];
+        // bit buffer: buf holds nb bits, the next of them at bit 0; bytes past the stream read as 0
+        unsigned long long buf = 0, bp = start >> 3, pos = start;
+        int nb = 0;
+        // four independent byte loads per refill, so that their latencies overlap
+        auto refill = [&]() {
+            uint32_t x = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) x |= (uint32_t)(bp + k < nbytes ? p[bp + k] : 0) << (8 * k);
+            buf |= (unsigned long long)x << nb;
+            bp += 4;
+            nb += 32;
+        };
+        refill();
+        buf >>= (start & 7);
+        nb -= (int)(start & 7);
+        auto next = [&]() -> int {
+            if (nb < 16) refill();
+            const uint16_t e = tab[buf & ((1u << DFL_LUT) - 1)];
+            if (e) {
+                const int l = e >> 9;
+                buf >>= l;
+                nb -= l;
+                pos += l;
+                return e & 511;
+            }
+            int code = 0, first = 0, index = 0;
+            for (int l = 1; l <= 15; l++) {
+                code |= (int)(buf & 1);
+                buf >>= 1;
+                nb--;
+                pos++;
+                const int n = count[l];
+                if (code - first < n) return sym[index + code - first];
+                index += n;
+                first = (first + n) << 1;
+                code <<= 1;
+            }
+            return -1;
+        };
+        const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
+        const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+        for (unsigned long long i = b0; i < b1; i++) {
+            const int v = next();
+            if (v < 0 || v > 255) { ok = false; break; }
+            o[i] = (uint8_t)v;
+        }
+        ok = ok && pos == stop && pos <= end;
+        if (ok && k + 1 == nseg) ok = next() == 256 && pos <= end;
     }
-    ok = ok && in.pos == end_of_seg;
-    if (ok && (s + 1 == S.comp[c + 1].seg0 || s + 1 == S.nseg)) ok = decode_sym(in, count, sym) == 256 && !in.bad;
     if (!ok) atomicOr(&S.err, DFL_CORRUPT);
 }
 

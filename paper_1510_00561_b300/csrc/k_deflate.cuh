@@ -9,6 +9,7 @@ constexpr int DFL_SEG = 256;         // input bytes per segment (one thread each
 constexpr int DFL_NLIT = 257;        // literal bytes and the end-of-block code
 constexpr int DFL_NSYM = 288;        // decoding table entries per component
 constexpr int DFL_HDR_BYTES = 512;   // room for one dynamic block header
+constexpr int DFL_LUT = 11;          // bits of the inflate lookup table
 
 enum : uint32_t { DFL_CORRUPT = 1, DFL_CAPACITY = 2, DFL_INTERNAL = 4 };
 
@@ -31,6 +32,7 @@ struct DflScratch {
     uint8_t* hdr;           // ncomp x DFL_HDR_BYTES block headers
     uint16_t* dcount;       // ncomp x 16 decoding: codes per length
     uint16_t* dsym;         // ncomp x DFL_NSYM decoding: symbols by code
+    uint16_t* dtab;         // ncomp x 2^DFL_LUT decoding: symbol | length << 9 by the next bits
     uint32_t* segbits;      // max_seg + 1
     uint32_t* segoff;       // max_seg + 1 (exclusive scan of segbits)
     int* segcomp;           // max_seg
