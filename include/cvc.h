@@ -281,9 +281,12 @@ cvc_status cvc_codec_inspect(const cvc_codec* codec, int which, float* d_out, si
  * (each byte-aligned, its header, literals and end-of-block code), then the
  * motion vectors of a type-2 frame.  Any inflater decodes each stream alone;
  * the segment lengths are the entry points of the parallel inflate.
- * A context holds device scratch for frames of one parameter set.          */
+ * A context holds device scratch for up to max_frames frames of one
+ * parameter set (cvc_deflate_create: 1); a call covers any number of frames
+ * up to it in one launch sequence.                                         */
 typedef struct cvc_deflate_ctx cvc_deflate_ctx;
 cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out);
+cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cvc_deflate_ctx** out);
 cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx);
 /* d_in: one frame of cvc_encode_frame (version byte 1, possibly without some
  * levels, cvc_stream_drop_levels) in device memory; d_out (device, 4-byte
@@ -299,6 +302,16 @@ cvc_status cvc_deflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t i
  * code).  Synchronises `stream`.                                            */
 cvc_status cvc_inflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t in_len, uint8_t* d_out,
                              size_t out_cap, size_t* out_len, cvc_stream_t stream);
+/* the same for n frames at once (n <= the context's max_frames): the pointer
+ * and size arrays are HOST arrays of n entries (the buffers they point to
+ * are device memory); out_len[i] and status[i] (may be NULL) are per frame.
+ * Returns INVALID_ARG or CUDA for the call, else the first non-OK status.  */
+cvc_status cvc_deflate_frames(cvc_deflate_ctx* ctx, int n, const uint8_t* const* d_in, const size_t* in_len,
+                              uint8_t* const* d_out, const size_t* out_cap, size_t* out_len, cvc_status* status,
+                              cvc_stream_t stream);
+cvc_status cvc_inflate_frames(cvc_deflate_ctx* ctx, int n, const uint8_t* const* d_in, const size_t* in_len,
+                              uint8_t* const* d_out, const size_t* out_cap, size_t* out_len, cvc_status* status,
+                              cvc_stream_t stream);
 
 /* --------------------------------------------------------------- batches
  * Many independent streams, each with its own cvc_params (any mix of frame

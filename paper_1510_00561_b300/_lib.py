@@ -122,6 +122,11 @@ def lib():
         L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
         L.cvc_decode_frame_scaled.argtypes = [_P, _P, _SZ, _I, _P, _SZ, _P]
         L.cvc_deflate_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_P)]
+        L.cvc_deflate_create_batch.argtypes = [ctypes.POINTER(Params), _I, ctypes.POINTER(_P)]
+        L.cvc_deflate_frames.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_SZ), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
+        L.cvc_inflate_frames.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_SZ), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_deflate_destroy.argtypes = [_P]
         L.cvc_deflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]
         L.cvc_inflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]

@@ -235,11 +235,13 @@ class Deflater:
     """The DEFLATE stage (§3.9, scalable mode) for frames of one parameter set:
     per-component Huffman-only DEFLATE streams on the GPU (cvc_deflate_*)."""
 
-    def __init__(self, **stream):
+    def __init__(self, max_frames=1, **stream):
         prm = _L.params(**stream)
         p = ctypes.c_void_p()
-        _L.check(_L.lib().cvc_deflate_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_deflate_create")
+        _L.check(_L.lib().cvc_deflate_create_batch(ctypes.byref(prm), int(max_frames), ctypes.byref(p)),
+                 "cvc_deflate_create_batch")
         self._h = p
+        self.max_frames = max_frames
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -270,6 +272,25 @@ class Deflater:
         """the frame inside a deflated frame (uint8 CUDA tensors)."""
         return self._run(_L.lib().cvc_inflate_frame, "cvc_inflate_frame", packed, out, 8 * packed.numel() + 65536,
                          stream)
+
+    def _many(self, fn, name, srcs, outs, stream):
+        n = len(srcs)
+        P, Z = ctypes.c_void_p * n, ctypes.c_size_t * n
+        lens, sts = Z(), (ctypes.c_int * n)()
+        st = fn(self._h, n, P(*[_ptr(x) for x in srcs]), Z(*[x.numel() for x in srcs]), P(*[_ptr(o) for o in outs]),
+                Z(*[o.numel() for o in outs]), lens, sts, _stream(stream))
+        if st in (1, 6):
+            raise _L.CvcError(st, name)
+        return [o[:lens[i]] if sts[i] == 0 else None for i, o in enumerate(outs)], list(sts)
+
+    def deflate_many(self, frames, outs, stream=None):
+        """deflate up to max_frames frames in one launch sequence (cvc_deflate_frames);
+        returns (views of outs, per-frame statuses)."""
+        return self._many(_L.lib().cvc_deflate_frames, "cvc_deflate_frames", frames, outs, stream)
+
+    def inflate_many(self, packed, outs, stream=None):
+        """inflate up to max_frames deflated frames in one launch sequence (cvc_inflate_frames)."""
+        return self._many(_L.lib().cvc_inflate_frames, "cvc_inflate_frames", packed, outs, stream)
 
 
 def _info(fn, h, i=None):

@@ -453,20 +453,24 @@ cvc_status cvc_codec_inspect(const cvc_codec* c, int which, float* d_out, size_t
 
 // --------------------------------------------------------------- DEFLATE
 struct cvc_deflate_ctx {
-    int ncomp = 0, max_seg = 0;
+    int ncomp = 0, max_seg = 0, max_frames = 0;
     long long hdr_bytes = 0, mv_bytes = 0;
     void* arena = nullptr;
-    DflScratch* d_S = nullptr;
-    DflScratch ptrs;             // host copy of the device pointers
-    DflScratch* h_S = nullptr;   // pinned: the scalars come back through it
+    DflScratch* d_S = nullptr;          // max_frames scratch records
+    std::vector<DflScratch> ptrs;       // host copies of their device pointers
+    DflFrame* d_fr = nullptr;           // the frames of a call
+    DflFrame* h_fr = nullptr;           // pinned staging of d_fr
+    DflScratch* h_S = nullptr;          // pinned: the scalars come back through it
+    uint32_t *segbits = nullptr, *segoff = nullptr, *scan_tmp = nullptr;   // all frames
     ~cvc_deflate_ctx() {
         if (arena) cudaFree(arena);
         if (h_S) cudaFreeHost(h_S);
+        if (h_fr) cudaFreeHost(h_fr);
     }
 };
 
-cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
-    if (!out) return CVC_ERR_INVALID_ARG;
+cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cvc_deflate_ctx** out) {
+    if (!out || max_frames < 1 || max_frames > 4096) return CVC_ERR_INVALID_ARG;
     *out = nullptr;
     Core core;   // the stream's layout: component count, token bound (host only)
     cvc_status s = core_plan(&core, params, 1);
@@ -477,13 +481,14 @@ cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
     x->ncomp = D.ncomp;
     x->hdr_bytes = D.hdr_bytes;
     x->mv_bytes = D.mv_bytes;
+    x->max_frames = max_frames;
     const long long segs = (2 * D.max_tok + DFL_SEG - 1) / DFL_SEG + D.ncomp;
-    if (segs > (1LL << 30)) {
+    if (segs * max_frames > (1LL << 30)) {
         delete x;
         return CVC_ERR_UNSUPPORTED;
     }
     x->max_seg = (int)segs;
-    const size_t n = (size_t)x->ncomp, m = (size_t)x->max_seg;
+    const size_t n = (size_t)x->ncomp, m = (size_t)x->max_seg, F = (size_t)max_frames;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         off = (off + 255) & ~size_t(255);
@@ -491,36 +496,51 @@ cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
         off += std::max<size_t>(bytes, 1);
         return at;
     };
-    const size_t o_S = take(sizeof(DflScratch)), o_comp = take((n + 1) * sizeof(DflComp)),
-                 o_hist = take(n * DFL_NLIT * 4), o_len = take(n * DFL_NLIT), o_code = take(n * DFL_NLIT * 2),
-                 o_hdr = take(n * DFL_HDR_BYTES), o_dc = take(n * 16 * 2), o_ds = take(n * DFL_NSYM * 2),
-                 o_dt = take(n * (1 << DFL_LUT) * 2),
-                 o_sb = take((m + 1) * 4), o_so = take((m + 1) * 4), o_sc = take(m * 4),
-                 o_tmp = take(((m + 2047) / 2048 + 8) * 4);
+    const size_t o_S = take(F * sizeof(DflScratch)), o_fr = take(F * sizeof(DflFrame)),
+                 o_sb = take((F * (m + 1)) * 4), o_so = take((F * (m + 1) + 1) * 4),
+                 o_tmp = take(((F * (m + 1) + 2047) / 2048 + 8) * 4);
+    std::vector<size_t> o_comp(F), o_hist(F), o_len(F), o_code(F), o_hdr(F), o_dc(F), o_ds(F), o_dt(F), o_sc(F);
+    for (size_t f = 0; f < F; f++) {
+        o_comp[f] = take((n + 1) * sizeof(DflComp));
+        o_hist[f] = take(n * DFL_NLIT * 4);
+        o_len[f] = take(n * DFL_NLIT);
+        o_code[f] = take(n * DFL_NLIT * 2);
+        o_hdr[f] = take(n * DFL_HDR_BYTES);
+        o_dc[f] = take(n * 16 * 2);
+        o_ds[f] = take(n * DFL_NSYM * 2);
+        o_dt[f] = take(n * (1 << DFL_LUT) * 2);
+        o_sc[f] = take(m * 4);
+    }
     if (cudaMalloc(&x->arena, off) != cudaSuccess ||
-        cudaMallocHost((void**)&x->h_S, sizeof(DflScratch)) != cudaSuccess) {
+        cudaMallocHost((void**)&x->h_S, F * sizeof(DflScratch)) != cudaSuccess ||
+        cudaMallocHost((void**)&x->h_fr, F * sizeof(DflFrame)) != cudaSuccess) {
         cudaGetLastError();
         delete x;
         return CVC_ERR_NOMEM;
     }
     char* b = static_cast<char*>(x->arena);
-    DflScratch S;
-    memset(&S, 0, sizeof(S));
-    S.comp = reinterpret_cast<DflComp*>(b + o_comp);
-    S.hist = reinterpret_cast<uint32_t*>(b + o_hist);
-    S.len = reinterpret_cast<uint8_t*>(b + o_len);
-    S.code = reinterpret_cast<uint16_t*>(b + o_code);
-    S.hdr = reinterpret_cast<uint8_t*>(b + o_hdr);
-    S.dcount = reinterpret_cast<uint16_t*>(b + o_dc);
-    S.dsym = reinterpret_cast<uint16_t*>(b + o_ds);
-    S.dtab = reinterpret_cast<uint16_t*>(b + o_dt);
-    S.segbits = reinterpret_cast<uint32_t*>(b + o_sb);
-    S.segoff = reinterpret_cast<uint32_t*>(b + o_so);
-    S.segcomp = reinterpret_cast<int*>(b + o_sc);
-    S.scan_tmp = reinterpret_cast<uint32_t*>(b + o_tmp);
     x->d_S = reinterpret_cast<DflScratch*>(b + o_S);
-    x->ptrs = S;
-    if (cudaMemcpy(x->d_S, &S, sizeof(S), cudaMemcpyHostToDevice) != cudaSuccess) {
+    x->d_fr = reinterpret_cast<DflFrame*>(b + o_fr);
+    x->segbits = reinterpret_cast<uint32_t*>(b + o_sb);
+    x->segoff = reinterpret_cast<uint32_t*>(b + o_so);
+    x->scan_tmp = reinterpret_cast<uint32_t*>(b + o_tmp);
+    x->ptrs.assign(F, DflScratch{});
+    for (size_t f = 0; f < F; f++) {
+        DflScratch& S = x->ptrs[f];
+        memset(&S, 0, sizeof(S));
+        S.comp = reinterpret_cast<DflComp*>(b + o_comp[f]);
+        S.hist = reinterpret_cast<uint32_t*>(b + o_hist[f]);
+        S.len = reinterpret_cast<uint8_t*>(b + o_len[f]);
+        S.code = reinterpret_cast<uint16_t*>(b + o_code[f]);
+        S.hdr = reinterpret_cast<uint8_t*>(b + o_hdr[f]);
+        S.dcount = reinterpret_cast<uint16_t*>(b + o_dc[f]);
+        S.dsym = reinterpret_cast<uint16_t*>(b + o_ds[f]);
+        S.dtab = reinterpret_cast<uint16_t*>(b + o_dt[f]);
+        S.segbits = x->segbits + f * (m + 1);
+        S.segoff = x->segoff + f * (m + 1);
+        S.segcomp = reinterpret_cast<int*>(b + o_sc[f]);
+    }
+    if (cudaMemcpy(x->d_S, x->ptrs.data(), F * sizeof(DflScratch), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         delete x;
         return CVC_ERR_CUDA;
@@ -529,72 +549,105 @@ cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
     return CVC_OK;
 }
 
+cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
+    return cvc_deflate_create_batch(params, 1, out);
+}
+
 cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx) {
     delete ctx;
     return CVC_OK;
 }
 
-static cvc_status dfl_finish(cvc_deflate_ctx* x, cudaStream_t st, size_t* out_len, long long launches) {
-    if (cudaMemcpyAsync(x->h_S, x->d_S, sizeof(DflScratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+// per-frame statuses and lengths after a call; returns the first non-OK one
+static cvc_status dfl_finish(cvc_deflate_ctx* x, int nf, cudaStream_t st, size_t* out_len, cvc_status* status,
+                             long long launches) {
+    if (cudaMemcpyAsync(x->h_S, x->d_S, nf * sizeof(DflScratch), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
     note_launches(launches);
-    const DflScratch& S = *x->h_S;
-    *out_len = (size_t)S.total;
-    if (S.err & DFL_INTERNAL) return CVC_ERR_CUDA;
-    if (S.err & DFL_CORRUPT) return CVC_ERR_CORRUPT;
-    if (S.err & DFL_CAPACITY) return CVC_ERR_CAPACITY;
-    return CVC_OK;
+    cvc_status first = CVC_OK;
+    for (int f = 0; f < nf; f++) {
+        const DflScratch& S = x->h_S[f];
+        cvc_status v = CVC_OK;
+        if (S.err & DFL_INTERNAL) v = CVC_ERR_CUDA;
+        else if (S.err & DFL_CORRUPT) v = CVC_ERR_CORRUPT;
+        else if (S.err & DFL_CAPACITY) v = CVC_ERR_CAPACITY;
+        out_len[f] = (size_t)S.total;
+        if (status) status[f] = v;
+        if (first == CVC_OK) first = v;
+    }
+    return first;
+}
+
+// stage the frame table of a call; false on bad arguments
+static bool dfl_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* d_in, const size_t* in_len,
+                       uint8_t* const* d_out, const size_t* out_cap, bool aligned_out, cudaStream_t st) {
+    if (!x || nf < 1 || nf > x->max_frames || !d_in || !in_len || !d_out || !out_cap) return false;
+    for (int f = 0; f < nf; f++) {
+        if (!d_in[f] || !d_out[f] || (aligned_out && ((uintptr_t)d_out[f] & 3))) return false;
+        // whole words only: the streams are OR-ed in 32-bit words
+        x->h_fr[f] = DflFrame{d_in[f], (long long)std::min<size_t>(in_len[f], (size_t)1 << 62), d_out[f],
+                              (long long)(std::min<size_t>(out_cap[f], (size_t)1 << 62) & ~(size_t)3), x->d_S + f};
+    }
+    return cudaMemcpyAsync(x->d_fr, x->h_fr, nf * sizeof(DflFrame), cudaMemcpyHostToDevice, st) == cudaSuccess;
+}
+
+cvc_status cvc_deflate_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* d_in, const size_t* in_len,
+                              uint8_t* const* d_out, const size_t* out_cap, size_t* out_len, cvc_status* status,
+                              cvc_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out_len || !dfl_frames(x, nf, d_in, in_len, d_out, out_cap, true, st)) return CVC_ERR_INVALID_ARG;
+    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg};
+    const dim3 one(1, nf), comps(x->ncomp, nf);
+    k_dfl_plan<<<one, 256, 0, st>>>(a);
+    k_dfl_hist<<<comps, 256, 0, st>>>(a);
+    k_dfl_code<<<comps, 256, 0, st>>>(a);
+    k_dfl_layout<<<one, 256, 0, st>>>(a);
+    k_dfl_seglen<<<comps, 256, 0, st>>>(a);
+    // one scan over every frame's slice; each frame only takes differences inside it
+    if (exclusive_scan(x->segbits, (uint32_t)(nf * (x->max_seg + 1)), x->segoff, x->scan_tmp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    k_dfl_zero<<<dim3(64, nf), 256, 0, st>>>(a);
+    k_dfl_write<<<comps, 256, 0, st>>>(a);
+    k_dfl_tables<<<dim3(16, nf), 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
+    return dfl_finish(x, nf, st, out_len, status, 11);
+}
+
+cvc_status cvc_inflate_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* d_in, const size_t* in_len,
+                              uint8_t* const* d_out, const size_t* out_cap, size_t* out_len, cvc_status* status,
+                              cvc_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out_len || !dfl_frames(x, nf, d_in, in_len, d_out, out_cap, false, st)) return CVC_ERR_INVALID_ARG;
+    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg};
+    const dim3 one(1, nf), comps(x->ncomp, nf);
+    k_ifl_plan<<<one, 256, 0, st>>>(a);
+    k_ifl_seglen<<<dim3((x->max_seg + 255) / 256, nf), 256, 0, st>>>(a);
+    if (exclusive_scan(x->segbits, (uint32_t)(nf * (x->max_seg + 1)), x->segoff, x->scan_tmp, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    k_ifl_tables<<<comps, 128, 0, st>>>(a);
+    k_ifl_decode<<<comps, 256, 0, st>>>(a);
+    k_ifl_finish<<<dim3(16, nf), 256, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
+    return dfl_finish(x, nf, st, out_len, status, 8);
 }
 
 cvc_status cvc_deflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_len, uint8_t* d_out, size_t out_cap,
                              size_t* out_len, cvc_stream_t stream) {
-    if (!x || !d_in || !d_out || !out_len || ((uintptr_t)d_out & 3)) return CVC_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    // whole words only: the streams are OR-ed in 32-bit words
-    const DflArgs a{d_in, (long long)std::min<size_t>(in_len, (size_t)1 << 62), d_out,
-                    (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
-                    x->ncomp, x->max_seg, x->d_S};
-    k_dfl_plan<<<1, 256, 0, st>>>(a);
-    k_dfl_hist<<<x->ncomp, 256, 0, st>>>(a);
-    k_dfl_code<<<x->ncomp, 256, 0, st>>>(a);
-    k_dfl_layout<<<1, 256, 0, st>>>(a);
-    k_dfl_seglen<<<x->ncomp, 256, 0, st>>>(a);
-    const DflScratch& S = x->ptrs;
-    if (exclusive_scan_dev(S.segbits, &x->d_S->nseg, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
-        cudaGetLastError();
-        return CVC_ERR_CUDA;
-    }
-    k_dfl_zero<<<148 * 4, 256, 0, st>>>(a);
-    k_dfl_write<<<x->ncomp, 256, 0, st>>>(a);
-    k_dfl_tables<<<64, 256, 0, st>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
-    return dfl_finish(x, st, out_len, 11);
+    if (!x || !d_in || !d_out || !out_len) return CVC_ERR_INVALID_ARG;
+    return cvc_deflate_frames(x, 1, &d_in, &in_len, &d_out, &out_cap, out_len, nullptr, stream);
 }
 
 cvc_status cvc_inflate_frame(cvc_deflate_ctx* x, const uint8_t* d_in, size_t in_len, uint8_t* d_out, size_t out_cap,
                              size_t* out_len, cvc_stream_t stream) {
     if (!x || !d_in || !d_out || !out_len) return CVC_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    // whole words only: the streams are OR-ed in 32-bit words
-    const DflArgs a{d_in, (long long)std::min<size_t>(in_len, (size_t)1 << 62), d_out,
-                    (long long)(std::min<size_t>(out_cap, (size_t)1 << 62) & ~(size_t)3), x->hdr_bytes, x->mv_bytes,
-                    x->ncomp, x->max_seg, x->d_S};
-    const int sg = (x->max_seg + 255) / 256;
-    k_ifl_plan<<<1, 256, 0, st>>>(a);
-    k_ifl_seglen<<<sg, 256, 0, st>>>(a);
-    const DflScratch& S = x->ptrs;
-    if (exclusive_scan(S.segbits, (uint32_t)x->max_seg, S.segoff, S.scan_tmp, st) != cudaSuccess) {
-        cudaGetLastError();
-        return CVC_ERR_CUDA;
-    }
-    k_ifl_tables<<<x->ncomp, 128, 0, st>>>(a);
-    k_ifl_decode<<<x->ncomp, 256, 0, st>>>(a);
-    k_ifl_finish<<<64, 256, 0, st>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
-    return dfl_finish(x, st, out_len, 8);
+    return cvc_inflate_frames(x, 1, &d_in, &in_len, &d_out, &out_cap, out_len, nullptr, stream);
 }
 
 // --------------------------------------------------------------- batches

@@ -271,14 +271,15 @@ __device__ void small_huffman(const uint32_t* f, int n, int maxlen, uint8_t* len
 // -------------------------------------------------------------- deflate
 // component byte offsets of the input tokens and the segments (one block)
 __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     __shared__ unsigned long long sh[8];
     __shared__ int s_bad;
-    const uint8_t* in = a.in;
+    const uint8_t* in = F.in;
     if (threadIdx.x == 0) {
         S.err = 0;
         S.total = 0;
-        s_bad = a.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] != 0 ||
+        s_bad = F.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] != 0 ||
                 rd32(in + 28) != (uint32_t)a.ncomp;
         if (s_bad) S.err = DFL_CORRUPT;
     }
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
         const int type = in[6];
         const long long mvb = type == 2 ? a.mv_bytes : 0;
         if ((type == 2 && a.mv_bytes == 0) || seg > (unsigned long long)a.max_seg ||
-            a.hdr_bytes + 2 * tok + mvb > (unsigned long long)a.in_len) {
+            a.hdr_bytes + 2 * tok + mvb > (unsigned long long)F.in_len) {
             S.err = DFL_CORRUPT;
             return;
         }
@@ -315,13 +316,14 @@ __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
 
 // byte histogram of each component: one block per component
 __global__ void __launch_bounds__(256) k_dfl_hist(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     if (S.err) return;
     const int c = blockIdx.x;
     __shared__ uint32_t h[8][256];     // one per warp: the few common bytes collide less
     for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i >> 8][i & 255] = 0;
     __syncthreads();
-    const uint8_t* p = a.in + S.comp[c].in_off;
+    const uint8_t* p = F.in + S.comp[c].in_off;
     const unsigned long long n = S.comp[c].bytes;
     uint32_t* hw = h[(threadIdx.x >> 5) & 7];
     for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hw[p[i]], 1u);
@@ -339,7 +341,8 @@ __global__ void __launch_bounds__(256) k_dfl_hist(DflArgs a) {
 // weights halved while a code would be longer than 15 bits), canonical codes,
 // the run-length coded block header and its bit length
 __global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const int c = blockIdx.x, tid = threadIdx.x;
     if (S.err) return;
     DflComp& C = S.comp[c];
@@ -532,7 +535,8 @@ __global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
 
 // stream offsets, container layout, the size check (one block)
 __global__ void __launch_bounds__(256) k_dfl_layout(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     __shared__ unsigned long long sh[8];
     if (S.err) return;
     const unsigned long long tables = a.hdr_bytes + 4ULL * a.ncomp + ((2ULL * S.nseg + 3) & ~3ULL);
@@ -554,14 +558,15 @@ __global__ void __launch_bounds__(256) k_dfl_layout(DflArgs a) {
     if (threadIdx.x == 0) {
         S.streams = tables;
         S.total = off + S.tail;
-        if (S.total > (unsigned long long)a.out_cap) S.err = DFL_CAPACITY;
+        if (S.total > (unsigned long long)F.out_cap) S.err = DFL_CAPACITY;
     }
 }
 
 // bit length of every segment: one block per component, its code lengths in
 // shared memory, one thread per segment at a time
 __global__ void __launch_bounds__(256) k_dfl_seglen(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const int c = blockIdx.x;
     if (S.err) return;
     const DflComp& C = S.comp[c];
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(256) k_dfl_seglen(DflArgs a) {
     __shared__ uint8_t len[DFL_NLIT];
     for (int i = threadIdx.x; i < DFL_NLIT; i += blockDim.x) len[i] = S.len[c * DFL_NLIT + i];
     __syncthreads();
-    const uint8_t* p = a.in + C.in_off;
+    const uint8_t* p = F.in + C.in_off;
     const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
     for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
         const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
@@ -583,9 +588,10 @@ __global__ void __launch_bounds__(256) k_dfl_seglen(DflArgs a) {
 
 // zero the words of the stream region (the streams are OR-ed in)
 __global__ void k_dfl_zero(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     if (S.err) return;
-    uint32_t* w = reinterpret_cast<uint32_t*>(a.out);
+    uint32_t* w = reinterpret_cast<uint32_t*>(F.out);
     const unsigned long long w0 = S.streams >> 2, w1 = (S.total - S.tail + 3) >> 2;
     for (unsigned long long i = w0 + blockIdx.x * blockDim.x + threadIdx.x; i < w1; i += gridDim.x * blockDim.x)
         w[i] = 0;
@@ -603,7 +609,8 @@ __device__ __forceinline__ void or_bits(uint32_t* w, unsigned long long ab, uint
 // memory, one thread per segment at a time; thread 0 adds the header, the
 // thread of the last segment the end-of-block code
 __global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const int c = blockIdx.x;
     if (S.err) return;
     const DflComp& C = S.comp[c];
@@ -615,13 +622,13 @@ __global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
         code[i] = S.code[c * DFL_NLIT + i];
     }
     __syncthreads();
-    uint32_t* w = reinterpret_cast<uint32_t*>(a.out);
+    uint32_t* w = reinterpret_cast<uint32_t*>(F.out);
     const unsigned long long base = 8ULL * C.out_off;
     if (threadIdx.x == 0) {
         const uint8_t* hb = S.hdr + (size_t)c * DFL_HDR_BYTES;
         for (uint32_t b = 0; b < C.hdr_bits; b += 8) or_bits(w, base + b, hb[b >> 3], (int)min(8u, C.hdr_bits - b));
     }
-    const uint8_t* p = a.in + C.in_off;
+    const uint8_t* p = F.in + C.in_off;
     const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
     for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
         const uint32_t s = C.seg0 + k;
@@ -650,11 +657,12 @@ __global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
 
 // container tables and the motion vectors (after the streams are written)
 __global__ void k_dfl_tables(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     if (S.err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    uint8_t* o = a.out;
-    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? 2 : a.in[i];   // version 2: deflated
+    uint8_t* o = F.out;
+    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? 2 : F.in[i];   // version 2: deflated
     for (int c = t; c < a.ncomp; c += nt) wr32(o + a.hdr_bytes + 4 * c, (uint32_t)S.comp[c].out_bytes);
     uint8_t* st = o + a.hdr_bytes + 4 * a.ncomp;
     for (uint32_t s = t; s < S.nseg; s += nt) {
@@ -663,21 +671,22 @@ __global__ void k_dfl_tables(DflArgs a) {
     }
     for (uint32_t s = 2 * S.nseg + t; s < ((2 * S.nseg + 3) & ~3u); s += nt) st[s] = 0;
     const unsigned long long tail_in = a.hdr_bytes + S.tok_bytes, tail_out = S.total - S.tail;
-    for (unsigned long long i = t; i < S.tail; i += nt) o[tail_out + i] = a.in[tail_in + i];
+    for (unsigned long long i = t; i < S.tail; i += nt) o[tail_out + i] = F.in[tail_in + i];
 }
 
 // -------------------------------------------------------------- inflate
 // the container's tables: token offsets, segments, stream offsets (one block)
 __global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     __shared__ unsigned long long sh[8];
     __shared__ int s_bad;
-    const uint8_t* in = a.in;
+    const uint8_t* in = F.in;
     const unsigned long long tabs = a.hdr_bytes + 4ULL * a.ncomp;
     if (threadIdx.x == 0) {
         S.err = 0;
         S.total = 0;
-        s_bad = a.in_len < (long long)tabs || rd32(in) != 0x31435643u || in[4] != 2 || in[5] != 0 ||
+        s_bad = F.in_len < (long long)tabs || rd32(in) != 0x31435643u || in[4] != 2 || in[5] != 0 ||
                 rd32(in + 28) != (uint32_t)a.ncomp;
         if (s_bad) S.err = DFL_CORRUPT;
     }
@@ -711,27 +720,28 @@ __global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
         S.comp[a.ncomp].seg0 = (uint32_t)seg;
         const long long mvb = in[6] == 2 ? a.mv_bytes : 0;
         if (seg > (unsigned long long)a.max_seg || (in[6] == 2 && a.mv_bytes == 0) ||
-            streams + sb + mvb > (unsigned long long)a.in_len)
+            streams + sb + mvb > (unsigned long long)F.in_len)
             atomicOr(&S.err, DFL_CORRUPT);
         S.nseg = (uint32_t)seg;
         S.tok_bytes = 2 * tok;
         S.tail = mvb;
         S.streams = streams + sb;                  // where the motion vectors start
         S.total = a.hdr_bytes + 2 * tok + mvb;
-        if (S.total > (unsigned long long)a.out_cap) atomicOr(&S.err, DFL_CAPACITY);
+        if (S.total > (unsigned long long)F.out_cap) atomicOr(&S.err, DFL_CAPACITY);
     }
 }
 
 // segment bit lengths from the container, with their component
 __global__ void k_ifl_seglen(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (S.err || s >= (uint32_t)a.max_seg) return;
     if (s >= S.nseg) {
         S.segbits[s] = 0;
         return;
     }
-    const uint8_t* st = a.in + a.hdr_bytes + 4 * a.ncomp;
+    const uint8_t* st = F.in + a.hdr_bytes + 4 * a.ncomp;
     S.segbits[s] = (uint32_t)st[2 * s] | ((uint32_t)st[2 * s + 1] << 8);
     int lo = 0, hi = a.ncomp;
     while (hi - lo > 1) {
@@ -749,7 +759,8 @@ __global__ void k_ifl_seglen(DflArgs a) {
 // stream (symbol | length << 9; 0 for longer codes, which take the
 // bit-serial canonical decoder)
 __global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const int c = blockIdx.x, tid = threadIdx.x;
     if (S.err) return;
     DflComp& C = S.comp[c];
@@ -759,7 +770,7 @@ __global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
     __shared__ uint16_t nextc[16];
     __shared__ uint8_t head[DFL_HDR_BYTES];     // a valid block header fits
     const unsigned long long nh = min((unsigned long long)DFL_HDR_BYTES, C.out_bytes);
-    for (unsigned long long i = tid; i < nh; i += blockDim.x) head[i] = a.in[C.out_off + i];
+    for (unsigned long long i = tid; i < nh; i += blockDim.x) head[i] = F.in[C.out_off + i];
     __syncthreads();
     if (tid == 0) {
         // bits of the header, LSB first, from shared memory through a 64-bit buffer
@@ -879,7 +890,8 @@ __global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
 // bit by bit); each segment must take exactly its recorded bits, and the
 // component's last one must be followed by the end-of-block code
 __global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     const int c = blockIdx.x;
     if (S.err) return;
     const DflComp& C = S.comp[c];
@@ -890,9 +902,9 @@ __global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
     for (int i = threadIdx.x; i < DFL_NSYM; i += blockDim.x) sym[i] = S.dsym[c * DFL_NSYM + i];
     if (threadIdx.x < 16) count[threadIdx.x] = S.dcount[c * 16 + threadIdx.x];
     __syncthreads();
-    const uint8_t* p = a.in + C.out_off;
+    const uint8_t* p = F.in + C.out_off;
     const unsigned long long nbytes = C.out_bytes, end = 8ULL * nbytes;
-    uint8_t* o = a.out + C.in_off;
+    uint8_t* o = F.out + C.in_off;
     const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
     bool ok = true;
     for (uint32_t k = threadIdx.x; ok && k < nseg; k += blockDim.x) {
@@ -952,13 +964,14 @@ __global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
 }
 
 __global__ void k_ifl_finish(DflArgs a) {
-    DflScratch& S = *a.S;
+    const DflFrame& F = a.fr[blockIdx.y];
+    DflScratch& S = *F.S;
     if (S.err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    uint8_t* o = a.out;
-    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? 1 : a.in[i];
+    uint8_t* o = F.out;
+    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? 1 : F.in[i];
     const unsigned long long tail_out = a.hdr_bytes + S.tok_bytes;
-    for (unsigned long long i = t; i < S.tail; i += nt) o[tail_out + i] = a.in[S.streams + i];
+    for (unsigned long long i = t; i < S.tail; i += nt) o[tail_out + i] = F.in[S.streams + i];
 }
 
 }  // namespace cvc

@@ -33,23 +33,27 @@ struct DflScratch {
     uint16_t* dcount;       // ncomp x 16 decoding: codes per length
     uint16_t* dsym;         // ncomp x DFL_NSYM decoding: symbols by code
     uint16_t* dtab;         // ncomp x 2^DFL_LUT decoding: symbol | length << 9 by the next bits
-    uint32_t* segbits;      // max_seg + 1
-    uint32_t* segoff;       // max_seg + 1 (exclusive scan of segbits)
+    uint32_t* segbits;      // max_seg + 1 (the frame's slice of one array for all frames)
+    uint32_t* segoff;       // max_seg + 1 (exclusive scan of that array, up to a constant per frame)
     int* segcomp;           // max_seg
-    uint32_t* scan_tmp;
     uint32_t err, nseg;
     unsigned long long tok_bytes, tail, total, streams;
 };
 
-struct DflArgs {
+// one frame of a call (grid dimension y)
+struct DflFrame {
     const uint8_t* in;
     long long in_len;
     uint8_t* out;
     long long out_cap;
+    DflScratch* S;          // device: the frame's scratch
+};
+
+struct DflArgs {
+    const DflFrame* fr;     // device: one per frame of the call
     long long hdr_bytes;    // 32 + 4 ncomp
     long long mv_bytes;     // motion vectors of a type-2 frame
     int ncomp, max_seg;
-    DflScratch* S;          // device
 };
 
 __global__ void k_dfl_plan(DflArgs a);

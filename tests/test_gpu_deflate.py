@@ -188,3 +188,30 @@ def test_dropping_levels_of_deflated_frames():
             assert np.array_equal(thin, ref)
             back = dfl.inflate(torch.from_numpy(thin).cuda()).clone()
             assert torch.equal(part.decode(back, scale=d), full.decode(s.clone(), scale=d))
+
+
+def test_batched_calls_equal_single_frame_calls():
+    """cvc_deflate_frames / cvc_inflate_frames over 8 frames (a K-frame period with
+    dropped levels mixed in) give exactly the single-frame results."""
+    kw = dict(QCIF, key_interval=3, motion_range=8)
+    g = _codec(kw)
+    one = Deflater(**kw)
+    many = Deflater(max_frames=8, **kw)
+    frames = S.SyntheticVideo(S.spec_for(176, 144, seed=75)).frames(8)
+    streams = [g.encode(torch.from_numpy(f).cuda())[0].clone() for f in frames]
+    streams[3] = torch.from_numpy(g.drop_levels(streams[3].cpu(), 2)).cuda()
+    outs = [torch.zeros(s.numel() + 65536, dtype=torch.uint8, device="cuda") for s in streams]
+    packed, sts = many.deflate_many(streams, outs)
+    assert sts == [0] * 8
+    for s, p in zip(streams, packed):
+        assert torch.equal(p, one.deflate(s))
+    backs = [torch.zeros(s.numel() + 16, dtype=torch.uint8, device="cuda") for s in streams]
+    back, sts = many.inflate_many([p.clone() for p in packed], backs)
+    assert sts == [0] * 8
+    for s, b in zip(streams, back):
+        assert torch.equal(b, s)
+    # a short buffer fails its own frame only
+    outs[5] = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    packed, sts = many.deflate_many(streams, outs)
+    assert sts[5] == 3 and all(v == 0 for i, v in enumerate(sts) if i != 5)
+    assert torch.equal(packed[4], one.deflate(streams[4]))
