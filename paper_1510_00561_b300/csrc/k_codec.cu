@@ -37,13 +37,44 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
         float* out = Y + (long long)row * g.Wp;
         // streams with motion also keep the padded luma as bytes (Y is in [0, 255]) for the search
         uint8_t* lum = D.mv_range ? (C.ecur ? luma0 : luma1) + D.luma_off + (long long)row * g.Wp : nullptr;
-        for (int x = threadIdx.x; x < g.Wp; x += blockDim.x) {
-            const uint8_t* p = src + 3 * mirror_idx(x, g.W);
-            const int R = p[0], G = p[1], Bv = p[2];
-            const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-            const int yv = t + (cg >> 1);
-            out[x] = (float)yv;
-            if (lum) lum[x] = (uint8_t)yv;
+        // four pixels per thread: three word loads, one float4 store, where the row is aligned
+        const bool vec = (((uintptr_t)src | (uintptr_t)out | (uintptr_t)(lum ? lum : src)) & 3) == 0 &&
+                         ((uintptr_t)out & 15) == 0;
+        for (int x0 = 4 * threadIdx.x; x0 < g.Wp; x0 += 4 * blockDim.x) {
+            int yv[4];
+            if (vec && x0 + 4 <= g.W) {
+                const uint32_t* w = reinterpret_cast<const uint32_t*>(src + 3 * x0);
+                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+                const int px[12] = {(int)(w0 & 255), (int)((w0 >> 8) & 255), (int)((w0 >> 16) & 255), (int)(w0 >> 24),
+                                    (int)(w1 & 255), (int)((w1 >> 8) & 255), (int)((w1 >> 16) & 255), (int)(w1 >> 24),
+                                    (int)(w2 & 255), (int)((w2 >> 8) & 255), (int)((w2 >> 16) & 255), (int)(w2 >> 24)};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int R = px[3 * k], G = px[3 * k + 1], Bv = px[3 * k + 2];
+                    const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
+                    yv[k] = t + (cg >> 1);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int x = min(x0 + k, g.Wp - 1);
+                    const uint8_t* p = src + 3 * mirror_idx(x, g.W);
+                    const int R = p[0], G = p[1], Bv = p[2];
+                    const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
+                    yv[k] = t + (cg >> 1);
+                }
+            }
+            if (vec && x0 + 4 <= g.Wp) {
+                *reinterpret_cast<float4*>(out + x0) = make_float4((float)yv[0], (float)yv[1], (float)yv[2], (float)yv[3]);
+                if (lum)
+                    *reinterpret_cast<uint32_t*>(lum + x0) =
+                        (uint32_t)yv[0] | ((uint32_t)yv[1] << 8) | ((uint32_t)yv[2] << 16) | ((uint32_t)yv[3] << 24);
+            } else {
+                for (int k = 0; k < 4 && x0 + k < g.Wp; k++) {
+                    out[x0 + k] = (float)yv[k];
+                    if (lum) lum[x0 + k] = (uint8_t)yv[k];
+                }
+            }
         }
     } else {
         const int cy = row - g.Hp;
@@ -99,26 +130,48 @@ __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall*
     const float* P[2][2] = {{Co + (long long)i0 * D.rs_c, Co + (long long)i1 * D.rs_c},
                             {Cg + (long long)i0 * D.rs_c, Cg + (long long)i1 * D.rs_c}};
     uint8_t* orow = C.rgb_out + (long long)y * C.pitch_out;
-    for (int x = threadIdx.x; x < D.W; x += blockDim.x) {
-        const int yy = round_clamp(Yrow[x] * norm, 0, 255);
-        const int j0 = min(x >> 1, Wc - 1), j1 = (x & 1) ? min((x >> 1) + 1, Wc - 1) : max((x >> 1) - 1, 0);
-        int c[2];
+    const bool vec = ((uintptr_t)orow & 3) == 0;
+    // four pixels per thread: their chroma columns x/2 - 1 .. x/2 + 2 (clamped) are rounded once
+    for (int x0 = 4 * threadIdx.x; x0 < D.W; x0 += 4 * blockDim.x) {
+        const int jb = x0 >> 1;
+        int cv[2][2][4];
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
-            const int a = round_clamp(P[q][0][j0] * norm, -255, 255);
-            const int b = round_clamp(P[q][1][j0] * norm, -255, 255);
-            const int d = round_clamp(P[q][0][j1] * norm, -255, 255);
-            const int e = round_clamp(P[q][1][j1] * norm, -255, 255);
-            c[q] = (9 * a + 3 * b + 3 * d + e + 8) >> 4;
+        for (int k = 0; k < 4; k++) {
+            const int j = min(max(jb - 1 + k, 0), Wc - 1);
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+#pragma unroll
+                for (int r = 0; r < 2; r++) cv[q][r][k] = round_clamp(P[q][r][j] * norm, -255, 255);
         }
-        const int t = yy - (c[1] >> 1);
-        const int G = c[1] + t;
-        const int Bv = t - (c[0] >> 1);
-        const int R = Bv + c[0];
-        uint8_t* o = orow + 3 * x;
-        o[0] = (uint8_t)min(max(R, 0), 255);
-        o[1] = (uint8_t)min(max(G, 0), 255);
-        o[2] = (uint8_t)min(max(Bv, 0), 255);
+        uint32_t px[3] = {0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int x = x0 + k;
+            if (x >= D.W) break;
+            const int yy = round_clamp(Yrow[x] * norm, 0, 255);
+            // columns min(x/2, Wc-1) and, for odd x, min(x/2 + 1, Wc-1), for even x, x/2 - 1 (>= 0)
+            const int i0 = (k >> 1) + 1, i1 = (k & 1) ? (k >> 1) + 2 : (k >> 1);
+            int c[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                c[q] = (9 * cv[q][0][i0] + 3 * cv[q][1][i0] + 3 * cv[q][0][i1] + cv[q][1][i1] + 8) >> 4;
+            const int t = yy - (c[1] >> 1);
+            const int G = c[1] + t;
+            const int Bv = t - (c[0] >> 1);
+            const int R = Bv + c[0];
+            const uint32_t rgb3[3] = {(uint32_t)min(max(R, 0), 255), (uint32_t)min(max(G, 0), 255),
+                                      (uint32_t)min(max(Bv, 0), 255)};
+#pragma unroll
+            for (int b = 0; b < 3; b++) px[(3 * k + b) >> 2] |= rgb3[b] << (8 * ((3 * k + b) & 3));
+        }
+        if (vec && x0 + 4 <= D.W) {
+            uint32_t* o = reinterpret_cast<uint32_t*>(orow + 3 * x0);
+            o[0] = px[0];
+            o[1] = px[1];
+            o[2] = px[2];
+        } else {
+            for (int b = 0; b < 12 && x0 + b / 3 < D.W; b++) orow[3 * x0 + b] = (uint8_t)(px[b >> 2] >> (8 * (b & 3)));
+        }
     }
 }
 
