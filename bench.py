@@ -285,43 +285,49 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
 
 
 def deflate_run(kstreams, dev, reps=3):
-    """§3.9 DEFLATE of one K-frame period of the batch's encoded 1080p frames: the B frames
-    of each step deflated, then inflated, in one call each (cvc_deflate_frames,
-    cvc_inflate_frames; CUDA events around the calls, which synchronise), their sizes, and
-    zlib's Huffman-only and default sizes of the same token bytes for reference."""
+    """§3.9 DEFLATE of one K-frame period of the batch's encoded 1080p frames, in both modes
+    (scalable: a stream per component; CVC-NTS: a stream per frame): the B frames of each
+    step deflated, then inflated, in one call each (cvc_deflate_frames, cvc_inflate_frames;
+    CUDA events around the calls, which synchronise), their sizes, and zlib's Huffman-only
+    and default sizes of the same token bytes for reference."""
     import zlib
     import numpy as np
     import torch
     from paper_1510_00561_b300 import Deflater
     B = len(kstreams[0])
-    dfl = Deflater(max_frames=B, width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
-                   key_interval=KINT)
     pouts = [[torch.empty(f.numel() + (1 << 16), dtype=torch.uint8, device=dev) for f in ks] for ks in kstreams]
     outs = [[torch.empty(f.numel() + 16, dtype=torch.uint8, device=dev) for f in ks] for ks in kstreams]
-    packed = []
-    for ks, po in zip(kstreams, pouts):                      # warm-up, and the outputs
-        p, sts = dfl.deflate_many(ks, po)
-        assert all(v == 0 for v in sts)
-        packed.append([x.clone() for x in p])
-    for pk, o, ks in zip(packed, outs, kstreams):
-        back, sts = dfl.inflate_many(pk, o)
-        assert all(v == 0 for v in sts) and all(torch.equal(b, k) for b, k in zip(back, ks))
     st = torch.cuda.current_stream()
-    times = {}
-    for name, fn in (("deflate", lambda t: dfl.deflate_many(kstreams[t], pouts[t])),
-                     ("inflate", lambda t: dfl.inflate_many(packed[t], outs[t]))):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        for _ in range(reps):
-            for t in range(len(kstreams)):
-                fn(t)
-        e1.record(st)
-        torch.cuda.synchronize()
-        times[name] = e0.elapsed_time(e1) / (reps * len(kstreams))
+
+    def mode(nts):
+        dfl = Deflater(max_frames=B, nts=nts, width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH,
+                       qpl=QPL, key_interval=KINT)
+        packed = []
+        for ks, po in zip(kstreams, pouts):                  # warm-up, and the outputs
+            p, sts = dfl.deflate_many(ks, po)
+            assert all(v == 0 for v in sts)
+            packed.append([x.clone() for x in p])
+        for pk, o, ks in zip(packed, outs, kstreams):
+            back, sts = dfl.inflate_many(pk, o)
+            assert all(v == 0 for v in sts) and all(torch.equal(b, k) for b, k in zip(back, ks))
+        times = {}
+        for name, fn in (("deflate", lambda t: dfl.deflate_many(kstreams[t], pouts[t])),
+                         ("inflate", lambda t: dfl.inflate_many(packed[t], outs[t]))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                for t in range(len(kstreams)):
+                    fn(t)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / (reps * len(kstreams))
+        return times, sum(x.numel() for pk in packed for x in pk)
+
+    times, out = mode(False)
+    times_nts, out_nts = mode(True)
     frames = [f for ks in kstreams for f in ks]
     raw = sum(f.numel() for f in frames)
-    out = sum(x.numel() for pk in packed for x in pk)
     tok = zh = zd = 0
     for f in frames[:KINT]:                                  # zlib on stream 0's period (host time)
         b = bytes(f.cpu().numpy())
@@ -339,19 +345,24 @@ def deflate_run(kstreams, dev, reps=3):
                     zh += k
                 else:
                     zd += k
-    return {"workload": "DEFLATE (scalable mode, per-component Huffman-only streams) of %d encoded 1080p frames "
-                        "(%d streams x one K-frame period), %d frames per call" % (len(frames), B, B),
+    return {"workload": "DEFLATE (scalable mode: per-component Huffman-only streams; nts: one per frame) of "
+                        "%d encoded 1080p frames (%d streams x one K-frame period), %d frames per call"
+                        % (len(frames), B, B),
             "deflate_ms_per_call": times["deflate"], "inflate_ms_per_call": times["inflate"],
             "deflate_frames_per_s": B * 1e3 / times["deflate"], "inflate_frames_per_s": B * 1e3 / times["inflate"],
             "mean_frame_bytes": raw / len(frames), "mean_deflated_bytes": out / len(frames),
             "ratio": out / raw, "token_bytes_ratio_zlib_huffman_only": zh / tok,
-            "token_bytes_ratio_zlib_default": zd / tok}
+            "token_bytes_ratio_zlib_default": zd / tok,
+            "nts": {"deflate_ms_per_call": times_nts["deflate"], "inflate_ms_per_call": times_nts["inflate"],
+                    "deflate_frames_per_s": B * 1e3 / times_nts["deflate"],
+                    "inflate_frames_per_s": B * 1e3 / times_nts["inflate"],
+                    "mean_deflated_bytes": out_nts / len(frames), "ratio": out_nts / raw}}
 
 
 def rd_run(dev, n_frames=30):
     """Rate-distortion analogues of the paper's QCIF experiments (§4.1, Figs 3, 4, 6-8) on the
     synthetic QCIF sequence: mean Y-PSNR of the decoded frames, and mean deflated bits per frame
-    (scalable DEFLATE stage).  rd: the whole QPH range with QPL = max(1, QPH // 14), motion
+    (DEFLATE stage, scalable and CVC-NTS).  rd: the whole QPH range with QPL = max(1, QPH // 14), motion
     search +-8, K every 10; qph: QPH with QPL = 1 (Fig. 3); qpl: QPL with QPH = 1 (Fig. 4)."""
     import numpy as np
     import torch
@@ -369,15 +380,16 @@ def rd_run(dev, n_frames=30):
 
     def point(qph, qpl, motion):
         kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=qph, qpl=qpl, key_interval=10, motion_range=motion)
-        enc, dec, dfl = Codec(**kw), Codec(**kw), Deflater(**kw)
-        mse, bits = 0.0, 0
+        enc, dec, dfl, nts = Codec(**kw), Codec(**kw), Deflater(**kw), Deflater(nts=True, **kw)
+        mse, bits, bits_nts = 0.0, 0, 0
         for f, ys in zip(d_src, y_src):
             s, _ = enc.encode(f)
             bits += 8 * dfl.deflate(s).numel()
+            bits_nts += 8 * nts.deflate(s).numel()
             mse += float(((luma(dec.decode(s.clone())) - ys) ** 2).mean())
         mse /= len(d_src)
         return {"qph": qph, "qpl": qpl, "y_psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-12)),
-                "kbit_per_frame": bits / len(d_src) / 1e3}
+                "kbit_per_frame": bits / len(d_src) / 1e3, "kbit_per_frame_nts": bits_nts / len(d_src) / 1e3}
 
     qphs = [1, 2, 4, 8, 16, 32, 64, 128, 181]
     return {"workload": "synthetic QCIF, %d frames, 3 levels 8/4/4 directions, 4:2:0" % n_frames,

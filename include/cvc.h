@@ -245,8 +245,9 @@ cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t
  * (version byte 2, cvc_deflate_frame) loses the DEFLATE streams and segment
  * entries of those components the same way (its stream lengths become 0),
  * and is byte-identical to deflating the frame with the levels dropped.  A
- * frame that
- * already left out d0 levels can only lose more (drop >= d0).  `out` may be
+ * CVC-NTS frame (version byte 3, one stream) has nothing to drop:
+ * UNSUPPORTED.  A frame that already left out d0 levels can only lose more
+ * (drop >= d0).  `out` may be
  * `in` (the tokens only move forward).  Host work only, no device call.
  * A decoder accepts such a frame at scales >= drop (cvc_decode_frame_scaled;
  * STATE below that).  Afterwards the decoder state of levels 1..drop is
@@ -281,6 +282,12 @@ cvc_status cvc_codec_inspect(const cvc_codec* codec, int which, float* d_out, si
  * (each byte-aligned, its header, literals and end-of-block code), then the
  * motion vectors of a type-2 frame.  Any inflater decodes each stream alone;
  * the segment lengths are the entry points of the parallel inflate.
+ * CVC-NTS ("non transmission scalable", §3.9; cvc_deflate_set_nts): the
+ * token bytes of the whole frame, in component order, become ONE stream.
+ * Its container has version byte 3 and one u32 stream length in place of
+ * the ncomp of them, and its 256-byte segments run over the whole token
+ * bytes; the rest is as above.  Levels can no longer be dropped in transit,
+ * but the inflated frame still decodes at any scale.
  * A context holds device scratch for up to max_frames frames of one
  * parameter set (cvc_deflate_create: 1); a call covers any number of frames
  * up to it in one launch sequence.                                         */
@@ -288,6 +295,10 @@ typedef struct cvc_deflate_ctx cvc_deflate_ctx;
 cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out);
 cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cvc_deflate_ctx** out);
 cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx);
+/* on != 0: later deflate calls write CVC-NTS containers (version 3), 0:
+ * scalable ones (version 2, the default).  Inflate reads either.
+ * Errors: INVALID_ARG (ctx NULL).                                           */
+cvc_status cvc_deflate_set_nts(cvc_deflate_ctx* ctx, int on);
 /* d_in: one frame of cvc_encode_frame (version byte 1, possibly without some
  * levels, cvc_stream_drop_levels) in device memory; d_out (device, 4-byte
  * aligned, out_cap bytes) receives the deflated frame; *out_len (host) its
@@ -296,8 +307,8 @@ cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx);
 cvc_status cvc_deflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t in_len, uint8_t* d_out,
                              size_t out_cap, size_t* out_len, cvc_stream_t stream);
 /* the inverse: a deflated frame of this context's parameters back to the
- * frame cvc_decode_frame reads (device memory both).  CORRUPT for anything
- * but the container above (a stream must decode to exactly its token bytes,
+ * frame cvc_decode_frame reads (device memory both), from either container
+ * form.  CORRUPT for anything but the containers above (a stream must decode to exactly its token bytes,
  * each segment to its recorded bit length, and end with the end-of-block
  * code).  Synchronises `stream`.                                            */
 cvc_status cvc_inflate_frame(cvc_deflate_ctx* ctx, const uint8_t* d_in, size_t in_len, uint8_t* d_out,

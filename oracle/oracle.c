@@ -1175,24 +1175,28 @@ static unsigned long rd32u(const uint8_t* p) { return get32(p); }
  * checked for its size */
 int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len) {
     long hdr = 32 + 4L * c->ncomp;
-    if (len < hdr + 4L * c->ncomp || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 2 ||
+    if (len < hdr || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || (in[4] != 2 && in[4] != 3) ||
         in[5] != 0 || get32(in + 28) != (unsigned long)c->ncomp)
         return OR_ECORRUPT;
+    /* version 2: a stream per component; 3 (CVC-NTS): one stream of all token bytes */
+    int nstr = in[4] == 3 ? 1 : c->ncomp;
+    if (len < hdr + 4L * nstr) return OR_ECORRUPT;
     long ntok = 0, nseg = 0;
     for (int j = 0; j < c->ncomp; j++) {
         long n = (long)rd32u(in + 32 + 4 * j);
         ntok += n;
         nseg += (2 * n + 255) / 256;
     }
+    if (nstr == 1) nseg = (2 * ntok + 255) / 256;
     long mvb = in[6] == 2 ? 2L * ((c->Hp + 15) / 16) * ((c->Wp + 15) / 16) : 0;
     *out_len = hdr + 2 * ntok + mvb;
     if (*out_len > cap) return OR_ECAPACITY;
-    long pos = hdr + 4L * c->ncomp + ((2 * nseg + 3) & ~3L);
+    long pos = hdr + 4L * nstr + ((2 * nseg + 3) & ~3L);
     memcpy(out, in, (size_t)hdr);
     out[4] = 1;
     long o = hdr;
-    for (int j = 0; j < c->ncomp; j++) {
-        long n = (long)rd32u(in + 32 + 4 * j), nb = (long)rd32u(in + hdr + 4 * j);
+    for (int j = 0; j < nstr; j++) {
+        long n = nstr == 1 ? ntok : (long)rd32u(in + 32 + 4 * j), nb = (long)rd32u(in + hdr + 4 * j);
         if ((n == 0) != (nb == 0) || pos + nb > len) return OR_ECORRUPT;
         if (n) {
             z_stream z;

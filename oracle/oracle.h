@@ -167,8 +167,10 @@ int or_stream_drop(const or_codec* c, const uint8_t* in, long len, int drop, uin
  * symbols (Huffman's pairing); *depth = its longest code */
 unsigned long long or_huffman_cost(const unsigned long* freq, int n, int* depth);
 /* the frame inside a deflated frame (per-component raw DEFLATE streams after
- * the header, token counts, stream lengths and segment table), inflated with
- * zlib; OR_ECORRUPT unless every stream inflates to exactly its tokens */
+ * the header, token counts, stream lengths and segment table, version byte
+ * 2; or, CVC-NTS of §3.9, version byte 3, one stream of all the token bytes),
+ * inflated with zlib; OR_ECORRUPT unless every stream inflates to exactly its
+ * tokens */
 int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len);
 
 #endif

@@ -128,6 +128,7 @@ def lib():
         L.cvc_inflate_frames.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_SZ), ctypes.POINTER(_P),
                                          ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_deflate_destroy.argtypes = [_P]
+        L.cvc_deflate_set_nts.argtypes = [_P, _I]
         L.cvc_deflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]
         L.cvc_inflate_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), _P]
         L.cvc_stream_drop_levels.argtypes = [ctypes.POINTER(Params), _P, _SZ, _I, _P, _SZ, ctypes.POINTER(_SZ)]

@@ -232,16 +232,19 @@ def drop_levels(params, stream_bytes, drop):
 
 
 class Deflater:
-    """The DEFLATE stage (§3.9, scalable mode) for frames of one parameter set:
-    per-component Huffman-only DEFLATE streams on the GPU (cvc_deflate_*)."""
+    """The DEFLATE stage (§3.9) for frames of one parameter set: Huffman-only
+    DEFLATE streams on the GPU (cvc_deflate_*), one per component (scalable
+    mode) or, with nts=True, one per frame (CVC-NTS).  Inflate reads both."""
 
-    def __init__(self, max_frames=1, **stream):
+    def __init__(self, max_frames=1, nts=False, **stream):
         prm = _L.params(**stream)
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_deflate_create_batch(ctypes.byref(prm), int(max_frames), ctypes.byref(p)),
                  "cvc_deflate_create_batch")
         self._h = p
         self.max_frames = max_frames
+        self.nts = bool(nts)
+        _L.check(_L.lib().cvc_deflate_set_nts(p, int(self.nts)), "cvc_deflate_set_nts")
 
     def __del__(self):
         h = getattr(self, "_h", None)

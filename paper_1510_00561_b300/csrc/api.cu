@@ -331,9 +331,10 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         return (uint32_t)in[at] | ((uint32_t)in[at + 1] << 8) | ((uint32_t)in[at + 2] << 16) |
                ((uint32_t)in[at + 3] << 24);
     };
-    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || (in[4] != 1 && in[4] != 2) || in[5] != 0 ||
+    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[4] < 1 || in[4] > 3 || in[5] != 0 ||
         in[7] != params->levels || rd32(28) != ncomp)
         return CVC_ERR_CORRUPT;
+    if (in[4] == 3) return CVC_ERR_UNSUPPORTED;   // CVC-NTS: one stream, no level can leave it
     const bool deflated = in[4] == 2;   // per-component DEFLATE streams (cvc_deflate_frame)
     const int d0 = in[26] | (in[27] << 8);
     if (drop < d0 || drop > params->levels) return CVC_ERR_INVALID_ARG;
@@ -453,7 +454,8 @@ cvc_status cvc_codec_inspect(const cvc_codec* c, int which, float* d_out, size_t
 
 // --------------------------------------------------------------- DEFLATE
 struct cvc_deflate_ctx {
-    int ncomp = 0, max_seg = 0, max_frames = 0;
+    int ncomp = 0, max_seg = 0, max_grp = 0, max_frames = 0;
+    int nts = 0;                        // deflate into one stream per frame (CVC-NTS)
     long long hdr_bytes = 0, mv_bytes = 0;
     void* arena = nullptr;
     DflScratch* d_S = nullptr;          // max_frames scratch records
@@ -488,6 +490,7 @@ cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cv
         return CVC_ERR_UNSUPPORTED;
     }
     x->max_seg = (int)segs;
+    x->max_grp = (int)((segs + DFL_GRP - 1) / DFL_GRP) + D.ncomp;
     const size_t n = (size_t)x->ncomp, m = (size_t)x->max_seg, F = (size_t)max_frames;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -499,7 +502,7 @@ cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cv
     const size_t o_S = take(F * sizeof(DflScratch)), o_fr = take(F * sizeof(DflFrame)),
                  o_sb = take((F * (m + 1)) * 4), o_so = take((F * (m + 1) + 1) * 4),
                  o_tmp = take(((F * (m + 1) + 2047) / 2048 + 8) * 4);
-    std::vector<size_t> o_comp(F), o_hist(F), o_len(F), o_code(F), o_hdr(F), o_dc(F), o_ds(F), o_dt(F), o_sc(F);
+    std::vector<size_t> o_comp(F), o_hist(F), o_len(F), o_code(F), o_hdr(F), o_dc(F), o_ds(F), o_dt(F);
     for (size_t f = 0; f < F; f++) {
         o_comp[f] = take((n + 1) * sizeof(DflComp));
         o_hist[f] = take(n * DFL_NLIT * 4);
@@ -509,7 +512,6 @@ cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cv
         o_dc[f] = take(n * 16 * 2);
         o_ds[f] = take(n * DFL_NSYM * 2);
         o_dt[f] = take(n * (1 << DFL_LUT) * 2);
-        o_sc[f] = take(m * 4);
     }
     if (cudaMalloc(&x->arena, off) != cudaSuccess ||
         cudaMallocHost((void**)&x->h_S, F * sizeof(DflScratch)) != cudaSuccess ||
@@ -538,7 +540,6 @@ cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cv
         S.dtab = reinterpret_cast<uint16_t*>(b + o_dt[f]);
         S.segbits = x->segbits + f * (m + 1);
         S.segoff = x->segoff + f * (m + 1);
-        S.segcomp = reinterpret_cast<int*>(b + o_sc[f]);
     }
     if (cudaMemcpy(x->d_S, x->ptrs.data(), F * sizeof(DflScratch), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
@@ -551,6 +552,12 @@ cvc_status cvc_deflate_create_batch(const cvc_params* params, int max_frames, cv
 
 cvc_status cvc_deflate_create(const cvc_params* params, cvc_deflate_ctx** out) {
     return cvc_deflate_create_batch(params, 1, out);
+}
+
+cvc_status cvc_deflate_set_nts(cvc_deflate_ctx* ctx, int on) {
+    if (!ctx) return CVC_ERR_INVALID_ARG;
+    ctx->nts = on != 0;
+    return CVC_OK;
 }
 
 cvc_status cvc_deflate_destroy(cvc_deflate_ctx* ctx) {
@@ -599,20 +606,20 @@ cvc_status cvc_deflate_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* 
                               cvc_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!out_len || !dfl_frames(x, nf, d_in, in_len, d_out, out_cap, true, st)) return CVC_ERR_INVALID_ARG;
-    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg};
-    const dim3 one(1, nf), comps(x->ncomp, nf);
+    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg, x->max_grp, x->nts};
+    const dim3 one(1, nf), strs(x->nts ? 1 : x->ncomp, nf), grps(x->max_grp, nf);
     k_dfl_plan<<<one, 256, 0, st>>>(a);
-    k_dfl_hist<<<comps, 256, 0, st>>>(a);
-    k_dfl_code<<<comps, 256, 0, st>>>(a);
+    k_dfl_hist<<<grps, 256, 0, st>>>(a);
+    k_dfl_code<<<strs, 256, 0, st>>>(a);
     k_dfl_layout<<<one, 256, 0, st>>>(a);
-    k_dfl_seglen<<<comps, 256, 0, st>>>(a);
+    k_dfl_seglen<<<grps, 256, 0, st>>>(a);
     // one scan over every frame's slice; each frame only takes differences inside it
     if (exclusive_scan(x->segbits, (uint32_t)(nf * (x->max_seg + 1)), x->segoff, x->scan_tmp, st) != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
     k_dfl_zero<<<dim3(64, nf), 256, 0, st>>>(a);
-    k_dfl_write<<<comps, 256, 0, st>>>(a);
+    k_dfl_write<<<grps, 256, 0, st>>>(a);
     k_dfl_tables<<<dim3(16, nf), 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
     return dfl_finish(x, nf, st, out_len, status, 11);
@@ -623,8 +630,8 @@ cvc_status cvc_inflate_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* 
                               cvc_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (!out_len || !dfl_frames(x, nf, d_in, in_len, d_out, out_cap, false, st)) return CVC_ERR_INVALID_ARG;
-    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg};
-    const dim3 one(1, nf), comps(x->ncomp, nf);
+    const DflArgs a{x->d_fr, x->hdr_bytes, x->mv_bytes, x->ncomp, x->max_seg, x->max_grp, 0};
+    const dim3 one(1, nf), comps(x->ncomp, nf), grps(x->max_grp, nf);
     k_ifl_plan<<<one, 256, 0, st>>>(a);
     k_ifl_seglen<<<dim3((x->max_seg + 255) / 256, nf), 256, 0, st>>>(a);
     if (exclusive_scan(x->segbits, (uint32_t)(nf * (x->max_seg + 1)), x->segoff, x->scan_tmp, st) != cudaSuccess) {
@@ -632,7 +639,7 @@ cvc_status cvc_inflate_frames(cvc_deflate_ctx* x, int nf, const uint8_t* const* 
         return CVC_ERR_CUDA;
     }
     k_ifl_tables<<<comps, 128, 0, st>>>(a);
-    k_ifl_decode<<<comps, 256, 0, st>>>(a);
+    k_ifl_decode<<<grps, 256, 0, st>>>(a);
     k_ifl_finish<<<dim3(16, nf), 256, 0, st>>>(a);
     if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
     return dfl_finish(x, nf, st, out_len, status, 8);

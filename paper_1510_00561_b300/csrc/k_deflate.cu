@@ -1,17 +1,20 @@
-// k_deflate.cu -- the DEFLATE stage of CVC (§3.9), scalable mode: every
+// k_deflate.cu -- the DEFLATE stage of CVC (§3.9).  Scalable mode: every
 // component's token bytes become one raw DEFLATE stream (RFC 1951) of its
-// own, so that a receiver can be sent any subset of components.
+// own, so that a receiver can be sent any subset of components.  CVC-NTS
+// mode: the token bytes of the whole frame become one stream.
 //
 // Each stream is one final block with dynamic Huffman codes over literal
 // bytes only (the Huffman-only strategy: no LZ77 matches), which makes both
 // directions data-parallel:
-//   deflate  a byte histogram per component, one length-limited Huffman code
-//            per component (one thread each), the block header, and the
-//            data written by one thread per 256-byte segment at a bit offset
-//            from a scan of the segments' bit lengths;
-//   inflate  one thread per component decodes its block header into
-//            canonical decoding tables, one thread per segment decodes its
-//            256 literals starting at the bit offset the container records.
+//   deflate  a byte histogram per stream, one length-limited Huffman code
+//            per stream (a block each), the block header, and the data
+//            written by one thread per 256-byte segment at a bit offset from
+//            a scan of the segments' bit lengths;
+//   inflate  a block per stream decodes its block header into decoding
+//            tables, one thread per segment decodes its 256 literals
+//            starting at the bit offset the container records.
+// Segments are handled in groups of 256 (a block each), so that one large
+// stream spreads over many blocks.
 // The container keeps the CVC header and token counts, adds each stream's
 // byte length and the bit length of each of its segments (the entry points
 // of the parallel inflate), then the streams, then the motion vectors.  Any
@@ -36,73 +39,6 @@ __device__ __forceinline__ uint32_t bit_reverse(uint32_t code, int len) { return
 
 // the order in which the code-length code's lengths are sent (RFC 1951, 3.2.7)
 __constant__ uint8_t CL_ORDER[19] = {16, 17, 18, 0, 8, 7, 9, 6, 10, 5, 11, 4, 12, 3, 13, 2, 14, 1, 15};
-
-// Huffman code lengths of n symbols (weights w, 0 = unused) limited to
-// maxlen bits.  A binary heap of (weight, node) builds the tree; if it is too
-// deep, the weights are halved (non-zero ones stay >= 1) and it is built
-// again.  A lone used symbol gets one bit.
-__device__ void huffman_lengths(const uint32_t* w_in, int n, int maxlen, uint8_t* len, uint32_t* w, uint16_t* parent,
-                                uint16_t* heap) {
-    int used = 0;
-    for (int i = 0; i < n; i++) {
-        w[i] = w_in[i];
-        len[i] = 0;
-        used += w_in[i] != 0;
-    }
-    if (used < 2) {                    // a lone symbol gets one bit (the caller completes the code)
-        for (int i = 0; i < n; i++) len[i] = w_in[i] ? 1 : 0;
-        return;
-    }
-    for (;;) {
-        int hn = 0, m = n;
-        auto less = [&](int a, int b) { return w[a] < w[b] || (w[a] == w[b] && a < b); };
-        auto push = [&](int x) {
-            int i = hn++;
-            heap[i] = (uint16_t)x;
-            while (i > 0) {
-                int p = (i - 1) >> 1;
-                if (!less(heap[i], heap[p])) break;
-                uint16_t t = heap[i]; heap[i] = heap[p]; heap[p] = t;
-                i = p;
-            }
-        };
-        auto pop = [&]() {
-            int top = heap[0];
-            heap[0] = heap[--hn];
-            int i = 0;
-            for (;;) {
-                int l = 2 * i + 1, r = l + 1, s = i;
-                if (l < hn && less(heap[l], heap[s])) s = l;
-                if (r < hn && less(heap[r], heap[s])) s = r;
-                if (s == i) break;
-                uint16_t t = heap[i]; heap[i] = heap[s]; heap[s] = t;
-                i = s;
-            }
-            return top;
-        };
-        for (int i = 0; i < n; i++)
-            if (w[i]) push(i);
-        while (hn > 1) {
-            int a = pop(), b = pop();
-            w[m] = w[a] + w[b];
-            parent[a] = parent[b] = (uint16_t)m;
-            push(m);
-            m++;
-        }
-        const int root = m - 1;
-        int deepest = 0;
-        for (int i = 0; i < n; i++) {
-            int d = 0;
-            if (w_in[i]) {
-                for (int x = i; x != root; x = parent[x]) d++;
-            }
-            len[i] = (uint8_t)d;
-            deepest = max(deepest, d);
-        }
-        if (deepest <= maxlen) return;
-        for (int i = 0; i < n; i++) w[i] = w[i] ? (w[i] + 1) >> 1 : 0;
-    }
-}
 
 // canonical codes (RFC 1951, 3.2.2), bit-reversed for LSB-first emission
 __device__ void canonical_codes(const uint8_t* len, int n, uint16_t* code) {
@@ -143,40 +79,10 @@ struct BitOut {
     }
 };
 
-// sequential bit reader over [0, nbits)
-struct BitIn {
-    const uint8_t* p;
-    unsigned long long pos, end;
-    bool bad;
-    __device__ uint32_t get(int n) {
-        uint32_t v = 0;
-        for (int i = 0; i < n; i++) {
-            if (pos >= end) { bad = true; return 0; }
-            v |= (uint32_t)((p[pos >> 3] >> (pos & 7)) & 1u) << i;
-            pos++;
-        }
-        return v;
-    }
-};
-
-// canonical decoding: the code of a symbol is read MSB first, one bit at a time.
-// This and build_decoder stay out of line: inlined into k_ifl_tables with its
-// local tables, our sm_103a build decoded wrong code-length symbols, while the
-// same source run on the host and the out-of-line form decode correctly.
-__device__ __noinline__ int decode_sym(BitIn& in, const uint16_t* count, const uint16_t* sym) {
-    int code = 0, first = 0, index = 0;
-    for (int len = 1; len <= 15; len++) {
-        code |= (int)in.get(1);
-        const int c = count[len];
-        if (code - first < c) return sym[index + code - first];
-        index += c;
-        first = (first + c) << 1;
-        code <<= 1;
-    }
-    in.bad = true;
-    return -1;
-}
-
+// canonical decoding arrays of a code: codes per length, symbols in code order.
+// Kept out of line: inlined into k_ifl_tables with its local tables, our
+// sm_103a build decoded wrong symbols, while the same source run on the host
+// and the out-of-line form are correct.
 __device__ __noinline__ bool build_decoder(const uint8_t* len, int n, uint16_t* count, uint16_t* sym) {
     for (int b = 0; b < 16; b++) count[b] = 0;
     for (int i = 0; i < n; i++) count[len[i]]++;
@@ -266,10 +172,22 @@ __device__ void small_huffman(const uint32_t* f, int n, int maxlen, uint8_t* len
     }
 }
 
+// the stream of group g: the last stream whose first group is <= g
+__device__ __forceinline__ int group_stream(const DflComp* comp, int nstr, uint32_t g) {
+    int lo = 0, hi = nstr;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (comp[mid].grp0 <= g) lo = mid;
+        else hi = mid;
+    }
+    while (lo + 1 < nstr && comp[lo + 1].grp0 <= g) lo++;
+    return lo;
+}
+
 }  // namespace
 
 // -------------------------------------------------------------- deflate
-// component byte offsets of the input tokens and the segments (one block)
+// stream byte offsets of the input tokens, segments, groups (one block per frame)
 __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
@@ -285,58 +203,81 @@ __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
     }
     __syncthreads();
     if (s_bad) return;
-    unsigned long long tok = 0, seg = 0, tt, ts;
+    const int nstr = a.nts ? 1 : a.ncomp;
+    unsigned long long tok = 0, seg = 0, grp = 0, tt, ts, tg;
     for (int b = 0; b < a.ncomp; b += blockDim.x) {
         const int c = b + threadIdx.x;
         const uint32_t n = c < a.ncomp ? rd32(in + 32 + 4 * c) : 0;
-        const unsigned long long segs = (2ULL * n + DFL_SEG - 1) / DFL_SEG;
-        const unsigned long long pt = block_scan(n, sh, &tt), ps = block_scan(segs, sh, &ts);
-        if (c < a.ncomp) {
+        const unsigned long long segs = a.nts ? 0 : (2ULL * n + DFL_SEG - 1) / DFL_SEG;
+        const unsigned long long grps = (segs + DFL_GRP - 1) / DFL_GRP;
+        const unsigned long long pt = block_scan(n, sh, &tt), ps = block_scan(segs, sh, &ts),
+                                 pg = block_scan(grps, sh, &tg);
+        if (c < a.ncomp && !a.nts) {
             S.comp[c].in_off = a.hdr_bytes + 2 * (tok + pt);
             S.comp[c].bytes = 2ULL * n;
             S.comp[c].seg0 = (uint32_t)(seg + ps);
+            S.comp[c].grp0 = (uint32_t)(grp + pg);
         }
         tok += tt;
         seg += ts;
+        grp += tg;
     }
+    if (a.nts) {                           // one stream over the frame's token bytes
+        seg = (2 * tok + DFL_SEG - 1) / DFL_SEG;
+        grp = (seg + DFL_GRP - 1) / DFL_GRP;
+        if (threadIdx.x == 0) {
+            S.comp[0].in_off = a.hdr_bytes;
+            S.comp[0].bytes = 2 * tok;
+            S.comp[0].seg0 = 0;
+            S.comp[0].grp0 = 0;
+        }
+    }
+    for (int i = threadIdx.x; i < nstr * DFL_NLIT; i += blockDim.x)
+        S.hist[i] = (i % DFL_NLIT) == 256 ? 1u : 0u;      // the end-of-block code occurs once
     if (threadIdx.x == 0) {
-        S.comp[a.ncomp].seg0 = (uint32_t)seg;
+        S.comp[nstr].seg0 = (uint32_t)seg;
+        S.comp[nstr].grp0 = (uint32_t)grp;
         const int type = in[6];
         const long long mvb = type == 2 ? a.mv_bytes : 0;
         if ((type == 2 && a.mv_bytes == 0) || seg > (unsigned long long)a.max_seg ||
-            a.hdr_bytes + 2 * tok + mvb > (unsigned long long)F.in_len) {
+            grp > (unsigned long long)a.max_grp || a.hdr_bytes + 2 * tok + mvb > (unsigned long long)F.in_len) {
             S.err = DFL_CORRUPT;
             return;
         }
         S.nseg = (uint32_t)seg;
+        S.nstr = (uint32_t)nstr;
+        S.ngrp = (uint32_t)grp;
         S.tok_bytes = 2 * tok;
         S.tail = mvb;
     }
 }
 
-// byte histogram of each component: one block per component
+// byte histogram of each stream: one block per group of segments, a
+// sub-histogram per warp in shared memory, added to the stream's
 __global__ void __launch_bounds__(256) k_dfl_hist(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
-    if (S.err) return;
-    const int c = blockIdx.x;
+    const uint32_t g = blockIdx.x;
+    if (S.err || g >= S.ngrp) return;
+    const int c = group_stream(S.comp, (int)S.nstr, g);
+    const DflComp& C = S.comp[c];
     __shared__ uint32_t h[8][256];     // one per warp: the few common bytes collide less
     for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i >> 8][i & 255] = 0;
     __syncthreads();
-    const uint8_t* p = F.in + S.comp[c].in_off;
-    const unsigned long long n = S.comp[c].bytes;
+    const unsigned long long b0 = (unsigned long long)(g - C.grp0) * DFL_GRP * DFL_SEG;
+    const unsigned long long b1 = min(C.bytes, b0 + (unsigned long long)DFL_GRP * DFL_SEG);
+    const uint8_t* p = F.in + C.in_off;
     uint32_t* hw = h[(threadIdx.x >> 5) & 7];
-    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hw[p[i]], 1u);
+    for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) atomicAdd(&hw[p[i]], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         uint32_t t = 0;
         for (int k = 0; k < 8; k++) t += h[k][i];
-        S.hist[c * DFL_NLIT + i] = t;
+        if (t) atomicAdd(&S.hist[c * DFL_NLIT + i], t);
     }
-    if (threadIdx.x == 0) S.hist[c * DFL_NLIT + 256] = 1;   // end of block
 }
 
-// code of each component (one block each): literal/length code lengths (two
+// code of each stream (one block each): literal/length code lengths (two
 // queues over the leaves sorted by (weight, symbol), in shared memory; the
 // weights halved while a code would be longer than 15 bits), canonical codes,
 // the run-length coded block header and its bit length
@@ -344,7 +285,7 @@ __global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
     const int c = blockIdx.x, tid = threadIdx.x;
-    if (S.err) return;
+    if (S.err || c >= (int)S.nstr) return;
     DflComp& C = S.comp[c];
     if (C.bytes == 0) {
         if (tid == 0) C.hdr_bits = 0, C.data_bits = 0;
@@ -353,7 +294,7 @@ __global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
     __shared__ uint32_t w[2 * DFL_NLIT];
     __shared__ uint16_t parent[2 * DFL_NLIT], order[DFL_NLIT], q[DFL_NLIT], scode[DFL_NLIT];
     __shared__ uint8_t len[DFL_NLIT];
-    __shared__ int s_n, s_root, s_deep;
+    __shared__ int s_n, s_root, s_deep, s_fixed;
     __shared__ uint16_t nextc[16];
     __shared__ uint8_t hbuf[DFL_HDR_BYTES];
     __shared__ unsigned long long sh[8];
@@ -423,10 +364,11 @@ __global__ void __launch_bounds__(256) k_dfl_code(DflArgs a) {
                 int k = 0;
                 for (int b = 15; b >= 1; b--)
                     for (int m = cnt[b]; m > 0; m--) len[order[k++]] = (uint8_t)b;
-                s_deep = (kraft == (1LL << 15) && k == s_n) ? 15 : 99;
+                // a flag of its own: other warps may still be reading s_deep above
+                s_fixed = kraft == (1LL << 15) && k == s_n;
             }
             __syncthreads();
-            if (s_deep <= 15) break;
+            if (s_fixed) break;
         }
         for (int i = tid; i < DFL_NLIT; i += blockDim.x) w[i] = w[i] ? (w[i] + 1) >> 1 : 0;
         __syncthreads();
@@ -539,17 +481,18 @@ __global__ void __launch_bounds__(256) k_dfl_layout(DflArgs a) {
     DflScratch& S = *F.S;
     __shared__ unsigned long long sh[8];
     if (S.err) return;
-    const unsigned long long tables = a.hdr_bytes + 4ULL * a.ncomp + ((2ULL * S.nseg + 3) & ~3ULL);
+    const int nstr = (int)S.nstr;
+    const unsigned long long tables = a.hdr_bytes + 4ULL * nstr + ((2ULL * S.nseg + 3) & ~3ULL);
     unsigned long long off = tables, tt;
-    for (int b = 0; b < a.ncomp; b += blockDim.x) {
+    for (int b = 0; b < nstr; b += blockDim.x) {
         const int c = b + threadIdx.x;
         unsigned long long nb = 0;
-        if (c < a.ncomp) {
+        if (c < nstr) {
             const DflComp& C = S.comp[c];
             nb = C.bytes ? (C.hdr_bits + C.data_bits + 7) >> 3 : 0;
         }
         const unsigned long long p = block_scan(nb, sh, &tt);
-        if (c < a.ncomp) {
+        if (c < nstr) {
             S.comp[c].out_off = off + p;
             S.comp[c].out_bytes = nb;
         }
@@ -562,28 +505,26 @@ __global__ void __launch_bounds__(256) k_dfl_layout(DflArgs a) {
     }
 }
 
-// bit length of every segment: one block per component, its code lengths in
-// shared memory, one thread per segment at a time
+// bit length of every segment: one block per group, the stream's code lengths
+// in shared memory, a thread per segment
 __global__ void __launch_bounds__(256) k_dfl_seglen(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
-    const int c = blockIdx.x;
-    if (S.err) return;
+    const uint32_t g = blockIdx.x;
+    if (S.err || g >= S.ngrp) return;
+    const int c = group_stream(S.comp, (int)S.nstr, g);
     const DflComp& C = S.comp[c];
-    if (C.bytes == 0) return;
     __shared__ uint8_t len[DFL_NLIT];
     for (int i = threadIdx.x; i < DFL_NLIT; i += blockDim.x) len[i] = S.len[c * DFL_NLIT + i];
     __syncthreads();
+    const uint32_t k = (g - C.grp0) * DFL_GRP + threadIdx.x;         // segment inside the stream
+    if (C.seg0 + k >= S.comp[c + 1].seg0) return;
+    const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
+    const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
     const uint8_t* p = F.in + C.in_off;
-    const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
-    for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
-        const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
-        const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
-        uint32_t bits = 0;
-        for (unsigned long long i = b0; i < b1; i++) bits += len[p[i]];
-        S.segbits[C.seg0 + k] = bits;
-        S.segcomp[C.seg0 + k] = c;
-    }
+    uint32_t bits = 0;
+    for (unsigned long long i = b0; i < b1; i++) bits += len[p[i]];
+    S.segbits[C.seg0 + k] = bits;
 }
 
 // zero the words of the stream region (the streams are OR-ed in)
@@ -605,16 +546,16 @@ __device__ __forceinline__ void or_bits(uint32_t* w, unsigned long long ab, uint
     if ((int)(ab & 31) + n > 32) atomicOr(&w[(ab >> 5) + 1], (uint32_t)(x >> 32));
 }
 
-// the data of every segment: one block per component, its codes in shared
-// memory, one thread per segment at a time; thread 0 adds the header, the
-// thread of the last segment the end-of-block code
+// the data of every segment: one block per group, the stream's codes in
+// shared memory, a thread per segment; the first group's thread 0 adds the
+// header, the thread of the last segment the end-of-block code
 __global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
-    const int c = blockIdx.x;
-    if (S.err) return;
+    const uint32_t g = blockIdx.x;
+    if (S.err || g >= S.ngrp) return;
+    const int c = group_stream(S.comp, (int)S.nstr, g);
     const DflComp& C = S.comp[c];
-    if (C.bytes == 0) return;
     __shared__ uint8_t len[DFL_NLIT];
     __shared__ uint16_t code[DFL_NLIT];
     for (int i = threadIdx.x; i < DFL_NLIT; i += blockDim.x) {
@@ -624,35 +565,35 @@ __global__ void __launch_bounds__(256) k_dfl_write(DflArgs a) {
     __syncthreads();
     uint32_t* w = reinterpret_cast<uint32_t*>(F.out);
     const unsigned long long base = 8ULL * C.out_off;
-    if (threadIdx.x == 0) {
+    if (g == C.grp0 && threadIdx.x == 0) {
         const uint8_t* hb = S.hdr + (size_t)c * DFL_HDR_BYTES;
         for (uint32_t b = 0; b < C.hdr_bits; b += 8) or_bits(w, base + b, hb[b >> 3], (int)min(8u, C.hdr_bits - b));
     }
-    const uint8_t* p = F.in + C.in_off;
     const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
-    for (uint32_t k = threadIdx.x; k < nseg; k += blockDim.x) {
-        const uint32_t s = C.seg0 + k;
-        // segment bit offset inside the stream: the header, then the earlier segments
-        const unsigned long long ab = base + C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
-        const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
-        const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
-        // accumulate into whole words, OR-ed at the word grid
-        unsigned long long acc = 0;
-        int nacc = (int)(ab & 31);
-        unsigned long long wi = ab >> 5;
-        auto emit = [&](uint32_t v, int n) {
-            acc |= (unsigned long long)v << nacc;
-            nacc += n;
-            if (nacc >= 32) {
-                atomicOr(&w[wi++], (uint32_t)acc);
-                acc >>= 32;
-                nacc -= 32;
-            }
-        };
-        for (unsigned long long i = b0; i < b1; i++) emit(code[p[i]], len[p[i]]);
-        if (k + 1 == nseg) emit(code[256], len[256]);
-        if (nacc > 0) atomicOr(&w[wi], (uint32_t)acc);
-    }
+    const uint32_t k = (g - C.grp0) * DFL_GRP + threadIdx.x;
+    if (k >= nseg) return;
+    const uint32_t s = C.seg0 + k;
+    // segment bit offset inside the stream: the header, then the earlier segments
+    const unsigned long long ab = base + C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
+    const unsigned long long b0 = (unsigned long long)k * DFL_SEG;
+    const unsigned long long b1 = min(C.bytes, b0 + DFL_SEG);
+    const uint8_t* p = F.in + C.in_off;
+    // accumulate into whole words, OR-ed at the word grid
+    unsigned long long acc = 0;
+    int nacc = (int)(ab & 31);
+    unsigned long long wi = ab >> 5;
+    auto emit = [&](uint32_t v, int n) {
+        acc |= (unsigned long long)v << nacc;
+        nacc += n;
+        if (nacc >= 32) {
+            atomicOr(&w[wi++], (uint32_t)acc);
+            acc >>= 32;
+            nacc -= 32;
+        }
+    };
+    for (unsigned long long i = b0; i < b1; i++) emit(code[p[i]], len[p[i]]);
+    if (k + 1 == nseg) emit(code[256], len[256]);
+    if (nacc > 0) atomicOr(&w[wi], (uint32_t)acc);
 }
 
 // container tables and the motion vectors (after the streams are written)
@@ -662,9 +603,11 @@ __global__ void k_dfl_tables(DflArgs a) {
     if (S.err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     uint8_t* o = F.out;
-    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? 2 : F.in[i];   // version 2: deflated
-    for (int c = t; c < a.ncomp; c += nt) wr32(o + a.hdr_bytes + 4 * c, (uint32_t)S.comp[c].out_bytes);
-    uint8_t* st = o + a.hdr_bytes + 4 * a.ncomp;
+    // version 2: a stream per component; 3: one stream (CVC-NTS)
+    for (int i = t; i < (int)a.hdr_bytes; i += nt) o[i] = i == 4 ? (a.nts ? 3 : 2) : F.in[i];
+    const int nstr = (int)S.nstr;
+    for (int c = t; c < nstr; c += nt) wr32(o + a.hdr_bytes + 4 * c, (uint32_t)S.comp[c].out_bytes);
+    uint8_t* st = o + a.hdr_bytes + 4 * nstr;
     for (uint32_t s = t; s < S.nseg; s += nt) {
         st[2 * s] = (uint8_t)S.segbits[s];
         st[2 * s + 1] = (uint8_t)(S.segbits[s] >> 8);
@@ -675,54 +618,78 @@ __global__ void k_dfl_tables(DflArgs a) {
 }
 
 // -------------------------------------------------------------- inflate
-// the container's tables: token offsets, segments, stream offsets (one block)
+// the container's tables: token offsets, segments, groups, stream offsets
+// (one block per frame).  Version 2: a stream per component; 3: one stream.
 __global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
     __shared__ unsigned long long sh[8];
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_one;
     const uint8_t* in = F.in;
-    const unsigned long long tabs = a.hdr_bytes + 4ULL * a.ncomp;
     if (threadIdx.x == 0) {
         S.err = 0;
         S.total = 0;
-        s_bad = F.in_len < (long long)tabs || rd32(in) != 0x31435643u || in[4] != 2 || in[5] != 0 ||
-                rd32(in + 28) != (uint32_t)a.ncomp;
+        s_bad = F.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || (in[4] != 2 && in[4] != 3) ||
+                in[5] != 0 || rd32(in + 28) != (uint32_t)a.ncomp;
+        s_one = !s_bad && in[4] == 3;
+        if (!s_bad && F.in_len < a.hdr_bytes + 4LL * (s_one ? 1 : a.ncomp)) s_bad = 1;
         if (s_bad) S.err = DFL_CORRUPT;
     }
     __syncthreads();
     if (s_bad) return;
-    unsigned long long tok = 0, seg = 0, sb = 0, tt, ts, tb;
+    const int one = s_one, nstr = one ? 1 : a.ncomp;
+    const unsigned long long tabs = a.hdr_bytes + 4ULL * nstr;
+    unsigned long long tok = 0, seg = 0, grp = 0, sb = 0, tt, ts, tg, tb;
     for (int b = 0; b < a.ncomp; b += blockDim.x) {
         const int c = b + threadIdx.x;
         const uint32_t n = c < a.ncomp ? rd32(in + 32 + 4 * c) : 0;
-        const uint32_t nb = c < a.ncomp ? rd32(in + a.hdr_bytes + 4 * c) : 0;
-        const unsigned long long segs = (2ULL * n + DFL_SEG - 1) / DFL_SEG;
+        const uint32_t nb = c < a.ncomp && !one ? rd32(in + a.hdr_bytes + 4 * c) : 0;
+        const unsigned long long segs = one ? 0 : (2ULL * n + DFL_SEG - 1) / DFL_SEG;
+        const unsigned long long grps = (segs + DFL_GRP - 1) / DFL_GRP;
         const unsigned long long pt = block_scan(n, sh, &tt), ps = block_scan(segs, sh, &ts),
-                                 pb = block_scan(nb, sh, &tb);
-        if (c < a.ncomp) {
+                                 pg = block_scan(grps, sh, &tg), pb = block_scan(nb, sh, &tb);
+        if (c < a.ncomp && !one) {
             S.comp[c].bytes = 2ULL * n;
             S.comp[c].in_off = a.hdr_bytes + 2 * (tok + pt);   // in the inflated frame
             S.comp[c].seg0 = (uint32_t)(seg + ps);
+            S.comp[c].grp0 = (uint32_t)(grp + pg);
             S.comp[c].out_off = sb + pb;                     // relative to the streams, fixed below
             S.comp[c].out_bytes = nb;
             if ((nb == 0) != (n == 0)) atomicOr(&S.err, DFL_CORRUPT);
         }
         tok += tt;
         seg += ts;
+        grp += tg;
         sb += tb;
+    }
+    if (one) {
+        seg = (2 * tok + DFL_SEG - 1) / DFL_SEG;
+        grp = (seg + DFL_GRP - 1) / DFL_GRP;
+        sb = rd32(in + a.hdr_bytes);
+        if (threadIdx.x == 0) {
+            S.comp[0].bytes = 2 * tok;
+            S.comp[0].in_off = a.hdr_bytes;
+            S.comp[0].seg0 = 0;
+            S.comp[0].grp0 = 0;
+            S.comp[0].out_off = 0;
+            S.comp[0].out_bytes = sb;
+            if ((sb == 0) != (tok == 0)) atomicOr(&S.err, DFL_CORRUPT);
+        }
     }
     __syncthreads();
     const unsigned long long streams = tabs + ((2ULL * seg + 3) & ~3ULL);
     if (seg <= (unsigned long long)a.max_seg)
-        for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) S.comp[c].out_off += streams;
+        for (int c = threadIdx.x; c < nstr; c += blockDim.x) S.comp[c].out_off += streams;
     if (threadIdx.x == 0) {
-        S.comp[a.ncomp].seg0 = (uint32_t)seg;
+        S.comp[nstr].seg0 = (uint32_t)seg;
+        S.comp[nstr].grp0 = (uint32_t)grp;
         const long long mvb = in[6] == 2 ? a.mv_bytes : 0;
-        if (seg > (unsigned long long)a.max_seg || (in[6] == 2 && a.mv_bytes == 0) ||
-            streams + sb + mvb > (unsigned long long)F.in_len)
+        if (seg > (unsigned long long)a.max_seg || grp > (unsigned long long)a.max_grp ||
+            (in[6] == 2 && a.mv_bytes == 0) || streams + sb + mvb > (unsigned long long)F.in_len)
             atomicOr(&S.err, DFL_CORRUPT);
         S.nseg = (uint32_t)seg;
+        S.nstr = (uint32_t)nstr;
+        S.ngrp = (uint32_t)grp;
         S.tok_bytes = 2 * tok;
         S.tail = mvb;
         S.streams = streams + sb;                  // where the motion vectors start
@@ -731,7 +698,7 @@ __global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
     }
 }
 
-// segment bit lengths from the container, with their component
+// segment bit lengths from the container
 __global__ void k_ifl_seglen(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
@@ -741,20 +708,12 @@ __global__ void k_ifl_seglen(DflArgs a) {
         S.segbits[s] = 0;
         return;
     }
-    const uint8_t* st = F.in + a.hdr_bytes + 4 * a.ncomp;
+    const uint8_t* st = F.in + a.hdr_bytes + 4 * S.nstr;
     S.segbits[s] = (uint32_t)st[2 * s] | ((uint32_t)st[2 * s + 1] << 8);
-    int lo = 0, hi = a.ncomp;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (S.comp[mid].seg0 <= s) lo = mid;
-        else hi = mid;
-    }
-    while (lo + 1 < a.ncomp && S.comp[lo + 1].seg0 <= s) lo++;
-    S.segcomp[s] = lo;
 }
 
-// block header of each component -> decoding tables (one block per
-// component): the header is read by one thread; the canonical code then
+// block header of each stream -> decoding tables (one block per stream):
+// the header is read by one thread; the canonical code then
 // fills a 2^DFL_LUT-entry table indexed by the next DFL_LUT bits of the
 // stream (symbol | length << 9; 0 for longer codes, which take the
 // bit-serial canonical decoder)
@@ -762,7 +721,7 @@ __global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
     const int c = blockIdx.x, tid = threadIdx.x;
-    if (S.err) return;
+    if (S.err || c >= (int)S.nstr) return;
     DflComp& C = S.comp[c];
     if (C.bytes == 0) return;
     __shared__ uint8_t lens[286 + 30];
@@ -885,17 +844,17 @@ __global__ void __launch_bounds__(128) k_ifl_tables(DflArgs a) {
     }
 }
 
-// the literals of every segment: one block per component, its decoding tables
-// in shared memory, one thread per segment at a time (lookup table, longer codes
+// the literals of every segment: one block per group, the stream's decoding
+// tables in shared memory, one thread per segment (lookup table, longer codes
 // bit by bit); each segment must take exactly its recorded bits, and the
-// component's last one must be followed by the end-of-block code
+// stream's last one must be followed by the end-of-block code
 __global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
     const DflFrame& F = a.fr[blockIdx.y];
     DflScratch& S = *F.S;
-    const int c = blockIdx.x;
-    if (S.err) return;
+    const uint32_t g = blockIdx.x;
+    if (S.err || g >= S.ngrp) return;
+    const int c = group_stream(S.comp, (int)S.nstr, g);
     const DflComp& C = S.comp[c];
-    if (C.bytes == 0) return;
     __shared__ uint16_t tab[1 << DFL_LUT];
     __shared__ uint16_t count[16], sym[DFL_NSYM];
     for (int i = threadIdx.x; i < (1 << DFL_LUT); i += blockDim.x) tab[i] = S.dtab[(size_t)c * (1 << DFL_LUT) + i];
@@ -907,7 +866,8 @@ __global__ void __launch_bounds__(256) k_ifl_decode(DflArgs a) {
     uint8_t* o = F.out + C.in_off;
     const uint32_t nseg = S.comp[c + 1].seg0 - C.seg0;
     bool ok = true;
-    for (uint32_t k = threadIdx.x; ok && k < nseg; k += blockDim.x) {
+    const uint32_t k = (g - C.grp0) * DFL_GRP + threadIdx.x;
+    if (k < nseg) {
         const uint32_t s = C.seg0 + k;
         const unsigned long long start = C.hdr_bits + (S.segoff[s] - S.segoff[C.seg0]);
         const unsigned long long stop = start + S.segbits[s];

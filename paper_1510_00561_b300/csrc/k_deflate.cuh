@@ -1,11 +1,13 @@
-// k_deflate.cuh -- the DEFLATE stage (§3.9, scalable mode): device
-// structures of the per-component Huffman-only DEFLATE and its inflate.
+// k_deflate.cuh -- the DEFLATE stage (§3.9): device structures of the
+// Huffman-only DEFLATE (one stream per component, or per frame for CVC-NTS)
+// and its inflate.
 #pragma once
 #include "k_codec.cuh"
 
 namespace cvc {
 
 constexpr int DFL_SEG = 256;         // input bytes per segment (one thread each)
+constexpr int DFL_GRP = 256;         // segments per group (one block each)
 constexpr int DFL_NLIT = 257;        // literal bytes and the end-of-block code
 constexpr int DFL_NSYM = 288;        // decoding table entries per component
 constexpr int DFL_HDR_BYTES = 512;   // room for one dynamic block header
@@ -21,11 +23,14 @@ struct DflComp {
     unsigned long long data_bits;  // literals and end-of-block code
     uint32_t seg0;                 // first segment
     uint32_t hdr_bits;             // dynamic block header
+    uint32_t grp0;                 // first group of segments
+    uint32_t pad;
 };
 
-// device scratch of one context (sized for the stream's largest frame)
+// device scratch of one frame (sized for the stream's largest frame).  A
+// "stream" below is a component (scalable mode) or the whole frame (CVC-NTS).
 struct DflScratch {
-    DflComp* comp;          // ncomp + 1
+    DflComp* comp;          // streams + 1
     uint32_t* hist;         // ncomp x DFL_NLIT
     uint8_t* len;           // ncomp x DFL_NLIT code lengths
     uint16_t* code;         // ncomp x DFL_NLIT bit-reversed codes
@@ -35,8 +40,8 @@ struct DflScratch {
     uint16_t* dtab;         // ncomp x 2^DFL_LUT decoding: symbol | length << 9 by the next bits
     uint32_t* segbits;      // max_seg + 1 (the frame's slice of one array for all frames)
     uint32_t* segoff;       // max_seg + 1 (exclusive scan of that array, up to a constant per frame)
-    int* segcomp;           // max_seg
     uint32_t err, nseg;
+    uint32_t nstr, ngrp;    // streams, groups of segments
     unsigned long long tok_bytes, tail, total, streams;
 };
 
@@ -53,7 +58,8 @@ struct DflArgs {
     const DflFrame* fr;     // device: one per frame of the call
     long long hdr_bytes;    // 32 + 4 ncomp
     long long mv_bytes;     // motion vectors of a type-2 frame
-    int ncomp, max_seg;
+    int ncomp, max_seg, max_grp;
+    int nts;                // deflate: one stream per frame (CVC-NTS) instead of one per component
 };
 
 __global__ void k_dfl_plan(DflArgs a);

@@ -1,5 +1,5 @@
-"""The DEFLATE stage on the GPU (§3.9, scalable mode), cvc_deflate_frame /
-cvc_inflate_frame.
+"""The DEFLATE stage on the GPU (§3.9, scalable and CVC-NTS modes),
+cvc_deflate_frame / cvc_inflate_frame.
 
 What is unique is checked exactly, the rest for validity:
   - every component stream is a raw DEFLATE stream that zlib inflates to
@@ -9,7 +9,9 @@ What is unique is checked exactly, the rest for validity:
   - each stream's code is an optimal prefix code of its bytes plus the
     end-of-block code (cost equal to the oracle's Huffman cost) whenever that
     optimum needs no code longer than 15 bits, and within 1% of it otherwise;
-  - corrupt containers and short buffers are refused.
+  - corrupt containers and short buffers are refused;
+  - CVC-NTS: the frame's token bytes are one such stream (version byte 3),
+    and the same checks hold for it.
 """
 import zlib
 
@@ -215,3 +217,82 @@ def test_batched_calls_equal_single_frame_calls():
     packed, sts = many.deflate_many(streams, outs)
     assert sts[5] == 3 and all(v == 0 for i, v in enumerate(sts) if i != 5)
     assert torch.equal(packed[4], one.deflate(streams[4]))
+
+
+def _check_nts(frame_dev, dfl, oc):
+    frame = frame_dev.cpu().numpy()
+    packed = dfl.deflate(frame_dev).clone()
+    pk = packed.cpu().numpy()
+    hdr = 32 + 4 * oc.ncomp
+    assert pk[4] == 3 and np.array_equal(pk[:4], frame[:4]) and np.array_equal(pk[5:hdr], frame[5:hdr])
+    counts = np.frombuffer(bytes(frame[32:hdr]), "<u4").astype(np.int64)
+    tok = bytes(frame[hdr:hdr + 2 * int(counts.sum())])
+    nb = int(np.frombuffer(bytes(pk[hdr:hdr + 4]), "<u4")[0])
+    nseg = (len(tok) + 255) // 256
+    segs = np.frombuffer(bytes(pk[hdr + 4:hdr + 4 + 2 * nseg]), "<u2").astype(np.int64)
+    pos = hdr + 4 + ((2 * nseg + 3) // 4) * 4
+    stream = bytes(pk[pos:pos + nb])
+    assert zlib.decompress(stream, wbits=-15) == tok
+    # segment k covers token bytes [256 k, 256 k + 256) of the frame
+    hist = np.bincount(np.frombuffer(tok, np.uint8), minlength=256).astype(np.uint64)
+    cost, depth = O.huffman_cost(np.append(hist, 1))
+    if depth <= 15:
+        assert cost - 15 <= int(segs.sum()) <= cost - 1
+    else:
+        assert int(segs.sum()) <= 1.01 * cost
+    assert np.array_equal(pk[pos + nb:], frame[hdr + len(tok):])     # the motion vectors
+    assert np.array_equal(oc.inflate_container(pk), frame)
+    assert torch.equal(dfl.inflate(packed), frame_dev)
+    return packed
+
+
+@pytest.mark.parametrize("kw,n", [(QCIF, 5), (VGA, 3), (HD, 2)], ids=["qcif", "vga_motion", "1080p"])
+def test_cvc_nts_round_trip(kw, n):
+    """§3.9 CVC-NTS: one stream over all the components of a frame; a frame of
+    1080p spans many segment groups"""
+    g = _codec(kw)
+    nts, sc = Deflater(nts=True, **kw), Deflater(**kw)
+    oc = _oracle(kw)
+    dec_a, dec_b = _codec(kw), _codec(kw)
+    for f in S.SyntheticVideo(S.spec_for(kw["width"], kw["height"], seed=76)).frames(n):
+        s, _ = g.encode(torch.from_numpy(f).cuda())
+        s = s.clone()
+        packed = _check_nts(s, nts, oc)
+        # the scalable inflater reads both forms
+        back = sc.inflate(packed).clone()
+        assert torch.equal(back, s)
+        # decoding at every scale is unaffected (scalability at the decoder stays)
+        assert torch.equal(dec_a.decode(back), dec_b.decode(s.clone()))
+
+
+def test_cvc_nts_refusals_and_batches():
+    kw = dict(QCIF, key_interval=3, motion_range=8)
+    g = _codec(kw)
+    frames = S.SyntheticVideo(S.spec_for(176, 144, seed=77)).frames(6)
+    streams = [g.encode(torch.from_numpy(f).cuda())[0].clone() for f in frames]
+    one, many = Deflater(nts=True, **kw), Deflater(max_frames=6, nts=True, **kw)
+    scal = Deflater(max_frames=6, **kw)
+    outs = [torch.zeros(s.numel() + 65536, dtype=torch.uint8, device="cuda") for s in streams]
+    packed, sts = many.deflate_many(streams, outs)
+    assert sts == [0] * 6
+    for s, p in zip(streams, packed):
+        assert torch.equal(p, one.deflate(s))
+    # an inflate call mixing both container forms
+    mixed = [p.clone() if i % 2 else scal.deflate(streams[i]).clone() for i, p in enumerate(packed)]
+    backs = [torch.zeros(s.numel() + 16, dtype=torch.uint8, device="cuda") for s in streams]
+    back, sts = many.inflate_many(mixed, backs)
+    assert sts == [0] * 6
+    for s, b in zip(streams, back):
+        assert torch.equal(b, s)
+    p = packed[0].clone()
+    with pytest.raises(CvcError) as e:
+        g.drop_levels(p.cpu(), 1)                     # one stream: nothing to drop in transit
+    assert e.value.status == 2
+    bad = p.clone()
+    bad[4] = 2                                        # read as a per-component container
+    with pytest.raises(CvcError) as e:
+        one.inflate(bad)
+    assert e.value.status == 5
+    with pytest.raises(CvcError) as e:
+        one.inflate(p[:-3].clone())
+    assert e.value.status == 5

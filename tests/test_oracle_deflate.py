@@ -3,7 +3,8 @@
     set of code lengths that satisfies Kraft's inequality (small alphabets),
     and known small cases;
   - the container inflater rebuilds a frame from per-component streams that
-    zlib wrote (any DEFLATE strategy), and refuses broken ones.
+    zlib wrote (any DEFLATE strategy), and from the one stream of a CVC-NTS
+    container, and refuses broken ones.
 """
 import itertools
 import zlib
@@ -43,29 +44,34 @@ def test_huffman_cost_is_the_optimal_prefix_code():
     assert O.huffman_cost(fib)[1] == len(fib) - 1
 
 
-def _container(frame, ncomp, strategy):
+def _container(frame, ncomp, strategy, nts=False):
     hdr = 32 + 4 * ncomp
     counts = np.frombuffer(bytes(frame[32:hdr]), "<u4")
-    streams, pos, nseg = [], hdr, 0
+    toks, pos = [], hdr
     for n in counts:
-        tok = bytes(frame[pos:pos + 2 * int(n)])
+        toks.append(bytes(frame[pos:pos + 2 * int(n)]))
         pos += 2 * int(n)
-        nseg += (2 * int(n) + 255) // 256
-        if n:
+    if nts:                                             # CVC-NTS: one stream over all token bytes
+        toks = [b"".join(toks)]
+    streams, nseg = [], 0
+    for tok in toks:
+        nseg += (len(tok) + 255) // 256
+        if tok:
             z = zlib.compressobj(6, zlib.DEFLATED, -15, 8, strategy)
             streams.append(z.compress(tok) + z.flush())
         else:
             streams.append(b"")
     tail = bytes(frame[pos:])
     head = bytearray(frame[:hdr])
-    head[4] = 2
+    head[4] = 3 if nts else 2
     lens = np.array([len(s) for s in streams], "<u4").tobytes()
     seg = bytes(((2 * nseg + 3) // 4) * 4)
     return np.frombuffer(bytes(head) + lens + seg + b"".join(streams) + tail, np.uint8)
 
 
+@pytest.mark.parametrize("nts", [False, True], ids=["scalable", "nts"])
 @pytest.mark.parametrize("strategy", [zlib.Z_DEFAULT_STRATEGY, zlib.Z_HUFFMAN_ONLY, zlib.Z_FIXED])
-def test_container_inflate_rebuilds_the_frame(strategy):
+def test_container_inflate_rebuilds_the_frame(strategy, nts):
     w, h = 176, 144
     kw = dict(width=w, height=h, levels=3, dirs_log2=[3, 2, 2], qph=8, qpl=1, key_interval=4, motion_range=8)
     c = O.Codec(**kw)
@@ -74,8 +80,12 @@ def test_container_inflate_rebuilds_the_frame(strategy):
         s, _ = c.encode(f)
         for d in (0, 2):
             x = c.drop_levels(s, d)
-            box = _container(x, c.ncomp, strategy)
+            box = _container(x, c.ncomp, strategy, nts)
             assert np.array_equal(c.inflate_container(box), x)
+    other = box.copy()
+    other[4] = 2 if nts else 3                           # the other container form: the tables disagree
+    with pytest.raises(RuntimeError, match="status 5"):
+        c.inflate_container(other)
     bad = box.copy()
     bad[32 + 4 * c.ncomp] += 1                           # the first stream's length
     with pytest.raises(RuntimeError, match="status 5"):

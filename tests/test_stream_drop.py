@@ -111,3 +111,14 @@ def test_drop_of_deflated_frames_equals_deflating_the_dropped_frame(motion):
             assert st == 0 and np.array_equal(got2, got)
             # and the oracle inflates what remains to the dropped frame
             assert np.array_equal(enc.inflate_container(got), enc.drop_levels(s, d))
+
+
+def test_cvc_nts_frames_cannot_lose_levels():
+    """§3.9: a CVC-NTS frame is one DEFLATE stream, so transmission scalability is gone"""
+    w, h, Lv, k = 176, 144, 3, [3, 2, 2]
+    prm = L.params(w, h, Lv, k, 8, 1, 0.0, 4)
+    enc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 4)
+    s, _ = enc.encode(S.SyntheticVideo(S.spec_for(w, h, seed=11)).frame(0))
+    box = _deflate_like_the_container(s, enc.ncomp).copy()
+    box[4] = 3
+    assert _drop(prm, box, 1)[0] == 2
