@@ -363,7 +363,8 @@ def rd_run(dev, n_frames=30):
     """Rate-distortion analogues of the paper's QCIF experiments (§4.1, Figs 3, 4, 6-8) on the
     synthetic QCIF sequence: mean Y-PSNR of the decoded frames, and mean deflated bits per frame
     (DEFLATE stage, scalable and CVC-NTS).  rd: the whole QPH range with QPL = max(1, QPH // 14), motion
-    search +-8, K every 10; qph: QPH with QPL = 1 (Fig. 3); qpl: QPL with QPH = 1 (Fig. 4)."""
+    search +-8, K every 10; rd8: the same with the paper's 8-bit storage; qph: QPH with QPL = 1 (Fig. 3);
+    qpl: QPL with QPH = 1 (Fig. 4).  k_subband_nonzero: the share of non-zero subband codes of the K-frames."""
     import numpy as np
     import torch
     from paper_1510_00561_b300 import Codec, Deflater
@@ -378,22 +379,47 @@ def rd_run(dev, n_frames=30):
 
     y_src = [luma(f) for f in d_src]
 
-    def point(qph, qpl, motion):
-        kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=qph, qpl=qpl, key_interval=10, motion_range=motion)
+    nsub = 1 + sum(1 << d for d in k)                        # components of one plane
+
+    def subband_codes(s, ncomp):
+        """(non-zero, all) subband codes of a K-frame, from its tokens"""
+        b = s.cpu().numpy()
+        counts = np.frombuffer(b[32:32 + 4 * ncomp].tobytes(), "<u4")
+        toks = np.frombuffer(b[32 + 4 * ncomp:32 + 4 * ncomp + 2 * int(counts.sum())].tobytes(), "<i2")
+        nz = tot = pos = 0
+        for j, n in enumerate(counts):
+            t = toks[pos:pos + int(n)]
+            pos += int(n)
+            if j % nsub:
+                runs = t == 0
+                run_len = np.roll(runs, 1)                   # the count after each run marker
+                run_len[0] = False
+                nz += int((~runs & ~run_len).sum())
+                tot += int((~runs & ~run_len).sum()) + int(t[np.flatnonzero(runs) + 1].sum())
+        return nz, tot
+
+    def point(qph, qpl, motion, storage8=False):
+        kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=qph, qpl=qpl, key_interval=10, motion_range=motion,
+                  storage8=storage8)
         enc, dec, dfl, nts = Codec(**kw), Codec(**kw), Deflater(**kw), Deflater(nts=True, **kw)
-        mse, bits, bits_nts = 0.0, 0, 0
+        mse, bits, bits_nts, nz, tot = 0.0, 0, 0, 0, 0
         for f, ys in zip(d_src, y_src):
-            s, _ = enc.encode(f)
+            s, ft = enc.encode(f)
             bits += 8 * dfl.deflate(s).numel()
             bits_nts += 8 * nts.deflate(s).numel()
             mse += float(((luma(dec.decode(s.clone())) - ys) ** 2).mean())
+            if ft == 0:
+                a, b = subband_codes(s, enc.ncomp)
+                nz, tot = nz + a, tot + b
         mse /= len(d_src)
         return {"qph": qph, "qpl": qpl, "y_psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-12)),
-                "kbit_per_frame": bits / len(d_src) / 1e3, "kbit_per_frame_nts": bits_nts / len(d_src) / 1e3}
+                "kbit_per_frame": bits / len(d_src) / 1e3, "kbit_per_frame_nts": bits_nts / len(d_src) / 1e3,
+                "k_subband_nonzero": nz / max(tot, 1)}
 
     qphs = [1, 2, 4, 8, 16, 32, 64, 128, 181]
     return {"workload": "synthetic QCIF, %d frames, 3 levels 8/4/4 directions, 4:2:0" % n_frames,
             "rd": [point(q, max(1, q // 14), 8) for q in qphs],
+            "rd8": [point(q, max(1, q // 14), 8, storage8=True) for q in qphs],
             "qph": [point(q, 1, 0) for q in qphs],
             "qpl": [point(1, q, 0) for q in [1, 2, 4, 8, 16, 32, 48, 71]]}
 

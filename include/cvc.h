@@ -164,7 +164,17 @@ cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* plan, const float* d_coef
  *                   (i 2^ey, j 2^ex) (the last block row / column past the
  *                   plane) and reads the previous code at (i + dy/2^ey,
  *                   j + dx/2^ex), each quotient rounded half away from zero,
- *                   clamped to the component.                               */
+ *                   clamped to the component.
+ *   storage8        0: lossless YCoCg-R colour and int16 codes.  1: the
+ *                   paper's 8-bit storage (§3.1, §3.6): the colour
+ *                   transform of Table I in its real-valued form, every
+ *                   component rounded (ties away from zero) to a byte,
+ *                   chroma offset by +127 and clamped to [0, 255] (the
+ *                   decoder subtracts 127); every code (the quotient by
+ *                   QPH / QPL, rounded) is clamped to a byte: subbands
+ *                   [-128, 127], the normalised lowpass [0, 255].
+ *                   Header byte 5 records it; a decoder refuses a stream of
+ *                   the other storage.                                      */
 #define CVC_MAX_MOTION_RANGE 64
 typedef struct {
     int width, height;
@@ -175,6 +185,7 @@ typedef struct {
     int key_interval;
     int chroma_420;
     int motion_range;
+    int storage8;
 } cvc_params;
 
 typedef struct {
@@ -199,9 +210,10 @@ cvc_status cvc_codec_info(const cvc_codec* codec, cvc_codec_info_t* out);
  *   d_out        receives the frame bitstream (device), capacity out_cap bytes
  *   *out_len     (host) bytes written; on CVC_ERR_CAPACITY the bytes needed
  *   *frame_type  (host, may be NULL) 0 = K-frame, 1 = P-frame
- * Bitstream (little-endian): 32-byte header {"CVC1", u16 version=1, u8 type,
- * u8 levels, u32 frame index, u16 height, u16 width, u8 dirs_log2[6],
- * u16 qph, u16 qpl, u16 0, u32 ncomp}, then ncomp u32 token counts, then the
+ * Bitstream (little-endian): 32-byte header {"CVC1", u8 version=1, u8
+ * storage8, u8 type, u8 levels, u32 frame index, u16 height, u16 width, u8
+ * dirs_log2[6], u16 qph, u16 qpl, u16 0, u32 ncomp}, then ncomp u32 token
+ * counts, then the
  * int16 tokens of every component.  Components run Y, Co, Cg, each in the
  * coefficient layout order.  The K-frame lowpass holds its column-differenced
  * codes raw; every other component holds, row by row, one token per non-zero

@@ -67,6 +67,10 @@ def lib():
         L.or_chroma_up.argtypes = [_I16, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I16]
         L.or_pad_mirror.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
         L.or_quantize.argtypes = [ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _IP]
+        L.or_quantize8.argtypes = [ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int]
+        L.or_ycocg8_forward.argtypes = [_U8, ctypes.c_long, _I16, _I16, _I16]
+        L.or_ycocg8_inverse.argtypes = [_I16, _I16, _I16, ctypes.c_long, _U8]
+        L.or_codec_set_storage8.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_rle_row.argtypes = [_I16, ctypes.c_int, _I16]
         L.or_rle_row.restype = ctypes.c_long
         L.or_rle_expand.argtypes = [_I16, ctypes.c_long, _I16, ctypes.c_long]
@@ -277,6 +281,24 @@ def ycocgr_inverse(y, co, cg):
     return rgb.reshape(y.shape + (3,))
 
 
+def ycocg8_forward(rgb):
+    """Table 1, real-valued, 8-bit storage: (Y, Co + 127, Cg + 127) as bytes in int16 arrays"""
+    rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+    n = rgb.size // 3
+    y, co, cg = (np.zeros(n, np.int16) for _ in range(3))
+    lib().or_ycocg8_forward(rgb.reshape(-1), n, y, co, cg)
+    shp = rgb.shape[:-1]
+    return y.reshape(shp), co.reshape(shp), cg.reshape(shp)
+
+
+def ycocg8_inverse(y, co, cg):
+    y, co, cg = (np.ascontiguousarray(a, dtype=np.int16) for a in (y, co, cg))
+    n = y.size
+    rgb = np.zeros(n * 3, np.uint8)
+    lib().or_ycocg8_inverse(y.reshape(-1), co.reshape(-1), cg.reshape(-1), n, rgb)
+    return rgb.reshape(y.shape + (3,))
+
+
 def chroma_down(p):
     p = np.ascontiguousarray(p, dtype=np.int16)
     H, W = p.shape
@@ -310,6 +332,11 @@ def quantize(c, qp, threshold, is_lowpass, levels):
     return q
 
 
+def quantize8(c, qp, threshold, is_lowpass, levels):
+    """the quantiser under 8-bit storage (the coefficient rounded and clamped to a byte first)"""
+    return lib().or_quantize8(ctypes.c_float(c), qp, ctypes.c_float(threshold), int(is_lowpass), levels)
+
+
 def rle_row(row):
     row = np.ascontiguousarray(row, dtype=np.int16)
     tok = np.zeros(2 * row.size + 2, np.int16)
@@ -330,7 +357,7 @@ class Codec:
     """The oracle codec: one video stream, encoder and decoder state."""
 
     def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10,
-                 motion_range=0):
+                 motion_range=0, storage8=False):
         if qpl is None:
             qpl = max(1, qph // 14)
         self.width, self.height, self.levels = width, height, levels
@@ -343,6 +370,8 @@ class Codec:
             raise ValueError("oracle codec: invalid parameters")
         if lib().or_codec_set_motion(self._h, motion_range):
             raise ValueError("oracle codec: invalid motion range")
+        self.storage8 = bool(storage8)
+        lib().or_codec_set_storage8(self._h, int(self.storage8))
         self.ncoef = lib().or_codec_coeff_count(self._h)
         self.ncomp = lib().or_codec_ncomp(self._h)
         self.max_stream = lib().or_codec_max_stream(self._h)

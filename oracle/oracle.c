@@ -527,6 +527,31 @@ void or_ycocgr_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, l
     }
 }
 
+/* v / d for d = 2 or 4, rounded half away from zero (exact integer arithmetic) */
+static long div_round(long v, long d) {
+    long a = v < 0 ? -v : v;
+    a = (a + d / 2) / d;
+    return v < 0 ? -a : a;
+}
+
+void or_ycocg8_forward(const uint8_t* rgb, long n, int16_t* y, int16_t* co, int16_t* cg) {
+    for (long i = 0; i < n; i++) {
+        long R = rgb[3 * i], G = rgb[3 * i + 1], B = rgb[3 * i + 2];
+        y[i] = (int16_t)div_round(R + 2 * G + B, 4);
+        co[i] = (int16_t)clampi(div_round(R - B, 2) + 127, 0, 255);
+        cg[i] = (int16_t)clampi(div_round(2 * G - R - B, 4) + 127, 0, 255);
+    }
+}
+
+void or_ycocg8_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, long n, uint8_t* rgb) {
+    for (long i = 0; i < n; i++) {
+        long Y = y[i], Co = (long)co[i] - 127, Cg = (long)cg[i] - 127;
+        rgb[3 * i] = (uint8_t)clampi(Y + Co - Cg, 0, 255);
+        rgb[3 * i + 1] = (uint8_t)clampi(Y + Cg, 0, 255);
+        rgb[3 * i + 2] = (uint8_t)clampi(Y - Co - Cg, 0, 255);
+    }
+}
+
 /* §3.1 chroma subsampling, factor N = 4 read as 2 x 2: rounded mean of each
  * 2x2 block, floor((s + 2) / 4); odd sizes replicate the last row / column. */
 void or_chroma_down(const int16_t* in, int H, int W, int16_t* out) {
@@ -586,6 +611,17 @@ int or_quantize(float c, int qp, float threshold, int is_lowpass, int levels, in
     else t = (fabsf(c) >= threshold) ? c : 0.0f;
     float v = roundf(t / (float)qp);
     if (!(fabsf(v) <= 32767.0f)) { *ovf = 1; return 0; }
+    return (int)v;
+}
+
+int or_quantize8(float c, int qp, float threshold, int is_lowpass, int levels) {
+    float t;
+    if (is_lowpass) t = ldexpf(c, -levels);
+    else t = (fabsf(c) >= threshold) ? c : 0.0f;
+    float v = roundf(t / (float)qp);                 /* §3.5 divide, §3.6 round: one rounding */
+    float lo = is_lowpass ? 0.0f : -128.0f, hi = is_lowpass ? 255.0f : 127.0f;
+    if (v < lo) v = lo;                              /* §3.6: the code is kept in a byte */
+    if (v > hi) v = hi;
     return (int)v;
 }
 
@@ -675,6 +711,7 @@ struct or_codec {
     int range;      /* motion search range W (0: zero-motion P-frames) */
     int nby, nbx;   /* 16 x 16 luma blocks */
     uint8_t* enc_luma;   /* the previous frame's padded luma (encoder) */
+    int st8;        /* 8-bit storage (§3.1, §3.6) */
 };
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -720,6 +757,11 @@ int or_codec_set_motion(or_codec* c, int range) {
     c->nbx = (c->Wp + 15) / 16;
     free(c->enc_luma);
     c->enc_luma = range ? (uint8_t*)calloc((size_t)c->Hp * c->Wp, 1) : NULL;
+    return OR_OK;
+}
+
+int or_codec_set_storage8(or_codec* c, int on) {
+    c->st8 = on != 0;
     return OR_OK;
 }
 
@@ -769,7 +811,8 @@ void or_codec_planes(const or_codec* c, const uint8_t* rgb, double* y, double* c
     int16_t* Co2 = (int16_t*)malloc(sizeof(int16_t) * nc);
     int16_t* Cg2 = (int16_t*)malloc(sizeof(int16_t) * nc);
     double* t = (double*)malloc(sizeof(double) * n);
-    or_ycocgr_forward(rgb, n, Y, Co, Cg);
+    if (c->st8) or_ycocg8_forward(rgb, n, Y, Co, Cg);
+    else or_ycocgr_forward(rgb, n, Y, Co, Cg);
     or_chroma_down(Co, c->Ho, c->Wo, Co2);
     or_chroma_down(Cg, c->Ho, c->Wo, Cg2);
     for (long i = 0; i < n; i++) t[i] = Y[i];
@@ -859,7 +902,9 @@ int or_encode_from_coeffs_luma(or_codec* c, const float* coeffs, const uint8_t* 
         int low = s->kind == 0;
         for (long e = 0; e < (long)s->h * s->w; e++) {
             long idx = base + s->off + e;
-            q[idx] = (int16_t)or_quantize(coeffs[idx], low ? c->qpl : c->qph, c->thr, low, c->L, &ovf);
+            int qp = low ? c->qpl : c->qph;
+            q[idx] = (int16_t)(c->st8 ? or_quantize8(coeffs[idx], qp, c->thr, low, c->L)
+                                      : or_quantize(coeffs[idx], qp, c->thr, low, c->L, &ovf));
         }
     }
     if (ovf) { free(q); free(r); return OR_EOVERFLOW; }
@@ -910,7 +955,8 @@ int or_encode_from_coeffs_luma(or_codec* c, const float* coeffs, const uint8_t* 
     if (need > cap) { free(q); free(r); free(tok); free(counts); free(mv); free(pred); return OR_ECAPACITY; }
     memset(out, 0, 32);
     out[0] = 'C'; out[1] = 'V'; out[2] = 'C'; out[3] = '1';
-    put16(out + 4, 1);
+    out[4] = 1;
+    out[5] = (uint8_t)c->st8;
     out[6] = (uint8_t)type;
     out[7] = (uint8_t)c->L;
     put32(out + 8, (unsigned long)c->enc_frame);
@@ -963,7 +1009,7 @@ int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* pl
 int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_t* rgb, double* planes_out) {
     if (scale < 0 || scale > c->L) return OR_EINVAL;
     if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
-    if (get16(in + 4) != 1) return OR_ECORRUPT;
+    if (in[4] != 1 || in[5] != c->st8) return OR_ECORRUPT;
     int type = in[6];
     if (type > 2 || (type == 2 && !c->range) || in[7] != c->L || get16(in + 12) != (unsigned)c->Ho || get16(in + 14) != (unsigned)c->Wo)
         return OR_ECORRUPT;
@@ -1076,17 +1122,20 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
     int16_t* Cg = (int16_t*)malloc(sizeof(int16_t) * n);
     int16_t* Co2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
     int16_t* Cg2 = (int16_t*)malloc(sizeof(int16_t) * ncs);
+    /* chroma: YCoCg-R values in [-255, 255], or bytes offset by 127 under 8-bit storage */
+    const int clo = c->st8 ? 0 : -255;
     for (int y = 0; y < Hos; y++)
         for (int x = 0; x < Wos; x++)
             Y[(long)y * Wos + x] = (int16_t)clampi((long)roundf((float)pl[(long)y * Wps + x]), 0, 255);
     for (int y = 0; y < Hcs; y++)
         for (int x = 0; x < Wcs; x++) {
-            Co2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + (long)y * Wcps + x]), -255, 255);
-            Cg2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + nc + (long)y * Wcps + x]), -255, 255);
+            Co2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + (long)y * Wcps + x]), clo, 255);
+            Cg2[(long)y * Wcs + x] = (int16_t)clampi((long)roundf((float)pl[ny + nc + (long)y * Wcps + x]), clo, 255);
         }
     or_chroma_up(Co2, Hcs, Wcs, Hos, Wos, Co);
     or_chroma_up(Cg2, Hcs, Wcs, Hos, Wos, Cg);
-    or_ycocgr_inverse(Y, Co, Cg, n, rgb);
+    if (c->st8) or_ycocg8_inverse(Y, Co, Cg, n, rgb);
+    else or_ycocgr_inverse(Y, Co, Cg, n, rgb);
     memcpy(c->dec_state, q, sizeof(int16_t) * (size_t)c->ncoef);
     c->dec_next = fidx + 1;
     c->dec_floor = type == 0 ? drop : (drop > c->dec_floor ? drop : c->dec_floor);
@@ -1176,7 +1225,7 @@ static unsigned long rd32u(const uint8_t* p) { return get32(p); }
 int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len) {
     long hdr = 32 + 4L * c->ncomp;
     if (len < hdr || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || (in[4] != 2 && in[4] != 3) ||
-        in[5] != 0 || get32(in + 28) != (unsigned long)c->ncomp)
+        in[5] != c->st8 || get32(in + 28) != (unsigned long)c->ncomp)
         return OR_ECORRUPT;
     /* version 2: a stream per component; 3 (CVC-NTS): one stream of all token bytes */
     int nstr = in[4] == 3 ? 1 : c->ncomp;

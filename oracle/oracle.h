@@ -75,9 +75,20 @@ void or_ycocgr_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, l
 void or_chroma_down(const int16_t* in, int H, int W, int16_t* out);
 void or_chroma_up(const int16_t* in, int Hc, int Wc, int H, int W, int16_t* out);
 void or_pad_mirror(const double* in, int H, int W, int Hp, int Wp, double* out);
+/* Table 1 in its real-valued form with the paper's 8-bit storage (§3.1):
+ * Y = (R + 2G + B)/4, Co = (R - B)/2, Cg = (2G - R - B)/4, each rounded half
+ * away from zero; Co and Cg offset by +127 and clamped to [0, 255].  The
+ * inverse removes the offset and applies R = Y + Co - Cg, G = Y + Cg,
+ * B = Y - Co - Cg, clamped to [0, 255].                                    */
+void or_ycocg8_forward(const uint8_t* rgb, long n, int16_t* y, int16_t* co, int16_t* cg);
+void or_ycocg8_inverse(const int16_t* y, const int16_t* co, const int16_t* cg, long n, uint8_t* rgb);
 
 /* quantiser of one value, single-precision decision (returns 0 on overflow flag set) */
 int or_quantize(float c, int qp, float threshold, int is_lowpass, int levels, int* ovf);
+/* the same under 8-bit storage (§3.6): the rounded quotient is clamped to
+ * a byte, [-128, 127] for subbands and [0, 255] for the lowpass; single
+ * precision                                                                */
+int or_quantize8(float c, int qp, float threshold, int is_lowpass, int levels);
 
 /* run-length coding of one row; returns tokens written */
 long or_rle_row(const int16_t* row, int w, int16_t* tokens);
@@ -131,6 +142,10 @@ void or_motion_search(const uint8_t* cur, const uint8_t* prev, int H, int W, int
  * with rounding half away from zero, and reads the previous code at the
  * displaced position clamped to the component.                              */
 int or_codec_set_motion(or_codec* c, int range);
+/* 8-bit storage (§3.1, §3.6), on != 0: the colour transform and quantiser
+ * above, header byte 5 = 1; a decoder accepts only streams of its own
+ * storage.  Default 0: YCoCg-R and int16 codes.                            */
+int or_codec_set_storage8(or_codec* c, int on);
 
 /* the entropy side of the encoder from given single-precision coefficients:
  * threshold, quantise, K/P differencing, state update, RLE, bitstream.      */

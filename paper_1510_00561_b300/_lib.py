@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("levels", ctypes.c_int),
                 ("dirs_log2", ctypes.c_int * MAX_LEVELS), ("qph", ctypes.c_int), ("qpl", ctypes.c_int),
                 ("subband_threshold", ctypes.c_float), ("key_interval", ctypes.c_int),
-                ("chroma_420", ctypes.c_int), ("motion_range", ctypes.c_int)]
+                ("chroma_420", ctypes.c_int), ("motion_range", ctypes.c_int), ("storage8", ctypes.c_int)]
 
 
 class CodecInfo(ctypes.Structure):
@@ -166,11 +166,13 @@ def lib():
     return _lib
 
 
-def params(width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10, motion_range=0):
+def params(width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10, motion_range=0,
+           storage8=False):
     """cvc_params of one stream (qpl defaults to max(1, qph // 14))."""
     if qpl is None:
         qpl = max(1, qph // 14)
-    return Params(width, height, levels, ints(dirs_log2), qph, qpl, threshold, key_interval, 1, motion_range)
+    return Params(width, height, levels, ints(dirs_log2), qph, qpl, threshold, key_interval, 1, motion_range,
+                  int(bool(storage8)))
 
 
 def check(status, where):

@@ -123,11 +123,11 @@ class Codec:
     """One CVC video stream on the GPU (encoder and decoder state resident in HBM)."""
 
     def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10,
-                 motion_range=0):
-        prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval, motion_range)
+                 motion_range=0, storage8=False):
+        prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval, motion_range, storage8)
         self.width, self.height, self.levels, self.dirs = width, height, levels, list(dirs_log2)
         self.qph, self.qpl, self.threshold, self.key_interval = qph, prm.qpl, threshold, key_interval
-        self.motion_range = motion_range
+        self.motion_range, self.storage8 = motion_range, bool(storage8)
         self._prm = prm
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_create")

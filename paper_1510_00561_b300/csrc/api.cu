@@ -331,7 +331,7 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         return (uint32_t)in[at] | ((uint32_t)in[at + 1] << 8) | ((uint32_t)in[at + 2] << 16) |
                ((uint32_t)in[at + 3] << 24);
     };
-    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[4] < 1 || in[4] > 3 || in[5] != 0 ||
+    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[4] < 1 || in[4] > 3 || in[5] > 1 ||
         in[7] != params->levels || rd32(28) != ncomp)
         return CVC_ERR_CORRUPT;
     if (in[4] == 3) return CVC_ERR_UNSUPPORTED;   // CVC-NTS: one stream, no level can leave it

@@ -115,6 +115,7 @@ cvc_status plan_scales(Core* c) {
             Q.Hc = (g.Hc + f - 1) >> sc;
             Q.Wc = (g.Wc + f - 1) >> sc;
             Q.norm = ldexpf(1.0f, -sc);
+            Q.st8 = D.qp.st8;
             Q.blk0 = (int)sp->h_blk.size();
             // padded planes are multiples of 2^L, so these sizes are exact
             const int hs[3] = {g.Hp >> sc, g.Hcp >> sc, g.Hcp >> sc}, ws[3] = {g.Wp >> sc, g.Wcp >> sc, g.Wcp >> sc};
@@ -186,7 +187,7 @@ bool codec_params_valid(const cvc_params* prm) {
     return prm && prm->width >= 1 && prm->height >= 1 && prm->width <= 65535 && prm->height <= 65535 &&
            dirs_valid(prm->levels, prm->dirs_log2) && prm->qph >= 1 && prm->qph <= 181 && prm->qpl >= 1 &&
            prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1 && prm->motion_range >= 0 &&
-           prm->motion_range <= CVC_MAX_MOTION_RANGE;
+           prm->motion_range <= CVC_MAX_MOTION_RANGE && (prm->storage8 == 0 || prm->storage8 == 1);
 }
 
 bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
@@ -268,6 +269,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.qp.threshold = P.subband_threshold;
         D.qp.low_scale = ldexpf(1.0f, -L);
         D.qp.qpl_denorm = ldexpf((float)P.qpl, L);
+        D.qp.st8 = P.storage8;
         D.hdr.levels = L;
         D.hdr.height = g.H;
         D.hdr.width = g.W;

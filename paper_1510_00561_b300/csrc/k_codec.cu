@@ -19,7 +19,22 @@ __device__ __forceinline__ int mirror_idx(int a, int n) { return a < n ? a : 2 *
 // Cg = G - t, Y = t + (Cg>>1).  One block per padded output row: rows
 // [0, Hp) are luma rows, rows [Hp, Hp + Hcp) chroma rows (each writes its Co
 // and Cg row; 2x2 rounded mean, odd edges replicated); padding mirrors about
-// the last row / column.
+// the last row / column.  8-bit storage (§3.1, §3.6): Table I's
+// real-valued form instead, each component rounded to a byte, chroma offset
+// by +127 and clamped to [0, 255].
+// v / 2^sh rounded half away from zero (sh >= 1)
+__device__ __forceinline__ int div_pow2_round(int v, int sh) {
+    const int r = (abs(v) + (1 << (sh - 1))) >> sh;
+    return v < 0 ? -r : r;
+}
+
+// luma of one pixel: YCoCg-R, or (8-bit storage) Table I's Y = (R + 2G + B)/4 rounded
+__device__ __forceinline__ int luma_of(int R, int G, int B, bool st8) {
+    if (st8) return (R + 2 * G + B + 2) >> 2;
+    const int co = R - B, t = B + (co >> 1), cg = G - t;
+    return t + (cg >> 1);
+}
+
 __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                const int* __restrict__ blk_stream, float* __restrict__ planes,
                                uint8_t* __restrict__ luma0, uint8_t* __restrict__ luma1) {
@@ -28,6 +43,7 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
     if (!C.enc_on) return;
     const SDesc& D = sd[s];
     const ColourGeom g = D.cg;
+    const bool st8 = D.qp.st8;
     const int row = blockIdx.x - D.blk_colour;
     const uint8_t* rgb = C.rgb_in;
     const long long pitch = C.pitch_in;
@@ -49,19 +65,13 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
                                     (int)(w1 & 255), (int)((w1 >> 8) & 255), (int)((w1 >> 16) & 255), (int)(w1 >> 24),
                                     (int)(w2 & 255), (int)((w2 >> 8) & 255), (int)((w2 >> 16) & 255), (int)(w2 >> 24)};
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const int R = px[3 * k], G = px[3 * k + 1], Bv = px[3 * k + 2];
-                    const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-                    yv[k] = t + (cg >> 1);
-                }
+                for (int k = 0; k < 4; k++) yv[k] = luma_of(px[3 * k], px[3 * k + 1], px[3 * k + 2], st8);
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const int x = min(x0 + k, g.Wp - 1);
                     const uint8_t* p = src + 3 * mirror_idx(x, g.W);
-                    const int R = p[0], G = p[1], Bv = p[2];
-                    const int co = R - Bv, t = Bv + (co >> 1), cg = G - t;
-                    yv[k] = t + (cg >> 1);
+                    yv[k] = luma_of(p[0], p[1], p[2], st8);
                 }
             }
             if (vec && x0 + 4 <= g.Wp) {
@@ -91,9 +101,15 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const int R = q[k][0], G = q[k][1], Bv = q[k][2];
-                const int co = R - Bv, t = Bv + (co >> 1);
-                sco += co;
-                scg += G - t;
+                if (st8) {
+                    // Table I: Co = (R - B)/2, Cg = (2G - R - B)/4, rounded, +127, clamped to a byte
+                    sco += min(max(div_pow2_round(R - Bv, 1) + 127, 0), 255);
+                    scg += min(max(div_pow2_round(2 * G - R - Bv, 2) + 127, 0), 255);
+                } else {
+                    const int co = R - Bv, t = Bv + (co >> 1);
+                    sco += co;
+                    scg += G - t;
+                }
             }
             oco[cx] = (float)((sco + 2) >> 2);
             ocg[cx] = (float)((scg + 2) >> 2);
@@ -109,7 +125,8 @@ __device__ __forceinline__ int round_clamp(float v, int lo, int hi) {
 
 // Decoder end: normalise by the scale's DC gain, round (ties away from zero)
 // and clamp the reconstructed planes, bilinear (9,3,3,1)/16 chroma
-// upsampling with centred siting and clamped edges, inverse YCoCg-R, clamp to
+// upsampling with centred siting and clamped edges, inverse YCoCg-R (8-bit
+// storage: Table I's inverse after removing the chroma offset), clamp to
 // [0, 255].  One block per output row.  A stream whose bitstream was
 // rejected leaves its output untouched.
 __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall* __restrict__ sc,
@@ -131,6 +148,8 @@ __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall*
                             {Cg + (long long)i0 * D.rs_c, Cg + (long long)i1 * D.rs_c}};
     uint8_t* orow = C.rgb_out + (long long)y * C.pitch_out;
     const bool vec = ((uintptr_t)orow & 3) == 0;
+    const bool st8 = D.st8;
+    const int clo = st8 ? 0 : -255;    // chroma bytes (offset by 127), or YCoCg-R chroma
     // four pixels per thread: their chroma columns x/2 - 1 .. x/2 + 2 (clamped) are rounded once
     for (int x0 = 4 * threadIdx.x; x0 < D.W; x0 += 4 * blockDim.x) {
         const int jb = x0 >> 1;
@@ -141,7 +160,7 @@ __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall*
 #pragma unroll
             for (int q = 0; q < 2; q++)
 #pragma unroll
-                for (int r = 0; r < 2; r++) cv[q][r][k] = round_clamp(P[q][r][j] * norm, -255, 255);
+                for (int r = 0; r < 2; r++) cv[q][r][k] = round_clamp(P[q][r][j] * norm, clo, 255);
         }
         uint32_t px[3] = {0, 0, 0};
 #pragma unroll
@@ -155,10 +174,18 @@ __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall*
 #pragma unroll
             for (int q = 0; q < 2; q++)
                 c[q] = (9 * cv[q][0][i0] + 3 * cv[q][1][i0] + 3 * cv[q][0][i1] + cv[q][1][i1] + 8) >> 4;
-            const int t = yy - (c[1] >> 1);
-            const int G = c[1] + t;
-            const int Bv = t - (c[0] >> 1);
-            const int R = Bv + c[0];
+            int R, G, Bv;
+            if (st8) {                   // Table I inverse: R = Y + Co - Cg, G = Y + Cg, B = Y - Co - Cg
+                const int co = c[0] - 127, cg = c[1] - 127;
+                R = yy + co - cg;
+                G = yy + cg;
+                Bv = yy - co - cg;
+            } else {
+                const int t = yy - (c[1] >> 1);
+                G = c[1] + t;
+                Bv = t - (c[0] >> 1);
+                R = Bv + c[0];
+            }
             const uint32_t rgb3[3] = {(uint32_t)min(max(R, 0), 255), (uint32_t)min(max(G, 0), 255),
                                       (uint32_t)min(max(Bv, 0), 255)};
 #pragma unroll
@@ -181,6 +208,8 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
     if (low) t = c * q.low_scale;                    // exact power-of-two normalisation
     else t = (fabsf(c) >= q.threshold) ? c : 0.0f;
     float v = roundf(t / (low ? q.qpl : q.qph));     // IEEE division, ties away from zero
+    // 8-bit storage (§3.6): the rounded code is kept in a byte
+    if (q.st8) v = low ? fminf(fmaxf(v, 0.0f), 255.0f) : fminf(fmaxf(v, -128.0f), 127.0f);
     if (!(fabsf(v) <= 32767.0f)) {
         atomicOr(err, EF_OVERFLOW);
         return 0;
@@ -588,7 +617,7 @@ __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __r
     if (threadIdx.x == 0) {
         const StreamHeader& h = D.hdr;
         o[0] = 'C'; o[1] = 'V'; o[2] = 'C'; o[3] = '1';
-        o[4] = 1; o[5] = 0;
+        o[4] = 1; o[5] = (uint8_t)D.qp.st8;
         o[6] = (uint8_t)(C.enc_key ? 0 : (mc ? 2 : 1));
         o[7] = (uint8_t)h.levels;
         for (int i = 0; i < 4; i++) o[8 + i] = (uint8_t)(C.enc_index >> (8 * i));
@@ -649,7 +678,8 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
         if (in_len < D.hdr_bytes) bad = EF_CORRUPT;
         else {
             const StreamHeader& e = D.hdr;
-            if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] != 0) bad = EF_CORRUPT;
+            if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] > 1) bad = EF_CORRUPT;
+            else if (in[5] != D.qp.st8) bad = EF_MISMATCH;              // the other storage
             int type = in[6];
             if (type > 2) bad = EF_CORRUPT;
             if (type == 2 && D.mv_range == 0) bad |= EF_MISMATCH;   // vectors for a decoder without motion

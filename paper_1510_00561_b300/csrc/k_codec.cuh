@@ -17,6 +17,7 @@ struct QuantParams {
     float threshold;
     float low_scale;    // 2^-L (exact)
     float qpl_denorm;   // qpl * 2^L (exact)
+    int st8;            // 8-bit storage (§3.6): codes clamped to a byte
 };
 
 struct StreamHeader {
@@ -65,7 +66,7 @@ struct ScaleDesc {
     int blk0;              // first block (output row) of the stream
     long long off[3];      // Y, Co, Cg in that buffer
     float norm;            // 2^-s: the DC gain of s pyramid levels (exact)
-    int pad;
+    int st8;               // 8-bit storage: Table I colour with chroma offset by 127
 };
 
 // per stream, refreshed every call

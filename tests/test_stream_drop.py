@@ -122,3 +122,15 @@ def test_cvc_nts_frames_cannot_lose_levels():
     box = _deflate_like_the_container(s, enc.ncomp).copy()
     box[4] = 3
     assert _drop(prm, box, 1)[0] == 2
+
+
+def test_drop_of_8bit_storage_frames():
+    """header byte 5 (the 8-bit storage of §3.6) passes through the dropper"""
+    w, h, Lv, k = 176, 144, 3, [3, 2, 2]
+    prm = L.params(w, h, Lv, k, 8, 1, 0.0, 3, storage8=True)
+    enc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 3, storage8=True)
+    for f in S.SyntheticVideo(S.spec_for(w, h, seed=12)).frames(2):
+        s, _ = enc.encode(f)
+        for d in range(Lv + 1):
+            st, got, _ = _drop(prm, s, d)
+            assert st == 0 and got[5] == 1 and np.array_equal(got, enc.drop_levels(s, d))
