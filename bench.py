@@ -364,7 +364,8 @@ def rd_run(dev, n_frames=30):
     synthetic QCIF sequence: mean Y-PSNR of the decoded frames, and mean deflated bits per frame
     (DEFLATE stage, scalable and CVC-NTS).  rd: the whole QPH range with QPL = max(1, QPH // 14), motion
     search +-8, K every 10; rd8: the same with the paper's 8-bit storage; qph: QPH with QPL = 1 (Fig. 3);
-    qpl: QPL with QPH = 1 (Fig. 4).  k_subband_nonzero: the share of non-zero subband codes of the K-frames."""
+    qpl: QPL with QPH = 1 (Fig. 4).  k_subband_nonzero: the share of non-zero subband codes of the K-frames.
+    fig5: deflated bytes of the K-frames' lowpass bands with and without the column filter (Fig. 5)."""
     import numpy as np
     import torch
     from paper_1510_00561_b300 import Codec, Deflater
@@ -416,8 +417,39 @@ def rd_run(dev, n_frames=30):
                 "kbit_per_frame": bits / len(d_src) / 1e3, "kbit_per_frame_nts": bits_nts / len(d_src) / 1e3,
                 "k_subband_nonzero": nz / max(tot, 1)}
 
+    def fig5(qpl):
+        """§3.7 / Fig. 5: deflated bytes of the K-frames' lowpass bands with the column
+        filter (as coded) and without it (the running sums of the coded differences)"""
+        kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=8, qpl=qpl, key_interval=10)
+        enc, dfl = Codec(**kw), Deflater(**kw)
+        shapes = [(enc.Hp >> L, enc.Wp >> L)] + [(enc.Hcp >> L, enc.Wcp >> L)] * 2
+        filt = raw = 0
+        for t, f in enumerate(d_src):
+            s, ft = enc.encode(f)
+            if ft != 0:
+                continue
+            b = s.cpu().numpy().copy()
+            nc = enc.ncomp
+            counts = np.frombuffer(b[32:32 + 4 * nc].tobytes(), "<u4").astype(np.int64)
+            starts = 32 + 4 * nc + 2 * np.concatenate([[0], np.cumsum(counts)[:-1]])
+            for p_, j in enumerate(range(0, nc, nsub)):
+                hh, ww = shapes[p_]
+                assert counts[j] == hh * ww
+                d = np.frombuffer(b[starts[j]:starts[j] + 2 * hh * ww].tobytes(), "<i2").reshape(hh, ww)
+                codes = np.cumsum(d.astype(np.int64), axis=0).astype(np.int16)   # undo the filter
+                b[starts[j]:starts[j] + 2 * hh * ww] = np.frombuffer(codes.tobytes(), np.uint8)
+            lens = []
+            for frame in (s, torch.from_numpy(b).to(dev)):
+                pk = dfl.deflate(frame).cpu().numpy()
+                sl = np.frombuffer(pk[32 + 4 * nc:32 + 8 * nc].tobytes(), "<u4")
+                lens.append(int(sl[::nsub].sum()))
+            filt, raw = filt + lens[0], raw + lens[1]
+        return {"qpl": qpl, "lowpass_bytes_filtered": filt, "lowpass_bytes_unfiltered": raw,
+                "gain": raw / max(filt, 1)}
+
     qphs = [1, 2, 4, 8, 16, 32, 64, 128, 181]
     return {"workload": "synthetic QCIF, %d frames, 3 levels 8/4/4 directions, 4:2:0" % n_frames,
+            "fig5": [fig5(q) for q in (1, 4, 12)],
             "rd": [point(q, max(1, q // 14), 8) for q in qphs],
             "rd8": [point(q, max(1, q // 14), 8, storage8=True) for q in qphs],
             "qph": [point(q, 1, 0) for q in qphs],

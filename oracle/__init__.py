@@ -58,6 +58,9 @@ def lib():
         L.or_lp_analysis_adjoint.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, _D]
         L.or_lp_synthesis_adjoint.argtypes = [_D, ctypes.c_int, ctypes.c_int, _D, _D]
         L.or_dfb.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.or_dfb_taps.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.or_ct_taps.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, _D]
+        L.or_codec_set_taps.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_soft_threshold.argtypes = [_D, ctypes.POINTER(_Layout), ctypes.c_int, _D, _D]
         L.or_soft_threshold_vjp.argtypes = [_D, ctypes.POINTER(_Layout), ctypes.c_int, _D, _D, _D, _D]
         L.or_ct.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, _D]
@@ -192,24 +195,25 @@ def lp_synthesis_adjoint(xbar):
     return c, d
 
 
-def dfb(mode, x, H, W, k):
+def dfb(mode, x, H, W, k, taps=4):
     """mode 0/3: x is an H x W plane, returns concatenated subbands (1-D);
-    mode 1/2: x is the concatenated subbands, returns the H x W plane."""
+    mode 1/2: x is the concatenated subbands, returns the H x W plane.
+    taps: the prototype's length (4, 6 or 8)."""
     x = _f64(x).ravel()
     out = np.zeros(H * W)
-    st = lib().or_dfb(mode, x, H, W, k, out)
+    st = lib().or_dfb_taps(mode, x, H, W, k, taps, out)
     if st:
         raise ValueError("dfb: invalid arguments")
     return out if mode in (0, 3) else out.reshape(H, W)
 
 
-def ct(mode, x, H, W, L, k):
+def ct(mode, x, H, W, L, k, taps=4):
     """mode 0/3: plane -> coefficient vector; mode 1/2: coefficient vector -> plane."""
     lay = layout(H, W, L, k)
     x = _f64(x).ravel()
     n_out = lay["total"] if mode in (0, 3) else H * W
     out = np.zeros(n_out)
-    st = lib().or_ct(mode, x, H, W, L, _ints(k), out)
+    st = lib().or_ct_taps(mode, x, H, W, L, _ints(k), taps, out)
     if st:
         raise ValueError("ct: invalid arguments")
     return out if mode in (0, 3) else out.reshape(H, W)
@@ -357,7 +361,7 @@ class Codec:
     """The oracle codec: one video stream, encoder and decoder state."""
 
     def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10,
-                 motion_range=0, storage8=False):
+                 motion_range=0, storage8=False, dfb_taps=4):
         if qpl is None:
             qpl = max(1, qph // 14)
         self.width, self.height, self.levels = width, height, levels
@@ -372,6 +376,9 @@ class Codec:
             raise ValueError("oracle codec: invalid motion range")
         self.storage8 = bool(storage8)
         lib().or_codec_set_storage8(self._h, int(self.storage8))
+        self.dfb_taps = dfb_taps
+        if lib().or_codec_set_taps(self._h, dfb_taps):
+            raise ValueError("oracle codec: invalid DFB prototype length")
         self.ncoef = lib().or_codec_coeff_count(self._h)
         self.ncomp = lib().or_codec_ncomp(self._h)
         self.max_stream = lib().or_codec_max_stream(self._h)

@@ -272,8 +272,30 @@ void or_lp_synthesis_adjoint(const double* xbar, int H, int W, double* cbar, dou
  * rectangular lattices: F_c on 2^(k-1) x 2 (rows x columns), F_r on
  * 2 x 2^(k-1); k = 1 keeps the two quincunx halves row-compacted.
  * Subband order = tree order (even child first at every split).            */
-static const int DFB_A[4] = {-3, -1, 1, 3};
-static const double DFB_BT[4] = {-1.0 / 16, -9.0 / 16, 9.0 / 16, 1.0 / 16};
+/* Longer prototypes (the PKVA structure admits any half-band beta): the
+ * Lagrange (maximally flat) half-band interpolators of 6 and 8 taps,
+ *   beta6 = (3, -25, 150, 150, -25, 3) / 256,
+ *   beta8 = (-5, 49, -245, 1225, 1225, -245, 49, -5) / 2048,
+ * at a = -5..5 and -7..7 (odd), modulated to the fan the same way.        */
+static const int DFB_A[8] = {-7, -5, -3, -1, 1, 3, 5, 7};
+static const double DFB_BETA4[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
+static const double DFB_BETA6[6] = {3.0 / 256, -25.0 / 256, 150.0 / 256, 150.0 / 256, -25.0 / 256, 3.0 / 256};
+static const double DFB_BETA8[8] = {-5.0 / 2048, 49.0 / 2048, -245.0 / 2048, 1225.0 / 2048,
+                                    1225.0 / 2048, -245.0 / 2048, 49.0 / 2048, -5.0 / 2048};
+
+/* the fan taps betat[a] = (-1)^((a-1)/2) beta[a] of an n-tap prototype, at
+ * offsets a = DFB_A[4 - n/2 ..]; 0 unless n is 4, 6 or 8 */
+static int dfb_taps(int n, const int** a, double* bt) {
+    const double* beta = n == 4 ? DFB_BETA4 : (n == 6 ? DFB_BETA6 : (n == 8 ? DFB_BETA8 : NULL));
+    if (!beta) return 0;
+    *a = DFB_A + 4 - n / 2;
+    for (int t = 0; t < n; t++) {
+        int av = (*a)[t];
+        int e = (av - 1) / 2;                         /* exact: av is odd */
+        bt[t] = ((e % 2 + 2) % 2 ? -1.0 : 1.0) * beta[t];
+    }
+    return n;
+}
 
 typedef struct { int o_r, o_c, T, i; } dfb_chan; /* T: 0 = F_c, 1 = F_r */
 
@@ -351,8 +373,9 @@ static void dfb_plan_free(dfb_plan* P) {
 }
 
 /* one lifting pass of stage s: every sample of parity `target` becomes
- * alpha * itself + gamma * (weighted sum of its 16 neighbours of the other parity) */
-static void dfb_pass(const dfb_plan* P, double* x, int s, int target, double alpha, double gamma) {
+ * alpha * itself + gamma * (weighted sum of its n^2 neighbours of the other parity) */
+static void dfb_pass(const dfb_plan* P, double* x, int s, int target, double alpha, double gamma, int n,
+                     const int* A, const double* BT) {
     int H = P->H, W = P->W;
     for (int r = 0; r < H; r++)
         for (int c = 0; c < W; c++) {
@@ -361,12 +384,12 @@ static void dfb_pass(const dfb_plan* P, double* x, int s, int target, double alp
             int b[4];
             dfb_basis(s, &P->chans[s][P->cid[s][idx]], b);
             double acc = 0.0;
-            for (int ia = 0; ia < 4; ia++)
-                for (int ib = 0; ib < 4; ib++) {
-                    int a = DFB_A[ia], bb = DFB_A[ib];
+            for (int ia = 0; ia < n; ia++)
+                for (int ib = 0; ib < n; ib++) {
+                    int a = A[ia], bb = A[ib];
                     int d1 = (a + bb) / 2, d2 = (a - bb) / 2;
                     int orr = d1 * b[0] + d2 * b[2], occ = d1 * b[1] + d2 * b[3];
-                    acc += DFB_BT[ia] * DFB_BT[ib] * x[(long)wrapi((long)r + orr, H) * W + wrapi((long)c + occ, W)];
+                    acc += BT[ia] * BT[ib] * x[(long)wrapi((long)r + orr, H) * W + wrapi((long)c + occ, W)];
                 }
             x[idx] = alpha * x[idx] + gamma * acc;
         }
@@ -393,7 +416,14 @@ static void dfb_leaf_dims(const dfb_plan* P, int ci, int* h, int* w) {
 }
 
 int or_dfb(int mode, const double* in, int H, int W, int k, double* out) {
-    if (k < 0 || k > OR_MAX_K) return OR_EINVAL;
+    return or_dfb_taps(mode, in, H, W, k, 4, out);
+}
+
+int or_dfb_taps(int mode, const double* in, int H, int W, int k, int taps, double* out) {
+    const int* A;
+    double BT[8];
+    int n = dfb_taps(taps, &A, BT);
+    if (!n || k < 0 || k > OR_MAX_K) return OR_EINVAL;
     int need = k >= 2 ? (1 << (k - 1)) : 2;
     if (k > 0 && (H % need || W % need)) return OR_EINVAL;
     long np = (long)H * W;
@@ -407,11 +437,11 @@ int or_dfb(int mode, const double* in, int H, int W, int k, double* out) {
         memcpy(x, in, sizeof(double) * np);
         for (int s = 1; s <= k; s++) {
             if (mode == 0) {            /* forward: predict odd, then update even */
-                dfb_pass(&P, x, s, 1, 0.5, -0.5);
-                dfb_pass(&P, x, s, 0, 1.0, 1.0);
+                dfb_pass(&P, x, s, 1, 0.5, -0.5, n, A, BT);
+                dfb_pass(&P, x, s, 0, 1.0, 1.0, n, A, BT);
             } else {                    /* transpose of the inverse stage */
-                dfb_pass(&P, x, s, 0, 1.0, 1.0);
-                dfb_pass(&P, x, s, 1, 2.0, -1.0);
+                dfb_pass(&P, x, s, 0, 1.0, 1.0, n, A, BT);
+                dfb_pass(&P, x, s, 1, 2.0, -1.0, n, A, BT);
             }
         }
         long o = 0;
@@ -440,11 +470,11 @@ int or_dfb(int mode, const double* in, int H, int W, int k, double* out) {
         }
         for (int s = k; s >= 1; s--) {
             if (mode == 1) {            /* inverse: undo update, then undo predict */
-                dfb_pass(&P, x, s, 0, 1.0, -1.0);
-                dfb_pass(&P, x, s, 1, 2.0, 1.0);
+                dfb_pass(&P, x, s, 0, 1.0, -1.0, n, A, BT);
+                dfb_pass(&P, x, s, 1, 2.0, 1.0, n, A, BT);
             } else {                    /* transpose of the forward stage */
-                dfb_pass(&P, x, s, 1, 0.5, 0.5);
-                dfb_pass(&P, x, s, 0, 1.0, -1.0);
+                dfb_pass(&P, x, s, 1, 0.5, 0.5, n, A, BT);
+                dfb_pass(&P, x, s, 0, 1.0, -1.0, n, A, BT);
             }
         }
         memcpy(out, x, sizeof(double) * np);
@@ -459,6 +489,10 @@ int or_dfb(int mode, const double* in, int H, int W, int k, double* out) {
  * feeds a DFB with k_j stages.  Modes: 0 forward A, 1 inverse S,
  * 2 adjoint A^T, 3 adjoint S^T.                                             */
 int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double* out) {
+    return or_ct_taps(mode, in, H, W, L, k, 4, out);
+}
+
+int or_ct_taps(int mode, const double* in, int H, int W, int L, const int* k, int taps, double* out) {
     or_layout lay;
     int st = or_layout_make(H, W, L, k, &lay);
     if (st) return st;
@@ -472,7 +506,7 @@ int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double*
             int Hj = H >> (j - 1), Wj = W >> (j - 1);
             if (mode == 0) or_lp_analysis(cur, Hj, Wj, nxt, det);
             else or_lp_synthesis_adjoint(cur, Hj, Wj, nxt, det);
-            st = or_dfb(mode, det, Hj, Wj, k[j - 1], out + off);
+            st = or_dfb_taps(mode, det, Hj, Wj, k[j - 1], taps, out + off);
             if (st) break;
             off += (long)Hj * Wj;
             double* t = cur; cur = nxt; nxt = t;
@@ -485,7 +519,7 @@ int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double*
         for (int j = 1; j <= L; j++) { offs[j] = off; off += (long)(H >> (j - 1)) * (W >> (j - 1)); }
         for (int j = L; j >= 1; j--) {
             int Hj = H >> (j - 1), Wj = W >> (j - 1);
-            st = or_dfb(mode, in + offs[j], Hj, Wj, k[j - 1], det);
+            st = or_dfb_taps(mode, in + offs[j], Hj, Wj, k[j - 1], taps, det);
             if (st) break;
             if (mode == 1) or_lp_synthesis(cur, det, Hj, Wj, nxt);
             else or_lp_analysis_adjoint(cur, det, Hj, Wj, nxt);
@@ -712,6 +746,7 @@ struct or_codec {
     int nby, nbx;   /* 16 x 16 luma blocks */
     uint8_t* enc_luma;   /* the previous frame's padded luma (encoder) */
     int st8;        /* 8-bit storage (§3.1, §3.6) */
+    int taps;       /* DFB prototype length: 4, 6 or 8 */
 };
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -724,7 +759,7 @@ or_codec* or_codec_create(int width, int height, int levels, const int* dirs, in
     if (!(threshold >= 0.0f)) return NULL;
     or_codec* c = (or_codec*)calloc(1, sizeof(or_codec));
     c->Wo = width; c->Ho = height; c->L = levels; c->qph = qph; c->qpl = qpl;
-    c->thr = threshold; c->kint = key_interval;
+    c->thr = threshold; c->kint = key_interval; c->taps = 4;
     for (int j = 0; j < levels; j++) c->k[j] = dirs[j];
     int M = or_modulus(levels, c->k);
     c->Hp = round_up(height, M); c->Wp = round_up(width, M);
@@ -764,6 +799,15 @@ int or_codec_set_storage8(or_codec* c, int on) {
     c->st8 = on != 0;
     return OR_OK;
 }
+
+int or_codec_set_taps(or_codec* c, int taps) {
+    if (taps != 4 && taps != 6 && taps != 8) return OR_EINVAL;
+    c->taps = taps;
+    return OR_OK;
+}
+
+/* header byte 5: bit 0 the 8-bit storage, bits 1-2 the DFB prototype (0: 4 taps, 1: 6, 2: 8) */
+static int flags_byte(const or_codec* c) { return c->st8 | ((c->taps / 2 - 2) << 1); }
 
 /* §3.2: full-search block matching on luma (see oracle.h) */
 void or_motion_search(const uint8_t* cur, const uint8_t* prev, int H, int W, int range, int8_t* mv) {
@@ -956,7 +1000,7 @@ int or_encode_from_coeffs_luma(or_codec* c, const float* coeffs, const uint8_t* 
     memset(out, 0, 32);
     out[0] = 'C'; out[1] = 'V'; out[2] = 'C'; out[3] = '1';
     out[4] = 1;
-    out[5] = (uint8_t)c->st8;
+    out[5] = (uint8_t)flags_byte(c);
     out[6] = (uint8_t)type;
     out[7] = (uint8_t)c->L;
     put32(out + 8, (unsigned long)c->enc_frame);
@@ -983,9 +1027,9 @@ int or_encode(or_codec* c, const uint8_t* rgb, uint8_t* out, long cap, long* out
     double* pl = (double*)malloc(sizeof(double) * (size_t)(ny + 2 * nc));
     double* co = (double*)malloc(sizeof(double) * (size_t)c->ncoef);
     or_codec_planes(c, rgb, pl, pl + ny, pl + ny + nc);
-    or_ct(0, pl, c->Hp, c->Wp, c->L, c->k, co);
-    or_ct(0, pl + ny, c->Hcp, c->Wcp, c->L, c->k, co + c->ly.total);
-    or_ct(0, pl + ny + nc, c->Hcp, c->Wcp, c->L, c->k, co + c->ly.total + c->lc.total);
+    or_ct_taps(0, pl, c->Hp, c->Wp, c->L, c->k, c->taps, co);
+    or_ct_taps(0, pl + ny, c->Hcp, c->Wcp, c->L, c->k, c->taps, co + c->ly.total);
+    or_ct_taps(0, pl + ny + nc, c->Hcp, c->Wcp, c->L, c->k, c->taps, co + c->ly.total + c->lc.total);
     float* cf = (float*)malloc(sizeof(float) * (size_t)c->ncoef);
     for (long i = 0; i < c->ncoef; i++) cf[i] = (float)co[i];
     if (coeffs_out) memcpy(coeffs_out, co, sizeof(double) * (size_t)c->ncoef);
@@ -1009,7 +1053,7 @@ int or_decode(or_codec* c, const uint8_t* in, long len, uint8_t* rgb, double* pl
 int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_t* rgb, double* planes_out) {
     if (scale < 0 || scale > c->L) return OR_EINVAL;
     if (len < 32 || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1') return OR_ECORRUPT;
-    if (in[4] != 1 || in[5] != c->st8) return OR_ECORRUPT;
+    if (in[4] != 1 || in[5] != flags_byte(c)) return OR_ECORRUPT;
     int type = in[6];
     if (type > 2 || (type == 2 && !c->range) || in[7] != c->L || get16(in + 12) != (unsigned)c->Ho || get16(in + 14) != (unsigned)c->Wo)
         return OR_ECORRUPT;
@@ -1110,7 +1154,7 @@ int or_decode_scaled(or_codec* c, const uint8_t* in, long len, int scale, uint8_
             double* sub = (double*)malloc(sizeof(double) * (size_t)(nlow + tail));
             memcpy(sub, cp, sizeof(double) * (size_t)nlow);
             memcpy(sub + nlow, cp + ly->sb[first].off, sizeof(double) * (size_t)tail);
-            or_ct(1, sub, ph[p], pw[p], c->L - s, c->k + s, pl + ploff[p]);
+            or_ct_taps(1, sub, ph[p], pw[p], c->L - s, c->k + s, c->taps, pl + ploff[p]);
             free(sub);
         }
         for (long e = 0; e < (long)ph[p] * pw[p]; e++) pl[ploff[p] + e] = ldexp(pl[ploff[p] + e], -s);
@@ -1225,7 +1269,7 @@ static unsigned long rd32u(const uint8_t* p) { return get32(p); }
 int or_inflate_container(const or_codec* c, const uint8_t* in, long len, uint8_t* out, long cap, long* out_len) {
     long hdr = 32 + 4L * c->ncomp;
     if (len < hdr || in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || (in[4] != 2 && in[4] != 3) ||
-        in[5] != c->st8 || get32(in + 28) != (unsigned long)c->ncomp)
+        in[5] != flags_byte(c) || get32(in + 28) != (unsigned long)c->ncomp)
         return OR_ECORRUPT;
     /* version 2: a stream per component; 3 (CVC-NTS): one stream of all token bytes */
     int nstr = in[4] == 3 ? 1 : c->ncomp;

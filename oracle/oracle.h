@@ -65,9 +65,14 @@ void or_lp_synthesis_adjoint(const double* xbar, int H, int W, double* cbar, dou
  * analysis direction (modes 0,3): plane -> subbands concatenated in tree order.
  * synthesis direction (modes 1,2): subbands -> plane.                              */
 int or_dfb(int mode, const double* in, int H, int W, int k, double* out);
+/* the same with an n-tap prototype, n = 4 (the one above), 6 or 8: the
+ * Lagrange half-band interpolators (3, -25, 150, 150, -25, 3)/256 and
+ * (-5, 49, -245, 1225, 1225, -245, 49, -5)/2048 at a = -5..5 / -7..7       */
+int or_dfb_taps(int mode, const double* in, int H, int W, int k, int taps, double* out);
 
 /* full contourlet transform on one plane, modes as above; coefficient layout of or_layout */
 int or_ct(int mode, const double* in, int H, int W, int L, const int* k, double* out);
+int or_ct_taps(int mode, const double* in, int H, int W, int L, const int* k, int taps, double* out);
 
 /* colour, chroma and padding steps */
 void or_ycocgr_forward(const uint8_t* rgb, long n, int16_t* y, int16_t* co, int16_t* cg);
@@ -146,6 +151,9 @@ int or_codec_set_motion(or_codec* c, int range);
  * above, header byte 5 = 1; a decoder accepts only streams of its own
  * storage.  Default 0: YCoCg-R and int16 codes.                            */
 int or_codec_set_storage8(or_codec* c, int on);
+/* the DFB prototype length of the codec (4, the default, 6 or 8); header
+ * byte 5 carries it in bits 1-2 (0, 1, 2), bit 0 being the 8-bit storage  */
+int or_codec_set_taps(or_codec* c, int taps);
 
 /* the entropy side of the encoder from given single-precision coefficients:
  * threshold, quantise, K/P differencing, state update, RLE, bitstream.      */

@@ -22,6 +22,22 @@ import numpy as np
 BETA_T = {-3: -1.0 / 16, -1: -9.0 / 16, 1: 9.0 / 16, 3: 1.0 / 16}
 
 
+def lagrange_fan_taps(n):
+    """Fan taps of the n-tap Lagrange half-band prototype, from the interpolation
+    formula rather than a table: beta[a] is the weight of the sample at odd a in
+    the polynomial interpolation of degree n - 1 evaluated at 0, i.e.
+    prod_{b != a} b / (b - a), then modulated to the fan by (-1)^((a - 1) / 2)."""
+    pts = list(range(-(n - 1), n, 2))
+    taps = {}
+    for a in pts:
+        w = 1.0
+        for b in pts:
+            if b != a:
+                w *= b / (b - a)
+        taps[a] = (-1.0) ** (((a - 1) // 2) % 2) * w
+    return taps
+
+
 def basis(s, T, i):
     if s == 1:
         return (1, 0), (0, 1)
@@ -31,8 +47,9 @@ def basis(s, T, i):
     return ((q, -2 * i), (q, -2 * i - 2)) if T == "c" else ((-2 * i, q), (-2 * i - 2, q))
 
 
-def leaves(H, W, k):
+def leaves(H, W, k, taps=None):
     """Leaf list in tree order: dict(o, T, i, F) with F the equivalent filter on the DFT grid."""
+    taps = BETA_T if taps is None else taps
     wr = 2 * np.pi * np.fft.fftfreq(H)[:, None]
     wc = 2 * np.pi * np.fft.fftfreq(W)[None, :]
     chans = [dict(o=(0, 0), T=None, i=None, F=np.ones((H, W), complex))]
@@ -41,8 +58,8 @@ def leaves(H, W, k):
         for ch in chans:
             (b1r, b1c), (b2r, b2c) = basis(s, ch["T"], ch["i"])
             Wf = np.zeros((H, W), complex)
-            for a, ba in BETA_T.items():
-                for b, bb in BETA_T.items():
+            for a, ba in taps.items():
+                for b, bb in taps.items():
                     d1, d2 = (a + b) // 2, (a - b) // 2
                     Wf += ba * bb * np.exp(1j * (wr * (d1 * b1r + d2 * b2r) + wc * (d1 * b1c + d2 * b2c)))
             Fo = 0.5 * (1 - Wf)
@@ -61,12 +78,12 @@ def leaves(H, W, k):
     return chans, wr, wc
 
 
-def analysis(x, k):
+def analysis(x, k, taps=None):
     """Concatenated subbands of plane x (tree order), computed by FFT filtering."""
     H, W = x.shape
     X = np.fft.fft2(x)
     out = []
-    chans, _, _ = leaves(H, W, k)
+    chans, _, _ = leaves(H, W, k, taps)
     for ch in chans:
         f = np.real(np.fft.ifft2(ch["F"] * X))
         if k == 1:
@@ -93,10 +110,10 @@ def wedge_mask(ch, k, wr, wc):
         return (np.abs(wr) > np.abs(wc)) & (t >= i / 2 ** m) & (t < (i + 1) / 2 ** m)
 
 
-def wedge_fractions(k, N=128):
+def wedge_fractions(k, N=128, taps=None):
     """Per leaf: fraction of its equivalent filter's energy, over the high-frequency
     annulus pi/2 < |w| (where LP details live), that falls inside its own wedge."""
-    chans, wr, wc = leaves(N, N, k)
+    chans, wr, wc = leaves(N, N, k, taps)
     ann = np.hypot(wr, wc) > np.pi / 2
     fr = []
     for ch in chans:

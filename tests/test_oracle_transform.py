@@ -188,6 +188,54 @@ def test_dfb_plane_wave_direction():
     assert hits >= 6, hits
 
 
+# ---------------------------------------------- longer PKVA prototypes
+def test_lagrange_taps_of_the_model():
+    """the interpolation formula gives the known prototypes: (-1, 9, 9, -1)/16 for
+    4 taps (the table the oracle and the model use) and sums of 1"""
+    t4 = dfb_model.lagrange_fan_taps(4)
+    assert t4 == pytest.approx(dfb_model.BETA_T, abs=1e-15)
+    for n in (6, 8):
+        t = dfb_model.lagrange_fan_taps(n)
+        beta = [(-1.0) ** (((a - 1) // 2) % 2) * v for a, v in sorted(t.items())]
+        assert sum(beta) == pytest.approx(1.0, abs=1e-14) and beta == pytest.approx(beta[::-1])
+    assert [round(v * 256) for _, v in sorted(dfb_model.lagrange_fan_taps(6).items())] == [-3, -25, -150, 150, 25, 3]
+
+
+@pytest.mark.parametrize("taps", [6, 8])
+@pytest.mark.parametrize("k,shape", [(1, (8, 8)), (2, (16, 16)), (3, (16, 24)), (4, (32, 16)), (5, (32, 32))])
+def test_longer_prototype_dfb_matches_frequency_model(taps, k, shape):
+    x = _rng(15).standard_normal(shape)
+    y = O.dfb(0, x, *shape, k, taps=taps)
+    np.testing.assert_allclose(y, dfb_model.analysis(x, k, dfb_model.lagrange_fan_taps(taps)), atol=1e-11)
+    np.testing.assert_allclose(O.dfb(1, y, *shape, k, taps=taps), x, atol=1e-10)
+
+
+@pytest.mark.parametrize("taps", [6, 8])
+def test_longer_prototype_adjoints_and_ct(taps):
+    r = _rng(16)
+    H, W, k = 32, 32, 4
+    x, yb = r.standard_normal((H, W)), r.standard_normal(H * W)
+    lhs, rhs = np.sum(O.dfb(0, x, H, W, k, taps) * yb), np.sum(x * O.dfb(2, yb, H, W, k, taps))
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+    lhs, rhs = np.sum(O.dfb(1, yb, H, W, k, taps) * x), np.sum(yb * O.dfb(3, x, H, W, k, taps))
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+    x = r.uniform(0, 255, (64, 96))
+    c = O.ct(0, x, 64, 96, 3, [3, 2, 2], taps)
+    np.testing.assert_allclose(O.ct(1, c, 64, 96, 3, [3, 2, 2], taps), x, atol=1e-9)
+    assert not np.allclose(c, O.ct(0, x, 64, 96, 3, [3, 2, 2]))     # a different transform
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_longer_prototypes_are_more_directional(k):
+    """the point of a longer beta: a sharper fan, so more of every subband's energy
+    stays in its own wedge"""
+    f4 = dfb_model.wedge_fractions(k)
+    f6 = dfb_model.wedge_fractions(k, taps=dfb_model.lagrange_fan_taps(6))
+    f8 = dfb_model.wedge_fractions(k, taps=dfb_model.lagrange_fan_taps(8))
+    assert np.mean(f4) < np.mean(f6) < np.mean(f8)
+    assert min(f4) < min(f6) <= min(f8) + 1e-12
+
+
 def test_dfb_adjoints():
     r = _rng(8)
     for k, (H, W) in ((1, (8, 8)), (3, (16, 24)), (4, (32, 32))):
