@@ -504,6 +504,7 @@ def main():
     ap.add_argument("--no-scalable", action="store_true", help="skip the per-scale decode pass")
     ap.add_argument("--motion-range", type=int, default=8, help="search range of the motion pass (0: skip)")
     ap.add_argument("--no-rd", action="store_true", help="skip the QCIF rate-distortion sweeps")
+    ap.add_argument("--no-taps", action="store_true", help="skip the 6- and 8-tap DFB prototype pass")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -756,6 +757,34 @@ def main():
                   "stages_ms_per_frame": {k: v[0] / (KINT * B) for k, v in m_stage.items()}}
         del mb, m_outs
 
+    # longer DFB prototypes (6 and 8 taps, the plain per-sample DFB path): the same batched
+    # encode+decode, and its per-stage times
+    taps = None
+    if not args.no_taps:
+        taps = []
+        for nt in (6, 8):
+            tb = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
+                             key_interval=KINT, dfb_taps=nt)] * B)
+            tb.set_shape(*shape)
+            t_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+
+            def taps_step(i, tb=tb, t_outs=t_outs):
+                tb.step(3, rgb=frames_at(i), rgb_out=t_outs)
+
+            for i in range(args.warmup):
+                taps_step(i)
+            t_steps = max(4, min(args.steps, KINT))
+            t_value, t_ms, _ = combine_ranks(timed(lambda i: taps_step(args.warmup + i), t_steps), t_steps * B,
+                                             dist, dev)
+            tb.set_timing(True)
+            timed(lambda i: taps_step(args.warmup + t_steps + i), KINT)
+            t_stage = tb.timing()
+            tb.set_timing(False)
+            taps.append({"dfb_taps": nt, "value": t_value, "unit": UNIT, "ms_per_step": t_ms / t_steps,
+                         "steps": t_steps,
+                         "stages_ms_per_frame": {k: v[0] / (KINT * B) for k, v in t_stage.items()}})
+            del tb, t_outs
+
     rd = rd_run(dev) if (not args.no_rd and rank == 0) else None
 
     # served form: continuous batching of concurrent streams under a memory budget
@@ -808,7 +837,7 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "deflate": deflate, "rd": rd,
+            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "taps": taps, "deflate": deflate, "rd": rd,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},

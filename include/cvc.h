@@ -105,6 +105,9 @@ typedef struct cvc_ct_plan cvc_ct_plan;
 
 cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, int batch,
                               cvc_ct_plan** out);
+/* the same with a DFB prototype of dfb_taps (4, 6 or 8; see cvc_params)   */
+cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log2, int batch, int dfb_taps,
+                                   cvc_ct_plan** out);
 cvc_status cvc_ct_plan_destroy(cvc_ct_plan* plan);
 /* total coefficients of one plane of this plan (layout.total) */
 long long cvc_ct_plan_coeffs(const cvc_ct_plan* plan);
@@ -173,8 +176,15 @@ cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* plan, const float* d_coef
  *                   decoder subtracts 127); every code (the quotient by
  *                   QPH / QPL, rounded) is clamped to a byte: subbands
  *                   [-128, 127], the normalised lowpass [0, 255].
- *                   Header byte 5 records it; a decoder refuses a stream of
- *                   the other storage.                                      */
+ *                   Header byte 5 bit 0 records it; a decoder refuses a
+ *                   stream of the other storage.
+ *   dfb_taps        length of the DFB ladder's half-band prototype (§2.1
+ *                   fixes none): 0 or 4, (-1, 9, 9, -1)/16, run by the
+ *                   tiled DFB kernels; 6 or 8, the longer Lagrange
+ *                   half-band interpolators (3, -25, 150, 150, -25, 3)/256
+ *                   and (-5, 49, -245, 1225, 1225, -245, 49, -5)/2048, a
+ *                   sharper directional split, run by a plain per-sample
+ *                   kernel.  Header byte 5 bits 1-2 record it (0, 1, 2).    */
 #define CVC_MAX_MOTION_RANGE 64
 typedef struct {
     int width, height;
@@ -186,6 +196,7 @@ typedef struct {
     int chroma_420;
     int motion_range;
     int storage8;
+    int dfb_taps;
 } cvc_params;
 
 typedef struct {
@@ -211,7 +222,7 @@ cvc_status cvc_codec_info(const cvc_codec* codec, cvc_codec_info_t* out);
  *   *out_len     (host) bytes written; on CVC_ERR_CAPACITY the bytes needed
  *   *frame_type  (host, may be NULL) 0 = K-frame, 1 = P-frame
  * Bitstream (little-endian): 32-byte header {"CVC1", u8 version=1, u8
- * storage8, u8 type, u8 levels, u32 frame index, u16 height, u16 width, u8
+ * flags (bit 0 storage8, bits 1-2 dfb_taps / 2 - 2), u8 type, u8 levels, u32 frame index, u16 height, u16 width, u8
  * dirs_log2[6], u16 qph, u16 qpl, u16 0, u32 ncomp}, then ncomp u32 token
  * counts, then the
  * int16 tokens of every component.  Components run Y, Co, Cg, each in the
@@ -537,10 +548,15 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  * otherwise; h, w, levels and dirs_log2 are ignored).  Layout written to buf, little
  * endian:
  *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 bytes of an LP-level
- *   job, u32 bytes of a DFB stage-1+2 job, u32 bytes of a DFB row-split job, u32 0,
+ *   job, u32 bytes of a DFB stage-1+2 job, u32 bytes of a DFB row-split job,
+ *   u32 bytes of the trailing records (cvc_debug_scale_tables; else 0),
+ *   u32 bytes of a plain DFB job (longer prototypes),
  *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
- *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage >= 3),
- *   u32 njobs, and njobs job records (the library's job structures).
+ *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage
+ *   >= 3, 3 = plain DFB lifting pass, 4 = plain DFB copy between the detail
+ *   images and the layout), u32 njobs, for kinds 3 and 4 four u32 (stage,
+ *   target parity or 1 = image -> layout, alpha and gamma as f32), and njobs
+ *   job records (the library's job structures).
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */

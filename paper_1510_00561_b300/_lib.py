@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("levels", ctypes.c_int),
                 ("dirs_log2", ctypes.c_int * MAX_LEVELS), ("qph", ctypes.c_int), ("qpl", ctypes.c_int),
                 ("subband_threshold", ctypes.c_float), ("key_interval", ctypes.c_int),
-                ("chroma_420", ctypes.c_int), ("motion_range", ctypes.c_int), ("storage8", ctypes.c_int)]
+                ("chroma_420", ctypes.c_int), ("motion_range", ctypes.c_int), ("storage8", ctypes.c_int),
+                ("dfb_taps", ctypes.c_int)]
 
 
 class CodecInfo(ctypes.Structure):
@@ -106,6 +107,7 @@ def lib():
         L.cvc_modulus.argtypes = [_I, ctypes.POINTER(_I)]
         L.cvc_ct_layout.argtypes = [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(CtLayout)]
         L.cvc_ct_plan_create.argtypes = [_I, _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_P)]
+        L.cvc_ct_plan_create_taps.argtypes = [_I, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_P)]
         L.cvc_ct_plan_destroy.argtypes = [_P]
         L.cvc_ct_plan_coeffs.argtypes = [_P]
         L.cvc_ct_plan_coeffs.restype = ctypes.c_longlong
@@ -167,12 +169,12 @@ def lib():
 
 
 def params(width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10, motion_range=0,
-           storage8=False):
+           storage8=False, dfb_taps=4):
     """cvc_params of one stream (qpl defaults to max(1, qph // 14))."""
     if qpl is None:
         qpl = max(1, qph // 14)
     return Params(width, height, levels, ints(dirs_log2), qph, qpl, threshold, key_interval, 1, motion_range,
-                  int(bool(storage8)))
+                  int(bool(storage8)), int(dfb_taps))
 
 
 def check(status, where):

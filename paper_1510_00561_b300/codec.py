@@ -45,12 +45,12 @@ class CtPlan:
     inverse: coefficients -> x;  forward_adjoint / inverse_adjoint: the transposes.
     """
 
-    def __init__(self, h, w, levels, dirs_log2, batch=1):
+    def __init__(self, h, w, levels, dirs_log2, batch=1, dfb_taps=4):
         self.h, self.w, self.levels, self.dirs = h, w, levels, list(dirs_log2)
-        self.batch = batch
+        self.batch, self.dfb_taps = batch, dfb_taps
         p = ctypes.c_void_p()
-        _L.check(_L.lib().cvc_ct_plan_create(h, w, levels, _L.ints(dirs_log2), batch, ctypes.byref(p)),
-                 "cvc_ct_plan_create")
+        _L.check(_L.lib().cvc_ct_plan_create_taps(h, w, levels, _L.ints(dirs_log2), batch, dfb_taps,
+                                                  ctypes.byref(p)), "cvc_ct_plan_create_taps")
         self._h = p
         self.total = _L.lib().cvc_ct_plan_coeffs(p)
         self.layout = ct_layout(h, w, levels, dirs_log2)
@@ -123,11 +123,12 @@ class Codec:
     """One CVC video stream on the GPU (encoder and decoder state resident in HBM)."""
 
     def __init__(self, width, height, levels, dirs_log2, qph, qpl=None, threshold=0.0, key_interval=10,
-                 motion_range=0, storage8=False):
-        prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval, motion_range, storage8)
+                 motion_range=0, storage8=False, dfb_taps=4):
+        prm = _L.params(width, height, levels, dirs_log2, qph, qpl, threshold, key_interval, motion_range, storage8,
+                        dfb_taps)
         self.width, self.height, self.levels, self.dirs = width, height, levels, list(dirs_log2)
         self.qph, self.qpl, self.threshold, self.key_interval = qph, prm.qpl, threshold, key_interval
-        self.motion_range, self.storage8 = motion_range, bool(storage8)
+        self.motion_range, self.storage8, self.dfb_taps = motion_range, bool(storage8), dfb_taps
         self._prm = prm
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_create(ctypes.byref(prm), ctypes.byref(p)), "cvc_create")

@@ -29,12 +29,13 @@ bool dalloc(std::vector<void*>& allocs, T** p, size_t n) {
     return true;
 }
 
-std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int batch, long long total) {
+std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int batch, long long total, int taps) {
     std::vector<PlaneRef> planes;
     for (int b = 0; b < batch; b++) {
         PlaneRef r;
         memset(&r, 0, sizeof(r));
         r.low_coef = -1;
+        r.taps = taps;
         r.H = h;
         r.W = w;
         r.L = levels;
@@ -155,9 +156,16 @@ cvc_status cvc_ct_layout(int h, int w, int levels, const int* dirs_log2, cvc_ct_
 
 // ------------------------------------------------------------------ plan
 cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, int batch, cvc_ct_plan** out) {
+    return cvc_ct_plan_create_taps(h, w, levels, dirs_log2, batch, 4, out);
+}
+
+cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log2, int batch, int dfb_taps,
+                                   cvc_ct_plan** out) {
     if (!out) return CVC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!dirs_valid(levels, dirs_log2) || batch < 1) return CVC_ERR_INVALID_ARG;
+    if (!dirs_valid(levels, dirs_log2) || batch < 1 ||
+        (dfb_taps != 0 && dfb_taps != 4 && dfb_taps != 6 && dfb_taps != 8))
+        return CVC_ERR_INVALID_ARG;
     cvc_ct_plan* p = new (std::nothrow) cvc_ct_plan();
     if (!p) return CVC_ERR_NOMEM;
     if (!make_layout(h, w, levels, dirs_log2, &p->lay)) {
@@ -169,7 +177,7 @@ cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, in
     p->L = levels;
     p->batch = batch;
     for (int j = 0; j < levels; j++) p->k[j] = dirs_log2[j];
-    std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, p->lay.total);
+    std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, p->lay.total, dfb_taps);
     std::vector<SoftJob> sj;
     std::vector<int> sf;
     soft_jobs(p->lay, batch, &sj, &sf);
@@ -331,7 +339,7 @@ cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, s
         return (uint32_t)in[at] | ((uint32_t)in[at + 1] << 8) | ((uint32_t)in[at + 2] << 16) |
                ((uint32_t)in[at + 3] << 24);
     };
-    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[4] < 1 || in[4] > 3 || in[5] > 1 ||
+    if (in_len < hdr || memcmp(in, "CVC1", 4) != 0 || in[4] < 1 || in[4] > 3 || in[5] > 5 ||
         in[7] != params->levels || rd32(28) != ncomp)
         return CVC_ERR_CORRUPT;
     if (in[4] == 3) return CVC_ERR_UNSUPPORTED;   // CVC-NTS: one stream, no level can leave it
@@ -824,35 +832,43 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
                               size_t tail_n, size_t tail_sz, void* buf, size_t cap, size_t* used) {
     unsigned long long elems[4] = {elems_in[0], elems_in[1], elems_in[2], elems_in[3]};
     elems[2] = std::max(elems[2], (unsigned long long)e.work_elems);
-    struct Item { int kind; const void* data; size_t n, sz; };
+    struct Item { int kind; const void* data; size_t n, sz; const LaunchDfb* L; };
     std::vector<Item> items;
     const bool analysis = (mode == FWD || mode == INV_ADJ);
     auto push_lp = [&]() {
-        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob)});
+        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob), nullptr});
     };
     auto push_dfb = [&]() {
         for (size_t i = 0; i < e.dfb[mode].size(); i++) {
             const LaunchDfb& L = e.dfb[mode][i];
-            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob);
-            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
+            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : (L.kind == 1 ? sizeof(DfbBJob) : sizeof(DfbGJob));
+            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz, &L});
         }
     };
     if (analysis) { push_lp(); push_dfb(); }
     else { push_dfb(); push_lp(); }
-    size_t need = 24 + 32 + tail_n * tail_sz;
-    for (const Item& it : items) need += 8 + it.n * it.sz;
+    size_t need = 28 + 32 + tail_n * tail_sz;
+    for (const Item& it : items) need += 8 + (it.kind >= 3 ? 16 : 0) + it.n * it.sz;
     *used = need;
     if (!buf || cap < need) return CVC_ERR_CAPACITY;
     uint8_t* o = (uint8_t*)buf;
-    uint32_t hdr[6] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
-                       (uint32_t)sizeof(DfbBJob), (uint32_t)(tail_n ? tail_sz : 0)};
-    memcpy(o, hdr, 24);
-    memcpy(o + 24, elems, 32);
-    size_t pos = 56;
+    uint32_t hdr[7] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
+                       (uint32_t)sizeof(DfbBJob), (uint32_t)(tail_n ? tail_sz : 0), (uint32_t)sizeof(DfbGJob)};
+    memcpy(o, hdr, 28);
+    memcpy(o + 28, elems, 32);
+    size_t pos = 60;
     for (const Item& it : items) {
         uint32_t h2[2] = {(uint32_t)it.kind, (uint32_t)it.n};
         memcpy(o + pos, h2, 8);
         pos += 8;
+        if (it.kind >= 3) {
+            // the launch's stage, target parity (kind 4: 1 = image -> layout), alpha, gamma
+            uint32_t lp[4] = {(uint32_t)it.L->s, (uint32_t)it.L->target, 0, 0};
+            memcpy(&lp[2], &it.L->alpha, 4);
+            memcpy(&lp[3], &it.L->gamma, 4);
+            memcpy(o + pos, lp, 16);
+            pos += 16;
+        }
         memcpy(o + pos, it.data, it.n * it.sz);
         pos += it.n * it.sz;
     }
@@ -877,7 +893,7 @@ cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int lev
         PlaneLayout lay;
         if (!dirs_valid(levels, dirs_log2) || batch < 1 || !make_layout(h, w, levels, dirs_log2, &lay))
             return CVC_ERR_INVALID_ARG;
-        std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, lay.total);
+        std::vector<PlaneRef> planes = plan_planes(h, w, levels, dirs_log2, batch, lay.total, 4);
         if (!engine_build(&plain, planes, false)) return CVC_ERR_INVALID_ARG;
         elems[0] = elems[3] = (unsigned long long)batch * h * w;
         elems[1] = (unsigned long long)batch * lay.total;

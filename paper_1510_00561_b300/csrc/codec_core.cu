@@ -156,6 +156,7 @@ cvc_status plan_scales(Core* c) {
                     r.in.cs = 1;
                     r.coef = poff[p] + Lp.sb[first].off - nlow;
                     r.low_coef = poff[p] + Lp.sb[0].off;
+                    r.taps = P.dfb_taps;
                     sub.push_back(r);
                 }
             }
@@ -187,7 +188,8 @@ bool codec_params_valid(const cvc_params* prm) {
     return prm && prm->width >= 1 && prm->height >= 1 && prm->width <= 65535 && prm->height <= 65535 &&
            dirs_valid(prm->levels, prm->dirs_log2) && prm->qph >= 1 && prm->qph <= 181 && prm->qpl >= 1 &&
            prm->qpl <= 71 && prm->subband_threshold >= 0.0f && prm->key_interval >= 1 && prm->motion_range >= 0 &&
-           prm->motion_range <= CVC_MAX_MOTION_RANGE && (prm->storage8 == 0 || prm->storage8 == 1);
+           prm->motion_range <= CVC_MAX_MOTION_RANGE && (prm->storage8 == 0 || prm->storage8 == 1) &&
+           (prm->dfb_taps == 0 || prm->dfb_taps == 4 || prm->dfb_taps == 6 || prm->dfb_taps == 8);
 }
 
 bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
@@ -204,7 +206,7 @@ bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
     return !(g->Hp > 2 * g->H || g->Wp > 2 * g->W || g->Hcp > 2 * g->Hc || g->Wcp > 2 * g->Wc);
 }
 
-std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, long long plane_off,
+std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, int taps, long long plane_off,
                                    const long long poff[3]) {
     std::vector<PlaneRef> planes(3);
     for (int p = 0; p < 3; p++) {
@@ -220,6 +222,7 @@ std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, 
         planes[p].in.rs = planes[p].W;
         planes[p].in.cs = 1;
         planes[p].coef = poff[p];
+        planes[p].taps = taps;
     }
     return planes;
 }
@@ -276,6 +279,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         for (int j = 0; j < 6; j++) D.hdr.dirs[j] = j < L ? P.dirs_log2[j] : 0;
         D.hdr.qph = P.qph;
         D.hdr.qpl = P.qpl;
+        D.hdr.flags = P.storage8 | (((P.dfb_taps ? P.dfb_taps : 4) / 2 - 2) << 1);
         D.plane_off = plane_off;
         D.nplane = (long long)g.Hp * g.Wp + 2LL * g.Hcp * g.Wcp;
         D.coef_off = coef_off;
@@ -358,7 +362,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             }
         }
         D.nrows = (int)c->h_row_off.size() - D.row0;
-        std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, plane_off, poff);
+        std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, P.dfb_taps, plane_off, poff);
         planes.insert(planes.end(), sp.begin(), sp.end());
         plane_off += D.nplane;
         coef_off += D.ncoef;

@@ -111,7 +111,7 @@ struct Core {
 bool dirs_valid(int levels, const int* dirs);
 bool codec_params_valid(const cvc_params* prm);
 bool codec_geometry(const cvc_params* prm, ColourGeom* g);
-std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, long long plane_off,
+std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, int taps, long long plane_off,
                                    const long long poff[3]);
 
 // host tables and sizes, no device call; CVC_OK, INVALID_ARG or UNSUPPORTED

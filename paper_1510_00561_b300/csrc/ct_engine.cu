@@ -25,6 +25,10 @@
 //   c: b1 = (2^(s-2), -2i), b2 = (2^(s-2), -2i-2);  r: b1 = (-2i, 2^(s-2)), b2 = (-2i-2, 2^(s-2)).
 // The even child takes the lower half of the slopes.
 //
+// Longer prototypes (6 or 8 taps, PlaneRef.taps) skip the tile kernels: every
+// pass of every stage is one launch of k_dfb_g over whole detail images, and
+// k_dfb_leaf moves between the images and the layout.
+//
 // Data flow of one level: the LP writes the detail image D; stages 1 and 2
 // run fused in k_dfb_a, whose stage-2 channels are D's four polyphase
 // classes; from stage 3 on every channel is a compact array, and a stage is a
@@ -217,6 +221,9 @@ int count_a(const DfbAJob& J) {
 int count_b(const DfbBJob& J) {
     return ((J.R2 + DFBB_ROWS - 1) / DFBB_ROWS) * J.tiles_x;
 }
+int count_g(const DfbGJob& J) {
+    return (int)(((long long)J.H * J.W + 255) / 256);
+}
 
 }  // namespace
 
@@ -240,6 +247,8 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         std::vector<std::vector<LpJob>> lpj(Lmax + 1);
         std::vector<DfbAJob> aj;
         std::vector<std::vector<DfbBJob>> bj(std::max(kmax, 2) + 1);
+        std::vector<DfbGJob> gj;       // levels of planes with a longer prototype
+        int kgmax = 0;
         for (size_t p = 0; p < e->planes.size(); p++) {
             const PlaneRef& P = e->planes[p];
             const PlaneLayout& Ly = lays[p];
@@ -280,7 +289,22 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                     J.out = spatial_prev;
                 }
                 lpj[j].push_back(J);
-                dfb_jobs(hj, wj, kj, doff[j], qoff[j], slots, aj, bj);
+                if (P.taps == 6 || P.taps == 8) {
+                    if (kj > 0) {
+                        DfbGJob G;
+                        memset(&G, 0, sizeof(G));
+                        G.D = mk(B_WORK, doff[j], wj, 1);
+                        G.slot0 = slots[0];
+                        G.H = hj;
+                        G.W = wj;
+                        G.k = kj;
+                        G.ntaps = P.taps;
+                        gj.push_back(G);
+                        kgmax = std::max(kgmax, kj);
+                    }
+                } else {
+                    dfb_jobs(hj, wj, kj, doff[j], qoff[j], slots, aj, bj);
+                }
             }
         }
         e->lp[m].clear();
@@ -317,13 +341,44 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                                      reinterpret_cast<uint8_t*>(v.data() + v.size()));
             return true;
         };
+        // plain path: a launch per lifting pass of stage s over the levels with k >= s,
+        // and one copy between the detail images and the layout
+        const PassParams pp = pass_params((Mode)m);
+        auto add_g = [&](int kind, int s, int target, float alpha, float gamma) {
+            std::vector<DfbGJob> v;
+            for (const DfbGJob& G : gj)
+                if (kind == 3 || G.k >= s) v.push_back(G);
+            if (v.empty()) return true;
+            LaunchDfb L{};
+            L.kind = kind;
+            L.s = s;
+            L.target = target;
+            L.alpha = alpha;
+            L.gamma = gamma;
+            if (!upload<DfbGJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_g)) return false;
+            L.njobs = (int)v.size();
+            e->dfb[m].push_back(L);
+            e->h_dfb[m].emplace_back(reinterpret_cast<uint8_t*>(v.data()),
+                                     reinterpret_cast<uint8_t*>(v.data() + v.size()));
+            return true;
+        };
+        auto add_stage = [&](int s) {
+            const int t1 = pp.first_odd ? 1 : 0;
+            return add_g(2, s, t1, pp.a1, pp.g1) && add_g(2, s, 1 - t1, pp.a2, pp.g2);
+        };
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)
                 if (!add_lp(lpj[j])) return false;
             if (!aj.empty() && !add_a(aj)) return false;
             for (int s = 3; s <= kmax; s++)
                 if (!bj[s].empty() && !add_b(bj[s])) return false;
+            for (int s = 1; s <= kgmax; s++)
+                if (!add_stage(s)) return false;
+            if (!add_g(3, 0, 1, 0.f, 0.f)) return false;
         } else {
+            if (!add_g(3, 0, 0, 0.f, 0.f)) return false;
+            for (int s = kgmax; s >= 1; s--)
+                if (!add_stage(s)) return false;
             for (int s = kmax; s >= 3; s--)
                 if (!bj[s].empty() && !add_b(bj[s])) return false;
             if (!aj.empty() && !add_a(aj)) return false;

@@ -69,6 +69,18 @@ struct DfbBJob {
     int tiles_x, first_block;
 };
 
+// Longer PKVA prototypes (6 or 8 taps) take a plain path: one lifting pass
+// of stage s over a whole detail image in place (k_dfb_g, a thread per
+// sample, its channel and lattice basis found from its position), then a
+// copy between the image and the subband layout (k_dfb_leaf).
+struct DfbGJob {
+    View D;            // H x W detail image (rs = pitch, cs = 1)
+    long long slot0;   // first subband of the level in B_COEF (2^k subbands of H*W/2^k)
+    int H, W, k;
+    int ntaps;         // 6 or 8
+    int first_block, pad;
+};
+
 constexpr int DFBA_TILE = 64, DFBA_HALO = 12;
 constexpr int DFBB_ROWS = 16, DFBB_COLS = 116;
 
@@ -106,6 +118,7 @@ struct PlaneRef {
     long long work;   // workspace offset in B_WORK
     long long low_coef;   // >= 0: the lowpass lives here instead of at coef (a sub-pyramid of a
                           // larger layout keeps its lowpass apart from its subbands)
+    int taps;             // DFB prototype length: 0 or 4 (tile kernels), 6 or 8 (DfbGJob path)
 };
 
 struct LaunchLp {
@@ -114,10 +127,12 @@ struct LaunchLp {
     int* d_block_job;
 };
 struct LaunchDfb {
-    int kind;  // 0: DfbAJob, 1: DfbBJob
+    int kind;  // 0: DfbAJob, 1: DfbBJob, 2: DfbGJob pass, 3: DfbGJob layout copy
     int njobs, nblocks;
     void* d_jobs;
     int* d_block_job;
+    int s, target;        // kind 2: stage and target parity; kind 3: target 1 = image -> layout
+    float alpha, gamma;   // kind 2
 };
 
 enum Mode { FWD = 0, INV = 1, FWD_ADJ = 2, INV_ADJ = 3 };

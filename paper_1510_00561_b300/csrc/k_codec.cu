@@ -617,7 +617,7 @@ __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __r
     if (threadIdx.x == 0) {
         const StreamHeader& h = D.hdr;
         o[0] = 'C'; o[1] = 'V'; o[2] = 'C'; o[3] = '1';
-        o[4] = 1; o[5] = (uint8_t)D.qp.st8;
+        o[4] = 1; o[5] = (uint8_t)h.flags;
         o[6] = (uint8_t)(C.enc_key ? 0 : (mc ? 2 : 1));
         o[7] = (uint8_t)h.levels;
         for (int i = 0; i < 4; i++) o[8 + i] = (uint8_t)(C.enc_index >> (8 * i));
@@ -678,8 +678,8 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
         if (in_len < D.hdr_bytes) bad = EF_CORRUPT;
         else {
             const StreamHeader& e = D.hdr;
-            if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] > 1) bad = EF_CORRUPT;
-            else if (in[5] != D.qp.st8) bad = EF_MISMATCH;              // the other storage
+            if (in[0] != 'C' || in[1] != 'V' || in[2] != 'C' || in[3] != '1' || in[4] != 1 || in[5] > 5) bad = EF_CORRUPT;
+            else if (in[5] != e.flags) bad = EF_MISMATCH;               // another storage or prototype
             int type = in[6];
             if (type > 2) bad = EF_CORRUPT;
             if (type == 2 && D.mv_range == 0) bad |= EF_MISMATCH;   // vectors for a decoder without motion

@@ -25,6 +25,7 @@ struct StreamHeader {
     int height, width;
     int dirs[6];
     int qph, qpl;
+    int flags;          // header byte 5: bit 0 8-bit storage, bits 1-2 DFB prototype (taps / 2 - 2)
 };
 
 // per stream, fixed at creation

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_dfl_plan(DflArgs a) {
     if (threadIdx.x == 0) {
         S.err = 0;
         S.total = 0;
-        s_bad = F.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] > 1 ||
+        s_bad = F.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || in[4] != 1 || in[5] > 5 ||
                 rd32(in + 28) != (uint32_t)a.ncomp;
         if (s_bad) S.err = DFL_CORRUPT;
     }
@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(256) k_ifl_plan(DflArgs a) {
         S.err = 0;
         S.total = 0;
         s_bad = F.in_len < (long long)a.hdr_bytes || rd32(in) != 0x31435643u || (in[4] != 2 && in[4] != 3) ||
-                in[5] > 1 || rd32(in + 28) != (uint32_t)a.ncomp;
+                in[5] > 5 || rd32(in + 28) != (uint32_t)a.ncomp;
         s_one = !s_bad && in[4] == 3;
         if (!s_bad && F.in_len < a.hdr_bytes + 4LL * (s_one ? 1 : a.ncomp)) s_bad = 1;
         if (s_bad) S.err = DFL_CORRUPT;

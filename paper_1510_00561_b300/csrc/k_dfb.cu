@@ -19,6 +19,9 @@
 //   per target.  Both passes of the stage run in one launch on a 16 x 128
 //   tile with a 3-row / 6-column halo.
 //
+// k_dfb_g / k_dfb_leaf: the plain path of the longer prototypes (6 or 8
+//   taps), one lifting pass over a whole detail image per launch.
+//
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
 // by the Laplacian-pyramid synthesis, which is compensated (k_lp.cu).
@@ -463,6 +466,122 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
 }
 
 // ============================================================ launches
+// ============================================================ k_dfb_g
+// Longer prototypes: the fan taps sign(a) |beta[a]| of the 6- and 8-tap
+// Lagrange half-band interpolators (3, -25, 150, 150, -25, 3)/256 and
+// (-5, 49, -245, 1225, 1225, -245, 49, -5)/2048 at odd a (dyadic: exact).
+__constant__ float c_fan6[6] = {-3.f / 256, -25.f / 256, -150.f / 256, 150.f / 256, 25.f / 256, 3.f / 256};
+__constant__ float c_fan8[8] = {-5.f / 2048, -49.f / 2048, -245.f / 2048, -1225.f / 2048,
+                                1225.f / 2048, 245.f / 2048, 49.f / 2048, 5.f / 2048};
+
+// a channel of the tree: origin, family (0: c, 1: r) and slope index
+struct GChan {
+    int o_r, o_c, T, i;
+};
+
+__device__ __forceinline__ void g_basis(int s, const GChan& ch, int b[4]) {
+    if (s == 1) {
+        b[0] = 1; b[1] = 0; b[2] = 0; b[3] = 1;
+    } else if (s == 2) {
+        b[0] = 1; b[1] = 1;
+        b[2] = ch.T == 0 ? 1 : -1;
+        b[3] = ch.T == 0 ? -1 : 1;
+    } else {
+        const int q = 1 << (s - 2), i = ch.i;
+        if (ch.T == 0) { b[0] = q; b[1] = -2 * i; b[2] = q; b[3] = -2 * i - 2; }
+        else { b[0] = -2 * i; b[1] = q; b[2] = -2 * i - 2; b[3] = q; }
+    }
+}
+
+// Follow sample (r, c) down the tree through stages 1..s: on return ch is its
+// stage-s channel, b that channel's basis, and the result its parity there.
+// With descend, the walk also steps into the stage-s child (the leaf for s = k)
+// and *cid is the child's index in tree order.
+__device__ __forceinline__ int g_walk(int r, int c, int s, bool descend, GChan& ch, int b[4], int* cid) {
+    ch = GChan{0, 0, 0, 0};
+    int id = 0, par = 0;
+    for (int st = 1; st <= s; st++) {
+        g_basis(st, ch, b);
+        const int det = b[0] * b[3] - b[1] * b[2];
+        const int dr = r - ch.o_r, dc = c - ch.o_c;
+        // lattice coordinates of the sample: exact divisions (it lies on the channel's lattice)
+        const int p1 = (b[3] * dr - b[2] * dc) / det, p2 = (b[0] * dc - b[1] * dr) / det;
+        par = (p1 + p2) & 1;
+        if (st == s && !descend) break;
+        id = 2 * id + par;
+        if (par) {
+            ch.o_r += b[0];
+            ch.o_c += b[1];
+        }
+        if (st == 1) { ch.T = par; ch.i = 0; }
+        else if (st == 2) ch.i = par ? 0 : -1;
+        else ch.i = 2 * ch.i + par;
+    }
+    if (cid) *cid = id;
+    return par;
+}
+
+// one lifting pass of stage s: every sample of parity `target` becomes
+// alpha * itself + gamma * sum_{a,b} bt[a] bt[b] x[p + delta(a,b)], the sum
+// taken separably (inner sums over b); in place, since targets read only the
+// other parity of their own channel
+__global__ void __launch_bounds__(256) k_dfb_g(const DfbGJob* __restrict__ jobs, const int* __restrict__ block_job,
+                                               int s, int target, float alpha, float gamma, Bases bases) {
+    const DfbGJob& J = jobs[block_job[blockIdx.x]];
+    const long long pix = (long long)(blockIdx.x - J.first_block) * 256 + threadIdx.x;
+    if (s > J.k || pix >= (long long)J.H * J.W) return;
+    const int r = (int)(pix / J.W), c = (int)(pix % J.W);
+    GChan ch;
+    int b[4];
+    if (g_walk(r, c, s, false, ch, b, nullptr) != target) return;
+    float* D = bases.p[J.D.b] + J.D.off;
+    const int rs = J.D.rs, n = J.ntaps;
+    const float* bt = n == 6 ? c_fan6 : c_fan8;
+    float acc = 0.f;
+    for (int ia = 0; ia < n; ia++) {
+        const int a = 2 * ia - (n - 1);
+        float inner = 0.f;
+        for (int ib = 0; ib < n; ib++) {
+            const int bb = 2 * ib - (n - 1);
+            const int d1 = (a + bb) / 2, d2 = (a - bb) / 2;
+            const int rr = wrapd(r + d1 * b[0] + d2 * b[2], J.H), cc = wrapd(c + d1 * b[1] + d2 * b[3], J.W);
+            inner = fmaf(bt[ib], D[(long long)rr * rs + cc], inner);
+        }
+        acc = fmaf(bt[ia], inner, acc);
+    }
+    float* x = D + (long long)r * rs + c;
+    *x = fmaf(alpha, *x, gamma * acc);
+}
+
+// copy between the detail image and the level's subbands (tree order, each
+// on its rectangular lattice: family c 2^(k-1) x 2, family r 2 x 2^(k-1); k = 1
+// the two row-compacted quincunx halves); to_layout: image -> subbands
+__global__ void __launch_bounds__(256) k_dfb_leaf(const DfbGJob* __restrict__ jobs,
+                                                  const int* __restrict__ block_job, int to_layout, Bases bases) {
+    const DfbGJob& J = jobs[block_job[blockIdx.x]];
+    const long long pix = (long long)(blockIdx.x - J.first_block) * 256 + threadIdx.x;
+    if (pix >= (long long)J.H * J.W) return;
+    const int r = (int)(pix / J.W), c = (int)(pix % J.W), k = J.k;
+    GChan ch;
+    int b[4], cid;
+    g_walk(r, c, k, true, ch, b, &cid);
+    int a, bc, w;
+    if (k == 1) {
+        a = r;
+        bc = c >> 1;
+        w = J.W / 2;
+    } else {
+        const int R = ch.T == 0 ? (1 << (k - 1)) : 2, C = ch.T == 0 ? 2 : (1 << (k - 1));
+        a = (r - wrapd(ch.o_r, R)) / R;
+        bc = (c - wrapd(ch.o_c, C)) / C;
+        w = J.W / C;
+    }
+    float* coef = bases.p[B_COEF] + J.slot0 + (long long)cid * (((long long)J.H * J.W) >> k) + (long long)a * w + bc;
+    float* x = bases.p[J.D.b] + J.D.off + (long long)r * J.D.rs + c;
+    if (to_layout) *coef = *x;
+    else *x = *coef;
+}
+
 PassParams pass_params(Mode m) {
     switch (m) {
         case FWD: return {1, 0.5f, -0.5f, 1.f, 1.f};       // predict odd, update even
@@ -480,10 +599,16 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
         const DfbAJob* j = static_cast<const DfbAJob*>(L.d_jobs);
         if (syn) k_dfb_a<true><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
         else k_dfb_a<false><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
-    } else {
+    } else if (L.kind == 1) {
         const DfbBJob* j = static_cast<const DfbBJob*>(L.d_jobs);
         if (syn) k_dfb_b<true><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
         else k_dfb_b<false><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
+    } else if (L.kind == 2) {
+        k_dfb_g<<<L.nblocks, 256, 0, st>>>(static_cast<const DfbGJob*>(L.d_jobs), L.d_block_job, L.s, L.target,
+                                           L.alpha, L.gamma, bases);
+    } else {
+        k_dfb_leaf<<<L.nblocks, 256, 0, st>>>(static_cast<const DfbGJob*>(L.d_jobs), L.d_block_job, L.target,
+                                              bases);
     }
     return cudaGetLastError();
 }

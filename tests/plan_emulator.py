@@ -16,6 +16,12 @@ semantics of the two kernels:
   DFB row-split job:         one stage s >= 3 of a channel: even / odd rows
                              E, O of its array, stencil row offset (a +- 1)/2,
                              column offset -i*a + (b-a)/2 (periodic)
+  plain DFB pass (longer     one lifting pass of stage s over a whole detail
+  prototypes):               image: the samples of the target parity in their
+                             stage-s channel, the n x n stencil of the n-tap
+                             fan taps (from the Lagrange formula) in the
+                             channel's lattice basis (periodic)
+  plain DFB copy:            the detail image to / from the level's subbands
 
 so that a test can compare the planned computation with the oracle before
 any kernel runs on a GPU.  Each pass sets target = alpha*target + gamma*sum.
@@ -34,6 +40,8 @@ AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), 
                  ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
 BJOB = np.dtype([("pe", VIEW), ("po", VIEW), ("c0", VIEW), ("c1", VIEW), ("R2", "<i4"), ("C", "<i4"),
                  ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
+GJOB = np.dtype([("D", VIEW), ("slot0", "<i8"), ("H", "<i4"), ("W", "<i4"), ("k", "<i4"), ("ntaps", "<i4"),
+                 ("first_block", "<i4"), ("pad", "<i4")])
 BT = np.array([-1.0, -9.0, 9.0, 1.0]) / 16
 A4 = [-3, -1, 1, 3]
 # (first target is the odd coset, alpha1, gamma1, alpha2, gamma2) per mode
@@ -75,20 +83,106 @@ def scale_tables(params, n, scale):
 
 
 def _parse(raw):
-    magic, nl, lpb, ab, bb, tail_sz = np.frombuffer(raw[:24], "<u4")
+    magic, nl, lpb, ab, bb, tail_sz, gb = np.frombuffer(raw[:28], "<u4")
     assert tail_sz in (0, SCALEDESC.itemsize)
     assert magic == 0x43564350 and lpb == LPJOB.itemsize and ab == AJOB.itemsize and bb == BJOB.itemsize
-    elems = np.frombuffer(raw[24:56], "<u8").astype(np.int64)
-    pos = 56
+    assert gb == GJOB.itemsize
+    elems = np.frombuffer(raw[28:60], "<u8").astype(np.int64)
+    pos = 60
     launches = []
     for _ in range(nl):
         kind, nj = np.frombuffer(raw[pos:pos + 8], "<u4")
         pos += 8
-        dt = (LPJOB, AJOB, BJOB)[kind]
+        extra = None
+        if kind >= 3:
+            st, tgt = np.frombuffer(raw[pos:pos + 8], "<u4")
+            al, ga = np.frombuffer(raw[pos + 8:pos + 16], "<f4")
+            extra = (int(st), int(tgt), float(al), float(ga))
+            pos += 16
+        dt = (LPJOB, AJOB, BJOB, GJOB, GJOB)[kind]
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
-        launches.append((int(kind), jobs))
+        launches.append((int(kind), jobs, extra))
     return elems, launches, raw[pos:]
+
+
+def _fan_taps(n):
+    """fan taps of the n-tap Lagrange half-band prototype: weight of the sample at odd a
+    when interpolating at 0, times (-1)^((a - 1) / 2)"""
+    pts = list(range(-(n - 1), n, 2))
+    out = []
+    for a in pts:
+        w = np.prod([b / (b - a) for b in pts if b != a])
+        out.append((a, (-1.0) ** (((a - 1) // 2) % 2) * w))
+    return out
+
+
+def _g_basis(s, T, i):
+    if s == 1:
+        return np.ones_like(i), np.zeros_like(i), np.zeros_like(i), np.ones_like(i)
+    if s == 2:
+        one = np.ones_like(i)
+        return one, one, np.where(T == 0, 1, -1), np.where(T == 0, -1, 1)
+    q = 2 ** (s - 2)
+    c = T == 0
+    return (np.where(c, q, -2 * i), np.where(c, -2 * i, q), np.where(c, q, -2 * i - 2),
+            np.where(c, -2 * i - 2, q))
+
+
+def _g_walk(H, W, s, descend):
+    """per sample of an H x W image: stage-s parity, basis, and (descend) the child's
+    origin, family and tree index after stage s"""
+    r, c = np.mgrid[0:H, 0:W]
+    o_r, o_c = np.zeros_like(r), np.zeros_like(r)
+    T, i, cid = np.zeros_like(r), np.zeros_like(r), np.zeros_like(r)
+    for st in range(1, s + 1):
+        b0, b1, b2, b3 = _g_basis(st, T, i)
+        det = b0 * b3 - b1 * b2
+        dr, dc = r - o_r, c - o_c
+        n1, n2 = b3 * dr - b2 * dc, b0 * dc - b1 * dr
+        assert np.all(n1 % det == 0) and np.all(n2 % det == 0), "sample off its channel's lattice"
+        par = (n1 // det + n2 // det) & 1
+        if st == s and not descend:
+            return par, (b0, b1, b2, b3)
+        cid = 2 * cid + par
+        o_r, o_c = o_r + par * b0, o_c + par * b1
+        if st == 1:
+            T, i = par, np.zeros_like(par)
+        elif st == 2:
+            i = np.where(par == 1, 0, -1)
+        else:
+            i = 2 * i + par
+    return cid, o_r, o_c, T
+
+
+def _g_pass(img, s, target, alpha, gamma, n):
+    H, W = img.shape
+    par, (b0, b1, b2, b3) = _g_walk(H, W, s, False)
+    r, c = np.mgrid[0:H, 0:W]
+    taps = _fan_taps(n)
+    acc = np.zeros_like(img)
+    for a, wa in taps:
+        for b, wb in taps:
+            d1, d2 = (a + b) // 2, (a - b) // 2
+            acc += wa * wb * img[(r + d1 * b0 + d2 * b2) % H, (c + d1 * b1 + d2 * b3) % W]
+    m = par == target
+    img[m] = alpha * img[m] + gamma * acc[m]
+
+
+def _g_leaf_index(J):
+    """coefficient offset (from slot0) of every sample of the job's detail image"""
+    H, W, k = int(J["H"]), int(J["W"]), int(J["k"])
+    cid, o_r, o_c, T = _g_walk(H, W, k, True)
+    r, c = np.mgrid[0:H, 0:W]
+    if k == 1:
+        a, b, w = r, c >> 1, W // 2
+    else:
+        R = np.where(T == 0, 2 ** (k - 1), 2)
+        C = np.where(T == 0, 2, 2 ** (k - 1))
+        a, b, w = (r - o_r % R) // R, (c - o_c % C) // C, W // C
+    idx = cid * ((H * W) >> k) + a * w + b
+    assert np.array_equal(np.sort(idx.ravel()), np.arange(H * W)), "the copy is not a bijection"
+    return idx
 
 
 def _stage_a_pass(img, stage, odd, alpha, gamma):
@@ -148,8 +242,17 @@ def _up(v, f):
     return sum(f[a + R] * np.roll(z, a, axis=0) for a in range(-R, R + 1))
 
 
-def _views_of(kind, J, synth):
+def _views_of(kind, J, synth, extra=None):
     """(reads, writes): lists of (name, view, rows, cols) a job touches."""
+    if kind == 3:
+        D = [("D", J["D"], int(J["H"]), int(J["W"]))]
+        return D, D
+    if kind == 4:
+        H, W = int(J["H"]), int(J["W"])
+        lay = np.zeros(1, VIEW)[0]
+        lay["off"], lay["b"], lay["rs"], lay["cs"] = int(J["slot0"]), 1, W, 1
+        D, L = [("D", J["D"], H, W)], [("layout", lay, H, W)]     # the level's 2^k subbands, H*W elements
+        return (D, L) if extra[1] == 1 else (L, D)
     if kind == 0:
         H, W = int(J["H"]), int(J["W"])
         if not synth:
@@ -172,10 +275,10 @@ def run(mode, elems, launches, bufs):
     fa, fs = (h, g) if mode in (0, 1) else (g, h)
     synth = mode in (1, 2)
     fo, a1, g1, a2, g2 = PASSES[mode]
-    for kind, jobs in launches:
+    for kind, jobs, extra in launches:
         results, wjob, rjob = [], [], []
         for ji, J in enumerate(jobs):
-            reads, writes = _views_of(kind, J, synth)
+            reads, writes = _views_of(kind, J, synth, extra)
             rd = {}
             for name, v, rr, cc in reads:
                 b, idx = _index(v, rr, cc)
@@ -183,7 +286,19 @@ def run(mode, elems, launches, bufs):
                 rd[name] = bufs[b][idx]
                 rjob.append((ji, (b, idx)))
             out = {}
-            if kind == 0:
+            if kind == 3:
+                img = rd["D"].copy()
+                _g_pass(img, extra[0], extra[1], extra[2], extra[3], int(J["ntaps"]))
+                out["D"] = img
+            elif kind == 4:
+                idx = _g_leaf_index(J)
+                if extra[1] == 1:
+                    lay = np.zeros(rd["D"].size)
+                    lay[idx.ravel()] = rd["D"].ravel()
+                    out["layout"] = lay.reshape(rd["D"].shape)
+                else:
+                    out["D"] = rd["layout"].ravel()[idx]
+            elif kind == 0:
                 X = rd["main"]
                 if not synth:
                     out["cout"] = _down(X, fa)
@@ -228,6 +343,7 @@ def run(mode, elems, launches, bufs):
                 results.append((b, idx, out[name]))
                 wjob.append((ji, b, idx))
         # no job writes an element that another job of the same launch reads or writes
+        # (a plain DFB pass reads and writes its own image: in place, by parity)
         for b in set(x[1] for x in wjob):
             w_idx = [(ji, ix.ravel()) for ji, wb, ix in wjob if wb == b]
             allw = np.concatenate([ix for _, ix in w_idx])
@@ -250,9 +366,9 @@ def run(mode, elems, launches, bufs):
 def check_only(elems, launches, mode):
     """Bounds of every job of every launch, without executing (for full-size plans)."""
     synth = mode in (1, 2)
-    for kind, jobs in launches:
+    for kind, jobs, extra in launches:
         for J in jobs:
-            reads, writes = _views_of(kind, J, synth)
+            reads, writes = _views_of(kind, J, synth, extra)
             for name, v, rr, cc in reads + writes:
                 b, idx = _index(v, rr, cc)
                 _check(b, idx, elems, name)
