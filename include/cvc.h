@@ -553,10 +553,11 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  *   u32 bytes of a plain DFB job (longer prototypes),
  *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
  *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage
- *   >= 3, 3 = plain DFB lifting pass, 4 = plain DFB copy between the detail
- *   images and the layout), u32 njobs, for kinds 3 and 4 four u32 (stage,
- *   target parity or 1 = image -> layout, alpha and gamma as f32), and njobs
- *   job records (the library's job structures).
+ *   >= 3, 3 = plain DFB diagonal sums of a lifting pass, 4 = plain DFB copy
+ *   between the detail images and the layout, 5 = plain DFB pass targets),
+ *   u32 njobs, for kinds 3-5 four u32 (stage, target parity or 1 = image ->
+ *   layout, alpha and gamma as f32), and njobs job records (the library's
+ *   job structures).
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */

@@ -862,7 +862,7 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
         memcpy(o + pos, h2, 8);
         pos += 8;
         if (it.kind >= 3) {
-            // the launch's stage, target parity (kind 4: 1 = image -> layout), alpha, gamma
+            // the launch's stage, target parity (kind 4: 1 = image -> layout), alpha, gamma (kind 5)
             uint32_t lp[4] = {(uint32_t)it.L->s, (uint32_t)it.L->target, 0, 0};
             memcpy(&lp[2], &it.L->alpha, 4);
             memcpy(&lp[3], &it.L->gamma, 4);

@@ -26,8 +26,9 @@
 // The even child takes the lower half of the slopes.
 //
 // Longer prototypes (6 or 8 taps, PlaneRef.taps) skip the tile kernels: every
-// pass of every stage is one launch of k_dfb_g over whole detail images, and
-// k_dfb_leaf moves between the images and the layout.
+// pass of every stage is two launches over whole detail images (k_dfb_gsum
+// into the level's spare buffer Q_j, then k_dfb_g), and k_dfb_leaf moves
+// between the images and the layout.
 //
 // Data flow of one level: the LP writes the detail image D; stages 1 and 2
 // run fused in k_dfb_a, whose stage-2 channels are D's four polyphase
@@ -294,6 +295,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                         DfbGJob G;
                         memset(&G, 0, sizeof(G));
                         G.D = mk(B_WORK, doff[j], wj, 1);
+                        G.T = mk(B_WORK, qoff[j], wj, 1);
                         G.slot0 = slots[0];
                         G.H = hj;
                         G.W = wj;
@@ -364,7 +366,8 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         };
         auto add_stage = [&](int s) {
             const int t1 = pp.first_odd ? 1 : 0;
-            return add_g(2, s, t1, pp.a1, pp.g1) && add_g(2, s, 1 - t1, pp.a2, pp.g2);
+            return add_g(2, s, t1, 0.f, 0.f) && add_g(4, s, t1, pp.a1, pp.g1) && add_g(2, s, 1 - t1, 0.f, 0.f) &&
+                   add_g(4, s, 1 - t1, pp.a2, pp.g2);
         };
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)

@@ -69,12 +69,14 @@ struct DfbBJob {
     int tiles_x, first_block;
 };
 
-// Longer PKVA prototypes (6 or 8 taps) take a plain path: one lifting pass
-// of stage s over a whole detail image in place (k_dfb_g, a thread per
-// sample, its channel and lattice basis found from its position), then a
-// copy between the image and the subband layout (k_dfb_leaf).
+// Longer PKVA prototypes (6 or 8 taps) take a plain path: each lifting pass
+// of stage s over a whole detail image in place, in two launches (diagonal
+// sums into T, then the targets; a thread per sample, its channel and lattice
+// basis found from its position), then a copy between the image and the
+// subband layout (k_dfb_leaf).
 struct DfbGJob {
     View D;            // H x W detail image (rs = pitch, cs = 1)
+    View T;            // H x W spare buffer of the level: the diagonal sums
     long long slot0;   // first subband of the level in B_COEF (2^k subbands of H*W/2^k)
     int H, W, k;
     int ntaps;         // 6 or 8
@@ -127,12 +129,12 @@ struct LaunchLp {
     int* d_block_job;
 };
 struct LaunchDfb {
-    int kind;  // 0: DfbAJob, 1: DfbBJob, 2: DfbGJob pass, 3: DfbGJob layout copy
+    int kind;  // 0: DfbAJob, 1: DfbBJob; DfbGJob: 2 diagonal sums, 3 layout copy, 4 pass targets
     int njobs, nblocks;
     void* d_jobs;
     int* d_block_job;
-    int s, target;        // kind 2: stage and target parity; kind 3: target 1 = image -> layout
-    float alpha, gamma;   // kind 2
+    int s, target;        // kinds 2, 4: stage and target parity; kind 3: target 1 = image -> layout
+    float alpha, gamma;   // kind 4
 };
 
 enum Mode { FWD = 0, INV = 1, FWD_ADJ = 2, INV_ADJ = 3 };

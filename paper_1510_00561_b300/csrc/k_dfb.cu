@@ -19,8 +19,9 @@
 //   per target.  Both passes of the stage run in one launch on a 16 x 128
 //   tile with a 3-row / 6-column halo.
 //
-// k_dfb_g / k_dfb_leaf: the plain path of the longer prototypes (6 or 8
-//   taps), one lifting pass over a whole detail image per launch.
+// k_dfb_gsum / k_dfb_g / k_dfb_leaf: the plain path of the longer
+//   prototypes (6 or 8 taps), each lifting pass over whole detail images in
+//   two launches (diagonal sums, then the targets).
 //
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
@@ -496,17 +497,16 @@ __device__ __forceinline__ void g_basis(int s, const GChan& ch, int b[4]) {
 // Follow sample (r, c) down the tree through stages 1..s: on return ch is its
 // stage-s channel, b that channel's basis, and the result its parity there.
 // With descend, the walk also steps into the stage-s child (the leaf for s = k)
-// and *cid is the child's index in tree order.
+// and *cid is the child's index in tree order.  The lattice coordinates are
+// (adj(B) (r - o)) / det B with |det B| = 2^(st-1); only their parity is
+// needed, so the exact divisions are shifts and the sign of det is dropped.
 __device__ __forceinline__ int g_walk(int r, int c, int s, bool descend, GChan& ch, int b[4], int* cid) {
     ch = GChan{0, 0, 0, 0};
     int id = 0, par = 0;
     for (int st = 1; st <= s; st++) {
         g_basis(st, ch, b);
-        const int det = b[0] * b[3] - b[1] * b[2];
         const int dr = r - ch.o_r, dc = c - ch.o_c;
-        // lattice coordinates of the sample: exact divisions (it lies on the channel's lattice)
-        const int p1 = (b[3] * dr - b[2] * dc) / det, p2 = (b[0] * dc - b[1] * dr) / det;
-        par = (p1 + p2) & 1;
+        par = (((b[3] * dr - b[2] * dc) >> (st - 1)) + ((b[0] * dc - b[1] * dr) >> (st - 1))) & 1;
         if (st == s && !descend) break;
         id = 2 * id + par;
         if (par) {
@@ -521,10 +521,37 @@ __device__ __forceinline__ int g_walk(int r, int c, int s, bool descend, GChan& 
     return par;
 }
 
-// one lifting pass of stage s: every sample of parity `target` becomes
-// alpha * itself + gamma * sum_{a,b} bt[a] bt[b] x[p + delta(a,b)], the sum
-// taken separably (inner sums over b); in place, since targets read only the
-// other parity of their own channel
+// A lifting pass of stage s makes every sample t of parity `target`
+//   alpha * x[t] + gamma * sum_{a,b} bt[a] bt[b] x[t + delta(a,b)],
+// delta(a,b) = ((a+b)/2) B1 + ((a-b)/2) B2 (B1, B2 the channel's basis).  With
+// u = (b+1)/2 the offset is ((a-1)/2) B1 + ((a+1)/2) B2 + u (B1 - B2), so the
+// sum splits into diagonal sums at the other parity,
+//   S[p] = sum_u bt[2u-1] x[p + u (B1 - B2)]                 (k_dfb_gsum)
+// and a sum of n of them per target,
+//   acc(t) = sum_a bt[a] S[t + ((a-1)/2) B1 + ((a+1)/2) B2]   (k_dfb_g):
+// 2n loads per target instead of n^2.  S lives in the level's spare buffer.
+__global__ void __launch_bounds__(256) k_dfb_gsum(const DfbGJob* __restrict__ jobs,
+                                                  const int* __restrict__ block_job, int s, int target,
+                                                  Bases bases) {
+    const DfbGJob& J = jobs[block_job[blockIdx.x]];
+    const long long pix = (long long)(blockIdx.x - J.first_block) * 256 + threadIdx.x;
+    if (s > J.k || pix >= (long long)J.H * J.W) return;
+    const int r = (int)(pix / J.W), c = (int)(pix % J.W);
+    GChan ch;
+    int b[4];
+    if (g_walk(r, c, s, false, ch, b, nullptr) == target) return;     // sums sit at the other parity
+    const float* D = bases.p[J.D.b] + J.D.off;
+    const int n = J.ntaps, h = n / 2;
+    const float* bt = n == 6 ? c_fan6 : c_fan8;
+    const int er = b[0] - b[2], ec = b[1] - b[3];                      // B1 - B2
+    float acc = 0.f;
+    for (int u = 1 - h; u <= h; u++) {
+        const int rr = wrapd(r + u * er, J.H), cc = wrapd(c + u * ec, J.W);
+        acc = fmaf(bt[u - 1 + h], D[(long long)rr * J.D.rs + cc], acc);   // tap b = 2u - 1
+    }
+    bases.p[J.T.b][J.T.off + (long long)r * J.T.rs + c] = acc;
+}
+
 __global__ void __launch_bounds__(256) k_dfb_g(const DfbGJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                int s, int target, float alpha, float gamma, Bases bases) {
     const DfbGJob& J = jobs[block_job[blockIdx.x]];
@@ -534,22 +561,16 @@ __global__ void __launch_bounds__(256) k_dfb_g(const DfbGJob* __restrict__ jobs,
     GChan ch;
     int b[4];
     if (g_walk(r, c, s, false, ch, b, nullptr) != target) return;
-    float* D = bases.p[J.D.b] + J.D.off;
-    const int rs = J.D.rs, n = J.ntaps;
+    const float* S = bases.p[J.T.b] + J.T.off;
+    const int n = J.ntaps;
     const float* bt = n == 6 ? c_fan6 : c_fan8;
     float acc = 0.f;
     for (int ia = 0; ia < n; ia++) {
-        const int a = 2 * ia - (n - 1);
-        float inner = 0.f;
-        for (int ib = 0; ib < n; ib++) {
-            const int bb = 2 * ib - (n - 1);
-            const int d1 = (a + bb) / 2, d2 = (a - bb) / 2;
-            const int rr = wrapd(r + d1 * b[0] + d2 * b[2], J.H), cc = wrapd(c + d1 * b[1] + d2 * b[3], J.W);
-            inner = fmaf(bt[ib], D[(long long)rr * rs + cc], inner);
-        }
-        acc = fmaf(bt[ia], inner, acc);
+        const int a = 2 * ia - (n - 1), d1 = (a - 1) / 2, d2 = (a + 1) / 2;     // exact: a is odd
+        const int rr = wrapd(r + d1 * b[0] + d2 * b[2], J.H), cc = wrapd(c + d1 * b[1] + d2 * b[3], J.W);
+        acc = fmaf(bt[ia], S[(long long)rr * J.T.rs + cc], acc);
     }
-    float* x = D + (long long)r * rs + c;
+    float* x = bases.p[J.D.b] + J.D.off + (long long)r * J.D.rs + c;
     *x = fmaf(alpha, *x, gamma * acc);
 }
 
@@ -604,6 +625,9 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
         if (syn) k_dfb_b<true><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
         else k_dfb_b<false><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
     } else if (L.kind == 2) {
+        k_dfb_gsum<<<L.nblocks, 256, 0, st>>>(static_cast<const DfbGJob*>(L.d_jobs), L.d_block_job, L.s, L.target,
+                                              bases);
+    } else if (L.kind == 4) {
         k_dfb_g<<<L.nblocks, 256, 0, st>>>(static_cast<const DfbGJob*>(L.d_jobs), L.d_block_job, L.s, L.target,
                                            L.alpha, L.gamma, bases);
     } else {

@@ -17,10 +17,15 @@ semantics of the two kernels:
                              E, O of its array, stencil row offset (a +- 1)/2,
                              column offset -i*a + (b-a)/2 (periodic)
   plain DFB pass (longer     one lifting pass of stage s over a whole detail
-  prototypes):               image: the samples of the target parity in their
+  prototypes), two launches: image: the samples of the target parity in their
                              stage-s channel, the n x n stencil of the n-tap
                              fan taps (from the Lagrange formula) in the
-                             channel's lattice basis (periodic)
+                             channel's lattice basis (periodic), split as the
+                             kernels split it: the first launch leaves the
+                             diagonal sums S[p] = sum_u bt[2u-1] x[p + u (B1 -
+                             B2)] at the other parity in the spare buffer T,
+                             the second sums bt[a] S[t + ((a-1)/2) B1 +
+                             ((a+1)/2) B2] at the targets
   plain DFB copy:            the detail image to / from the level's subbands
 
 so that a test can compare the planned computation with the oracle before
@@ -40,7 +45,7 @@ AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), 
                  ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
 BJOB = np.dtype([("pe", VIEW), ("po", VIEW), ("c0", VIEW), ("c1", VIEW), ("R2", "<i4"), ("C", "<i4"),
                  ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
-GJOB = np.dtype([("D", VIEW), ("slot0", "<i8"), ("H", "<i4"), ("W", "<i4"), ("k", "<i4"), ("ntaps", "<i4"),
+GJOB = np.dtype([("D", VIEW), ("T", VIEW), ("slot0", "<i8"), ("H", "<i4"), ("W", "<i4"), ("k", "<i4"), ("ntaps", "<i4"),
                  ("first_block", "<i4"), ("pad", "<i4")])
 BT = np.array([-1.0, -9.0, 9.0, 1.0]) / 16
 A4 = [-3, -1, 1, 3]
@@ -99,7 +104,7 @@ def _parse(raw):
             al, ga = np.frombuffer(raw[pos + 8:pos + 16], "<f4")
             extra = (int(st), int(tgt), float(al), float(ga))
             pos += 16
-        dt = (LPJOB, AJOB, BJOB, GJOB, GJOB)[kind]
+        dt = (LPJOB, AJOB, BJOB, GJOB, GJOB, GJOB)[kind]
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
         launches.append((int(kind), jobs, extra))
@@ -155,16 +160,28 @@ def _g_walk(H, W, s, descend):
     return cid, o_r, o_c, T
 
 
-def _g_pass(img, s, target, alpha, gamma, n):
+def _g_sums(img, T, s, target, n):
+    """first launch of a pass: diagonal sums at the samples of the other parity"""
     H, W = img.shape
     par, (b0, b1, b2, b3) = _g_walk(H, W, s, False)
     r, c = np.mgrid[0:H, 0:W]
-    taps = _fan_taps(n)
+    S = np.zeros_like(img)
+    for b, wb in _fan_taps(n):
+        u = (b + 1) // 2
+        S += wb * img[(r + u * (b0 - b2)) % H, (c + u * (b1 - b3)) % W]
+    m = par != target
+    T[m] = S[m]
+
+
+def _g_pass(img, T, s, target, alpha, gamma, n):
+    """second launch: the targets from the sums"""
+    H, W = img.shape
+    par, (b0, b1, b2, b3) = _g_walk(H, W, s, False)
+    r, c = np.mgrid[0:H, 0:W]
     acc = np.zeros_like(img)
-    for a, wa in taps:
-        for b, wb in taps:
-            d1, d2 = (a + b) // 2, (a - b) // 2
-            acc += wa * wb * img[(r + d1 * b0 + d2 * b2) % H, (c + d1 * b1 + d2 * b3) % W]
+    for a, wa in _fan_taps(n):
+        d1, d2 = (a - 1) // 2, (a + 1) // 2
+        acc += wa * T[(r + d1 * b0 + d2 * b2) % H, (c + d1 * b1 + d2 * b3) % W]
     m = par == target
     img[m] = alpha * img[m] + gamma * acc[m]
 
@@ -245,8 +262,12 @@ def _up(v, f):
 def _views_of(kind, J, synth, extra=None):
     """(reads, writes): lists of (name, view, rows, cols) a job touches."""
     if kind == 3:
-        D = [("D", J["D"], int(J["H"]), int(J["W"]))]
-        return D, D
+        H, W = int(J["H"]), int(J["W"])
+        return [("D", J["D"], H, W), ("T", J["T"], H, W)], [("T", J["T"], H, W)]
+    if kind == 5:
+        H, W = int(J["H"]), int(J["W"])
+        D = [("D", J["D"], H, W)]
+        return D + [("T", J["T"], H, W)], D
     if kind == 4:
         H, W = int(J["H"]), int(J["W"])
         lay = np.zeros(1, VIEW)[0]
@@ -287,8 +308,12 @@ def run(mode, elems, launches, bufs):
                 rjob.append((ji, (b, idx)))
             out = {}
             if kind == 3:
+                T = rd["T"].copy()
+                _g_sums(rd["D"], T, extra[0], extra[1], int(J["ntaps"]))
+                out["T"] = T
+            elif kind == 5:
                 img = rd["D"].copy()
-                _g_pass(img, extra[0], extra[1], extra[2], extra[3], int(J["ntaps"]))
+                _g_pass(img, rd["T"], extra[0], extra[1], extra[2], extra[3], int(J["ntaps"]))
                 out["D"] = img
             elif kind == 4:
                 idx = _g_leaf_index(J)
