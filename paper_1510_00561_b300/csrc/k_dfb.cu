@@ -521,6 +521,63 @@ __device__ __forceinline__ int g_walk(int r, int c, int s, bool descend, GChan& 
     return par;
 }
 
+// The stage-s channel of a sample (its family, slope index and parity) depends
+// on (r, c) alone and repeats with period P_s = 2^(s-1) (2 for s = 1): every
+// stage-s channel lattice contains P_s Z^2 and has a power-of-two index.  The
+// patterns of stages 1..6 are generated at compile time (the walk above, on
+// the host) into one table of 16-bit entries parity | family << 1 |
+// (slope + 32) << 2, so that the passes look a sample's channel up.
+__host__ __device__ constexpr int g_period(int s) { return s == 1 ? 2 : 1 << (s - 1); }
+__host__ __device__ constexpr int g_tab_off(int s) {
+    int o = 0;
+    for (int t = 1; t < s; t++) o += g_period(t) * g_period(t);
+    return o;
+}
+constexpr int G_TAB_N = g_tab_off(CVC_MAX_DIRS_LOG2 + 1);
+struct GTab {
+    uint16_t v[G_TAB_N];
+};
+constexpr GTab g_make_tab() {
+    GTab t{};
+    for (int s = 1; s <= CVC_MAX_DIRS_LOG2; s++) {
+        const int P = g_period(s);
+        for (int r = 0; r < P; r++)
+            for (int c = 0; c < P; c++) {
+                int o_r = 0, o_c = 0, T = 0, i = 0, par = 0;
+                for (int st = 1; st <= s; st++) {
+                    int b0 = 1, b1 = 0, b2 = 0, b3 = 1;
+                    if (st == 2) {
+                        b1 = 1;
+                        b2 = T == 0 ? 1 : -1;
+                        b3 = T == 0 ? -1 : 1;
+                    } else if (st >= 3) {
+                        const int q = 1 << (st - 2);
+                        if (T == 0) { b0 = q; b1 = -2 * i; b2 = q; b3 = -2 * i - 2; }
+                        else { b0 = -2 * i; b1 = q; b2 = -2 * i - 2; b3 = q; }
+                    }
+                    const int det = b0 * b3 - b1 * b2, dr = r - o_r, dc = c - o_c;
+                    par = ((b3 * dr - b2 * dc) / det + (b0 * dc - b1 * dr) / det) & 1;
+                    if (st == s) break;
+                    if (par) { o_r += b0; o_c += b1; }
+                    if (st == 1) { T = par; i = 0; }
+                    else if (st == 2) i = par ? 0 : -1;
+                    else i = 2 * i + par;
+                }
+                t.v[g_tab_off(s) + r * P + c] = (uint16_t)(par | (T << 1) | ((i + 32) << 2));
+            }
+    }
+    return t;
+}
+__device__ const GTab c_gtab = g_make_tab();
+
+// channel of sample (r, c) at stage s from the table: its basis, and its parity
+__device__ __forceinline__ int g_lookup(int r, int c, int s, int b[4]) {
+    const int P = g_period(s);
+    const unsigned e = __ldg(&c_gtab.v[g_tab_off(s) + (r & (P - 1)) * P + (c & (P - 1))]);
+    g_basis(s, GChan{0, 0, (int)((e >> 1) & 1), (int)(e >> 2) - 32}, b);
+    return (int)(e & 1);
+}
+
 // A lifting pass of stage s makes every sample t of parity `target`
 //   alpha * x[t] + gamma * sum_{a,b} bt[a] bt[b] x[t + delta(a,b)],
 // delta(a,b) = ((a+b)/2) B1 + ((a-b)/2) B2 (B1, B2 the channel's basis).  With
@@ -537,9 +594,8 @@ __global__ void __launch_bounds__(256) k_dfb_gsum(const DfbGJob* __restrict__ jo
     const long long pix = (long long)(blockIdx.x - J.first_block) * 256 + threadIdx.x;
     if (s > J.k || pix >= (long long)J.H * J.W) return;
     const int r = (int)(pix / J.W), c = (int)(pix % J.W);
-    GChan ch;
     int b[4];
-    if (g_walk(r, c, s, false, ch, b, nullptr) == target) return;     // sums sit at the other parity
+    if (g_lookup(r, c, s, b) == target) return;                        // sums sit at the other parity
     const float* D = bases.p[J.D.b] + J.D.off;
     const int n = J.ntaps, h = n / 2;
     const float* bt = n == 6 ? c_fan6 : c_fan8;
@@ -558,9 +614,8 @@ __global__ void __launch_bounds__(256) k_dfb_g(const DfbGJob* __restrict__ jobs,
     const long long pix = (long long)(blockIdx.x - J.first_block) * 256 + threadIdx.x;
     if (s > J.k || pix >= (long long)J.H * J.W) return;
     const int r = (int)(pix / J.W), c = (int)(pix % J.W);
-    GChan ch;
     int b[4];
-    if (g_walk(r, c, s, false, ch, b, nullptr) != target) return;
+    if (g_lookup(r, c, s, b) != target) return;
     const float* S = bases.p[J.T.b] + J.T.off;
     const int n = J.ntaps;
     const float* bt = n == 6 ? c_fan6 : c_fan8;
