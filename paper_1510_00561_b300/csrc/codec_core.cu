@@ -302,9 +302,11 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             c->luma_total += (long long)g.Hp * g.Wp;
             if ((long long)c->h_blk_motion.size() + D.nby * D.nbx > (1LL << 30)) return CVC_ERR_UNSUPPORTED;
             c->h_blk_motion.insert(c->h_blk_motion.end(), (size_t)D.nby * D.nbx, s);
-            // 256 threads walk the candidates (one per candidate measured slower at W = 8:
-            // 320-thread blocks took 109 against 83 us per 1080p frame)
-            c->motion_threads = 256;
+            // 128 threads walk the candidates in groups of four displacements
+            c->motion_threads = 128;
+            c->motion_rmax = std::max(c->motion_rmax, P.motion_range);
+            c->motion_ws = (16 + 2 * c->motion_rmax + 4 + 3) & ~3;   // word reads: a multiple of 4
+            c->motion_smem = (16 + 2 * c->motion_rmax) * c->motion_ws;
         }
         D.blk_colour = (int)c->h_blk_colour.size();
         // forward colour kernel: one block per padded luma row and per padded chroma row
@@ -538,8 +540,8 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         CK(cudaGetLastError());
         if (motion) {
             // §3.2 motion search, then the residuals of the motion-compensated P-frames
-            k_motion_b<<<(int)c->h_blk_motion.size(), c->motion_threads, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_motion, c->d_luma[0],
-                                                                    c->d_luma[1], c->d_mv);
+            k_motion_b<<<(int)c->h_blk_motion.size(), c->motion_threads, c->motion_smem, st>>>(
+                c->d_sd, c->d_sc, c->d_blk_motion, c->d_luma[0], c->d_luma[1], c->d_mv, c->motion_ws);
             k_mc_resid_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_est_buf[0], c->d_est_buf[1], rt, ct, c->d_sd, c->d_sc,
                                                      c->d_mv, c->d_res);
             CK(cudaGetLastError());

@@ -64,7 +64,9 @@ struct Core {
     std::vector<int> h_row_w, h_row_stream, h_row_comp, h_comp_row0, h_comp_stream;
     std::vector<uint8_t> h_row_low, h_comp_low, h_comp_level, h_comp_plane, h_comp_ey, h_comp_ex;
     long long luma_total = 0, mv_pairs = 0;   // motion: luma bytes per buffer, vector pairs
-    int motion_threads = 256;                  // block size of the motion search
+    int motion_threads = 128;                  // block size of the motion search
+    int motion_rmax = 0;                       // largest search range of the batch
+    int motion_ws = 0, motion_smem = 0;        // its window row stride (a multiple of 4) and shared-memory bytes
     CtEngine eng;
     int max_levels = 0;
     std::vector<std::unique_ptr<ScalePlan>> scale;   // index = scale, 0 .. max_levels

@@ -318,16 +318,17 @@ __global__ void k_unquant_keylow_b(const int16_t* __restrict__ res, int16_t* dst
 // first term is the same for every candidate of a block, so the search ranks
 // the exact integer sum p^2 - 2 sum c p, with the same order and the same
 // ties.  Ties go to the smaller |dy| + |dx|, then to the first candidate in
-// raster order.  Full blocks use four-byte dot products of packed rows.
-constexpr int ME_MAXR = CVC_MAX_MOTION_RANGE;
-constexpr int ME_WIN = 16 + 2 * ME_MAXR;    // window rows / columns
-constexpr int ME_WS = ME_WIN + 4;           // row stride (bytes): room for the last packed word
-
+// raster order.  Full blocks use four-byte dot products of packed rows, a
+// thread taking four neighbouring displacements (dx = 4g - W .. 4g - W + 3,
+// one dy): the five window words of a row serve all four, shifted by a
+// whole number of bytes known at compile time.
 __global__ void __launch_bounds__(1024) k_motion_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                                   const int* __restrict__ blk_stream,
                                                   const uint8_t* __restrict__ luma0,
-                                                  const uint8_t* __restrict__ luma1, int8_t* __restrict__ mv) {
-    __shared__ __align__(16) uint8_t s_win[ME_WIN * ME_WS];
+                                                  const uint8_t* __restrict__ luma1, int8_t* __restrict__ mv, int ws) {
+    // the window, (16 + 2 W_max) rows of ws >= 16 + 2 W_max + 4 bytes, ws a multiple of 4 (W_max: the
+    // batch's largest range)
+    extern __shared__ __align__(16) uint8_t s_win[];
     __shared__ uint32_t s_cur[16 * 4];
     __shared__ unsigned long long s_best[32];
     const int s = blk_stream[blockIdx.x];
@@ -343,11 +344,18 @@ __global__ void __launch_bounds__(1024) k_motion_b(const SDesc* __restrict__ sd,
     const uint8_t* prev = (C.ecur ? luma1 : luma0) + D.luma_off;
     // the window: previous-frame rows [y0 - R, y0 + bh + R), columns [x0 - R, x0 + bw + R),
     // in-plane bytes only (a valid candidate never reads the others)
+    // a warp per window row, lanes along it
     const int nr = bh + 2 * R, nc = bw + 2 * R;
-    for (int i = threadIdx.x; i < nr * nc; i += blockDim.x) {
-        const int r = i / nc, c = i - r * nc;
-        const int gy = y0 - R + r, gx = x0 - R + c;
-        s_win[r * ME_WS + c] = (gy >= 0 && gy < Hp && gx >= 0 && gx < Wp) ? prev[(long long)gy * Wp + gx] : 0;
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < nr; r += nwarp) {
+        const int gy = y0 - R + r;
+        uint8_t* dst = s_win + r * ws;
+        const bool row_in = gy >= 0 && gy < Hp;
+        const uint8_t* src = prev + (long long)(row_in ? gy : 0) * Wp;
+        for (int c = lane; c < nc; c += 32) {
+            const int gx = x0 - R + c;
+            dst[c] = (row_in && gx >= 0 && gx < Wp) ? src[gx] : 0;
+        }
     }
     for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         const int r = t >> 2, w = t & 3;
@@ -360,40 +368,66 @@ __global__ void __launch_bounds__(1024) k_motion_b(const SDesc* __restrict__ sd,
         s_cur[t] = v;
     }
     __syncthreads();
-    const int side = 2 * R + 1, ncand = side * side;
+    const int side = 2 * R + 1;
+    // key = (pp - 2 cp) + 2^26 (27 bits), then |dy| + |dx| (8 bits), then the raster index (15 bits)
+    auto key_of = [&](unsigned cp, unsigned pp, int dy, int dx) {
+        const int k = (dy + R) * side + (dx + R);
+        return ((unsigned long long)(unsigned)((int)pp - 2 * (int)cp + (1 << 26)) << 23) |
+               ((unsigned long long)(abs(dy) + abs(dx)) << 15) | (unsigned long long)k;
+    };
     unsigned long long best = ~0ull;
-    for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
-        const int dy = k / side - R, dx = k - (k / side) * side - R;
-        if (y0 + dy < 0 || y0 + dy + bh > Hp || x0 + dx < 0 || x0 + dx + bw > Wp) continue;
-        unsigned cp = 0, pp = 0;                   // bytes are unsigned: the unsigned dot products
-        const uint8_t* w0 = s_win + (dy + R) * ME_WS + (dx + R);
-        if (bw == 16) {
-            const int sh = 8 * ((dx + R) & 3);
+    if (bw == 16) {
+        // bytes are unsigned: the unsigned dot products.  Group g: dy = g / ngx - W, dx = 4 (g % ngx) - W + j;
+        // its window words start at byte 4 (g % ngx) of the row (the last group may read up to
+        // four bytes past the window's columns, inside the row stride: only for dx > W, never kept)
+        const int ngx = (side + 3) >> 2, ng = side * ngx;
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+            const int gy = g / ngx, gx = g - gy * ngx;
+            const int dy = gy - R, dx0 = 4 * gx - R;
+            if (y0 + dy < 0 || y0 + dy + bh > Hp) continue;
+            unsigned cp[4] = {0, 0, 0, 0}, pp[4] = {0, 0, 0, 0};
+            const uint8_t* wbase = s_win + (dy + R) * ws + 4 * gx;
             for (int r = 0; r < bh; r++) {
-                const uint32_t* wr = reinterpret_cast<const uint32_t*>(s_win + (dy + R + r) * ME_WS + ((dx + R) & ~3));
-                uint32_t w[5];
+                const uint32_t* wr = reinterpret_cast<const uint32_t*>(wbase + r * ws);
+                uint32_t w[5], cw[4];
 #pragma unroll
                 for (int q = 0; q < 5; q++) w[q] = wr[q];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const uint32_t pw = __funnelshift_r(w[q], w[q + 1], sh);
-                    cp = __dp4a(s_cur[4 * r + q], pw, cp);
-                    pp = __dp4a(pw, pw, pp);
-                }
+                for (int q = 0; q < 4; q++) cw[q] = s_cur[4 * r + q];
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t pw = j == 0 ? w[q] : __funnelshift_r(w[q], w[q + 1], 8 * j);
+                        cp[j] = __dp4a(cw[q], pw, cp[j]);
+                        pp[j] = __dp4a(pw, pw, pp[j]);
+                    }
             }
-        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int dx = dx0 + j;
+                if (dx > R || x0 + dx < 0 || x0 + dx + bw > Wp) continue;
+                const unsigned long long key = key_of(cp[j], pp[j], dy, dx);
+                best = key < best ? key : best;
+            }
+        }
+    } else {
+        const int ncand = side * side;
+        for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+            const int dy = k / side - R, dx = k - (k / side) * side - R;
+            if (y0 + dy < 0 || y0 + dy + bh > Hp || x0 + dx < 0 || x0 + dx + bw > Wp) continue;
+            unsigned cp = 0, pp = 0;
+            const uint8_t* w0 = s_win + (dy + R) * ws + (dx + R);
             for (int r = 0; r < bh; r++)
                 for (int x = 0; x < bw; x++) {
-                    const unsigned p = w0[r * ME_WS + x];
+                    const unsigned p = w0[r * ws + x];
                     const unsigned c = (s_cur[4 * r + (x >> 2)] >> (8 * (x & 3))) & 255u;
                     cp += c * p;
                     pp += p * p;
                 }
+            const unsigned long long key = key_of(cp, pp, dy, dx);
+            best = key < best ? key : best;
         }
-        // key = (pp - 2 cp) + 2^26 (27 bits), then |dy| + |dx| (8 bits), then the raster index (15 bits)
-        const unsigned long long key = ((unsigned long long)(unsigned)((int)pp - 2 * (int)cp + (1 << 26)) << 23) |
-                                       ((unsigned long long)(abs(dy) + abs(dx)) << 15) | (unsigned long long)k;
-        best = key < best ? key : best;
     }
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);

@@ -135,9 +135,11 @@ constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS
 __global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes,
                                uint8_t* luma0, uint8_t* luma1);
 // motion search of the P-frames of streams with a motion range: one block per 16 x 16 luma block,
-// any multiple of 32 threads up to 1024 walking the (2W + 1)^2 candidates
+// any multiple of 32 threads up to 1024 walking the (2W + 1)^2 candidates; dynamic shared memory of
+// (16 + 2 W_max) * ws bytes, ws = 16 + 2 W_max + 4 rounded up to a multiple of 4 (W_max the largest
+// range of the launch)
 __global__ void k_motion_b(const SDesc* sd, const SCall* sc, const int* blk_stream, const uint8_t* luma0,
-                           const uint8_t* luma1, int8_t* mv);
+                           const uint8_t* luma1, int8_t* mv, int ws);
 // residuals of motion-compensated P-frames (after k_quant_b wrote their codes)
 __global__ void k_mc_resid_b(const int16_t* est0, const int16_t* est1, RowTable rt, CompTable ct,
                              const SDesc* sd, const SCall* sc, const int8_t* mv, int16_t* res);
