@@ -40,6 +40,7 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_row_w, c->h_row_w.size());
     k.add(&c->d_row_stream, c->h_row_stream.size());
     k.add(&c->d_row_comp, c->h_row_comp.size());
+    k.add(&c->d_row_mc, c->h_row_mc.size());
     k.add(&c->d_row_low, c->h_row_low.size());
     k.add(&c->d_comp_row0, c->h_comp_row0.size());
     k.add(&c->d_comp_stream, c->h_comp_stream.size());
@@ -360,6 +361,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
                     c->h_row_low.push_back(sb.kind == 0);
                     c->h_row_stream.push_back(s);
                     c->h_row_comp.push_back(comp);
+                    c->h_row_mc.push_back(make_int4(r, sb.h, ey, ex));
                 }
             }
         }
@@ -431,7 +433,7 @@ cvc_status core_alloc(Core* c) {
               put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
               put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
               put(c->d_comp_level, c->h_comp_level) && put(c->d_comp_plane, c->h_comp_plane) &&
-              put(c->d_row_comp, c->h_row_comp) && put(c->d_comp_ey, c->h_comp_ey) &&
+              put(c->d_row_comp, c->h_row_comp) && put(c->d_row_mc, c->h_row_mc) && put(c->d_comp_ey, c->h_comp_ey) &&
               put(c->d_comp_ex, c->h_comp_ex) && put(c->d_blk_motion, c->h_blk_motion);
     for (const auto& sp : c->scale) ok = ok && put(sp->d_desc, sp->h_desc) && put(sp->d_blk, sp->h_blk);
     // state buffers start at zero (no frame may read them before a K-frame)
@@ -507,7 +509,7 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
     *nl = 0;
     CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->d_rs, 0, sizeof(SResult) * n, st));
-    const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->d_row_comp, c->nrows};
+    const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->d_row_comp, c->d_row_mc, c->nrows};
     const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
                        c->d_comp_level, c->d_comp_plane, c->d_comp_ey, c->d_comp_ex, c->ncomp};
     const bool motion = !c->h_blk_motion.empty();

@@ -82,6 +82,8 @@ struct Core {
     long long *d_row_off = nullptr, *d_comp_elem = nullptr;
     int *d_row_w = nullptr, *d_row_stream = nullptr, *d_row_comp = nullptr, *d_comp_row0 = nullptr,
         *d_comp_stream = nullptr;
+    std::vector<int4> h_row_mc;
+    int4* d_row_mc = nullptr;
     uint8_t *d_row_low = nullptr, *d_comp_low = nullptr, *d_comp_level = nullptr, *d_comp_plane = nullptr,
             *d_comp_ey = nullptr, *d_comp_ex = nullptr;
     uint8_t* d_luma[2] = {nullptr, nullptr};   // previous / current padded luma of streams with motion

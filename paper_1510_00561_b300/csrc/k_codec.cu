@@ -459,17 +459,17 @@ struct McRow {
     long long base;        // global index of the component's first element
     int i, h, w, ey, ex, nbx;
 };
-__device__ __forceinline__ McRow mc_row(int row, const RowTable& rt, const CompTable& ct, const SDesc& D,
-                                        const int8_t* mv) {
+// (one table load per row: the component's rows are contiguous, so its first
+// element is the row's minus i rows)
+__device__ __forceinline__ McRow mc_row(int row, const RowTable& rt, const SDesc& D, const int8_t* mv) {
     McRow m;
-    const int c = rt.comp[row];
-    const int r0 = ct.row0[c];
-    m.i = row - r0;
-    m.h = ct.row0[c + 1] - r0;
+    const int4 t = rt.mc[row];
+    m.i = t.x;
+    m.h = t.y;
     m.w = rt.w[row];
-    m.base = rt.off[r0];
-    m.ey = ct.ey[c];
-    m.ex = ct.ex[c];
+    m.base = rt.off[row] - (long long)t.x * m.w;
+    m.ey = t.z;
+    m.ex = t.w;
     m.nbx = D.nbx;
     const int by = min((m.i << m.ey) >> 4, D.nby - 1);
     m.mvrow = mv + 2LL * by * D.nbx;
@@ -495,10 +495,17 @@ __global__ void k_mc_resid_b(const int16_t* __restrict__ est0, const int16_t* __
     if (!C.enc_on || C.enc_key || D.mv_range == 0) return;
     const int16_t* prev = C.ecur ? est1 : est0;
     const int16_t* q = C.ecur ? est0 : est1;       // this frame's codes (k_quant_b)
-    const McRow m = mc_row(row, rt, ct, D, mv + 2 * D.mv_off);
+    const McRow m = mc_row(row, rt, D, mv + 2 * D.mv_off);
     const long long off = rt.off[row];
-    for (int x = lane; x < m.w; x += 32)
-        res[off + x] = (int16_t)(uint16_t)((q[off + x] - prev[mc_src(m, x)]) & 0xFFFF);
+    // two elements per lane in flight: their gathers do not wait on each other
+    for (int x = lane; x < m.w; x += 64) {
+        const bool two = x + 32 < m.w;
+        const long long s0 = mc_src(m, x), s1 = two ? mc_src(m, x + 32) : s0;
+        const int16_t p0 = prev[s0], p1 = prev[s1], q0 = q[off + x];
+        const int16_t q1 = two ? q[off + x + 32] : (int16_t)0;
+        res[off + x] = (int16_t)(uint16_t)((q0 - p0) & 0xFFFF);
+        if (two) res[off + x + 32] = (int16_t)(uint16_t)((q1 - p1) & 0xFFFF);
+    }
 }
 
 __global__ void k_mc_recon_b(const int16_t* __restrict__ res, int16_t* dst0, int16_t* dst1, RowTable rt,
@@ -514,13 +521,22 @@ __global__ void k_mc_recon_b(const int16_t* __restrict__ res, int16_t* dst0, int
     const int16_t* prev = C.dcur ? dst1 : dst0;
     int16_t* nxt = C.dcur ? dst0 : dst1;
     const int8_t* v = reinterpret_cast<const int8_t*>(C.in + D.hdr_bytes + 2LL * rs[s].dec_tokens);
-    const McRow m = mc_row(row, rt, ct, D, v);
+    const McRow m = mc_row(row, rt, D, v);
     const long long off = rt.off[row];
     const float scale = rt.low[row] ? D.qp.qpl_denorm : D.qp.qph;
-    for (int x = lane; x < m.w; x += 32) {
-        const int16_t qv = (int16_t)(uint16_t)((res[off + x] + prev[mc_src(m, x)]) & 0xFFFF);
-        nxt[off + x] = qv;
-        coef[off + x] = (float)qv * scale;
+    for (int x = lane; x < m.w; x += 64) {
+        const bool two = x + 32 < m.w;
+        const long long s0 = mc_src(m, x), s1 = two ? mc_src(m, x + 32) : s0;
+        const int16_t p0 = prev[s0], p1 = prev[s1], r0 = res[off + x];
+        const int16_t r1 = two ? res[off + x + 32] : (int16_t)0;
+        const int16_t q0 = (int16_t)(uint16_t)((r0 + p0) & 0xFFFF);
+        nxt[off + x] = q0;
+        coef[off + x] = (float)q0 * scale;
+        if (two) {
+            const int16_t q1 = (int16_t)(uint16_t)((r1 + p1) & 0xFFFF);
+            nxt[off + x + 32] = q1;
+            coef[off + x + 32] = (float)q1 * scale;
+        }
     }
 }
 

@@ -114,6 +114,7 @@ struct RowTable {
     const uint8_t* low;     // row belongs to a lowpass component
     const int* stream;
     const int* comp;        // global component index
+    const int4* mc;         // motion compensation: the row's index and the height of its component, ey, ex
     int nrows;
 };
 
