@@ -146,3 +146,24 @@ def test_mixed_prototypes_in_one_batch_and_refusals():
     _gpu(ODD, 6).decode(s6.clone())
     with pytest.raises(CvcError):
         Codec(*_args(ODD), dfb_taps=5)
+
+
+def test_1080p_codec_with_a_longer_prototype():
+    """the bench's size: one 1080p K-frame with the 6-tap prototype; every coefficient
+    against the oracle's transform of the GPU's own planes, and the bitstream bit for bit"""
+    kw = dict(width=1920, height=1080, levels=5, dirs_log2=[5, 4, 4, 3, 3], qph=8, qpl=1, key_interval=10)
+    g, o = _gpu(kw, 6), _oracle(kw, 6)
+    f = S.SyntheticVideo(S.spec_for(1920, 1080, seed=93)).frames(1)[0]
+    s, ft = g.encode(torch.from_numpy(f).cuda())
+    planes = g.inspect(0).cpu().numpy().astype(np.float64)
+    coef = g.inspect(1).cpu().numpy()
+    dims = [(g.Hp, g.Wp), (g.Hcp, g.Wcp), (g.Hcp, g.Wcp)]
+    po = co = 0
+    for H, W in dims:
+        n = O.layout(H, W, 5, kw["dirs_log2"])["total"]
+        ref = O.ct(0, planes[po:po + H * W].reshape(H, W), H, W, 5, kw["dirs_log2"], 6)
+        assert _coef_err(coef[co:co + n], ref, H, W, 5, kw["dirs_log2"]) < FORWARD
+        po += H * W
+        co += n
+    ref_stream, rft = o.encode_from_coeffs(coef)
+    assert rft == ft == 0 and np.array_equal(s.cpu().numpy(), ref_stream)
