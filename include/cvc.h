@@ -183,8 +183,8 @@ cvc_status cvc_ct_soft_threshold_backward(cvc_ct_plan* plan, const float* d_coef
  *                   tiled DFB kernels; 6 or 8, the longer Lagrange
  *                   half-band interpolators (3, -25, 150, 150, -25, 3)/256
  *                   and (-5, 49, -245, 1225, 1225, -245, 49, -5)/2048, a
- *                   sharper directional split, run by a plain per-sample
- *                   kernel.  Header byte 5 bits 1-2 record it (0, 1, 2).    */
+ *                   sharper directional split, run by the same kernels with
+ *                   wider halos.  Header byte 5 bits 1-2 record it (0, 1, 2). */
 #define CVC_MAX_MOTION_RANGE 64
 typedef struct {
     int width, height;
@@ -550,14 +550,10 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  *   u32 magic 0x43564350 ('CVCP'), u32 n_launches, u32 bytes of an LP-level
  *   job, u32 bytes of a DFB stage-1+2 job, u32 bytes of a DFB row-split job,
  *   u32 bytes of the trailing records (cvc_debug_scale_tables; else 0),
- *   u32 bytes of a plain DFB job (longer prototypes),
  *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
  *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage
- *   >= 3, 3 = plain DFB diagonal sums of a lifting pass, 4 = plain DFB copy
- *   between the detail images and the layout, 5 = plain DFB pass targets),
- *   u32 njobs, for kinds 3-5 four u32 (stage, target parity or 1 = image ->
- *   layout, alpha and gamma as f32), and njobs job records (the library's
- *   job structures).
+ *   >= 3), u32 njobs, and njobs job records (the library's job structures;
+ *   DFB jobs carry their prototype length).
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */

@@ -188,7 +188,7 @@ cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log
         !dalloc(p->allocs, &p->d_soft_partial, sj.size()) ||
         cudaMemcpy(p->d_soft, sj.data(), sj.size() * sizeof(SoftJob), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_soft_first, sf.data(), sf.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        lp_prepare() != cudaSuccess) {
+        lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return CVC_ERR_NOMEM;
@@ -832,43 +832,35 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
                               size_t tail_n, size_t tail_sz, void* buf, size_t cap, size_t* used) {
     unsigned long long elems[4] = {elems_in[0], elems_in[1], elems_in[2], elems_in[3]};
     elems[2] = std::max(elems[2], (unsigned long long)e.work_elems);
-    struct Item { int kind; const void* data; size_t n, sz; const LaunchDfb* L; };
+    struct Item { int kind; const void* data; size_t n, sz; };
     std::vector<Item> items;
     const bool analysis = (mode == FWD || mode == INV_ADJ);
     auto push_lp = [&]() {
-        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob), nullptr});
+        for (auto& v : e.h_lp[mode]) items.push_back({0, v.data(), v.size(), sizeof(LpJob)});
     };
     auto push_dfb = [&]() {
         for (size_t i = 0; i < e.dfb[mode].size(); i++) {
             const LaunchDfb& L = e.dfb[mode][i];
-            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : (L.kind == 1 ? sizeof(DfbBJob) : sizeof(DfbGJob));
-            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz, &L});
+            const size_t sz = L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob);
+            items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
         }
     };
     if (analysis) { push_lp(); push_dfb(); }
     else { push_dfb(); push_lp(); }
-    size_t need = 28 + 32 + tail_n * tail_sz;
-    for (const Item& it : items) need += 8 + (it.kind >= 3 ? 16 : 0) + it.n * it.sz;
+    size_t need = 24 + 32 + tail_n * tail_sz;
+    for (const Item& it : items) need += 8 + it.n * it.sz;
     *used = need;
     if (!buf || cap < need) return CVC_ERR_CAPACITY;
     uint8_t* o = (uint8_t*)buf;
-    uint32_t hdr[7] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
-                       (uint32_t)sizeof(DfbBJob), (uint32_t)(tail_n ? tail_sz : 0), (uint32_t)sizeof(DfbGJob)};
-    memcpy(o, hdr, 28);
-    memcpy(o + 28, elems, 32);
-    size_t pos = 60;
+    uint32_t hdr[6] = {0x43564350u, (uint32_t)items.size(), (uint32_t)sizeof(LpJob), (uint32_t)sizeof(DfbAJob),
+                       (uint32_t)sizeof(DfbBJob), (uint32_t)(tail_n ? tail_sz : 0)};
+    memcpy(o, hdr, 24);
+    memcpy(o + 24, elems, 32);
+    size_t pos = 56;
     for (const Item& it : items) {
         uint32_t h2[2] = {(uint32_t)it.kind, (uint32_t)it.n};
         memcpy(o + pos, h2, 8);
         pos += 8;
-        if (it.kind >= 3) {
-            // the launch's stage, target parity (kind 4: 1 = image -> layout), alpha, gamma (kind 5)
-            uint32_t lp[4] = {(uint32_t)it.L->s, (uint32_t)it.L->target, 0, 0};
-            memcpy(&lp[2], &it.L->alpha, 4);
-            memcpy(&lp[3], &it.L->gamma, 4);
-            memcpy(o + pos, lp, 16);
-            pos += 16;
-        }
         memcpy(o + pos, it.data, it.n * it.sz);
         pos += it.n * it.sz;
     }

@@ -409,7 +409,7 @@ cvc_status core_alloc(Core* c) {
             return CVC_ERR_NOMEM;
         }
     }
-    if (lp_prepare() != cudaSuccess) return CVC_ERR_CUDA;
+    if (lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess) return CVC_ERR_CUDA;
     Carve k;
     carve_all(c, k);
     c->arena_bytes = k.total;

@@ -25,10 +25,9 @@
 //   c: b1 = (2^(s-2), -2i), b2 = (2^(s-2), -2i-2);  r: b1 = (-2i, 2^(s-2)), b2 = (-2i-2, 2^(s-2)).
 // The even child takes the lower half of the slopes.
 //
-// Longer prototypes (6 or 8 taps, PlaneRef.taps) skip the tile kernels: every
-// pass of every stage is two launches over whole detail images (k_dfb_gsum
-// into the level's spare buffer Q_j, then k_dfb_g), and k_dfb_leaf moves
-// between the images and the layout.
+// Longer prototypes (6 or 8 taps, PlaneRef.taps) take the same tile kernels
+// instantiated for their length; planes of different lengths get separate
+// launches of each step.
 //
 // Data flow of one level: the LP writes the detail image D; stages 1 and 2
 // run fused in k_dfb_a, whose stage-2 channels are D's four polyphase
@@ -113,7 +112,7 @@ View mk(int b, long long off, int rs, int cs) {
 
 // DFB jobs of one (plane, level): detail D_j at doff, partner Q_j at qoff,
 // subband slots (coefficient offsets) in tree order.
-void dfb_jobs(int H, int W, int k, long long doff, long long qoff, const std::vector<long long>& slot,
+void dfb_jobs(int H, int W, int k, int ntaps, long long doff, long long qoff, const std::vector<long long>& slot,
               std::vector<DfbAJob>& ajobs, std::vector<std::vector<DfbBJob>>& bjobs) {
     if (k == 0) return;
     const int h2 = H / 2, w2 = W / 2;
@@ -125,6 +124,7 @@ void dfb_jobs(int H, int W, int k, long long doff, long long qoff, const std::ve
     A.W = W;
     A.nst = k == 1 ? 1 : 2;
     A.tiles_x = (W + DFBA_TILE - 1) / DFBA_TILE;
+    A.ntaps = ntaps;
     // polyphase classes q = 2*pr + pc: 00, 01, 10, 11
     if (k == 1) {
         // stage-1 cosets are the subbands: {00, 11} row-compacted into slot 0, {01, 10} into slot 1
@@ -180,7 +180,8 @@ void dfb_jobs(int H, int W, int k, long long doff, long long qoff, const std::ve
             J.R2 = R2;
             J.C = C;
             J.i = i;
-            J.tiles_x = (C + DFBB_COLS - 1) / DFBB_COLS;
+            J.tiles_x = (C + dfbb_cols(ntaps) - 1) / dfbb_cols(ntaps);
+            J.ntaps = ntaps;
             bjobs[s].push_back(J);
             next.push_back({fam, 2 * i});
             next.push_back({fam, 2 * i + 1});
@@ -222,9 +223,7 @@ int count_a(const DfbAJob& J) {
 int count_b(const DfbBJob& J) {
     return ((J.R2 + DFBB_ROWS - 1) / DFBB_ROWS) * J.tiles_x;
 }
-int count_g(const DfbGJob& J) {
-    return (int)(((long long)J.H * J.W + 255) / 256);
-}
+
 
 }  // namespace
 
@@ -246,10 +245,11 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         const bool analysis = (m == FWD || m == INV_ADJ);
         const int spatial_base = analysis ? B_IN : B_OUT;
         std::vector<std::vector<LpJob>> lpj(Lmax + 1);
-        std::vector<DfbAJob> aj;
-        std::vector<std::vector<DfbBJob>> bj(std::max(kmax, 2) + 1);
-        std::vector<DfbGJob> gj;       // levels of planes with a longer prototype
-        int kgmax = 0;
+        // tile jobs by prototype length (4, 6, 8): one launch per length and step
+        std::vector<DfbAJob> aj[3];
+        std::vector<std::vector<DfbBJob>> bj[3];
+        for (auto& v : bj) v.resize(std::max(kmax, 2) + 1);
+
         for (size_t p = 0; p < e->planes.size(); p++) {
             const PlaneRef& P = e->planes[p];
             const PlaneLayout& Ly = lays[p];
@@ -290,23 +290,8 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                     J.out = spatial_prev;
                 }
                 lpj[j].push_back(J);
-                if (P.taps == 6 || P.taps == 8) {
-                    if (kj > 0) {
-                        DfbGJob G;
-                        memset(&G, 0, sizeof(G));
-                        G.D = mk(B_WORK, doff[j], wj, 1);
-                        G.T = mk(B_WORK, qoff[j], wj, 1);
-                        G.slot0 = slots[0];
-                        G.H = hj;
-                        G.W = wj;
-                        G.k = kj;
-                        G.ntaps = P.taps;
-                        gj.push_back(G);
-                        kgmax = std::max(kgmax, kj);
-                    }
-                } else {
-                    dfb_jobs(hj, wj, kj, doff[j], qoff[j], slots, aj, bj);
-                }
+                const int nt = (P.taps == 6 || P.taps == 8) ? P.taps : 4;
+                dfb_jobs(hj, wj, kj, nt, doff[j], qoff[j], slots, aj[nt / 2 - 2], bj[nt / 2 - 2]);
             }
         }
         e->lp[m].clear();
@@ -326,6 +311,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         auto add_a = [&](std::vector<DfbAJob>& v) {
             LaunchDfb L{};
             L.kind = 0;
+            L.ntaps = v.front().ntaps;
             if (!upload<DfbAJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_a)) return false;
             L.njobs = (int)v.size();
             e->dfb[m].push_back(L);
@@ -336,6 +322,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         auto add_b = [&](std::vector<DfbBJob>& v) {
             LaunchDfb L{};
             L.kind = 1;
+            L.ntaps = v.front().ntaps;
             if (!upload<DfbBJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_b)) return false;
             L.njobs = (int)v.size();
             e->dfb[m].push_back(L);
@@ -343,48 +330,20 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                                      reinterpret_cast<uint8_t*>(v.data() + v.size()));
             return true;
         };
-        // plain path: a launch per lifting pass of stage s over the levels with k >= s,
-        // and one copy between the detail images and the layout
-        const PassParams pp = pass_params((Mode)m);
-        auto add_g = [&](int kind, int s, int target, float alpha, float gamma) {
-            std::vector<DfbGJob> v;
-            for (const DfbGJob& G : gj)
-                if (kind == 3 || G.k >= s) v.push_back(G);
-            if (v.empty()) return true;
-            LaunchDfb L{};
-            L.kind = kind;
-            L.s = s;
-            L.target = target;
-            L.alpha = alpha;
-            L.gamma = gamma;
-            if (!upload<DfbGJob>(v, to_device, e, &L.d_jobs, &L.d_block_job, &L.nblocks, count_g)) return false;
-            L.njobs = (int)v.size();
-            e->dfb[m].push_back(L);
-            e->h_dfb[m].emplace_back(reinterpret_cast<uint8_t*>(v.data()),
-                                     reinterpret_cast<uint8_t*>(v.data() + v.size()));
-            return true;
-        };
-        auto add_stage = [&](int s) {
-            const int t1 = pp.first_odd ? 1 : 0;
-            return add_g(2, s, t1, 0.f, 0.f) && add_g(4, s, t1, pp.a1, pp.g1) && add_g(2, s, 1 - t1, 0.f, 0.f) &&
-                   add_g(4, s, 1 - t1, pp.a2, pp.g2);
-        };
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)
                 if (!add_lp(lpj[j])) return false;
-            if (!aj.empty() && !add_a(aj)) return false;
+            for (int n = 0; n < 3; n++)
+                if (!aj[n].empty() && !add_a(aj[n])) return false;
             for (int s = 3; s <= kmax; s++)
-                if (!bj[s].empty() && !add_b(bj[s])) return false;
-            for (int s = 1; s <= kgmax; s++)
-                if (!add_stage(s)) return false;
-            if (!add_g(3, 0, 1, 0.f, 0.f)) return false;
+                for (int n = 0; n < 3; n++)
+                    if (!bj[n][s].empty() && !add_b(bj[n][s])) return false;
         } else {
-            if (!add_g(3, 0, 0, 0.f, 0.f)) return false;
-            for (int s = kgmax; s >= 1; s--)
-                if (!add_stage(s)) return false;
             for (int s = kmax; s >= 3; s--)
-                if (!bj[s].empty() && !add_b(bj[s])) return false;
-            if (!aj.empty() && !add_a(aj)) return false;
+                for (int n = 0; n < 3; n++)
+                    if (!bj[n][s].empty() && !add_b(bj[n][s])) return false;
+            for (int n = 0; n < 3; n++)
+                if (!aj[n].empty() && !add_a(aj[n])) return false;
             for (int j = Lmax; j >= 1; j--)
                 if (!add_lp(lpj[j])) return false;
         }

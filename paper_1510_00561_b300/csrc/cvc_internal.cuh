@@ -55,6 +55,7 @@ struct DfbAJob {
     int H, W;
     int nst;
     int tiles_x, first_block;
+    int ntaps;     // prototype length (4, 6 or 8)
 };
 
 // One stage s >= 3 of one channel: its array splits into even / odd rows,
@@ -67,24 +68,12 @@ struct DfbBJob {
     int R2, C;
     int i;
     int tiles_x, first_block;
+    int ntaps;     // prototype length (4, 6 or 8)
 };
 
-// Longer PKVA prototypes (6 or 8 taps) take a plain path: each lifting pass
-// of stage s over a whole detail image in place, in two launches (diagonal
-// sums into T, then the targets; a thread per sample, its channel and lattice
-// basis found from its position), then a copy between the image and the
-// subband layout (k_dfb_leaf).
-struct DfbGJob {
-    View D;            // H x W detail image (rs = pitch, cs = 1)
-    View T;            // H x W spare buffer of the level: the diagonal sums
-    long long slot0;   // first subband of the level in B_COEF (2^k subbands of H*W/2^k)
-    int H, W, k;
-    int ntaps;         // 6 or 8
-    int first_block, pad;
-};
-
-constexpr int DFBA_TILE = 64, DFBA_HALO = 12;
-constexpr int DFBB_ROWS = 16, DFBB_COLS = 116;
+constexpr int DFBA_TILE = 64, DFBA_HALO = 12;   // the halo of the 4-tap prototype (4 (NT - 1) in general)
+constexpr int DFBB_ROWS = 16, DFBB_COLS = 116;  // columns of the 4-tap prototype (128 - 4 (NT - 1) in general)
+constexpr int dfbb_cols(int ntaps) { return 128 - 4 * (ntaps - 1); }
 
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)
@@ -120,7 +109,7 @@ struct PlaneRef {
     long long work;   // workspace offset in B_WORK
     long long low_coef;   // >= 0: the lowpass lives here instead of at coef (a sub-pyramid of a
                           // larger layout keeps its lowpass apart from its subbands)
-    int taps;             // DFB prototype length: 0 or 4 (tile kernels), 6 or 8 (DfbGJob path)
+    int taps;             // DFB prototype length: 0 or 4, 6 or 8
 };
 
 struct LaunchLp {
@@ -129,12 +118,11 @@ struct LaunchLp {
     int* d_block_job;
 };
 struct LaunchDfb {
-    int kind;  // 0: DfbAJob, 1: DfbBJob; DfbGJob: 2 diagonal sums, 3 layout copy, 4 pass targets
+    int kind;  // 0: DfbAJob, 1: DfbBJob
     int njobs, nblocks;
     void* d_jobs;
     int* d_block_job;
-    int s, target;        // kinds 2, 4: stage and target parity; kind 3: target 1 = image -> layout
-    float alpha, gamma;   // kind 4
+    int ntaps;  // the prototype length of the launch's planes (4, 6 or 8)
 };
 
 enum Mode { FWD = 0, INV = 1, FWD_ADJ = 2, INV_ADJ = 3 };
@@ -171,6 +159,8 @@ cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st);
 // one-time kernel attributes of the LP kernels (call before any stream capture)
 cudaError_t lp_prepare();
 cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st);
+// one-time kernel attributes of the DFB kernels (call before any stream capture)
+cudaError_t dfb_prepare();
 PassParams pass_params(Mode m);
 
 }  // namespace cvc

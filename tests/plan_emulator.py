@@ -16,17 +16,9 @@ semantics of the two kernels:
   DFB row-split job:         one stage s >= 3 of a channel: even / odd rows
                              E, O of its array, stencil row offset (a +- 1)/2,
                              column offset -i*a + (b-a)/2 (periodic)
-  plain DFB pass (longer     one lifting pass of stage s over a whole detail
-  prototypes), two launches: image: the samples of the target parity in their
-                             stage-s channel, the n x n stencil of the n-tap
-                             fan taps (from the Lagrange formula) in the
-                             channel's lattice basis (periodic), split as the
-                             kernels split it: the first launch leaves the
-                             diagonal sums S[p] = sum_u bt[2u-1] x[p + u (B1 -
-                             B2)] at the other parity in the spare buffer T,
-                             the second sums bt[a] S[t + ((a-1)/2) B1 +
-                             ((a+1)/2) B2] at the targets
-  plain DFB copy:            the detail image to / from the level's subbands
+
+DFB jobs carry their prototype length n; their stencils use the n fan taps
+computed here from the Lagrange interpolation formula, not from the library.
 
 so that a test can compare the planned computation with the oracle before
 any kernel runs on a GPU.  Each pass sets target = alpha*target + gamma*sum.
@@ -42,13 +34,9 @@ VIEW = np.dtype([("off", "<i8"), ("b", "<i4"), ("rs", "<i4"), ("cs", "<i4"), ("p
 LPJOB = np.dtype([("main", VIEW), ("cin", VIEW), ("cout", VIEW), ("out", VIEW), ("H", "<i4"), ("W", "<i4"),
                   ("tiles_x", "<i4"), ("first_block", "<i4")])
 AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), ("nst", "<i4"),
-                 ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
+                 ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4")])
 BJOB = np.dtype([("pe", VIEW), ("po", VIEW), ("c0", VIEW), ("c1", VIEW), ("R2", "<i4"), ("C", "<i4"),
-                 ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("pad", "<i4")])
-GJOB = np.dtype([("D", VIEW), ("T", VIEW), ("slot0", "<i8"), ("H", "<i4"), ("W", "<i4"), ("k", "<i4"), ("ntaps", "<i4"),
-                 ("first_block", "<i4"), ("pad", "<i4")])
-BT = np.array([-1.0, -9.0, 9.0, 1.0]) / 16
-A4 = [-3, -1, 1, 3]
+                 ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4")])
 # (first target is the odd coset, alpha1, gamma1, alpha2, gamma2) per mode
 PASSES = {0: (1, 0.5, -0.5, 1.0, 1.0), 3: (0, 1.0, 1.0, 2.0, -1.0),
           1: (0, 1.0, -1.0, 2.0, 1.0), 2: (1, 0.5, 0.5, 1.0, -1.0)}
@@ -88,23 +76,17 @@ def scale_tables(params, n, scale):
 
 
 def _parse(raw):
-    magic, nl, lpb, ab, bb, tail_sz, gb = np.frombuffer(raw[:28], "<u4")
+    magic, nl, lpb, ab, bb, tail_sz = np.frombuffer(raw[:24], "<u4")
     assert tail_sz in (0, SCALEDESC.itemsize)
     assert magic == 0x43564350 and lpb == LPJOB.itemsize and ab == AJOB.itemsize and bb == BJOB.itemsize
-    assert gb == GJOB.itemsize
-    elems = np.frombuffer(raw[28:60], "<u8").astype(np.int64)
-    pos = 60
+    elems = np.frombuffer(raw[24:56], "<u8").astype(np.int64)
+    pos = 56
     launches = []
     for _ in range(nl):
         kind, nj = np.frombuffer(raw[pos:pos + 8], "<u4")
         pos += 8
         extra = None
-        if kind >= 3:
-            st, tgt = np.frombuffer(raw[pos:pos + 8], "<u4")
-            al, ga = np.frombuffer(raw[pos + 8:pos + 16], "<f4")
-            extra = (int(st), int(tgt), float(al), float(ga))
-            pos += 16
-        dt = (LPJOB, AJOB, BJOB, GJOB, GJOB, GJOB)[kind]
+        dt = (LPJOB, AJOB, BJOB)[kind]
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
         launches.append((int(kind), jobs, extra))
@@ -122,112 +104,31 @@ def _fan_taps(n):
     return out
 
 
-def _g_basis(s, T, i):
-    if s == 1:
-        return np.ones_like(i), np.zeros_like(i), np.zeros_like(i), np.ones_like(i)
-    if s == 2:
-        one = np.ones_like(i)
-        return one, one, np.where(T == 0, 1, -1), np.where(T == 0, -1, 1)
-    q = 2 ** (s - 2)
-    c = T == 0
-    return (np.where(c, q, -2 * i), np.where(c, -2 * i, q), np.where(c, q, -2 * i - 2),
-            np.where(c, -2 * i - 2, q))
-
-
-def _g_walk(H, W, s, descend):
-    """per sample of an H x W image: stage-s parity, basis, and (descend) the child's
-    origin, family and tree index after stage s"""
-    r, c = np.mgrid[0:H, 0:W]
-    o_r, o_c = np.zeros_like(r), np.zeros_like(r)
-    T, i, cid = np.zeros_like(r), np.zeros_like(r), np.zeros_like(r)
-    for st in range(1, s + 1):
-        b0, b1, b2, b3 = _g_basis(st, T, i)
-        det = b0 * b3 - b1 * b2
-        dr, dc = r - o_r, c - o_c
-        n1, n2 = b3 * dr - b2 * dc, b0 * dc - b1 * dr
-        assert np.all(n1 % det == 0) and np.all(n2 % det == 0), "sample off its channel's lattice"
-        par = (n1 // det + n2 // det) & 1
-        if st == s and not descend:
-            return par, (b0, b1, b2, b3)
-        cid = 2 * cid + par
-        o_r, o_c = o_r + par * b0, o_c + par * b1
-        if st == 1:
-            T, i = par, np.zeros_like(par)
-        elif st == 2:
-            i = np.where(par == 1, 0, -1)
-        else:
-            i = 2 * i + par
-    return cid, o_r, o_c, T
-
-
-def _g_sums(img, T, s, target, n):
-    """first launch of a pass: diagonal sums at the samples of the other parity"""
-    H, W = img.shape
-    par, (b0, b1, b2, b3) = _g_walk(H, W, s, False)
-    r, c = np.mgrid[0:H, 0:W]
-    S = np.zeros_like(img)
-    for b, wb in _fan_taps(n):
-        u = (b + 1) // 2
-        S += wb * img[(r + u * (b0 - b2)) % H, (c + u * (b1 - b3)) % W]
-    m = par != target
-    T[m] = S[m]
-
-
-def _g_pass(img, T, s, target, alpha, gamma, n):
-    """second launch: the targets from the sums"""
-    H, W = img.shape
-    par, (b0, b1, b2, b3) = _g_walk(H, W, s, False)
-    r, c = np.mgrid[0:H, 0:W]
-    acc = np.zeros_like(img)
-    for a, wa in _fan_taps(n):
-        d1, d2 = (a - 1) // 2, (a + 1) // 2
-        acc += wa * T[(r + d1 * b0 + d2 * b2) % H, (c + d1 * b1 + d2 * b3) % W]
-    m = par == target
-    img[m] = alpha * img[m] + gamma * acc[m]
-
-
-def _g_leaf_index(J):
-    """coefficient offset (from slot0) of every sample of the job's detail image"""
-    H, W, k = int(J["H"]), int(J["W"]), int(J["k"])
-    cid, o_r, o_c, T = _g_walk(H, W, k, True)
-    r, c = np.mgrid[0:H, 0:W]
-    if k == 1:
-        a, b, w = r, c >> 1, W // 2
-    else:
-        R = np.where(T == 0, 2 ** (k - 1), 2)
-        C = np.where(T == 0, 2, 2 ** (k - 1))
-        a, b, w = (r - o_r % R) // R, (c - o_c % C) // C, W // C
-    idx = cid * ((H * W) >> k) + a * w + b
-    assert np.array_equal(np.sort(idx.ravel()), np.arange(H * W)), "the copy is not a bijection"
-    return idx
-
-
-def _stage_a_pass(img, stage, odd, alpha, gamma):
-    """One pass of DFB stage 1 or 2 over the whole periodic image, in place."""
+def _stage_a_pass(img, stage, odd, alpha, gamma, n=4):
+    """One pass of DFB stage 1 or 2 over the whole periodic image, in place (n-tap prototype)."""
     H, W = img.shape
     r, c = np.mgrid[0:H, 0:W]
+    taps = _fan_taps(n)
     if stage == 1:
         mask = ((r + c) & 1) == odd
-        offs = [((a + b) // 2, (a - b) // 2) for a in A4 for b in A4]
-        acc = sum(BT[t // 4] * BT[t % 4] * np.roll(img, (-dy, -dx), axis=(0, 1)) for t, (dy, dx) in enumerate(offs))
+        acc = sum(wa * wb * np.roll(img, (-((a + b) // 2), -((a - b) // 2)), axis=(0, 1))
+                  for a, wa in taps for b, wb in taps)
     else:
         mask = (c & 1) == odd
         fam_c = (r & 1) == (c & 1)
-        acc_c = sum(BT[ia] * BT[ib] * np.roll(img, (-a, -b), axis=(0, 1))
-                    for ia, a in enumerate(A4) for ib, b in enumerate(A4))
-        acc_r = sum(BT[ia] * BT[ib] * np.roll(img, (-b, -a), axis=(0, 1))
-                    for ia, a in enumerate(A4) for ib, b in enumerate(A4))
+        acc_c = sum(wa * wb * np.roll(img, (-a, -b), axis=(0, 1)) for a, wa in taps for b, wb in taps)
+        acc_r = sum(wa * wb * np.roll(img, (-b, -a), axis=(0, 1)) for a, wa in taps for b, wb in taps)
         acc = np.where(fam_c, acc_c, acc_r)
     img[mask] = alpha * img[mask] + gamma * acc[mask]
 
 
-def _rowsplit_stencil(S, i, odd_target):
+def _rowsplit_stencil(S, i, odd_target, n=4):
     acc = np.zeros_like(S)
-    for ia, a in enumerate(A4):
-        for ib, b in enumerate(A4):
+    for a, wa in _fan_taps(n):
+        for b, wb in _fan_taps(n):
             dr = (a + 1) // 2 if odd_target else (a - 1) // 2
             dc = -i * a + (b - a) // 2
-            acc += BT[ia] * BT[ib] * np.roll(S, (-dr, -dc), axis=(0, 1))
+            acc += wa * wb * np.roll(S, (-dr, -dc), axis=(0, 1))
     return acc
 
 
@@ -261,19 +162,6 @@ def _up(v, f):
 
 def _views_of(kind, J, synth, extra=None):
     """(reads, writes): lists of (name, view, rows, cols) a job touches."""
-    if kind == 3:
-        H, W = int(J["H"]), int(J["W"])
-        return [("D", J["D"], H, W), ("T", J["T"], H, W)], [("T", J["T"], H, W)]
-    if kind == 5:
-        H, W = int(J["H"]), int(J["W"])
-        D = [("D", J["D"], H, W)]
-        return D + [("T", J["T"], H, W)], D
-    if kind == 4:
-        H, W = int(J["H"]), int(J["W"])
-        lay = np.zeros(1, VIEW)[0]
-        lay["off"], lay["b"], lay["rs"], lay["cs"] = int(J["slot0"]), 1, W, 1
-        D, L = [("D", J["D"], H, W)], [("layout", lay, H, W)]     # the level's 2^k subbands, H*W elements
-        return (D, L) if extra[1] == 1 else (L, D)
     if kind == 0:
         H, W = int(J["H"]), int(J["W"])
         if not synth:
@@ -307,23 +195,7 @@ def run(mode, elems, launches, bufs):
                 rd[name] = bufs[b][idx]
                 rjob.append((ji, (b, idx)))
             out = {}
-            if kind == 3:
-                T = rd["T"].copy()
-                _g_sums(rd["D"], T, extra[0], extra[1], int(J["ntaps"]))
-                out["T"] = T
-            elif kind == 5:
-                img = rd["D"].copy()
-                _g_pass(img, rd["T"], extra[0], extra[1], extra[2], extra[3], int(J["ntaps"]))
-                out["D"] = img
-            elif kind == 4:
-                idx = _g_leaf_index(J)
-                if extra[1] == 1:
-                    lay = np.zeros(rd["D"].size)
-                    lay[idx.ravel()] = rd["D"].ravel()
-                    out["layout"] = lay.reshape(rd["D"].shape)
-                else:
-                    out["D"] = rd["layout"].ravel()[idx]
-            elif kind == 0:
+            if kind == 0:
                 X = rd["main"]
                 if not synth:
                     out["cout"] = _down(X, fa)
@@ -340,9 +212,10 @@ def run(mode, elems, launches, bufs):
                     for q in range(4):
                         img[q >> 1::2, q & 1::2] = rd["comp%d" % q]
                 stages = list(range(1, nst + 1)) if not synth else list(range(nst, 0, -1))
+                n = int(J["ntaps"])
                 for stg in stages:
-                    _stage_a_pass(img, stg, fo, a1, g1)
-                    _stage_a_pass(img, stg, 1 - fo, a2, g2)
+                    _stage_a_pass(img, stg, fo, a1, g1, n)
+                    _stage_a_pass(img, stg, 1 - fo, a2, g2, n)
                 if not synth:
                     for q in range(4):
                         out["comp%d" % q] = img[q >> 1::2, q & 1::2].copy()
@@ -352,12 +225,13 @@ def run(mode, elems, launches, bufs):
                 i = int(J["i"])
                 E, Od = (rd["pe"], rd["po"]) if not synth else (rd["c0"], rd["c1"])
                 E, Od = E.copy(), Od.copy()
+                n = int(J["ntaps"])
                 if fo:
-                    Od = a1 * Od + g1 * _rowsplit_stencil(E, i, True)
-                    E = a2 * E + g2 * _rowsplit_stencil(Od, i, False)
+                    Od = a1 * Od + g1 * _rowsplit_stencil(E, i, True, n)
+                    E = a2 * E + g2 * _rowsplit_stencil(Od, i, False, n)
                 else:
-                    E = a1 * E + g1 * _rowsplit_stencil(Od, i, False)
-                    Od = a2 * Od + g2 * _rowsplit_stencil(E, i, True)
+                    E = a1 * E + g1 * _rowsplit_stencil(Od, i, False, n)
+                    Od = a2 * Od + g2 * _rowsplit_stencil(E, i, True, n)
                 if not synth:
                     out["c0"], out["c1"] = E, Od
                 else:
@@ -368,7 +242,6 @@ def run(mode, elems, launches, bufs):
                 results.append((b, idx, out[name]))
                 wjob.append((ji, b, idx))
         # no job writes an element that another job of the same launch reads or writes
-        # (a plain DFB pass reads and writes its own image: in place, by parity)
         for b in set(x[1] for x in wjob):
             w_idx = [(ji, ix.ravel()) for ji, wb, ix in wjob if wb == b]
             allw = np.concatenate([ix for _, ix in w_idx])

@@ -183,17 +183,16 @@ def test_scale_tables_refuse_a_scale_beyond_every_stream():
     assert lib.cvc_debug_scale_tables(prms, 2, 2, None, 0, ctypes.byref(used)) == 3
 
 
-# ------------------------------------------ longer DFB prototypes (plain path)
+# ------------------------------------------------- longer DFB prototypes
 @pytest.mark.parametrize("taps", [6, 8])
 @pytest.mark.parametrize("w,h,Lv,k", [(176, 144, 3, [3, 2, 2]), (64, 48, 2, [1, 0]), (128, 96, 3, [4, 3, 1])])
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_longer_prototype_plan_tables_compute_the_transform(taps, w, h, Lv, k, mode):
-    """the plain DFB launches (a lifting pass per launch, then the copy to the layout)
-    executed with their semantics reproduce the oracle's transform with that prototype"""
+    """the tile launches of a longer prototype, executed with their semantics (the
+    prototype's taps), reproduce the oracle's transform with that prototype"""
     prm = L.params(w, h, Lv, k, 8, 1, 0.0, 8, dfb_taps=taps)
     elems, launches = E.tables(mode, params=prm)
-    kinds = {kd for kd, _, _ in launches}
-    assert {3, 4} <= kinds and not ({1, 2} & kinds)          # no tile kernel for these planes
+    assert all(int(J["ntaps"]) == taps for kd, jobs, _ in launches if kd in (1, 2) for J in jobs)
     oc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 8)
     dims = [(oc.Hp, oc.Wp), (oc.Hcp, oc.Wcp), (oc.Hcp, oc.Wcp)]
     ns = [O.layout(a, b, Lv, k)["total"] for a, b in dims]
@@ -217,13 +216,12 @@ def test_longer_prototype_plan_tables_compute_the_transform(taps, w, h, Lv, k, m
 
 
 def test_mixed_prototype_codec_plans_in_bounds():
-    """a batch mixing prototypes: tile and plain launches side by side, in bounds, at 1080p"""
+    """a batch mixing prototypes: launches of each length side by side, in bounds, at 1080p"""
     prms = (L.Params * 3)(L.params(1920, 1080, 5, [5, 4, 4, 3, 3], 8, 1, 0.0, 10, dfb_taps=6),
                           L.params(1920, 1080, 5, [5, 4, 4, 3, 3], 8, 1, 0.0, 10),
                           L.params(640, 480, 4, [4, 3, 3, 2], 8, 1, 0.0, 10, dfb_taps=8))
     import ctypes
     for mode in (0, 1):
         elems, launches = E.tables(mode, params=ctypes.cast(prms, ctypes.POINTER(L.Params)).contents, batch=3)
-        kinds = {kd for kd, _, _ in launches}
-        assert {1, 2, 3, 4} <= kinds
+        assert {int(J["ntaps"]) for kd, jobs, _ in launches if kd in (1, 2) for J in jobs} == {4, 6, 8}
         E.check_only(elems, launches, mode)
