@@ -1,5 +1,6 @@
 """Longer PKVA prototypes on the GPU (6- and 8-tap Lagrange half-band DFB,
-the plain per-sample path) against the oracle, through the C ABI.
+the tile kernels instantiated for their length) against the oracle, through
+the C ABI.
 
 Bar (as for the 4-tap tile kernels):
   - the transform within 1e-4 per level on the 0-255 scale, the inverse of
