@@ -236,16 +236,29 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
     const int total = (int)P.total, low_n = (int)P.low_n, low_w = P.low_w;
     const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
     const float* cp = coef + P.coef_off;
+    // every load of the thread first, so that they are in flight together
+    float cv[ELEM_PER_THREAD], ca[ELEM_PER_THREAD];
+    int pv[ELEM_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < ELEM_PER_THREAD; k++) {
+        const int le = base + k * ELEM_THREADS;
+        cv[k] = ca[k] = 0.f;
+        pv[k] = 0;
+        if (le >= total) continue;
+        cv[k] = cp[le];
+        if (!key) pv[k] = cur[P.coef_off + le];
+        else if (le < low_n && le >= low_w) ca[k] = cp[le - low_w];
+    }
 #pragma unroll
     for (int k = 0; k < ELEM_PER_THREAD; k++) {
         const int le = base + k * ELEM_THREADS;
         if (le >= total) break;
         const long long e = P.coef_off + le;
         const bool low = le < low_n;
-        const int q = quant(cp[le], low, qp, err);
+        const int q = quant(cv[k], low, qp, err);
         int r;
-        if (!key) r = q - cur[e];
-        else if (low && le >= low_w) r = q - quant(cp[le - low_w], true, qp, err);
+        if (!key) r = q - pv[k];
+        else if (low && le >= low_w) r = q - quant(ca[k], true, qp, err);
         else r = q;
         nxt[e] = (int16_t)q;
         if (!mc) res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
