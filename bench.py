@@ -19,6 +19,7 @@ shards by stream; there is no exchange step), so scaling is weak.
 workload (a horizontal band of the same frames and decomposition).
 """
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -88,8 +89,12 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of SM clocks and throttle reasons around the timed region.
+    Started before the warm-up steps (nvidia-smi takes a few hundred ms to its first
+    sample); every sample carries its timestamp, and the report keeps those taken
+    between begin() and end(), or, for a region shorter than the sampling period,
+    the samples adjacent to it ("window": "adjacent")."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -97,6 +102,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -109,29 +115,55 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
+
+    def _rows(self):
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                continue
+            rows.append((ts, parts[1:]))
+        return rows
+
     def stop(self):
         if self.proc is None:
             return None
+        # wait (at most 2 s) for a sample after the region, so that a short region has a neighbour
+        deadline = time.time() + 2.0
+        while self.t1 is not None and time.time() < deadline and not any(ts >= self.t1 for ts, _ in self._rows()):
+            time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
+        window = "timed region"
+        if not inside:
+            before = [r for ts, r in rows if self.t0 is not None and ts < self.t0][-1:]
+            after = [r for ts, r in rows if self.t1 is not None and ts > self.t1][:1]
+            inside = before + after or [rows[-1][1]]
+            window = "adjacent"
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "window": window}
 
 
 def stage_bytes(info, tokens):
@@ -613,16 +645,20 @@ def main():
         res = batch.step(3, rgb=frames_at(i), rgb_out=outs_rgb)
         batch_bytes[0] += sum(r["out_len"] for r in res)
 
-    for i in range(args.warmup):
-        batch_step(i)
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()
+    for i in range(args.warmup):
+        batch_step(i)
     launches0 = kernel_launches()
+    if clocks:
+        clocks.begin()
     t_wall = time.perf_counter()
     value, tot_ms, _ = combine_ranks(timed(lambda i: batch_step(args.warmup + i), args.steps), args.steps * B,
                                      dist, dev)
     t_wall = time.perf_counter() - t_wall
+    if clocks:
+        clocks.end()
     launches = kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
 
