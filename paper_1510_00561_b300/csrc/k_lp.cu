@@ -49,6 +49,24 @@ __device__ __forceinline__ void lp_cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// stage the MN x MN main tile at (ty0, tx0) (periodic): a warp per row, lanes along it;
+// a tile whose columns do not wrap takes no per-element index arithmetic
+template <int MN>
+__device__ __forceinline__ void lp_stage(float* s_main, const float* mainp, int mrs, int ty0, int tx0, int H, int W) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const bool inner = tx0 >= 0 && tx0 + MN <= W;
+    for (int r = warp; r < MN; r += nwarp) {
+        const float* row = mainp + (long long)wrap_idx(ty0 + r, H) * mrs;
+        float* dst = s_main + r * MN;
+        if (inner) {
+            const float* src = row + tx0;
+            for (int c = lane; c < MN; c += 32) lp_cp_async4(dst + c, src + c);
+        } else {
+            for (int c = lane; c < MN; c += 32) lp_cp_async4(dst + c, row + wrap_idx(tx0 + c, W));
+        }
+    }
+}
+
 template <int RA>
 __device__ __forceinline__ float tap_a(int t) { return RA == 4 ? c_h[t + 4] : c_g[t + 3]; }
 template <int RS>
@@ -79,11 +97,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     const float* mainp = B.p[J.main.b] + J.main.off;
     const int mrs = J.main.rs;
 
-    for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
-        int r = i / MN, c = i - r * MN;
-        int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
-        lp_cp_async4(&s_main[i], mainp + (long long)y * mrs + x);
-    }
+    lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
     __syncthreads();
     // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]
@@ -227,11 +241,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
     const float* mainp = B.p[J.main.b] + J.main.off;
     const int mrs = J.main.rs;
-    for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
-        int r = i / MN, c = i - r * MN;
-        int y = wrap_idx(y0 + Y0 + r, H), x = wrap_idx(x0 + Y0 + c, W);
-        lp_cp_async4(&s_main[i], mainp + (long long)y * mrs + x);
-    }
+    lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
     __syncthreads();
     // Every pass computes two outputs per thread with paired instructions.
