@@ -26,6 +26,16 @@ struct Bases {
     float* p[N_BASES];
 };
 
+// Base pointer b, chosen by selects: a run-time index into a by-value kernel
+// parameter makes the compiler copy the whole parameter to the stack and
+// every thread read it back from local memory.
+__device__ __forceinline__ float* base_ptr(const Bases& B, int b) {
+    float* p = B.p[0];
+#pragma unroll
+    for (int k = 1; k < N_BASES; k++) p = b == k ? B.p[k] : p;
+    return p;
+}
+
 // Strided 2-D view: element (u, v) is at base[b] + off + u*rs + v*cs.
 struct View {
     long long off;

@@ -976,7 +976,7 @@ __global__ void k_dec_scatter_b(const SDesc* __restrict__ sd, const SCall* __res
 }
 
 // ------------------------------------------------------ exclusive scans
-constexpr int SCAN_CHUNK = 2048;
+constexpr int SCAN_CHUNK = 2048, SCAN_THREADS = 256;
 
 __device__ __forceinline__ uint32_t block_reduce(uint32_t v, uint32_t* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1032,19 +1032,20 @@ __global__ void k_scan_sums(uint32_t* sums, int nb) {
 }
 
 // each block scans its range in sub-chunks of SCAN_CHUNK (8 values per thread)
-__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t n_host, const uint32_t* d_n,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __restrict__ in, uint32_t n_host, const uint32_t* d_n,
                              const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_carry;
     const uint32_t n = d_n ? *d_n : n_host;
     const uint32_t chunk = scan_chunk(n, d_n);
     const uint32_t base = blockIdx.x * chunk, end = min(base + chunk, n);
-    const int per = SCAN_CHUNK / blockDim.x;
+    constexpr int per = SCAN_CHUNK / SCAN_THREADS;   // a compile-time count keeps loc[] in registers
     if (threadIdx.x == 0) s_carry = sums[blockIdx.x];
     __syncthreads();
     for (uint32_t sub = base; sub < end; sub += SCAN_CHUNK) {
-        uint32_t loc[16];
+        uint32_t loc[per];
         uint32_t tsum = 0;
+#pragma unroll
         for (int k = 0; k < per; k++) {
             uint32_t i = sub + threadIdx.x * per + k;
             loc[k] = i < end ? in[i] : 0;
@@ -1067,6 +1068,7 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t n_host, c
         }
         __syncthreads();
         uint32_t excl = s_carry + x - tsum + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0);
+#pragma unroll
         for (int k = 0; k < per; k++) {
             uint32_t i = sub + threadIdx.x * per + k;
             if (i < end) out[i] = excl;
@@ -1084,7 +1086,7 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t n, uint32_t* out, uint32
     if (nb == 0) nb = 1;
     k_scan_reduce<<<nb, 256, 0, st>>>(in, n, nullptr, tmp);
     k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, 256, 0, st>>>(in, n, nullptr, tmp, out);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, n, nullptr, tmp, out);
     return cudaGetLastError();
 }
 
@@ -1094,7 +1096,7 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, const uint32_t* d_n, uint32_t
     if (nb < 1) nb = 1;
     k_scan_reduce<<<nb, 256, 0, st>>>(in, 0, d_n, tmp);
     k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, 256, 0, st>>>(in, 0, d_n, tmp, out);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, 0, d_n, tmp, out);
     return cudaGetLastError();
 }
 

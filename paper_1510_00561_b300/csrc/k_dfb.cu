@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     const int cu0 = (y0 - HALO) / 2, cv0 = (x0 - HALO) / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!SYN) {
-        const float* Dp = B.p[J.D.b] + J.D.off;
+        const float* Dp = base_ptr(B, J.D.b) + J.D.off;
         const bool inner = x0 - HALO >= 0 && x0 - HALO + SA <= W;   // no column wrap in this tile
         for (int r = warp; r < SA; r += 8) {
             const float* row = Dp + (long long)wrapd(y0 - HALO + r, H) * J.D.rs;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     } else {
         for (int q = 0; q < 4; q++) {
             const View& V = J.comp[q];
-            const float* P = B.p[V.b] + V.off;
+            const float* P = base_ptr(B, V.b) + V.off;
             if (V.cs == 1) {
                 // row-major channel: plane row u is a run of array row cu
                 const bool inner = cv0 >= 0 && cv0 + PA <= W2;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     if (!SYN) {
         for (int q = 0; q < 4; q++) {
             const View& V = J.comp[q];
-            float* P = B.p[V.b] + V.off;
+            float* P = base_ptr(B, V.b) + V.off;
             const bool trans = V.cs != 1;
             for (int k = threadIdx.x; k < T2 * T2; k += blockDim.x) {
                 int a = k / T2, b = k - a * T2;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
             }
         }
     } else {
-        float* Do = B.p[J.D.b] + J.D.off;
+        float* Do = base_ptr(B, J.D.b) + J.D.off;
         for (int k = threadIdx.x; k < DFBA_TILE * DFBA_TILE; k += blockDim.x) {
             int r = k / DFBA_TILE, c = k - r * DFBA_TILE;
             int y = y0 + r, x = x0 + c;
@@ -409,14 +409,15 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int fo = pp.first_odd;
     // the first-updated coset (odd if fo) sits one float to the right
-    float* arr[2] = {sE + (fo ? 0 : 1), sO + (fo ? 1 : 0)};
+    float* const arrE = sE + (fo ? 0 : 1);
+    float* const arrO = sO + (fo ? 1 : 0);
     // inputs: analysis reads the parent's cosets, synthesis the children.
     // Smem row r <-> coset row t0 - R + r; smem column x <-> sheared column c0 - 2R + x,
     // i.e. array column (c0 - 2R + x - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
     for (int par = 0; par < 2; par++) {
         const View V = par ? (SYN ? J.c1 : J.po) : (SYN ? J.c0 : J.pe);
-        const float* P = B.p[V.b] + V.off;
-        float* S = arr[par];
+        const float* P = base_ptr(B, V.b) + V.off;
+        float* S = par ? arrO : arrE;
         if (V.cs == 1) {
             for (int r = warp; r < RB; r += nwarp) {
                 const int tu = t0 - R + r;
@@ -450,8 +451,8 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
     // pass 1 updates F on columns [R, CB - R), which covers what pass 2 reads; pass 2
     // updates S on the tile [R, R + ROWS) x [2R, CB - 2R).  Pass-1 row sums sit at the
     // base of sH, pass-2 row sums one float to the right.
-    float* F = arr[fo ? 1 : 0];
-    float* Sx = arr[fo ? 0 : 1];
+    float* F = fo ? arrO : arrE;
+    float* Sx = fo ? arrE : arrO;
     constexpr int NP1 = (CB - 2 * R) / 2, NH1 = (CB - R + 1) / 2, NP2 = COLS / 2, NH2 = (CB - 3 * R + 1) / 2;
     static_assert(R + 2 * NP1 == CB - R && 2 * R + 2 * NP2 == CB - 2 * R, "pass windows");
     constexpr int ROWS = DFBB_ROWS;
@@ -477,8 +478,8 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
     const int ncol = min(COLS, C - c0);
     for (int par = 0; par < 2; par++) {
         const View V = par ? (SYN ? J.po : J.c1) : (SYN ? J.pe : J.c0);
-        float* P = B.p[V.b] + V.off;
-        const float* S = arr[par];
+        float* P = base_ptr(B, V.b) + V.off;
+        const float* S = par ? arrO : arrE;
         if (V.cs == 1) {
             for (int rr = warp; rr < DFBB_ROWS; rr += nwarp) {
                 const int t = t0 + rr;

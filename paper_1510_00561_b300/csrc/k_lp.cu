@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     const int y0 = ty * T, x0 = tx * T;
     const int m0 = y0 / 2, n0 = x0 / 2;
     const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
-    const float* mainp = B.p[J.main.b] + J.main.off;
+    const float* mainp = base_ptr(B, J.main.b) + J.main.off;
     const int mrs = J.main.rs;
 
     lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     }
     __syncthreads();
     // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI]
-    const float* cinp = SYNTH ? B.p[J.cin.b] + J.cin.off : nullptr;
+    const float* cinp = SYNTH ? base_ptr(B, J.cin.b) + J.cin.off : nullptr;
     for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
         int m = i / VN, n = i - m * VN;
         float acc = 0.f;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     __syncthreads();
     if (!SYNTH) {
         // interior 32 x 32 of v is this tile's share of the lowpass output
-        float* coutp = B.p[J.cout.b] + J.cout.off;
+        float* coutp = base_ptr(B, J.cout.b) + J.cout.off;
         for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
             int m = i / (T / 2), n = i - m * (T / 2);
             int gm = m0 + m, gn = n0 + n;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     }
     __syncthreads();
     // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main input
-    float* outp = B.p[J.out.b] + J.out.off;
+    float* outp = base_ptr(B, J.out.b) + J.out.off;
     for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
         const int p = i / T, x = i - p * T;
         const float* ar = s_a + (p - MLO) * T + x;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     const int y0 = ty * T, x0 = tx * T;
     const int m0 = y0 / 2, n0 = x0 / 2;
     const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
-    const float* mainp = B.p[J.main.b] + J.main.off;
+    const float* mainp = base_ptr(B, J.main.b) + J.main.off;
     const int mrs = J.main.rs;
     lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     }
     __syncthreads();
     // decimating column pass over row pairs (ma, mb), then e = cin - down(main) (normalised float-float)
-    const float* cinp = B.p[J.cin.b] + J.cin.off;
+    const float* cinp = base_ptr(B, J.cin.b) + J.cin.off;
     for (int i = threadIdx.x; i < NM * VN; i += blockDim.x) {
         const int q = i / VN, n = i - q * VN;
         const int ma = 2 * q, mb = min(2 * q + 1, VN - 1);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     }
     __syncthreads();
     // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input
-    float* outp = B.p[J.out.b] + J.out.off;
+    float* outp = base_ptr(B, J.out.b) + J.out.off;
     for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
         const int p = i / (T / 2), w = i - p * (T / 2);
         const int x = 2 * w;
