@@ -49,15 +49,15 @@ __device__ __forceinline__ void lp_cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// stage the MN x MN main tile at (ty0, tx0) (periodic): a warp per row, lanes along it;
-// a tile whose columns do not wrap takes no per-element index arithmetic
-template <int MN>
+// stage the MN x MN main tile at (ty0, tx0) (periodic) with row stride MNS: a warp per
+// row, lanes along it; a tile whose columns do not wrap takes no per-element index arithmetic
+template <int MN, int MNS = MN>
 __device__ __forceinline__ void lp_stage(float* s_main, const float* mainp, int mrs, int ty0, int tx0, int H, int W) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const bool inner = tx0 >= 0 && tx0 + MN <= W;
     for (int r = warp; r < MN; r += nwarp) {
         const float* row = mainp + (long long)wrap_idx(ty0 + r, H) * mrs;
-        float* dst = s_main + r * MN;
+        float* dst = s_main + r * MNS;
         if (inner) {
             const float* src = row + tx0;
             for (int c = lane; c < MN; c += 32) lp_cp_async4(dst + c, src + c);
@@ -225,11 +225,14 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
     constexpr int Y0 = 2 * MLO - RA;
     constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
-    extern __shared__ float sm[];
-    float* s_main = sm;                 // MN * MN
-    float* s_ah = s_main + MN * MN;     // NA
-    float* s_al = s_ah + NA;            // NA
-    float* s_vh = s_al + NA;            // VN * VN
+    // the main tile's rows have an even stride and the float-float arrays start on
+    // 16-byte boundaries, so that the passes below move pairs and quadruples
+    constexpr int MNS = MN + (MN & 1), OA = (MN * MNS + 3) & ~3, NA4 = (NA + 3) & ~3;
+    extern __shared__ __align__(16) float sm[];
+    float* s_main = sm;                 // MN rows of MNS
+    float* s_ah = s_main + OA;          // NA
+    float* s_al = s_ah + NA4;           // NA
+    float* s_vh = s_al + NA4;           // VN * VN
     float* s_vl = s_vh + VN * VN;       // VN * VN
 
     const int jid = block_job[blockIdx.x];
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
     const float* mainp = base_ptr(B, J.main.b) + J.main.off;
     const int mrs = J.main.rs;
-    lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
+    lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
     __syncthreads();
     // Every pass computes two outputs per thread with paired instructions.
@@ -252,11 +255,22 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
     for (int i = threadIdx.x; i < NR * VN; i += blockDim.x) {
         const int q = i / VN, n = i - q * VN;
         const int ra = 2 * q, rb = min(2 * q + 1, MN - 1);
-        const float* rowa = s_main + ra * MN + 2 * n + RA;
-        const float* rowb = s_main + rb * MN + 2 * n + RA;
+        // the window x[2n + j], j = 0 .. 2 RA, of both rows (even offsets: RA pairs and one more)
+        const float* wa = s_main + ra * MNS + 2 * n;
+        const float* wb = s_main + rb * MNS + 2 * n;
+        float va[2 * RA + 1], vb[2 * RA + 1];
+#pragma unroll
+        for (int j = 0; j < RA; j++) {
+            const float2 pa = *reinterpret_cast<const float2*>(wa + 2 * j);
+            const float2 pb = *reinterpret_cast<const float2*>(wb + 2 * j);
+            va[2 * j] = pa.x; va[2 * j + 1] = pa.y;
+            vb[2 * j] = pb.x; vb[2 * j + 1] = pb.y;
+        }
+        va[2 * RA] = wa[2 * RA];
+        vb[2 * RA] = wb[2 * RA];
         float2 hi = zero2, lo = zero2;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++) ff2_fma(hi, lo, tap_a<RA>(b), make_float2(rowa[-b], rowb[-b]), zero2);
+        for (int b = -RA; b <= RA; b++) ff2_fma(hi, lo, tap_a<RA>(b), make_float2(va[RA - b], vb[RA - b]), zero2);
         s_ah[ra * VN + n] = hi.x;
         s_al[ra * VN + n] = lo.x;
         if (rb != ra) {
@@ -308,10 +322,8 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
                 ff2_fma(oh, ol, tap_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]), make_float2(s_vl[k], s_vl[k + 1]));
             }
         }
-        float* ah = s_ah + m * T + 4 * w;
-        float* al = s_al + m * T + 4 * w;
-        ah[0] = eh.x; ah[1] = oh.x; ah[2] = eh.y; ah[3] = oh.y;
-        al[0] = el.x; al[1] = ol.x; al[2] = el.y; al[3] = ol.y;
+        *reinterpret_cast<float4*>(s_ah + m * T + 4 * w) = make_float4(eh.x, oh.x, eh.y, oh.y);
+        *reinterpret_cast<float4*>(s_al + m * T + 4 * w) = make_float4(el.x, ol.x, el.y, ol.y);
     }
     __syncthreads();
     // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input
@@ -325,10 +337,12 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - (t / 2) * T;
-                ff2_fma(eh, el, tap_s<RS>(t), make_float2(s_ah[k], s_ah[k + 1]), make_float2(s_al[k], s_al[k + 1]));
+                ff2_fma(eh, el, tap_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                        *reinterpret_cast<const float2*>(s_al + k));
             } else {
                 const int k = kb + ((1 - t) / 2) * T;
-                ff2_fma(oh, ol, tap_s<RS>(t), make_float2(s_ah[k], s_ah[k + 1]), make_float2(s_al[k], s_al[k + 1]));
+                ff2_fma(oh, ol, tap_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                        *reinterpret_cast<const float2*>(s_al + k));
             }
         }
         const int gx = x0 + x;
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
             const int y = 2 * p + h, gy = y0 + y;
             if (gy >= H) continue;
             float2 hi = h ? oh : eh, lo = h ? ol : el;
-            const float* mrow = s_main + (y - Y0) * MN + (x - Y0);
+            const float* mrow = s_main + (y - Y0) * MNS + (x - Y0);
             ff2_add(hi, lo, make_float2(mrow[0], mrow[1]));
             const float2 o = __fadd2_rn(hi, lo);
             float* orow = outp + (long long)gy * J.out.rs;
@@ -355,7 +369,8 @@ constexpr size_t synth_ff_smem() {
     constexpr int VN = MHI - MLO + 1;
     constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
     constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
-    return sizeof(float) * (size_t)(MN * MN + 2 * NA + 2 * VN * VN);
+    constexpr int MNS = MN + (MN & 1), OA = (MN * MNS + 3) & ~3, NA4 = (NA + 3) & ~3;
+    return sizeof(float) * (size_t)(OA + 2 * NA4 + 2 * VN * VN);
 }
 
 cudaError_t lp_prepare() {
