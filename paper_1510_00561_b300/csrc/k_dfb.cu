@@ -86,7 +86,7 @@ __host__ __device__ constexpr int pl1(int hi, int p) { return (hi - 1 - p) / 2 +
 //     D[p] = sum_m bt[m] x[p + (m, -m)] at the source coset's points, then
 //     acc(t) = sum_n bt[n] D[t + (n - R, n)].
 //   Stage 2 (taps at (a, b) in both families): row sums along the target's
-//     source plane, then sums down its columns.
+//     source plane, then sums down its columns, the row sums kept in registers.
 // A pass over image-local [lo, hi)^2, lo = R n, reads the region the previous
 // pass left valid, [lo - R, hi + R)^2.  Consecutive threads take consecutive
 // elements of a region row.
@@ -149,39 +149,6 @@ __device__ __forceinline__ void s1_target(float* planes, const float* tmp, float
     });
 }
 
-// stage 2, target class (tr, tc) reads class (1-tr, 1-tc) at (u + ky + tr - NT/2, v + kx + tc - NT/2):
-// row sums into tmp plane tr, then sums down the columns
-template <int NT, int N, bool ODD, int K>
-__device__ __forceinline__ void s2_rowsum(const float* planes, float* tmp) {
-    using G = AGeo<NT>;
-    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
-    constexpr int tr = K, tc = ODD ? 1 : 0;
-    constexpr int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
-    constexpr int os = (2 * (1 - tr) + (1 - tc)) * G::PA * G::PAS + (tc - NT / 2);
-    float* Rs = tmp + tr * G::PA * G::PAS;
-    region_walk<NT, u0 + tr - NT / 2, u1 + tr - NT / 2 + NT - 1, v0, v1>([&](int off) {
-        float acc = fan_tap(NT, 0) * planes[off + os];
-#pragma unroll
-        for (int kx = 1; kx < NT; kx++) acc = fmaf(fan_tap(NT, kx), planes[off + os + kx], acc);
-        Rs[off] = acc;
-    });
-}
-
-template <int NT, int N, bool ODD, int K>
-__device__ __forceinline__ void s2_target(float* planes, const float* tmp, float alpha, float gamma) {
-    using G = AGeo<NT>;
-    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
-    constexpr int tr = K, tc = ODD ? 1 : 0;
-    constexpr int oh = tr * G::PA * G::PAS + (tr - NT / 2) * G::PAS;
-    float* T = planes + (2 * tr + tc) * G::PA * G::PAS;
-    region_walk<NT, pl0(lo, tr), pl1(hi, tr), pl0(lo, tc), pl1(hi, tc)>([&](int off) {
-        float acc = fan_tap(NT, 0) * tmp[off + oh];
-#pragma unroll
-        for (int ky = 1; ky < NT; ky++) acc = fmaf(fan_tap(NT, ky), tmp[off + oh + ky * G::PAS], acc);
-        T[off] = fmaf(alpha, T[off], gamma * acc);
-    });
-}
-
 template <int NT, int N, bool ODD>
 __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alpha, float gamma) {
     // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones
@@ -194,14 +161,60 @@ __device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alp
     __syncthreads();
 }
 
+// stage 2, target class (tr, tc), which reads class (1-tr, 1-tc) at
+// (u + ky + tr - NT/2, v + kx + tc - NT/2), with the row sums kept in
+// registers: thread t owns column v of the target region and a run of L
+// consecutive rows; it forms each source row sum once (the NT - 1 rows above
+// its run once more) and keeps the NT its current target needs, so nothing
+// goes through the scratch planes.  Each row sum accumulates its taps in kx
+// order and each target its row sums in ky order, as a staged evaluation does.
+template <int NT>
+__device__ __forceinline__ float s2_row(const float* p) {
+    float acc = fan_tap(NT, 0) * p[0];
+#pragma unroll
+    for (int kx = 1; kx < NT; kx++) acc = fmaf(fan_tap(NT, kx), p[kx], acc);
+    return acc;
+}
+
+template <int NT, int N, bool ODD, int K>
+__device__ __forceinline__ void s2_fused(float* planes, float alpha, float gamma) {
+    using G = AGeo<NT>;
+    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
+    constexpr int tr = K, tc = ODD ? 1 : 0;
+    constexpr int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
+    constexpr int NV = v1 - v0, NU = u1 - u0, S = 256 / NV, L = (NU + S - 1) / S;
+    constexpr int PAS = G::PAS, PL = G::PA * G::PAS;
+    // source rows u0 + tr - NT/2 .. u1 + tr - NT/2 + NT - 2, columns v0 + tc - NT/2 .. v1 + tc - NT/2 + NT - 2
+    static_assert(u0 + tr - NT / 2 >= 0 && u1 + tr - NT / 2 + NT - 1 <= G::PA, "source rows inside the plane");
+    static_assert(v0 + tc - NT / 2 >= 0 && v1 + tc - NT / 2 + NT - 1 <= G::PA, "source columns inside the plane");
+    static_assert(NV >= 1 && NV <= 256 && S * L >= NU, "runs cover the region");
+    const int t = threadIdx.x;
+    if (t >= S * NV) return;
+    const int v = v0 + t % NV;
+    const int ua = u0 + (t / NV) * L, ub = min(ua + L, u1);
+    if (ua >= ub) return;
+    float* T = planes + (2 * tr + tc) * PL + ua * PAS + v;
+    const float* src = planes + (2 * (1 - tr) + (1 - tc)) * PL + (ua + tr - NT / 2) * PAS + v + tc - NT / 2;
+    float w[NT];
+#pragma unroll
+    for (int j = 0; j < NT - 1; j++) w[j] = s2_row<NT>(src + j * PAS);
+    src += (NT - 1) * PAS;
+    for (int u = ua; u < ub; u++, T += PAS, src += PAS) {
+        w[NT - 1] = s2_row<NT>(src);
+        float acc = fan_tap(NT, 0) * w[0];
+#pragma unroll
+        for (int ky = 1; ky < NT; ky++) acc = fmaf(fan_tap(NT, ky), w[ky], acc);
+        *T = fmaf(alpha, *T, gamma * acc);
+#pragma unroll
+        for (int j = 0; j < NT - 1; j++) w[j] = w[j + 1];
+    }
+}
+
 template <int NT, int N, bool ODD>
-__device__ __forceinline__ void dfba_stage2(float* planes, float* tmp, float alpha, float gamma) {
-    // targets: {11, 01} (odd) or {00, 10}
-    s2_rowsum<NT, N, ODD, 0>(planes, tmp);
-    s2_rowsum<NT, N, ODD, 1>(planes, tmp);
-    __syncthreads();
-    s2_target<NT, N, ODD, 0>(planes, tmp, alpha, gamma);
-    s2_target<NT, N, ODD, 1>(planes, tmp, alpha, gamma);
+__device__ __forceinline__ void dfba_stage2(float* planes, float alpha, float gamma) {
+    // targets: {11, 01} (odd) or {00, 10}; each reads only the other class of its row parity
+    s2_fused<NT, N, ODD, 0>(planes, alpha, gamma);
+    s2_fused<NT, N, ODD, 1>(planes, alpha, gamma);
     __syncthreads();
 }
 
@@ -212,12 +225,12 @@ __device__ __forceinline__ void dfba_passes(float* planes, float* tmp, int nst, 
         dfba_stage1<NT, 1, FO>(planes, tmp, pp.a1, pp.g1);
         dfba_stage1<NT, 2, !FO>(planes, tmp, pp.a2, pp.g2);
         if (nst == 2) {
-            dfba_stage2<NT, 3, FO>(planes, tmp, pp.a1, pp.g1);
-            dfba_stage2<NT, 4, !FO>(planes, tmp, pp.a2, pp.g2);
+            dfba_stage2<NT, 3, FO>(planes, pp.a1, pp.g1);
+            dfba_stage2<NT, 4, !FO>(planes, pp.a2, pp.g2);
         }
     } else if (nst == 2) {
-        dfba_stage2<NT, 1, FO>(planes, tmp, pp.a1, pp.g1);
-        dfba_stage2<NT, 2, !FO>(planes, tmp, pp.a2, pp.g2);
+        dfba_stage2<NT, 1, FO>(planes, pp.a1, pp.g1);
+        dfba_stage2<NT, 2, !FO>(planes, pp.a2, pp.g2);
         dfba_stage1<NT, 3, FO>(planes, tmp, pp.a1, pp.g1);
         dfba_stage1<NT, 4, !FO>(planes, tmp, pp.a2, pp.g2);
     } else {
