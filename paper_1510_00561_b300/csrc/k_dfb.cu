@@ -195,18 +195,19 @@ __device__ __forceinline__ void s2_fused(float* planes, float alpha, float gamma
     if (ua >= ub) return;
     float* T = planes + (2 * tr + tc) * PL + ua * PAS + v;
     const float* src = planes + (2 * (1 - tr) + (1 - tc)) * PL + (ua + tr - NT / 2) * PAS + v + tc - NT / 2;
-    float w[NT];
+    const int cnt = ub - ua;
+    float w[L + NT - 1];   // w[j]: row sum of source row ua + tr - NT/2 + j
 #pragma unroll
     for (int j = 0; j < NT - 1; j++) w[j] = s2_row<NT>(src + j * PAS);
-    src += (NT - 1) * PAS;
-    for (int u = ua; u < ub; u++, T += PAS, src += PAS) {
-        w[NT - 1] = s2_row<NT>(src);
-        float acc = fan_tap(NT, 0) * w[0];
 #pragma unroll
-        for (int ky = 1; ky < NT; ky++) acc = fmaf(fan_tap(NT, ky), w[ky], acc);
-        *T = fmaf(alpha, *T, gamma * acc);
+    for (int k = 0; k < L; k++) {
+        if (k < cnt) {
+            w[k + NT - 1] = s2_row<NT>(src + (k + NT - 1) * PAS);
+            float acc = fan_tap(NT, 0) * w[k];
 #pragma unroll
-        for (int j = 0; j < NT - 1; j++) w[j] = w[j + 1];
+            for (int ky = 1; ky < NT; ky++) acc = fmaf(fan_tap(NT, ky), w[k + ky], acc);
+            T[k * PAS] = fmaf(alpha, T[k * PAS], gamma * acc);
+        }
     }
 }
 
