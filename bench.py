@@ -38,7 +38,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per 1080p frame of the transform stages (dram__bytes_read.sum +
 # dram__bytes_write.sum over the stage's launches), from one ncu capture of a
 # batched step of 8 streams; to be dropped when those kernels change
-DRAM_PER_FRAME = {"lp_analysis": 27.4e6, "dfb_analysis": 104.7e6, "dfb_synthesis": 105.0e6, "lp_synthesis": 28.9e6}
+DRAM_PER_FRAME = {"lp_analysis": 27.5e6, "dfb_analysis": 104.8e6, "dfb_synthesis": 105.0e6, "lp_synthesis": 29.0e6}
 
 
 def _gen_frames(seed, n, start=0):
