@@ -82,9 +82,10 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
     constexpr int Y0 = 2 * MLO - RA;  // main tile origin relative to the output tile origin
     constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
+    constexpr int MNS = MN + (MN & 1);   // even row stride: the row pass reads its windows in pairs
 
-    __shared__ float s_main[MN * MN];
-    __shared__ float s_a[NA];        // row pass (MN x VN), later expanded rows (VN x T)
+    __shared__ __align__(16) float s_main[MN * MNS];
+    __shared__ __align__(16) float s_a[NA];   // row pass (MN x VN), later expanded rows (VN x T)
     __shared__ float s_v[VN * VN];
 
     const int jid = block_job[blockIdx.x];
@@ -97,16 +98,25 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     const float* mainp = base_ptr(B, J.main.b) + J.main.off;
     const int mrs = J.main.rs;
 
-    lp_stage<MN>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
+    lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
     __syncthreads();
-    // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]
+    // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]; the window
+    // main[r][2n' + j], j = 0 .. 2 RA, starts at an even offset: RA pairs and one more
     for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
         int r = i / VN, n = i - r * VN;
-        const float* row = s_main + r * MN + 2 * n + RA;
+        const float* w = s_main + r * MNS + 2 * n;
+        float x[2 * RA + 1];
+#pragma unroll
+        for (int j = 0; j < RA; j++) {
+            const float2 pr = *reinterpret_cast<const float2*>(w + 2 * j);
+            x[2 * j] = pr.x;
+            x[2 * j + 1] = pr.y;
+        }
+        x[2 * RA] = w[2 * RA];
         float acc = 0.f;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), row[-b], acc);
+        for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), x[RA - b], acc);
         s_a[i] = acc;
     }
     __syncthreads();
@@ -144,8 +154,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
             if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), vr[-(t / 2)], ev);               // x = 2p
             else od = fmaf(tap_s<RS>(t), vr[(1 - t) / 2], od);                           // x = 2p + 1
         }
-        s_a[m * T + 2 * p] = ev;
-        s_a[m * T + 2 * p + 1] = od;
+        *reinterpret_cast<float2*>(s_a + m * T + 2 * p) = make_float2(ev, od);
     }
     __syncthreads();
     // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main input
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
             const int y = 2 * p + h, gy = y0 + y;
             if (gy < H && gx < W) {
                 const float acc = h ? od : ev;
-                const float mv = s_main[(y - Y0) * MN + (x - Y0)];
+                const float mv = s_main[(y - Y0) * MNS + (x - Y0)];
                 outp[(long long)gy * J.out.rs + gx] = SYNTH ? mv + acc : mv - acc;
             }
         }
