@@ -314,12 +314,29 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
         }
     } else {
         float* Do = base_ptr(B, J.D.b) + J.D.off;
-        for (int k = threadIdx.x; k < DFBA_TILE * DFBA_TILE; k += blockDim.x) {
-            int r = k / DFBA_TILE, c = k - r * DFBA_TILE;
-            int y = y0 + r, x = x0 + c;
-            if (y < H && x < W) {
-                int rr = HALO + r, cc = HALO + c;
-                Do[(long long)y * J.D.rs + x] = planes[(2 * (rr & 1) + (cc & 1)) * PA * PAS + (rr >> 1) * PAS + (cc >> 1)];
+        static_assert(HALO % 2 == 0 && DFBA_TILE % 2 == 0, "column pairs start on even plane columns");
+        if ((reinterpret_cast<uintptr_t>(Do) & 7) == 0 && (J.D.rs & 1) == 0) {
+            // column pairs (c, c + 1), c even: the same column of the two planes of row parity rr & 1,
+            // one 8-byte store per pair
+            constexpr int HP = DFBA_TILE / 2;
+            for (int k = threadIdx.x; k < DFBA_TILE * HP; k += blockDim.x) {
+                const int r = k / HP, c = 2 * (k - r * HP);
+                const int y = y0 + r, x = x0 + c;
+                if (y >= H || x >= W) continue;
+                const int rr = HALO + r, cc = HALO + c;
+                const float* pl = planes + 2 * (rr & 1) * PA * PAS + (rr >> 1) * PAS + (cc >> 1);
+                float* dst = Do + (long long)y * J.D.rs + x;
+                if (x + 1 < W) *reinterpret_cast<float2*>(dst) = make_float2(pl[0], pl[PA * PAS]);
+                else dst[0] = pl[0];
+            }
+        } else {
+            for (int k = threadIdx.x; k < DFBA_TILE * DFBA_TILE; k += blockDim.x) {
+                int r = k / DFBA_TILE, c = k - r * DFBA_TILE;
+                int y = y0 + r, x = x0 + c;
+                if (y < H && x < W) {
+                    int rr = HALO + r, cc = HALO + c;
+                    Do[(long long)y * J.D.rs + x] = planes[(2 * (rr & 1) + (cc & 1)) * PA * PAS + (rr >> 1) * PAS + (cc >> 1)];
+                }
             }
         }
     }
