@@ -529,8 +529,13 @@ unsigned long long cvc_kernel_launches(void);
  *     most 16,384 tiles of 64 x 64.  Larger planes return
  *     CVC_ERR_UNSUPPORTED before any device work.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     process; make that first call before any stream capture.  A
+ *     cudaDeviceReset() of that device invalidates the kept address: do not
+ *     call this entry point on a device after resetting it.
+ *   - Each call writes its job records into the array with a one-block
+ *     set-up kernel on `stream` (no host-to-device copy), then runs one
+ *     launch per pyramid level.
  *   - Every call shares the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and corrupt each other.  Calls on a
  *     single stream are ordered and safe.

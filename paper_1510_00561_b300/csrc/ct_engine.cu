@@ -280,6 +280,8 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 J.H = hj;
                 J.W = wj;
                 J.tiles_x = (wj + LP_TILE - 1) / LP_TILE;
+                J.cin_lo = mk(-1, 0, 0, 0);
+                J.out_lo = mk(-1, 0, 0, 0);
                 if (analysis) {
                     J.main = spatial_prev;
                     J.cout = low;
@@ -288,6 +290,11 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                     J.main = det;
                     J.cin = low;
                     J.out = spatial_prev;
+                    // the lowpass images between synthesis levels are float-float: the low-order
+                    // part of c_{j-1} (level j's output, hj x wj) goes to Q_j, free once the DFB
+                    // synthesis has run; level j reads that of c_j from Q_{j+1}
+                    if (j >= 2) J.out_lo = mk(B_WORK, qoff[j], wj, 1);
+                    if (j < P.L) J.cin_lo = mk(B_WORK, qoff[j + 1], wj / 2, 1);
                 }
                 lpj[j].push_back(J);
                 const int nt = (P.taps == 6 || P.taps == 8) ? P.taps : 4;

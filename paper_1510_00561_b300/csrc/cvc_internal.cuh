@@ -88,8 +88,11 @@ constexpr int dfbb_cols(int ntaps) { return 128 - 4 * (ntaps - 1); }
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)
 //   synthesis: v = cin - down(main, fa);        out = main + up(v, fs)
+// A synthesis job may carry the low-order halves of cin and out (float-float
+// lowpass images between the levels; b < 0: absent, the value is cin alone).
 struct LpJob {
     View main, cin, cout, out;  // rs = row pitch, cs = 1
+    View cin_lo, out_lo;        // synthesis only: low-order parts of cin / out
     int H, W;                   // full-resolution size of this level
     int tiles_x;
     int first_block;

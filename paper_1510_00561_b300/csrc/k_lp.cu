@@ -1,7 +1,7 @@
 // k_lp.cu -- Laplacian pyramid level kernels (§2.1, Fig. 1).
 //
 // One CTA computes a 64 x 64 full-resolution tile of one pyramid level of
-// one plane, with periodic extension.  Two kernels share one body:
+// one plane, with periodic extension:
 //   analysis:  c = down(x, fa);           d = x - up(c, fs)
 //   synthesis: e = c - down(d, fa);       x = d + up(e, fs)
 // down(., f) filters separably with f and keeps even samples; up(., f)
@@ -15,11 +15,17 @@
 // with halo, and the expanded row pass; every input element is read from
 // global memory once per tile plus the halo.
 //
-// Synthesis accumulates in float-float (error-free TwoSum / FMA-based
-// TwoProd transformations, Dekker 1971 / Knuth): the pyramid's DC gain of 2
-// per level makes coarse levels carry numbers up to 2^L * 255, and each
-// level's single-precision roundings would otherwise add ~ulp(255) to the
-// reconstruction; with compensated sums only the stored values round.
+// The forward transform and the inverse accumulate in float-float (k_lp_ff:
+// error-free TwoSum / FMA-based TwoProd transformations, Dekker 1971 /
+// Knuth): the pyramid's DC gain of 2 per level makes coarse levels carry
+// numbers up to 2^L * 255, and single-precision roundings of such numbers
+// would otherwise reach ~ulp(255) in the detail images and the
+// reconstruction.  The taps carry their low-order parts; the analysis forms
+// the detail from the unrounded lowpass, and the lowpass images passed
+// between synthesis levels are stored as (hi, lo) pairs, so that every
+// output rounds once.  The adjoint of the inverse (an analysis with the
+// filter pair swapped, whose outputs are gradients) runs in single
+// precision (k_lp_level).
 #include <mutex>
 
 #include "cvc_internal.cuh"
@@ -28,11 +34,29 @@ namespace cvc {
 
 // CDF 9/7 lowpass pair normalised to DC gain sqrt(2) (published values,
 // 12 significant digits): analysis h (taps -4..4), synthesis g (-3..3).
-__constant__ float c_h[9] = {0.037828455507f, -0.023849465020f, -0.110624404418f, 0.377402855613f,
-                             0.852698679009f,  0.377402855613f, -0.110624404418f, -0.023849465020f,
-                             0.037828455507f};
-__constant__ float c_g[7] = {-0.064538882629f, -0.040689417609f, 0.418092273222f, 0.788485616406f,
-                             0.418092273222f,  -0.040689417609f, -0.064538882629f};
+// Each tap is held as a float and, for the float-float synthesis, the float
+// nearest its remainder: the remainder matters there because a level-j
+// lowpass carries numbers up to 2^j * 255, and the taps' single-precision
+// representation error (up to 2^-25 relative) times such numbers is
+// ~ulp(255) at the coarse levels.
+#define CVC_H4 0.037828455507
+#define CVC_H3 -0.023849465020
+#define CVC_H2 -0.110624404418
+#define CVC_H1 0.377402855613
+#define CVC_H0 0.852698679009
+#define CVC_G3 -0.064538882629
+#define CVC_G2 -0.040689417609
+#define CVC_G1 0.418092273222
+#define CVC_G0 0.788485616406
+#define CVC_LO(t) ((float)((t) - (double)(float)(t)))
+__constant__ float c_h[9] = {(float)CVC_H4, (float)CVC_H3, (float)CVC_H2, (float)CVC_H1, (float)CVC_H0,
+                             (float)CVC_H1, (float)CVC_H2, (float)CVC_H3, (float)CVC_H4};
+__constant__ float c_g[7] = {(float)CVC_G3, (float)CVC_G2, (float)CVC_G1, (float)CVC_G0,
+                             (float)CVC_G1, (float)CVC_G2, (float)CVC_G3};
+__constant__ float c_hl[9] = {CVC_LO(CVC_H4), CVC_LO(CVC_H3), CVC_LO(CVC_H2), CVC_LO(CVC_H1), CVC_LO(CVC_H0),
+                              CVC_LO(CVC_H1), CVC_LO(CVC_H2), CVC_LO(CVC_H3), CVC_LO(CVC_H4)};
+__constant__ float c_gl[7] = {CVC_LO(CVC_G3), CVC_LO(CVC_G2), CVC_LO(CVC_G1), CVC_LO(CVC_G0),
+                              CVC_LO(CVC_G1), CVC_LO(CVC_G2), CVC_LO(CVC_G3)};
 
 __device__ __forceinline__ int wrap_idx(int a, int n) {
     if ((unsigned)a < (unsigned)n) return a;
@@ -71,8 +95,14 @@ template <int RA>
 __device__ __forceinline__ float tap_a(int t) { return RA == 4 ? c_h[t + 4] : c_g[t + 3]; }
 template <int RS>
 __device__ __forceinline__ float tap_s(int t) { return RS == 3 ? c_g[t + 3] : c_h[t + 4]; }
+// the taps' low-order parts
+template <int RA>
+__device__ __forceinline__ float tapl_a(int t) { return RA == 4 ? c_hl[t + 4] : c_gl[t + 3]; }
+template <int RS>
+__device__ __forceinline__ float tapl_s(int t) { return RS == 3 ? c_gl[t + 3] : c_hl[t + 4]; }
 
-template <int RA, int RS, bool SYNTH>
+// single-precision analysis tile: cout = down(main, fa); out = main - up(cout, fs)
+template <int RA, int RS>
 __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs,
                                                   const int* __restrict__ block_job, Bases B) {
     constexpr int T = LP_TILE;
@@ -121,20 +151,15 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     }
     __syncthreads();
     // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI]
-    const float* cinp = SYNTH ? base_ptr(B, J.cin.b) + J.cin.off : nullptr;
     for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
         int m = i / VN, n = i - m * VN;
         float acc = 0.f;
 #pragma unroll
         for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), s_a[(2 * m + RA - a) * VN + n], acc);
-        if (SYNTH) {
-            int gm = wrap_idx(m0 + MLO + m, Hh), gn = wrap_idx(n0 + MLO + n, Wh);
-            acc = cinp[(long long)gm * J.cin.rs + gn] - acc;
-        }
         s_v[i] = acc;
     }
     __syncthreads();
-    if (!SYNTH) {
+    {
         // interior 32 x 32 of v is this tile's share of the lowpass output
         float* coutp = base_ptr(B, J.cout.b) + J.cout.off;
         for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
@@ -175,37 +200,16 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
             if (gy < H && gx < W) {
                 const float acc = h ? od : ev;
                 const float mv = s_main[(y - Y0) * MNS + (x - Y0)];
-                outp[(long long)gy * J.out.rs + gx] = SYNTH ? mv + acc : mv - acc;
+                outp[(long long)gy * J.out.rs + gx] = mv - acc;
             }
         }
     }
 }
 
 // ------------------------------------------------- float-float helpers
-// (hi, lo) accumulators; __fadd_rn / __fmul_rn keep the compiler from
-// contracting the error-free transformations into FMAs.
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-    float s = __fadd_rn(hi, x);
-    float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-}
-// (hi, lo) += f * (xh + xl)
-__device__ __forceinline__ void ff_fma(float& hi, float& lo, float f, float xh, float xl) {
-    float p = __fmul_rn(f, xh);
-    float pe = fmaf(f, xh, -p);
-    ff_add(hi, lo, p);
-    lo = fmaf(f, xl, __fadd_rn(lo, pe));
-}
-__device__ __forceinline__ void ff_norm(float& hi, float& lo) {
-    float s = __fadd_rn(hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(s, hi));
-    hi = s;
-}
-
-// The same transformations on two independent lanes at once (paired FP32
-// instructions; each lane rounds exactly as the scalar sequence above).
+// (hi, lo) accumulators on two independent lanes at once (paired FP32
+// instructions); __fadd2_rn / __fmul2_rn keep the compiler from contracting
+// the error-free transformations into FMAs.
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ void ff2_add(float2& hi, float2& lo, float2 x) {
     const float2 s = __fadd2_rn(hi, x);
@@ -214,19 +218,32 @@ __device__ __forceinline__ void ff2_add(float2& hi, float2& lo, float2 x) {
     hi = s;
     lo = __fadd2_rn(lo, e);
 }
-__device__ __forceinline__ void ff2_fma(float2& hi, float2& lo, float f, float2 xh, float2 xl) {
+// (hi, lo) += (f + fl) * (xh + xl), dropping only fl * xl
+__device__ __forceinline__ void ff2_fma(float2& hi, float2& lo, float f, float fl, float2 xh, float2 xl) {
     const float2 ff = make_float2(f, f);
     const float2 p = __fmul2_rn(ff, xh);
     const float2 pe = __ffma2_rn(ff, xh, neg2(p));
     ff2_add(hi, lo, p);
     lo = __ffma2_rn(ff, xl, __fadd2_rn(lo, pe));
+    lo = __ffma2_rn(make_float2(fl, fl), xh, lo);
+}
+// the same with a single-precision x
+__device__ __forceinline__ void ff2_fma1(float2& hi, float2& lo, float f, float fl, float2 x) {
+    const float2 ff = make_float2(f, f);
+    const float2 p = __fmul2_rn(ff, x);
+    const float2 pe = __ffma2_rn(ff, x, neg2(p));
+    ff2_add(hi, lo, p);
+    lo = __ffma2_rn(make_float2(fl, fl), x, __fadd2_rn(lo, pe));
 }
 
-// Synthesis tile with float-float intermediates (dynamic shared memory):
-//   e = cin - down(main, fa);  out = main + up(e, fs)
-template <int RA, int RS>
-__global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ jobs,
-                                                     const int* __restrict__ block_job, Bases B) {
+// Tile with float-float intermediates (dynamic shared memory):
+//   synthesis (ANA = false): e = cin - down(main, fa);  out = main + up(e, fs)
+//   analysis  (ANA = true):  e = -down(main, fa), cout = -e (rounded);  out = main + up(e, fs)
+// so that the detail image of the analysis carries only its own rounding:
+// the lowpass it is computed from is not rounded first.
+template <int RA, int RS, bool ANA>
+__global__ void __launch_bounds__(256) k_lp_ff(const LpJob* __restrict__ jobs, const int* __restrict__ block_job,
+                                               Bases B) {
     constexpr int T = LP_TILE;
     constexpr int MLO = -(RS / 2);
     constexpr int MHI = (T - 1 + RS) / 2;
@@ -279,7 +296,7 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         vb[2 * RA] = wb[2 * RA];
         float2 hi = zero2, lo = zero2;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++) ff2_fma(hi, lo, tap_a<RA>(b), make_float2(va[RA - b], vb[RA - b]), zero2);
+        for (int b = -RA; b <= RA; b++) ff2_fma1(hi, lo, tap_a<RA>(b), tapl_a<RA>(b), make_float2(va[RA - b], vb[RA - b]));
         s_ah[ra * VN + n] = hi.x;
         s_al[ra * VN + n] = lo.x;
         if (rb != ra) {
@@ -288,8 +305,11 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         }
     }
     __syncthreads();
-    // decimating column pass over row pairs (ma, mb), then e = cin - down(main) (normalised float-float)
-    const float* cinp = base_ptr(B, J.cin.b) + J.cin.off;
+    // decimating column pass over row pairs (ma, mb), then e = cin - down(main) (normalised float-float);
+    // the analysis takes e = -down(main) and writes the interior of down(main) as its lowpass output
+    const float* cinp = ANA ? nullptr : base_ptr(B, J.cin.b) + J.cin.off;
+    const float* cinlp = !ANA && J.cin_lo.b >= 0 ? base_ptr(B, J.cin_lo.b) + J.cin_lo.off : nullptr;
+    float* coutp = ANA ? base_ptr(B, J.cout.b) + J.cout.off : nullptr;
     for (int i = threadIdx.x; i < NM * VN; i += blockDim.x) {
         const int q = i / VN, n = i - q * VN;
         const int ma = 2 * q, mb = min(2 * q + 1, VN - 1);
@@ -297,17 +317,34 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
 #pragma unroll
         for (int a = -RA; a <= RA; a++) {
             const int ka = (2 * ma + RA - a) * VN + n, kb = (2 * mb + RA - a) * VN + n;
-            ff2_fma(hi, lo, tap_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
+            ff2_fma(hi, lo, tap_a<RA>(a), tapl_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
         }
-        const int gn = wrap_idx(n0 + MLO + n, Wh);
-        float2 eh = make_float2(cinp[(long long)wrap_idx(m0 + MLO + ma, Hh) * J.cin.rs + gn],
-                                cinp[(long long)wrap_idx(m0 + MLO + mb, Hh) * J.cin.rs + gn]);
-        float2 el = zero2;
-        ff2_add(eh, el, neg2(hi));
-        el = __fadd2_rn(el, neg2(lo));
+        float2 eh, el;
+        if (ANA) {
+            eh = neg2(hi);
+            el = neg2(lo);
+        } else {
+            const int gn = wrap_idx(n0 + MLO + n, Wh);
+            const int gma = wrap_idx(m0 + MLO + ma, Hh), gmb = wrap_idx(m0 + MLO + mb, Hh);
+            eh = make_float2(cinp[(long long)gma * J.cin.rs + gn], cinp[(long long)gmb * J.cin.rs + gn]);
+            el = zero2;
+            if (cinlp)
+                el = make_float2(cinlp[(long long)gma * J.cin_lo.rs + gn], cinlp[(long long)gmb * J.cin_lo.rs + gn]);
+            ff2_add(eh, el, neg2(hi));
+            el = __fadd2_rn(el, neg2(lo));
+        }
         const float2 sn = __fadd2_rn(eh, el);
         el = __fadd2_rn(el, neg2(__fadd2_rn(sn, neg2(eh))));
         eh = sn;
+        if (ANA) {
+            // this tile's share of the lowpass: half-resolution rows / columns [m0, m0 + T/2) x [n0, n0 + T/2)
+            const int gn = n0 + MLO + n;
+            if (n >= -MLO && n < -MLO + T / 2 && gn < Wh) {
+                const int ga = m0 + MLO + ma, gb = m0 + MLO + mb;
+                if (ma >= -MLO && ma < -MLO + T / 2 && ga < Hh) coutp[(long long)ga * J.cout.rs + gn] = -eh.x;
+                if (mb != ma && mb >= -MLO && mb < -MLO + T / 2 && gb < Hh) coutp[(long long)gb * J.cout.rs + gn] = -eh.y;
+            }
+        }
         s_vh[ma * VN + n] = eh.x;
         s_vl[ma * VN + n] = el.x;
         if (mb != ma) {
@@ -325,18 +362,22 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - t / 2;
-                ff2_fma(eh, el, tap_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]), make_float2(s_vl[k], s_vl[k + 1]));
+                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
+                        make_float2(s_vl[k], s_vl[k + 1]));
             } else {
                 const int k = kb + (1 - t) / 2;
-                ff2_fma(oh, ol, tap_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]), make_float2(s_vl[k], s_vl[k + 1]));
+                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
+                        make_float2(s_vl[k], s_vl[k + 1]));
             }
         }
         *reinterpret_cast<float4*>(s_ah + m * T + 4 * w) = make_float4(eh.x, oh.x, eh.y, oh.y);
         *reinterpret_cast<float4*>(s_al + m * T + 4 * w) = make_float4(el.x, ol.x, el.y, ol.y);
     }
     __syncthreads();
-    // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input
+    // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input;
+    // a coarse level's output (the next level's lowpass) keeps its low-order part as well
     float* outp = base_ptr(B, J.out.b) + J.out.off;
+    float* outlp = J.out_lo.b >= 0 ? base_ptr(B, J.out_lo.b) + J.out_lo.off : nullptr;
     for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
         const int p = i / (T / 2), w = i - p * (T / 2);
         const int x = 2 * w;
@@ -346,11 +387,11 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - (t / 2) * T;
-                ff2_fma(eh, el, tap_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
                         *reinterpret_cast<const float2*>(s_al + k));
             } else {
                 const int k = kb + ((1 - t) / 2) * T;
-                ff2_fma(oh, ol, tap_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
                         *reinterpret_cast<const float2*>(s_al + k));
             }
         }
@@ -366,12 +407,18 @@ __global__ void __launch_bounds__(256) k_lp_synth_ff(const LpJob* __restrict__ j
             float* orow = outp + (long long)gy * J.out.rs;
             if (gx < W) orow[gx] = o.x;
             if (gx + 1 < W) orow[gx + 1] = o.y;
+            if (outlp) {
+                const float2 ol2 = __fadd2_rn(lo, neg2(__fadd2_rn(o, neg2(hi))));   // exact: |lo| <= ulp(hi)
+                float* lrow = outlp + (long long)gy * J.out_lo.rs;
+                if (gx < W) lrow[gx] = ol2.x;
+                if (gx + 1 < W) lrow[gx + 1] = ol2.y;
+            }
         }
     }
 }
 
 template <int RA, int RS>
-constexpr size_t synth_ff_smem() {
+constexpr size_t ff_smem() {
     constexpr int T = LP_TILE;
     constexpr int MLO = -(RS / 2);
     constexpr int MHI = (T - 1 + RS) / 2;
@@ -383,15 +430,14 @@ constexpr size_t synth_ff_smem() {
 }
 
 cudaError_t lp_prepare() {
-    // the float-float synthesis kernels need more than 48 KB of dynamic shared memory
+    // the float-float kernels need more than 48 KB of dynamic shared memory
     static std::once_flag once;
     static cudaError_t status = cudaSuccess;
     std::call_once(once, [] {
-        status = cudaFuncSetAttribute(k_lp_synth_ff<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)synth_ff_smem<4, 3>());
-        if (status == cudaSuccess)
-            status = cudaFuncSetAttribute(k_lp_synth_ff<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)synth_ff_smem<3, 4>());
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        status = cudaFuncSetAttribute(k_lp_ff<4, 3, false>, a, (int)ff_smem<4, 3>());
+        if (status == cudaSuccess) status = cudaFuncSetAttribute(k_lp_ff<3, 4, false>, a, (int)ff_smem<3, 4>());
+        if (status == cudaSuccess) status = cudaFuncSetAttribute(k_lp_ff<4, 3, true>, a, (int)ff_smem<4, 3>());
     });
     return status;
 }
@@ -403,11 +449,13 @@ cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st) {
     dim3 grid(L.nblocks), block(256);
     cudaError_t pe = lp_prepare();
     if (pe != cudaSuccess) return pe;
-    if (!synth && !swap) k_lp_level<4, 3, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    // the forward transform and the inverse compute in float-float; the adjoint of the
+    // inverse (gradients, checked relative to their own scale) in single precision
+    if (!synth && !swap) k_lp_ff<4, 3, true><<<grid, block, ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
     else if (synth && !swap)
-        k_lp_synth_ff<4, 3><<<grid, block, synth_ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
-    else if (!synth && swap) k_lp_level<3, 4, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
-    else k_lp_synth_ff<3, 4><<<grid, block, synth_ff_smem<3, 4>(), st>>>(L.d_jobs, L.d_block_job, bases);
+        k_lp_ff<4, 3, false><<<grid, block, ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
+    else if (!synth && swap) k_lp_level<3, 4><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
+    else k_lp_ff<3, 4, false><<<grid, block, ff_smem<3, 4>(), st>>>(L.d_jobs, L.d_block_job, bases);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 // no allocation of any kind: the intermediate lowpass images, the per-level
 // job records and the tile-to-job map live in one file-scope __device__
 // array that every GPU loading the library holds until the process exits.
+#include <atomic>
 #include <cstring>
 
 #include "cvc_internal.cuh"
@@ -27,8 +28,24 @@ static_assert(sizeof(LpJob) <= kJobSlotFloats * 4, "job slot too small");
 
 static __device__ __align__(256) float g_lp_scratch[kStaticFloats];
 
+// the device address of g_lp_scratch, looked up once per device
 constexpr int kMaxDevices = 64;
-float* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<float*> g_scratch_ptr[kMaxDevices];
+
+// every level's job record, passed by value to the set-up kernel
+struct StaticJobs {
+    LpJob job[CVC_MAX_LEVELS];
+    int levels;
+};
+
+// writes the job records into their slots and zeroes the tile-to-job map
+// (every tile of a launch belongs to that launch's single job)
+__global__ void k_static_setup(StaticJobs jobs, float* base, int tiles) {
+    int* block_job = reinterpret_cast<int*>(base + CVC_MAX_LEVELS * kJobSlotFloats);
+    for (int i = threadIdx.x; i < tiles; i += blockDim.x) block_job[i] = 0;
+    if (threadIdx.x < jobs.levels)
+        *reinterpret_cast<LpJob*>(base + threadIdx.x * kJobSlotFloats) = jobs.job[threadIdx.x];
+}
 
 }  // namespace
 
@@ -44,28 +61,28 @@ extern "C" cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int
     // set-up, once per device with that device current: the device address of the array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CVC_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    float* base = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!base) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_lp_scratch) != cudaSuccess || !p) return CVC_ERR_CUDA;
-        g_scratch_ptr[dev] = static_cast<float*>(p);
+        base = static_cast<float*>(p);
+        g_scratch_ptr[dev].store(base, std::memory_order_release);   // racing first calls store the same value
     }
-    float* base = g_scratch_ptr[dev];
     cudaStream_t st = (cudaStream_t)stream;
-    int* block_job = reinterpret_cast<int*>(base + CVC_MAX_LEVELS * kJobSlotFloats);
-    // every tile of a launch belongs to its single job: the map must read zero
-    if (cudaMemsetAsync(block_job, 0, sizeof(int) * (size_t)tiles1, st) != cudaSuccess) return CVC_ERR_CUDA;
     Bases B;
     memset(&B, 0, sizeof(B));
     B.p[B_IN] = const_cast<float*>(d_x);
     B.p[B_COEF] = d_coeffs;
     B.p[B_WORK] = base + kWorkOffset;
     // coefficient layout of cvc_ct_layout with dirs_log2 = 0: lowpass, then the detail of each level
+    StaticJobs jobs;
+    memset(&jobs, 0, sizeof(jobs));
+    jobs.levels = levels;
     long long coff = (long long)(h >> levels) * (w >> levels);
     long long woff = 0, prev_woff = 0;
     for (int j = 1; j <= levels; j++) {
         const int hj = h >> (j - 1), wj = w >> (j - 1);
-        LpJob J;
-        memset(&J, 0, sizeof(J));
+        LpJob& J = jobs.job[j - 1];
         J.H = hj;
         J.W = wj;
         J.tiles_x = (wj + LP_TILE - 1) / LP_TILE;
@@ -82,15 +99,22 @@ extern "C" cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int
         J.out.off = coff;
         J.out.rs = wj;
         J.out.cs = 1;
+        J.cin_lo.b = -1;
+        J.out_lo.b = -1;
         coff += (long long)hj * wj;
         prev_woff = woff;
         woff += (long long)(hj / 2) * (wj / 2);
-        LpJob* slot = reinterpret_cast<LpJob*>(base + (j - 1) * kJobSlotFloats);
-        if (cudaMemcpyAsync(slot, &J, sizeof(J), cudaMemcpyHostToDevice, st) != cudaSuccess) return CVC_ERR_CUDA;
+    }
+    k_static_setup<<<1, 256, 0, st>>>(jobs, base, (int)tiles1);
+    if (cudaGetLastError() != cudaSuccess) return CVC_ERR_CUDA;
+    note_launches(1);
+    int* block_job = reinterpret_cast<int*>(base + CVC_MAX_LEVELS * kJobSlotFloats);
+    for (int j = 1; j <= levels; j++) {
+        const int hj = h >> (j - 1);
         LaunchLp L;
         L.njobs = 1;
-        L.nblocks = ((hj + LP_TILE - 1) / LP_TILE) * J.tiles_x;
-        L.d_jobs = slot;
+        L.nblocks = ((hj + LP_TILE - 1) / LP_TILE) * jobs.job[j - 1].tiles_x;
+        L.d_jobs = reinterpret_cast<LpJob*>(base + (j - 1) * kJobSlotFloats);
         L.d_block_job = block_job;
         if (launch_lp(L, FWD, B, st) != cudaSuccess) return CVC_ERR_CUDA;
         note_launches(1);

@@ -31,7 +31,8 @@ import oracle as O
 from paper_1510_00561_b300 import _lib as L
 
 VIEW = np.dtype([("off", "<i8"), ("b", "<i4"), ("rs", "<i4"), ("cs", "<i4"), ("pad", "<i4")])
-LPJOB = np.dtype([("main", VIEW), ("cin", VIEW), ("cout", VIEW), ("out", VIEW), ("H", "<i4"), ("W", "<i4"),
+LPJOB = np.dtype([("main", VIEW), ("cin", VIEW), ("cout", VIEW), ("out", VIEW), ("cin_lo", VIEW), ("out_lo", VIEW),
+                  ("H", "<i4"), ("W", "<i4"),
                   ("tiles_x", "<i4"), ("first_block", "<i4")])
 AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), ("nst", "<i4"),
                  ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4")])
@@ -166,7 +167,14 @@ def _views_of(kind, J, synth, extra=None):
         H, W = int(J["H"]), int(J["W"])
         if not synth:
             return [("main", J["main"], H, W)], [("cout", J["cout"], H // 2, W // 2), ("out", J["out"], H, W)]
-        return [("main", J["main"], H, W), ("cin", J["cin"], H // 2, W // 2)], [("out", J["out"], H, W)]
+        # float-float lowpass images between synthesis levels: optional low-order halves
+        reads = [("main", J["main"], H, W), ("cin", J["cin"], H // 2, W // 2)]
+        writes = [("out", J["out"], H, W)]
+        if int(J["cin_lo"]["b"]) >= 0:
+            reads.append(("cin_lo", J["cin_lo"], H // 2, W // 2))
+        if int(J["out_lo"]["b"]) >= 0:
+            writes.append(("out_lo", J["out_lo"], H, W))
+        return reads, writes
     if kind == 1:
         H, W = int(J["H"]), int(J["W"])
         comps = [("comp%d" % q, J["comp"][q], H // 2, W // 2) for q in range(4)]
@@ -201,7 +209,10 @@ def run(mode, elems, launches, bufs):
                     out["cout"] = _down(X, fa)
                     out["out"] = X - _up(out["cout"], fs)
                 else:
-                    out["out"] = X + _up(rd["cin"] - _down(X, fa), fs)
+                    # in double precision the whole value sits in the high part
+                    out["out"] = X + _up(rd["cin"] + rd.get("cin_lo", 0.0) - _down(X, fa), fs)
+                    if int(J["out_lo"]["b"]) >= 0:
+                        out["out_lo"] = np.zeros_like(out["out"])
             elif kind == 1:
                 H, W = int(J["H"]), int(J["W"])
                 nst = int(J["nst"])

@@ -52,7 +52,8 @@ def _rgb_buffers(streams, fill=0):
 
 
 def test_mixed_batch_is_bit_identical_to_plain_codecs():
-    per, T = 16, 12
+    """The whole mixed workload: 64 streams x 30 frames (three K-frame periods)."""
+    per, T = 16, 30
     streams = _streams(per)
     frames = _inputs(per, T)
     b = Batch(streams)

@@ -5,10 +5,11 @@ Bar (per stage):
   - transform: 1e-4 on the 0-255 scale (see tolerances.py);
   - quantiser, K/P differencing, RLE, bitstream: bit-exact when the oracle is
     fed the GPU's own single-precision coefficients;
-  - decoder: reconstructed planes within the single-precision storage bound of
-    the synthesis path (tolerances.inverse_bound) of the oracle's decode of the
-    same stream; final RGB identical except where a plane value sits within
-    that bound of a rounding tie; PSNR within 0.01 dB.
+  - decoder: reconstructed planes within the inverse bar (tolerances.INVERSE,
+    1e-4) of the oracle's decode of the same stream; the output stage bit-exact
+    on the GPU's own planes, and a rounded plane sample different from the
+    oracle's only where the oracle's value lies within that bar of a rounding
+    tie (decode_check.py); PSNR within 0.01 dB.
 """
 import numpy as np
 import pytest
@@ -17,7 +18,8 @@ import torch
 import oracle as O
 from paper_1510_00561_b300 import Codec, CvcError
 from paper_1510_00561_b300 import synthetic as S
-from tolerances import FORWARD, inverse_bound
+from decode_check import check_decode
+from tolerances import FORWARD, INVERSE
 
 pytestmark = pytest.mark.gpu
 
@@ -83,9 +85,8 @@ def _run_sequence(kw, frames, check_coeffs_every=1):
         recon = g.inspect(2).cpu().numpy()
         rgb_ref, planes_ref = og.decode(s_np, want_planes=True)
         pref = np.concatenate([p.ravel() for p in planes_ref])
-        assert np.abs(recon.astype(np.float64) - pref).max() < inverse_bound(kw["levels"], kw["dirs_log2"])
-        diff = np.abs(rgb.astype(int) - rgb_ref.astype(int))
-        assert (diff > 0).mean() <= 1e-3
+        assert np.abs(recon.astype(np.float64) - pref).max() < INVERSE
+        check_decode(rgb, recon, planes_ref, kw["height"], kw["width"], g.Hc, g.Wc)
         assert abs(_psnr(rgb, f) - _psnr(rgb_ref, f)) <= 0.01
     return g
 
@@ -98,10 +99,11 @@ def test_qcif_sequence_matches_oracle():
 
 @pytest.mark.parametrize("qph", [4, 8, 16])
 def test_vga_frames_match_oracle(qph):
-    """VGA decomposition (4 levels, 16/8/8/4 directions, K every 10) over a K and two P frames."""
+    """VGA decomposition (4 levels, 16/8/8/4 directions, K every 10) over 12 frames: a whole
+    K-frame period (a K-frame and its chain of nine P-frames) and the next K-frame and P-frame."""
     kw = dict(width=640, height=480, levels=4, dirs_log2=[4, 3, 3, 2], qph=qph, qpl=1, key_interval=10)
     v = S.SyntheticVideo(S.spec_for(640, 480, seed=qph))
-    _run_sequence(kw, v.frames(3), check_coeffs_every=3)
+    _run_sequence(kw, v.frames(12), check_coeffs_every=4)
 
 
 def test_odd_frame_size_padding_paths():
@@ -123,39 +125,55 @@ def test_full_size_1080p_frame():
     _run_sequence(kw, v.frames(2), check_coeffs_every=1)
 
 
-def test_end_to_end_against_fp64_oracle_symbols():
-    """Oracle coefficients in FP64 vs the GPU's FP32: quantised symbols agree except
-    for rare rounding ties, each off by one."""
-    g, o = _pair(**QCIF)
-    f = S.SyntheticVideo(S.spec_for(176, 144, seed=9)).frame(0)
-    s, _ = g.encode(torch.from_numpy(f).cuda())
-    so, _ = o.encode(f)
-    n = g.ncomp
-    tg = np.frombuffer(bytes(s.cpu().numpy()[32 + 4 * n:]), "<i2")
-    to = np.frombuffer(bytes(so[32 + 4 * n:]), "<i2")
-    if tg.size == to.size and np.array_equal(tg, to):
-        return
-    # expand both to codes and compare
-    cg = np.frombuffer(bytes(s.cpu().numpy()[32:32 + 4 * n]), "<u4")
-    co = np.frombuffer(bytes(so[32:32 + 4 * n]), "<u4")
-    lays = [O.layout(g.Hp, g.Wp, 3, [3, 2, 2])] + [O.layout(g.Hcp, g.Wcp, 3, [3, 2, 2])] * 2
-    pg = po = 0
-    mism = total = 0
-    j = 0
+def _codes(stream, lays, prev):
+    """The quantised codes a frame carries: its tokens expanded per component (§3.8), the K-frame
+    lowpass column differences summed back and P-frame residuals added to the previous codes
+    (§3.7), with 16-bit wrap-around; the oracle's RLE expander does the expansion."""
+    ncomp = sum(len(lay["subbands"]) for lay in lays)
+    ftype = int(stream[6])
+    cnt = np.frombuffer(bytes(stream[32:32 + 4 * ncomp]), "<u4")
+    tok = np.frombuffer(bytes(stream[32 + 4 * ncomp:]), "<i2")
+    parts, pos, j = [], 0, 0
     for lay in lays:
         for sb in lay["subbands"]:
-            m = sb["h"] * sb["w"]
-            if sb["kind"] == 0:
-                a, b = tg[pg:pg + cg[j]], to[po:po + co[j]]
+            h, w = sb["h"], sb["w"]
+            t = tok[pos:pos + cnt[j]]
+            if ftype == 0 and sb["kind"] == 0:
+                r = np.cumsum(t.astype(np.int64).reshape(h, w), axis=0).ravel()
             else:
-                a, b = O.rle_expand(tg[pg:pg + cg[j]], m), O.rle_expand(to[po:po + co[j]], m)
-            mism += int(np.count_nonzero(a != b))
-            assert np.abs(a.astype(int) - b.astype(int)).max() <= 1
-            total += m
-            pg += cg[j]
-            po += co[j]
+                r = O.rle_expand(t, h * w).astype(np.int64)
+            parts.append(r)
+            pos += cnt[j]
             j += 1
-    assert mism / total <= 1e-4
+    q = np.concatenate(parts)
+    if ftype == 1:
+        q = q + prev
+    return ((q + 32768) % 65536) - 32768
+
+
+def test_fp64_oracle_symbols_1080p_key_and_p_frame():
+    """The quantised symbols of the GPU's FP32 coefficients against those of the oracle's FP64
+    coefficients (both through the oracle's own quantiser, §3.5-3.6), on a 1080p K-frame and the
+    P-frame after it: they agree except at rounding ties, at most 1e-5 of the symbols, each off by
+    one."""
+    kw = dict(width=1920, height=1080, levels=5, dirs_log2=[5, 4, 4, 3, 3], qph=8, qpl=1, key_interval=10)
+    g, o32 = _pair(**kw)
+    o64 = O.Codec(1920, 1080, 5, kw["dirs_log2"], 8, 1, 0.0, 10)
+    ofp = O.Codec(1920, 1080, 5, kw["dirs_log2"], 8, 1, 0.0, 10)
+    lays = [O.layout(g.Hp, g.Wp, 5, kw["dirs_log2"])] + [O.layout(g.Hcp, g.Wcp, 5, kw["dirs_log2"])] * 2
+    q32 = q64 = None
+    for t, f in enumerate(S.SyntheticVideo(S.spec_for(1920, 1080, seed=9)).frames(2)):
+        s, ft = g.encode(torch.from_numpy(f).cuda())
+        assert ft == t
+        s32, _ = o32.encode_from_coeffs(g.inspect(1).cpu().numpy())
+        assert np.array_equal(s.cpu().numpy(), s32)
+        _, _, c64 = ofp.encode(f, want_coeffs=True)
+        s64, _ = o64.encode_from_coeffs(c64.astype(np.float32))
+        q32 = _codes(s32, lays, q32)
+        q64 = _codes(s64, lays, q64)
+        d = q32 != q64
+        assert np.abs(q32 - q64)[d].max(initial=0) <= 1
+        assert d.sum() <= 1e-5 * d.size, (t, int(d.sum()), d.size)
 
 
 def test_capacity_error_leaves_state_unchanged():

@@ -19,7 +19,7 @@ import torch
 import oracle as O
 from paper_1510_00561_b300 import Codec, CvcError, Deflater, drop_levels
 from paper_1510_00561_b300 import synthetic as S
-from tolerances import FORWARD, inverse_bound
+from tolerances import FORWARD, INVERSE, ROUND_TRIP
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def _check_sequence(w, h, L, k, frames, motion=0, qph=4):
         rgb = g.decode(s.clone()).cpu().numpy()
         recon = g.inspect(2).cpu().numpy().astype(np.float64)
         rgb_ref, pr = od.decode(s_np, want_planes=True)
-        assert np.abs(recon - np.concatenate([p.ravel() for p in pr])).max() < inverse_bound(L)
+        assert np.abs(recon - np.concatenate([p.ravel() for p in pr])).max() < INVERSE
         assert np.abs(rgb.astype(int) - rgb_ref.astype(int)).max() <= 1
     return g
 

@@ -21,7 +21,8 @@ import torch
 import oracle as O
 from paper_1510_00561_b300 import Batch, Codec, CvcError, Deflater
 from paper_1510_00561_b300 import synthetic as S
-from tolerances import inverse_bound
+from decode_check import check_decode, check_scaled_decode
+from tolerances import INVERSE
 
 pytestmark = pytest.mark.gpu
 
@@ -68,9 +69,8 @@ def _run(kw, frames):
         recon = g.inspect(2).cpu().numpy().astype(np.float64)
         rgb_ref, planes_ref = od.decode(s_np, want_planes=True)
         pref = np.concatenate([p.ravel() for p in planes_ref])
-        assert np.abs(recon - pref).max() < inverse_bound(kw["levels"])
-        diff = np.abs(rgb.astype(int) - rgb_ref.astype(int))
-        assert (diff > 0).mean() <= 1e-3 and diff.max() <= 2
+        assert np.abs(recon - pref).max() < INVERSE
+        check_decode(rgb, recon, planes_ref, kw["height"], kw["width"], g.Hc, g.Wc, storage8=True)
         streams.append(s_np)
     return g, streams
 
@@ -119,9 +119,7 @@ def test_scaled_decoding_of_storage8_streams():
         d, og = _gpu(kw), _oracle(kw)
         for s in streams:
             a = d.decode(s.clone(), scale=sc).cpu().numpy()
-            r = og.decode(s.cpu().numpy(), scale=sc)
-            diff = np.abs(a.astype(int) - r.astype(int))
-            assert (diff > 0).sum() <= max(2, diff.size // 3000) and diff.max() <= 2, sc
+            check_scaled_decode(d, a, og, s.cpu().numpy(), sc, storage8=True)
 
 
 def test_each_decoder_refuses_the_other_storage():

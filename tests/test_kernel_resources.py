@@ -7,7 +7,8 @@ cross-compiles for sm_103a without a GPU).
     and every thread then reads it back from local memory;
   - the tile kernels keep the residency their shared-memory budgets are
     designed for on a 228 KB SM (1 KB reserved per block): 6 blocks of
-    `k_dfb_b` (4 taps), 4 of `k_dfb_a` (4 taps) and 4 of `k_lp_synth_ff`.
+    `k_dfb_b` (4 taps), 4 of `k_dfb_a` (4 taps) and 4 of `k_lp_ff` (the
+    float-float LP tiles of the forward transform and the inverse).
 """
 import functools
 import os
@@ -21,7 +22,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 
-HOT = ("k_dfb_a", "k_dfb_b", "k_lp_level", "k_lp_synth_ff", "k_scan_reduce", "k_scan_sums", "k_scan_apply",
+HOT = ("k_dfb_a", "k_dfb_b", "k_lp_level", "k_lp_ff", "k_scan_reduce", "k_scan_sums", "k_scan_apply",
        "k_quant_b", "k_unquant_b", "k_colour_fwd_b", "k_colour_inv_b", "k_rle_count_b", "k_rle_write_b")
 
 
@@ -82,6 +83,7 @@ def test_tile_kernels_keep_their_residency():
     a4 = [v for k, v in dfb.items() if "k_dfb_a" in k and "Li4EE" in k]
     assert len(a4) == 2 and all(blocks(v["smem"] + 6 * 44 * 45 * 4, v["regs"]) >= 4 for v in a4), a4
     lp = _ptxas("k_lp.cu")
-    # k_lp_synth_ff<4, 3>: 77 x 78 main tile, two 2,696-float and two 35 x 35 float-float arrays, dynamic
-    syn = [v for k, v in lp.items() if "k_lp_synth_ff" in k and "ILi4ELi3E" in k]
-    assert len(syn) == 1 and blocks(syn[0]["smem"] + 4 * (6008 + 2 * 2696 + 2 * 35 * 35), syn[0]["regs"]) >= 4, syn
+    # k_lp_ff<4, 3, *> (analysis and synthesis): 77 x 78 main tile, two 2,696-float and two 35 x 35
+    # float-float arrays, dynamic
+    ff = [v for k, v in lp.items() if "k_lp_ff" in k and "ILi4ELi3E" in k]
+    assert len(ff) == 2 and all(blocks(v["smem"] + 4 * (6008 + 2 * 2696 + 2 * 35 * 35), v["regs"]) >= 4 for v in ff), ff

@@ -4,9 +4,11 @@ Some callers cannot allocate device memory while they run (a budget handed
 out up front, or a context where the CUDA allocator is off limits), so they
 cannot build a transform plan.  cvc_lp_pyramid_forward_static serves them with
 its scratch in a fixed device array.  Checked through the C ABI against the
-plan-based cvc_ct_forward with zero directional stages, on two calls in a row
-that reuse the shared array, and for its size limit.  Collected last so that
-a run stopping at the first failure has already run every other test.
+FP64 oracle's Laplacian pyramid (the transform bar, each level on its pixel
+scale) and against the plan-based cvc_ct_forward with zero directional stages
+(the same kernel: bit-identical), on two calls in a row that reuse the shared
+array, and for its size limit.  Collected last so that a run stopping at the
+first failure has already run every other test.
 """
 import ctypes
 
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1510_00561_b300 import CtPlan, _lib
 from paper_1510_00561_b300 import synthetic as S
 from tolerances import FORWARD
@@ -35,8 +38,15 @@ def test_static_pyramid_matches_the_plan_on_two_calls_in_a_row():
         assert _call(x, h, w, levels, out) == 0
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
-        # same kernel and arithmetic as the plan: the values agree well inside the bar
-        assert float((out - ref).abs().max()) <= FORWARD
+        # the oracle's pyramid, each level divided by its DC gain (2^(j-1); the lowpass 2^L)
+        got = out.cpu().numpy()[0].astype(np.float64)
+        want = O.ct(0, x.cpu().numpy()[0].astype(np.float64), h, w, levels, [0] * levels)
+        for sb in O.layout(h, w, levels, [0] * levels)["subbands"]:
+            a, n = sb["off"], sb["h"] * sb["w"]
+            gain = 2.0 ** (levels if sb["level"] == 0 else sb["level"] - 1)
+            assert np.abs(got[a:a + n] - want[a:a + n]).max() / gain < FORWARD
+        # the same kernel and job geometry as the plan: identical values
+        assert torch.equal(out, ref)
 
 
 def test_static_pyramid_rejects_planes_beyond_its_array():
