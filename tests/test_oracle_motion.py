@@ -8,6 +8,13 @@
   - a global translation by a multiple of 2^L makes every LP component's
     prediction exact away from the borders (the vector mapping to each
     component's scale);
+  - the element size (ey, ex) of every component kind, both directional
+    families included, and the rounding of the scaled vectors, against a
+    hand-worked table (a swapped (ey, ex) for the transposed family or a
+    truncating shift fails it);
+  - a periodic translation by a multiple of the pyramid modulus makes the
+    residual of every component exactly zero wherever its block found the
+    translation, directional subbands included (8/4/4 and 32/16/16/8/8);
   - streams with motion survive level dropping and scaled decoding.
 """
 import numpy as np
@@ -198,3 +205,143 @@ def test_motion_stream_refusals():
     d.decode(s1)
     with pytest.raises(ValueError):
         O.Codec(**kw, motion_range=65)
+
+
+# Element size of every component of a 176 x 144 frame with 3 levels and 8/4/4
+# directions, worked out by hand from the layout (§2.1: level j of a plane is
+# (H >> (j-1)) x (W >> (j-1)); with k stages, directions d < 2^(k-1) are
+# (h >> (k-1)) x (w / 2) and the others (h / 2) x (w >> (k-1)); chroma planes
+# are half size): (luma rows, luma columns) per element, as powers of two.
+QCIF_ELEMENT = {
+    # plane 0 (luma 144 x 176)
+    (0, 0, "low"): (3, 3),        # 18 x 22
+    (0, 1, "c"): (2, 1),          # 36 x 88
+    (0, 1, "r"): (1, 2),          # 72 x 44
+    (0, 2, "c"): (2, 2),          # 36 x 44
+    (0, 2, "r"): (2, 2),          # 36 x 44
+    (0, 3, "c"): (3, 3),          # 18 x 22
+    (0, 3, "r"): (3, 3),          # 18 x 22
+    # planes 1, 2 (chroma 72 x 88): one element of a 72 x 88 plane is 2 x 2 luma samples
+    (1, 0, "low"): (4, 4),        # 9 x 11
+    (1, 1, "c"): (3, 2),          # 18 x 44
+    (1, 1, "r"): (2, 3),          # 36 x 22
+    (1, 2, "c"): (3, 3),          # 18 x 22
+    (1, 2, "r"): (3, 3),
+    (1, 3, "c"): (4, 4),          # 9 x 11
+    (1, 3, "r"): (4, 4),
+}
+
+# v / 2^e rounded half away from zero, written out for v = -8 .. 8
+ROUNDED = {
+    0: list(range(-8, 9)),
+    1: [-4, -4, -3, -3, -2, -2, -1, -1, 0, 1, 1, 2, 2, 3, 3, 4, 4],
+    2: [-2, -2, -2, -1, -1, -1, -1, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2],
+    3: [-1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1],
+    4: [-1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1],
+}
+
+
+def test_prediction_of_every_component_kind_against_a_hand_worked_table():
+    """§3.7 maps the block vectors "to the corresponding scale and range" of each
+    component.  A K-frame whose codes are distinct within each component, then a
+    P-frame of zero coefficients whose luma moves every 16 x 16 block by its own
+    vector (odd and even values in -8..8, so that halving rounds): the P-frame's
+    residual is minus the prediction, which must read, for element (i, k), the
+    previous code at (i + rnd(dy / 2^ey), k + rnd(dx / 2^ex)) clamped, with (ey, ex)
+    from the table above (transposed between the two directional families) and the
+    rounding of the table ROUNDED; (dy, dx) is the vector of the block holding the
+    element's first luma sample."""
+    H, W, L, k = 144, 176, 3, [3, 2, 2]
+    c = O.Codec(W, H, L, k, 1, 1, 0.0, 100, motion_range=8)
+    lays = [O.layout(H, W, L, k)] + [O.layout(H // 2, W // 2, L, k)] * 2
+    # K-frame: codes 1 + (index within the component); the lowpass carries the 2^-L normalisation
+    coef = np.zeros(c.ncoef, np.float32)
+    prev_codes, pos = [], 0
+    for lay in lays:
+        for sb in lay["subbands"]:
+            n = sb["h"] * sb["w"]
+            q = (1 + np.arange(n)).reshape(sb["h"], sb["w"])
+            coef[pos:pos + n] = (q * (2 ** L if sb["kind"] == 0 else 1)).ravel()
+            prev_codes.append(q)
+            pos += n
+    rng = np.random.default_rng(7)
+    tex = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    s0, ft0 = c.encode_from_coeffs(coef, luma=tex)
+    assert ft0 == 0
+    # P-frame luma: block (by, bx) shows the texture displaced by its vector
+    nby, nbx = H // 16, W // 16
+    vec = np.zeros((nby, nbx, 2), np.int64)
+    cur = np.zeros_like(tex)
+    for by in range(nby):
+        for bx in range(nbx):
+            y0, x0 = 16 * by, 16 * bx
+            dy, dx = (3 * by + 5 * bx) % 17 - 8, (7 * by + 2 * bx + 4) % 17 - 8
+            if not 0 <= y0 + dy <= H - 16:
+                dy = -dy
+            if not 0 <= x0 + dx <= W - 16:
+                dx = -dx
+            vec[by, bx] = dy, dx
+            cur[y0:y0 + 16, x0:x0 + 16] = tex[y0 + dy:y0 + dy + 16, x0 + dx:x0 + dx + 16]
+    assert len(set(vec[..., 0].ravel())) == 17 and len(set(vec[..., 1].ravel())) == 17
+    s1, ft1 = c.encode_from_coeffs(np.zeros(c.ncoef, np.float32), luma=cur)
+    assert ft1 == 2
+    mv = np.frombuffer(bytes(s1[-2 * nby * nbx:]), np.int8).reshape(nby, nbx, 2)
+    assert np.array_equal(mv, vec)                      # the search finds the designed vectors
+    for (p, sb, r), q in zip(_components(s1, c, lays), prev_codes):
+        kind = "low" if sb["kind"] == 0 else ("c" if sb["kind"] == 1 or sb["dir"] < (1 << k[sb["level"] - 1]) // 2
+                                              else "r")
+        ey, ex = QCIF_ELEMENT[(min(p, 1), sb["level"], kind)]
+        h, w = sb["h"], sb["w"]
+        want = np.zeros((h, w), np.int64)
+        for i in range(h):
+            for kk in range(w):
+                by, bx = min((i << ey) >> 4, nby - 1), min((kk << ex) >> 4, nbx - 1)
+                dy, dx = vec[by, bx]
+                si = min(max(i + ROUNDED[ey][dy + 8], 0), h - 1)
+                sk = min(max(kk + ROUNDED[ex][dx + 8], 0), w - 1)
+                want[i, kk] = q[si, sk]
+        assert np.array_equal(-r.astype(np.int64), want), (p, sb["level"], kind)
+
+
+@pytest.mark.parametrize("W,H,L,k,shift", [(176, 144, 3, [3, 2, 2], 16), (256, 256, 5, [5, 4, 4, 3, 3], 64)],
+                         ids=["qcif_8-4-4", "256_32-16-16-8-8"])
+def test_periodic_translation_is_predicted_exactly_in_every_directional_subband(W, H, L, k, shift):
+    """A frame and its periodic translation by a multiple of the pyramid modulus (8 for
+    8/4/4, 64 for 32/16/16/8/8): with periodic extension every stage of the LP and the
+    DFB commutes with that translation, so every component whose element spans a divisor
+    of the shift in luma samples (all of them at 8/4/4; at 32/16/16/8/8 all but the
+    coarsest chroma subbands, whose elements span 128) is the previous one moved by
+    (shift / 2^ey, -shift / 2^ex) elements, directional subbands of both families
+    included.  The P-frame residual must then be exactly zero wherever the element's
+    block found the translation and its source lies inside the component."""
+    rng = np.random.default_rng(11)
+    prev = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    cur = np.roll(prev, (-shift, shift), axis=(0, 1))           # cur(y, x) = prev(y + shift, x - shift)
+    c = O.Codec(W, H, L, k, 4, 1, 0.0, 100, motion_range=shift)
+    assert (c.Hp, c.Wp) == (H, W)
+    c.encode(prev)
+    s, ft = c.encode(cur)
+    assert ft == 2
+    nby, nbx = H // 16, W // 16
+    mv = np.frombuffer(bytes(s[-2 * nby * nbx:]), np.int8).reshape(nby, nbx, 2)
+    good = (mv[..., 0] == shift) & (mv[..., 1] == -shift)
+    assert good[:nby - shift // 16 - 1, shift // 16:].all()
+    lays = [O.layout(H, W, L, k)] + [O.layout(H // 2, W // 2, L, k)] * 2
+    checked = set()
+    for p, sb, r in _components(s, c, lays):
+        ph, pw = (H, W) if p == 0 else (H // 2, W // 2)
+        ey = int(np.log2(ph / sb["h"])) + (p > 0)               # luma samples per element, as powers of two
+        ex = int(np.log2(pw / sb["w"])) + (p > 0)
+        if shift % (1 << ey) or shift % (1 << ex):
+            assert p > 0 and sb["level"] == L                   # only the coarsest chroma subbands
+            continue
+        sy, sx = shift >> ey, -(shift >> ex)
+        i = np.arange(sb["h"])[:, None]
+        kk = np.arange(sb["w"])[None, :]
+        blk = good[np.minimum((i << ey) >> 4, nby - 1), np.minimum((kk << ex) >> 4, nbx - 1)]
+        inside = (i + sy < sb["h"]) & (kk + sx >= 0)
+        region = blk & inside
+        assert region.any(), (p, sb["level"], sb["dir"])
+        assert not r[region].any(), (p, sb["level"], sb["dir"], int(np.count_nonzero(r[region])))
+        checked.add((p > 0, sb["kind"]))
+    assert {(False, 0), (False, 1), (False, 2), (True, 1), (True, 2)} <= checked
