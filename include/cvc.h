@@ -212,7 +212,9 @@ typedef struct cvc_codec cvc_codec;
 
 cvc_status cvc_create(const cvc_params* params, cvc_codec** out);
 cvc_status cvc_destroy(cvc_codec* codec);
-/* Next encoded frame is a K-frame; the decoder expects a K-frame next. */
+/* Next encoded frame is a K-frame; the decoder expects a K-frame next.  The
+ * reset travels with the codec's next call (it takes effect in stream order,
+ * after calls already queued); no device call is made here.                */
 cvc_status cvc_reset(cvc_codec* codec);
 cvc_status cvc_codec_info(const cvc_codec* codec, cvc_codec_info_t* out);
 
@@ -257,6 +259,43 @@ cvc_status cvc_decode_frame(cvc_codec* codec, const uint8_t* d_in, size_t in_len
  * scale outside [0, levels].                                                */
 cvc_status cvc_decode_frame_scaled(cvc_codec* codec, const uint8_t* d_in, size_t in_len, int scale,
                                    uint8_t* d_rgb, size_t pitch_bytes, cvc_stream_t stream);
+
+/* Asynchronous encode and decode.  The paper's encoder keeps a frame on the
+ * GPU from the colour conversion to the frame-type step (§3.7, §3.10);
+ * these forms keep the whole call there: nothing waits on the host, the
+ * outcome goes to DEVICE memory, and the coder state (frame index, K/P
+ * schedule, the decoder's reference) lives and advances on the device, so
+ * calls queue back to back on `stream` and give exactly the bytes and
+ * pixels of the synchronous calls made in the same order.
+ *   cvc_encode_frame_async: as cvc_encode_frame; the step writes the
+ *     encoded length (the length needed when out_cap is too small) to
+ *     *d_out_len, the frame type (0 K, 1 P, 2 P with motion) to
+ *     *d_frame_type and the call's status (OK, CAPACITY, OVERFLOW) to
+ *     *d_status; each pointer is device memory and may be NULL.
+ *   cvc_decode_frame_async: as cvc_decode_frame_scaled; d_in holds in_cap
+ *     bytes, and the frame's length is *d_in_len (device memory, read when
+ *     the step runs, at most in_cap; NULL: in_cap is the length), e.g. the
+ *     d_out_len of an encode queued before it.  The status (OK, CORRUPT,
+ *     STATE) goes to *d_status (device, may be NULL).
+ * A failed call leaves the coder state unchanged, as the synchronous forms
+ * do; the first failure since the last cvc_get_error is also kept in the
+ * codec's device status word.  Argument checks that need no device data
+ * happen on the host (INVALID_ARG: nothing queued); the call returns CUDA
+ * if queueing failed, otherwise OK.  The host may run up to 8 calls ahead
+ * of the device; a ninth waits for the first of them to finish.  Stage
+ * timing (cvc_codec_set_timing) counts synchronous calls only.  Buffers
+ * must stay valid until the stream has run the call.                        */
+cvc_status cvc_encode_frame_async(cvc_codec* codec, const uint8_t* d_rgb, size_t pitch_bytes, uint8_t* d_out,
+                                  size_t out_cap, size_t* d_out_len, int* d_frame_type, cvc_status* d_status,
+                                  cvc_stream_t stream);
+cvc_status cvc_decode_frame_async(cvc_codec* codec, const uint8_t* d_in, size_t in_cap, const size_t* d_in_len,
+                                  int scale, uint8_t* d_rgb, size_t pitch_bytes, cvc_status* d_status,
+                                  cvc_stream_t stream);
+/* The codec's device status word: the first non-OK status of an
+ * asynchronous call since the last read (CVC_OK if none), read and cleared
+ * in `stream` order (calls queued on `stream` before this one are seen).
+ * Synchronises `stream`.  Errors: INVALID_ARG, CUDA.                        */
+cvc_status cvc_get_error(cvc_codec* codec, cvc_stream_t stream, cvc_status* status);
 
 /* Transmission-side scalability (§3.3: a receiver's resolution is served by
  * dropping what refers to higher resolutions, without re-encoding).  Copies
@@ -408,6 +447,19 @@ cvc_status cvc_batch_step(cvc_batch* batch, int what, const cvc_batch_io* io, cv
  * scale replays its own captured graph.                                     */
 cvc_status cvc_batch_step_scaled(cvc_batch* batch, int what, const cvc_batch_io* io, int scale,
                                  cvc_batch_result* res, cvc_stream_t stream);
+
+/* The asynchronous batch step (see cvc_encode_frame_async): io as for
+ * cvc_batch_step_scaled (host array, checked on the host); d_in_len, if not
+ * NULL, is a DEVICE array of n decoder input lengths read when the step
+ * runs (each at most io[i].in_len, the buffer's capacity); d_res, if not
+ * NULL, a DEVICE array of n results that the step writes.  Every stream's
+ * coder state advances on the device where its call succeeded; the first
+ * failure of a stream is kept in its device status word
+ * (cvc_batch_get_error).  Returns INVALID_ARG (nothing queued), CUDA, or OK. */
+cvc_status cvc_batch_step_async(cvc_batch* batch, int what, const cvc_batch_io* io, const size_t* d_in_len,
+                                int scale, cvc_batch_result* d_res, cvc_stream_t stream);
+/* as cvc_get_error for stream i of a batch */
+cvc_status cvc_batch_get_error(cvc_batch* batch, int i, cvc_stream_t stream, cvc_status* status);
 
 /* Launch shapes (they change no result): rows per block of the run-length
  * kernels (1..32) and blocks of the decoder's token kernels (1..65535).

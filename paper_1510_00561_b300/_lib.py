@@ -123,6 +123,9 @@ def lib():
         L.cvc_encode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I), _P]
         L.cvc_decode_frame.argtypes = [_P, _P, _SZ, _P, _SZ, _P]
         L.cvc_decode_frame_scaled.argtypes = [_P, _P, _SZ, _I, _P, _SZ, _P]
+        L.cvc_encode_frame_async.argtypes = [_P, _P, _SZ, _P, _SZ, _P, _P, _P, _P]
+        L.cvc_decode_frame_async.argtypes = [_P, _P, _SZ, _P, _I, _P, _SZ, _P, _P]
+        L.cvc_get_error.argtypes = [_P, _P, ctypes.POINTER(_I)]
         L.cvc_deflate_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_P)]
         L.cvc_deflate_create_batch.argtypes = [ctypes.POINTER(Params), _I, ctypes.POINTER(_P)]
         L.cvc_deflate_frames.argtypes = [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_SZ), ctypes.POINTER(_P),
@@ -147,6 +150,8 @@ def lib():
         L.cvc_batch_reset.argtypes = [_P, _I]
         L.cvc_batch_step.argtypes = [_P, _I, ctypes.POINTER(BatchIo), ctypes.POINTER(BatchResult), _P]
         L.cvc_batch_step_scaled.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(BatchResult), _P]
+        L.cvc_batch_step_async.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _P, _I, _P, _P]
+        L.cvc_batch_get_error.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
         L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
         L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
         L.cvc_batch_set_graphs.argtypes = [_P, _I]

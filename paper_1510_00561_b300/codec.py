@@ -20,6 +20,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _opt(t, dtype):
+    """device pointer of an optional one-element CUDA tensor of `dtype`"""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.numel() >= 1):
+        raise ValueError("expected a CUDA tensor of %s" % dtype)
+    return t.data_ptr()
+
+
 def kernel_launches():
     """Kernels libcvc has launched in this process."""
     return int(_L.lib().cvc_kernel_launches())
@@ -166,6 +175,35 @@ class Codec:
             err.needed = n.value
             raise err
         return out[:n.value], ft.value
+
+    def encode_async(self, rgb, out, out_len=None, frame_type=None, status=None, stream=None):
+        """cvc_encode_frame_async: queue the encode of rgb into out (uint8 CUDA tensor) without
+        waiting; the device writes the length, frame type and status into the given CUDA tensors
+        (int64 / int32 / int32 of one element each, or None)."""
+        if not (rgb.is_cuda and rgb.dtype == torch.uint8 and rgb.dim() == 3 and rgb.shape[2] == 3
+                and rgb.stride(2) == 1 and rgb.stride(1) == 3):
+            raise ValueError("expected an (H, W, 3) uint8 CUDA tensor with interleaved channels")
+        _L.check(_L.lib().cvc_encode_frame_async(self._h, _ptr(rgb), rgb.stride(0), _ptr(out), out.numel(),
+                                                 _opt(out_len, torch.int64), _opt(frame_type, torch.int32),
+                                                 _opt(status, torch.int32), _stream(stream)),
+                 "cvc_encode_frame_async")
+
+    def decode_async(self, stream_bytes, out, in_len=None, status=None, scale=0, stream=None):
+        """cvc_decode_frame_async: queue the decode of stream_bytes (uint8 CUDA tensor, its whole
+        size the capacity) into out; in_len (int64 CUDA tensor of one element, e.g. an encode's
+        out_len) gives the frame's length on the device; status receives the decoder's status."""
+        if not (stream_bytes.is_cuda and stream_bytes.dtype == torch.uint8 and stream_bytes.is_contiguous()):
+            raise ValueError("expected a contiguous uint8 CUDA tensor")
+        _L.check(_L.lib().cvc_decode_frame_async(self._h, _ptr(stream_bytes), stream_bytes.numel(),
+                                                 _opt(in_len, torch.int64), int(scale), _ptr(out), out.stride(0),
+                                                 _opt(status, torch.int32), _stream(stream)),
+                 "cvc_decode_frame_async")
+
+    def get_error(self, stream=None):
+        """cvc_get_error: the first failure of an asynchronous call since the last read (0: none)."""
+        v = ctypes.c_int(0)
+        _L.check(_L.lib().cvc_get_error(self._h, _stream(stream), ctypes.byref(v)), "cvc_get_error")
+        return v.value
 
     def scaled_size(self, scale):
         """(height, width) of the decoder's output at pyramid scale `scale`."""
@@ -395,6 +433,42 @@ class Batch:
         if check and st != 0:
             raise _L.CvcError(st, "cvc_batch_step")
         return res
+
+    def step_async(self, what, rgb=None, streams_in=None, rgb_out=None, outs=None, in_len=None, results=None,
+                   stream=None, scale=0):
+        """cvc_batch_step_async: queue one step without waiting.  in_len: int64 CUDA tensor of n
+        decoder input lengths (or None: each input's size); results: uint8 CUDA tensor of
+        n * sizeof(cvc_batch_result) bytes receiving the per-stream results (see results_of)."""
+        self._fill(rgb, streams_in, rgb_out, outs)
+        if in_len is not None and not (in_len.is_cuda and in_len.dtype == torch.int64 and in_len.numel() >= self.n):
+            raise ValueError("in_len: an int64 CUDA tensor of one length per stream")
+        if results is not None and results.numel() < self.n * ctypes.sizeof(_L.BatchResult):
+            raise ValueError("results: too small")
+        _L.check(_L.lib().cvc_batch_step_async(self._h, what, self._io,
+                                               in_len.data_ptr() if in_len is not None else None, int(scale),
+                                               results.data_ptr() if results is not None else None,
+                                               _stream(stream)), "cvc_batch_step_async")
+
+    def results_buffer(self, device="cuda"):
+        """a device buffer for step_async's per-stream results"""
+        return torch.zeros(self.n * ctypes.sizeof(_L.BatchResult), dtype=torch.uint8, device=device)
+
+    def results_of(self, buf):
+        """the per-stream result dicts held in a results buffer (copied to the host)"""
+        raw = bytes(buf.cpu().numpy())
+        out = []
+        for i in range(self.n):
+            r = _L.BatchResult.from_buffer_copy(raw, i * ctypes.sizeof(_L.BatchResult))
+            out.append(dict(enc_status=r.enc_status, dec_status=r.dec_status, out_len=r.out_len,
+                            frame_type=r.frame_type, dec_frame_type=r.dec_frame_type,
+                            dec_frame_index=r.dec_frame_index))
+        return out
+
+    def get_error(self, i, stream=None):
+        """cvc_batch_get_error for stream i"""
+        v = ctypes.c_int(0)
+        _L.check(_L.lib().cvc_batch_get_error(self._h, i, _stream(stream), ctypes.byref(v)), "cvc_batch_get_error")
+        return v.value
 
     def set_shape(self, rle_rows, tok_blocks):
         _L.check(_L.lib().cvc_batch_set_shape(self._h, rle_rows, tok_blocks), "cvc_batch_set_shape")

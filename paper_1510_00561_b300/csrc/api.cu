@@ -295,6 +295,7 @@ cvc_status cvc_encode_frame(cvc_codec* c, const uint8_t* d_rgb, size_t pitch_byt
                             size_t* out_len, int* frame_type, cvc_stream_t stream) {
     if (!c || !d_rgb || !d_out || !out_len) return CVC_ERR_INVALID_ARG;
     StreamIo io{d_rgb, pitch_bytes, d_out, out_cap, nullptr, 0, nullptr, 0};
+    if (!core_begin(&c->core)) return CVC_ERR_CUDA;
     if (!core_fill_call(&c->core, 0, STEP_ENC, io)) return CVC_ERR_INVALID_ARG;
     cvc_status s = run_step(&c->core, STEP_ENC, (cudaStream_t)stream);
     if (s != CVC_OK) return s;
@@ -314,12 +315,51 @@ cvc_status cvc_decode_frame_scaled(cvc_codec* c, const uint8_t* d_in, size_t in_
                                    size_t pitch_bytes, cvc_stream_t stream) {
     if (!c || !d_in || !d_rgb) return CVC_ERR_INVALID_ARG;
     StreamIo io{nullptr, 0, nullptr, 0, d_in, in_len, d_rgb, pitch_bytes};
+    if (!core_begin(&c->core)) return CVC_ERR_CUDA;
     if (!core_fill_call(&c->core, 0, STEP_DEC, io, scale)) return CVC_ERR_INVALID_ARG;
     cvc_status s = run_step(&c->core, STEP_DEC, (cudaStream_t)stream, scale);
     if (s != CVC_OK) return s;
     cvc_status ds;
     core_commit(&c->core, 0, STEP_DEC, nullptr, &ds, nullptr, nullptr, nullptr, nullptr);
     return ds;
+}
+
+// ---------------------------------------------------------- asynchronous calls
+// The same steps without the host waiting: the outcome goes to device memory
+// (written by the step's last kernel), and the coder state advances on the
+// device, so calls queue back to back on a stream.
+
+cvc_status cvc_encode_frame_async(cvc_codec* c, const uint8_t* d_rgb, size_t pitch_bytes, uint8_t* d_out,
+                                  size_t out_cap, size_t* d_out_len, int* d_frame_type, cvc_status* d_status,
+                                  cvc_stream_t stream) {
+    if (!c || !d_rgb || !d_out) return CVC_ERR_INVALID_ARG;
+    StreamIo io{d_rgb, pitch_bytes, d_out, out_cap, nullptr, 0, nullptr, 0};
+    if (!core_begin(&c->core)) return CVC_ERR_CUDA;
+    if (!core_fill_call(&c->core, 0, STEP_ENC, io)) return CVC_ERR_INVALID_ARG;
+    SCall& C = c->core.h_sc[0];
+    C.async = 1;
+    C.out_len_dev = d_out_len;
+    C.type_dev = d_frame_type;
+    C.enc_status_dev = d_status;
+    return core_enqueue(&c->core, STEP_ENC, (cudaStream_t)stream);
+}
+
+cvc_status cvc_decode_frame_async(cvc_codec* c, const uint8_t* d_in, size_t in_cap, const size_t* d_in_len, int scale,
+                                  uint8_t* d_rgb, size_t pitch_bytes, cvc_status* d_status, cvc_stream_t stream) {
+    if (!c || !d_in || !d_rgb) return CVC_ERR_INVALID_ARG;
+    StreamIo io{nullptr, 0, nullptr, 0, d_in, in_cap, d_rgb, pitch_bytes};
+    if (!core_begin(&c->core)) return CVC_ERR_CUDA;
+    if (!core_fill_call(&c->core, 0, STEP_DEC, io, scale)) return CVC_ERR_INVALID_ARG;
+    SCall& C = c->core.h_sc[0];
+    C.async = 1;
+    C.in_len_dev = d_in_len;
+    C.dec_status_dev = d_status;
+    return core_enqueue(&c->core, STEP_DEC, (cudaStream_t)stream, scale);
+}
+
+cvc_status cvc_get_error(cvc_codec* c, cvc_stream_t stream, cvc_status* status) {
+    if (!c || !status) return CVC_ERR_INVALID_ARG;
+    return core_take_error(&c->core, 0, (cudaStream_t)stream, status);
 }
 
 cvc_status cvc_stream_drop_levels(const cvc_params* params, const uint8_t* in, size_t in_len, int drop,
@@ -725,6 +765,7 @@ cvc_status cvc_batch_step_scaled(cvc_batch* b, int what, const cvc_batch_io* io,
                                  cvc_stream_t stream) {
     if (!b || !io || !res || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
     Core* c = &b->core;
+    if (!core_begin(c)) return CVC_ERR_CUDA;
     if (!batch_fill(c, what, io, scale)) return CVC_ERR_INVALID_ARG;
     cvc_status s = run_step(c, what, (cudaStream_t)stream, scale);
     if (s != CVC_OK) return s;
@@ -737,6 +778,26 @@ cvc_status cvc_batch_step_scaled(cvc_batch* b, int what, const cvc_batch_io* io,
         if (first == CVC_OK) first = r.enc_status != CVC_OK ? r.enc_status : r.dec_status;
     }
     return first;
+}
+
+cvc_status cvc_batch_step_async(cvc_batch* b, int what, const cvc_batch_io* io, const size_t* d_in_len, int scale,
+                                cvc_batch_result* d_res, cvc_stream_t stream) {
+    if (!b || !io || what < CVC_STEP_ENCODE || what > CVC_STEP_ENCODE_DECODE) return CVC_ERR_INVALID_ARG;
+    Core* c = &b->core;
+    if (!core_begin(c)) return CVC_ERR_CUDA;
+    if (!batch_fill(c, what, io, scale)) return CVC_ERR_INVALID_ARG;
+    for (int i = 0; i < c->n; i++) {
+        SCall& C = c->h_sc[i];
+        C.async = 1;
+        C.in_len_dev = d_in_len ? d_in_len + i : nullptr;
+        C.res_dev = d_res ? d_res + i : nullptr;
+    }
+    return core_enqueue(c, what, (cudaStream_t)stream, scale);
+}
+
+cvc_status cvc_batch_get_error(cvc_batch* b, int i, cvc_stream_t stream, cvc_status* status) {
+    if (!b || !status || i < 0 || i >= b->core.n) return CVC_ERR_INVALID_ARG;
+    return core_take_error(&b->core, i, (cudaStream_t)stream, status);
 }
 
 cvc_status cvc_batch_set_shape(cvc_batch* b, int rle_rows, int tok_blocks) {
@@ -777,12 +838,14 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    // time `reps` steps of one shape; the records are refilled from the
-    // uncommitted state every time, so every run codes the same frame
+    // time `reps` steps of one shape; no run commits its coder state, so
+    // every run codes the same frame
     auto measure = [&](LaunchShape sh, float* ms) -> cvc_status {
         c->shape = sh;
         core_drop_graphs(c);
+        if (!core_begin(c)) return CVC_ERR_CUDA;
         if (!batch_fill(c, what, io)) return CVC_ERR_INVALID_ARG;
+        for (int i = 0; i < c->n; i++) c->h_sc[i].no_commit = 1;
         cvc_status s = core_enqueue(c, what, st);   // warm-up (and graph capture)
         if (s != CVC_OK) return s;
         cudaEventRecord(e0, st);

@@ -33,6 +33,7 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_sd, n);
     k.add(&c->d_sc, n);
     k.add(&c->d_rs, n);
+    k.add(&c->d_ctl, n);
     k.add(&c->d_pd, c->h_pd.size());
     k.add(&c->d_blk_colour, c->h_blk_colour.size());
     k.add(&c->d_blk_plane, c->h_blk_plane.size());
@@ -237,8 +238,11 @@ Core::~Core() {
     scale.clear();   // graphs first
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (arena) cudaFree(arena);
-    if (h_sc) cudaFreeHost(h_sc);
-    if (h_rs) cudaFreeHost(h_rs);
+    for (int k = 0; k < CORE_RING; k++) {
+        if (ring_sc[k]) cudaFreeHost(ring_sc[k]);
+        if (ring_rs[k]) cudaFreeHost(ring_rs[k]);
+        if (ring_ev[k]) cudaEventDestroy(ring_ev[k]);
+    }
     for (int s = 0; s < CVC_NUM_STAGES; s++)
         for (int e = 0; e < 2; e++)
             if (ev[s][e]) cudaEventDestroy(ev[s][e]);
@@ -291,6 +295,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.hdr_bytes = 32 + 4LL * D.ncomp;
         D.max_tok = 2 * D.ncoef + 64;
         D.mv_range = P.motion_range;
+        D.key_interval = P.key_interval;
         if (P.motion_range > 0) {
             // 16 x 16 blocks of the padded luma plane, one motion search block each
             D.nby = (g.Hp + 15) / 16;
@@ -419,13 +424,23 @@ cvc_status core_alloc(Core* c) {
         return CVC_ERR_NOMEM;
     }
     k.assign(static_cast<char*>(c->arena));
-    if (cudaMallocHost((void**)&c->h_sc, sizeof(SCall) * c->n) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_rs, sizeof(SResult) * c->n) != cudaSuccess) {
-        cudaGetLastError();
-        return CVC_ERR_NOMEM;
+    for (int r = 0; r < Core::CORE_RING; r++) {
+        if (cudaMallocHost((void**)&c->ring_sc[r], sizeof(SCall) * c->n) != cudaSuccess ||
+            cudaMallocHost((void**)&c->ring_rs[r], sizeof(SResult) * c->n) != cudaSuccess) {
+            cudaGetLastError();
+            return CVC_ERR_NOMEM;
+        }
+        memset(c->ring_sc[r], 0, sizeof(SCall) * c->n);
+        memset(c->ring_rs[r], 0, sizeof(SResult) * c->n);
+        if (cudaEventCreateWithFlags(&c->ring_ev[r], cudaEventDisableTiming) != cudaSuccess) {
+            c->ring_ev[r] = nullptr;
+            cudaGetLastError();
+            return CVC_ERR_CUDA;
+        }
     }
-    memset(c->h_sc, 0, sizeof(SCall) * c->n);
-    memset(c->h_rs, 0, sizeof(SResult) * c->n);
+    c->ring_slot = 0;
+    c->h_sc = c->ring_sc[0];
+    c->h_rs = c->ring_rs[0];
     bool ok = put(c->d_sd, c->sd) && put(c->d_pd, c->h_pd) && put(c->d_blk_colour, c->h_blk_colour) &&
               put(c->d_blk_plane, c->h_blk_plane) &&
               put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
@@ -440,26 +455,38 @@ cvc_status core_alloc(Core* c) {
     for (int b = 0; b < 2 && ok; b++)
         ok = cudaMemset(c->d_est_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess &&
              cudaMemset(c->d_dst_buf[b], 0, (size_t)c->ncoef * 2) == cudaSuccess;
+    // coder state: frame 0 next, the decoder waiting for a K-frame
+    std::vector<SCtl> ctl(c->n);
+    for (SCtl& t : ctl) {
+        memset(&t, 0, sizeof(t));
+        t.dec_next = -1;
+    }
+    ok = ok && put(c->d_ctl, ctl);
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    c->enc_frame.assign(c->n, 0);
-    c->dec_next.assign(c->n, -1);
-    c->ecur.assign(c->n, 0);
-    c->dcur.assign(c->n, 0);
-    c->dec_floor.assign(c->n, 0);
+    c->pend_reset.assign(c->n, 0);
     return CVC_OK;
 }
 
 void core_reset(Core* c, int s) {
     for (int i = 0; i < c->n; i++)
-        if (s < 0 || s == i) {
-            c->enc_frame[i] = 0;
-            c->dec_next[i] = -1;
-            c->dec_floor[i] = 0;
-        }
+        if (s < 0 || s == i) c->pend_reset[i] = 1;
+}
+
+bool core_begin(Core* c) {
+    const int r = (c->ring_slot + 1) % Core::CORE_RING;
+    if (c->ring_used[r] && cudaEventSynchronize(c->ring_ev[r]) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->ring_slot = r;
+    c->h_sc = c->ring_sc[r];
+    c->h_rs = c->ring_rs[r];
+    memset(c->h_sc, 0, sizeof(SCall) * c->n);
+    return true;
 }
 
 void core_drop_graphs(Core* c) {
@@ -507,8 +534,11 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
     const int n = c->n;
     long long k = 0;
     *nl = 0;
-    CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->d_rs, 0, sizeof(SResult) * n, st));
+    // the call records' coder-state fields from the device-resident state
+    k_step_begin<<<(int)cdiv(n, 128), 128, 0, st>>>(c->d_sd, c->d_sc, c->d_ctl, n);
+    CK(cudaGetLastError());
+    k += 1;
     const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->d_row_comp, c->d_row_mc, c->nrows};
     const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
                        c->d_comp_level, c->d_comp_plane, c->d_comp_ey, c->d_comp_ex, c->ncomp};
@@ -620,7 +650,10 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         clk.end(9, ncol);
         k += 8 + 2 + ncol + engine_part_launches(ie, INV, 1) + engine_part_launches(ie, INV, 0);
     }
-    CK(cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(SResult) * n, cudaMemcpyDeviceToHost, st));
+    // statuses, lengths and frame types; the coder state advances where the call succeeded
+    k_step_commit<<<(int)cdiv(n, 128), 128, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_ctl, n);
+    CK(cudaGetLastError());
+    k += 1;
     *nl = k;
     return cudaSuccess;
 }
@@ -657,23 +690,35 @@ cvc_status core_enqueue(Core* c, int mode, cudaStream_t st, int scale) {
     // every decoder output buffer was checked for the scale the step writes
     for (int i = 0; i < c->n; i++)
         if (c->h_sc[i].dec_on && c->h_sc[i].dec_scale != scale) return CVC_ERR_INVALID_ARG;
-    if (!c->use_graphs || c->timing) {
-        long long nl = 0;
-        if (enqueue_direct(c, mode, scale, st, c->timing, &nl) != cudaSuccess) {
-            cudaGetLastError();
-            return CVC_ERR_CUDA;
-        }
-        note_launches(nl);
-        return CVC_OK;
+    const bool graph = c->use_graphs && !c->timing;
+    if (graph) {
+        cvc_status s = core_capture(c, mode, scale);
+        if (s != CVC_OK) return s;
     }
-    cvc_status s = core_capture(c, mode, scale);
-    if (s != CVC_OK) return s;
-    const ScalePlan& sp = *c->scale[scale];
-    if (cudaGraphLaunch(sp.gexec[mode], st) != cudaSuccess) {
+    // resets requested since the last step go with this one
+    for (int i = 0; i < c->n; i++)
+        if (c->pend_reset[i]) c->h_sc[i].reset = 1;
+    // the records in, the step, the results out; the slot is free again once they are back
+    const size_t n = (size_t)c->n;
+    cudaError_t e = cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(SCall) * n, cudaMemcpyHostToDevice, st);
+    long long nl = 0;
+    if (e == cudaSuccess) {
+        if (graph) {
+            e = cudaGraphLaunch(c->scale[scale]->gexec[mode], st);
+            nl = c->scale[scale]->gkernels[mode];
+        } else {
+            e = enqueue_direct(c, mode, scale, st, c->timing, &nl);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(SResult) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ring_ev[c->ring_slot], st);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
     }
-    note_launches(sp.gkernels[mode]);
+    c->ring_used[c->ring_slot] = true;
+    for (int i = 0; i < c->n; i++) c->pend_reset[i] = 0;
+    note_launches(nl);
     return CVC_OK;
 }
 
@@ -712,8 +757,6 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale) {
         C.pitch_in = (long long)io.pitch;
         C.out = io.out;
         C.out_cap = (long long)std::min<size_t>(io.out_cap, (size_t)1 << 62);
-        C.enc_key = (c->enc_frame[s] % c->prm[s].key_interval) == 0;
-        C.enc_index = (uint32_t)c->enc_frame[s];
     }
     if ((mode & STEP_DEC) && io.rgb_out) {
         if (scale < 0 || scale > c->prm[s].levels) return false;
@@ -731,55 +774,35 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale) {
             C.in = io.in;
             C.in_len = (long long)std::min<size_t>(io.in_len, (size_t)1 << 62);
         }
-        C.dec_expect = c->dec_next[s];
         C.dec_scale = scale;
-        C.dec_floor = c->dec_floor[s];
     }
-    C.ecur = c->ecur[s];
-    C.dcur = c->dcur[s];
     return true;
 }
 
 void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
                  int* dec_type, unsigned* dec_index) {
     (void)mode;
-    const SCall& C = c->h_sc[s];
-    const SResult& R = c->h_rs[s];
-    const SDesc& D = c->sd[s];
-    cvc_status es = CVC_OK, ds = CVC_OK;
-    size_t len = 0;
-    int ty = -1, dty = -1;
-    unsigned didx = 0;
-    if (C.enc_on) {
-        const bool mc = !C.enc_key && D.mv_range > 0;
-        const long long need = D.hdr_bytes + 2LL * R.enc_tokens + (mc ? D.mv_bytes : 0);
-        len = (size_t)need;
-        ty = C.enc_key ? 0 : (mc ? 2 : 1);
-        if (R.enc_err & EF_OVERFLOW) es = CVC_ERR_OVERFLOW;
-        else if (need > C.out_cap || (R.enc_err & EF_CAPACITY)) es = CVC_ERR_CAPACITY;
-        if (es == CVC_OK) {
-            c->ecur[s] = 1 - c->ecur[s];
-            c->enc_frame[s] += 1;
-        }
+    const cvc_batch_result& R = c->h_rs[s].res;
+    if (enc) *enc = R.enc_status;
+    if (dec) *dec = R.dec_status;
+    if (out_len) *out_len = R.out_len;
+    if (type) *type = R.frame_type;
+    if (dec_type) *dec_type = R.dec_frame_type;
+    if (dec_index) *dec_index = R.dec_frame_index;
+}
+
+cvc_status core_take_error(Core* c, int s, cudaStream_t st, cvc_status* err) {
+    // the word is read and cleared in stream order: errors of calls queued before
+    // this one on `st` are seen, later ones are kept for the next read
+    int* word = &c->d_ctl[s].first_err;
+    int v = 0;
+    if (cudaMemcpyAsync(&v, word, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(word, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
     }
-    if (C.dec_on) {
-        if (R.dec_err & EF_STATE) ds = CVC_ERR_STATE;
-        else if (R.dec_err & (EF_CORRUPT | EF_MISMATCH)) ds = CVC_ERR_CORRUPT;
-        if (ds == CVC_OK) {
-            dty = (int)R.dec_type;
-            didx = R.dec_index;
-            c->dcur[s] = 1 - c->dcur[s];
-            c->dec_next[s] = (long long)R.dec_index + 1;
-            const int drop = (int)R.dec_drop;
-            c->dec_floor[s] = R.dec_type == 0 ? drop : std::max(c->dec_floor[s], drop);
-        }
-    }
-    if (enc) *enc = es;
-    if (dec) *dec = ds;
-    if (out_len) *out_len = len;
-    if (type) *type = ty;
-    if (dec_type) *dec_type = dty;
-    if (dec_index) *dec_index = didx;
+    *err = (cvc_status)v;
+    return CVC_OK;
 }
 
 }  // namespace cvc

@@ -7,12 +7,15 @@
 // records copied from pinned host memory at the start of the step, and the
 // per-stream results come back through one copy at its end, so a step is a
 // fixed launch sequence that is captured once in a CUDA graph and replayed
-// for every frame.
+// for every frame.  The pinned records form a ring of CORE_RING slots, so
+// that the host can fill the next calls while earlier ones are in flight.
 //
-// Coder state stays consistent without host work between steps: a step
-// writes the NEXT state buffers (est[1-ecur], dst[1-dcur]) and the host flips
-// ecur / dcur only for streams whose step succeeded, so a failed or skipped
-// step leaves the stream exactly as it was.
+// Coder state lives on the device (SCtl per stream) and stays consistent
+// without host work between steps: a step writes the NEXT state buffers
+// (est[1-ecur], dst[1-dcur]) and its last kernel flips ecur / dcur and
+// advances the frame counters only for streams whose call succeeded, so a
+// failed or skipped call leaves the stream exactly as it was, and calls can
+// be queued back to back.
 #pragma once
 #include <memory>
 #include <vector>
@@ -90,16 +93,23 @@ struct Core {
     int8_t* d_mv = nullptr;                    // the encoder's motion vectors
     float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
     int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
+    SCtl* d_ctl = nullptr;                     // device-resident coder state, one per stream
     uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
     uint32_t *d_comp_tok = nullptr, *d_tok_base = nullptr, *d_contrib = nullptr, *d_pos = nullptr,
              *d_scan_tmp2 = nullptr;
-    // pinned per-call records
+    // pinned per-call records: a ring of slots, each a call's SCall and SResult
+    // arrays; ring_ev[k] completes when the last step that used slot k has
+    // copied its results back.  h_sc / h_rs point at the current slot.
+    static constexpr int CORE_RING = 8;
+    SCall* ring_sc[CORE_RING] = {};
+    SResult* ring_rs[CORE_RING] = {};
+    cudaEvent_t ring_ev[CORE_RING] = {};
+    bool ring_used[CORE_RING] = {};
+    int ring_slot = 0;
     SCall* h_sc = nullptr;
     SResult* h_rs = nullptr;
-    // per-stream coder state (host side)
-    std::vector<long long> enc_frame, dec_next;
-    std::vector<int> ecur, dcur;
-    std::vector<int> dec_floor;   // finest levels whose decoder state is missing (dropped in transmission)
+    // streams whose coder state the next step resets (cvc_reset: stream-ordered)
+    std::vector<uint8_t> pend_reset;
     // CUDA graphs of the step modes: one set per decoding scale (in ScalePlan)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
@@ -124,8 +134,12 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n);
 size_t core_device_bytes(const Core* c);
 // allocate, upload, reset the state; CVC_OK or NOMEM / CUDA
 cvc_status core_alloc(Core* c);
-// reset the coder state of stream s (s < 0: all)
+// reset the coder state of stream s (s < 0: all), from the next step on
 void core_reset(Core* c, int s);
+// start filling a new call: the next slot of the record ring (waits until the
+// step that used it CORE_RING calls ago has returned its results), all
+// streams' records cleared; false on a CUDA error
+bool core_begin(Core* c);
 // enqueue one step whose decoders output pyramid scale `scale` (the records
 // in h_sc must be filled for that scale); no synchronisation
 cvc_status core_enqueue(Core* c, int mode, cudaStream_t st, int scale = 0);
@@ -137,7 +151,7 @@ cvc_status core_set_timing(Core* c, bool on);
 // drop the captured graphs (after a change of launch shape)
 void core_drop_graphs(Core* c);
 
-// fill the call record of stream s for a step; returns false on bad arguments
+// fill the call record of stream s for a step (after core_begin); returns false on bad arguments
 struct StreamIo {
     const uint8_t* rgb;
     size_t pitch;
@@ -152,8 +166,11 @@ struct StreamIo {
 bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale = 0);
 // output size of stream s at a decoding scale
 void core_scaled_size(const Core* c, int s, int scale, int* h, int* w);
-// statuses of stream s after the step completed; commits the state on success
+// statuses of stream s after the step completed (the device has already
+// advanced the coder state of the streams whose call succeeded)
 void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
                  int* dec_type, unsigned* dec_index);
+// read and clear the first error of an asynchronous call of stream s (ordered on st; synchronises st)
+cvc_status core_take_error(Core* c, int s, cudaStream_t st, cvc_status* err);
 
 }  // namespace cvc

@@ -4,8 +4,9 @@
 //   normalisation and thresholding (§3.4-§3.6), K/P differencing (§3.7),
 //   run-length coding of rows (§3.8), their inverses, and device-wide scans.
 // Blocks find their stream / plane through block maps built at creation, so
-// no grid depends on per-call sizes; per-call arguments (buffers, frame type,
-// state parity) come from device records refreshed by one copy per call.
+// no grid depends on per-call sizes; per-call arguments (buffers) come from
+// device records refreshed by one copy per call, and the coder state (frame
+// index, state parity, the decoder's expectations) lives on the device.
 #include <algorithm>
 
 #include "k_codec.cuh"
@@ -13,6 +14,97 @@
 namespace cvc {
 
 __device__ __forceinline__ int mirror_idx(int a, int n) { return a < n ? a : 2 * n - 1 - a; }
+
+// ------------------------------------------------------- step begin / commit
+// §3.7: frame i of a stream (counted from its last reset) is a K-frame iff
+// i % key_interval == 0; a decoder accepts a P-frame only with the index
+// following the last frame it decoded, and only at scales its state covers.
+__global__ void k_step_begin(const SDesc* __restrict__ sd, SCall* __restrict__ sc, SCtl* __restrict__ ctl, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    SCall& C = sc[s];
+    SCtl& T = ctl[s];
+    if (C.reset) {
+        T.enc_frame = 0;
+        T.dec_next = -1;
+        T.dec_floor = 0;
+    }
+    C.ecur = T.ecur;
+    C.dcur = T.dcur;
+    if (C.enc_on) {
+        C.enc_key = (T.enc_frame % sd[s].key_interval) == 0;
+        C.enc_index = (uint32_t)T.enc_frame;
+    }
+    if (C.dec_on) {
+        C.dec_expect = T.dec_next;
+        C.dec_floor = T.dec_floor;
+        if (C.in_len_dev && C.in_len >= 0) {
+            const size_t len = *C.in_len_dev;
+            if (len < (size_t)C.in_len) C.in_len = (long long)len;
+        }
+    }
+}
+
+// The outcome of one stream's call.  Encoder: OVERFLOW when a code left int16,
+// CAPACITY when the frame does not fit out_cap (out_len is then the size it
+// needs); decoder: STATE for a P-frame without its reference (or below the
+// state's scale floor), CORRUPT for a malformed or mismatched stream.  A
+// successful call advances the coder state: the encoder's frame index and
+// state parity; the decoder's parity, expected index and scale floor (a
+// K-frame sets the floor to its own dropped levels, a P-frame can only raise
+// it).  A failed call leaves it as it was.
+__global__ void k_step_commit(const SDesc* __restrict__ sd, const SCall* __restrict__ sc, SResult* __restrict__ rs,
+                              SCtl* __restrict__ ctl, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const SDesc& D = sd[s];
+    const SCall& C = sc[s];
+    SResult& R = rs[s];
+    SCtl& T = ctl[s];
+    cvc_batch_result out;
+    out.enc_status = CVC_OK;
+    out.dec_status = CVC_OK;
+    out.out_len = 0;
+    out.frame_type = -1;
+    out.dec_frame_type = -1;
+    out.dec_frame_index = 0;
+    if (C.enc_on) {
+        const bool mc = !C.enc_key && D.mv_range > 0;
+        const long long need = D.hdr_bytes + 2LL * R.enc_tokens + (mc ? D.mv_bytes : 0);
+        out.out_len = (size_t)need;
+        out.frame_type = C.enc_key ? 0 : (mc ? 2 : 1);
+        if (R.enc_err & EF_OVERFLOW) out.enc_status = CVC_ERR_OVERFLOW;
+        else if (need > C.out_cap || (R.enc_err & EF_CAPACITY)) out.enc_status = CVC_ERR_CAPACITY;
+        if (out.enc_status == CVC_OK && !C.no_commit) {
+            T.ecur = 1 - T.ecur;
+            T.enc_frame += 1;
+        }
+    }
+    if (C.dec_on) {
+        if (R.dec_err & EF_STATE) out.dec_status = CVC_ERR_STATE;
+        else if (R.dec_err & (EF_CORRUPT | EF_MISMATCH)) out.dec_status = CVC_ERR_CORRUPT;
+        if (out.dec_status == CVC_OK) {
+            out.dec_frame_type = (int)R.dec_type;
+            out.dec_frame_index = R.dec_index;
+            if (!C.no_commit) {
+                const int drop = (int)R.dec_drop;
+                T.dcur = 1 - T.dcur;
+                T.dec_next = (long long)R.dec_index + 1;
+                T.dec_floor = R.dec_type == 0 ? drop : max(T.dec_floor, drop);
+            }
+        }
+    }
+    R.res = out;
+    const cvc_status first = out.enc_status != CVC_OK ? out.enc_status : out.dec_status;
+    if (C.async && first != CVC_OK && T.first_err == CVC_OK) T.first_err = first;
+    if (C.res_dev) *C.res_dev = out;
+    if (C.enc_on) {
+        if (C.out_len_dev) *C.out_len_dev = out.out_len;
+        if (C.type_dev) *C.type_dev = out.frame_type;
+        if (C.enc_status_dev) *C.enc_status_dev = out.enc_status;
+    }
+    if (C.dec_on && C.dec_status_dev) *C.dec_status_dev = out.dec_status;
+}
 
 // ------------------------------------------------------------- colour
 // YCoCg-R lifting (integer form of Table 1): Co = R-B, t = B + (Co>>1),

@@ -54,6 +54,7 @@ struct SDesc {
     long long mv_off;      // first block's (dy, dx) pair
     long long luma_off;    // bytes
     long long mv_bytes;    // 2 * nby * nbx
+    int key_interval;      // frame i is a K-frame iff i % key_interval == 0 (§3.7)
 };
 
 // the decoder's output stage of one stream at pyramid scale s (s = 0: full
@@ -70,7 +71,9 @@ struct ScaleDesc {
     int st8;               // 8-bit storage: Table I colour with chroma offset by 127
 };
 
-// per stream, refreshed every call
+// per stream, refreshed every call.  The host fills the buffers and switches;
+// the step's first kernel (k_step_begin) fills the coder-state fields (ecur ..
+// dec_floor) from the stream's device-resident SCtl.
 struct SCall {
     const uint8_t* rgb_in;
     long long pitch_in;
@@ -86,6 +89,17 @@ struct SCall {
     long long dec_expect;  // frame index a P-frame must carry; -1: a K-frame is required
     int dec_scale;         // pyramid scale of the decoder's output (its buffer was checked for it)
     int dec_floor;         // finest levels 1..dec_floor of the decoder state are missing
+    int reset;             // reset the stream's coder state before this step (cvc_reset)
+    int no_commit;         // leave the coder state as it was (autotuner runs)
+    int async;             // an asynchronous call: its first error is kept in SCtl::first_err
+    int pad;
+    const size_t* in_len_dev;         // non-NULL: the decoder's input length, read on the device
+                                      // (at most in_len, the capacity of the input buffer)
+    size_t* out_len_dev;              // non-NULL: where the device writes the encoded length
+    int* type_dev;                    // non-NULL: where the device writes the encoded frame type
+    cvc_status* enc_status_dev;       // non-NULL: where the device writes the encoder's status
+    cvc_status* dec_status_dev;       // non-NULL: where the device writes the decoder's status
+    cvc_batch_result* res_dev;        // non-NULL: where the device writes the stream's whole result
 };
 
 // per stream, written by the device every call
@@ -95,6 +109,20 @@ struct SResult {
     uint32_t dec_type, dec_index, dec_tokens;
     uint32_t dec_drop;       // finest levels the decoded frame left out
     uint32_t pad;
+    cvc_batch_result res;    // the call's outcome (k_step_commit)
+};
+
+// per stream, resident on the device: the coder state that decides each
+// call's frame type, the state buffers' parity and the decoder's checks.  A
+// step reads it first (k_step_begin) and updates it last (k_step_commit) only
+// where the call succeeded, so that calls can be queued without host work
+// between them.
+struct SCtl {
+    long long enc_frame;     // the encoder's next frame index
+    long long dec_next;      // frame index the decoder's next P-frame must carry; -1: a K-frame is required
+    int ecur, dcur;          // which of the two state buffers holds the current codes
+    int dec_floor;           // finest levels whose decoder state is missing (dropped in transmission)
+    int first_err;           // first non-OK status of an asynchronous call since the last read (cvc_get_error)
 };
 
 // per plane (three per stream)
@@ -133,6 +161,11 @@ struct CompTable {
 // element-wise kernels: ELEM_THREADS threads, ELEM_PER_THREAD elements each
 constexpr int ELEM_THREADS = 256, ELEM_PER_THREAD = 8, ELEM_BLOCK = ELEM_THREADS * ELEM_PER_THREAD;
 
+// first and last kernel of every step: the call records' coder-state fields from
+// the device-resident state, and the outcome of the call (statuses, lengths,
+// frame types; the state advanced where the call succeeded); a thread per stream
+__global__ void k_step_begin(const SDesc* sd, SCall* sc, SCtl* ctl, int n);
+__global__ void k_step_commit(const SDesc* sd, const SCall* sc, SResult* rs, SCtl* ctl, int n);
 __global__ void k_colour_fwd_b(const SDesc* sd, const SCall* sc, const int* blk_stream, float* planes,
                                uint8_t* luma0, uint8_t* luma1);
 // motion search of the P-frames of streams with a motion range: one block per 16 x 16 luma block,

@@ -258,11 +258,12 @@ struct cvc_server {
             }
             if (!mode) continue;
             const StreamIo none{nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0};
-            for (int s = 0; s < (int)sh->slot_session.size(); s++)
+            cvc_status st = core_begin(&sh->core) ? CVC_OK : CVC_ERR_CUDA;
+            for (int s = 0; s < (int)sh->slot_session.size() && st == CVC_OK; s++)
                 core_fill_call(&sh->core, s, mode, sh->inflight[s].kind ? stream_io(sh->inflight[s]) : none);
             sh->mode = mode;
             sh->t_launch = now_ns();
-            cvc_status st = core_enqueue(&sh->core, mode, sh->st);
+            if (st == CVC_OK) st = core_enqueue(&sh->core, mode, sh->st);
             if (st == CVC_OK && cudaEventRecord(sh->ev, sh->st) != cudaSuccess) st = CVC_ERR_CUDA;
             if (st != CVC_OK) {
                 cudaGetLastError();
