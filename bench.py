@@ -35,10 +35,42 @@ W_, H_, LEVELS, DIRS, QPH, QPL, KINT = 1920, 1080, 5, [5, 4, 4, 3, 3], 8, 1, 10
 METRIC = "1080p encode+decode frames/s"
 UNIT = "frames/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes per 1080p frame of the transform stages (dram__bytes_read.sum +
-# dram__bytes_write.sum over the stage's launches), from one ncu capture of a
-# batched step of 8 streams; to be dropped when those kernels change
-DRAM_PER_FRAME = {"lp_analysis": 27.5e6, "dfb_analysis": 104.8e6, "dfb_synthesis": 105.0e6, "lp_synthesis": 29.0e6}
+CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
+# Counters of one ncu capture of a batched 1080p step (8 streams), per frame:
+# the DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each
+# transform stage's launches and the warp instructions (smsp__inst_executed.sum)
+# of the whole step.  They hold only for the kernel sources they were taken on:
+# `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
+# them (roofline.traffic, roofline.alu) only while the sources still match.
+CAPTURE = {"sources_sha256": None, "dram_per_frame": {}, "warp_inst_per_frame": None,
+           "profile": None}
+# issue rate of one SM sub-partition: one warp instruction per cycle
+SMSP_PER_SM, N_SM = 4, 148
+
+
+def kernel_sources_sha():
+    """SHA-256 over the library's CUDA sources (file names and contents, sorted)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def host_info():
+    """nproc and the CPU model of this host"""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def _gen_frames(seed, n, start=0):
@@ -62,6 +94,23 @@ def make_frames(seed, n):
         return _gen_frames(seed, n)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_gen_one, [(seed, t) for t in range(n)]))
+
+
+def _gen_sized(args):
+    w, h, seed, t = args
+    from paper_1510_00561_b300 import synthetic as S
+    return S.SyntheticVideo(S.spec_for(w, h, seed=seed)).frame(t)
+
+
+def make_frames_sized(jobs):
+    """frames for a list of (width, height, seed, index), drawn in a spawn pool"""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = max(1, min(len(jobs), (os.cpu_count() or 2) - 1, 16))
+    if workers == 1:
+        return [_gen_sized(j) for j in jobs]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_sized, jobs))
 
 
 def combine_ranks(local_ms, local_units, dist=None, device=None):
@@ -201,6 +250,263 @@ def stage_bytes(info, tokens):
     }
 
 
+def _luma(x):
+    x = x.float()
+    return (x[..., 0] + 2 * x[..., 1] + x[..., 2]) / 4
+
+
+def sequence_run(dev, flush, w, h, L, k, qph, qpl, kint, n, seed, frames=None):
+    """The plain per-frame pipeline on one stream: n frames encoded one call each, then
+    decoded one call each, through the synchronous API (every call waits for its result),
+    each call bracketed by CUDA events with L2 flushed before it; then the same calls
+    through the asynchronous API, queued back to back (n encodes, then n decodes reading
+    their lengths from device memory), one synchronisation per direction, L2 flushed once
+    before each queue.  Also the mean stream size and the luma PSNR of the decoded frames."""
+    import numpy as np
+    import torch
+    from paper_1510_00561_b300 import Codec
+    from paper_1510_00561_b300 import synthetic as S
+    if frames is None:
+        frames = S.SyntheticVideo(S.spec_for(w, h, seed=seed)).frames(n)
+    frames = [torch.from_numpy(f).to(dev) for f in frames]
+    kw = dict(width=w, height=h, levels=L, dirs_log2=k, qph=qph, qpl=qpl, key_interval=kint)
+    enc, dec = Codec(**kw), Codec(**kw)
+    outs = [torch.empty(enc.max_stream, dtype=torch.uint8, device=dev) for _ in range(n)]
+    rgbs = [torch.empty((h, w, 3), dtype=torch.uint8, device=dev) for _ in range(n)]
+    st = torch.cuda.current_stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    for t in range(min(n, 3)):                               # warm-up of both APIs, then fresh coder state
+        s_, _ = enc.encode(frames[t], out=outs[t])
+        dec.decode(s_, out=rgbs[t])
+    enc.reset()
+    dec.reset()
+    w_len = torch.zeros(1, dtype=torch.int64, device=dev)
+    for t in range(min(n, 3)):
+        enc.encode_async(frames[t], outs[t], out_len=w_len)
+        dec.decode_async(outs[t], rgbs[t], in_len=w_len)
+    torch.cuda.synchronize()
+    assert enc.get_error() == 0 and dec.get_error() == 0
+    enc.reset()
+    dec.reset()
+    lens = [0] * n
+
+    def per_call(fn):
+        tot = 0.0
+        for t in range(n):
+            flush.zero_()
+            e0, e1 = ev(), ev()
+            e0.record(st)
+            fn(t)
+            e1.record(st)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    def enc_call(t):
+        s_, _ = enc.encode(frames[t], out=outs[t])
+        lens[t] = s_.numel()
+
+    enc_ms = per_call(enc_call)
+    dec_ms = per_call(lambda t: dec.decode(outs[t][:lens[t]], out=rgbs[t]))
+    mse = [float(((_luma(rgbs[t]) - _luma(frames[t])) ** 2).mean()) for t in range(n)]
+    enc.reset()
+    dec.reset()
+    d_len = torch.zeros(n, dtype=torch.int64, device=dev)
+
+    def queued(fn):
+        flush.zero_()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        for t in range(n):
+            fn(t)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    aenc_ms = queued(lambda t: enc.encode_async(frames[t], outs[t], out_len=d_len[t:t + 1]))
+    adec_ms = queued(lambda t: dec.decode_async(outs[t], rgbs[t], in_len=d_len[t:t + 1]))
+    assert d_len.cpu().tolist() == lens and enc.get_error() == 0 and dec.get_error() == 0
+    return {"frames": n, "qph": qph, "qpl": qpl,
+            "encode_frames_per_s": n * 1e3 / enc_ms, "decode_frames_per_s": n * 1e3 / dec_ms,
+            "encode_decode_frames_per_s": n * 1e3 / (enc_ms + dec_ms),
+            "async_encode_frames_per_s": n * 1e3 / aenc_ms, "async_decode_frames_per_s": n * 1e3 / adec_ms,
+            "async_encode_decode_frames_per_s": n * 1e3 / (aenc_ms + adec_ms),
+            "mean_stream_bytes": sum(lens) / n,
+            "y_psnr_db": float(np.mean([10 * np.log10(255.0 ** 2 / max(m, 1e-12)) for m in mse]))}
+
+
+def differentiable_run(dev, flush, steps=10, warm=3):
+    """The differentiable transform: batch 8 of 1088 x 1920 float luma planes (the 1080p
+    decomposition, 5 levels, 32/16/16/8/8), loss mean((S soft_T(A x) - x)^2) with one learnable
+    threshold per directional subband, forward and backward (hand-written adjoints) per step.
+    Algorithmic bytes of a step, each FP32 array read or written once per use: forward A (x in,
+    c out), soft threshold (c in, y out), inverse S (y in, x' out), the loss (x', x in) and its
+    gradient (out), S^T (in, out), the threshold backward (c and the gradient in, dL/dc out) and
+    A^T (in, out): 28 P + 36 C bytes per plane (P pixels, C coefficients)."""
+    import torch
+    from paper_1510_00561_b300 import synthetic as S
+    from paper_1510_00561_b300.autograd import ThresholdedReconstruction
+    H, W, B = 1088, 1920, 8
+    x = torch.from_numpy(S.luma_planes(B, W, H, seed=3)).to(dev)
+    m = ThresholdedReconstruction(H, W, LEVELS, DIRS, B, t_init=4.0, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        m.T.grad = None
+        loss = ((m(x) - x) ** 2).mean()
+        loss.backward()
+        return loss
+
+    for _ in range(warm):
+        step()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        loss = step()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    P, C = H * W, m.plan.total
+    nbytes = B * (28 * P + 36 * C)
+    pk = peaks()
+    return {"workload": "differentiable CT, batch 8 of 1088x1920 float32 luma planes, 5 levels, 32/16/16/8/8, "
+                        "forward + adjoint backward with 80 learnable thresholds",
+            "ms_per_step": ms, "planes_per_s": B * 1e3 / ms, "steps": steps, "loss": float(loss),
+            "algorithmic_bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms / 1e3) / 1e9,
+            "frac": nbytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "l2": "flushed before every step"}
+
+
+MIXED_CLASSES = [(176, 144, 3, [3, 2, 2]), (352, 288, 3, [3, 2, 2]), (640, 480, 4, [4, 3, 3, 2]),
+                 (1280, 720, 5, [5, 4, 4, 3, 3])]
+
+
+def mixed_batch_run(dev, flush, T=30, warm=3, per_class=16, distinct=30):
+    """Batched multi-stream coding: 64 streams (16 each of QCIF, CIF, VGA, 720p, pyramid depth
+    3/3/4/5), step 8, K every 10, one encode+decode per stream per step, each step one CUDA-graph
+    launch; stream j of a class shows its class's sequence shifted by 2j frames.  T timed steps,
+    L2 flushed before each."""
+    import torch
+    from paper_1510_00561_b300 import Batch
+    jobs = [(w, h, 70 + ci, t) for ci, (w, h, _, _) in enumerate(MIXED_CLASSES) for t in range(distinct)]
+    flat = make_frames_sized(jobs)
+    seqs = [[torch.from_numpy(f).to(dev) for f in flat[ci * distinct:(ci + 1) * distinct]]
+            for ci in range(len(MIXED_CLASSES))]
+    streams = [dict(width=w, height=h, levels=L, dirs_log2=k, qph=QPH, qpl=QPL, key_interval=KINT)
+               for (w, h, L, k) in MIXED_CLASSES for _ in range(per_class)]
+    b = Batch(streams)
+    outs = [torch.empty((s["height"], s["width"], 3), dtype=torch.uint8, device=dev) for s in streams]
+
+    def frames_at(t):
+        return [seqs[ci][(t + 2 * j) % distinct] for ci in range(len(MIXED_CLASSES)) for j in range(per_class)]
+
+    for t in range(warm):
+        b.step(3, rgb=frames_at(t), rgb_out=outs)
+    b.reset()
+    st = torch.cuda.current_stream()
+    tot, nbytes = 0.0, 0
+    for t in range(T):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        res = b.step(3, rgb=frames_at(t), rgb_out=outs)
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        nbytes += sum(r["out_len"] for r in res)
+    n = len(streams)
+    return {"workload": "64 streams (16 each QCIF, CIF, VGA, 720p; 3/3/4/5 levels), encode+decode, one "
+                        "graph launch per step, %d steps" % T,
+            "frames_per_s": n * T * 1e3 / tot, "ms_per_step": tot / T, "steps": T,
+            "mean_stream_bytes": nbytes / (n * T), "l2": "flushed before every step"}
+
+
+def plain_e2e_async(kw, h_frames, dev, steps, ring=4):
+    """The plain per-frame path end to end through host buffers, with the asynchronous API: per
+    frame the pinned RGB frame goes up, is encoded, its bitstream comes down to pinned memory and
+    goes back up (a sender's and a receiver's copies), is decoded, and the decoded frame comes
+    down.  Coding runs on the compute stream, copies on a copy stream; the host reads each
+    frame's length (8 bytes copied after its encode) while the next frame's encode is already
+    queued, so the device never waits for the host.  Returns (frames/s, H2D bytes/frame,
+    D2H bytes/frame)."""
+    import torch
+    from paper_1510_00561_b300 import Codec
+    enc, dec = Codec(**kw), Codec(**kw)
+    H, W = kw["height"], kw["width"]
+    cs, cp = torch.cuda.current_stream(), torch.cuda.Stream(dev)
+    R = ring
+    d_in = [torch.empty((H, W, 3), dtype=torch.uint8, device=dev) for _ in range(R)]
+    d_out = [torch.empty(enc.max_stream, dtype=torch.uint8, device=dev) for _ in range(R)]
+    d_sin = [torch.empty(enc.max_stream, dtype=torch.uint8, device=dev) for _ in range(R)]
+    d_rgb = [torch.empty((H, W, 3), dtype=torch.uint8, device=dev) for _ in range(R)]
+    h_str = [torch.empty(enc.max_stream, dtype=torch.uint8).pin_memory() for _ in range(R)]
+    h_rgb = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(R)]
+    d_len = torch.zeros(R, dtype=torch.int64, device=dev)
+    h_len = torch.zeros(R, dtype=torch.int64).pin_memory()
+    ev = {name: [torch.cuda.Event() for _ in range(R)] for name in ("in", "enc", "sin", "dec", "done")}
+    io = [0, 0]
+
+    def upload_encode(t):
+        k = t % R
+        if t >= R:
+            ev["done"][k].synchronize()          # frame t - R has left slot k
+        with torch.cuda.stream(cp):
+            d_in[k].copy_(h_frames[t % len(h_frames)], non_blocking=True)
+            ev["in"][k].record(cp)
+        cs.wait_event(ev["in"][k])
+        enc.encode_async(d_in[k], d_out[k], out_len=d_len[k:k + 1], stream=cs)
+        h_len[k:k + 1].copy_(d_len[k:k + 1], non_blocking=True)
+        ev["enc"][k].record(cs)
+        io[0] += d_in[k].numel()
+
+    def round_trip_decode(t):
+        k = t % R
+        ev["enc"][k].synchronize()
+        n = int(h_len[k])
+        with torch.cuda.stream(cp):
+            cp.wait_event(ev["enc"][k])
+            h_str[k][:n].copy_(d_out[k][:n], non_blocking=True)
+            d_sin[k][:n].copy_(h_str[k][:n], non_blocking=True)
+            ev["sin"][k].record(cp)
+        cs.wait_event(ev["sin"][k])
+        dec.decode_async(d_sin[k][:n], d_rgb[k], stream=cs)
+        ev["dec"][k].record(cs)
+        with torch.cuda.stream(cp):
+            cp.wait_event(ev["dec"][k])
+            h_rgb[k].copy_(d_rgb[k], non_blocking=True)
+            ev["done"][k].record(cp)
+        io[0] += n
+        io[1] += n + d_rgb[k].numel() + 8
+
+    def run(nsteps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cs)
+        cp.wait_event(e0)
+        upload_encode(0)
+        for t in range(1, nsteps):
+            upload_encode(t)
+            round_trip_decode(t - 1)
+        round_trip_decode(nsteps - 1)
+        cs.wait_stream(cp)
+        e1.record(cs)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    run(min(steps, 4))
+    enc.reset()
+    dec.reset()
+    io[0] = io[1] = 0
+    ms = run(steps)
+    assert enc.get_error() == 0 and dec.get_error() == 0
+    return steps * 1e3 / ms, io[0] // steps, io[1] // steps
+
+
 def cpu_oracle_rate(frames, band_rows=None, seconds_cap=30.0):
     """Oracle encode+decode frames/s on host cores (single thread), on a bounded
     sample: whole frames, or horizontal bands of band_rows rows of them."""
@@ -218,6 +524,34 @@ def cpu_oracle_rate(frames, band_rows=None, seconds_cap=30.0):
             break
     dt = time.perf_counter() - t0
     return done * rows / H_ / dt, done, dt
+
+
+def _oracle_stream(args):
+    """One worker process: the oracle encodes and decodes `n` frames of its own 1080p stream
+    (single-threaded); returns (frames, wall-clock start, wall-clock end) of the coding alone."""
+    seed, n = args
+    import numpy as np
+    import oracle as O
+    frames = _gen_frames(seed, n)
+    cod = O.Codec(W_, H_, LEVELS, DIRS, QPH, QPL, 0.0, KINT)
+    t0 = time.time()
+    for f in frames:
+        s, _ = cod.encode(np.ascontiguousarray(f))
+        cod.decode(s)
+    return n, t0, time.time()
+
+
+def cpu_oracle_parallel(workers, frames_each=2):
+    """Oracle encode+decode frames/s with `workers` processes on the host cores, each coding
+    its own stream (streams are independent, so this is how the oracle uses many cores
+    without any change to it).  Rate = all frames / (last end - first start)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_stream, [(100 + i, frames_each) for i in range(workers)]))
+    n = sum(r[0] for r in res)
+    dt = max(r[2] for r in res) - min(r[1] for r in res)
+    return n / dt, n, dt
 
 
 SERVE_CLASSES = [  # (width, height, levels, dirs_log2, weight)
@@ -514,7 +848,8 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "1080p CVC encode+decode, 5-level CT 32/16/16/8/8, step 8, K every 10",
                        "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -537,6 +872,13 @@ def main():
     ap.add_argument("--motion-range", type=int, default=8, help="search range of the motion pass (0: skip)")
     ap.add_argument("--no-rd", action="store_true", help="skip the QCIF rate-distortion sweeps")
     ap.add_argument("--no-taps", action="store_true", help="skip the 6- and 8-tap DFB prototype pass")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the QCIF / VGA sequences, the differentiable transform and the mixed batch")
+    ap.add_argument("--profile", action="store_true",
+                    help="for ncu: --warmup batched steps, then one step inside the NVTX range 'profile_step'; "
+                         "no timing, no JSON line")
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="processes of the many-core oracle baseline (0: min(nproc, 16))")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -549,6 +891,9 @@ def main():
         return
 
     frames = make_frames(seed=rank, n=args.frames)
+    vga_frames = None
+    if not args.no_suite:
+        vga_frames = make_frames_sized([(640, 480, 0, t) for t in range(60)])
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -562,6 +907,22 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.profile:
+        d_frames = [torch.from_numpy(f).to(dev) for f in frames]
+        B = args.batch
+        pb = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
+                         key_interval=KINT)] * B)
+        p_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
+        for i in range(args.warmup + 1):
+            if i == args.warmup:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("profile_step")
+            pb.step(3, rgb=[d_frames[(i + 3 * j) % len(d_frames)] for j in range(B)], rgb_out=p_outs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("profiled one batched step of %d streams (P-frame %d)" % (B, args.warmup), flush=True)
+        return
 
     codec = Codec(W_, H_, LEVELS, DIRS, QPH, QPL, 0.0, KINT)
     d_frames = [torch.from_numpy(f).to(dev) for f in frames]
@@ -622,10 +983,15 @@ def main():
         io_bytes[1] += n + rgb.numel()
 
     plain_e2e_value = combine_ranks(timed(plain_e2e_step, e2e_steps, flush_between=False), e2e_steps, dist, dev)[0]
-    plain = {"value": plain_value, "ms_per_step": plain_ms / args.steps, "streams_per_gpu": 1,
-             "e2e": {"value": plain_e2e_value, "unit": UNIT,
-                     "h2d_bytes_per_step": io_bytes[0] // e2e_steps, "d2h_bytes_per_step": io_bytes[1] // e2e_steps}}
     del codec
+    kw1080 = dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL, key_interval=KINT)
+    a_rate, a_h2d, a_d2h = plain_e2e_async(kw1080, h_frames, dev, e2e_steps)
+    a_value = combine_ranks(e2e_steps * 1e3 / a_rate, e2e_steps, dist, dev)[0]
+    plain = {"value": plain_value, "ms_per_step": plain_ms / args.steps, "streams_per_gpu": 1,
+             "e2e": {"value": plain_e2e_value, "unit": UNIT, "api": "synchronous calls",
+                     "h2d_bytes_per_step": io_bytes[0] // e2e_steps, "d2h_bytes_per_step": io_bytes[1] // e2e_steps},
+             "e2e_async": {"value": a_value, "unit": UNIT, "api": "asynchronous calls, copies on a copy stream",
+                           "h2d_bytes_per_step": a_h2d, "d2h_bytes_per_step": a_d2h}}
 
     # -------------------------------------------------------------- batched
     # B concurrent 1080p streams; stream j shows the rank's sequence shifted by 3j frames
@@ -823,6 +1189,15 @@ def main():
 
     rd = rd_run(dev) if (not args.no_rd and rank == 0) else None
 
+    # the other workloads: QCIF and VGA plain sequences, the differentiable transform, the mixed batch
+    suite = None
+    if not args.no_suite:
+        suite = {"qcif_plain": sequence_run(dev, flush, 176, 144, 3, [3, 2, 2], 8, 1, 8, 16, seed=0),
+                 "vga": [sequence_run(dev, flush, 640, 480, 4, [4, 3, 3, 2], q, 1, 10, 60, seed=0,
+                                      frames=vga_frames) for q in (4, 8, 16)],
+                 "differentiable": differentiable_run(dev, flush),
+                 "mixed_batch": mixed_batch_run(dev, flush)}
+
     # served form: continuous batching of concurrent streams under a memory budget
     served = None
     if args.serve_seconds > 0:
@@ -837,7 +1212,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant stage (per-stage CUDA events, batched steps)
+    # ---- rooflines (per-stage CUDA events of batched steps; ncu counters where they match the sources)
     pk = peaks()
     frames_staged = stage_steps * B
     mean_bytes = batch_bytes[0] / ((args.warmup + args.steps + stage_steps) * B)
@@ -849,19 +1224,55 @@ def main():
     per_launch_ms = ms_dom / max(1, n_dom)
     bytes_per_launch = sb[dom] * frames_staged / max(1, n_dom)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    traffic = None
-    if dom in DRAM_PER_FRAME:
-        traffic = DRAM_PER_FRAME[dom] * frames_staged / max(1, n_dom)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": dom,
-            "peak_source": pk["source"], "launches": n_dom,
+    sources_ok = CAPTURE["sources_sha256"] is not None and CAPTURE["sources_sha256"] == kernel_sources_sha()
+    dram = CAPTURE["dram_per_frame"] if sources_ok else {}
+    # the whole path, as the survey defines its algorithmic traffic: per frame the encoder reads
+    # the RGB frame (3N) and the coder state (2C), writes the state (2C) and the stream (S); the
+    # decoder reads the stream (S) and its state (2C), writes the state (2C) and the frame (3N)
+    N, C = W_ * H_, info.coeffs
+    path_bytes = 6 * N + 8 * C + 2 * mean_bytes
+    path_gbs = path_bytes * value / 1e9
+    bw_roof = pk["hbm_gbs"] * 1e9 / path_bytes
+    # issue-slot roof: the step's warp instructions per frame (ncu) against 148 SMs x 4
+    # sub-partitions x one warp instruction per cycle at the SM clock sampled in the timed region
+    alu = None
+    if sources_ok and CAPTURE["warp_inst_per_frame"]:
+        mhz = (clk or {}).get("sm_mhz") or 2032.0
+        slots = N_SM * SMSP_PER_SM * mhz * 1e6
+        alu = {"warp_inst_per_frame": CAPTURE["warp_inst_per_frame"], "issue_slots_per_s": slots,
+               "sm_mhz": mhz, "roof_frames_per_s": slots / CAPTURE["warp_inst_per_frame"],
+               "frac": value / (slots / CAPTURE["warp_inst_per_frame"])}
+    roofs = {"hbm": bw_roof}
+    if alu:
+        roofs["alu"] = alu["roof_frames_per_s"]
+    binding = min(roofs, key=roofs.get)
+    roof = {"bound": "hbm", "achieved": path_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": path_gbs / pk["hbm_gbs"], "path_frac": path_gbs / pk["hbm_gbs"],
+            "traffic": dram.get("step") * 1.0 if dram.get("step") else None,
+            "definition": "whole encode+decode path per 1080p frame: algorithmic bytes 6N + 8C + 2S "
+                          "(N pixels, C coefficients, S mean stream bytes) x frames/s, against the measured "
+                          "copy bandwidth; traffic = DRAM bytes of one step's launches per frame (ncu)",
+            "bytes_per_frame": path_bytes, "roof_frames_per_s": bw_roof, "peak_source": pk["source"],
+            "alu": alu, "binding_roof": binding, "frac_of_binding_roof": value / roofs[binding],
+            "counters": CAPTURE["profile"] if sources_ok else "no ncu capture of the current kernel sources",
+            "dominant_stage": {"stage": dom, "achieved": achieved, "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                               "launches": n_dom, "bytes_per_launch": bytes_per_launch,
+                               "traffic": dram[dom] * frames_staged / max(1, n_dom) if dom in dram else None,
+                               "definition": "the stage's algorithmic bytes (each launch reads and writes "
+                                             "what it touches once) over the stage's CUDA-event time"},
             "stages_ms_per_frame": {k: v[0] / frames_staged for k, v in stage.items()}}
 
     cpu = None
     if not args.no_cpu_baseline:
         rate, done, dt = cpu_oracle_rate(frames[:2], seconds_cap=25.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d full 1080p frames (K then P) encoded+decoded by the FP64 oracle in %.1f s" % (done, dt)}
+        hi = host_info()
+        workers = args.cpu_workers or max(1, min(hi["nproc"] or 1, 16))
+        prate, pdone, pdt = cpu_oracle_parallel(workers)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", **hi,
+               "sample": "%d full 1080p frames (K then P) encoded+decoded by the FP64 oracle in %.1f s" % (done, dt),
+               "all_cores": {"value": prate, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": "%d processes, each coding 2 frames (K then P) of its own 1080p stream: "
+                                       "%d frames in %.1f s" % (workers, pdone, pdt)}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -873,7 +1284,8 @@ def main():
                        "l2": "flushed (256 MB write) before every step" if not args.no_flush else "not flushed",
                        "parallelism": "replicas (stream sharding)" if world > 1 else "single GPU",
                        "mean_stream_bytes": mean_bytes},
-            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "taps": taps, "deflate": deflate, "rd": rd,
+            "plain": plain, "served": served, "scalable": scalable, "motion": motion, "taps": taps, "deflate": deflate,
+            "rd": rd, "suite": suite,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes[0] // e2e_steps,
                     "d2h_bytes_per_step": io_bytes[1] // e2e_steps},
