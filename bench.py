@@ -560,7 +560,7 @@ SERVE_CLASSES = [  # (width, height, levels, dirs_log2, weight)
 
 
 def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, budget=120 << 30, slots=16,
-               ring=4, seed=0):
+               ring=4, seed=0, depth=1):
     """Continuous-batching run: n_streams sessions with resolutions drawn by
     the class weights, Poisson frame arrivals at fps * load per session, each
     arrival an encode + decode request.  Frames are crops of the 1080p
@@ -570,9 +570,10 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
     import numpy as np
     import torch
     from paper_1510_00561_b300 import Codec, Server
+    from paper_1510_00561_b300 import _lib as cvclib
     rng = np.random.default_rng(seed)
     cls = rng.choice(len(SERVE_CLASSES), n_streams, p=[c[4] for c in SERVE_CLASSES])
-    srv = Server(budget, slots_per_shard=slots)
+    srv = Server(budget, slots_per_shard=slots, steps_in_flight=depth)
     sess = []
     max_stream = {}
     for i in range(n_streams):
@@ -582,8 +583,18 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
             max_stream[(w, h)] = Codec(**cfg).max_stream
         bufs = [(torch.empty(max_stream[(w, h)], dtype=torch.uint8, device=dev),
                  torch.empty((h, w, 3), dtype=torch.uint8, device=dev)) for _ in range(ring)]
-        sess.append(dict(id=srv.open(**cfg), w=w, h=h, bufs=bufs, free=list(range(ring)),
+        # one prepared request record per ring buffer; a request only sets its frame
+        ios = []
+        for out, rgb_out in bufs:
+            io = cvclib.BatchIo()
+            io.pitch_bytes = d_frames[0].stride(0)
+            io.d_out, io.out_cap = out.data_ptr(), out.numel()
+            io.d_rgb_out, io.pitch_out = rgb_out.data_ptr(), rgb_out.stride(0)
+            ios.append(io)
+        sess.append(dict(id=srv.open(**cfg), w=w, h=h, bufs=bufs, ios=ios, free=list(range(ring)),
                          arrivals=collections.deque(), t=0))
+    # frames are top-left crops of the 1080p frames: the same base pointers and row pitch
+    frame_ptr = [f.data_ptr() for f in d_frames]
     setup = srv.stats()
     # arrival times (seconds from start) of every session
     events = []
@@ -601,6 +612,9 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
     deadline = t0 + int(seconds * 4e9)
     pending = set()        # sessions with arrivals not yet submitted
 
+    F = len(d_frames)
+    ev_t = [t0 + int(t * 1e9) for t, _ in events]
+
     def pump():
         nonlocal tag
         for i in list(pending):
@@ -608,10 +622,10 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
             while S["arrivals"] and S["free"]:
                 arr = S["arrivals"].popleft()
                 b = S["free"].pop()
-                out, rgb_out = S["bufs"][b]
-                f = d_frames[S["t"] % len(d_frames)][:S["h"], :S["w"]]
+                io = S["ios"][b]
+                io.d_rgb = frame_ptr[S["t"] % F]
                 S["t"] += 1
-                srv.submit(S["id"], 3, rgb=f, out=out, rgb_out=rgb_out, tag=tag)
+                srv.submit_io(S["id"], 3, io, tag)
                 inflight[tag] = (i, b, arr)
                 tag += 1
             if not S["arrivals"]:
@@ -619,17 +633,17 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
 
     while True:
         now = Server.now_ns()
-        while ev_i < len(events) and t0 + int(events[ev_i][0] * 1e9) <= now:
-            t_arr, i = events[ev_i]
-            sess[i]["arrivals"].append(t0 + int(t_arr * 1e9))
+        while ev_i < len(events) and ev_t[ev_i] <= now:
+            i = events[ev_i][1]
+            sess[i]["arrivals"].append(ev_t[ev_i])
             pending.add(i)
             ev_i += 1
         pump()
-        for c in srv.poll(wait_us=200):
-            i, b, arr = inflight.pop(c["tag"])
+        for tg, es, ds, t_done in srv.poll_raw(wait_us=200):
+            i, b, arr = inflight.pop(tg)
             sess[i]["free"].append(b)
-            if c["enc_status"] == 0 and c["dec_status"] == 0:
-                lat.append((c["t_done_ns"] - arr) / 1e6)
+            if es == 0 and ds == 0:
+                lat.append((t_done - arr) / 1e6)
                 done += 1
             if sess[i]["arrivals"]:
                 pending.add(i)
@@ -642,7 +656,8 @@ def served_run(d_frames, dev, n_streams=256, fps=30.0, load=1.0, seconds=3.0, bu
     wall = (t_end - t0) / 1e9
     lat_sorted = sorted(lat)
     q = lambda p: lat_sorted[min(len(lat_sorted) - 1, int(p * len(lat_sorted)))] if lat_sorted else None
-    return {"streams": n_streams, "load": load, "offered_fps": len(events) / seconds,
+    return {"streams": n_streams, "load": load, "slots_per_shard": slots, "steps_in_flight": depth,
+            "offered_fps": len(events) / seconds,
             "completed": done, "requests": len(events), "frames_per_s": done / wall, "wall_s": wall,
             "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat_sorted[-1] if lat_sorted else None,
             "shards": setup["shards"], "admitted": setup["active_sessions"], "waiting": setup["waiting_sessions"],
@@ -868,6 +883,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served run (0: skip)")
     ap.add_argument("--serve-sweep", default="", help="comma-separated load multipliers for extra served runs")
+    ap.add_argument("--serve-slots", type=int, default=8, help="slots per shard of the served loop")
+    ap.add_argument("--serve-depth", type=int, default=2, help="steps in flight per shard of the served loop")
     ap.add_argument("--no-scalable", action="store_true", help="skip the per-scale decode pass")
     ap.add_argument("--motion-range", type=int, default=8, help="search range of the motion pass (0: skip)")
     ap.add_argument("--no-rd", action="store_true", help="skip the QCIF rate-distortion sweeps")
@@ -882,6 +899,9 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
+    # the served loop runs one CUDA stream per shard: give the device as many hardware
+    # queues as it allows, so that shards do not share queues (read at context creation)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -1202,9 +1222,11 @@ def main():
     served = None
     if args.serve_seconds > 0:
         torch.cuda.synchronize()
-        served = served_run(d_frames, dev, seconds=args.serve_seconds, seed=rank)
+        served = served_run(d_frames, dev, seconds=args.serve_seconds, seed=rank, slots=args.serve_slots,
+                            depth=args.serve_depth)
         if args.serve_sweep:
-            served["sweep"] = [served_run(d_frames, dev, seconds=args.serve_seconds, load=float(m), seed=rank)
+            served["sweep"] = [served_run(d_frames, dev, seconds=args.serve_seconds, load=float(m), seed=rank,
+                                          slots=args.serve_slots, depth=args.serve_depth)
                                for m in args.serve_sweep.split(",")]
 
     if rank != 0:

@@ -490,7 +490,8 @@ cvc_status cvc_batch_timing(const cvc_batch* batch, double* ms, long long* launc
  *     slots_per_shard slots; one step of a shard codes the next queued
  *     request of each of its sessions (one CUDA-graph launch).  Every shard
  *     runs on its own CUDA stream, so shards overlap on the device; requests
- *     that arrive while a shard's step runs go into its next step.
+ *     that arrive while a shard's steps run go into its next step, which is
+ *     queued at once when steps_in_flight allows it.
  *   - Coder state stays resident in the shard; a session's requests run in
  *     submission order.  Each result is bit-identical to a cvc_codec of the
  *     same parameters fed the same requests, whatever else is in flight.
@@ -503,6 +504,12 @@ typedef struct cvc_server cvc_server;
 typedef struct {
     size_t budget_bytes;   /* device bytes the server may hold (shards' state and workspace) */
     int slots_per_shard;   /* 1..256 */
+    int steps_in_flight;   /* steps a shard may have queued on the device at once, 1..8 (0: 1).
+                              With 2 or more, requests that arrive while a step runs are queued
+                              behind it at once instead of after its completion is collected;
+                              a step skips the work of the slots that have no request in it.
+                              Shards of frames up to 352x288 run on the highest-priority
+                              stream, up to 640x480 on a middle one, larger on the lowest.  */
 } cvc_server_config;
 
 typedef struct {

@@ -69,7 +69,8 @@ class BatchResult(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("budget_bytes", ctypes.c_size_t), ("slots_per_shard", ctypes.c_int)]
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("slots_per_shard", ctypes.c_int),
+                ("steps_in_flight", ctypes.c_int)]
 
 
 class ServerCompletion(ctypes.Structure):

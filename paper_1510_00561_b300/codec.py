@@ -505,8 +505,8 @@ class Server:
     buffers must stay alive until their completion is returned.
     """
 
-    def __init__(self, budget_bytes, slots_per_shard=8):
-        cfg = _L.ServerConfig(int(budget_bytes), int(slots_per_shard))
+    def __init__(self, budget_bytes, slots_per_shard=8, steps_in_flight=1):
+        cfg = _L.ServerConfig(int(budget_bytes), int(slots_per_shard), int(steps_in_flight))
         p = ctypes.c_void_p()
         _L.check(_L.lib().cvc_server_create(ctypes.byref(cfg), ctypes.byref(p)), "cvc_server_create")
         self._h = p
@@ -544,6 +544,18 @@ class Server:
             io.d_rgb_out, io.pitch_out = rgb_out.data_ptr(), rgb_out.stride(0)
         _L.check(_L.lib().cvc_server_submit(self._h, session, kind, ctypes.byref(io), int(tag)), "cvc_server_submit")
         self._keep[int(tag)] = (rgb, out, stream_in, rgb_out)   # alive until completion
+
+    def submit_io(self, session, kind, io, tag):
+        """submit with a prepared cvc_batch_io (_lib.BatchIo); the caller keeps its buffers alive"""
+        _L.check(_L.lib().cvc_server_submit(self._h, session, kind, ctypes.byref(io), int(tag)), "cvc_server_submit")
+
+    def poll_raw(self, wait_us=0):
+        """poll() as (tag, enc_status, dec_status, t_done_ns) tuples, for callers that keep their own buffers"""
+        n = ctypes.c_int(0)
+        _L.check(_L.lib().cvc_server_poll(self._h, int(wait_us), self._cpl, len(self._cpl), ctypes.byref(n)),
+                 "cvc_server_poll")
+        c = self._cpl
+        return [(c[i].tag, c[i].enc_status, c[i].dec_status, c[i].t_done_ns) for i in range(n.value)]
 
     def poll(self, wait_us=0):
         n = ctypes.c_int(0)

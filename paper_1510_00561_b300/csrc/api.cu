@@ -35,6 +35,7 @@ std::vector<PlaneRef> plan_planes(int h, int w, int levels, const int* dirs, int
         PlaneRef r;
         memset(&r, 0, sizeof(r));
         r.low_coef = -1;
+        r.stream = -1;
         r.taps = taps;
         r.H = h;
         r.W = w;

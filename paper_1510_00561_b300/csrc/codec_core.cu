@@ -159,6 +159,7 @@ cvc_status plan_scales(Core* c) {
                     r.coef = poff[p] + Lp.sb[first].off - nlow;
                     r.low_coef = poff[p] + Lp.sb[0].off;
                     r.taps = P.dfb_taps;
+                    r.stream = s;
                     sub.push_back(r);
                 }
             }
@@ -209,11 +210,12 @@ bool codec_geometry(const cvc_params* prm, ColourGeom* g) {
 }
 
 std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, int taps, long long plane_off,
-                                   const long long poff[3]) {
+                                   const long long poff[3], int stream) {
     std::vector<PlaneRef> planes(3);
     for (int p = 0; p < 3; p++) {
         memset(&planes[p], 0, sizeof(PlaneRef));
         planes[p].low_coef = -1;
+        planes[p].stream = stream;
         planes[p].H = p == 0 ? g.Hp : g.Hcp;
         planes[p].W = p == 0 ? g.Wp : g.Wcp;
         planes[p].L = L;
@@ -371,7 +373,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             }
         }
         D.nrows = (int)c->h_row_off.size() - D.row0;
-        std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, P.dfb_taps, plane_off, poff);
+        std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, P.dfb_taps, plane_off, poff, s);
         planes.insert(planes.end(), sp.begin(), sp.end());
         plane_off += D.nplane;
         coef_off += D.ncoef;
@@ -551,6 +553,9 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         B.p[B_IN] = c->d_planes;
         B.p[B_COEF] = c->d_coef;
         B.p[B_WORK] = c->d_work;
+        // the transform skips the planes of streams that do not encode in this call
+        B.act = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_sc) + offsetof(SCall, enc_on));
+        B.act_stride = (int)sizeof(SCall);
         // S1-S3: colour, 4:2:0, padding
         clk.begin(0);
         k_colour_fwd_b<<<(int)c->h_blk_colour.size(), 256, 0, st>>>(c->d_sd, c->d_sc, c->d_blk_colour, c->d_planes,
@@ -632,6 +637,9 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         B.p[B_COEF] = c->d_dcoef;
         B.p[B_WORK] = c->d_work;
         B.p[B_OUT] = c->d_rplanes;
+        // ... and of those that do not decode
+        B.act = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_sc) + offsetof(SCall, dec_on));
+        B.act_stride = (int)sizeof(SCall);
         clk.begin(7);
         CK(engine_run_part(ie, INV, 1, B, st));
         clk.end(7, engine_part_launches(ie, INV, 1));
@@ -779,10 +787,17 @@ bool core_fill_call(Core* c, int s, int mode, const StreamIo& io, int scale) {
     return true;
 }
 
+int core_ring_slot(const Core* c) { return c->ring_slot; }
+
 void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
                  int* dec_type, unsigned* dec_index) {
     (void)mode;
-    const cvc_batch_result& R = c->h_rs[s].res;
+    core_commit_at(c, c->ring_slot, s, enc, dec, out_len, type, dec_type, dec_index);
+}
+
+void core_commit_at(Core* c, int ring_slot, int s, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
+                    int* dec_type, unsigned* dec_index) {
+    const cvc_batch_result& R = c->ring_rs[ring_slot][s].res;
     if (enc) *enc = R.enc_status;
     if (dec) *dec = R.dec_status;
     if (out_len) *out_len = R.out_len;

@@ -126,7 +126,7 @@ bool dirs_valid(int levels, const int* dirs);
 bool codec_params_valid(const cvc_params* prm);
 bool codec_geometry(const cvc_params* prm, ColourGeom* g);
 std::vector<PlaneRef> codec_planes(const ColourGeom& g, int L, const int* dirs, int taps, long long plane_off,
-                                   const long long poff[3]);
+                                   const long long poff[3], int stream);
 
 // host tables and sizes, no device call; CVC_OK, INVALID_ARG or UNSUPPORTED
 cvc_status core_plan(Core* c, const cvc_params* params, int n);
@@ -170,6 +170,12 @@ void core_scaled_size(const Core* c, int s, int scale, int* h, int* w);
 // advanced the coder state of the streams whose call succeeded)
 void core_commit(Core* c, int s, int mode, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
                  int* dec_type, unsigned* dec_index);
+// the record-ring slot of the call being filled / last enqueued, and the
+// statuses of stream s of the call that used slot `ring_slot` (for callers
+// with several steps in flight)
+int core_ring_slot(const Core* c);
+void core_commit_at(Core* c, int ring_slot, int s, cvc_status* enc, cvc_status* dec, size_t* out_len, int* type,
+                    int* dec_type, unsigned* dec_index);
 // read and clear the first error of an asynchronous call of stream s (ordered on st; synchronises st)
 cvc_status core_take_error(Core* c, int s, cudaStream_t st, cvc_status* err);
 

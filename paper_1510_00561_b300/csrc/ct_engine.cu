@@ -112,8 +112,9 @@ View mk(int b, long long off, int rs, int cs) {
 
 // DFB jobs of one (plane, level): detail D_j at doff, partner Q_j at qoff,
 // subband slots (coefficient offsets) in tree order.
-void dfb_jobs(int H, int W, int k, int ntaps, long long doff, long long qoff, const std::vector<long long>& slot,
-              std::vector<DfbAJob>& ajobs, std::vector<std::vector<DfbBJob>>& bjobs) {
+void dfb_jobs(int H, int W, int k, int ntaps, int stream, long long doff, long long qoff,
+              const std::vector<long long>& slot, std::vector<DfbAJob>& ajobs,
+              std::vector<std::vector<DfbBJob>>& bjobs) {
     if (k == 0) return;
     const int h2 = H / 2, w2 = W / 2;
     const long long hw = (long long)H * W;
@@ -125,6 +126,7 @@ void dfb_jobs(int H, int W, int k, int ntaps, long long doff, long long qoff, co
     A.nst = k == 1 ? 1 : 2;
     A.tiles_x = (W + DFBA_TILE - 1) / DFBA_TILE;
     A.ntaps = ntaps;
+    A.stream = stream;
     // polyphase classes q = 2*pr + pc: 00, 01, 10, 11
     if (k == 1) {
         // stage-1 cosets are the subbands: {00, 11} row-compacted into slot 0, {01, 10} into slot 1
@@ -182,6 +184,7 @@ void dfb_jobs(int H, int W, int k, int ntaps, long long doff, long long qoff, co
             J.i = i;
             J.tiles_x = (C + dfbb_cols(ntaps) - 1) / dfbb_cols(ntaps);
             J.ntaps = ntaps;
+            J.stream = stream;
             bjobs[s].push_back(J);
             next.push_back({fam, 2 * i});
             next.push_back({fam, 2 * i + 1});
@@ -280,6 +283,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 J.H = hj;
                 J.W = wj;
                 J.tiles_x = (wj + LP_TILE - 1) / LP_TILE;
+                J.stream = P.stream;
                 J.cin_lo = mk(-1, 0, 0, 0);
                 J.out_lo = mk(-1, 0, 0, 0);
                 if (analysis) {
@@ -298,7 +302,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 }
                 lpj[j].push_back(J);
                 const int nt = (P.taps == 6 || P.taps == 8) ? P.taps : 4;
-                dfb_jobs(hj, wj, kj, nt, doff[j], qoff[j], slots, aj[nt / 2 - 2], bj[nt / 2 - 2]);
+                dfb_jobs(hj, wj, kj, nt, P.stream, doff[j], qoff[j], slots, aj[nt / 2 - 2], bj[nt / 2 - 2]);
             }
         }
         e->lp[m].clear();

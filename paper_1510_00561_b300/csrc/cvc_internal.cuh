@@ -21,10 +21,21 @@ enum : uint32_t {
 
 // Base pointers of one transform invocation; job tables address memory as
 // (base id, element offset) so that the tables stay valid across calls.
+// `act` (may be NULL) marks the streams that take part in the call: stream
+// s takes part iff the int at byte offset s * act_stride is non-zero; the
+// tile kernels skip the jobs of the other streams (a job's stream < 0: always).
 enum { B_IN = 0, B_COEF = 1, B_WORK = 2, B_OUT = 3, N_BASES = 4 };
 struct Bases {
     float* p[N_BASES];
+    const int* act;
+    int act_stride;
 };
+
+// the job's stream does not take part in this call: the whole block returns
+__device__ __forceinline__ bool job_idle(const Bases& B, int stream) {
+    return B.act != nullptr && stream >= 0 &&
+           *reinterpret_cast<const int*>(reinterpret_cast<const char*>(B.act) + (size_t)stream * B.act_stride) == 0;
+}
 
 // Base pointer b, chosen by selects: a run-time index into a by-value kernel
 // parameter makes the compiler copy the whole parameter to the stack and
@@ -66,6 +77,7 @@ struct DfbAJob {
     int nst;
     int tiles_x, first_block;
     int ntaps;     // prototype length (4, 6 or 8)
+    int stream;    // the plane's stream (Bases::act), -1: none
 };
 
 // One stage s >= 3 of one channel: its array splits into even / odd rows,
@@ -79,6 +91,7 @@ struct DfbBJob {
     int i;
     int tiles_x, first_block;
     int ntaps;     // prototype length (4, 6 or 8)
+    int stream;    // the plane's stream (Bases::act), -1: none
 };
 
 constexpr int DFBA_TILE = 64, DFBA_HALO = 12;   // the halo of the 4-tap prototype (4 (NT - 1) in general)
@@ -96,6 +109,8 @@ struct LpJob {
     int H, W;                   // full-resolution size of this level
     int tiles_x;
     int first_block;
+    int stream;                 // the plane's stream (Bases::act), -1: none
+    int pad;
 };
 
 constexpr int LP_TILE = 64;  // full-resolution output tile edge
@@ -123,6 +138,7 @@ struct PlaneRef {
     long long low_coef;   // >= 0: the lowpass lives here instead of at coef (a sub-pyramid of a
                           // larger layout keeps its lowpass apart from its subbands)
     int taps;             // DFB prototype length: 0 or 4, 6 or 8
+    int stream;           // the codec stream the plane belongs to (Bases::act), -1: none
 };
 
 struct LaunchLp {

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     float* planes = smem_a;
     float* tmp = smem_a + 4 * PA * PAS;
     const DfbAJob& J = jobs[block_job[blockIdx.x]];
+    if (job_idle(B, J.stream)) return;
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * DFBA_TILE, x0 = tx * DFBA_TILE;
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs,
     __shared__ __align__(16) float sO[G::SMB];
     __shared__ __align__(16) float sH[G::SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
+    if (job_idle(B, J.stream)) return;
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
 
     const int jid = block_job[blockIdx.x];
     const LpJob& J = jobs[jid];
+    if (job_idle(B, J.stream)) return;
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * T, x0 = tx * T;
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(256) k_lp_ff(const LpJob* __restrict__ jobs, c
 
     const int jid = block_job[blockIdx.x];
     const LpJob& J = jobs[jid];
+    if (job_idle(B, J.stream)) return;
     const int tile = blockIdx.x - J.first_block;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * T, x0 = tx * T;

@@ -1,7 +1,12 @@
 // server.cu -- the continuous-batching request loop (cvc_server_*): sessions
 // admitted against a device-memory budget, grouped by parameters into
 // shards of slots, each shard a multi-stream core replaying its step graph on
-// its own CUDA stream.  Host code only; every step runs in the codec kernels.
+// its own CUDA stream.  A shard keeps up to `depth` steps in flight: requests
+// that arrive while a step runs are queued behind it at once (the coder state
+// lives on the device, so the next step needs nothing from the host), and
+// shards of smaller frames run on higher-priority streams so that their short
+// steps do not wait behind large frames.  Host code only; every step runs in
+// the codec kernels.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -37,27 +42,40 @@ struct Session {
     bool closing = false;
     int shard = -1, slot = -1;
     std::deque<Request> q;
-    bool inflight = false;
+    int inflight = 0;   // requests in steps on the device (in consecutive steps, completing in order)
+};
+
+constexpr int kMaxDepth = 8;   // steps in flight per shard, at most
+
+// one enqueued step of a shard: its requests by slot (kind 0: none), the
+// record-ring slot its results come back in, and its completion event
+struct Step {
+    cudaEvent_t ev = nullptr;
+    int ring = 0;
+    int mode = 0;
+    int64_t t_launch = 0;
+    std::vector<Request> req;
 };
 
 struct Shard {
     Core core;
     cvc_params prm;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    bool busy = false;
-    int mode = 0;
-    int64_t t_launch = 0;
-    std::vector<int> slot_session;   // -1: free
-    std::vector<Request> inflight;   // kind 0: none
+    std::deque<Step> flying;          // in launch order, at most the server's depth
+    std::vector<cudaEvent_t> events;  // one per step in flight, handed to steps in turn
+    int next_event = 0;
+    std::vector<int> slot_session;    // -1: free
+    std::vector<int> slot_flying;     // requests of the slot in flight
     size_t bytes = 0;
+    bool busy() const { return !flying.empty(); }
     int live() const {
         int n = 0;
         for (int s : slot_session) n += s >= 0;
         return n;
     }
     ~Shard() {
-        if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t e : events)
+            if (e) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
     }
 };
@@ -85,6 +103,7 @@ StreamIo stream_io(const Request& r) {
 
 struct cvc_server {
     cvc_server_config cfg{};
+    int depth = 1;   // steps in flight per shard
     std::vector<Session> sessions;
     std::vector<std::unique_ptr<Shard>> shards;   // null: freed
     std::deque<int> waiting;
@@ -110,8 +129,8 @@ struct cvc_server {
         return CVC_OK;
     }
 
-    void complete(Shard* sh, int slot, cvc_status fail) {
-        Request& r = sh->inflight[slot];
+    void complete(Shard* sh, Step& step, int slot, cvc_status fail) {
+        Request& r = step.req[slot];
         cvc_server_completion cpl;
         memset(&cpl, 0, sizeof(cpl));
         cpl.tag = r.tag;
@@ -120,39 +139,42 @@ struct cvc_server {
         cpl.frame_type = cpl.dec_frame_type = -1;
         if (fail == CVC_OK) {
             unsigned didx = 0;
-            core_commit(&sh->core, slot, sh->mode, &cpl.enc_status, &cpl.dec_status, &cpl.out_len, &cpl.frame_type,
-                        &cpl.dec_frame_type, &didx);
+            core_commit_at(&sh->core, step.ring, slot, &cpl.enc_status, &cpl.dec_status, &cpl.out_len,
+                           &cpl.frame_type, &cpl.dec_frame_type, &didx);
         } else {
             cpl.enc_status = (r.kind & 1) ? fail : CVC_OK;
             cpl.dec_status = (r.kind & 2) ? fail : CVC_OK;
         }
         cpl.t_submit_ns = r.t_submit;
-        cpl.t_launch_ns = sh->t_launch;
+        cpl.t_launch_ns = step.t_launch;
         cpl.t_done_ns = now_ns();
         done.push_back(cpl);
         requests_done++;
         r.kind = 0;
-        sessions[cpl.session].inflight = false;
+        sh->slot_flying[slot]--;
+        sessions[cpl.session].inflight--;
     }
 
-    // collect finished steps; returns the number of shards that finished
+    // collect finished steps, oldest first per shard; returns the number of steps that finished
     int reap() {
         int n = 0;
         for (auto& up : shards) {
             Shard* sh = up.get();
-            if (!sh || !sh->busy) continue;
-            cudaError_t q = cudaEventQuery(sh->ev);
-            if (q == cudaErrorNotReady) continue;
-            cvc_status fail = CVC_OK;
-            if (q != cudaSuccess) {
-                cudaGetLastError();
-                fail = CVC_ERR_CUDA;
-                sticky = CVC_ERR_CUDA;
+            while (sh && sh->busy()) {
+                Step& step = sh->flying.front();
+                cudaError_t q = cudaEventQuery(step.ev);
+                if (q == cudaErrorNotReady) break;
+                cvc_status fail = CVC_OK;
+                if (q != cudaSuccess) {
+                    cudaGetLastError();
+                    fail = CVC_ERR_CUDA;
+                    sticky = CVC_ERR_CUDA;
+                }
+                for (int s = 0; s < (int)step.req.size(); s++)
+                    if (step.req[s].kind) complete(sh, step, s, fail);
+                sh->flying.pop_front();
+                n++;
             }
-            for (int s = 0; s < (int)sh->inflight.size(); s++)
-                if (sh->inflight[s].kind) complete(sh, s, fail);
-            sh->busy = false;
-            n++;
         }
         return n;
     }
@@ -160,7 +182,7 @@ struct cvc_server {
     void retire() {
         for (int id = 0; id < (int)sessions.size(); id++) {
             Session& S = sessions[id];
-            if (S.state == S_DONE || !S.closing || !S.q.empty() || S.inflight) continue;
+            if (S.state == S_DONE || !S.closing || !S.q.empty() || S.inflight > 0) continue;
             if (S.state == S_WAITING) {
                 waiting.erase(std::remove(waiting.begin(), waiting.end(), id), waiting.end());
             } else {
@@ -169,7 +191,7 @@ struct cvc_server {
             S.state = S_DONE;
         }
         for (auto& up : shards) {
-            if (!up || up->busy || up->live() > 0) continue;
+            if (!up || up->busy() || up->live() > 0) continue;
             used -= up->bytes;
             up.reset();
         }
@@ -183,15 +205,30 @@ struct cvc_server {
             return false;
         for (int m = STEP_ENC; m <= STEP_ENCDEC; m++)
             if (core_capture(&sh->core, m) != CVC_OK) return false;
-        if (cudaStreamCreateWithFlags(&sh->st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sh->ev, cudaEventDisableTiming) != cudaSuccess) {
+        // smaller frames, shorter steps: a higher stream priority (numerically lower), so that
+        // they do not wait behind the kernels of large frames
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            least = greatest = 0;
+        }
+        const long long px = (long long)p.width * p.height;
+        const int prio = px <= 110000 ? greatest : (px <= 400000 ? (least + greatest) / 2 : least);
+        if (cudaStreamCreateWithPriority(&sh->st, cudaStreamNonBlocking, prio) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
+        sh->events.assign(depth, nullptr);
+        for (cudaEvent_t& e : sh->events)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                e = nullptr;
+                cudaGetLastError();
+                return false;
+            }
         sh->prm = p;
         sh->bytes = bytes;
         sh->slot_session.assign(cfg.slots_per_shard, -1);
-        sh->inflight.assign(cfg.slots_per_shard, Request{0, {}, 0, 0});
+        sh->slot_flying.assign(cfg.slots_per_shard, 0);
         for (size_t i = 0; i < shards.size(); i++)
             if (!shards[i]) {
                 shards[i] = std::move(sh);
@@ -212,7 +249,7 @@ struct cvc_server {
                 Shard* sh = shards[i].get();
                 if (!sh || !same_params(sh->prm, S.prm)) continue;
                 for (int s = 0; s < (int)sh->slot_session.size(); s++)
-                    if (sh->slot_session[s] < 0 && !sh->inflight[s].kind) {
+                    if (sh->slot_session[s] < 0 && !sh->slot_flying[s]) {
                         where = (int)i;
                         slot = s;
                         break;
@@ -244,42 +281,50 @@ struct cvc_server {
     void launch() {
         for (auto& up : shards) {
             Shard* sh = up.get();
-            if (!sh || sh->busy) continue;
+            if (!sh || (int)sh->flying.size() >= depth) continue;
+            Step step;
+            step.req.assign(sh->slot_session.size(), Request{0, {}, 0, 0});
             int mode = 0;
             for (int s = 0; s < (int)sh->slot_session.size(); s++) {
                 const int id = sh->slot_session[s];
                 if (id < 0) continue;
                 Session& S = sessions[id];
-                if (S.q.empty() || S.inflight) continue;
-                sh->inflight[s] = S.q.front();
+                // one request per session per step; a session's later requests go into later
+                // steps, which the shard's stream runs in order
+                if (S.q.empty()) continue;
+                step.req[s] = S.q.front();
                 S.q.pop_front();
-                S.inflight = true;
-                mode |= sh->inflight[s].kind;
+                S.inflight++;
+                sh->slot_flying[s]++;
+                mode |= step.req[s].kind;
             }
             if (!mode) continue;
             const StreamIo none{nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0};
             cvc_status st = core_begin(&sh->core) ? CVC_OK : CVC_ERR_CUDA;
             for (int s = 0; s < (int)sh->slot_session.size() && st == CVC_OK; s++)
-                core_fill_call(&sh->core, s, mode, sh->inflight[s].kind ? stream_io(sh->inflight[s]) : none);
-            sh->mode = mode;
-            sh->t_launch = now_ns();
+                core_fill_call(&sh->core, s, mode, step.req[s].kind ? stream_io(step.req[s]) : none);
+            step.mode = mode;
+            step.t_launch = now_ns();
+            step.ring = core_ring_slot(&sh->core);
+            step.ev = sh->events[sh->next_event];
             if (st == CVC_OK) st = core_enqueue(&sh->core, mode, sh->st);
-            if (st == CVC_OK && cudaEventRecord(sh->ev, sh->st) != cudaSuccess) st = CVC_ERR_CUDA;
+            if (st == CVC_OK && cudaEventRecord(step.ev, sh->st) != cudaSuccess) st = CVC_ERR_CUDA;
             if (st != CVC_OK) {
                 cudaGetLastError();
                 sticky = st;
-                for (int s = 0; s < (int)sh->inflight.size(); s++)
-                    if (sh->inflight[s].kind) complete(sh, s, st);
+                for (int s = 0; s < (int)step.req.size(); s++)
+                    if (step.req[s].kind) complete(sh, step, s, st);
                 continue;
             }
-            sh->busy = true;
+            sh->next_event = (sh->next_event + 1) % depth;
+            sh->flying.push_back(std::move(step));
             steps++;
         }
     }
 
     bool any_busy() const {
         for (auto& up : shards)
-            if (up && up->busy) return true;
+            if (up && up->busy()) return true;
         return false;
     }
 
@@ -298,11 +343,13 @@ int64_t cvc_server_now_ns(void) { return now_ns(); }
 cvc_status cvc_server_create(const cvc_server_config* cfg, cvc_server** out) {
     if (!out) return CVC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!cfg || cfg->slots_per_shard < 1 || cfg->slots_per_shard > 256 || cfg->budget_bytes == 0)
+    if (!cfg || cfg->slots_per_shard < 1 || cfg->slots_per_shard > 256 || cfg->budget_bytes == 0 ||
+        cfg->steps_in_flight < 0 || cfg->steps_in_flight > kMaxDepth)
         return CVC_ERR_INVALID_ARG;
     cvc_server* s = new (std::nothrow) cvc_server();
     if (!s) return CVC_ERR_NOMEM;
     s->cfg = *cfg;
+    s->depth = cfg->steps_in_flight > 0 ? cfg->steps_in_flight : 1;
     *out = s;
     return CVC_OK;
 }
@@ -310,7 +357,8 @@ cvc_status cvc_server_create(const cvc_server_config* cfg, cvc_server** out) {
 cvc_status cvc_server_destroy(cvc_server* s) {
     if (!s) return CVC_OK;
     for (auto& up : s->shards)
-        if (up && up->busy) cudaEventSynchronize(up->ev);
+        if (up)
+            for (Step& step : up->flying) cudaEventSynchronize(step.ev);
     delete s;
     return CVC_OK;
 }

@@ -101,6 +101,7 @@ extern "C" cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int
         J.out.cs = 1;
         J.cin_lo.b = -1;
         J.out_lo.b = -1;
+        J.stream = -1;
         coff += (long long)hj * wj;
         prev_woff = woff;
         woff += (long long)(hj / 2) * (wj / 2);

@@ -33,11 +33,13 @@ from paper_1510_00561_b300 import _lib as L
 VIEW = np.dtype([("off", "<i8"), ("b", "<i4"), ("rs", "<i4"), ("cs", "<i4"), ("pad", "<i4")])
 LPJOB = np.dtype([("main", VIEW), ("cin", VIEW), ("cout", VIEW), ("out", VIEW), ("cin_lo", VIEW), ("out_lo", VIEW),
                   ("H", "<i4"), ("W", "<i4"),
-                  ("tiles_x", "<i4"), ("first_block", "<i4")])
+                  ("tiles_x", "<i4"), ("first_block", "<i4"), ("stream", "<i4"), ("pad2", "<i4")])
 AJOB = np.dtype([("D", VIEW), ("comp", VIEW, (4,)), ("H", "<i4"), ("W", "<i4"), ("nst", "<i4"),
-                 ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4")])
+                 ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4"), ("stream", "<i4"),
+                 ("pad2", "<i4")])
 BJOB = np.dtype([("pe", VIEW), ("po", VIEW), ("c0", VIEW), ("c1", VIEW), ("R2", "<i4"), ("C", "<i4"),
-                 ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4")])
+                 ("i", "<i4"), ("tiles_x", "<i4"), ("first_block", "<i4"), ("ntaps", "<i4"), ("stream", "<i4"),
+                 ("pad2", "<i4")])
 # (first target is the odd coset, alpha1, gamma1, alpha2, gamma2) per mode
 PASSES = {0: (1, 0.5, -0.5, 1.0, 1.0), 3: (0, 1.0, 1.0, 2.0, -1.0),
           1: (0, 1.0, -1.0, 2.0, 1.0), 2: (1, 0.5, 0.5, 1.0, -1.0)}

@@ -62,11 +62,11 @@ def _plain_results(cfg, frames):
     return out
 
 
-def _serve(mix, order_seed, budget=64 << 30, slots=4):
+def _serve(mix, order_seed, budget=64 << 30, slots=4, depth=1):
     """Run sessions `mix` = [(cfg, frames)] through one server, submitting
     their frames interleaved in a seeded random order (each session's frames
     in order) with polls in between; returns per session [(bytes, rgb, type)]."""
-    srv = Server(budget, slots_per_shard=slots)
+    srv = Server(budget, slots_per_shard=slots, steps_in_flight=depth)
     sids = [srv.open(**cfg) for cfg, _ in mix]
     ms = [_max_stream(cfg) for cfg, _ in mix]
     rng = np.random.default_rng(order_seed)
@@ -114,8 +114,9 @@ def test_results_are_the_same_alone_and_in_a_mix():
     _same(alone, _plain_results(*target))
     mix = [target] + [(cfg, _video(cfg, 10 + j, 5)) for j, cfg in
                       enumerate([QCIF, CIF, VGA, ODD, QCIF, CIF, ODD, QCIF, VGA, QCIF, CIF])]
-    for seed in (1, 2):
-        res, st = _serve(mix, seed)
+    for seed, depth in ((1, 1), (2, 1), (3, 2), (4, 3)):
+        # with several steps in flight per shard, partly filled steps skip their idle slots
+        res, st = _serve(mix, seed, depth=depth)
         _same(res[0], alone)
         assert st["shards"] >= 4 and st["peak_used_bytes"] <= st["budget_bytes"]
     for (cfg, fr), r in zip(mix[1:4], res[1:4]):
