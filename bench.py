@@ -405,6 +405,7 @@ def mixed_batch_run(dev, flush, T=30, warm=3, per_class=16, distinct=30):
     def frames_at(t):
         return [seqs[ci][(t + 2 * j) % distinct] for ci in range(len(MIXED_CLASSES)) for j in range(per_class)]
 
+    shape = b.autotune(3, rgb=frames_at(0), rgb_out=outs, reps=3)
     for t in range(warm):
         b.step(3, rgb=frames_at(t), rgb_out=outs)
     b.reset()
@@ -423,6 +424,7 @@ def mixed_batch_run(dev, flush, T=30, warm=3, per_class=16, distinct=30):
     return {"workload": "64 streams (16 each QCIF, CIF, VGA, 720p; 3/3/4/5 levels), encode+decode, one "
                         "graph launch per step, %d steps" % T,
             "frames_per_s": n * T * 1e3 / tot, "ms_per_step": tot / T, "steps": T,
+            "launch_shape": list(shape),
             "mean_stream_bytes": nbytes / (n * T), "l2": "flushed before every step"}
 
 
@@ -1023,7 +1025,7 @@ def main():
     def frames_at(i):
         return [d_frames[(i + 3 * j) % F] for j in range(B)]
 
-    shape = (8, 148 * 8) if args.no_autotune else batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
+    shape = (8, 148 * 8, 6) if args.no_autotune else batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
     info0 = batch.info[0]
     batch_bytes = [0]
 
@@ -1124,7 +1126,8 @@ def main():
         del batch, outs_rgb
         dbatch = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
                              key_interval=KINT)] * B)
-        dbatch.set_shape(*shape)
+        dbatch.set_shape(*shape[:2])
+        dbatch.set_fusion(shape[2])
         sc_steps = max(KINT, min(args.steps, 2 * KINT))
         scales = []
         for sc in range(LEVELS + 1):
@@ -1153,7 +1156,8 @@ def main():
     if args.motion_range > 0:
         mb = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
                          key_interval=KINT, motion_range=args.motion_range)] * B)
-        mb.set_shape(*shape)
+        mb.set_shape(*shape[:2])
+        mb.set_fusion(shape[2])
         m_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
         m_bytes = [0, 0]
 
@@ -1187,7 +1191,8 @@ def main():
         for nt in (6, 8):
             tb = Batch([dict(width=W_, height=H_, levels=LEVELS, dirs_log2=DIRS, qph=QPH, qpl=QPL,
                              key_interval=KINT, dfb_taps=nt)] * B)
-            tb.set_shape(*shape)
+            tb.set_shape(*shape[:2])
+            tb.set_fusion(shape[2])
             t_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
 
             def taps_step(i, tb=tb, t_outs=t_outs):

@@ -109,6 +109,11 @@ cvc_status cvc_ct_plan_create(int h, int w, int levels, const int* dirs_log2, in
 cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log2, int batch, int dfb_taps,
                                    cvc_ct_plan** out);
 cvc_status cvc_ct_plan_destroy(cvc_ct_plan* plan);
+/* Fusion depth of the forward transform and the inverse (see
+ * cvc_batch_set_fusion): the most coarse levels of each plane run in one
+ * block with their images in shared memory; changes no result.  Waits for
+ * the device, rebuilds the plan's tables.  Errors: INVALID_ARG, NOMEM.     */
+cvc_status cvc_ct_plan_set_fusion(cvc_ct_plan* plan, int levels);
 /* total coefficients of one plane of this plan (layout.total) */
 long long cvc_ct_plan_coeffs(const cvc_ct_plan* plan);
 
@@ -463,11 +468,22 @@ cvc_status cvc_batch_get_error(cvc_batch* batch, int i, cvc_stream_t stream, cvc
 
 /* Launch shapes (they change no result): rows per block of the run-length
  * kernels (1..32) and blocks of the decoder's token kernels (1..65535).
- * cvc_batch_autotune times candidate shapes on steps over `io` (the outputs
- * of io are written; no coder state changes), keeps the fastest and returns
- * it in shape[2] (may be NULL).  Graph replay can be switched off (on = 0)
- * to run the same launches one by one.                                      */
+ * Fusion depth (changes no result either): the most coarse pyramid levels of
+ * each plane that run in its pyramid tail, one block per plane with the
+ * levels' images resident in shared memory (§2.1: the LP iterated on the
+ * lowpass, a DFB on every detail); a plane's tail takes as many of them as
+ * fit 227 KB of shared memory (1080p: luma level 5, chroma levels 4-5; QCIF:
+ * luma levels 2-3, the whole chroma planes); 0 runs every level as its own
+ * launches, the default (one block per plane runs the coarse levels' tiles
+ * one after the other, which on a 1080p frame is slower than their own
+ * launches; the autotuner tries tails of 1, 2 and CVC_MAX_LEVELS levels).
+ * cvc_batch_autotune times candidate shapes and fusion depths on steps over
+ * `io` (the outputs of io are written; no coder state changes), keeps the
+ * fastest and returns it in shape[3] = {rle_rows, tok_blocks, fusion depth}
+ * (may be NULL).  Graph replay can be switched off (on = 0) to run the same
+ * launches one by one.                                                      */
 cvc_status cvc_batch_set_shape(cvc_batch* batch, int rle_rows, int tok_blocks);
+cvc_status cvc_batch_set_fusion(cvc_batch* batch, int levels);
 cvc_status cvc_batch_autotune(cvc_batch* batch, int what, const cvc_batch_io* io, int reps, int* shape,
                               cvc_stream_t stream);
 cvc_status cvc_batch_set_graphs(cvc_batch* batch, int on);
@@ -605,7 +621,8 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
 /* ------------------------------------------------------------ diagnostics
  * Host-only dump of the launch plan of a transform (no device call is
  * made, so it works without a GPU): the job tables of every launch of
- * `mode` (0 forward, 1 inverse, 2 adjoint of forward, 3 adjoint of inverse)
+ * `mode` & 255 (0 forward, 1 inverse, 2 adjoint of forward, 3 adjoint of
+ * inverse) at fusion depth `mode` >> 8 (cvc_batch_set_fusion)
  * for a transform plan (params == NULL; h, w, levels, dirs_log2, batch as in
  * cvc_ct_plan_create) or for the planes of the codec streams params[0 ..
  * batch-1] (params != NULL: cvc_create for batch = 1, cvc_batch_create
@@ -617,7 +634,11 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  *   u64 elems[4]   floats of the input, coefficient, workspace and output buffers,
  *   then per launch: u32 kind (0 = LP level, 1 = DFB stages 1-2, 2 = DFB stage
  *   >= 3), u32 njobs, and njobs job records (the library's job structures;
- *   DFB jobs carry their prototype length).
+ *   DFB jobs carry their prototype length); or, for a pyramid-tail launch,
+ *   u32 kind 3, u32 byte count, and the tail's tables: u32 planes, u32
+ *   prototype length, then per plane i32 shared-memory floats, i32 stream,
+ *   u32 steps, u32 0, and per step u32 kind (0, 1 or 2 as above), u32 0
+ *   and the job record; the tail's own images are base 4.
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.
  * Returns CAPACITY with *used = bytes needed when cap is too small.          */

@@ -110,6 +110,7 @@ def lib():
         L.cvc_ct_plan_create.argtypes = [_I, _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_P)]
         L.cvc_ct_plan_create_taps.argtypes = [_I, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_P)]
         L.cvc_ct_plan_destroy.argtypes = [_P]
+        L.cvc_ct_plan_set_fusion.argtypes = [_P, _I]
         L.cvc_ct_plan_coeffs.argtypes = [_P]
         L.cvc_ct_plan_coeffs.restype = ctypes.c_longlong
         for name in ("cvc_ct_forward", "cvc_ct_inverse", "cvc_ct_forward_adjoint", "cvc_ct_inverse_adjoint"):
@@ -154,6 +155,7 @@ def lib():
         L.cvc_batch_step_async.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _P, _I, _P, _P]
         L.cvc_batch_get_error.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
         L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
+        L.cvc_batch_set_fusion.argtypes = [_P, _I]
         L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
         L.cvc_batch_set_graphs.argtypes = [_P, _I]
         L.cvc_batch_set_timing.argtypes = [_P, _I]

@@ -92,6 +92,10 @@ class CtPlan:
     def inverse_adjoint(self, xbar, out=None):
         return self._run("cvc_ct_inverse_adjoint", xbar, (self.batch, self.h, self.w), (self.batch, self.total), out)
 
+    def set_fusion(self, levels):
+        """cvc_ct_plan_set_fusion: the most coarse levels of each plane in one block (0: none)"""
+        _L.check(_L.lib().cvc_ct_plan_set_fusion(self._h, int(levels)), "cvc_ct_plan_set_fusion")
+
     @property
     def subbands(self):
         """Number of directional subbands (one soft threshold each)."""
@@ -487,12 +491,17 @@ class Batch:
         return {name: (ms[i], n[i]) for i, name in enumerate(_L.STAGE_NAMES)}
 
     def autotune(self, what, rgb=None, streams_in=None, rgb_out=None, reps=5, stream=None):
-        """Time candidate launch shapes on these inputs, keep the fastest; returns (rle_rows, tok_blocks)."""
+        """Time candidate launch shapes and fusion depths on these inputs, keep the fastest;
+        returns (rle_rows, tok_blocks, fusion depth)."""
         self._fill(rgb, streams_in, rgb_out, None)
-        shape = (ctypes.c_int * 2)()
+        shape = (ctypes.c_int * 3)()
         _L.check(_L.lib().cvc_batch_autotune(self._h, what, self._io, reps, shape, _stream(stream)),
                  "cvc_batch_autotune")
-        return shape[0], shape[1]
+        return shape[0], shape[1], shape[2]
+
+    def set_fusion(self, levels):
+        """cvc_batch_set_fusion: the most coarse levels of each plane in its pyramid tail (0: none)"""
+        _L.check(_L.lib().cvc_batch_set_fusion(self._h, int(levels)), "cvc_batch_set_fusion")
 
 
 class Server:

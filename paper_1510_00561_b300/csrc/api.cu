@@ -189,7 +189,7 @@ cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log
         !dalloc(p->allocs, &p->d_soft_partial, sj.size()) ||
         cudaMemcpy(p->d_soft, sj.data(), sj.size() * sizeof(SoftJob), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_soft_first, sf.data(), sf.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess) {
+        lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess || tail_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return CVC_ERR_NOMEM;
@@ -200,6 +200,21 @@ cvc_status cvc_ct_plan_create_taps(int h, int w, int levels, const int* dirs_log
 
 cvc_status cvc_ct_plan_destroy(cvc_ct_plan* plan) {
     delete plan;
+    return CVC_OK;
+}
+
+cvc_status cvc_ct_plan_set_fusion(cvc_ct_plan* p, int levels) {
+    if (!p || levels < 0 || levels > CVC_MAX_LEVELS) return CVC_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    p->eng.tail_levels = levels;
+    const std::vector<PlaneRef> planes = p->eng.planes;
+    if (!engine_build(&p->eng, planes, true)) {
+        cudaGetLastError();
+        return CVC_ERR_NOMEM;
+    }
     return CVC_OK;
 }
 
@@ -879,6 +894,19 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
         s = measure(sh, &ms);
         if (s == CVC_OK && ms < best_ms) best = sh, best_ms = ms;
     }
+    // then the fusion depth: every level as its own launches, or tails of 1, 2 or as many
+    // levels as fit
+    const int fuse_cand[] = {0, 1, 2, CVC_MAX_LEVELS};
+    int best_fuse = c->eng.tail_levels;
+    for (int f : fuse_cand) {
+        if (s != CVC_OK) break;
+        if (f == best_fuse) continue;
+        s = core_set_fusion(c, f);
+        float ms = 0.f;
+        if (s == CVC_OK) s = measure(best, &ms);
+        if (s == CVC_OK && ms < best_ms) best_fuse = f, best_ms = ms;
+    }
+    if (s == CVC_OK && c->eng.tail_levels != best_fuse) s = core_set_fusion(c, best_fuse);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->shape = best;
@@ -886,8 +914,14 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
     if (shape) {
         shape[0] = best.rle_rows;
         shape[1] = best.tok_blocks;
+        shape[2] = best_fuse;
     }
     return s;
+}
+
+cvc_status cvc_batch_set_fusion(cvc_batch* b, int levels) {
+    if (!b) return CVC_ERR_INVALID_ARG;
+    return core_set_fusion(&b->core, levels);
 }
 
 // the launches of one direction of an engine (and optional trailing
@@ -909,8 +943,36 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
             items.push_back({1 + L.kind, e.h_dfb[mode][i].data(), (size_t)L.njobs, sz});
         }
     };
-    if (analysis) { push_lp(); push_dfb(); }
-    else { push_dfb(); push_lp(); }
+    // pyramid-tail launches (kind 3): u32 nplanes, u32 ntaps; per plane i32 resident floats, i32 stream,
+    // u32 nsteps, u32 0, then per step u32 kind (0 LP, 1 DFB stages 1-2, 2 DFB stage >= 3), u32 0 and
+    // the job record; item size = blob bytes
+    std::vector<std::vector<uint8_t>> blobs;
+    for (const TailTables& T : e.h_tail[mode]) {
+        std::vector<uint8_t> b;
+        auto put = [&](const void* p, size_t n) {
+            b.insert(b.end(), (const uint8_t*)p, (const uint8_t*)p + n);
+        };
+        uint32_t h2[2] = {(uint32_t)T.planes.size(), (uint32_t)T.ntaps};
+        put(h2, 8);
+        for (const TailPlane& P : T.planes) {
+            int32_t ph[4] = {P.ws_floats, P.stream, P.nsteps, 0};
+            put(ph, 16);
+            for (int k = 0; k < P.nsteps; k++) {
+                const TailStep& st = T.steps[(size_t)P.first_step + k];
+                uint32_t sh[2] = {(uint32_t)st.kind, 0};
+                put(sh, 8);
+                if (st.kind == 0) put(&T.lp[st.job], sizeof(LpJob));
+                else if (st.kind == 1) put(&T.a[st.job], sizeof(DfbAJob));
+                else put(&T.b[st.job], sizeof(DfbBJob));
+            }
+        }
+        blobs.push_back(std::move(b));
+    }
+    auto push_tail = [&]() {
+        for (auto& b : blobs) items.push_back({3, b.data(), b.size(), 1});
+    };
+    if (analysis) { push_lp(); push_tail(); push_dfb(); }
+    else { push_dfb(); push_tail(); push_lp(); }
     size_t need = 24 + 32 + tail_n * tail_sz;
     for (const Item& it : items) need += 8 + it.n * it.sz;
     *used = need;
@@ -934,14 +996,22 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
 
 cvc_status cvc_debug_plan_tables(const cvc_params* params, int h, int w, int levels, const int* dirs_log2, int batch,
                                  int mode, void* buf, size_t cap, size_t* used) {
-    if (!used || mode < 0 || mode > 3) return CVC_ERR_INVALID_ARG;
+    const int fuse = mode >> 8;
+    mode &= 255;
+    if (!used || mode < 0 || mode > 3 || fuse > CVC_MAX_LEVELS) return CVC_ERR_INVALID_ARG;
     unsigned long long elems[4] = {0, 0, 0, 0};
     Core core;   // host tables only: core_plan makes no device call
     CtEngine plain;
+    plain.tail_levels = fuse;
     const CtEngine* ep = nullptr;
     if (params) {
         cvc_status s = core_plan(&core, params, std::max(batch, 1));
         if (s != CVC_OK) return s;
+        if (fuse) {
+            core.eng.tail_levels = fuse;
+            const std::vector<PlaneRef> planes = core.eng.planes;
+            if (!engine_build(&core.eng, planes, false)) return CVC_ERR_UNSUPPORTED;
+        }
         elems[0] = elems[3] = (unsigned long long)core.nplane;
         elems[1] = (unsigned long long)core.ncoef;
         ep = &core.eng;

@@ -88,6 +88,9 @@ size_t engine_table_bytes_of(const CtEngine& e) {
         for (const LaunchLp& L : e.lp[m]) b += L.njobs * sizeof(LpJob) + (size_t)L.nblocks * sizeof(int) + 1024;
         for (const LaunchDfb& L : e.dfb[m])
             b += L.njobs * (L.kind == 0 ? sizeof(DfbAJob) : sizeof(DfbBJob)) + (size_t)L.nblocks * sizeof(int) + 1024;
+        for (const TailTables& T : e.h_tail[m])
+            b += T.planes.size() * sizeof(TailPlane) + T.steps.size() * sizeof(TailStep) +
+                 T.lp.size() * sizeof(LpJob) + T.a.size() * sizeof(DfbAJob) + T.b.size() * sizeof(DfbBJob) + 5 * 1024;
     }
     return b;
 }
@@ -239,6 +242,11 @@ ScalePlan::~ScalePlan() {
 Core::~Core() {
     scale.clear();   // graphs first
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side) cudaStreamDestroy(side);
+    for (int k = 0; k < 2; k++) {
+        if (ev_fork[k]) cudaEventDestroy(ev_fork[k]);
+        if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+    }
     if (arena) cudaFree(arena);
     for (int k = 0; k < CORE_RING; k++) {
         if (ring_sc[k]) cudaFreeHost(ring_sc[k]);
@@ -416,7 +424,8 @@ cvc_status core_alloc(Core* c) {
             return CVC_ERR_NOMEM;
         }
     }
-    if (lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess) return CVC_ERR_CUDA;
+    if (lp_prepare() != cudaSuccess || dfb_prepare() != cudaSuccess || tail_prepare() != cudaSuccess)
+        return CVC_ERR_CUDA;
     Carve k;
     carve_all(c, k);
     c->arena_bytes = k.total;
@@ -465,6 +474,10 @@ cvc_status core_alloc(Core* c) {
     }
     ok = ok && put(c->d_ctl, ctl);
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; k++)
+        ok = cudaEventCreateWithFlags(&c->ev_fork[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return CVC_ERR_CUDA;
@@ -498,6 +511,28 @@ void core_drop_graphs(Core* c) {
             sp->gexec[m] = nullptr;
             sp->gkernels[m] = 0;
         }
+}
+
+cvc_status core_set_fusion(Core* c, int levels) {
+    if (levels < 0 || levels > CVC_MAX_LEVELS) return CVC_ERR_INVALID_ARG;
+    // the old tables go: nothing may still be running on them
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    core_drop_graphs(c);
+    auto rebuild = [&](CtEngine& e) {
+        e.tail_levels = levels;
+        const std::vector<PlaneRef> planes = e.planes;
+        return engine_build(&e, planes, true);
+    };
+    bool ok = rebuild(c->eng);
+    for (size_t sc = 1; sc < c->scale.size() && ok; sc++) ok = rebuild(c->scale[sc]->eng);
+    if (!ok) {
+        cudaGetLastError();
+        return CVC_ERR_NOMEM;
+    }
+    return CVC_OK;
 }
 
 void core_scaled_size(const Core* c, int s, int scale, int* h, int* w) {
@@ -566,10 +601,19 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         clk.begin(1);
         CK(engine_run_part(&c->eng, FWD, 0, B, st));
         clk.end(1, engine_part_launches(&c->eng, FWD, 0));
+        // the pyramid tails (coarse levels) on the side stream, beside the DFB stages of the others
+        const int ntail = engine_part_launches(&c->eng, FWD, 2);
+        if (ntail) {
+            CK(cudaEventRecord(c->ev_fork[0], st));
+            CK(cudaStreamWaitEvent(c->side, c->ev_fork[0], 0));
+            CK(engine_run_part(&c->eng, FWD, 2, B, c->side));
+            CK(cudaEventRecord(c->ev_join[0], c->side));
+        }
         clk.begin(2);
         CK(engine_run_part(&c->eng, FWD, 1, B, st));
-        clk.end(2, engine_part_launches(&c->eng, FWD, 1));
-        k += 1 + engine_part_launches(&c->eng, FWD, 0) + engine_part_launches(&c->eng, FWD, 1);
+        if (ntail) CK(cudaStreamWaitEvent(st, c->ev_join[0], 0));
+        clk.end(2, engine_part_launches(&c->eng, FWD, 1) + ntail);
+        k += 1 + engine_part_launches(&c->eng, FWD, 0) + engine_part_launches(&c->eng, FWD, 1) + ntail;
         // S6-S8: normalise, threshold, quantise, K/P differencing
         clk.begin(3);
         k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_THREADS, 0, st>>>(
@@ -641,8 +685,16 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         B.act = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_sc) + offsetof(SCall, dec_on));
         B.act_stride = (int)sizeof(SCall);
         clk.begin(7);
+        const int ntail = engine_part_launches(ie, INV, 2);
+        if (ntail) {
+            CK(cudaEventRecord(c->ev_fork[1], st));
+            CK(cudaStreamWaitEvent(c->side, c->ev_fork[1], 0));
+            CK(engine_run_part(ie, INV, 2, B, c->side));
+            CK(cudaEventRecord(c->ev_join[1], c->side));
+        }
         CK(engine_run_part(ie, INV, 1, B, st));
-        clk.end(7, engine_part_launches(ie, INV, 1));
+        if (ntail) CK(cudaStreamWaitEvent(st, c->ev_join[1], 0));
+        clk.end(7, engine_part_launches(ie, INV, 1) + ntail);
         clk.begin(8);
         CK(engine_run_part(ie, INV, 0, B, st));
         clk.end(8, engine_part_launches(ie, INV, 0));
@@ -656,7 +708,7 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
             ncol = 1;
         }
         clk.end(9, ncol);
-        k += 8 + 2 + ncol + engine_part_launches(ie, INV, 1) + engine_part_launches(ie, INV, 0);
+        k += 8 + 2 + ncol + engine_part_launches(ie, INV, 1) + engine_part_launches(ie, INV, 0) + ntail;
     }
     // statuses, lengths and frame types; the coder state advances where the call succeeded
     k_step_commit<<<(int)cdiv(n, 128), 128, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_ctl, n);

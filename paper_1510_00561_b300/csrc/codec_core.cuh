@@ -113,6 +113,10 @@ struct Core {
     // CUDA graphs of the step modes: one set per decoding scale (in ScalePlan)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
+    // the pyramid tails run on a side stream, beside the DFB launches of the other levels
+    // (fork / join events: [0] analysis, [1] synthesis)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
     // stage timing (direct launches only)
     bool timing = false;
     cudaEvent_t ev[CVC_NUM_STAGES][2] = {};
@@ -150,6 +154,9 @@ void core_collect(Core* c);
 cvc_status core_set_timing(Core* c, bool on);
 // drop the captured graphs (after a change of launch shape)
 void core_drop_graphs(Core* c);
+// the most coarse levels of each plane in its pyramid tail (0..CVC_MAX_LEVELS); rebuilds
+// the transform tables of every scale and drops the graphs
+cvc_status core_set_fusion(Core* c, int levels);
 
 // fill the call record of stream s for a step (after core_begin); returns false on bad arguments
 struct StreamIo {

@@ -112,7 +112,7 @@ View mk(int b, long long off, int rs, int cs) {
 
 // DFB jobs of one (plane, level): detail D_j at doff, partner Q_j at qoff,
 // subband slots (coefficient offsets) in tree order.
-void dfb_jobs(int H, int W, int k, int ntaps, int stream, long long doff, long long qoff,
+void dfb_jobs(int H, int W, int k, int ntaps, int stream, int wb, long long doff, long long qoff,
               const std::vector<long long>& slot, std::vector<DfbAJob>& ajobs,
               std::vector<std::vector<DfbBJob>>& bjobs) {
     if (k == 0) return;
@@ -120,7 +120,7 @@ void dfb_jobs(int H, int W, int k, int ntaps, int stream, long long doff, long l
     const long long hw = (long long)H * W;
     DfbAJob A;
     memset(&A, 0, sizeof(A));
-    A.D = mk(B_WORK, doff, W, 1);
+    A.D = mk(wb, doff, W, 1);
     A.H = H;
     A.W = W;
     A.nst = k == 1 ? 1 : 2;
@@ -142,10 +142,10 @@ void dfb_jobs(int H, int W, int k, int ntaps, int stream, long long doff, long l
         A.comp[1] = mk(B_COEF, slot[3], w2, 1);
     } else {
         // compact channel arrays in Q_j, family r transposed ((W/2) x (H/2))
-        A.comp[0] = mk(B_WORK, qoff, w2, 1);
-        A.comp[3] = mk(B_WORK, qoff + hw / 4, w2, 1);
-        A.comp[2] = mk(B_WORK, qoff + 2 * hw / 4, 1, h2);
-        A.comp[1] = mk(B_WORK, qoff + 3 * hw / 4, 1, h2);
+        A.comp[0] = mk(wb, qoff, w2, 1);
+        A.comp[3] = mk(wb, qoff + hw / 4, w2, 1);
+        A.comp[2] = mk(wb, qoff + 2 * hw / 4, 1, h2);
+        A.comp[1] = mk(wb, qoff + 3 * hw / 4, 1, h2);
     }
     ajobs.push_back(A);
     if (k <= 2) return;
@@ -165,12 +165,12 @@ void dfb_jobs(int H, int W, int k, int ntaps, int stream, long long doff, long l
             DfbBJob J;
             memset(&J, 0, sizeof(J));
             const long long off = xin + (long long)c * csize;
-            J.pe = mk(B_WORK, off, 2 * C, 1);
-            J.po = mk(B_WORK, off + C, 2 * C, 1);
+            J.pe = mk(wb, off, 2 * C, 1);
+            J.po = mk(wb, off + C, 2 * C, 1);
             if (!fin) {
                 const long long co = yout + (long long)c * csize;
-                J.c0 = mk(B_WORK, co, C, 1);
-                J.c1 = mk(B_WORK, co + csize / 2, C, 1);
+                J.c0 = mk(wb, co, C, 1);
+                J.c1 = mk(wb, co + csize / 2, C, 1);
             } else if (fam == 0) {
                 J.c0 = mk(B_COEF, slot[2 * c], C, 1);
                 J.c1 = mk(B_COEF, slot[2 * c + 1], C, 1);
@@ -227,10 +227,44 @@ int count_b(const DfbBJob& J) {
     return ((J.R2 + DFBB_ROWS - 1) / DFBB_ROWS) * J.tiles_x;
 }
 
+// the levels t..L of a plane whose resident workspace (detail, partner and lowpass
+// image of each) fits `budget` floats, at most `most` of them; returns t (L + 1: none)
+int tail_start(const PlaneRef& P, int most, long long budget) {
+    int t = P.L + 1;
+    long long ws = 0;
+    for (int j = P.L; j >= 1 && P.L - j + 1 <= most; j--) {
+        const long long hj = P.H >> (j - 1), wj = P.W >> (j - 1);
+        ws += 2 * hj * wj + (hj / 2) * (wj / 2);
+        if (ws > budget) break;
+        t = j;
+    }
+    return t;
+}
+
+bool upload_tail(TailTables& T, bool to_device, CtEngine* e, LaunchTail* L) {
+    L->nplanes = (int)T.planes.size();
+    L->ntaps = T.ntaps;
+    L->ws_floats = 0;
+    for (const TailPlane& P : T.planes) L->ws_floats = std::max(L->ws_floats, P.ws_floats);
+    if (!to_device || T.planes.empty()) return true;
+    auto put = [&](const void* src, size_t bytes, void** dst) {
+        if (bytes == 0) return true;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+        e->allocs.push_back(*dst);
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    return put(T.planes.data(), sizeof(TailPlane) * T.planes.size(), (void**)&L->d_planes) &&
+           put(T.steps.data(), sizeof(TailStep) * T.steps.size(), (void**)&L->d_steps) &&
+           put(T.lp.data(), sizeof(LpJob) * T.lp.size(), (void**)&L->d_lp) &&
+           put(T.a.data(), sizeof(DfbAJob) * T.a.size(), (void**)&L->d_a) &&
+           put(T.b.data(), sizeof(DfbBJob) * T.b.size(), (void**)&L->d_b);
+}
 
 }  // namespace
 
 bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_device) {
+    for (void* p : e->allocs) cudaFree(p);
+    e->allocs.clear();
     e->planes = planes_in;
     int Lmax = 0, kmax = 0;
     long long work = 0;
@@ -246,16 +280,21 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
     e->work_elems = work;
     for (int m = 0; m < 4; m++) {
         const bool analysis = (m == FWD || m == INV_ADJ);
+        const bool tails = (m == FWD || m == INV) && e->tail_levels > 0;
         const int spatial_base = analysis ? B_IN : B_OUT;
         std::vector<std::vector<LpJob>> lpj(Lmax + 1);
         // tile jobs by prototype length (4, 6, 8): one launch per length and step
         std::vector<DfbAJob> aj[3];
         std::vector<std::vector<DfbBJob>> bj[3];
         for (auto& v : bj) v.resize(std::max(kmax, 2) + 1);
+        TailTables tt[3];
+        for (int n = 0; n < 3; n++) tt[n].ntaps = 4 + 2 * n;
 
         for (size_t p = 0; p < e->planes.size(); p++) {
             const PlaneRef& P = e->planes[p];
             const PlaneLayout& Ly = lays[p];
+            const int nt = (P.taps == 6 || P.taps == 8) ? P.taps : 4;
+            const int t = tails ? tail_start(P, e->tail_levels, tail_ws_budget(nt)) : P.L + 1;
             long long w = P.work;
             std::vector<long long> coff(P.L + 1), doff(P.L + 1), qoff(P.L + 1);
             for (int j = 1; j <= P.L; j++) {
@@ -267,17 +306,41 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 coff[j] = w;
                 w += (hj / 2) * (wj / 2);
             }
+            // the tail's resident workspace: the same layout for levels t..L, from 0
+            std::vector<long long> sd(P.L + 1), sq(P.L + 1), scf(P.L + 1);
+            long long ws = 0;
+            for (int j = t; j <= P.L; j++) {
+                long long hj = P.H >> (j - 1), wj = P.W >> (j - 1);
+                sd[j] = ws;
+                ws += hj * wj;
+                sq[j] = ws;
+                ws += hj * wj;
+                scf[j] = ws;
+                ws += (hj / 2) * (wj / 2);
+            }
+            TailTables& T = tt[nt / 2 - 2];
+            TailPlane tp{(int)T.steps.size(), 0, (int)ws, P.stream};
+            // the jobs of each level, in the order the tail runs them
+            std::vector<std::vector<TailStep>> level_steps(P.L + 1);
             size_t sbi = 1;
             for (int j = 1; j <= P.L; j++) {
                 int hj = P.H >> (j - 1), wj = P.W >> (j - 1), kj = P.k[j - 1];
+                const bool in_tail = j >= t;
+                const int wb = in_tail ? B_SMEM : B_WORK;
+                const std::vector<long long>& D = in_tail ? sd : doff;
+                const std::vector<long long>& Q = in_tail ? sq : qoff;
+                const std::vector<long long>& Cf = in_tail ? scf : coff;
                 std::vector<long long> slots;
                 for (int d = 0; d < (1 << kj); d++) slots.push_back(P.coef + Ly.sb[sbi + d].off);
                 sbi += (size_t)1 << kj;
+                // level j's input (analysis) / output (synthesis) image: the plane at level 1, else
+                // the lowpass c_{j-1}, resident when level j-1 is in the tail as well
                 View spatial_prev = (j == 1) ? mk(spatial_base, P.in.off, P.in.rs, 1)
-                                             : mk(B_WORK, coff[j - 1], wj, 1);
+                                             : (j - 1 >= t ? mk(B_SMEM, scf[j - 1], wj, 1)
+                                                           : mk(B_WORK, coff[j - 1], wj, 1));
                 const long long low_at = P.low_coef >= 0 ? P.low_coef : P.coef + Ly.sb[0].off;
-                View low = (j == P.L) ? mk(B_COEF, low_at, wj / 2, 1) : mk(B_WORK, coff[j], wj / 2, 1);
-                View det = (kj == 0) ? mk(B_COEF, slots[0], wj, 1) : mk(B_WORK, doff[j], wj, 1);
+                View low = (j == P.L) ? mk(B_COEF, low_at, wj / 2, 1) : mk(wb, Cf[j], wj / 2, 1);
+                View det = (kj == 0) ? mk(B_COEF, slots[0], wj, 1) : mk(wb, D[j], wj, 1);
                 LpJob J;
                 memset(&J, 0, sizeof(J));
                 J.H = hj;
@@ -296,19 +359,61 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                     J.out = spatial_prev;
                     // the lowpass images between synthesis levels are float-float: the low-order
                     // part of c_{j-1} (level j's output, hj x wj) goes to Q_j, free once the DFB
-                    // synthesis has run; level j reads that of c_j from Q_{j+1}
-                    if (j >= 2) J.out_lo = mk(B_WORK, qoff[j], wj, 1);
-                    if (j < P.L) J.cin_lo = mk(B_WORK, qoff[j + 1], wj / 2, 1);
+                    // synthesis has run; level j reads that of c_j from Q_{j+1} (resident inside
+                    // the tail; the tail's last output goes to the global Q_t for level t-1)
+                    if (j >= 2) J.out_lo = (j - 1 >= t) ? mk(B_SMEM, sq[j], wj, 1) : mk(B_WORK, qoff[j], wj, 1);
+                    if (j < P.L) J.cin_lo = mk(wb, Q[j + 1], wj / 2, 1);
                 }
-                lpj[j].push_back(J);
-                const int nt = (P.taps == 6 || P.taps == 8) ? P.taps : 4;
-                dfb_jobs(hj, wj, kj, nt, P.stream, doff[j], qoff[j], slots, aj[nt / 2 - 2], bj[nt / 2 - 2]);
+                if (!in_tail) {
+                    lpj[j].push_back(J);
+                    dfb_jobs(hj, wj, kj, nt, P.stream, B_WORK, doff[j], qoff[j], slots, aj[nt / 2 - 2],
+                             bj[nt / 2 - 2]);
+                    continue;
+                }
+                std::vector<DfbAJob> la;
+                std::vector<std::vector<DfbBJob>> lb(std::max(kj, 2) + 1);
+                dfb_jobs(hj, wj, kj, nt, P.stream, B_SMEM, sd[j], sq[j], slots, la, lb);
+                std::vector<TailStep>& st = level_steps[j];
+                auto step_lp = [&]() {
+                    st.push_back({0, (int)T.lp.size()});
+                    T.lp.push_back(J);
+                };
+                auto step_a = [&]() {
+                    for (DfbAJob& A : la) {
+                        st.push_back({1, (int)T.a.size()});
+                        T.a.push_back(A);
+                    }
+                };
+                auto step_b = [&](int s) {
+                    for (DfbBJob& Bj : lb[s]) {
+                        st.push_back({2, (int)T.b.size()});
+                        T.b.push_back(Bj);
+                    }
+                };
+                if (analysis) {
+                    step_lp();
+                    step_a();
+                    for (int s = 3; s <= kj; s++) step_b(s);
+                } else {
+                    for (int s = kj; s >= 3; s--) step_b(s);
+                    step_a();
+                    step_lp();
+                }
+            }
+            if (t <= P.L) {
+                // analysis runs levels t..L, synthesis L..t
+                for (int j = analysis ? t : P.L; analysis ? j <= P.L : j >= t; j += analysis ? 1 : -1)
+                    T.steps.insert(T.steps.end(), level_steps[j].begin(), level_steps[j].end());
+                tp.nsteps = (int)T.steps.size() - tp.first_step;
+                T.planes.push_back(tp);
             }
         }
         e->lp[m].clear();
         e->dfb[m].clear();
+        e->tail[m].clear();
         e->h_lp[m].clear();
         e->h_dfb[m].clear();
+        e->h_tail[m].clear();
         auto add_lp = [&](std::vector<LpJob>& v) {
             LaunchLp L{};
             void* dj = nullptr;
@@ -341,6 +446,13 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                                      reinterpret_cast<uint8_t*>(v.data() + v.size()));
             return true;
         };
+        for (int n = 0; n < 3; n++) {
+            if (tt[n].planes.empty()) continue;
+            LaunchTail L;
+            if (!upload_tail(tt[n], to_device, e, &L)) return false;
+            e->tail[m].push_back(L);
+            e->h_tail[m].push_back(tt[n]);
+        }
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)
                 if (!add_lp(lpj[j])) return false;
@@ -365,13 +477,14 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
 cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cudaStream_t st) {
     cudaError_t err = cudaSuccess;
     if (part == 0) {
-        for (const LaunchLp& L : e->lp[m]) {
+        for (const LaunchLp& L : e->lp[m])
             if ((err = launch_lp(L, m, bases, st)) != cudaSuccess) return err;
-        }
-    } else {
-        for (const LaunchDfb& L : e->dfb[m]) {
+    } else if (part == 1) {
+        for (const LaunchDfb& L : e->dfb[m])
             if ((err = launch_dfb(L, m, bases, st)) != cudaSuccess) return err;
-        }
+    } else {
+        for (const LaunchTail& L : e->tail[m])
+            if ((err = launch_tail(L, m, bases, st)) != cudaSuccess) return err;
     }
     return err;
 }
@@ -380,16 +493,22 @@ int engine_part_launches(const CtEngine* e, Mode m, int part) {
     int n = 0;
     if (part == 0)
         for (const LaunchLp& L : e->lp[m]) n += L.nblocks > 0;
-    else
+    else if (part == 1)
         for (const LaunchDfb& L : e->dfb[m]) n += L.nblocks > 0;
+    else
+        for (const LaunchTail& L : e->tail[m]) n += L.nplanes > 0;
     return n;
 }
 
+// everything on one stream: analysis LP levels, tails (they read the last global level's
+// lowpass), DFB stages; synthesis DFB stages, tails (they write it), LP levels
 cudaError_t engine_run(const CtEngine* e, Mode m, Bases bases, cudaStream_t st) {
     const bool analysis = (m == FWD || m == INV_ADJ);
-    cudaError_t err = engine_run_part(e, m, analysis ? 0 : 1, bases, st);
-    if (err == cudaSuccess) err = engine_run_part(e, m, analysis ? 1 : 0, bases, st);
-    if (err == cudaSuccess) note_launches(engine_part_launches(e, m, 0) + engine_part_launches(e, m, 1));
+    const int order[3] = {analysis ? 0 : 1, 2, analysis ? 1 : 0};
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < 3 && err == cudaSuccess; k++) err = engine_run_part(e, m, order[k], bases, st);
+    if (err == cudaSuccess)
+        note_launches(engine_part_launches(e, m, 0) + engine_part_launches(e, m, 1) + engine_part_launches(e, m, 2));
     return err;
 }
 

@@ -24,7 +24,8 @@ enum : uint32_t {
 // `act` (may be NULL) marks the streams that take part in the call: stream
 // s takes part iff the int at byte offset s * act_stride is non-zero; the
 // tile kernels skip the jobs of the other streams (a job's stream < 0: always).
-enum { B_IN = 0, B_COEF = 1, B_WORK = 2, B_OUT = 3, N_BASES = 4 };
+// B_SMEM: inside the pyramid-tail kernel, the block's resident workspace in shared memory.
+enum { B_IN = 0, B_COEF = 1, B_WORK = 2, B_OUT = 3, B_SMEM = 4, N_BASES = 5 };
 struct Bases {
     float* p[N_BASES];
     const int* act;
@@ -154,6 +155,41 @@ struct LaunchDfb {
     int ntaps;  // the prototype length of the launch's planes (4, 6 or 8)
 };
 
+// Pyramid tail: the coarse levels of a plane whose working images fit in one
+// block's shared memory (§2.1 "where the data fits") run in one block of one
+// launch: the LP level jobs and the DFB stage jobs of those levels, the same
+// tile computations as the per-level launches, executed one after the other
+// with the intermediate images resident in shared memory (base B_SMEM); only
+// the level's input lowpass (analysis) or output lowpass (synthesis) and the
+// coefficients go through global memory.
+struct TailStep {
+    int kind;  // 0: LpJob, 1: DfbAJob, 2: DfbBJob
+    int job;   // index into the launch's table of that kind
+};
+struct TailPlane {
+    int first_step, nsteps;
+    int ws_floats;  // resident workspace of the plane's levels (floats of shared memory)
+    int stream;     // Bases::act
+};
+struct LaunchTail {
+    int nplanes = 0;   // one block each
+    int ntaps = 4;
+    int ws_floats = 0; // largest resident workspace of the launch's planes
+    TailPlane* d_planes = nullptr;
+    TailStep* d_steps = nullptr;
+    LpJob* d_lp = nullptr;
+    DfbAJob* d_a = nullptr;
+    DfbBJob* d_b = nullptr;
+};
+struct TailTables {   // host copy of a tail launch's tables
+    int ntaps = 4;
+    std::vector<TailPlane> planes;
+    std::vector<TailStep> steps;
+    std::vector<LpJob> lp;
+    std::vector<DfbAJob> a;
+    std::vector<DfbBJob> b;
+};
+
 enum Mode { FWD = 0, INV = 1, FWD_ADJ = 2, INV_ADJ = 3 };
 
 struct CtEngine {
@@ -165,6 +201,14 @@ struct CtEngine {
     // host copies of the job tables, launch by launch (for plan self-checks)
     std::vector<std::vector<LpJob>> h_lp[4];
     std::vector<std::vector<uint8_t>> h_dfb[4];
+    // pyramid-tail launches (forward and inverse only), one per prototype length
+    std::vector<LaunchTail> tail[4];
+    std::vector<TailTables> h_tail[4];
+    // fusion depth: the most coarse levels of a plane that run in its tail (0: none, the
+    // default: on B300 one block per plane is slower than the coarse levels' own launches
+    // for 1080p planes; the autotuner tries the others); a plane's tail takes as many of
+    // them as fit the shared-memory budget
+    int tail_levels = 0;
     std::vector<void*> allocs;
     ~CtEngine();
 };
@@ -175,8 +219,10 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes, bool to_devi
 size_t workspace_elems(int H, int W, int L);
 // the whole transform of mode m (counted in the launch counter)
 cudaError_t engine_run(const CtEngine* e, Mode m, Bases bases, cudaStream_t st);
-// one part of a mode's launch sequence: part 0 = LP levels, part 1 = DFB passes
-// (not counted: the caller adds engine_part_launches)
+// one part of a mode's launch sequence: part 0 = LP levels, part 1 = DFB passes,
+// part 2 = pyramid tails (not counted: the caller adds engine_part_launches).  The tails
+// depend on the LP levels in the analysis direction and the LP levels on the tails in
+// the synthesis direction; the DFB passes of the other levels are independent of them.
 cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cudaStream_t st);
 int engine_part_launches(const CtEngine* e, Mode m, int part);
 
@@ -191,5 +237,10 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
 // one-time kernel attributes of the DFB kernels (call before any stream capture)
 cudaError_t dfb_prepare();
 PassParams pass_params(Mode m);
+// pyramid tail: shared-memory floats a tail block has for its resident workspace
+// (beyond the tile scratch), the launch, and its one-time attributes
+int tail_ws_budget(int ntaps);
+cudaError_t launch_tail(const LaunchTail& L, Mode m, Bases bases, cudaStream_t st);
+cudaError_t tail_prepare();
 
 }  // namespace cvc

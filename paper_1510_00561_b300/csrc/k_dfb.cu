@@ -27,521 +27,31 @@
 // by the Laplacian-pyramid synthesis, which is compensated (k_lp.cu).
 #include <mutex>
 
-#include "cvc_internal.cuh"
+#include "dfb_tile.cuh"
 
 namespace cvc {
 
-__device__ __forceinline__ int wrapd(int a, int n) {
-    if ((unsigned)a < (unsigned)n) return a;
-    int r = a % n;
-    return r < 0 ? r + n : r;
-}
-
-// the fan taps sign(a) |beta[a]| of the NT-tap prototype, a = 2t - (NT - 1), as
-// compile-time immediates: NT = 4, (-1, 9, 9, -1)/16; NT = 6 and 8, the longer
-// Lagrange half-band interpolators (3, -25, 150, 150, -25, 3)/256 and
-// (-5, 49, -245, 1225, 1225, -245, 49, -5)/2048 (all dyadic: exact)
-__host__ __device__ constexpr float fan_tap(int NT, int t) {
-    return NT == 4 ? (t == 0 ? -1.f : t == 1 ? -9.f : t == 2 ? 9.f : 1.f) / 16.f
-         : NT == 6 ? (t == 0 ? -3.f : t == 1 ? -25.f : t == 2 ? -150.f : t == 3 ? 150.f : t == 4 ? 25.f : 3.f) / 256.f
-                   : (t == 0 ? -5.f : t == 1 ? -49.f : t == 2 ? -245.f : t == 3 ? -1225.f
-                      : t == 4 ? 1225.f : t == 5 ? 245.f : t == 6 ? 49.f : 5.f) / 2048.f;
-}
-
-// 4-byte asynchronous global -> shared copies: a thread issues all of its
-// staging loads before waiting, so a tile's whole halo is in flight at once
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4s(unsigned dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ unsigned smem_addr(const float* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// ============================================================ k_dfb_a
-// Geometry of the NT-tap tiles: one pass reaches R = NT - 1 samples, the four
-// passes of stages 1 and 2 need a halo of 4R around the 64 x 64 tile.
-template <int NT>
-struct AGeo {
-    static constexpr int R = NT - 1;
-    static constexpr int HALO = 4 * R;                   // 12, 20, 28
-    static constexpr int SA = DFBA_TILE + 2 * HALO;      // tile + halo, image samples
-    static constexpr int PA = SA / 2;                    // polyphase plane side
-    static constexpr int PAS = PA + 1;                   // padded plane row stride
-    static constexpr int SMEM = 6 * PA * PAS * 4;        // four planes and two scratch planes (bytes)
-};
-static_assert(AGeo<4>::HALO == DFBA_HALO, "4-tap halo");
-
-__host__ __device__ constexpr int fdiv2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
-// plane rows (or columns) of parity p whose image index lies in [lo, hi)
-__host__ __device__ constexpr int pl0(int lo, int p) { return (lo - p + 1) / 2; }
-__host__ __device__ constexpr int pl1(int hi, int p) { return (hi - 1 - p) / 2 + 1; }
-
-// Both stages evaluate their NT x NT stencils separably.
-//   Stage 1 (quincunx, taps at ((a+b)/2, (a-b)/2)): the anti-diagonal sums
-//     D[p] = sum_m bt[m] x[p + (m, -m)] at the source coset's points, then
-//     acc(t) = sum_n bt[n] D[t + (n - R, n)].
-//   Stage 2 (taps at (a, b) in both families): row sums along the target's
-//     source plane, then sums down its columns, the row sums kept in registers.
-// A pass over image-local [lo, hi)^2, lo = R n, reads the region the previous
-// pass left valid, [lo - R, hi + R)^2.  Consecutive threads take consecutive
-// elements of a region row.
-
-// element offset of plane class (r, c) at plane-local (u, v)
-template <int NT>
-__host__ __device__ constexpr int pofs(int r, int c, int u, int v) {
-    return (2 * r + c) * AGeo<NT>::PA * AGeo<NT>::PAS + u * AGeo<NT>::PAS + v;
-}
-
-// Visit every (u, v) of [U0, U1) x [V0, V1) with the element offset u*PAS + v:
-// thread t owns column V0 + t % NV and walks down rows U0 + t / NV, stepping
-// by the number of row chunks, so an access is one running offset plus a
-// compile-time displacement.
-template <int NT, int U0, int U1, int V0, int V1, class F>
-__device__ __forceinline__ void region_walk(F&& f) {
-    constexpr int NV = V1 - V0, CH = 256 / NV, PAS = AGeo<NT>::PAS;
-    static_assert(NV >= 1 && NV <= 256 && U1 > U0, "region");
-    static_assert(U0 >= 0 && V0 >= 0 && U1 <= AGeo<NT>::PA && V1 <= AGeo<NT>::PA, "region inside the planes");
-    const int t = threadIdx.x;
-    if (t >= CH * NV) return;
-    const int v = V0 + t % NV;
-    int off = (U0 + t / NV) * PAS + v;
-    for (int u = U0 + t / NV; u < U1; u += CH, off += CH * PAS) f(off);
-}
-
-// stage 1, source class (sr, sc): D[p] = sum_m bt[m] x[p + (m, -m)] over image rows
-// [lo-R, hi) and columns [lo, hi+R) of the class, into tmp plane sr
-template <int NT, int N, bool ODD, int K>
-__device__ __forceinline__ void s1_dsum(const float* planes, float* tmp) {
-    using G = AGeo<NT>;
-    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
-    constexpr int sr = K, sc = ODD ? K : 1 - K;
-    float* D = tmp + sr * G::PA * G::PAS;
-    region_walk<NT, pl0(lo - G::R, sr), pl1(hi, sr), pl0(lo, sc), pl1(hi + G::R, sc)>([&](int off) {
-        float acc = fan_tap(NT, 0) * planes[off + pofs<NT>(sr & 1, sc & 1, fdiv2(sr), fdiv2(sc))];
-#pragma unroll
-        for (int m = 1; m < NT; m++)
-            acc = fmaf(fan_tap(NT, m), planes[off + pofs<NT>((sr + m) & 1, (sc - m) & 1, fdiv2(sr + m), fdiv2(sc - m))],
-                       acc);
-        D[off] = acc;
-    });
-}
-
-// stage 1, target class (tr, tc): acc(t) = sum_n bt[n] D[t + (n - R, n)]
-template <int NT, int N, bool ODD, int K>
-__device__ __forceinline__ void s1_target(float* planes, const float* tmp, float alpha, float gamma) {
-    using G = AGeo<NT>;
-    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
-    constexpr int tr = K, tc = ODD ? 1 - K : K;
-    float* T = planes + (2 * tr + tc) * G::PA * G::PAS;
-    region_walk<NT, pl0(lo, tr), pl1(hi, tr), pl0(lo, tc), pl1(hi, tc)>([&](int off) {
-        float acc = 0.f;
-#pragma unroll
-        for (int n = 0; n < NT; n++) {
-            const int o = ((tr - G::R + n) & 1) * G::PA * G::PAS + fdiv2(tr - G::R + n) * G::PAS + fdiv2(tc + n);
-            acc = n == 0 ? fan_tap(NT, 0) * tmp[off + o] : fmaf(fan_tap(NT, n), tmp[off + o], acc);
-        }
-        T[off] = fmaf(alpha, T[off], gamma * acc);
-    });
-}
-
-template <int NT, int N, bool ODD>
-__device__ __forceinline__ void dfba_stage1(float* planes, float* tmp, float alpha, float gamma) {
-    // sources: the even coset {00, 11} for odd targets, {01, 10} for even ones
-    s1_dsum<NT, N, ODD, 0>(planes, tmp);
-    s1_dsum<NT, N, ODD, 1>(planes, tmp);
-    __syncthreads();
-    // targets: {01, 10} (odd) or {00, 11}
-    s1_target<NT, N, ODD, 0>(planes, tmp, alpha, gamma);
-    s1_target<NT, N, ODD, 1>(planes, tmp, alpha, gamma);
-    __syncthreads();
-}
-
-// stage 2, target class (tr, tc), which reads class (1-tr, 1-tc) at
-// (u + ky + tr - NT/2, v + kx + tc - NT/2), with the row sums kept in
-// registers: thread t owns column v of the target region and a run of L
-// consecutive rows; it forms each source row sum once (the NT - 1 rows above
-// its run once more) and keeps the NT its current target needs, so nothing
-// goes through the scratch planes.  Each row sum accumulates its taps in kx
-// order and each target its row sums in ky order, as a staged evaluation does.
-template <int NT>
-__device__ __forceinline__ float s2_row(const float* p) {
-    float acc = fan_tap(NT, 0) * p[0];
-#pragma unroll
-    for (int kx = 1; kx < NT; kx++) acc = fmaf(fan_tap(NT, kx), p[kx], acc);
-    return acc;
-}
-
-template <int NT, int N, bool ODD, int K>
-__device__ __forceinline__ void s2_fused(float* planes, float alpha, float gamma) {
-    using G = AGeo<NT>;
-    constexpr int lo = G::R * N, hi = G::SA - G::R * N;
-    constexpr int tr = K, tc = ODD ? 1 : 0;
-    constexpr int u0 = pl0(lo, tr), u1 = pl1(hi, tr), v0 = pl0(lo, tc), v1 = pl1(hi, tc);
-    constexpr int NV = v1 - v0, NU = u1 - u0, S = 256 / NV, L = (NU + S - 1) / S;
-    constexpr int PAS = G::PAS, PL = G::PA * G::PAS;
-    // source rows u0 + tr - NT/2 .. u1 + tr - NT/2 + NT - 2, columns v0 + tc - NT/2 .. v1 + tc - NT/2 + NT - 2
-    static_assert(u0 + tr - NT / 2 >= 0 && u1 + tr - NT / 2 + NT - 1 <= G::PA, "source rows inside the plane");
-    static_assert(v0 + tc - NT / 2 >= 0 && v1 + tc - NT / 2 + NT - 1 <= G::PA, "source columns inside the plane");
-    static_assert(NV >= 1 && NV <= 256 && S * L >= NU, "runs cover the region");
-    const int t = threadIdx.x;
-    if (t >= S * NV) return;
-    const int v = v0 + t % NV;
-    const int ua = u0 + (t / NV) * L, ub = min(ua + L, u1);
-    if (ua >= ub) return;
-    float* T = planes + (2 * tr + tc) * PL + ua * PAS + v;
-    const float* src = planes + (2 * (1 - tr) + (1 - tc)) * PL + (ua + tr - NT / 2) * PAS + v + tc - NT / 2;
-    const int cnt = ub - ua;
-    float w[L + NT - 1];   // w[j]: row sum of source row ua + tr - NT/2 + j
-#pragma unroll
-    for (int j = 0; j < NT - 1; j++) w[j] = s2_row<NT>(src + j * PAS);
-#pragma unroll
-    for (int k = 0; k < L; k++) {
-        if (k < cnt) {
-            w[k + NT - 1] = s2_row<NT>(src + (k + NT - 1) * PAS);
-            float acc = fan_tap(NT, 0) * w[k];
-#pragma unroll
-            for (int ky = 1; ky < NT; ky++) acc = fmaf(fan_tap(NT, ky), w[k + ky], acc);
-            T[k * PAS] = fmaf(alpha, T[k * PAS], gamma * acc);
-        }
-    }
-}
-
-template <int NT, int N, bool ODD>
-__device__ __forceinline__ void dfba_stage2(float* planes, float alpha, float gamma) {
-    // targets: {11, 01} (odd) or {00, 10}; each reads only the other class of its row parity
-    s2_fused<NT, N, ODD, 0>(planes, alpha, gamma);
-    s2_fused<NT, N, ODD, 1>(planes, alpha, gamma);
-    __syncthreads();
-}
-
-// the passes of one tile: analysis runs stage 1 then 2, synthesis stage 2 then 1
-template <int NT, bool SYN, bool FO>
-__device__ __forceinline__ void dfba_passes(float* planes, float* tmp, int nst, const PassParams& pp) {
-    if (!SYN) {
-        dfba_stage1<NT, 1, FO>(planes, tmp, pp.a1, pp.g1);
-        dfba_stage1<NT, 2, !FO>(planes, tmp, pp.a2, pp.g2);
-        if (nst == 2) {
-            dfba_stage2<NT, 3, FO>(planes, pp.a1, pp.g1);
-            dfba_stage2<NT, 4, !FO>(planes, pp.a2, pp.g2);
-        }
-    } else if (nst == 2) {
-        dfba_stage2<NT, 1, FO>(planes, pp.a1, pp.g1);
-        dfba_stage2<NT, 2, !FO>(planes, pp.a2, pp.g2);
-        dfba_stage1<NT, 3, FO>(planes, tmp, pp.a1, pp.g1);
-        dfba_stage1<NT, 4, !FO>(planes, tmp, pp.a2, pp.g2);
-    } else {
-        dfba_stage1<NT, 1, FO>(planes, tmp, pp.a1, pp.g1);
-        dfba_stage1<NT, 2, !FO>(planes, tmp, pp.a2, pp.g2);
-    }
-}
-
-// dynamic shared memory: AGeo<NT>::SMEM bytes (four planes, then two scratch planes)
+// stages 1 + 2, one block per (job, tile); blocks of streams that take no part return
 template <bool SYN, int NT>
 __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
-    using G = AGeo<NT>;
-    constexpr int SA = G::SA, PA = G::PA, PAS = G::PAS, HALO = G::HALO;
     extern __shared__ __align__(16) float smem_a[];
-    float* planes = smem_a;
-    float* tmp = smem_a + 4 * PA * PAS;
     const DfbAJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    const int tile = blockIdx.x - J.first_block;
-    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
-    const int y0 = ty * DFBA_TILE, x0 = tx * DFBA_TILE;
-    const int H = J.H, W = J.W, H2 = H / 2, W2 = W / 2;
-    // plane-local (u, v) of class (pr, pc) <-> image (y0 - HALO + 2u + pr, x0 - HALO + 2v + pc);
-    // class-array index ((y0 - HALO)/2 + u, (x0 - HALO)/2 + v), periodic in (H/2, W/2)
-    const int cu0 = (y0 - HALO) / 2, cv0 = (x0 - HALO) / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (!SYN) {
-        const float* Dp = base_ptr(B, J.D.b) + J.D.off;
-        const bool inner = x0 - HALO >= 0 && x0 - HALO + SA <= W;   // no column wrap in this tile
-        for (int r = warp; r < SA; r += 8) {
-            const float* row = Dp + (long long)wrapd(y0 - HALO + r, H) * J.D.rs;
-            // image column c of the tile -> plane (r & 1, c & 1), plane column c >> 1
-            const unsigned sb = smem_addr(planes + 2 * (r & 1) * PA * PAS + (r >> 1) * PAS);
-            for (int c = lane; c < SA; c += 32) {
-                const int x = inner ? x0 - HALO + c : wrapd(x0 - HALO + c, W);
-                cp_async4s(sb + 4u * ((c & 1) * PA * PAS + (c >> 1)), row + x);
-            }
-        }
-    } else {
-        for (int q = 0; q < 4; q++) {
-            const View& V = J.comp[q];
-            const float* P = base_ptr(B, V.b) + V.off;
-            if (V.cs == 1) {
-                // row-major channel: plane row u is a run of array row cu
-                const bool inner = cv0 >= 0 && cv0 + PA <= W2;
-                for (int u = warp; u < PA; u += 8) {
-                    const float* row = P + (long long)wrapd(cu0 + u, H2) * V.rs;
-                    const unsigned sb = smem_addr(planes + q * PA * PAS + u * PAS);
-                    for (int v = lane; v < PA; v += 32)
-                        cp_async4s(sb + 4u * v, row + (inner ? cv0 + v : wrapd(cv0 + v, W2)));
-                }
-            } else {
-                // transposed channel (rs = 1): walk along its memory rows, plane column v
-                for (int v = warp; v < PA; v += 8) {
-                    const float* col = P + (long long)wrapd(cv0 + v, W2) * V.cs;
-                    for (int u = lane; u < PA; u += 32)
-                        cp_async4s(smem_addr(planes + q * PA * PAS + u * PAS + v), col + wrapd(cu0 + u, H2) * V.rs);
-                }
-            }
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (pp.first_odd) dfba_passes<NT, SYN, true>(planes, tmp, J.nst, pp);
-    else dfba_passes<NT, SYN, false>(planes, tmp, J.nst, pp);
-    // store the 64 x 64 tile: plane-local rows / columns [HALO/2, HALO/2 + 32)
-    constexpr int T2 = DFBA_TILE / 2, H6 = HALO / 2;
-    if (!SYN) {
-        for (int q = 0; q < 4; q++) {
-            const View& V = J.comp[q];
-            float* P = base_ptr(B, V.b) + V.off;
-            const bool trans = V.cs != 1;
-            for (int k = threadIdx.x; k < T2 * T2; k += blockDim.x) {
-                int a = k / T2, b = k - a * T2;
-                int u = trans ? b : a, v = trans ? a : b;
-                int cu = y0 / 2 + u, cv = x0 / 2 + v;
-                if (cu < H2 && cv < W2)
-                    P[(long long)cu * V.rs + (long long)cv * V.cs] = planes[q * PA * PAS + (H6 + u) * PAS + H6 + v];
-            }
-        }
-    } else {
-        float* Do = base_ptr(B, J.D.b) + J.D.off;
-        static_assert(HALO % 2 == 0 && DFBA_TILE % 2 == 0, "column pairs start on even plane columns");
-        if ((reinterpret_cast<uintptr_t>(Do) & 7) == 0 && (J.D.rs & 1) == 0) {
-            // column pairs (c, c + 1), c even: the same column of the two planes of row parity rr & 1,
-            // one 8-byte store per pair
-            constexpr int HP = DFBA_TILE / 2;
-            for (int k = threadIdx.x; k < DFBA_TILE * HP; k += blockDim.x) {
-                const int r = k / HP, c = 2 * (k - r * HP);
-                const int y = y0 + r, x = x0 + c;
-                if (y >= H || x >= W) continue;
-                const int rr = HALO + r, cc = HALO + c;
-                const float* pl = planes + 2 * (rr & 1) * PA * PAS + (rr >> 1) * PAS + (cc >> 1);
-                float* dst = Do + (long long)y * J.D.rs + x;
-                if (x + 1 < W) *reinterpret_cast<float2*>(dst) = make_float2(pl[0], pl[PA * PAS]);
-                else dst[0] = pl[0];
-            }
-        } else {
-            for (int k = threadIdx.x; k < DFBA_TILE * DFBA_TILE; k += blockDim.x) {
-                int r = k / DFBA_TILE, c = k - r * DFBA_TILE;
-                int y = y0 + r, x = x0 + c;
-                if (y < H && x < W) {
-                    int rr = HALO + r, cc = HALO + c;
-                    Do[(long long)y * J.D.rs + x] = planes[(2 * (rr & 1) + (cc & 1)) * PA * PAS + (rr >> 1) * PAS + (cc >> 1)];
-                }
-            }
-        }
-    }
+    dfb_a_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, smem_a);
 }
 
-// ============================================================ k_dfb_b
-// Tile frame for an NT-tap prototype (reach R = NT - 1 per pass): RB = 16 + 2R
-// rows (R-row halo) by CB = 128 columns, of which COLS = 128 - 4R are outputs
-// (2R-column halo: 116, 108, 100), rows stored with stride CBS = CB + 4.  The
-// coset updated first (F) and the second pass's row sums are stored one float
-// to the right of their array base, so that every column-pair window below is
-// 8-byte aligned (R is odd for every even NT).  A thread owns one column pair
-// and one of four interleaved row chunks and walks its rows with constant
-// pointer steps; pairs of lanes compute with paired FP32 instructions,
-// rounding each lane exactly as the scalar sequence would.
-template <int NT>
-struct BGeo {
-    static constexpr int R = NT - 1;
-    static constexpr int CB = 128, CBS = CB + 4;
-    static constexpr int COLS = CB - 4 * R;
-    static constexpr int RB = DFBB_ROWS + 2 * R;
-    static constexpr int SMB = RB * CBS + 2;     // floats per tile array (room for the shift)
-};
-constexpr int NPAIR = 64, NCHUNK = 4;   // 256 threads
-static_assert(BGeo<4>::COLS == DFBB_COLS && BGeo<8>::CB / 2 <= NPAIR, "one column pair per thread");
-static_assert(3 * BGeo<8>::SMB * 4 <= 48 * 1024, "static shared memory");
-
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// row sums h[rr][x] = sum_b bt[b] S[rr][x + b], rows [SR0, SR1), pairs x = X0 + 2p, p < NP
-template <int NT, int SR0, int SR1, int X0, int NP>
-__device__ __forceinline__ void rowsum_pairs(const float* S, float* H) {
-    using G = BGeo<NT>;
-    static_assert(SR0 >= 0 && SR1 <= G::RB && X0 >= 0 && X0 + 2 * NP + NT - 1 <= G::CBS, "row-sum window");
-    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
-    if (p >= NP) return;
-    const float* s = S + (SR0 + c) * G::CBS + X0 + 2 * p;
-    float* h = H + (SR0 + c) * G::CBS + X0 + 2 * p;
-    for (int rr = SR0 + c; rr < SR1; rr += NCHUNK, s += NCHUNK * G::CBS, h += NCHUNK * G::CBS) {
-        float2 v[NT / 2];
-#pragma unroll
-        for (int k = 0; k < NT / 2; k++) v[k] = *reinterpret_cast<const float2*>(s + 2 * k);
-        const float e = s[NT];
-        float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), v[0]);
-#pragma unroll
-        for (int b = 1; b < NT; b++) {
-            // the pair (S[x + b], S[x + 1 + b])
-            const float2 pr = (b & 1) ? f2(v[b >> 1].y, b + 1 < NT ? v[(b + 1) >> 1].x : e) : v[b >> 1];
-            acc = __ffma2_rn(f2(fan_tap(NT, b), fan_tap(NT, b)), pr, acc);
-        }
-        *reinterpret_cast<float2*>(h) = acc;
-    }
-}
-
-// targets t[r][x] = alpha t + gamma sum_ia bt[ia] h[r + DB + ia][x - ia], rows [R0, R1),
-// pairs x = X0 + 2p, p < NP.  The layout makes the ia-odd pairs 8-byte aligned.
-template <int NT, int R0, int R1, int X0, int NP, bool ODD>
-__device__ __forceinline__ void target_pairs(float* T, const float* H, float alpha, float gamma) {
-    using G = BGeo<NT>;
-    constexpr int DB = ODD ? -(NT - 2) / 2 : -NT / 2;
-    static_assert(R0 + DB >= 0 && R1 + DB + NT - 1 <= G::RB && X0 >= NT - 1 && X0 + 2 * NP <= G::CB, "target window");
-    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
-    if (p >= NP) return;
-    const float* h = H + (R0 + c + DB) * G::CBS + X0 + 2 * p;
-    float* t = T + (R0 + c) * G::CBS + X0 + 2 * p;
-    const float2 al = f2(alpha, alpha), ga = f2(gamma, gamma);
-    for (int r = R0 + c; r < R1; r += NCHUNK, h += NCHUNK * G::CBS, t += NCHUNK * G::CBS) {
-        float2 acc;
-#pragma unroll
-        for (int ia = 0; ia < NT; ia++) {
-            const float* hp = h + ia * G::CBS - ia;                  // columns x - ia, x + 1 - ia
-            const float2 pr = (ia & 1) ? *reinterpret_cast<const float2*>(hp) : f2(hp[0], hp[1]);
-            acc = ia == 0 ? __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), pr)
-                          : __ffma2_rn(f2(fan_tap(NT, ia), fan_tap(NT, ia)), pr, acc);
-        }
-        float2 tv = *reinterpret_cast<const float2*>(t);
-        tv = __ffma2_rn(al, tv, __fmul2_rn(ga, acc));
-        *reinterpret_cast<float2*>(t) = tv;
-    }
-}
-
-template <int CB>
-__device__ __forceinline__ int wrap_fast(int v, int C) {
-    // v in [0, C + CB): one subtraction when C >= CB, a remainder otherwise
-    return v < C ? v : (C >= CB ? v - C : v % C);
-}
-
+// one row-split stage, one block per (job, tile)
 template <bool SYN, int NT>
 __global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     using G = BGeo<NT>;
-    constexpr int R = G::R, RB = G::RB, CB = G::CB, CBS = G::CBS, COLS = G::COLS;
     __shared__ __align__(16) float sE[G::SMB];
     __shared__ __align__(16) float sO[G::SMB];
     __shared__ __align__(16) float sH[G::SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    const int tile = blockIdx.x - J.first_block;
-    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
-    const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;
-    const int R2 = J.R2, C = J.C, i = J.i;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const int fo = pp.first_odd;
-    // the first-updated coset (odd if fo) sits one float to the right
-    float* const arrE = sE + (fo ? 0 : 1);
-    float* const arrO = sO + (fo ? 1 : 0);
-    // inputs: analysis reads the parent's cosets, synthesis the children.
-    // Smem row r <-> coset row t0 - R + r; smem column x <-> sheared column c0 - 2R + x,
-    // i.e. array column (c0 - 2R + x - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
-    for (int par = 0; par < 2; par++) {
-        const View V = par ? (SYN ? J.c1 : J.po) : (SYN ? J.c0 : J.pe);
-        const float* P = base_ptr(B, V.b) + V.off;
-        float* S = par ? arrO : arrE;
-        if (V.cs == 1) {
-            for (int r = warp; r < RB; r += nwarp) {
-                const int tu = t0 - R + r;
-                const float* row = P + (long long)wrapd(tu, R2) * V.rs;
-                const int vs = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
-                const unsigned sb = smem_addr(S + r * CBS);
-                if (vs + CB <= C) {                  // the sheared window does not wrap: no per-element checks
-                    const float* src = row + vs;
-                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
-                } else {
-                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
-                }
-            }
-        } else {
-            // transposed array (rows contiguous in memory along t): walk the sheared
-            // tile along memory order; for offset w every row r shares the array
-            // column v, at tile column x = w + 2*i*r
-            const int wlo = i > 0 ? -2 * i * (RB - 1) : 0, whi = CB + (i < 0 ? -2 * i * (RB - 1) : 0);
-            const int vbase = c0 - 2 * R - i * (2 * (t0 - R) + par);
-            for (int k = threadIdx.x; k < (whi - wlo) * RB; k += blockDim.x) {
-                const int w = wlo + k / RB, r = k - (k / RB) * RB;
-                const int x = w + 2 * i * r;
-                if (x < 0 || x >= CB) continue;
-                const int v = wrapd(vbase + w, C);
-                cp_async4(&S[r * CBS + x], P + (long long)wrapd(t0 - R + r, R2) * V.rs + (long long)v * V.cs);
-            }
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // pass 1 updates F on columns [R, CB - R), which covers what pass 2 reads; pass 2
-    // updates S on the tile [R, R + ROWS) x [2R, CB - 2R).  Pass-1 row sums sit at the
-    // base of sH, pass-2 row sums one float to the right.
-    float* F = fo ? arrO : arrE;
-    float* Sx = fo ? arrE : arrO;
-    constexpr int NP1 = (CB - 2 * R) / 2, NH1 = (CB - R + 1) / 2, NP2 = COLS / 2, NH2 = (CB - 3 * R + 1) / 2;
-    static_assert(R + 2 * NP1 == CB - R && 2 * R + 2 * NP2 == CB - 2 * R, "pass windows");
-    constexpr int ROWS = DFBB_ROWS;
-    if (fo) {
-        rowsum_pairs<NT, 0, RB, 0, NH1>(Sx, sH);
-        __syncthreads();
-        target_pairs<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, NP1, true>(F, sH, pp.a1, pp.g1);
-        __syncthreads();
-        rowsum_pairs<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, NH2>(F, sH + 1);
-        __syncthreads();
-        target_pairs<NT, R, R + ROWS, 2 * R, NP2, false>(Sx, sH + 1, pp.a2, pp.g2);
-    } else {
-        rowsum_pairs<NT, 0, RB, 0, NH1>(Sx, sH);
-        __syncthreads();
-        target_pairs<NT, NT / 2, R + ROWS + NT / 2, R, NP1, false>(F, sH, pp.a1, pp.g1);
-        __syncthreads();
-        rowsum_pairs<NT, NT / 2, R + ROWS + NT / 2, R, NH2>(F, sH + 1);
-        __syncthreads();
-        target_pairs<NT, R, R + ROWS, 2 * R, NP2, true>(Sx, sH + 1, pp.a2, pp.g2);
-    }
-    __syncthreads();
-    // outputs: analysis writes the children, synthesis the parent's cosets
-    const int ncol = min(COLS, C - c0);
-    for (int par = 0; par < 2; par++) {
-        const View V = par ? (SYN ? J.po : J.c1) : (SYN ? J.pe : J.c0);
-        float* P = base_ptr(B, V.b) + V.off;
-        const float* S = par ? arrO : arrE;
-        if (V.cs == 1) {
-            for (int rr = warp; rr < DFBB_ROWS; rr += nwarp) {
-                const int t = t0 + rr;
-                if (t >= R2) break;
-                float* row = P + (long long)t * V.rs;
-                const int vs = wrapd(c0 - i * (2 * t + par), C);
-                const float* srow = S + (R + rr) * CBS + 2 * R;
-                if (vs + ncol <= C) {
-                    float* dst = row + vs;
-                    for (int xx = lane; xx < ncol; xx += 32) dst[xx] = srow[xx];
-                } else {
-                    for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
-                }
-            }
-        } else {
-            // transposed subband: walk along memory order as in the load
-            const int wlo = i > 0 ? -2 * i * (DFBB_ROWS - 1) : 0;
-            const int whi = COLS + (i < 0 ? -2 * i * (DFBB_ROWS - 1) : 0);
-            const int vbase = c0 - i * (2 * t0 + par);
-            for (int k = threadIdx.x; k < (whi - wlo) * DFBB_ROWS; k += blockDim.x) {
-                const int w = wlo + k / DFBB_ROWS, rr = k - (k / DFBB_ROWS) * DFBB_ROWS;
-                const int xx = w + 2 * i * rr;
-                const int t = t0 + rr;
-                if (xx < 0 || xx >= ncol || t >= R2) continue;
-                const int v = wrapd(vbase + w, C);
-                P[(long long)t * V.rs + (long long)v * V.cs] = S[(R + rr) * CBS + 2 * R + xx];
-            }
-        }
-    }
+    dfb_b_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, sE, sO, sH);
 }
 
 // ============================================================ launches

@@ -28,78 +28,9 @@
 // precision (k_lp_level).
 #include <mutex>
 
-#include "cvc_internal.cuh"
+#include "lp_tile.cuh"
 
 namespace cvc {
-
-// CDF 9/7 lowpass pair normalised to DC gain sqrt(2) (published values,
-// 12 significant digits): analysis h (taps -4..4), synthesis g (-3..3).
-// Each tap is held as a float and, for the float-float synthesis, the float
-// nearest its remainder: the remainder matters there because a level-j
-// lowpass carries numbers up to 2^j * 255, and the taps' single-precision
-// representation error (up to 2^-25 relative) times such numbers is
-// ~ulp(255) at the coarse levels.
-#define CVC_H4 0.037828455507
-#define CVC_H3 -0.023849465020
-#define CVC_H2 -0.110624404418
-#define CVC_H1 0.377402855613
-#define CVC_H0 0.852698679009
-#define CVC_G3 -0.064538882629
-#define CVC_G2 -0.040689417609
-#define CVC_G1 0.418092273222
-#define CVC_G0 0.788485616406
-#define CVC_LO(t) ((float)((t) - (double)(float)(t)))
-__constant__ float c_h[9] = {(float)CVC_H4, (float)CVC_H3, (float)CVC_H2, (float)CVC_H1, (float)CVC_H0,
-                             (float)CVC_H1, (float)CVC_H2, (float)CVC_H3, (float)CVC_H4};
-__constant__ float c_g[7] = {(float)CVC_G3, (float)CVC_G2, (float)CVC_G1, (float)CVC_G0,
-                             (float)CVC_G1, (float)CVC_G2, (float)CVC_G3};
-__constant__ float c_hl[9] = {CVC_LO(CVC_H4), CVC_LO(CVC_H3), CVC_LO(CVC_H2), CVC_LO(CVC_H1), CVC_LO(CVC_H0),
-                              CVC_LO(CVC_H1), CVC_LO(CVC_H2), CVC_LO(CVC_H3), CVC_LO(CVC_H4)};
-__constant__ float c_gl[7] = {CVC_LO(CVC_G3), CVC_LO(CVC_G2), CVC_LO(CVC_G1), CVC_LO(CVC_G0),
-                              CVC_LO(CVC_G1), CVC_LO(CVC_G2), CVC_LO(CVC_G3)};
-
-__device__ __forceinline__ int wrap_idx(int a, int n) {
-    if ((unsigned)a < (unsigned)n) return a;
-    int r = a % n;
-    return r < 0 ? r + n : r;
-}
-
-// 4-byte asynchronous global -> shared copies (all of a tile's staging in flight at once)
-__device__ __forceinline__ void lp_cp_async4(float* dst, const float* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void lp_cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// stage the MN x MN main tile at (ty0, tx0) (periodic) with row stride MNS: a warp per
-// row, lanes along it; a tile whose columns do not wrap takes no per-element index arithmetic
-template <int MN, int MNS = MN>
-__device__ __forceinline__ void lp_stage(float* s_main, const float* mainp, int mrs, int ty0, int tx0, int H, int W) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const bool inner = tx0 >= 0 && tx0 + MN <= W;
-    for (int r = warp; r < MN; r += nwarp) {
-        const float* row = mainp + (long long)wrap_idx(ty0 + r, H) * mrs;
-        float* dst = s_main + r * MNS;
-        if (inner) {
-            const float* src = row + tx0;
-            for (int c = lane; c < MN; c += 32) lp_cp_async4(dst + c, src + c);
-        } else {
-            for (int c = lane; c < MN; c += 32) lp_cp_async4(dst + c, row + wrap_idx(tx0 + c, W));
-        }
-    }
-}
-
-template <int RA>
-__device__ __forceinline__ float tap_a(int t) { return RA == 4 ? c_h[t + 4] : c_g[t + 3]; }
-template <int RS>
-__device__ __forceinline__ float tap_s(int t) { return RS == 3 ? c_g[t + 3] : c_h[t + 4]; }
-// the taps' low-order parts
-template <int RA>
-__device__ __forceinline__ float tapl_a(int t) { return RA == 4 ? c_hl[t + 4] : c_gl[t + 3]; }
-template <int RS>
-__device__ __forceinline__ float tapl_s(int t) { return RS == 3 ? c_gl[t + 3] : c_hl[t + 4]; }
 
 // single-precision analysis tile: cout = down(main, fa); out = main - up(cout, fs)
 template <int RA, int RS>
@@ -207,228 +138,14 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     }
 }
 
-// ------------------------------------------------- float-float helpers
-// (hi, lo) accumulators on two independent lanes at once (paired FP32
-// instructions); __fadd2_rn / __fmul2_rn keep the compiler from contracting
-// the error-free transformations into FMAs.
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ void ff2_add(float2& hi, float2& lo, float2 x) {
-    const float2 s = __fadd2_rn(hi, x);
-    const float2 bb = __fadd2_rn(s, neg2(hi));
-    const float2 e = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(x, neg2(bb)));
-    hi = s;
-    lo = __fadd2_rn(lo, e);
-}
-// (hi, lo) += (f + fl) * (xh + xl), dropping only fl * xl
-__device__ __forceinline__ void ff2_fma(float2& hi, float2& lo, float f, float fl, float2 xh, float2 xl) {
-    const float2 ff = make_float2(f, f);
-    const float2 p = __fmul2_rn(ff, xh);
-    const float2 pe = __ffma2_rn(ff, xh, neg2(p));
-    ff2_add(hi, lo, p);
-    lo = __ffma2_rn(ff, xl, __fadd2_rn(lo, pe));
-    lo = __ffma2_rn(make_float2(fl, fl), xh, lo);
-}
-// the same with a single-precision x
-__device__ __forceinline__ void ff2_fma1(float2& hi, float2& lo, float f, float fl, float2 x) {
-    const float2 ff = make_float2(f, f);
-    const float2 p = __fmul2_rn(ff, x);
-    const float2 pe = __ffma2_rn(ff, x, neg2(p));
-    ff2_add(hi, lo, p);
-    lo = __ffma2_rn(make_float2(fl, fl), x, __fadd2_rn(lo, pe));
-}
-
-// Tile with float-float intermediates (dynamic shared memory):
-//   synthesis (ANA = false): e = cin - down(main, fa);  out = main + up(e, fs)
-//   analysis  (ANA = true):  e = -down(main, fa), cout = -e (rounded);  out = main + up(e, fs)
-// so that the detail image of the analysis carries only its own rounding:
-// the lowpass it is computed from is not rounded first.
+// float-float tile kernel: one block per (job, tile); blocks of streams that take no part return
 template <int RA, int RS, bool ANA>
 __global__ void __launch_bounds__(256) k_lp_ff(const LpJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B) {
-    constexpr int T = LP_TILE;
-    constexpr int MLO = -(RS / 2);
-    constexpr int MHI = (T - 1 + RS) / 2;
-    constexpr int VN = MHI - MLO + 1;
-    constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
-    constexpr int Y0 = 2 * MLO - RA;
-    constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
-    // the main tile's rows have an even stride and the float-float arrays start on
-    // 16-byte boundaries, so that the passes below move pairs and quadruples
-    constexpr int MNS = MN + (MN & 1), OA = (MN * MNS + 3) & ~3, NA4 = (NA + 3) & ~3;
     extern __shared__ __align__(16) float sm[];
-    float* s_main = sm;                 // MN rows of MNS
-    float* s_ah = s_main + OA;          // NA
-    float* s_al = s_ah + NA4;           // NA
-    float* s_vh = s_al + NA4;           // VN * VN
-    float* s_vl = s_vh + VN * VN;       // VN * VN
-
-    const int jid = block_job[blockIdx.x];
-    const LpJob& J = jobs[jid];
+    const LpJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    const int tile = blockIdx.x - J.first_block;
-    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
-    const int y0 = ty * T, x0 = tx * T;
-    const int m0 = y0 / 2, n0 = x0 / 2;
-    const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
-    const float* mainp = base_ptr(B, J.main.b) + J.main.off;
-    const int mrs = J.main.rs;
-    lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
-    lp_cp_async_wait_all();
-    __syncthreads();
-    // Every pass computes two outputs per thread with paired instructions.
-    // decimating row pass, row pairs (ra, rb) (an odd last row pairs with itself), so that
-    // consecutive threads read consecutive columns as in a scalar pass
-    constexpr int NR = (MN + 1) / 2, NM = (VN + 1) / 2;
-    const float2 zero2 = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < NR * VN; i += blockDim.x) {
-        const int q = i / VN, n = i - q * VN;
-        const int ra = 2 * q, rb = min(2 * q + 1, MN - 1);
-        // the window x[2n + j], j = 0 .. 2 RA, of both rows (even offsets: RA pairs and one more)
-        const float* wa = s_main + ra * MNS + 2 * n;
-        const float* wb = s_main + rb * MNS + 2 * n;
-        float va[2 * RA + 1], vb[2 * RA + 1];
-#pragma unroll
-        for (int j = 0; j < RA; j++) {
-            const float2 pa = *reinterpret_cast<const float2*>(wa + 2 * j);
-            const float2 pb = *reinterpret_cast<const float2*>(wb + 2 * j);
-            va[2 * j] = pa.x; va[2 * j + 1] = pa.y;
-            vb[2 * j] = pb.x; vb[2 * j + 1] = pb.y;
-        }
-        va[2 * RA] = wa[2 * RA];
-        vb[2 * RA] = wb[2 * RA];
-        float2 hi = zero2, lo = zero2;
-#pragma unroll
-        for (int b = -RA; b <= RA; b++) ff2_fma1(hi, lo, tap_a<RA>(b), tapl_a<RA>(b), make_float2(va[RA - b], vb[RA - b]));
-        s_ah[ra * VN + n] = hi.x;
-        s_al[ra * VN + n] = lo.x;
-        if (rb != ra) {
-            s_ah[rb * VN + n] = hi.y;
-            s_al[rb * VN + n] = lo.y;
-        }
-    }
-    __syncthreads();
-    // decimating column pass over row pairs (ma, mb), then e = cin - down(main) (normalised float-float);
-    // the analysis takes e = -down(main) and writes the interior of down(main) as its lowpass output
-    const float* cinp = ANA ? nullptr : base_ptr(B, J.cin.b) + J.cin.off;
-    const float* cinlp = !ANA && J.cin_lo.b >= 0 ? base_ptr(B, J.cin_lo.b) + J.cin_lo.off : nullptr;
-    float* coutp = ANA ? base_ptr(B, J.cout.b) + J.cout.off : nullptr;
-    for (int i = threadIdx.x; i < NM * VN; i += blockDim.x) {
-        const int q = i / VN, n = i - q * VN;
-        const int ma = 2 * q, mb = min(2 * q + 1, VN - 1);
-        float2 hi = zero2, lo = zero2;
-#pragma unroll
-        for (int a = -RA; a <= RA; a++) {
-            const int ka = (2 * ma + RA - a) * VN + n, kb = (2 * mb + RA - a) * VN + n;
-            ff2_fma(hi, lo, tap_a<RA>(a), tapl_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
-        }
-        float2 eh, el;
-        if (ANA) {
-            eh = neg2(hi);
-            el = neg2(lo);
-        } else {
-            const int gn = wrap_idx(n0 + MLO + n, Wh);
-            const int gma = wrap_idx(m0 + MLO + ma, Hh), gmb = wrap_idx(m0 + MLO + mb, Hh);
-            eh = make_float2(cinp[(long long)gma * J.cin.rs + gn], cinp[(long long)gmb * J.cin.rs + gn]);
-            el = zero2;
-            if (cinlp)
-                el = make_float2(cinlp[(long long)gma * J.cin_lo.rs + gn], cinlp[(long long)gmb * J.cin_lo.rs + gn]);
-            ff2_add(eh, el, neg2(hi));
-            el = __fadd2_rn(el, neg2(lo));
-        }
-        const float2 sn = __fadd2_rn(eh, el);
-        el = __fadd2_rn(el, neg2(__fadd2_rn(sn, neg2(eh))));
-        eh = sn;
-        if (ANA) {
-            // this tile's share of the lowpass: half-resolution rows / columns [m0, m0 + T/2) x [n0, n0 + T/2)
-            const int gn = n0 + MLO + n;
-            if (n >= -MLO && n < -MLO + T / 2 && gn < Wh) {
-                const int ga = m0 + MLO + ma, gb = m0 + MLO + mb;
-                if (ma >= -MLO && ma < -MLO + T / 2 && ga < Hh) coutp[(long long)ga * J.cout.rs + gn] = -eh.x;
-                if (mb != ma && mb >= -MLO && mb < -MLO + T / 2 && gb < Hh) coutp[(long long)gb * J.cout.rs + gn] = -eh.y;
-            }
-        }
-        s_vh[ma * VN + n] = eh.x;
-        s_vl[ma * VN + n] = el.x;
-        if (mb != ma) {
-            s_vh[mb * VN + n] = eh.y;
-            s_vl[mb * VN + n] = el.y;
-        }
-    }
-    __syncthreads();
-    // expanding row pass: output pairs x = 2p, 2p + 1 for p = 2w and 2w + 1
-    for (int i = threadIdx.x; i < VN * (T / 4); i += blockDim.x) {
-        const int m = i / (T / 4), w = i - m * (T / 4);
-        const int kb = m * VN + 2 * w - MLO;
-        float2 eh = zero2, el = zero2, oh = zero2, ol = zero2;
-#pragma unroll
-        for (int t = -RS; t <= RS; t++) {
-            if ((t & 1) == 0) {
-                const int k = kb - t / 2;
-                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
-                        make_float2(s_vl[k], s_vl[k + 1]));
-            } else {
-                const int k = kb + (1 - t) / 2;
-                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
-                        make_float2(s_vl[k], s_vl[k + 1]));
-            }
-        }
-        *reinterpret_cast<float4*>(s_ah + m * T + 4 * w) = make_float4(eh.x, oh.x, eh.y, oh.y);
-        *reinterpret_cast<float4*>(s_al + m * T + 4 * w) = make_float4(el.x, ol.x, el.y, ol.y);
-    }
-    __syncthreads();
-    // expanding column pass: output rows 2p, 2p + 1 for the column pair (2w, 2w + 1), plus the main input;
-    // a coarse level's output (the next level's lowpass) keeps its low-order part as well
-    float* outp = base_ptr(B, J.out.b) + J.out.off;
-    float* outlp = J.out_lo.b >= 0 ? base_ptr(B, J.out_lo.b) + J.out_lo.off : nullptr;
-    for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
-        const int p = i / (T / 2), w = i - p * (T / 2);
-        const int x = 2 * w;
-        const int kb = (p - MLO) * T + x;
-        float2 eh = zero2, el = zero2, oh = zero2, ol = zero2;
-#pragma unroll
-        for (int t = -RS; t <= RS; t++) {
-            if ((t & 1) == 0) {
-                const int k = kb - (t / 2) * T;
-                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
-                        *reinterpret_cast<const float2*>(s_al + k));
-            } else {
-                const int k = kb + ((1 - t) / 2) * T;
-                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
-                        *reinterpret_cast<const float2*>(s_al + k));
-            }
-        }
-        const int gx = x0 + x;
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int y = 2 * p + h, gy = y0 + y;
-            if (gy >= H) continue;
-            float2 hi = h ? oh : eh, lo = h ? ol : el;
-            const float* mrow = s_main + (y - Y0) * MNS + (x - Y0);
-            ff2_add(hi, lo, make_float2(mrow[0], mrow[1]));
-            const float2 o = __fadd2_rn(hi, lo);
-            float* orow = outp + (long long)gy * J.out.rs;
-            if (gx < W) orow[gx] = o.x;
-            if (gx + 1 < W) orow[gx + 1] = o.y;
-            if (outlp) {
-                const float2 ol2 = __fadd2_rn(lo, neg2(__fadd2_rn(o, neg2(hi))));   // exact: |lo| <= ulp(hi)
-                float* lrow = outlp + (long long)gy * J.out_lo.rs;
-                if (gx < W) lrow[gx] = ol2.x;
-                if (gx + 1 < W) lrow[gx + 1] = ol2.y;
-            }
-        }
-    }
-}
-
-template <int RA, int RS>
-constexpr size_t ff_smem() {
-    constexpr int T = LP_TILE;
-    constexpr int MLO = -(RS / 2);
-    constexpr int MHI = (T - 1 + RS) / 2;
-    constexpr int VN = MHI - MLO + 1;
-    constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
-    constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
-    constexpr int MNS = MN + (MN & 1), OA = (MN * MNS + 3) & ~3, NA4 = (NA + 3) & ~3;
-    return sizeof(float) * (size_t)(OA + 2 * NA4 + 2 * VN * VN);
+    lp_ff_tile<RA, RS, ANA>(J, blockIdx.x - J.first_block, B, sm);
 }
 
 cudaError_t lp_prepare() {

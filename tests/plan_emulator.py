@@ -89,11 +89,50 @@ def _parse(raw):
         kind, nj = np.frombuffer(raw[pos:pos + 8], "<u4")
         pos += 8
         extra = None
+        if kind == 3:
+            launches.append((3, _parse_tail(raw[pos:pos + nj]), None))
+            pos += nj
+            continue
         dt = (LPJOB, AJOB, BJOB)[kind]
         jobs = np.frombuffer(raw[pos:pos + nj * dt.itemsize], dt)
         pos += nj * dt.itemsize
         launches.append((int(kind), jobs, extra))
     return elems, launches, raw[pos:]
+
+
+def _parse_tail(blob):
+    """a pyramid-tail launch: [(resident floats, stream, [(kind, job record), ...]) per plane]"""
+    nplanes, _ntaps = np.frombuffer(blob[:8], "<u4")
+    pos, planes = 8, []
+    for _ in range(nplanes):
+        ws, stream, nsteps, _ = np.frombuffer(blob[pos:pos + 16], "<i4")
+        pos += 16
+        steps = []
+        for _ in range(nsteps):
+            kind = int(np.frombuffer(blob[pos:pos + 4], "<u4")[0])
+            pos += 8
+            dt = (LPJOB, AJOB, BJOB)[kind]
+            steps.append((kind, np.frombuffer(blob[pos:pos + dt.itemsize], dt)))
+            pos += dt.itemsize
+        planes.append((int(ws), int(stream), steps))
+    assert pos == len(blob)
+    return planes
+
+
+def _flatten(elems, launches):
+    """the launches with every tail expanded into one-job launches, each with the bounds it runs
+    under: (kind, jobs, extra, elems), where base 4 (B_SMEM) is the plane's resident workspace,
+    and a fresh workspace marker before each tail plane"""
+    base = list(elems) + [0]
+    for kind, jobs, extra in launches:
+        if kind != 3:
+            yield kind, jobs, extra, base
+            continue
+        for ws, _stream, steps in jobs:
+            e = list(elems) + [ws]
+            yield "smem", ws, None, e
+            for k, J in steps:
+                yield k, J, None, e
 
 
 def _fan_taps(n):
@@ -194,7 +233,10 @@ def run(mode, elems, launches, bufs):
     fa, fs = (h, g) if mode in (0, 1) else (g, h)
     synth = mode in (1, 2)
     fo, a1, g1, a2, g2 = PASSES[mode]
-    for kind, jobs, extra in launches:
+    for kind, jobs, extra, elems in _flatten(elems, launches):
+        if kind == "smem":
+            bufs[4] = np.full(jobs, np.nan)     # a tail plane's resident workspace, never read before written
+            continue
         results, wjob, rjob = [], [], []
         for ji, J in enumerate(jobs):
             reads, writes = _views_of(kind, J, synth, extra)
@@ -277,7 +319,9 @@ def run(mode, elems, launches, bufs):
 def check_only(elems, launches, mode):
     """Bounds of every job of every launch, without executing (for full-size plans)."""
     synth = mode in (1, 2)
-    for kind, jobs, extra in launches:
+    for kind, jobs, extra, elems in _flatten(elems, launches):
+        if kind == "smem":
+            continue
         for J in jobs:
             reads, writes = _views_of(kind, J, synth, extra)
             for name, v, rr, cc in reads + writes:

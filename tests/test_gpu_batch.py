@@ -107,14 +107,20 @@ def test_encode_and_decode_steps_with_idle_streams():
             assert torch.equal(outs[i], dec_plain[i].decode(ins[i]))
 
 
-def test_launch_shapes_and_graph_replay_change_nothing():
+def test_launch_shapes_fusion_depths_and_graph_replay_change_nothing():
+    """Launch shapes, graph replay and the pyramid tail's fusion depth (0: every level its own
+    launches, the default; 1, 2: tails of at most that many levels; 6: as many levels as fit)
+    give bit-identical bitstreams and reconstructions: a tail runs the same tile computations."""
     streams = _streams(1)
     frames = _inputs(1, 3)
     ref = None
-    for graphs, rows, tok in [(True, 8, 1184), (False, 8, 1184), (True, 1, 1), (True, 32, 65535), (True, 3, 7)]:
+    for graphs, rows, tok, fuse in [(True, 8, 1184, 0), (False, 8, 1184, 0), (True, 1, 1, 0), (True, 32, 65535, 0),
+                                    (True, 3, 7, 0), (True, 8, 1184, 6), (False, 8, 1184, 6), (True, 8, 1184, 1),
+                                    (True, 8, 1184, 2)]:
         b = Batch(streams)
         b.set_graphs(graphs)
         b.set_shape(rows, tok)
+        b.set_fusion(fuse)
         outs = _rgb_buffers(streams)
         got = []
         for t in range(3):
@@ -125,7 +131,7 @@ def test_launch_shapes_and_graph_replay_change_nothing():
             continue
         for a, c in zip(ref, got):
             for x, y in zip(a, c):
-                assert torch.equal(x, y), (graphs, rows, tok)
+                assert torch.equal(x, y), (graphs, rows, tok, fuse)
 
 
 def test_autotune_keeps_state_and_output():
@@ -134,8 +140,8 @@ def test_autotune_keeps_state_and_output():
     b = Batch(streams)
     plain = [Codec(**s) for s in streams]
     outs = _rgb_buffers(streams)
-    rows, tok = b.autotune(3, rgb=[f[0] for f in frames], rgb_out=outs, reps=2)
-    assert 1 <= rows <= 32 and 1 <= tok <= 65535
+    rows, tok, fuse = b.autotune(3, rgb=[f[0] for f in frames], rgb_out=outs, reps=2)
+    assert 1 <= rows <= 32 and 1 <= tok <= 65535 and fuse in (0, 1, 2, 6)
     for t in range(3):
         res = b.step(3, rgb=[f[t] for f in frames], rgb_out=outs)
         for i, c in enumerate(plain):

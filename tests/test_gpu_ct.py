@@ -130,3 +130,18 @@ def test_constant_plane_has_zero_details():
     nlow = (H >> L) * (W >> L)
     np.testing.assert_allclose(c[:nlow], 99.0 * 2 ** L, atol=1e-3)
     assert np.abs(c[nlow:]).max() < 1e-3
+
+
+@pytest.mark.parametrize("H,W,L,k", [(144, 176, 3, [3, 2, 2]), (72, 88, 3, [3, 2, 2]), (1088, 1920, 5, [5, 4, 4, 3, 3])])
+def test_pyramid_tail_gives_the_same_bits(H, W, L, k):
+    """With its coarse levels in one block per plane (the pyramid tail, as many levels as fit in
+    shared memory: QCIF luma levels 2-3, a whole QCIF chroma plane, 1080p luma level 5), the
+    transform and its inverse give exactly the bits of the per-level launches."""
+    x = _planes(2, H, W, seed=7)
+    xt = torch.from_numpy(x).cuda()
+    ref = CtPlan(H, W, L, k, batch=2)
+    fused = CtPlan(H, W, L, k, batch=2)
+    fused.set_fusion(6)
+    c0, c1 = ref.forward(xt), fused.forward(xt)
+    assert torch.equal(c0, c1)
+    assert torch.equal(ref.inverse(c0), fused.inverse(c1))

@@ -22,7 +22,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 
-HOT = ("k_dfb_a", "k_dfb_b", "k_lp_level", "k_lp_ff", "k_scan_reduce", "k_scan_sums", "k_scan_apply",
+HOT = ("k_dfb_a", "k_dfb_b", "k_lp_level", "k_lp_ff", "k_pyr_tail", "k_scan_reduce", "k_scan_sums", "k_scan_apply",
        "k_quant_b", "k_unquant_b", "k_colour_fwd_b", "k_colour_inv_b", "k_rle_count_b", "k_rle_write_b")
 
 
@@ -58,7 +58,7 @@ def _hot(mangled):
 
 
 @pytest.mark.skipif(not os.path.exists(NVCC), reason="nvcc not available")
-@pytest.mark.parametrize("src", ["k_dfb.cu", "k_lp.cu", "k_codec.cu"])
+@pytest.mark.parametrize("src", ["k_dfb.cu", "k_lp.cu", "k_codec.cu", "k_tail.cu"])
 def test_hot_kernels_have_no_stack_frame(src):
     res = _ptxas(src)
     seen = [k for k in res if _hot(k)]

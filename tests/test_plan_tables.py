@@ -19,9 +19,12 @@ def _buffers(elems):
 
 
 @pytest.mark.parametrize("H,W,Lv,k,batch", PLANS)
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])
-def test_plan_tables_compute_the_transform(H, W, Lv, k, batch, mode):
-    elems, launches = E.tables(mode, h=H, w=W, levels=Lv, dirs=k, batch=batch)
+@pytest.mark.parametrize("mode,fuse", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 6), (1, 6), (0, 1), (1, 2)])
+def test_plan_tables_compute_the_transform(H, W, Lv, k, batch, mode, fuse):
+    """fuse: the pyramid tail's fusion depth (the forward and inverse run their coarse levels
+    in one block per plane, the images resident in a per-plane scratch buffer)"""
+    elems, launches = E.tables(mode | (fuse << 8), h=H, w=W, levels=Lv, dirs=k, batch=batch)
+    assert (fuse > 0) == any(kind == 3 for kind, _, _ in launches)
     n = O.layout(H, W, Lv, k)["total"]
     assert elems[0] == batch * H * W and elems[1] == batch * n and elems[3] == batch * H * W
     rng = np.random.default_rng(mode)
@@ -42,10 +45,11 @@ def test_plan_tables_compute_the_transform(H, W, Lv, k, batch, mode):
         assert np.abs(got - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("fuse", [0, 6])
 @pytest.mark.parametrize("w,h,Lv,k", [(176, 144, 3, [3, 2, 2]), (99, 77, 2, [2, 2]), (64, 48, 2, [1, 0])])
-def test_codec_plan_tables(w, h, Lv, k):
+def test_codec_plan_tables(w, h, Lv, k, fuse):
     prm = L.Params(w, h, Lv, L.ints(k), 8, 1, 0.0, 8, 1)
-    elems, launches = E.tables(0, params=prm)
+    elems, launches = E.tables(0 | (fuse << 8), params=prm)
     oc = O.Codec(w, h, Lv, k, 8, 1, 0.0, 8)
     rng = np.random.default_rng(1)
     frame = rng.integers(0, 256, (h, w, 3), dtype=np.uint8)
@@ -56,7 +60,7 @@ def test_codec_plan_tables(w, h, Lv, k):
     ref = np.concatenate([O.ct(0, p, p.shape[0], p.shape[1], Lv, k) for p in (yp, cop, cgp)])
     assert np.abs(bufs[1] - ref).max() < 1e-7
     # and the inverse tables invert it
-    elems, launches = E.tables(1, params=prm)
+    elems, launches = E.tables(1 | (fuse << 8), params=prm)
     E.run(1, elems, launches, bufs)
     assert np.abs(bufs[3] - bufs[0]).max() < 1e-8
 
@@ -64,9 +68,9 @@ def test_codec_plan_tables(w, h, Lv, k):
 def test_benchmark_codec_plan_is_in_bounds():
     """The 1080p configuration: bounds and hazards of every forward and inverse job."""
     prm = L.Params(1920, 1080, 5, L.ints([5, 4, 4, 3, 3]), 8, 1, 0.0, 10, 1)
-    for mode in (0, 1):
+    for mode in (0, 1, 0 | 6 << 8, 1 | 6 << 8):
         elems, launches = E.tables(mode, params=prm)
-        E.check_only(elems, launches, mode)
+        E.check_only(elems, launches, mode & 255)
 
 
 MIXED = [(99, 77, 2, [2, 2]), (64, 48, 3, [3, 2, 2]), (40, 30, 1, [0]), (96, 64, 2, [1, 0])]
