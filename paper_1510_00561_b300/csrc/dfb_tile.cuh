@@ -36,9 +36,12 @@
 
 namespace cvc {
 
+// a mod n in [0, n); indices at most one period outside take no division
 __device__ __forceinline__ int wrapd(int a, int n) {
     if ((unsigned)a < (unsigned)n) return a;
-    int r = a % n;
+    const int b = a < 0 ? a + n : a - n;
+    if ((unsigned)b < (unsigned)n) return b;
+    const int r = a % n;
     return r < 0 ? r + n : r;
 }
 
@@ -251,9 +254,11 @@ template <bool SYN, int NT>
 __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bases& B, const PassParams& pp,
                                            float* smem_a) {
     using G = AGeo<NT>;
-    constexpr int SA = G::SA, PA = G::PA, PAS = G::PAS, HALO = G::HALO;
+    constexpr int SA = G::SA, PA = G::PA, PAS = G::PAS, HALO = G::HALO, PL = PA * PAS;
+    static_assert(HALO % 4 == 0 && DFBA_TILE % 4 == 0, "a tile's halo starts on a 16-byte column boundary");
+    static_assert(SA / 4 <= 32 && PA / 2 <= 32 && DFBA_TILE / 2 == 32, "one lane per vector of a row");
     float* planes = smem_a;
-    float* tmp = smem_a + 4 * PA * PAS;
+    float* tmp = smem_a + 4 * PL;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * DFBA_TILE, x0 = tx * DFBA_TILE;
     const int H = J.H, W = J.W, H2 = H / 2, W2 = W / 2;
@@ -268,35 +273,100 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
             // a tail kernel's resident detail image: plain copies
             for (int r = warp; r < SA; r += 8) {
                 const float* row = Dp + (long long)wrapd(y0 - HALO + r, H) * J.D.rs;
-                float* pr = planes + 2 * (r & 1) * PA * PAS + (r >> 1) * PAS;
-                for (int c = lane; c < SA; c += 32) pr[(c & 1) * PA * PAS + (c >> 1)] = row[wrapd(x0 - HALO + c, W)];
+                float* pr = planes + 2 * (r & 1) * PL + (r >> 1) * PAS;
+                for (int c = lane; c < SA; c += 32) pr[(c & 1) * PL + (c >> 1)] = row[wrapd(x0 - HALO + c, W)];
             }
-        } else
-        for (int r = warp; r < SA; r += 8) {
-            const float* row = Dp + (long long)wrapd(y0 - HALO + r, H) * J.D.rs;
-            // image column c of the tile -> plane (r & 1, c & 1), plane column c >> 1
-            const unsigned sb = smem_addr(planes + 2 * (r & 1) * PA * PAS + (r >> 1) * PAS);
-            for (int c = lane; c < SA; c += 32) {
-                const int x = inner ? x0 - HALO + c : wrapd(x0 - HALO + c, W);
-                cp_async4s(sb + 4u * ((c & 1) * PA * PAS + (c >> 1)), row + x);
+        } else if (inner && (reinterpret_cast<uintptr_t>(Dp) & 15) == 0 && (J.D.rs & 3) == 0) {
+            // 16-byte loads: lane k < SA/4 takes image columns 4k .. 4k+3 of a row, i.e. plane
+            // columns 2k, 2k+1 of the row's two planes; a warp has half of its rows in flight at once
+            constexpr int RPW = (SA + 7) / 8, NB = (RPW + 1) / 2;
+            const float* base = Dp + (x0 - HALO) + 4 * lane;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                float4 v[NB];
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    const int r = warp + 8 * (h * NB + b);
+                    if (r < SA && lane < SA / 4)
+                        v[b] = *reinterpret_cast<const float4*>(base + (long long)wrapd(y0 - HALO + r, H) * J.D.rs);
+                }
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    const int r = warp + 8 * (h * NB + b);
+                    if (r < SA && lane < SA / 4) {
+                        float* p = planes + 2 * (r & 1) * PL + (r >> 1) * PAS + 2 * lane;
+                        p[0] = v[b].x;
+                        p[PL] = v[b].y;
+                        p[1] = v[b].z;
+                        p[PL + 1] = v[b].w;
+                    }
+                }
+            }
+        } else {
+            for (int r = warp; r < SA; r += 8) {
+                const float* row = Dp + (long long)wrapd(y0 - HALO + r, H) * J.D.rs;
+                // image column c of the tile -> plane (r & 1, c & 1), plane column c >> 1
+                const unsigned sb = smem_addr(planes + 2 * (r & 1) * PL + (r >> 1) * PAS);
+                for (int c = lane; c < SA; c += 32) {
+                    const int x = inner ? x0 - HALO + c : wrapd(x0 - HALO + c, W);
+                    cp_async4s(sb + 4u * ((c & 1) * PL + (c >> 1)), row + x);
+                }
             }
         }
     } else {
+        const bool inner = cu0 >= 0 && cu0 + PA <= H2 && cv0 >= 0 && cv0 + PA <= W2;   // no wrap in this tile
+        constexpr int RPW = (PA + 7) / 8;
         for (int q = 0; q < 4; q++) {
             const View& V = J.comp[q];
             const float* P = base_ptr(B, V.b) + V.off;
+            float* pl = planes + q * PL;
+            const bool al8 = (reinterpret_cast<uintptr_t>(P) & 7) == 0;
             if (__isShared(P)) {
                 // a tail kernel's resident channel array: plain copies
                 for (int u = warp; u < PA; u += 8)
                     for (int v = lane; v < PA; v += 32)
-                        planes[q * PA * PAS + u * PAS + v] =
-                            P[(long long)wrapd(cu0 + u, H2) * V.rs + (long long)wrapd(cv0 + v, W2) * V.cs];
+                        pl[u * PAS + v] = P[(long long)wrapd(cu0 + u, H2) * V.rs + (long long)wrapd(cv0 + v, W2) * V.cs];
+            } else if (V.cs == 1 && inner && al8 && (V.rs & 1) == 0) {
+                // row-major channel, 8-byte loads: lane k < PA/2 takes plane columns 2k, 2k+1 of
+                // plane row u = warp + 8b (cv0 is even)
+                const float* base = P + (long long)cu0 * V.rs + cv0 + 2 * lane;
+                float2 v[RPW];
+#pragma unroll
+                for (int b = 0; b < RPW; b++) {
+                    const int u = warp + 8 * b;
+                    if (u < PA && lane < PA / 2) v[b] = *reinterpret_cast<const float2*>(base + (long long)u * V.rs);
+                }
+#pragma unroll
+                for (int b = 0; b < RPW; b++) {
+                    const int u = warp + 8 * b;
+                    if (u < PA && lane < PA / 2) {
+                        pl[u * PAS + 2 * lane] = v[b].x;
+                        pl[u * PAS + 2 * lane + 1] = v[b].y;
+                    }
+                }
+            } else if (V.rs == 1 && inner && al8 && (V.cs & 1) == 0) {
+                // transposed channel (contiguous along u), 8-byte loads: lane k < PA/2 takes plane
+                // rows 2k, 2k+1 of plane column v = warp + 8b (cu0 is even)
+                const float* base = P + cu0 + 2 * lane + (long long)cv0 * V.cs;
+                float2 w[RPW];
+#pragma unroll
+                for (int b = 0; b < RPW; b++) {
+                    const int v = warp + 8 * b;
+                    if (v < PA && lane < PA / 2) w[b] = *reinterpret_cast<const float2*>(base + (long long)v * V.cs);
+                }
+#pragma unroll
+                for (int b = 0; b < RPW; b++) {
+                    const int v = warp + 8 * b;
+                    if (v < PA && lane < PA / 2) {
+                        pl[2 * lane * PAS + v] = w[b].x;
+                        pl[(2 * lane + 1) * PAS + v] = w[b].y;
+                    }
+                }
             } else if (V.cs == 1) {
                 // row-major channel: plane row u is a run of array row cu
-                const bool inner = cv0 >= 0 && cv0 + PA <= W2;
                 for (int u = warp; u < PA; u += 8) {
                     const float* row = P + (long long)wrapd(cu0 + u, H2) * V.rs;
-                    const unsigned sb = smem_addr(planes + q * PA * PAS + u * PAS);
+                    const unsigned sb = smem_addr(pl + u * PAS);
                     for (int v = lane; v < PA; v += 32)
                         cp_async4s(sb + 4u * v, row + (inner ? cv0 + v : wrapd(cv0 + v, W2)));
                 }
@@ -305,7 +375,7 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
                 for (int v = warp; v < PA; v += 8) {
                     const float* col = P + (long long)wrapd(cv0 + v, W2) * V.cs;
                     for (int u = lane; u < PA; u += 32)
-                        cp_async4s(smem_addr(planes + q * PA * PAS + u * PAS + v), col + wrapd(cu0 + u, H2) * V.rs);
+                        cp_async4s(smem_addr(pl + u * PAS + v), col + wrapd(cu0 + u, H2) * V.rs);
                 }
             }
         }
@@ -317,34 +387,42 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
     // store the 64 x 64 tile: plane-local rows / columns [HALO/2, HALO/2 + 32)
     constexpr int T2 = DFBA_TILE / 2, H6 = HALO / 2;
     if (!SYN) {
+        const int cub = y0 / 2, cvb = x0 / 2;
         for (int q = 0; q < 4; q++) {
             const View& V = J.comp[q];
             float* P = base_ptr(B, V.b) + V.off;
-            const bool trans = V.cs != 1;
-            for (int k = threadIdx.x; k < T2 * T2; k += blockDim.x) {
-                int a = k / T2, b = k - a * T2;
-                int u = trans ? b : a, v = trans ? a : b;
-                int cu = y0 / 2 + u, cv = x0 / 2 + v;
-                if (cu < H2 && cv < W2)
-                    P[(long long)cu * V.rs + (long long)cv * V.cs] = planes[q * PA * PAS + (H6 + u) * PAS + H6 + v];
+            const float* pl = planes + q * PL + H6 * PAS + H6;
+            if (V.cs == 1) {
+                // lane = plane column: each warp store is a run of one array row
+                const int cv = cvb + lane;
+                for (int u = warp; u < T2; u += 8) {
+                    const int cu = cub + u;
+                    if (cu < H2 && cv < W2) P[(long long)cu * V.rs + cv] = pl[u * PAS + lane];
+                }
+            } else {
+                // transposed: lane = plane row, a run along the array's contiguous axis
+                const int cu = cub + lane;
+                for (int v = warp; v < T2; v += 8) {
+                    const int cv = cvb + v;
+                    if (cu < H2 && cv < W2) P[(long long)cu * V.rs + (long long)cv * V.cs] = pl[lane * PAS + v];
+                }
             }
         }
     } else {
         float* Do = base_ptr(B, J.D.b) + J.D.off;
         static_assert(HALO % 2 == 0 && DFBA_TILE % 2 == 0, "column pairs start on even plane columns");
         if ((reinterpret_cast<uintptr_t>(Do) & 7) == 0 && (J.D.rs & 1) == 0) {
-            // column pairs (c, c + 1), c even: the same column of the two planes of row parity rr & 1,
-            // one 8-byte store per pair
-            constexpr int HP = DFBA_TILE / 2;
-            for (int k = threadIdx.x; k < DFBA_TILE * HP; k += blockDim.x) {
-                const int r = k / HP, c = 2 * (k - r * HP);
-                const int y = y0 + r, x = x0 + c;
-                if (y >= H || x >= W) continue;
-                const int rr = HALO + r, cc = HALO + c;
-                const float* pl = planes + 2 * (rr & 1) * PA * PAS + (rr >> 1) * PAS + (cc >> 1);
+            // image row r per warp step, lane k = column pair (2k, 2k + 1): plane column
+            // HALO/2 + k of the two planes of row parity (HALO + r) & 1, one 8-byte store
+            const int x = x0 + 2 * lane;
+            for (int r = warp; r < DFBA_TILE; r += 8) {
+                const int y = y0 + r;
+                if (y >= H) break;
+                const int rr = HALO + r;
+                const float* p = planes + 2 * (rr & 1) * PL + (rr >> 1) * PAS + H6 + lane;
                 float* dst = Do + (long long)y * J.D.rs + x;
-                if (x + 1 < W) *reinterpret_cast<float2*>(dst) = make_float2(pl[0], pl[PA * PAS]);
-                else dst[0] = pl[0];
+                if (x + 1 < W) *reinterpret_cast<float2*>(dst) = make_float2(p[0], p[PL]);
+                else if (x < W) dst[0] = p[0];
             }
         } else {
             for (int k = threadIdx.x; k < DFBA_TILE * DFBA_TILE; k += blockDim.x) {
@@ -352,7 +430,7 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
                 int y = y0 + r, x = x0 + c;
                 if (y < H && x < W) {
                     int rr = HALO + r, cc = HALO + c;
-                    Do[(long long)y * J.D.rs + x] = planes[(2 * (rr & 1) + (cc & 1)) * PA * PAS + (rr >> 1) * PAS + (cc >> 1)];
+                    Do[(long long)y * J.D.rs + x] = planes[(2 * (rr & 1) + (cc & 1)) * PL + (rr >> 1) * PAS + (cc >> 1)];
                 }
             }
         }
@@ -450,7 +528,8 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;
     const int R2 = J.R2, C = J.C, i = J.i;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    constexpr int NW = NPAIR * NCHUNK / 32;   // warps of the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fo = pp.first_odd;
     // the first-updated coset (odd if fo) sits one float to the right
     float* const arrE = sE + (fo ? 0 : 1);
@@ -458,43 +537,74 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     // inputs: analysis reads the parent's cosets, synthesis the children.
     // Smem row r <-> coset row t0 - R + r; smem column x <-> sheared column c0 - 2R + x,
     // i.e. array column (c0 - 2R + x - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
-    for (int par = 0; par < 2; par++) {
-        const View V = par ? (SYN ? J.c1 : J.po) : (SYN ? J.c0 : J.pe);
-        const float* P = base_ptr(B, V.b) + V.off;
-        float* S = par ? arrO : arrE;
-        if (__isShared(P)) {
-            // a tail kernel's resident channel array: plain copies of the sheared rows
-            for (int r = warp; r < RB; r += nwarp) {
-                const int tu = t0 - R + r;
-                const float* row = P + (long long)wrapd(tu, R2) * V.rs;
-                const int vs = c0 - 2 * R - i * (2 * tu + par);
-                for (int x = lane; x < CB; x += 32) S[r * CBS + x] = row[(long long)wrapd(vs + x, C) * V.cs];
+    const View V0 = SYN ? J.c0 : J.pe, V1 = SYN ? J.c1 : J.po;
+    const float* const P0 = base_ptr(B, V0.b) + V0.off;
+    const float* const P1 = base_ptr(B, V1.b) + V1.off;
+    if (!__isShared(P0) && !__isShared(P1) && V0.cs == 1 && V1.cs == 1) {
+        // row-major arrays.  Warp w stages rows w, w + NW, ... of both parities; lane
+        // 2k + p first places row w + NW k of parity p (array row and sheared start
+        // column, one modular reduction for all of them), then the warp copies the rows
+        // one by one, taking each row's placement from its lane.
+        constexpr int RPW = (RB + NW - 1) / NW;
+        static_assert(2 * RPW <= 32, "one lane per (row, parity) of a warp");
+        const int lp = lane & 1, tl = t0 - R + warp + NW * (lane >> 1);
+        const int vl = wrapd(c0 - 2 * R - i * (2 * tl + lp), C);
+        const float* rl = (lp ? P1 : P0) + (long long)wrapd(tl, R2) * (lp ? V1.rs : V0.rs);
+#pragma unroll
+        for (int k = 0; k < 2 * RPW; k++) {
+            const int r = warp + NW * (k >> 1);
+            if (r >= RB) break;
+            const float* row = reinterpret_cast<const float*>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rl), k));
+            const int vs = __shfl_sync(0xffffffffu, vl, k);
+            const unsigned sb = smem_addr(((k & 1) ? arrO : arrE) + r * CBS);
+            if (vs + CB <= C) {                  // the sheared window does not wrap: no per-element checks
+                const float* src = row + vs;
+#pragma unroll
+                for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
+            } else {
+#pragma unroll
+                for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
             }
-        } else if (V.cs == 1) {
-            for (int r = warp; r < RB; r += nwarp) {
-                const int tu = t0 - R + r;
-                const float* row = P + (long long)wrapd(tu, R2) * V.rs;
-                const int vs = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
-                const unsigned sb = smem_addr(S + r * CBS);
-                if (vs + CB <= C) {                  // the sheared window does not wrap: no per-element checks
-                    const float* src = row + vs;
-                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
-                } else {
+        }
+    } else {
+        for (int par = 0; par < 2; par++) {
+            const View V = par ? V1 : V0;
+            const float* P = par ? P1 : P0;
+            float* S = par ? arrO : arrE;
+            if (__isShared(P)) {
+                // a tail kernel's resident channel array: plain copies of the sheared rows
+                for (int r = warp; r < RB; r += NW) {
+                    const int tu = t0 - R + r;
+                    const float* row = P + (long long)wrapd(tu, R2) * V.rs;
+                    const int vs = c0 - 2 * R - i * (2 * tu + par);
+                    for (int x = lane; x < CB; x += 32) S[r * CBS + x] = row[(long long)wrapd(vs + x, C) * V.cs];
+                }
+            } else if (V.cs == 1) {
+                for (int r = warp; r < RB; r += NW) {
+                    const int tu = t0 - R + r;
+                    const float* row = P + (long long)wrapd(tu, R2) * V.rs;
+                    const int vs = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
+                    const unsigned sb = smem_addr(S + r * CBS);
                     for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
                 }
-            }
-        } else {
-            // transposed array (rows contiguous in memory along t): walk the sheared
-            // tile along memory order; for offset w every row r shares the array
-            // column v, at tile column x = w + 2*i*r
-            const int wlo = i > 0 ? -2 * i * (RB - 1) : 0, whi = CB + (i < 0 ? -2 * i * (RB - 1) : 0);
-            const int vbase = c0 - 2 * R - i * (2 * (t0 - R) + par);
-            for (int k = threadIdx.x; k < (whi - wlo) * RB; k += blockDim.x) {
-                const int w = wlo + k / RB, r = k - (k / RB) * RB;
-                const int x = w + 2 * i * r;
-                if (x < 0 || x >= CB) continue;
-                const int v = wrapd(vbase + w, C);
-                cp_async4(&S[r * CBS + x], P + (long long)wrapd(t0 - R + r, R2) * V.rs + (long long)v * V.cs);
+            } else {
+                // transposed array (contiguous along the rows t): lane r < RB takes smem row
+                // r, and at step j tile column x = (j + 2 i r) mod CB, whose array column
+                // (c0 - 2R - i (2 tu + par) + x) mod C is the same for all rows until x wraps,
+                // so a warp reads a run of consecutive t
+                static_assert(RB <= 32 && (CB & (CB - 1)) == 0, "one lane per tile row; CB a power of two");
+                const int tu = t0 - R + lane;
+                const int vr = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
+                const int sh = (2 * i * lane) & (CB - 1);
+                const float* rowp = P + (long long)wrapd(tu, R2) * V.rs;
+                const unsigned sb = smem_addr(S + lane * CBS);
+                if (lane < RB) {
+                    for (int j = warp; j < CB; j += NW) {
+                        const int x = (j + sh) & (CB - 1);
+                        cp_async4s(sb + 4u * x, rowp + (long long)wrap_fast<CB>(vr + x, C) * V.cs);
+                    }
+                }
             }
         }
     }
@@ -528,36 +638,67 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     __syncthreads();
     // outputs: analysis writes the children, synthesis the parent's cosets
     const int ncol = min(COLS, C - c0);
-    for (int par = 0; par < 2; par++) {
-        const View V = par ? (SYN ? J.po : J.c1) : (SYN ? J.pe : J.c0);
-        float* P = base_ptr(B, V.b) + V.off;
-        const float* S = par ? arrO : arrE;
-        if (V.cs == 1) {
-            for (int rr = warp; rr < DFBB_ROWS; rr += nwarp) {
-                const int t = t0 + rr;
-                if (t >= R2) break;
-                float* row = P + (long long)t * V.rs;
-                const int vs = wrapd(c0 - i * (2 * t + par), C);
-                const float* srow = S + (R + rr) * CBS + 2 * R;
-                if (vs + ncol <= C) {
-                    float* dst = row + vs;
-                    for (int xx = lane; xx < ncol; xx += 32) dst[xx] = srow[xx];
-                } else {
+    const View W0 = SYN ? J.pe : J.c0, W1 = SYN ? J.po : J.c1;
+    float* const Q0 = base_ptr(B, W0.b) + W0.off;
+    float* const Q1 = base_ptr(B, W1.b) + W1.off;
+    if (W0.cs == 1 && W1.cs == 1) {
+        // row-major arrays: warp w writes rows w, w + NW of both parities, placed by
+        // lanes 0..3 as in the row-major staging
+        constexpr int RPW = DFBB_ROWS / NW;
+        static_assert(DFBB_ROWS % NW == 0 && 2 * RPW <= 32, "one lane per (row, parity) of a warp");
+        const int lp = lane & 1, tl = t0 + warp + NW * (lane >> 1);
+        const int vl = wrapd(c0 - i * (2 * tl + lp), C);
+        float* rl = (lp ? Q1 : Q0) + (long long)tl * (lp ? W1.rs : W0.rs);
+#pragma unroll
+        for (int k = 0; k < 2 * RPW; k++) {
+            const int rr = warp + NW * (k >> 1);
+            if (t0 + rr >= R2) break;
+            float* row = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rl), k));
+            const int vs = __shfl_sync(0xffffffffu, vl, k);
+            const float* srow = ((k & 1) ? arrO : arrE) + (R + rr) * CBS + 2 * R;
+            if (vs + ncol <= C) {
+                float* dst = row + vs;
+#pragma unroll
+                for (int xx = lane; xx < COLS; xx += 32)
+                    if (xx < ncol) dst[xx] = srow[xx];
+            } else {
+#pragma unroll
+                for (int xx = lane; xx < COLS; xx += 32)
+                    if (xx < ncol) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
+            }
+        }
+    } else {
+        for (int par = 0; par < 2; par++) {
+            const View V = par ? W1 : W0;
+            float* P = par ? Q1 : Q0;
+            const float* S = par ? arrO : arrE;
+            if (V.cs == 1) {
+                for (int rr = warp; rr < DFBB_ROWS; rr += NW) {
+                    const int t = t0 + rr;
+                    if (t >= R2) break;
+                    float* row = P + (long long)t * V.rs;
+                    const int vs = wrapd(c0 - i * (2 * t + par), C);
+                    const float* srow = S + (R + rr) * CBS + 2 * R;
                     for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
                 }
-            }
-        } else {
-            // transposed subband: walk along memory order as in the load
-            const int wlo = i > 0 ? -2 * i * (DFBB_ROWS - 1) : 0;
-            const int whi = COLS + (i < 0 ? -2 * i * (DFBB_ROWS - 1) : 0);
-            const int vbase = c0 - i * (2 * t0 + par);
-            for (int k = threadIdx.x; k < (whi - wlo) * DFBB_ROWS; k += blockDim.x) {
-                const int w = wlo + k / DFBB_ROWS, rr = k - (k / DFBB_ROWS) * DFBB_ROWS;
-                const int xx = w + 2 * i * rr;
-                const int t = t0 + rr;
-                if (xx < 0 || xx >= ncol || t >= R2) continue;
-                const int v = wrapd(vbase + w, C);
-                P[(long long)t * V.rs + (long long)v * V.cs] = S[(R + rr) * CBS + 2 * R + xx];
+            } else {
+                // transposed subband (contiguous along t): lanes 0..15 take the tile rows of
+                // one column chunk j, lanes 16..31 those of chunk j + 1; row rr writes tile
+                // column xx = (j + 2 i rr) mod COLS, whose subband column
+                // (c0 - i (2 t + par) + xx) mod C is the same for all rows until xx wraps
+                static_assert(DFBB_ROWS == 16, "half a warp per column chunk");
+                const int rr = lane & 15, t = t0 + rr;
+                const int vr = wrapd(c0 - i * (2 * t + par), C);
+                const int sh = wrapd(2 * i * rr, COLS);
+                float* colp = P + (long long)t * V.rs;
+                const float* srow = S + (R + rr) * CBS + 2 * R;
+                if (t < R2) {
+                    for (int j = 2 * warp + (lane >> 4); j < COLS; j += 2 * NW) {
+                        int xx = j + sh;
+                        xx -= xx >= COLS ? COLS : 0;
+                        if (xx < ncol) colp[(long long)wrap_fast<COLS>(vr + xx, C) * V.cs] = srow[xx];
+                    }
+                }
             }
         }
     }

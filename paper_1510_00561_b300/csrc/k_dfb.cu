@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 
 // one row-split stage, one block per (job, tile)
 template <bool SYN, int NT>
-__global__ void __launch_bounds__(256) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
+__global__ void __launch_bounds__(256, 6) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     using G = BGeo<NT>;
     __shared__ __align__(16) float sE[G::SMB];

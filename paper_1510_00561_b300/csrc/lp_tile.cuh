@@ -44,7 +44,9 @@ static __constant__ float c_gl[7] = {CVC_LO(CVC_G3), CVC_LO(CVC_G2), CVC_LO(CVC_
 
 __device__ __forceinline__ int wrap_idx(int a, int n) {
     if ((unsigned)a < (unsigned)n) return a;
-    int r = a % n;
+    const int b = a < 0 ? a + n : a - n;   // one period outside: no division
+    if ((unsigned)b < (unsigned)n) return b;
+    const int r = a % n;
     return r < 0 ? r + n : r;
 }
 
