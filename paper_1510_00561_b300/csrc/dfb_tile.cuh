@@ -20,9 +20,11 @@
 //   rows).  Rows are staged in shared memory SHEARED by i*q columns (q the
 //   parent row), which turns the slope-i stencil (row offset a, column offset
 //   -i*a + (b-a)/2) into the same NT x NT window for every i; it is evaluated
-//   separably, an NT-tap row sum per source sample and an NT-tap sum across
-//   rows per target.  Both passes of the stage run in one launch on a 16-row
-//   tile, 128 columns staged with an R-row / 2R-column halo.
+//   separably, an NT-tap sum across rows of NT-tap row sums.  A thread walks
+//   an anti-diagonal of targets, along which consecutive targets share all
+//   but one row sum, so the row sums live in registers.  Both passes of the
+//   stage run in one launch on a 16-row tile, 128 columns staged with an
+//   R-row / 2R-column halo.
 //
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
@@ -440,76 +442,95 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
 // ============================================================ k_dfb_b
 // Tile frame for an NT-tap prototype (reach R = NT - 1 per pass): RB = 16 + 2R
 // rows (R-row halo) by CB = 128 columns, of which COLS = 128 - 4R are outputs
-// (2R-column halo: 116, 108, 100), rows stored with stride CBS = CB + 4.  The
-// coset updated first (F) and the second pass's row sums are stored one float
-// to the right of their array base, so that every column-pair window below is
-// 8-byte aligned (R is odd for every even NT).  A thread owns one column pair
-// and one of four interleaved row chunks and walks its rows with constant
-// pointer steps; pairs of lanes compute with paired FP32 instructions,
-// rounding each lane exactly as the scalar sequence would.
+// (2R-column halo: 116, 108, 100), rows stored with stride CBS = CB + 4.
 template <int NT>
 struct BGeo {
     static constexpr int R = NT - 1;
     static constexpr int CB = 128, CBS = CB + 4;
     static constexpr int COLS = CB - 4 * R;
     static constexpr int RB = DFBB_ROWS + 2 * R;
-    static constexpr int SMB = RB * CBS + 2;     // floats per tile array (room for the shift)
+    static constexpr int SMB = RB * CBS;     // floats per tile array
 };
-constexpr int NPAIR = 64, NCHUNK = 4;   // 256 threads
-static_assert(BGeo<4>::COLS == DFBB_COLS && BGeo<8>::CB / 2 <= NPAIR, "one column pair per thread");
-static_assert(3 * BGeo<8>::SMB * 4 <= 48 * 1024, "static shared memory");
+constexpr int DFBB_THREADS = 256;
+static_assert(BGeo<4>::COLS == DFBB_COLS && BGeo<4>::CB - 2 * BGeo<4>::R <= DFBB_THREADS / 2, "one line per thread");
+static_assert(2 * BGeo<8>::SMB * 4 <= 48 * 1024, "static shared memory");
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// row sums h[rr][x] = sum_b bt[b] S[rr][x + b], rows [SR0, SR1), pairs x = X0 + 2p, p < NP
-template <int NT, int SR0, int SR1, int X0, int NP>
-__device__ __forceinline__ void rowsum_pairs(const float* S, float* H) {
-    using G = BGeo<NT>;
-    static_assert(SR0 >= 0 && SR1 <= G::RB && X0 >= 0 && X0 + 2 * NP + NT - 1 <= G::CBS, "row-sum window");
-    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
-    if (p >= NP) return;
-    const float* s = S + (SR0 + c) * G::CBS + X0 + 2 * p;
-    float* h = H + (SR0 + c) * G::CBS + X0 + 2 * p;
-    for (int rr = SR0 + c; rr < SR1; rr += NCHUNK, s += NCHUNK * G::CBS, h += NCHUNK * G::CBS) {
-        float2 v[NT / 2];
+// the row sums h(rho, c) = sum_b bt[b] S[rho][c + b] of rows ra (.x) and rb (.y) at column c
+// (s = S + c), accumulated in b order (the rows are compile-time constants once the
+// caller's loop is unrolled, so every load takes an immediate offset)
+template <int NT>
+__device__ __forceinline__ float2 rowsum2(const float* s, int ra, int rb) {
+    constexpr int CBS = BGeo<NT>::CBS;
+    float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), f2(s[ra * CBS], s[rb * CBS]));
 #pragma unroll
-        for (int k = 0; k < NT / 2; k++) v[k] = *reinterpret_cast<const float2*>(s + 2 * k);
-        const float e = s[NT];
-        float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), v[0]);
-#pragma unroll
-        for (int b = 1; b < NT; b++) {
-            // the pair (S[x + b], S[x + 1 + b])
-            const float2 pr = (b & 1) ? f2(v[b >> 1].y, b + 1 < NT ? v[(b + 1) >> 1].x : e) : v[b >> 1];
-            acc = __ffma2_rn(f2(fan_tap(NT, b), fan_tap(NT, b)), pr, acc);
-        }
-        *reinterpret_cast<float2*>(h) = acc;
-    }
+    for (int b = 1; b < NT; b++)
+        acc = __ffma2_rn(f2(fan_tap(NT, b), fan_tap(NT, b)), f2(s[ra * CBS + b], s[rb * CBS + b]), acc);
+    return acc;
 }
 
-// targets t[r][x] = alpha t + gamma sum_ia bt[ia] h[r + DB + ia][x - ia], rows [R0, R1),
-// pairs x = X0 + 2p, p < NP.  The layout makes the ia-odd pairs 8-byte aligned.
-template <int NT, int R0, int R1, int X0, int NP, bool ODD>
-__device__ __forceinline__ void target_pairs(float* T, const float* H, float alpha, float gamma) {
+// One ladder pass over the targets T[r][x], rows [R0, R1), columns [X0, X0 + NL):
+//   T[r][x] = alpha T[r][x] + gamma sum_ia bt[ia] h(r + DB + ia, x - ia),
+// h the row sums of S.  The rows are cut into 2 NG runs of KC; thread (grp, j), j < NL,
+// grp < NG, walks the wrapped anti-diagonal r = r0 + k, x = X0 + (j - k) mod NL, k < KC,
+// in runs 2 grp (.x) and 2 grp + 1 (.y) at once (paired FP32 instructions round each
+// half exactly as the scalar sequence would).  Consecutive targets of the walk share
+// NT - 1 of their NT row sums, so each thread forms one new row sum per target and
+// keeps the window in registers.  At a fixed step the lanes take consecutive columns
+// of one row.
+template <int NT, int R0, int R1, int X0, int NL, bool ODD, int NG>
+__device__ __forceinline__ void ladder_pass(float* T, const float* S, float alpha, float gamma) {
     using G = BGeo<NT>;
+    constexpr int CBS = G::CBS;
     constexpr int DB = ODD ? -(NT - 2) / 2 : -NT / 2;
-    static_assert(R0 + DB >= 0 && R1 + DB + NT - 1 <= G::RB && X0 >= NT - 1 && X0 + 2 * NP <= G::CB, "target window");
-    const int p = threadIdx.x & (NPAIR - 1), c = threadIdx.x >> 6;
-    if (p >= NP) return;
-    const float* h = H + (R0 + c + DB) * G::CBS + X0 + 2 * p;
-    float* t = T + (R0 + c) * G::CBS + X0 + 2 * p;
+    constexpr int NR = R1 - R0, KC = (NR + 2 * NG - 1) / (2 * NG), LN = DFBB_THREADS / NG;
+    static_assert(R0 + DB >= 0 && R1 + DB + NT - 1 <= G::RB, "row sums inside the rows");
+    static_assert(X0 >= NT - 1 && X0 + NL <= G::CB && NL <= LN && LN % 32 == 0, "columns inside the tile");
+    static_assert(KC >= 1 && (2 * NG - 1) * KC <= NR, "every .x run is full; only the last .y run may be short");
+    const int j = NG == 1 ? (int)threadIdx.x : (int)threadIdx.x % LN, grp = NG == 1 ? 0 : (int)threadIdx.x / LN;
+    if (j >= NL) return;
+    const int r0 = R0 + 2 * grp * KC;                 // first row of the .x run
+    const int ny = min(KC, R1 - r0 - KC);            // valid steps of the .y run
+    const float* Sg = S + r0 * CBS;
+    float* Tg = T + r0 * CBS;
     const float2 al = f2(alpha, alpha), ga = f2(gamma, gamma);
-    for (int r = R0 + c; r < R1; r += NCHUNK, h += NCHUNK * G::CBS, t += NCHUNK * G::CBS) {
-        float2 acc;
+    // lane j < KC - 1 wraps to the right edge at step j + 1: its window there, formed
+    // before the walk (by the lanes of one warp together) rather than inside it
+    float2 w[NT - 1];
+    if (j < KC - 1) {
+        const int kb = j + 1 < ny ? KC + j + 1 : j + 1;
 #pragma unroll
-        for (int ia = 0; ia < NT; ia++) {
-            const float* hp = h + ia * G::CBS - ia;                  // columns x - ia, x + 1 - ia
-            const float2 pr = (ia & 1) ? *reinterpret_cast<const float2*>(hp) : f2(hp[0], hp[1]);
-            acc = ia == 0 ? __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), pr)
-                          : __ffma2_rn(f2(fan_tap(NT, ia), fan_tap(NT, ia)), pr, acc);
+        for (int ia = 0; ia < NT - 1; ia++) w[ia] = rowsum2<NT>(Sg + X0 + NL - 1 - ia, j + 1 + DB + ia, kb + DB + ia);
+    }
+    float2 g[NT];   // g[ia] = h(r + DB + ia, x - ia) for the current target of each half
+#pragma unroll
+    for (int k = 0; k < KC; k++) {
+        const bool hi_ok = k < ny;
+        const int kb = hi_ok ? KC + k : k;   // a missing .y step repeats the .x row
+        int q = j - k;
+        q += q < 0 ? NL : 0;
+        const int x = X0 + q;
+        const float* s = Sg + x;
+        // the window: NT - 1 row sums carried over from the previous target, formed at
+        // the start of the walk, or (where the walk wrapped) the ones formed before it
+        if (k == 0) {
+#pragma unroll
+            for (int ia = 0; ia < NT - 1; ia++) g[ia] = rowsum2<NT>(s - ia, k + DB + ia, kb + DB + ia);
+        } else {
+            const bool wrapped = j == k - 1;
+#pragma unroll
+            for (int ia = 0; ia < NT - 1; ia++) g[ia] = wrapped ? w[ia] : g[ia + 1];
         }
-        float2 tv = *reinterpret_cast<const float2*>(t);
-        tv = __ffma2_rn(al, tv, __fmul2_rn(ga, acc));
-        *reinterpret_cast<float2*>(t) = tv;
+        g[NT - 1] = rowsum2<NT>(s - (NT - 1), k + DB + NT - 1, kb + DB + NT - 1);
+        float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), g[0]);
+#pragma unroll
+        for (int ia = 1; ia < NT; ia++) acc = __ffma2_rn(f2(fan_tap(NT, ia), fan_tap(NT, ia)), g[ia], acc);
+        float* ta = Tg + k * CBS + x;
+        float* tb = Tg + kb * CBS + x;
+        const float2 tv = __ffma2_rn(al, f2(*ta, *tb), __fmul2_rn(ga, acc));
+        *ta = tv.x;
+        if (hi_ok) *tb = tv.y;
     }
 }
 
@@ -519,21 +540,20 @@ __device__ __forceinline__ int wrap_fast(int v, int C) {
     return v < C ? v : (C >= CB ? v - C : v % C);
 }
 
-// one tile of a row-split stage (sE, sO, sH: BGeo<NT>::SMB floats of shared memory each, 16-byte aligned)
+// one tile of a row-split stage (sE, sO: BGeo<NT>::SMB floats of shared memory each, 16-byte aligned)
 template <bool SYN, int NT>
 __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bases& B, const PassParams& pp,
-                                           float* sE, float* sO, float* sH) {
+                                           float* sE, float* sO) {
     using G = BGeo<NT>;
     constexpr int R = G::R, RB = G::RB, CB = G::CB, CBS = G::CBS, COLS = G::COLS;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;
     const int R2 = J.R2, C = J.C, i = J.i;
-    constexpr int NW = NPAIR * NCHUNK / 32;   // warps of the block
+    constexpr int NW = DFBB_THREADS / 32;   // warps of the block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fo = pp.first_odd;
-    // the first-updated coset (odd if fo) sits one float to the right
-    float* const arrE = sE + (fo ? 0 : 1);
-    float* const arrO = sO + (fo ? 1 : 0);
+    float* const arrE = sE;
+    float* const arrO = sO;
     // inputs: analysis reads the parent's cosets, synthesis the children.
     // Smem row r <-> coset row t0 - R + r; smem column x <-> sheared column c0 - 2R + x,
     // i.e. array column (c0 - 2R + x - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
@@ -611,29 +631,19 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     cp_async_wait_all();
     __syncthreads();
     // pass 1 updates F on columns [R, CB - R), which covers what pass 2 reads; pass 2
-    // updates S on the tile [R, R + ROWS) x [2R, CB - 2R).  Pass-1 row sums sit at the
-    // base of sH, pass-2 row sums one float to the right.
+    // updates S on the tile [R, R + ROWS) x [2R, CB - 2R)
     float* F = fo ? arrO : arrE;
     float* Sx = fo ? arrE : arrO;
-    constexpr int NP1 = (CB - 2 * R) / 2, NH1 = (CB - R + 1) / 2, NP2 = COLS / 2, NH2 = (CB - 3 * R + 1) / 2;
-    static_assert(R + 2 * NP1 == CB - R && 2 * R + 2 * NP2 == CB - 2 * R, "pass windows");
     constexpr int ROWS = DFBB_ROWS;
+    constexpr int LG = NT == 4 ? 1 : 2;   // row groups of a ladder pass: the longer windows walk shorter runs
     if (fo) {
-        rowsum_pairs<NT, 0, RB, 0, NH1>(Sx, sH);
+        ladder_pass<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, CB - 2 * R, true, LG>(F, Sx, pp.a1, pp.g1);
         __syncthreads();
-        target_pairs<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, NP1, true>(F, sH, pp.a1, pp.g1);
-        __syncthreads();
-        rowsum_pairs<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, NH2>(F, sH + 1);
-        __syncthreads();
-        target_pairs<NT, R, R + ROWS, 2 * R, NP2, false>(Sx, sH + 1, pp.a2, pp.g2);
+        ladder_pass<NT, R, R + ROWS, 2 * R, COLS, false, LG>(Sx, F, pp.a2, pp.g2);
     } else {
-        rowsum_pairs<NT, 0, RB, 0, NH1>(Sx, sH);
+        ladder_pass<NT, NT / 2, R + ROWS + NT / 2, R, CB - 2 * R, false, LG>(F, Sx, pp.a1, pp.g1);
         __syncthreads();
-        target_pairs<NT, NT / 2, R + ROWS + NT / 2, R, NP1, false>(F, sH, pp.a1, pp.g1);
-        __syncthreads();
-        rowsum_pairs<NT, NT / 2, R + ROWS + NT / 2, R, NH2>(F, sH + 1);
-        __syncthreads();
-        target_pairs<NT, R, R + ROWS, 2 * R, NP2, true>(Sx, sH + 1, pp.a2, pp.g2);
+        ladder_pass<NT, R, R + ROWS, 2 * R, COLS, true, LG>(Sx, F, pp.a2, pp.g2);
     }
     __syncthreads();
     // outputs: analysis writes the children, synthesis the parent's cosets

@@ -18,9 +18,11 @@
 //   rows).  Rows are staged in shared memory SHEARED by i*q columns (q the
 //   parent row), which turns the slope-i stencil (row offset a, column offset
 //   -i*a + (b-a)/2) into the same NT x NT window for every i; it is evaluated
-//   separably, an NT-tap row sum per source sample and an NT-tap sum across
-//   rows per target.  Both passes of the stage run in one launch on a 16-row
-//   tile, 128 columns staged with an R-row / 2R-column halo.
+//   separably, an NT-tap sum across rows of NT-tap row sums.  A thread walks
+//   an anti-diagonal of targets, along which consecutive targets share all
+//   but one row sum, so the row sums live in registers.  Both passes of the
+//   stage run in one launch on a 16-row tile, 128 columns staged with an
+//   R-row / 2R-column halo.
 //
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
@@ -43,15 +45,14 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 
 // one row-split stage, one block per (job, tile)
 template <bool SYN, int NT>
-__global__ void __launch_bounds__(256, 6) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
+__global__ void __launch_bounds__(256, NT == 4 ? 6 : 4) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     using G = BGeo<NT>;
     __shared__ __align__(16) float sE[G::SMB];
     __shared__ __align__(16) float sO[G::SMB];
-    __shared__ __align__(16) float sH[G::SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    dfb_b_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, sE, sO, sH);
+    dfb_b_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, sE, sO);
 }
 
 // ============================================================ launches

@@ -31,7 +31,7 @@ template <int NT>
 constexpr int scratch_floats() {
     constexpr int lp = (int)(ff_smem<4, 3>() / 4);
     constexpr int a = AGeo<NT>::SMEM / 4;
-    constexpr int b = 3 * b_array_floats<NT>();
+    constexpr int b = 2 * b_array_floats<NT>();
     return (((lp > a ? lp : a) > b ? (lp > a ? lp : a) : b) + 3) & ~3;
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, 1) k_pyr_tail(const TailPlane* __restrict
             const int n = b_tiles(J);
             for (int tile = 0; tile < n; tile++) {
                 __syncthreads();
-                dfb_b_tile<SYN, NT>(J, tile, Bt, pp, sm, sm + BA, sm + 2 * BA);
+                dfb_b_tile<SYN, NT>(J, tile, Bt, pp, sm, sm + BA);
             }
         }
         __syncthreads();   // the step's resident outputs are complete before the next step reads them
