@@ -102,34 +102,62 @@ __device__ __forceinline__ void ff2_add(float2& hi, float2& lo, float2 x) {
     hi = s;
     lo = __fadd2_rn(lo, e);
 }
-// (hi, lo) += (f + fl) * (xh + xl), dropping only fl * xl
-__device__ __forceinline__ void ff2_fma(float2& hi, float2& lo, float f, float fl, float2 xh, float2 xl) {
+// ------------------------------------------------- fixed-grid compensated sums
+// A pass accumulates sum_k f_k x_k as a pair (sh, sl): every product is rounded
+// to a multiple of a grid step G (a power of two) by one fused multiply-add with
+// the constant C = 1.5 * 2^23 * G, whose unit in the last place is G, and the
+// rest of the product goes to sl.  Sums of multiples of G below 2^24 G are
+// exact, so sh carries no rounding at all and sl only small terms (|sl| below a
+// few G, a few dozen roundings of 2^-24 |sl| each): the pair holds the sum to
+// about 2^-37 of the bound that chose G, at 7 paired instructions per tap where
+// a float-float (TwoProduct + TwoSum) update takes 11.
+// grid_c(B): C for G = 2^(ceil(log2 B) - 21), B >= every product and partial sum.
+__device__ __forceinline__ float2 grid_c(float bound) {
+    const int e = (__float_as_int(bound) >> 23) & 255;   // biased exponent of |bound|
+    const int ec = min(e + 3, 254);                      // C = 1.5 * 2^(e - 124)
+    const float c = __int_as_float((ec << 23) | 0x400000);
+    return make_float2(c, c);
+}
+// (sh, sl) += (f + fl) * (xh + xl), dropping only fl * xl
+__device__ __forceinline__ void gacc(float2& sh, float2& sl, float2 c, float f, float fl, float2 xh, float2 xl) {
     const float2 ff = make_float2(f, f);
-    const float2 p = __fmul2_rn(ff, xh);
-    const float2 pe = __ffma2_rn(ff, xh, neg2(p));
-    ff2_add(hi, lo, p);
-    lo = __ffma2_rn(ff, xl, __fadd2_rn(lo, pe));
-    lo = __ffma2_rn(make_float2(fl, fl), xh, lo);
+    const float2 ph = __fadd2_rn(__ffma2_rn(ff, xh, c), neg2(c));   // f xh on the grid
+    const float2 pl = __ffma2_rn(ff, xh, neg2(ph));                 // the rest of f xh
+    sh = __fadd2_rn(sh, ph);
+    sl = __fadd2_rn(sl, pl);
+    sl = __ffma2_rn(ff, xl, sl);
+    sl = __ffma2_rn(make_float2(fl, fl), xh, sl);
 }
 // the same with a single-precision x
-__device__ __forceinline__ void ff2_fma1(float2& hi, float2& lo, float f, float fl, float2 x) {
+__device__ __forceinline__ void gacc1(float2& sh, float2& sl, float2 c, float f, float fl, float2 x) {
     const float2 ff = make_float2(f, f);
-    const float2 p = __fmul2_rn(ff, x);
-    const float2 pe = __ffma2_rn(ff, x, neg2(p));
-    ff2_add(hi, lo, p);
-    lo = __ffma2_rn(make_float2(fl, fl), x, __fadd2_rn(lo, pe));
+    const float2 ph = __fadd2_rn(__ffma2_rn(ff, x, c), neg2(c));
+    const float2 pl = __ffma2_rn(ff, x, neg2(ph));
+    sh = __fadd2_rn(sh, ph);
+    sl = __fadd2_rn(sl, pl);
+    sl = __ffma2_rn(make_float2(fl, fl), x, sl);
+}
+// (hi, lo) <- TwoSum(hi, lo): hi the rounded sum, lo its exact error (any magnitudes)
+__device__ __forceinline__ void two_sum2(float2& hi, float2& lo) {
+    const float2 s = __fadd2_rn(hi, lo);
+    const float2 bb = __fadd2_rn(s, neg2(hi));
+    lo = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(lo, neg2(bb)));
+    hi = s;
+}
+__device__ __forceinline__ float lp_warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// Tile with float-float intermediates (dynamic shared memory):
+// One tile with compensated intermediates (sm: ff_smem<RA, RS>() bytes of shared memory):
 //   synthesis (ANA = false): e = cin - down(main, fa);  out = main + up(e, fs)
 //   analysis  (ANA = true):  e = -down(main, fa), cout = -e (rounded);  out = main + up(e, fs)
 // so that the detail image of the analysis carries only its own rounding:
-
-// One tile with float-float intermediates (sm: ff_smem<RA, RS>() bytes of shared memory):
-//   synthesis (ANA = false): e = cin - down(main, fa);  out = main + up(e, fs)
-//   analysis  (ANA = true):  e = -down(main, fa), cout = -e (rounded);  out = main + up(e, fs)
-// so that the detail image of the analysis carries only its own rounding:
-// the lowpass it is computed from is not rounded first.
+// the lowpass it is computed from is not rounded first.  The two decimating
+// passes sum on a grid chosen from the largest magnitude of the staged tile,
+// the two expanding passes on one chosen from the largest |e| (a block-wide
+// maximum each); e itself and the output take float-float additions.
 template <int RA, int RS, bool ANA>
 __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases& B, float* sm) {
     constexpr int T = LP_TILE;
@@ -147,6 +175,7 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
     float* s_al = s_ah + NA4;           // NA
     float* s_vh = s_al + NA4;           // VN * VN
     float* s_vl = s_vh + VN * VN;       // VN * VN
+    float* s_red = s_vl + VN * VN;      // 16: per-warp maxima of the two grids
 
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * T, x0 = tx * T;
@@ -157,6 +186,20 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
     lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
     lp_cp_async_wait_all();
     __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    // the grid of the decimating passes: products and partial sums stay below
+    // sum|h| max|a| <= 1.96^2 max|main| < 4 max|main|
+    float2 c1;
+    {
+        float m = 0.f;
+        for (int r = warp; r < MN; r += nwarp)
+            for (int c = lane; c < MN; c += 32) m = fmaxf(m, fabsf(s_main[r * MNS + c]));
+        m = lp_warp_max(m);
+        if (lane == 0) s_red[warp] = m;
+        __syncthreads();
+        for (int w = 0; w < nwarp; w++) m = fmaxf(m, s_red[w]);
+        c1 = grid_c(4.f * m);
+    }
     // Every pass computes two outputs per thread with paired instructions.
     // decimating row pass, row pairs (ra, rb) (an odd last row pairs with itself), so that
     // consecutive threads read consecutive columns as in a scalar pass
@@ -180,7 +223,7 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
         vb[2 * RA] = wb[2 * RA];
         float2 hi = zero2, lo = zero2;
 #pragma unroll
-        for (int b = -RA; b <= RA; b++) ff2_fma1(hi, lo, tap_a<RA>(b), tapl_a<RA>(b), make_float2(va[RA - b], vb[RA - b]));
+        for (int b = -RA; b <= RA; b++) gacc1(hi, lo, c1, tap_a<RA>(b), tapl_a<RA>(b), make_float2(va[RA - b], vb[RA - b]));
         s_ah[ra * VN + n] = hi.x;
         s_al[ra * VN + n] = lo.x;
         if (rb != ra) {
@@ -194,6 +237,7 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
     const float* cinp = ANA ? nullptr : base_ptr(B, J.cin.b) + J.cin.off;
     const float* cinlp = !ANA && J.cin_lo.b >= 0 ? base_ptr(B, J.cin_lo.b) + J.cin_lo.off : nullptr;
     float* coutp = ANA ? base_ptr(B, J.cout.b) + J.cout.off : nullptr;
+    float me = 0.f;   // this thread's largest |e|
     for (int i = threadIdx.x; i < NM * VN; i += blockDim.x) {
         const int q = i / VN, n = i - q * VN;
         const int ma = 2 * q, mb = min(2 * q + 1, VN - 1);
@@ -201,7 +245,7 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
 #pragma unroll
         for (int a = -RA; a <= RA; a++) {
             const int ka = (2 * ma + RA - a) * VN + n, kb = (2 * mb + RA - a) * VN + n;
-            ff2_fma(hi, lo, tap_a<RA>(a), tapl_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
+            gacc(hi, lo, c1, tap_a<RA>(a), tapl_a<RA>(a), make_float2(s_ah[ka], s_ah[kb]), make_float2(s_al[ka], s_al[kb]));
         }
         float2 eh, el;
         if (ANA) {
@@ -217,9 +261,8 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
             ff2_add(eh, el, neg2(hi));
             el = __fadd2_rn(el, neg2(lo));
         }
-        const float2 sn = __fadd2_rn(eh, el);
-        el = __fadd2_rn(el, neg2(__fadd2_rn(sn, neg2(eh))));
-        eh = sn;
+        two_sum2(eh, el);
+        me = fmaxf(me, fmaxf(fabsf(eh.x), fabsf(eh.y)));
         if (ANA) {
             // this tile's share of the lowpass: half-resolution rows / columns [m0, m0 + T/2) x [n0, n0 + T/2)
             const int gn = n0 + MLO + n;
@@ -236,7 +279,17 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
             s_vl[mb * VN + n] = el.y;
         }
     }
+    me = lp_warp_max(me);
+    if (lane == 0) s_red[8 + warp] = me;
     __syncthreads();
+    // the grid of the expanding passes: each output phase has sum|g| < 1, so products
+    // and partial sums of both passes stay below max|e| (plus the low parts)
+    float2 c2;
+    {
+        float m = 0.f;
+        for (int w = 0; w < nwarp; w++) m = fmaxf(m, s_red[8 + w]);
+        c2 = grid_c(2.f * m);
+    }
     // expanding row pass: output pairs x = 2p, 2p + 1 for p = 2w and 2w + 1
     for (int i = threadIdx.x; i < VN * (T / 4); i += blockDim.x) {
         const int m = i / (T / 4), w = i - m * (T / 4);
@@ -246,12 +299,12 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - t / 2;
-                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
-                        make_float2(s_vl[k], s_vl[k + 1]));
+                gacc(eh, el, c2, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
+                     make_float2(s_vl[k], s_vl[k + 1]));
             } else {
                 const int k = kb + (1 - t) / 2;
-                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
-                        make_float2(s_vl[k], s_vl[k + 1]));
+                gacc(oh, ol, c2, tap_s<RS>(t), tapl_s<RS>(t), make_float2(s_vh[k], s_vh[k + 1]),
+                     make_float2(s_vl[k], s_vl[k + 1]));
             }
         }
         *reinterpret_cast<float4*>(s_ah + m * T + 4 * w) = make_float4(eh.x, oh.x, eh.y, oh.y);
@@ -271,12 +324,12 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
         for (int t = -RS; t <= RS; t++) {
             if ((t & 1) == 0) {
                 const int k = kb - (t / 2) * T;
-                ff2_fma(eh, el, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
-                        *reinterpret_cast<const float2*>(s_al + k));
+                gacc(eh, el, c2, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                     *reinterpret_cast<const float2*>(s_al + k));
             } else {
                 const int k = kb + ((1 - t) / 2) * T;
-                ff2_fma(oh, ol, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
-                        *reinterpret_cast<const float2*>(s_al + k));
+                gacc(oh, ol, c2, tap_s<RS>(t), tapl_s<RS>(t), *reinterpret_cast<const float2*>(s_ah + k),
+                     *reinterpret_cast<const float2*>(s_al + k));
             }
         }
         const int gx = x0 + x;
@@ -287,15 +340,14 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
             float2 hi = h ? oh : eh, lo = h ? ol : el;
             const float* mrow = s_main + (y - Y0) * MNS + (x - Y0);
             ff2_add(hi, lo, make_float2(mrow[0], mrow[1]));
-            const float2 o = __fadd2_rn(hi, lo);
+            two_sum2(hi, lo);   // the rounded output and its exact remainder
             float* orow = outp + (long long)gy * J.out.rs;
-            if (gx < W) orow[gx] = o.x;
-            if (gx + 1 < W) orow[gx + 1] = o.y;
+            if (gx < W) orow[gx] = hi.x;
+            if (gx + 1 < W) orow[gx + 1] = hi.y;
             if (outlp) {
-                const float2 ol2 = __fadd2_rn(lo, neg2(__fadd2_rn(o, neg2(hi))));   // exact: |lo| <= ulp(hi)
                 float* lrow = outlp + (long long)gy * J.out_lo.rs;
-                if (gx < W) lrow[gx] = ol2.x;
-                if (gx + 1 < W) lrow[gx + 1] = ol2.y;
+                if (gx < W) lrow[gx] = lo.x;
+                if (gx + 1 < W) lrow[gx + 1] = lo.y;
             }
         }
     }
@@ -310,7 +362,7 @@ constexpr size_t ff_smem() {
     constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
     constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
     constexpr int MNS = MN + (MN & 1), OA = (MN * MNS + 3) & ~3, NA4 = (NA + 3) & ~3;
-    return sizeof(float) * (size_t)(OA + 2 * NA4 + 2 * VN * VN);
+    return sizeof(float) * (size_t)(OA + 2 * NA4 + 2 * VN * VN + 16);
 }
 
 }  // namespace cvc
