@@ -96,8 +96,8 @@ struct DfbBJob {
 };
 
 constexpr int DFBA_TILE = 64, DFBA_HALO = 12;   // the halo of the 4-tap prototype (4 (NT - 1) in general)
-constexpr int DFBB_ROWS = 16, DFBB_COLS = 116;  // columns of the 4-tap prototype (128 - 4 (NT - 1) in general)
-constexpr int dfbb_cols(int ntaps) { return 128 - 4 * (ntaps - 1); }
+constexpr int DFBB_ROWS = 16, DFBB_COLS = 120;  // columns of the 4-tap prototype ((128 - 2 (NT - 1)) & ~3 in general)
+constexpr int dfbb_cols(int ntaps) { return (128 - 2 * (ntaps - 1)) & ~3; }
 
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)

@@ -17,14 +17,15 @@
 //   the four passes run in place; the planes are written to the channel
 //   arrays, or read from them in the synthesis direction.
 // k_dfb_b: one stage s >= 3 of a channel array (a split into even / odd
-//   rows).  Rows are staged in shared memory SHEARED by i*q columns (q the
-//   parent row), which turns the slope-i stencil (row offset a, column offset
-//   -i*a + (b-a)/2) into the same NT x NT window for every i; it is evaluated
-//   separably, an NT-tap sum across rows of NT-tap row sums.  A thread walks
-//   an anti-diagonal of targets, along which consecutive targets share all
-//   but one row sum, so the row sums live in registers.  Both passes of the
-//   stage run in one launch on a 16-row tile, 128 columns staged with an
-//   R-row / 2R-column halo.
+//   rows).  Rows are staged in shared memory SHEARED by i*q + r columns (q
+//   the parent row, r the tile row), which turns the slope-i stencil (row
+//   offset a, column offset -i*a + (b-a)/2) into one NT x NT rectangle for
+//   every i; it is evaluated separably, an NT-tap sum across rows of NT-tap
+//   row sums.  A thread takes a quad of 4 adjacent targets and walks down
+//   its rows: consecutive targets share all but one row sum, so the row sums
+//   live in registers, and every shared-memory access is a 16-byte vector.
+//   Both passes of the stage run in one launch on a 16-row tile, 128 columns
+//   staged with an R-row / R-column halo.
 //
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
@@ -441,96 +442,160 @@ __device__ __forceinline__ void dfb_a_tile(const DfbAJob& J, int tile, const Bas
 
 // ============================================================ k_dfb_b
 // Tile frame for an NT-tap prototype (reach R = NT - 1 per pass): RB = 16 + 2R
-// rows (R-row halo) by CB = 128 columns, of which COLS = 128 - 4R are outputs
-// (2R-column halo: 116, 108, 100), rows stored with stride CBS = CB + 4.
+// rows (R-row halo) by CB = 128 staged columns, rows stored with stride CBS.
+// Shared-memory column x of tile row r holds column c0 + x - r - i*q of the
+// row's coset array (q the parent row, c0 the tile's first output column):
+//   - the shear by i*q turns the slope-i stencil (row offset a, column offset
+//     -i*a + (b-a)/2) into one NT x NT pattern for every i, a parallelogram
+//     that steps one column left per row;
+//   - the extra column per row straightens it: target (r, x) reads the
+//     rectangle rows [r + DB, r + DB + NT), columns [x + DB, x + DB + NT).
+// So a pass is a separable NT x NT stencil on a plain grid.  COLS outputs per
+// row (an R-column halo on each side; a multiple of 4); the output rows of a
+// tile are shifted one column per row, which still cuts every array row into
+// whole tiles because the arrays are periodic along their rows.
+// The two coset arrays start MARGIN floats into their buffers; the pass-1
+// source array is shifted by D more floats, so that every quad of targets and
+// every source window of both passes starts on (or one float past) a 16-byte
+// boundary.
 template <int NT>
 struct BGeo {
     static constexpr int R = NT - 1;
     static constexpr int CB = 128, CBS = CB + 4;
-    static constexpr int COLS = CB - 4 * R;
+    static constexpr int COLS = (CB - 2 * R) & ~3;       // 120, 116, 112
     static constexpr int RB = DFBB_ROWS + 2 * R;
-    static constexpr int SMB = RB * CBS;     // floats per tile array
+    static constexpr int MARGIN = 8;                    // reads of unused quads stay inside the buffer
+    static constexpr int SMB = RB * CBS + 2 * MARGIN;   // floats per tile array
+    static constexpr int D = NT == 4 ? 2 : 0;
 };
-constexpr int DFBB_THREADS = 256;
-static_assert(BGeo<4>::COLS == DFBB_COLS && BGeo<4>::CB - 2 * BGeo<4>::R <= DFBB_THREADS / 2, "one line per thread");
+constexpr int DFBB_THREADS = 128;    // four warps: one run of rows each in the ladder passes
+static_assert(BGeo<4>::COLS == DFBB_COLS && dfbb_cols(4) == BGeo<4>::COLS && dfbb_cols(6) == BGeo<6>::COLS &&
+                  dfbb_cols(8) == BGeo<8>::COLS,
+              "host and device tile widths");
 static_assert(2 * BGeo<8>::SMB * 4 <= 48 * 1024, "static shared memory");
+
+// The passes of a stage with the first target coset odd (FO) or even.  Pass 1
+// updates the first target coset F from the other one, S, over the rows and
+// columns pass 2 reads; pass 2 updates S on the output tile.  A pass targets
+// quads of 4 columns starting at X (16-byte aligned in its target array);
+// the window of a quad, columns [x + DB, x + DB + NT + 3) of a source row,
+// starts M floats past a 16-byte boundary.
+template <int NT, bool FO>
+struct BPass {
+    using G = BGeo<NT>;
+    static constexpr int R = G::R;
+    static constexpr int DB1 = FO ? -(NT - 2) / 2 : -NT / 2;
+    static constexpr int DB2 = FO ? -NT / 2 : -(NT - 2) / 2;
+    // pass 1: F rows [R + DB2, R + DB2 + ROWS + R), columns [R + DB2, 2R + DB2 + COLS)
+    static constexpr int R10 = R + DB2, R11 = R + DB2 + DFBB_ROWS + R;
+    static constexpr int X1 = (R + DB2) & ~3;
+    static constexpr int NQ1 = (2 * R + DB2 + G::COLS - X1 + 3) / 4;
+    static constexpr int M1 = ((G::D + X1 + DB1) % 4 + 4) % 4;
+    // pass 2: S rows [R, R + ROWS), columns [R, R + COLS)
+    static constexpr int X2 = R - (R + G::D) % 4;
+    static constexpr int NQ2 = (R + G::COLS - X2 + 3) / 4;
+    static constexpr int M2 = ((X2 + DB2) % 4 + 4) % 4;
+    static_assert(R10 + DB1 >= 0 && R11 - 1 + DB1 + NT - 1 < G::RB, "pass-1 rows inside the tile");
+    static_assert(R + DB2 >= R10 && R + DFBB_ROWS - 1 + DB2 + NT - 1 < R11, "pass 2 reads pass-1 rows");
+    static_assert(NQ1 <= 32 && NQ2 <= 32, "one quad per lane");
+    static_assert(X1 + DB1 - M1 >= -G::MARGIN && X2 + DB2 - M2 >= -G::MARGIN, "left windows inside the margin");
+    // right edge: the last quad's window, read as whole 16-byte chunks, ends inside the margin
+    static constexpr int NCH1 = (M1 + NT + 6) / 4, NCH2 = (M2 + NT + 6) / 4;
+    static_assert(X1 + 4 * NQ1 - 4 + DB1 - M1 + 4 * NCH1 <= G::CBS + G::MARGIN - G::D &&
+                      X2 + 4 * NQ2 - 4 + DB2 - M2 + 4 * NCH2 <= G::CBS + G::MARGIN - G::D,
+                  "right windows inside the margin");
+    static_assert(X1 + 4 * NQ1 <= G::CBS && X2 + 4 * NQ2 + G::D <= G::CBS, "target quads inside their rows");
+};
+
+// The NT + 3 samples of a quad's window in one source row: p is 16-byte
+// aligned, the window starts at p[M]
+template <int NT, int M>
+struct QWin {
+    static constexpr int NCH = (M + NT + 3 + 3) / 4;
+    float v[4 * NCH];
+    __device__ __forceinline__ void load(const float* p) {
+#pragma unroll
+        for (int k = 0; k < NCH; k++) {
+            const float4 t = reinterpret_cast<const float4*>(p)[k];
+            v[4 * k] = t.x;
+            v[4 * k + 1] = t.y;
+            v[4 * k + 2] = t.z;
+            v[4 * k + 3] = t.w;
+        }
+    }
+};
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// the row sums h(rho, c) = sum_b bt[b] S[rho][c + b] of rows ra (.x) and rb (.y) at column c
-// (s = S + c), accumulated in b order (the rows are compile-time constants once the
-// caller's loop is unrolled, so every load takes an immediate offset)
-template <int NT>
-__device__ __forceinline__ float2 rowsum2(const float* s, int ra, int rb) {
-    constexpr int CBS = BGeo<NT>::CBS;
-    float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), f2(s[ra * CBS], s[rb * CBS]));
+// the row sums h(x + j) = sum_b bt[b] S[x + j + DB + b], j < 4, of one window, in b
+// order; columns j and j + 1 in one paired instruction where the pair sits in
+// adjacent loaded registers
+template <int NT, int M>
+__device__ __forceinline__ void quad_rowsums(const QWin<NT, M>& w, float2& h01, float2& h23) {
+    constexpr float b0 = fan_tap(NT, 0);
+    h01 = __fmul2_rn(f2(b0, b0), f2(w.v[M], w.v[M + 1]));
+    h23 = __fmul2_rn(f2(b0, b0), f2(w.v[M + 2], w.v[M + 3]));
 #pragma unroll
-    for (int b = 1; b < NT; b++)
-        acc = __ffma2_rn(f2(fan_tap(NT, b), fan_tap(NT, b)), f2(s[ra * CBS + b], s[rb * CBS + b]), acc);
-    return acc;
+    for (int b = 1; b < NT; b++) {
+        const float bt = fan_tap(NT, b);
+        h01 = __ffma2_rn(f2(bt, bt), f2(w.v[M + b], w.v[M + b + 1]), h01);
+        h23 = __ffma2_rn(f2(bt, bt), f2(w.v[M + b + 2], w.v[M + b + 3]), h23);
+    }
 }
 
-// One ladder pass over the targets T[r][x], rows [R0, R1), columns [X0, X0 + NL):
-//   T[r][x] = alpha T[r][x] + gamma sum_ia bt[ia] h(r + DB + ia, x - ia),
-// h the row sums of S.  The rows are cut into 2 NG runs of KC; thread (grp, j), j < NL,
-// grp < NG, walks the wrapped anti-diagonal r = r0 + k, x = X0 + (j - k) mod NL, k < KC,
-// in runs 2 grp (.x) and 2 grp + 1 (.y) at once (paired FP32 instructions round each
-// half exactly as the scalar sequence would).  Consecutive targets of the walk share
-// NT - 1 of their NT row sums, so each thread forms one new row sum per target and
-// keeps the window in registers.  At a fixed step the lanes take consecutive columns
-// of one row.
-template <int NT, int R0, int R1, int X0, int NL, bool ODD, int NG>
-__device__ __forceinline__ void ladder_pass(float* T, const float* S, float alpha, float gamma) {
-    using G = BGeo<NT>;
-    constexpr int CBS = G::CBS;
-    constexpr int DB = ODD ? -(NT - 2) / 2 : -NT / 2;
-    constexpr int NR = R1 - R0, KC = (NR + 2 * NG - 1) / (2 * NG), LN = DFBB_THREADS / NG;
-    static_assert(R0 + DB >= 0 && R1 + DB + NT - 1 <= G::RB, "row sums inside the rows");
-    static_assert(X0 >= NT - 1 && X0 + NL <= G::CB && NL <= LN && LN % 32 == 0, "columns inside the tile");
-    static_assert(KC >= 1 && (2 * NG - 1) * KC <= NR, "every .x run is full; only the last .y run may be short");
-    const int j = NG == 1 ? (int)threadIdx.x : (int)threadIdx.x % LN, grp = NG == 1 ? 0 : (int)threadIdx.x / LN;
-    if (j >= NL) return;
-    const int r0 = R0 + 2 * grp * KC;                 // first row of the .x run
-    const int ny = min(KC, R1 - r0 - KC);            // valid steps of the .y run
-    const float* Sg = S + r0 * CBS;
-    float* Tg = T + r0 * CBS;
+// One ladder pass: for every target quad T[r][x .. x+3] of rows [R0, R1),
+//   T[r][x+j] = alpha T[r][x+j] + gamma sum_ia bt[ia] h(r + DB + ia, x + j),
+//   h(rho, c) = sum_b bt[b] S[rho][c + DB + b].
+// Lane k takes the quad at column X + 4k (k < NQ); warp w walks the rows
+// [R0 + w KC, R0 + (w+1) KC) down its quad with the NT row sums of the current
+// target in registers, forming one new row sum per target.  Every sum is
+// accumulated in the order of the scalar definition (taps in index order, the
+// first a product), so each element rounds as a plain loop would round it.
+template <int NT, int R0, int R1, int X, int NQ, int DB, int M>
+__device__ __forceinline__ void ladder_quads(float* T, const float* S, float alpha, float gamma) {
+    constexpr int CBS = BGeo<NT>::CBS, NWARPS = DFBB_THREADS / 32;
+    constexpr int NR = R1 - R0, KC = (NR + NWARPS - 1) / NWARPS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = R0 + warp * KC;
+    if (lane >= NQ || warp >= NWARPS || r0 >= R1) return;
+    const int x = X + 4 * lane;
+    const float* s = S + (r0 + DB) * CBS + (x + DB - M);
+    float* t = T + r0 * CBS + x;
     const float2 al = f2(alpha, alpha), ga = f2(gamma, gamma);
-    // lane j < KC - 1 wraps to the right edge at step j + 1: its window there, formed
-    // before the walk (by the lanes of one warp together) rather than inside it
-    float2 w[NT - 1];
-    if (j < KC - 1) {
-        const int kb = j + 1 < ny ? KC + j + 1 : j + 1;
+    float2 g01[NT], g23[NT];    // row sums of source rows r + DB + ia of the current target row r
 #pragma unroll
-        for (int ia = 0; ia < NT - 1; ia++) w[ia] = rowsum2<NT>(Sg + X0 + NL - 1 - ia, j + 1 + DB + ia, kb + DB + ia);
+    for (int ia = 0; ia < NT - 1; ia++) {
+        QWin<NT, M> w;
+        w.load(s + ia * CBS);
+        quad_rowsums<NT, M>(w, g01[ia], g23[ia]);
     }
-    float2 g[NT];   // g[ia] = h(r + DB + ia, x - ia) for the current target of each half
 #pragma unroll
     for (int k = 0; k < KC; k++) {
-        const bool hi_ok = k < ny;
-        const int kb = hi_ok ? KC + k : k;   // a missing .y step repeats the .x row
-        int q = j - k;
-        q += q < 0 ? NL : 0;
-        const int x = X0 + q;
-        const float* s = Sg + x;
-        // the window: NT - 1 row sums carried over from the previous target, formed at
-        // the start of the walk, or (where the walk wrapped) the ones formed before it
-        if (k == 0) {
-#pragma unroll
-            for (int ia = 0; ia < NT - 1; ia++) g[ia] = rowsum2<NT>(s - ia, k + DB + ia, kb + DB + ia);
-        } else {
-            const bool wrapped = j == k - 1;
-#pragma unroll
-            for (int ia = 0; ia < NT - 1; ia++) g[ia] = wrapped ? w[ia] : g[ia + 1];
+        if (NR % NWARPS != 0 && r0 + k >= R1) break;
+        {
+            QWin<NT, M> w;
+            w.load(s + (k + NT - 1) * CBS);
+            quad_rowsums<NT, M>(w, g01[NT - 1], g23[NT - 1]);
         }
-        g[NT - 1] = rowsum2<NT>(s - (NT - 1), k + DB + NT - 1, kb + DB + NT - 1);
-        float2 acc = __fmul2_rn(f2(fan_tap(NT, 0), fan_tap(NT, 0)), g[0]);
+        constexpr float b0 = fan_tap(NT, 0);
+        float2 a01 = __fmul2_rn(f2(b0, b0), g01[0]);
+        float2 a23 = __fmul2_rn(f2(b0, b0), g23[0]);
 #pragma unroll
-        for (int ia = 1; ia < NT; ia++) acc = __ffma2_rn(f2(fan_tap(NT, ia), fan_tap(NT, ia)), g[ia], acc);
-        float* ta = Tg + k * CBS + x;
-        float* tb = Tg + kb * CBS + x;
-        const float2 tv = __ffma2_rn(al, f2(*ta, *tb), __fmul2_rn(ga, acc));
-        *ta = tv.x;
-        if (hi_ok) *tb = tv.y;
+        for (int ia = 1; ia < NT; ia++) {
+            const float bt = fan_tap(NT, ia);
+            a01 = __ffma2_rn(f2(bt, bt), g01[ia], a01);
+            a23 = __ffma2_rn(f2(bt, bt), g23[ia], a23);
+        }
+        float4* tp = reinterpret_cast<float4*>(t + k * CBS);
+        const float4 tv = *tp;
+        const float2 o01 = __ffma2_rn(al, f2(tv.x, tv.y), __fmul2_rn(ga, a01));
+        const float2 o23 = __ffma2_rn(al, f2(tv.z, tv.w), __fmul2_rn(ga, a23));
+        *tp = make_float4(o01.x, o01.y, o23.x, o23.y);
+#pragma unroll
+        for (int ia = 0; ia < NT - 1; ia++) {
+            g01[ia] = g01[ia + 1];
+            g23[ia] = g23[ia + 1];
+        }
     }
 }
 
@@ -540,7 +605,18 @@ __device__ __forceinline__ int wrap_fast(int v, int C) {
     return v < C ? v : (C >= CB ? v - C : v % C);
 }
 
-// one tile of a row-split stage (sE, sO: BGeo<NT>::SMB floats of shared memory each, 16-byte aligned)
+template <int NT, bool FO>
+__device__ __forceinline__ void dfb_b_passes(float* F, float* Sx, const PassParams& pp) {
+    using P = BPass<NT, FO>;
+    constexpr int R = BGeo<NT>::R;
+    ladder_quads<NT, P::R10, P::R11, P::X1, P::NQ1, P::DB1, P::M1>(F, Sx, pp.a1, pp.g1);
+    __syncthreads();
+    ladder_quads<NT, R, R + DFBB_ROWS, P::X2, P::NQ2, P::DB2, P::M2>(Sx, F, pp.a2, pp.g2);
+}
+
+// One tile of a row-split stage (sE, sO: BGeo<NT>::SMB floats of shared memory
+// each, 16-byte aligned).  The first DFBB_THREADS threads of the block do the
+// work; every thread of the block must call it (it holds barriers).
 template <bool SYN, int NT>
 __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bases& B, const PassParams& pp,
                                            float* sE, float* sO) {
@@ -549,26 +625,29 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;
     const int R2 = J.R2, C = J.C, i = J.i;
-    constexpr int NW = DFBB_THREADS / 32;   // warps of the block
+    constexpr int NW = DFBB_THREADS / 32;   // working warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool worker = threadIdx.x < DFBB_THREADS;
     const int fo = pp.first_odd;
-    float* const arrE = sE;
-    float* const arrO = sO;
+    // the first target coset's array at the margin, the other D floats further
+    float* const arrE = sE + G::MARGIN + (fo ? G::D : 0);
+    float* const arrO = sO + G::MARGIN + (fo ? 0 : G::D);
     // inputs: analysis reads the parent's cosets, synthesis the children.
-    // Smem row r <-> coset row t0 - R + r; smem column x <-> sheared column c0 - 2R + x,
-    // i.e. array column (c0 - 2R + x - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
+    // Smem row r <-> coset row t0 - R + r; smem column x <-> array column
+    // (c0 + x - r - i*q) mod C for parent row q = 2*(t0 - R + r) + parity
     const View V0 = SYN ? J.c0 : J.pe, V1 = SYN ? J.c1 : J.po;
     const float* const P0 = base_ptr(B, V0.b) + V0.off;
     const float* const P1 = base_ptr(B, V1.b) + V1.off;
-    if (!__isShared(P0) && !__isShared(P1) && V0.cs == 1 && V1.cs == 1) {
+    if (!worker) {
+    } else if (!__isShared(P0) && !__isShared(P1) && V0.cs == 1 && V1.cs == 1) {
         // row-major arrays.  Warp w stages rows w, w + NW, ... of both parities; lane
-        // 2k + p first places row w + NW k of parity p (array row and sheared start
-        // column, one modular reduction for all of them), then the warp copies the rows
-        // one by one, taking each row's placement from its lane.
+        // 2k + p first places row w + NW k of parity p (array row and start column, one
+        // modular reduction for all of them), then the warp copies the rows one by one,
+        // taking each row's placement from its lane.
         constexpr int RPW = (RB + NW - 1) / NW;
         static_assert(2 * RPW <= 32, "one lane per (row, parity) of a warp");
-        const int lp = lane & 1, tl = t0 - R + warp + NW * (lane >> 1);
-        const int vl = wrapd(c0 - 2 * R - i * (2 * tl + lp), C);
+        const int lp = lane & 1, rl0 = warp + NW * (lane >> 1), tl = t0 - R + rl0;
+        const int vl = wrapd(c0 - rl0 - i * (2 * tl + lp), C);
         const float* rl = (lp ? P1 : P0) + (long long)wrapd(tl, R2) * (lp ? V1.rs : V0.rs);
 #pragma unroll
         for (int k = 0; k < 2 * RPW; k++) {
@@ -578,7 +657,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rl), k));
             const int vs = __shfl_sync(0xffffffffu, vl, k);
             const unsigned sb = smem_addr(((k & 1) ? arrO : arrE) + r * CBS);
-            if (vs + CB <= C) {                  // the sheared window does not wrap: no per-element checks
+            if (vs + CB <= C) {                  // the window does not wrap: no per-element checks
                 const float* src = row + vs;
 #pragma unroll
                 for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
@@ -597,26 +676,26 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
                 for (int r = warp; r < RB; r += NW) {
                     const int tu = t0 - R + r;
                     const float* row = P + (long long)wrapd(tu, R2) * V.rs;
-                    const int vs = c0 - 2 * R - i * (2 * tu + par);
+                    const int vs = c0 - r - i * (2 * tu + par);
                     for (int x = lane; x < CB; x += 32) S[r * CBS + x] = row[(long long)wrapd(vs + x, C) * V.cs];
                 }
             } else if (V.cs == 1) {
                 for (int r = warp; r < RB; r += NW) {
                     const int tu = t0 - R + r;
                     const float* row = P + (long long)wrapd(tu, R2) * V.rs;
-                    const int vs = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
+                    const int vs = wrapd(c0 - r - i * (2 * tu + par), C);
                     const unsigned sb = smem_addr(S + r * CBS);
                     for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
                 }
             } else {
                 // transposed array (contiguous along the rows t): lane r < RB takes smem row
-                // r, and at step j tile column x = (j + 2 i r) mod CB, whose array column
-                // (c0 - 2R - i (2 tu + par) + x) mod C is the same for all rows until x wraps,
+                // r, and at step j tile column x = (j + (2i + 1) r) mod CB, whose array column
+                // (c0 - r - i (2 tu + par) + x) mod C is the same for all rows until x wraps,
                 // so a warp reads a run of consecutive t
                 static_assert(RB <= 32 && (CB & (CB - 1)) == 0, "one lane per tile row; CB a power of two");
                 const int tu = t0 - R + lane;
-                const int vr = wrapd(c0 - 2 * R - i * (2 * tu + par), C);
-                const int sh = (2 * i * lane) & (CB - 1);
+                const int vr = wrapd(c0 - lane - i * (2 * tu + par), C);
+                const int sh = ((2 * i + 1) * lane) & (CB - 1);
                 const float* rowp = P + (long long)wrapd(tu, R2) * V.rs;
                 const unsigned sb = smem_addr(S + lane * CBS);
                 if (lane < RB) {
@@ -630,42 +709,31 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     }
     cp_async_wait_all();
     __syncthreads();
-    // pass 1 updates F on columns [R, CB - R), which covers what pass 2 reads; pass 2
-    // updates S on the tile [R, R + ROWS) x [2R, CB - 2R)
-    float* F = fo ? arrO : arrE;
-    float* Sx = fo ? arrE : arrO;
-    constexpr int ROWS = DFBB_ROWS;
-    constexpr int LG = NT == 4 ? 1 : 2;   // row groups of a ladder pass: the longer windows walk shorter runs
-    if (fo) {
-        ladder_pass<NT, NT / 2 - 1, R + ROWS + NT / 2 - 1, R, CB - 2 * R, true, LG>(F, Sx, pp.a1, pp.g1);
-        __syncthreads();
-        ladder_pass<NT, R, R + ROWS, 2 * R, COLS, false, LG>(Sx, F, pp.a2, pp.g2);
-    } else {
-        ladder_pass<NT, NT / 2, R + ROWS + NT / 2, R, CB - 2 * R, false, LG>(F, Sx, pp.a1, pp.g1);
-        __syncthreads();
-        ladder_pass<NT, R, R + ROWS, 2 * R, COLS, true, LG>(Sx, F, pp.a2, pp.g2);
-    }
+    if (fo) dfb_b_passes<NT, true>(arrO, arrE, pp);
+    else dfb_b_passes<NT, false>(arrE, arrO, pp);
     __syncthreads();
-    // outputs: analysis writes the children, synthesis the parent's cosets
+    if (!worker) return;
+    // outputs: analysis writes the children, synthesis the parent's cosets.  Output
+    // (rr, u) of the tile is smem (R + rr, R + u), array column c0 + u - rr - i (2t + par)
     const int ncol = min(COLS, C - c0);
     const View W0 = SYN ? J.pe : J.c0, W1 = SYN ? J.po : J.c1;
     float* const Q0 = base_ptr(B, W0.b) + W0.off;
     float* const Q1 = base_ptr(B, W1.b) + W1.off;
     if (W0.cs == 1 && W1.cs == 1) {
-        // row-major arrays: warp w writes rows w, w + NW of both parities, placed by
-        // lanes 0..3 as in the row-major staging
+        // row-major arrays: warp w writes rows w, w + NW, ... of both parities, placed by
+        // its lanes as in the row-major staging
         constexpr int RPW = DFBB_ROWS / NW;
         static_assert(DFBB_ROWS % NW == 0 && 2 * RPW <= 32, "one lane per (row, parity) of a warp");
-        const int lp = lane & 1, tl = t0 + warp + NW * (lane >> 1);
-        const int vl = wrapd(c0 - i * (2 * tl + lp), C);
-        float* rl = (lp ? Q1 : Q0) + (long long)tl * (lp ? W1.rs : W0.rs);
+        const int lp = lane & 1, rl = warp + NW * (lane >> 1), tl = t0 + rl;
+        const int vl = wrapd(c0 - rl - i * (2 * tl + lp), C);
+        float* ql = (lp ? Q1 : Q0) + (long long)tl * (lp ? W1.rs : W0.rs);
 #pragma unroll
         for (int k = 0; k < 2 * RPW; k++) {
             const int rr = warp + NW * (k >> 1);
             if (t0 + rr >= R2) break;
-            float* row = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rl), k));
+            float* row = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ql), k));
             const int vs = __shfl_sync(0xffffffffu, vl, k);
-            const float* srow = ((k & 1) ? arrO : arrE) + (R + rr) * CBS + 2 * R;
+            const float* srow = ((k & 1) ? arrO : arrE) + (R + rr) * CBS + R;
             if (vs + ncol <= C) {
                 float* dst = row + vs;
 #pragma unroll
@@ -687,21 +755,21 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
                     const int t = t0 + rr;
                     if (t >= R2) break;
                     float* row = P + (long long)t * V.rs;
-                    const int vs = wrapd(c0 - i * (2 * t + par), C);
-                    const float* srow = S + (R + rr) * CBS + 2 * R;
+                    const int vs = wrapd(c0 - rr - i * (2 * t + par), C);
+                    const float* srow = S + (R + rr) * CBS + R;
                     for (int xx = lane; xx < ncol; xx += 32) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
                 }
             } else {
                 // transposed subband (contiguous along t): lanes 0..15 take the tile rows of
                 // one column chunk j, lanes 16..31 those of chunk j + 1; row rr writes tile
-                // column xx = (j + 2 i rr) mod COLS, whose subband column
-                // (c0 - i (2 t + par) + xx) mod C is the same for all rows until xx wraps
+                // column xx = (j + (2i + 1) rr) mod COLS, whose subband column
+                // (c0 - rr - i (2 t + par) + xx) mod C is the same for all rows until xx wraps
                 static_assert(DFBB_ROWS == 16, "half a warp per column chunk");
                 const int rr = lane & 15, t = t0 + rr;
-                const int vr = wrapd(c0 - i * (2 * t + par), C);
-                const int sh = wrapd(2 * i * rr, COLS);
+                const int vr = wrapd(c0 - rr - i * (2 * t + par), C);
+                const int sh = wrapd((2 * i + 1) * rr, COLS);
                 float* colp = P + (long long)t * V.rs;
-                const float* srow = S + (R + rr) * CBS + 2 * R;
+                const float* srow = S + (R + rr) * CBS + R;
                 if (t < R2) {
                     for (int j = 2 * warp + (lane >> 4); j < COLS; j += 2 * NW) {
                         int xx = j + sh;

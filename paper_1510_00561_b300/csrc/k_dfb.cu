@@ -15,14 +15,15 @@
 //   the four passes run in place; the planes are written to the channel
 //   arrays, or read from them in the synthesis direction.
 // k_dfb_b: one stage s >= 3 of a channel array (a split into even / odd
-//   rows).  Rows are staged in shared memory SHEARED by i*q columns (q the
-//   parent row), which turns the slope-i stencil (row offset a, column offset
-//   -i*a + (b-a)/2) into the same NT x NT window for every i; it is evaluated
-//   separably, an NT-tap sum across rows of NT-tap row sums.  A thread walks
-//   an anti-diagonal of targets, along which consecutive targets share all
-//   but one row sum, so the row sums live in registers.  Both passes of the
-//   stage run in one launch on a 16-row tile, 128 columns staged with an
-//   R-row / 2R-column halo.
+//   rows).  Rows are staged in shared memory SHEARED by i*q + r columns (q
+//   the parent row, r the tile row), which turns the slope-i stencil (row
+//   offset a, column offset -i*a + (b-a)/2) into one NT x NT rectangle for
+//   every i; it is evaluated separably, an NT-tap sum across rows of NT-tap
+//   row sums.  A thread takes a quad of 4 adjacent targets and walks down
+//   its rows: consecutive targets share all but one row sum, so the row sums
+//   live in registers, and every shared-memory access is a 16-byte vector.
+//   Both passes of the stage run in one launch on a 16-row tile, 128 columns
+//   staged with an R-row / R-column halo.
 //
 // Both directions compute in single precision: the filter-bank weights are
 // dyadic and alpha, gamma powers of two, and the inverse's error is dominated
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 
 // one row-split stage, one block per (job, tile)
 template <bool SYN, int NT>
-__global__ void __launch_bounds__(256, NT == 4 ? 6 : 4) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
+__global__ void __launch_bounds__(DFBB_THREADS, NT == 8 ? 7 : 8) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     using G = BGeo<NT>;
     __shared__ __align__(16) float sE[G::SMB];
@@ -99,14 +100,14 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
     } else {
         const DfbBJob* j = static_cast<const DfbBJob*>(L.d_jobs);
         if (L.ntaps == 6) {
-            if (syn) k_dfb_b<true, 6><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 6><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) k_dfb_b<true, 6><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            else k_dfb_b<false, 6><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
         } else if (L.ntaps == 8) {
-            if (syn) k_dfb_b<true, 8><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 8><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) k_dfb_b<true, 8><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            else k_dfb_b<false, 8><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
         } else {
-            if (syn) k_dfb_b<true, 4><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 4><<<L.nblocks, 256, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) k_dfb_b<true, 4><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            else k_dfb_b<false, 4><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
         }
     }
     return cudaGetLastError();
