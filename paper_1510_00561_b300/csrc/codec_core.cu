@@ -43,7 +43,12 @@ void carve_all(Core* c, Carve& k) {
     k.add(&c->d_row_comp, c->h_row_comp.size());
     k.add(&c->d_row_mc, c->h_row_mc.size());
     k.add(&c->d_row_low, c->h_row_low.size());
-    k.add(&c->d_comp_row0, c->h_comp_row0.size());
+    k.add(&c->d_comp_tile0, c->h_comp_tile0.size());
+    k.add(&c->d_tile_off, c->h_tile_off.size());
+    k.add(&c->d_tile_n, c->h_tile_n.size());
+    k.add(&c->d_tile_w, c->h_tile_w.size());
+    k.add(&c->d_tile_stream, c->h_tile_stream.size());
+    k.add(&c->d_tile_low, c->h_tile_low.size());
     k.add(&c->d_comp_stream, c->h_comp_stream.size());
     k.add(&c->d_comp_low, c->h_comp_low.size());
     k.add(&c->d_comp_level, c->h_comp_level.size());
@@ -71,14 +76,16 @@ void carve_all(Core* c, Carve& k) {
         k.add(&c->d_est_buf[b], (size_t)c->ncoef);
         k.add(&c->d_dst_buf[b], (size_t)c->ncoef);
     }
-    k.add(&c->d_res, (size_t)c->ncoef);
-    k.add(&c->d_rowcnt, (size_t)c->nrows);
-    k.add(&c->d_rowoff, (size_t)c->nrows + 1);
-    k.add(&c->d_scan_tmp, (size_t)cdiv(c->nrows, 2048) + 8);
+    k.add(&c->d_res, (size_t)c->ncoef + 8);   // the RLE reads whole 16-byte chunks
+    k.add(&c->d_tilecnt, (size_t)c->ntiles);
+    k.add(&c->d_tileoff, (size_t)c->ntiles + 1);
+    k.add(&c->d_scan_tmp, (size_t)cdiv(c->ntiles, 2048) + 8);
     k.add(&c->d_comp_tok, (size_t)c->ncomp);
     k.add(&c->d_tok_base, n + 1);
-    k.add(&c->d_contrib, (size_t)c->sum_max_tok);
-    k.add(&c->d_pos, (size_t)c->sum_max_tok + 1);
+    k.add(&c->d_dtile_base, n + 1);
+    k.add(&c->d_dtile_sum, (size_t)c->max_dtiles);
+    k.add(&c->d_dtile_pre, (size_t)c->max_dtiles + 1);
+    k.add(&c->d_comp_codes, (size_t)c->ncomp);
     k.add(&c->d_scan_tmp2, 1024 + 8);
 }
 
@@ -300,7 +307,8 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.coef_off = coef_off;
         D.ncoef = Ly.total + 2 * Lc.total;
         D.row0 = (int)c->h_row_off.size();
-        D.comp0 = (int)c->h_comp_row0.size();
+        D.tile0 = (int)c->h_tile_off.size();
+        D.comp0 = (int)c->h_comp_low.size();
         D.ncomp = (int)(Ly.sb.size() + 2 * Lc.sb.size());
         D.hdr_bytes = 32 + 4LL * D.ncomp;
         D.max_tok = 2 * D.ncoef + 64;
@@ -358,7 +366,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             // rows of every component, in stream order
             for (const SubbandG& sb : Lp.sb) {
                 const int comp = (int)c->h_comp_low.size();
-                c->h_comp_row0.push_back((int)c->h_row_off.size());
+                c->h_comp_tile0.push_back((int)c->h_tile_off.size());
                 c->h_comp_low.push_back(sb.kind == 0);
                 c->h_comp_level.push_back((uint8_t)sb.level);
                 c->h_comp_plane.push_back((uint8_t)p);
@@ -370,6 +378,14 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
                 c->h_comp_ex.push_back((uint8_t)ex);
                 c->h_comp_stream.push_back(s);
                 c->h_comp_elem.push_back(poff[p] - coef_off + sb.off);
+                const int rpt = std::max(1, RLE_TILE / sb.w);   // rows per RLE tile
+                for (int r = 0; r < sb.h; r += rpt) {
+                    c->h_tile_off.push_back(poff[p] + sb.off + (long long)r * sb.w);
+                    c->h_tile_n.push_back(std::min(rpt, sb.h - r) * sb.w);
+                    c->h_tile_w.push_back(sb.w);
+                    c->h_tile_stream.push_back(s);
+                    c->h_tile_low.push_back(sb.kind == 0);
+                }
                 for (int r = 0; r < sb.h; r++) {
                     c->h_row_off.push_back(poff[p] + sb.off + (long long)r * sb.w);
                     c->h_row_w.push_back(sb.w);
@@ -381,17 +397,21 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
             }
         }
         D.nrows = (int)c->h_row_off.size() - D.row0;
+        D.ntiles = (int)c->h_tile_off.size() - D.tile0;
         std::vector<PlaneRef> sp = codec_planes(g, L, P.dirs_log2, P.dfb_taps, plane_off, poff, s);
         planes.insert(planes.end(), sp.begin(), sp.end());
         plane_off += D.nplane;
         coef_off += D.ncoef;
         sum_tok += D.max_tok;
+        c->max_dtiles += cdiv(D.max_tok, DEC_TILE);
+        if (D.ncomp > DEC_MAX_COMP) return CVC_ERR_UNSUPPORTED;
     }
-    c->h_comp_row0.push_back((int)c->h_row_off.size());   // sentinel: end of the last component
+    c->h_comp_tile0.push_back((int)c->h_tile_off.size());   // sentinel: end of the last component
     c->nplane = plane_off;
     c->ncoef = coef_off;
     c->sum_max_tok = sum_tok;
     c->nrows = (int)c->h_row_off.size();
+    c->ntiles = (int)c->h_tile_off.size();
     c->ncomp = (int)c->h_comp_low.size();
     c->nplanes = (int)c->h_pd.size();
     // token positions and element offsets are 32-bit on the device
@@ -456,7 +476,9 @@ cvc_status core_alloc(Core* c) {
               put(c->d_blk_plane, c->h_blk_plane) &&
               put(c->d_row_off, c->h_row_off) && put(c->d_row_w, c->h_row_w) &&
               put(c->d_row_stream, c->h_row_stream) && put(c->d_row_low, c->h_row_low) &&
-              put(c->d_comp_row0, c->h_comp_row0) && put(c->d_comp_stream, c->h_comp_stream) &&
+              put(c->d_comp_tile0, c->h_comp_tile0) && put(c->d_tile_off, c->h_tile_off) &&
+              put(c->d_tile_n, c->h_tile_n) && put(c->d_tile_w, c->h_tile_w) && put(c->d_tile_stream, c->h_tile_stream) &&
+              put(c->d_tile_low, c->h_tile_low) && put(c->d_comp_stream, c->h_comp_stream) &&
               put(c->d_comp_low, c->h_comp_low) && put(c->d_comp_elem, c->h_comp_elem) &&
               put(c->d_comp_level, c->h_comp_level) && put(c->d_comp_plane, c->h_comp_plane) &&
               put(c->d_row_comp, c->h_row_comp) && put(c->d_row_mc, c->h_row_mc) && put(c->d_comp_ey, c->h_comp_ey) &&
@@ -577,7 +599,8 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
     CK(cudaGetLastError());
     k += 1;
     const RowTable rt{c->d_row_off, c->d_row_w, c->d_row_low, c->d_row_stream, c->d_row_comp, c->d_row_mc, c->nrows};
-    const CompTable ct{c->d_comp_row0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
+    const RleTiles tt{c->d_tile_off, c->d_tile_n, c->d_tile_w, c->d_tile_stream, c->d_tile_low, c->ntiles};
+    const CompTable ct{c->d_comp_tile0, c->d_comp_low, c->d_comp_stream, c->d_comp_elem,
                        c->d_comp_level, c->d_comp_plane, c->d_comp_ey, c->d_comp_ex, c->ncomp};
     const bool motion = !c->h_blk_motion.empty();
     const int rpb = c->shape.rle_rows;
@@ -631,11 +654,11 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         clk.end(3, motion ? 3 : 1);
         // S9: RLE rows, row offsets, tokens, headers
         clk.begin(4);
-        k_rle_count_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sc, c->d_rowcnt);
+        k_rle_count_b<<<c->ntiles, RLE_THREADS, 0, st>>>(c->d_res, tt, c->d_sc, c->d_tilecnt);
         CK(cudaGetLastError());
-        CK(exclusive_scan(c->d_rowcnt, (uint32_t)c->nrows, c->d_rowoff, c->d_scan_tmp, st));
-        k_rle_write_b<<<rgrid, 32 * rpb, 0, st>>>(c->d_res, rt, c->d_sd, c->d_sc, c->d_rowoff, c->d_rs);
-        k_stream_header_b<<<n, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rowoff, ct, c->d_mv, c->d_rs);
+        CK(exclusive_scan(c->d_tilecnt, (uint32_t)c->ntiles, c->d_tileoff, c->d_scan_tmp, st));
+        k_rle_write_b<<<c->ntiles, RLE_THREADS, 0, st>>>(c->d_res, tt, c->d_sd, c->d_sc, c->d_tileoff, c->d_rs);
+        k_stream_header_b<<<n, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_tileoff, ct, c->d_mv, c->d_rs);
         CK(cudaGetLastError());
         clk.end(4, 6);
         k += 7;
@@ -645,17 +668,17 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         // parse, token -> element counts, positions, checks, scatter of non-zero codes
         clk.begin(5);
         k_dec_parse_b<<<n, 1024, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, ct, c->d_comp_tok, c->d_rs);
-        k_dec_base_b<<<1, 32, 0, st>>>(c->d_sd, n, c->d_rs, c->d_tok_base);
-        k_dec_contrib_b<<<tg, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_tok_base, n, c->d_comp_tok, ct,
-                                            c->d_contrib, c->d_rs);
+        k_dec_base_b<<<1, 32, 0, st>>>(c->d_sd, n, c->d_rs, c->d_tok_base, c->d_dtile_base);
+        k_dec_count_b<<<tg, DEC_THREADS, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_dtile_base, n, c->d_comp_tok, ct,
+                                                 c->d_dtile_sum, c->d_rs);
         CK(cudaGetLastError());
-        CK(exclusive_scan_dev(c->d_contrib, c->d_tok_base + n, (uint32_t)c->sum_max_tok, c->d_pos, c->d_scan_tmp2,
-                              st));
-        k_dec_check_b<<<(int)cdiv(c->ncomp, 256), 256, 0, st>>>(c->d_sd, c->d_rs, c->d_tok_base, c->d_comp_tok,
-                                                                c->d_pos, ct, c->d_rs);
+        CK(exclusive_scan_dev(c->d_dtile_sum, c->d_dtile_base + n, (uint32_t)c->max_dtiles, c->d_dtile_pre,
+                              c->d_scan_tmp2, st));
         CK(cudaMemsetAsync(c->d_res, 0, (size_t)c->ncoef * 2, st));
-        k_dec_scatter_b<<<tg, 256, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_tok_base, n, c->d_comp_tok, ct,
-                                            c->d_pos, c->d_res);
+        CK(cudaMemsetAsync(c->d_comp_codes, 0, (size_t)c->ncomp * 4, st));
+        k_dec_scatter_b<<<tg, DEC_THREADS, 0, st>>>(c->d_sd, c->d_sc, c->d_rs, c->d_dtile_base, n, c->d_comp_tok, ct,
+                                                   c->d_dtile_pre, c->d_comp_codes, c->d_res);
+        k_dec_check_b<<<(int)cdiv(c->ncomp, 256), 256, 0, st>>>(c->d_sd, c->d_rs, c->d_comp_codes, ct, c->d_rs);
         CK(cudaGetLastError());
         clk.end(5, 8);
         // inverse K/P differencing and dequantisation

@@ -58,13 +58,16 @@ struct Core {
     std::vector<cvc_params> prm;
     std::vector<SDesc> sd;
     std::vector<PlaneLayout> ly, lc;
-    long long nplane = 0, ncoef = 0, sum_max_tok = 0;
-    int nrows = 0, ncomp = 0, nplanes = 0, lowcols = 0;
+    long long nplane = 0, ncoef = 0, sum_max_tok = 0, max_dtiles = 0;
+    int nrows = 0, ncomp = 0, nplanes = 0, lowcols = 0, ntiles = 0;
     // host tables (kept for the size estimate and the upload)
     std::vector<PDesc> h_pd;
     std::vector<int> h_blk_colour, h_blk_plane, h_blk_motion;
     std::vector<long long> h_row_off, h_comp_elem;
-    std::vector<int> h_row_w, h_row_stream, h_row_comp, h_comp_row0, h_comp_stream;
+    std::vector<int> h_row_w, h_row_stream, h_row_comp, h_comp_tile0, h_comp_stream;
+    std::vector<long long> h_tile_off;         // RLE tiles (RleTiles)
+    std::vector<int> h_tile_n, h_tile_w, h_tile_stream;
+    std::vector<uint8_t> h_tile_low;
     std::vector<uint8_t> h_row_low, h_comp_low, h_comp_level, h_comp_plane, h_comp_ey, h_comp_ex;
     long long luma_total = 0, mv_pairs = 0;   // motion: luma bytes per buffer, vector pairs
     int motion_threads = 128;                  // block size of the motion search
@@ -83,8 +86,11 @@ struct Core {
     PDesc* d_pd = nullptr;
     int *d_blk_colour = nullptr, *d_blk_plane = nullptr, *d_blk_motion = nullptr;
     long long *d_row_off = nullptr, *d_comp_elem = nullptr;
-    int *d_row_w = nullptr, *d_row_stream = nullptr, *d_row_comp = nullptr, *d_comp_row0 = nullptr,
+    int *d_row_w = nullptr, *d_row_stream = nullptr, *d_row_comp = nullptr, *d_comp_tile0 = nullptr,
         *d_comp_stream = nullptr;
+    long long* d_tile_off = nullptr;
+    int *d_tile_n = nullptr, *d_tile_w = nullptr, *d_tile_stream = nullptr;
+    uint8_t* d_tile_low = nullptr;
     std::vector<int4> h_row_mc;
     int4* d_row_mc = nullptr;
     uint8_t *d_row_low = nullptr, *d_comp_low = nullptr, *d_comp_level = nullptr, *d_comp_plane = nullptr,
@@ -94,9 +100,11 @@ struct Core {
     float *d_planes = nullptr, *d_rplanes = nullptr, *d_coef = nullptr, *d_dcoef = nullptr, *d_work = nullptr;
     int16_t *d_est_buf[2] = {nullptr, nullptr}, *d_dst_buf[2] = {nullptr, nullptr}, *d_res = nullptr;
     SCtl* d_ctl = nullptr;                     // device-resident coder state, one per stream
-    uint32_t *d_rowcnt = nullptr, *d_rowoff = nullptr, *d_scan_tmp = nullptr;
-    uint32_t *d_comp_tok = nullptr, *d_tok_base = nullptr, *d_contrib = nullptr, *d_pos = nullptr,
-             *d_scan_tmp2 = nullptr;
+    uint32_t *d_tilecnt = nullptr, *d_tileoff = nullptr, *d_scan_tmp = nullptr;
+    uint32_t *d_comp_tok = nullptr, *d_tok_base = nullptr, *d_scan_tmp2 = nullptr;
+    // the decoder's token tiles: first tile per stream, codes per tile, their exclusive scan,
+    // codes per component
+    uint32_t *d_dtile_base = nullptr, *d_dtile_sum = nullptr, *d_dtile_pre = nullptr, *d_comp_codes = nullptr;
     // pinned per-call records: a ring of slots, each a call's SCall and SResult
     // arrays; ring_ev[k] completes when the last step that used slot k has
     // copied its results back.  h_sc / h_rs point at the current slot.

@@ -569,12 +569,15 @@ __device__ __forceinline__ void ladder_quads(float* T, const float* S, float alp
         w.load(s + ia * CBS);
         quad_rowsums<NT, M>(w, g01[ia], g23[ia]);
     }
-#pragma unroll
-    for (int k = 0; k < KC; k++) {
-        if (NR % NWARPS != 0 && r0 + k >= R1) break;
+    // a rolled loop: the whole pass stays a few hundred instructions, so the
+    // blocks of an SM in their different phases share the instruction cache
+    const int steps = min(KC, R1 - r0);
+    s += (NT - 1) * CBS;
+#pragma unroll 1
+    for (int k = 0; k < steps; k++, s += CBS, t += CBS) {
         {
             QWin<NT, M> w;
-            w.load(s + (k + NT - 1) * CBS);
+            w.load(s);
             quad_rowsums<NT, M>(w, g01[NT - 1], g23[NT - 1]);
         }
         constexpr float b0 = fan_tap(NT, 0);
@@ -586,7 +589,7 @@ __device__ __forceinline__ void ladder_quads(float* T, const float* S, float alp
             a01 = __ffma2_rn(f2(bt, bt), g01[ia], a01);
             a23 = __ffma2_rn(f2(bt, bt), g23[ia], a23);
         }
-        float4* tp = reinterpret_cast<float4*>(t + k * CBS);
+        float4* tp = reinterpret_cast<float4*>(t);
         const float4 tv = *tp;
         const float2 o01 = __ffma2_rn(al, f2(tv.x, tv.y), __fmul2_rn(ga, a01));
         const float2 o23 = __ffma2_rn(al, f2(tv.z, tv.w), __fmul2_rn(ga, a23));
@@ -615,9 +618,11 @@ __device__ __forceinline__ void dfb_b_passes(float* F, float* Sx, const PassPara
 }
 
 // One tile of a row-split stage (sE, sO: BGeo<NT>::SMB floats of shared memory
-// each, 16-byte aligned).  The first DFBB_THREADS threads of the block do the
-// work; every thread of the block must call it (it holds barriers).
-template <bool SYN, int NT>
+// each, 16-byte aligned), first target coset odd (FO = pp.first_odd) or even;
+// RESIDENT: the channel arrays may live in shared memory (the tail kernel).
+// The first DFBB_THREADS threads of the block do the work; every thread of
+// the block must call it (it holds barriers).
+template <bool SYN, int NT, bool FO, bool RESIDENT>
 __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bases& B, const PassParams& pp,
                                            float* sE, float* sO) {
     using G = BGeo<NT>;
@@ -628,7 +633,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     constexpr int NW = DFBB_THREADS / 32;   // working warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool worker = threadIdx.x < DFBB_THREADS;
-    const int fo = pp.first_odd;
+    constexpr bool fo = FO;
     // the first target coset's array at the margin, the other D floats further
     float* const arrE = sE + G::MARGIN + (fo ? G::D : 0);
     float* const arrO = sO + G::MARGIN + (fo ? 0 : G::D);
@@ -639,7 +644,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     const float* const P0 = base_ptr(B, V0.b) + V0.off;
     const float* const P1 = base_ptr(B, V1.b) + V1.off;
     if (!worker) {
-    } else if (!__isShared(P0) && !__isShared(P1) && V0.cs == 1 && V1.cs == 1) {
+    } else if ((!RESIDENT || (!__isShared(P0) && !__isShared(P1))) && V0.cs == 1 && V1.cs == 1) {
         // row-major arrays.  Warp w stages rows w, w + NW, ... of both parities; lane
         // 2k + p first places row w + NW k of parity p (array row and start column, one
         // modular reduction for all of them), then the warp copies the rows one by one,
@@ -649,7 +654,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
         const int lp = lane & 1, rl0 = warp + NW * (lane >> 1), tl = t0 - R + rl0;
         const int vl = wrapd(c0 - rl0 - i * (2 * tl + lp), C);
         const float* rl = (lp ? P1 : P0) + (long long)wrapd(tl, R2) * (lp ? V1.rs : V0.rs);
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < 2 * RPW; k++) {
             const int r = warp + NW * (k >> 1);
             if (r >= RB) break;
@@ -671,7 +676,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
             const View V = par ? V1 : V0;
             const float* P = par ? P1 : P0;
             float* S = par ? arrO : arrE;
-            if (__isShared(P)) {
+            if (RESIDENT && __isShared(P)) {
                 // a tail kernel's resident channel array: plain copies of the sheared rows
                 for (int r = warp; r < RB; r += NW) {
                     const int tu = t0 - R + r;
@@ -709,7 +714,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     }
     cp_async_wait_all();
     __syncthreads();
-    if (fo) dfb_b_passes<NT, true>(arrO, arrE, pp);
+    if (FO) dfb_b_passes<NT, true>(arrO, arrE, pp);
     else dfb_b_passes<NT, false>(arrE, arrO, pp);
     __syncthreads();
     if (!worker) return;
@@ -727,7 +732,7 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
         const int lp = lane & 1, rl = warp + NW * (lane >> 1), tl = t0 + rl;
         const int vl = wrapd(c0 - rl - i * (2 * tl + lp), C);
         float* ql = (lp ? Q1 : Q0) + (long long)tl * (lp ? W1.rs : W0.rs);
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < 2 * RPW; k++) {
             const int rr = warp + NW * (k >> 1);
             if (t0 + rr >= R2) break;

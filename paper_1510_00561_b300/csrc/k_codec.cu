@@ -646,54 +646,116 @@ __global__ void k_mc_recon_b(const int16_t* __restrict__ res, int16_t* dst0, int
 }
 
 // ------------------------------------------------------------------ RLE
-// Rows of every component of every stream, in stream order.  Token count of
-// a row: one per non-zero code plus two per maximal zero run; raw rows
-// (K-frame lowpass) carry one token per code.
-__global__ void k_rle_count_b(const int16_t* __restrict__ res, RowTable rt, const SCall* __restrict__ sc,
-                              uint32_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= rt.nrows) return;
-    const SCall& C = sc[rt.stream[row]];
-    if (!C.enc_on) {
-        if (lane == 0) cnt[row] = 0;
-        return;
-    }
-    const long long off = rt.off[row];
-    const int w = rt.w[row];
-    if (C.enc_key && rt.low[row]) {
-        if (lane == 0) cnt[row] = (uint32_t)w;
-        return;
-    }
-    uint32_t n = 0;
-    bool prev_zero = false;
-    int16_t vn = lane < w ? res[off + lane] : (int16_t)1;     // the next chunk, loaded one chunk ahead
-    for (int x0 = 0; x0 < w; x0 += 32) {
-        int x = x0 + lane;
-        bool valid = x < w;
-        const int16_t v = vn;
-        if (x + 32 < w) vn = res[off + x + 32];
-        bool z = valid && v == 0;
-        unsigned zb = __ballot_sync(0xffffffffu, z);
-        unsigned vb = __ballot_sync(0xffffffffu, valid);
-        unsigned starts = zb & ~((zb << 1) | (prev_zero ? 1u : 0u));
-        n += __popc(vb & ~zb) + 2 * __popc(starts);
-        prev_zero = (zb >> 31) & 1u;
-    }
-    if (lane == 0) cnt[row] = n;
+// Work units are tiles: runs of whole rows of one component (all of width w),
+// in stream order, of at most RLE_TILE codes unless one row is longer.  A
+// row's tokens (§3.8): one per non-zero code and two (0, n) per maximal zero
+// run; the rows of a K-frame lowpass are stored raw, one token per code.
+// A token's position in its stream is the exclusive scan of the tiles' token
+// counts plus its place inside the tile, so the rows of a tile need no table.
+//
+// A thread takes 8 consecutive codes (one 16-byte load) and describes them by
+// bit masks: inside the tile, non-zero, start and end of a zero run (a zero
+// whose predecessor, resp. successor, in the row is non-zero or absent).
+
+struct RleChunk {
+    uint32_t w[4];          // the 8 codes, two per word, low half first
+    unsigned nz, rs, re;    // non-zero codes, zero-run starts, zero-run ends (inside the tile)
+};
+
+__device__ __forceinline__ int16_t chunk_code(const RleChunk& k, int j) {
+    const uint32_t v = (j & 4) ? ((j & 2) ? k.w[3] : k.w[2]) : ((j & 2) ? k.w[1] : k.w[0]);
+    return (int16_t)(uint16_t)((j & 1) ? (v >> 16) : (v & 0xFFFFu));
 }
 
-__device__ __forceinline__ void put_tok(int16_t* tok, uint32_t pos, uint32_t cap_tok, int16_t v, uint32_t* err) {
-    if (pos < cap_tok) tok[pos] = v;
-    else atomicOr(err, EF_CAPACITY);
+// the codes g .. g+7 (g a multiple of 8, g + 8 > e0) of the tile [e0, e1) of rows of width w
+__device__ __forceinline__ RleChunk rle_chunk(const int16_t* __restrict__ res, long long g, long long e0, long long e1,
+                                              int w) {
+    RleChunk k;
+    const int4 v = *reinterpret_cast<const int4*>(res + g);
+    k.w[0] = (uint32_t)v.x;
+    k.w[1] = (uint32_t)v.y;
+    k.w[2] = (uint32_t)v.z;
+    k.w[3] = (uint32_t)v.w;
+    const int rel = (int)(g - e0);                 // tile index of code 0 (negative in the first chunk)
+    const int jf = rel < 0 ? -rel : 0;             // first code inside the tile
+    const int jl = (int)min(8LL, e1 - g);          // one past the last
+    const unsigned valid = (jl > jf ? (1u << jl) - (1u << jf) : 0u);
+    unsigned zero = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint32_t z = __vcmpeq2(k.w[q], 0u);  // 0xFFFF per zero half
+        zero |= ((z & 1u) | ((z >> 15) & 2u)) << (2 * q);
+    }
+    zero &= valid;
+    // row starts and ends among codes jf .. 7; code jf sits at row position p0
+    const int p0 = (rel + jf) % w;
+    unsigned rstart = 0, rend = 0;
+    if (w >= 8) {
+        const int js = jf + (p0 == 0 ? 0 : w - p0), je = jf + w - 1 - p0;
+        rstart = js < 8 ? 1u << js : 0u;
+        rend = je < 8 ? 1u << je : 0u;
+    } else {
+        int p = p0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (j >= jf) {
+                rstart |= (p == 0 ? 1u : 0u) << j;
+                rend |= (p == w - 1 ? 1u : 0u) << j;
+                p = p + 1 == w ? 0 : p + 1;
+            }
+        }
+    }
+    // the codes just outside the chunk, where they are in the tile
+    const bool zprev = jf == 0 && rel > 0 && res[g - 1] == 0;
+    const bool znext = g + 8 < e1 && res[g + 8] == 0;
+    const unsigned zp = (zero << 1) | (zprev ? 1u : 0u);   // zero-ness of each code's predecessor
+    const unsigned zn = (zero >> 1) | (znext ? 0x80u : 0u); // ... and successor
+    k.nz = valid & ~zero;
+    k.rs = zero & (rstart | ~zp);
+    k.re = zero & (rend | ~zn);
+    return k;
 }
 
-__global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, const SDesc* __restrict__ sd,
-                              const SCall* __restrict__ sc, const uint32_t* __restrict__ tokoff, SResult* out) {
-    const int lane = threadIdx.x & 31;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= rt.nrows) return;
-    const int s = rt.stream[row];
+__device__ __forceinline__ bool rle_raw(const SCall& C, const RleTiles& tt, int tile) {
+    return C.enc_key && tt.low[tile];
+}
+
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_count_b(const int16_t* __restrict__ res, RleTiles tt,
+                                                              const SCall* __restrict__ sc, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t s_part[RLE_THREADS / 32];
+    const int tile = blockIdx.x;
+    const SCall& C = sc[tt.stream[tile]];
+    const long long e0 = tt.off[tile];
+    const int n = tt.n[tile];
+    if (!C.enc_on || rle_raw(C, tt, tile)) {
+        if (threadIdx.x == 0) cnt[tile] = C.enc_on ? (uint32_t)n : 0u;
+        return;
+    }
+    const long long e1 = e0 + n;
+    const int w = tt.w[tile];
+    uint32_t c = 0;
+    for (long long g = (e0 & ~7LL) + 8LL * threadIdx.x; g < e1; g += RLE_CHUNK) {
+        const RleChunk k = rle_chunk(res, g, e0, e1, w);
+        c += __popc(k.nz) + 2 * __popc(k.rs);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int i = 0; i < RLE_THREADS / 32; i++) t += s_part[i];
+        cnt[tile] = t;
+    }
+}
+
+__global__ void __launch_bounds__(RLE_THREADS) k_rle_write_b(const int16_t* __restrict__ res, RleTiles tt,
+                                                              const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+                                                              const uint32_t* __restrict__ tileoff, SResult* out) {
+    __shared__ uint32_t s_sum[RLE_THREADS / 32];
+    __shared__ int s_max[RLE_THREADS / 32];
+    const int tile = blockIdx.x;
+    const int s = tt.stream[tile];
     const SCall& C = sc[s];
     if (!C.enc_on) return;
     const SDesc& D = sd[s];
@@ -701,66 +763,108 @@ __global__ void k_rle_write_b(const int16_t* __restrict__ res, RowTable rt, cons
     int16_t* tok = reinterpret_cast<int16_t*>(C.out + D.hdr_bytes);
     const long long capl = (C.out_cap - D.hdr_bytes) / 2;
     const uint32_t cap_tok = (uint32_t)(capl > 0xFFFFFFFFLL ? 0xFFFFFFFFLL : capl);
-    uint32_t* err = &out[s].enc_err;
-    const long long off = rt.off[row];
-    const int w = rt.w[row];
-    uint32_t pos = tokoff[row] - tokoff[D.row0];
-    if (C.enc_key && rt.low[row]) {
-        for (int x = lane; x < w; x += 32) put_tok(tok, pos + x, cap_tok, res[off + x], err);
-        return;
-    }
-    const unsigned lt = (1u << lane) - 1u;
-    bool prev_zero = false;
-    uint32_t open_pos = 0;   // token position of the marker of a run left open by the previous chunk
-    int open_x = 0;
-    int16_t vn = lane < w ? res[off + lane] : (int16_t)1;     // the next chunk, loaded one chunk ahead
-    for (int x0 = 0; x0 < w; x0 += 32) {
-        int x = x0 + lane;
-        bool valid = x < w;
-        const int16_t v = valid ? vn : (int16_t)1;
-        if (x + 32 < w) vn = res[off + x + 32];
-        bool z = valid && v == 0;
-        unsigned zb = __ballot_sync(0xffffffffu, z);
-        unsigned vb = __ballot_sync(0xffffffffu, valid);
-        unsigned starts = zb & ~((zb << 1) | (prev_zero ? 1u : 0u));
-        unsigned nz = vb & ~zb;
-        bool start = (starts >> lane) & 1u;
-        uint32_t my = pos + __popc(nz & lt) + 2 * __popc(starts & lt);
-        if (valid && !z) put_tok(tok, my, cap_tok, v, err);
-        if (start) put_tok(tok, my, cap_tok, 0, err);
-        // the run containing this lane started at the highest start lane <= lane, or before the chunk
-        unsigned le = starts & (lt | (1u << lane));
-        int sl = le ? 31 - __clz(le) : -1;
-        uint32_t spos = __shfl_sync(0xffffffffu, my, sl < 0 ? 0 : sl);
-        int sx = sl < 0 ? open_x : x0 + sl;
-        if (sl < 0) spos = open_pos;
-        // this lane ends its run if it is zero and the next element is not (or the row ends)
-        // the element after lane 31 is the first of the next chunk (lane 0's prefetched value)
-        const int16_t after = __shfl_sync(0xffffffffu, vn, 0);
-        bool next_zero;
-        if (lane < 31) next_zero = (zb >> (lane + 1)) & 1u;
-        else next_zero = (x + 1 < w) && after == 0;
-        if (z && !next_zero) put_tok(tok, spos + 1, cap_tok, (int16_t)(x - sx + 1), err);
-        uint32_t spos31 = __shfl_sync(0xffffffffu, spos, 31);
-        int sx31 = __shfl_sync(0xffffffffu, sx, 31);
-        prev_zero = (zb >> 31) & 1u;
-        if (prev_zero) {
-            open_pos = spos31;
-            open_x = sx31;
+    const long long e0 = tt.off[tile];
+    const int n = tt.n[tile];
+    const uint32_t pos0 = tileoff[tile] - tileoff[D.tile0];
+    bool over = false;
+    if (rle_raw(C, tt, tile)) {
+        for (int x = threadIdx.x; x < n; x += RLE_THREADS) {
+            const uint32_t p = pos0 + x;
+            if (p < cap_tok) tok[p] = res[e0 + x];
+            else over = true;
         }
-        pos += __popc(nz) + 2 * __popc(starts);
+    } else {
+        const long long e1 = e0 + n;
+        const int w = tt.w[tile];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t carry = 0;     // tokens of the tile's earlier chunks
+        int carry_s = -1;       // latest zero-run start among them (tile index)
+        for (long long gb = e0 & ~7LL; gb < e1; gb += RLE_CHUNK) {
+            const long long g = gb + 8LL * threadIdx.x;
+            RleChunk k;
+            if (g < e1) k = rle_chunk(res, g, e0, e1, w);
+            else k.nz = k.rs = k.re = 0u;
+            const int rel = (int)(g - e0);
+            const uint32_t cn = __popc(k.nz) + 2 * __popc(k.rs);
+            const int ls = k.rs ? rel + 31 - __clz(k.rs) : -1;
+            // block scans: exclusive token offset, latest run start before this chunk
+            uint32_t x = cn;
+            int mx = ls;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                const int ym = __shfl_up_sync(0xffffffffu, mx, o);
+                if (lane >= o) {
+                    x += y;
+                    mx = max(mx, ym);
+                }
+            }
+            int mprev = __shfl_up_sync(0xffffffffu, mx, 1);
+            if (lane == 0) mprev = -1;
+            if (lane == 31) {
+                s_sum[warp] = x;
+                s_max[warp] = mx;
+            }
+            __syncthreads();
+            uint32_t wpre = 0, tot = 0;
+            int wmax = -1, bmax = -1;
+#pragma unroll
+            for (int i = 0; i < RLE_THREADS / 32; i++) {
+                const uint32_t a = s_sum[i];
+                const int b = s_max[i];
+                if (i < warp) {
+                    wpre += a;
+                    wmax = max(wmax, b);
+                }
+                tot += a;
+                bmax = max(bmax, b);
+            }
+            const uint32_t tpos = pos0 + carry + wpre + x - cn;
+            const int sprev = max(carry_s, max(wmax, mprev));
+            unsigned m = k.nz | k.rs | k.re;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned bit = 1u << j, below = bit - 1u;
+                const uint32_t pj = tpos + __popc(k.nz & below) + 2 * __popc(k.rs & below);
+                uint32_t p1 = pj, p2 = 0xFFFFFFFFu;
+                int16_t v1 = 0, v2 = 0;
+                if (k.nz & bit) v1 = chunk_code(k, j);   // a non-zero code, or a run's marker (0)
+                if (k.re & bit) {
+                    // the count of the run this code ends, after the run's marker
+                    const unsigned le = k.rs & (below | bit);
+                    const int sr = le ? rel + 31 - __clz(le) : sprev;
+                    const int er = rel + j;
+                    p2 = sr == er ? pj + 1 : pj - 1;
+                    v2 = (int16_t)(er - sr + 1);
+                    if (!(k.rs & bit)) p1 = 0xFFFFFFFFu;   // a run's last code writes only its count
+                }
+                if (p1 != 0xFFFFFFFFu) {
+                    if (p1 < cap_tok) tok[p1] = v1;
+                    else over = true;
+                }
+                if (p2 != 0xFFFFFFFFu) {
+                    if (p2 < cap_tok) tok[p2] = v2;
+                    else over = true;
+                }
+            }
+            carry += tot;
+            carry_s = max(carry_s, bmax);
+            __syncthreads();    // the scan arrays are reused by the next chunk
+        }
     }
+    if (over) atomicOr(&out[s].enc_err, EF_CAPACITY);
 }
 
 // one block per stream: header, component token counts, motion vectors, capacity check
 __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                                  const uint32_t* __restrict__ tokoff, CompTable ct, const int8_t* __restrict__ mv,
+                                  const uint32_t* __restrict__ tileoff, CompTable ct, const int8_t* __restrict__ mv,
                                   SResult* out) {
     const int s = blockIdx.x;
     const SCall& C = sc[s];
     if (!C.enc_on) return;
     const SDesc& D = sd[s];
-    const uint32_t tokens = tokoff[D.row0 + D.nrows] - tokoff[D.row0];
+    const uint32_t tokens = tileoff[D.tile0 + D.ntiles] - tileoff[D.tile0];
     const bool mc = !C.enc_key && D.mv_range > 0;
     const long long need = D.hdr_bytes + 2LL * tokens + (mc ? D.mv_bytes : 0);
     if (threadIdx.x == 0) {
@@ -786,7 +890,7 @@ __global__ void k_stream_header_b(const SDesc* __restrict__ sd, const SCall* __r
     }
     for (int c = threadIdx.x; c < D.ncomp; c += blockDim.x) {
         const int g = D.comp0 + c;
-        reinterpret_cast<uint32_t*>(o + 32)[c] = tokoff[ct.row0[g + 1]] - tokoff[ct.row0[g]];
+        reinterpret_cast<uint32_t*>(o + 32)[c] = tileoff[ct.tile0[g + 1]] - tileoff[ct.tile0[g]];
     }
     // the vectors follow the tokens
     if (mc && need <= C.out_cap) {
@@ -905,103 +1009,152 @@ __global__ void k_dec_parse_b(const SDesc* __restrict__ sd, const SCall* __restr
     }
 }
 
-// exclusive scan of the streams' token counts: the base of each stream in
-// the compact token space of this call; tok_base[n] = all tokens
+// Token tiles of the decoder: every stream's tokens cut into tiles of
+// DEC_TILE (a stream's last tile may be short), numbered stream after stream.
+// k_dec_base_b: per stream the first token of the call's compact token space
+// and the first tile; tile_base[n] = all tiles.
 __global__ void k_dec_base_b(const SDesc* __restrict__ sd, int nstreams, const SResult* __restrict__ rs,
-                             uint32_t* __restrict__ tok_base) {
+                             uint32_t* __restrict__ tok_base, uint32_t* __restrict__ tile_base) {
     (void)sd;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    uint32_t acc = 0;
+    uint32_t acc = 0, tiles = 0;
     for (int s = 0; s < nstreams; s++) {
         tok_base[s] = acc;
+        tile_base[s] = tiles;
         acc += rs[s].dec_tokens;
+        tiles += (rs[s].dec_tokens + DEC_TILE - 1) / DEC_TILE;
     }
     tok_base[nstreams] = acc;
+    tile_base[nstreams] = tiles;
 }
 
-__device__ __forceinline__ int find_last_le(const uint32_t* a, int lo, int hi, uint32_t t) {
-    // largest i in [lo, hi) with a[i] <= t (a non-decreasing, a[lo] <= t)
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (a[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// per token of the compact token space: stream, local index, component and its end
-struct TokCtx {
-    int s, c;
-    uint32_t t, c0, c1;
+// The DEC_PER_THREAD tokens of one thread: values, codes produced (raw and
+// value tokens one, counts n, markers none), component of each token, and
+// whether the group broke a rule of the format.
+struct DecGroup {
+    int16_t v[DEC_PER_THREAD];
+    uint32_t n[DEC_PER_THREAD];
+    int comp[DEC_PER_THREAD];     // global component index; -1 past the stream's last token
+    bool code[DEC_PER_THREAD];    // the token is a code (raw or non-zero value) to place
+    bool bad;
 };
-__device__ __forceinline__ TokCtx tok_ctx(uint32_t g, const SDesc* sd, const SResult* rs, const uint32_t* tok_base,
-                                          int nstreams, const uint32_t* comp_tok) {
-    TokCtx k;
-    // the stream whose range [tok_base[s], tok_base[s+1]) holds g (empty ranges skipped)
-    int lo = 0, hi = nstreams;
+
+// the tile's stream (thread 0 searches; the block reads it from shared memory)
+__device__ __forceinline__ int dec_tile_stream(const uint32_t* tile_base, int nstreams, int tile, int* s_sh) {
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nstreams;   // largest s with tile_base[s] <= tile (skips streams without tiles)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tile_base[mid] <= (uint32_t)tile) lo = mid;
+            else hi = mid;
+        }
+        *s_sh = lo;
+    }
+    __syncthreads();
+    return *s_sh;
+}
+
+// tokens t0 .. t0 + DEC_PER_THREAD - 1 of stream s (t0 a multiple of DEC_PER_THREAD);
+// ctok: the stream's component token offsets in shared memory (ncomp of them)
+__device__ __forceinline__ DecGroup dec_group(const uint8_t* tok, uint32_t t0, uint32_t ntok, const uint32_t* ctok,
+                                              int ncomp, int comp0, bool key, const CompTable& ct) {
+    DecGroup G;
+    G.bad = false;
+    // the group's values (4-byte loads where the token array allows them)
+    if ((reinterpret_cast<uintptr_t>(tok) & 3) == 0) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(tok + 2ull * t0);
+#pragma unroll
+        for (int k = 0; k < DEC_PER_THREAD / 2; k++) {
+            // the word of the stream's last token may reach 2 bytes past it, inside that aligned word
+            const uint32_t x = t0 + 2 * k < ntok ? w[k] : 0u;
+            G.v[2 * k] = (int16_t)(uint16_t)(x & 0xFFFFu);
+            G.v[2 * k + 1] = (int16_t)(uint16_t)(x >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DEC_PER_THREAD; k++) G.v[k] = t0 + k < ntok ? rd16(tok + 2ull * (t0 + k)) : (int16_t)0;
+    }
+    int16_t prev = t0 > 0 ? rd16(tok + 2ull * (t0 - 1)) : (int16_t)1;
+    // the component of t0: largest c with ctok[c] <= t0
+    int lo = 0, hi = ncomp;
     while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (tok_base[mid] <= g) lo = mid;
+        const int mid = (lo + hi) >> 1;
+        if (ctok[mid] <= t0) lo = mid;
         else hi = mid;
     }
-    k.s = lo;
-    const SDesc& D = sd[k.s];
-    k.t = g - tok_base[k.s];
-    k.c = find_last_le(comp_tok, D.comp0, D.comp0 + D.ncomp, k.t);
-    k.c0 = comp_tok[k.c];
-    k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
-    return k;
-}
-
-// elements produced by each token: value (and raw K-lowpass) tokens 1,
-// zero markers 0, run counts n.  A thread takes TOK_GROUP consecutive tokens:
-// one search for the first token's stream and component, then a forward walk.
-constexpr int TOK_GROUP = 8;
-
-__device__ __forceinline__ void tok_advance(TokCtx& k, uint32_t g, const SDesc* sd, const SResult* rs,
-                                            const uint32_t* tok_base, int nstreams, const uint32_t* comp_tok) {
-    // move k (valid for some g' < g) forward to token g
-    while (k.s + 1 < nstreams && g >= tok_base[k.s + 1]) {
-        k.s++;
-        k.c = sd[k.s].comp0;
-        k.c0 = comp_tok[k.c];
-        const SDesc& D = sd[k.s];
-        k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
-    }
-    k.t = g - tok_base[k.s];
-    const SDesc& D = sd[k.s];
-    while (k.t >= k.c1 && k.c + 1 < D.comp0 + D.ncomp) {
-        k.c++;
-        k.c0 = k.c1;
-        k.c1 = (k.c + 1 < D.comp0 + D.ncomp) ? comp_tok[k.c + 1] : rs[k.s].dec_tokens;
-    }
-}
-
-__global__ void k_dec_contrib_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                                const SResult* __restrict__ rs, const uint32_t* __restrict__ tok_base, int nstreams,
-                                const uint32_t* __restrict__ comp_tok, CompTable ct, uint32_t* __restrict__ contrib,
-                                SResult* out) {
-    const uint32_t total = tok_base[nstreams];
-    const uint32_t stride = gridDim.x * blockDim.x * TOK_GROUP;
-    for (uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) * TOK_GROUP; g0 < total; g0 += stride) {
-        TokCtx k = tok_ctx(g0, sd, rs, tok_base, nstreams, comp_tok);
-        const uint32_t g1 = min(total, g0 + TOK_GROUP);
-        for (uint32_t g = g0; g < g1; g++) {
-            if (g > g0) tok_advance(k, g, sd, rs, tok_base, nstreams, comp_tok);
-            const uint8_t* tok = sc[k.s].in + sd[k.s].hdr_bytes;
-            const int16_t v = rd16(tok + 2LL * k.t);
-            uint32_t n;
-            if (rs[k.s].dec_type == 0 && ct.low[k.c]) n = 1;
-            else if (k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0) {
-                n = v > 0 ? (uint32_t)v : 0;
-                if (v <= 0) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
-            } else if (v != 0) n = 1;
-            else {
-                n = 0;
-                if (k.t + 1 >= k.c1) atomicOr(&out[k.s].dec_err, EF_CORRUPT);
+    int c = lo;
+    uint32_t c0 = ctok[c], c1 = c + 1 < ncomp ? ctok[c + 1] : ntok;
+#pragma unroll
+    for (int k = 0; k < DEC_PER_THREAD; k++) {
+        const uint32_t t = t0 + k;
+        G.n[k] = 0;
+        G.code[k] = false;
+        G.comp[k] = -1;
+        if (t < ntok) {
+            while (t >= c1 && c + 1 < ncomp) {
+                c++;
+                c0 = c1;
+                c1 = c + 1 < ncomp ? ctok[c + 1] : ntok;
             }
-            contrib[g] = n;
+            G.comp[k] = comp0 + c;
+            const int16_t v = G.v[k];
+            if (key && ct.low[comp0 + c]) {
+                G.n[k] = 1;                      // a K-frame lowpass code, stored raw
+                G.code[k] = true;
+            } else if (t > c0 && prev == 0) {
+                // the count of the zero run opened by the previous token
+                if (v > 0) G.n[k] = (uint32_t)v;
+                else G.bad = true;
+            } else if (v != 0) {
+                G.n[k] = 1;
+                G.code[k] = true;
+            } else if (t + 1 >= c1) {
+                G.bad = true;                    // a run marker without its count
+            }
         }
+        prev = G.v[k];
+    }
+    return G;
+}
+
+// codes produced by every token tile (a grid-stride loop over the call's tiles)
+__global__ void __launch_bounds__(DEC_THREADS) k_dec_count_b(const SDesc* __restrict__ sd,
+                                                              const SCall* __restrict__ sc,
+                                                              const SResult* __restrict__ rs,
+                                                              const uint32_t* __restrict__ tile_base, int nstreams,
+                                                              const uint32_t* __restrict__ comp_tok, CompTable ct,
+                                                              uint32_t* __restrict__ tile_sum, SResult* out) {
+    __shared__ int s_stream;
+    __shared__ uint32_t s_part[DEC_THREADS / 32];
+    __shared__ uint32_t s_ctok[DEC_MAX_COMP];
+    const int ntiles = (int)tile_base[nstreams];
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int s = dec_tile_stream(tile_base, nstreams, tile, &s_stream);
+        const SDesc& D = sd[s];
+        for (int i = threadIdx.x; i < D.ncomp; i += DEC_THREADS) s_ctok[i] = comp_tok[D.comp0 + i];
+        __syncthreads();
+        const uint32_t ntok = rs[s].dec_tokens;
+        const uint32_t t0 = (uint32_t)(tile - (int)tile_base[s]) * DEC_TILE + DEC_PER_THREAD * threadIdx.x;
+        uint32_t sum = 0;
+        bool bad = false;
+        if (t0 < ntok) {
+            const DecGroup G = dec_group(sc[s].in + D.hdr_bytes, t0, ntok, s_ctok, D.ncomp, D.comp0,
+                                         rs[s].dec_type == 0, ct);
+#pragma unroll
+            for (int k = 0; k < DEC_PER_THREAD; k++) sum += G.n[k];
+            bad = G.bad;
+        }
+        if (bad) atomicOr(&out[s].dec_err, EF_CORRUPT);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int i = 0; i < DEC_THREADS / 32; i++) t += s_part[i];
+            tile_sum[tile] = t;
+        }
+        __syncthreads();   // shared arrays are reused by the next tile
     }
 }
 
@@ -1021,50 +1174,104 @@ __device__ __forceinline__ long long dense_to_layout(const SDesc& D, int d, long
     return D.pstart[q] + (u < D.nlow[q] ? u : u + D.absent[d][q]);
 }
 
+// every token tile again: the position of each code (its tile's exclusive
+// prefix inside the stream plus a block scan), the codes placed into the
+// zeroed residual frame, and the codes of each component summed for the check
+__global__ void __launch_bounds__(DEC_THREADS) k_dec_scatter_b(const SDesc* __restrict__ sd,
+                                                                const SCall* __restrict__ sc,
+                                                                const SResult* __restrict__ rs,
+                                                                const uint32_t* __restrict__ tile_base, int nstreams,
+                                                                const uint32_t* __restrict__ comp_tok, CompTable ct,
+                                                                const uint32_t* __restrict__ tile_pre,
+                                                                uint32_t* __restrict__ comp_codes,
+                                                                int16_t* __restrict__ res) {
+    __shared__ int s_stream;
+    __shared__ uint32_t s_part[DEC_THREADS / 32];
+    __shared__ uint32_t s_ctok[DEC_MAX_COMP];
+    __shared__ uint32_t s_cc[DEC_MAX_COMP];     // codes of the tile per component of its stream
+    const int ntiles = (int)tile_base[nstreams];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int s = dec_tile_stream(tile_base, nstreams, tile, &s_stream);
+        const SDesc& D = sd[s];
+        for (int i = threadIdx.x; i < D.ncomp; i += DEC_THREADS) {
+            s_ctok[i] = comp_tok[D.comp0 + i];
+            s_cc[i] = 0;
+        }
+        __syncthreads();
+        const uint32_t ntok = rs[s].dec_tokens;
+        const uint32_t t0 = (uint32_t)(tile - (int)tile_base[s]) * DEC_TILE + DEC_PER_THREAD * threadIdx.x;
+        DecGroup G;
+        uint32_t sum = 0;
+        if (t0 < ntok) {
+            G = dec_group(sc[s].in + D.hdr_bytes, t0, ntok, s_ctok, D.ncomp, D.comp0, rs[s].dec_type == 0, ct);
+#pragma unroll
+            for (int k = 0; k < DEC_PER_THREAD; k++) sum += G.n[k];
+        }
+        // block exclusive scan of the threads' codes
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_part[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int i = 0; i < DEC_THREADS / 32; i++)
+            if (i < warp) wpre += s_part[i];
+        // codes per component: the group's first component's codes are summed over the
+        // lanes sharing it (one shared-memory add per component per warp), the rest added alone
+        int cfirst = -1;
+        uint32_t cs_first = 0;
+        if (t0 < ntok) {
+            const int d = min((int)rs[s].dec_drop, CVC_MAX_LEVELS);
+            const long long ndense = D.ncoef - absent_before(D, d, 3);
+            long long p = (long long)(tile_pre[tile] - tile_pre[tile_base[s]]) + wpre + x - sum;
+            cfirst = G.comp[0] - D.comp0;
+            int cprev = cfirst;
+            uint32_t csum = 0;
+#pragma unroll
+            for (int k = 0; k < DEC_PER_THREAD; k++) {
+                if (G.comp[k] < 0) break;
+                const int cl = G.comp[k] - D.comp0;
+                if (cl != cprev) {
+                    if (cprev == cfirst) cs_first = csum;
+                    else if (csum) atomicAdd(&s_cc[cprev], csum);
+                    cprev = cl;
+                    csum = 0;
+                }
+                csum += G.n[k];
+                if (G.code[k] && p >= 0 && p < ndense) res[D.coef_off + (d > 0 ? dense_to_layout(D, d, p) : p)] = G.v[k];
+                p += G.n[k];
+            }
+            if (cprev == cfirst) cs_first = csum;
+            else if (csum) atomicAdd(&s_cc[cprev], csum);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, cfirst);
+        const uint32_t tot = __reduce_add_sync(peers, cs_first);
+        if (cfirst >= 0 && lane == __ffs(peers) - 1 && tot) atomicAdd(&s_cc[cfirst], tot);
+        __syncthreads();
+        for (int i = threadIdx.x; i < D.ncomp; i += DEC_THREADS)
+            if (s_cc[i]) atomicAdd(&comp_codes[D.comp0 + i], s_cc[i]);
+        __syncthreads();   // shared arrays are reused by the next tile
+    }
+}
+
 // every component must expand to exactly its number of codes (none if dropped)
 __global__ void k_dec_check_b(const SDesc* __restrict__ sd, const SResult* __restrict__ rs,
-                              const uint32_t* __restrict__ tok_base, const uint32_t* __restrict__ comp_tok,
-                              const uint32_t* __restrict__ pos, CompTable ct, SResult* out) {
+                              const uint32_t* __restrict__ comp_codes, CompTable ct, SResult* out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ct.ncomp) return;
     const int s = ct.stream[c];
     if (rs[s].dec_tokens == 0) return;        // not decoding, or the header was rejected
     const SDesc& D = sd[s];
     const int d = min((int)rs[s].dec_drop, CVC_MAX_LEVELS);
-    const int q = ct.plane[c], lv = ct.level[c];
-    long long before = absent_before(D, d, q);
-    if (lv >= 1 && lv <= d) before += ct.elem[c] - D.pstart[q] - D.nlow[q];
-    else if (lv > d) before += D.absent[d][q];
-    const uint32_t b = tok_base[s];
-    const uint32_t p0 = pos[b];
-    if ((long long)(pos[b + comp_tok[c]] - p0) != ct.elem[c] - before) atomicOr(&out[s].dec_err, EF_CORRUPT);
-    if (c == D.comp0 + D.ncomp - 1 &&
-        (long long)(pos[b + rs[s].dec_tokens] - p0) != D.ncoef - absent_before(D, d, 3))
-        atomicOr(&out[s].dec_err, EF_CORRUPT);
-}
-
-__global__ void k_dec_scatter_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
-                                const SResult* __restrict__ rs, const uint32_t* __restrict__ tok_base, int nstreams,
-                                const uint32_t* __restrict__ comp_tok, CompTable ct, const uint32_t* __restrict__ pos,
-                                int16_t* __restrict__ res) {
-    const uint32_t total = tok_base[nstreams];
-    const uint32_t stride = gridDim.x * blockDim.x * TOK_GROUP;
-    for (uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) * TOK_GROUP; g0 < total; g0 += stride) {
-        TokCtx k = tok_ctx(g0, sd, rs, tok_base, nstreams, comp_tok);
-        const uint32_t g1 = min(total, g0 + TOK_GROUP);
-        for (uint32_t g = g0; g < g1; g++) {
-            if (g > g0) tok_advance(k, g, sd, rs, tok_base, nstreams, comp_tok);
-            const SDesc& D = sd[k.s];
-            const uint8_t* tok = sc[k.s].in + D.hdr_bytes;
-            const int16_t v = rd16(tok + 2LL * k.t);
-            const bool raw = rs[k.s].dec_type == 0 && ct.low[k.c];
-            const bool count = !raw && k.t > k.c0 && rd16(tok + 2LL * (k.t - 1)) == 0;
-            long long p = (long long)pos[g] - (long long)pos[tok_base[k.s]];
-            const int d = min((int)rs[k.s].dec_drop, CVC_MAX_LEVELS);
-            if (d > 0) p = dense_to_layout(D, d, p);
-            if ((raw || (v != 0 && !count)) && p >= 0 && p < D.ncoef) res[D.coef_off + p] = v;
-        }
-    }
+    const int lv = ct.level[c];
+    const long long size = (c + 1 < D.comp0 + D.ncomp ? ct.elem[c + 1] : D.ncoef) - ct.elem[c];
+    const long long want = (lv >= 1 && lv <= d) ? 0 : size;
+    if ((long long)comp_codes[c] != want) atomicOr(&out[s].dec_err, EF_CORRUPT);
 }
 
 // ------------------------------------------------------ exclusive scans

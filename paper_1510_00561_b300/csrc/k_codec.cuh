@@ -38,6 +38,7 @@ struct SDesc {
     long long coef_off;    // coefficients of this stream in the frame buffers
     long long ncoef;
     int row0, nrows;       // its component rows in the row table
+    int tile0, ntiles;     // its RLE tiles
     int comp0, ncomp;      // its components in the component table
     long long hdr_bytes;   // 32 + 4 * ncomp
     long long max_tok;     // largest valid token count of one frame
@@ -146,8 +147,20 @@ struct RowTable {
     int nrows;
 };
 
+// RLE work units: whole rows of one component (all of one width), in stream
+// order; at most RLE_TILE codes unless a single row is longer
+struct RleTiles {
+    const long long* off;     // global coefficient index of the tile's first code
+    const int* n;             // codes
+    const int* w;             // row width
+    const int* stream;
+    const uint8_t* low;       // rows of a lowpass component (raw in a K-frame)
+    int ntiles;
+};
+constexpr int RLE_THREADS = 256, RLE_PER_THREAD = 8, RLE_CHUNK = RLE_THREADS * RLE_PER_THREAD, RLE_TILE = 4096;
+
 struct CompTable {
-    const int* row0;          // first row of the component (global)
+    const int* tile0;         // first RLE tile of the component (global)
     const uint8_t* low;
     const int* stream;
     const long long* elem;    // element offset of the component inside its stream
@@ -188,22 +201,27 @@ __global__ void k_unquant_b(const int16_t* res, int16_t* dst0, int16_t* dst1, co
                             const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
 __global__ void k_unquant_keylow_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, int nplanes,
                                    const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
-__global__ void k_rle_count_b(const int16_t* res, RowTable rt, const SCall* sc, uint32_t* cnt);
-__global__ void k_rle_write_b(const int16_t* res, RowTable rt, const SDesc* sd, const SCall* sc,
-                              const uint32_t* tokoff, SResult* out);
-__global__ void k_stream_header_b(const SDesc* sd, const SCall* sc, const uint32_t* tokoff, CompTable ct,
+// RLE: one block of RLE_THREADS per tile; token counts, then (after their
+// exclusive scan) the tokens; the header writes the component counts
+__global__ void k_rle_count_b(const int16_t* res, RleTiles tt, const SCall* sc, uint32_t* cnt);
+__global__ void k_rle_write_b(const int16_t* res, RleTiles tt, const SDesc* sd, const SCall* sc,
+                              const uint32_t* tileoff, SResult* out);
+__global__ void k_stream_header_b(const SDesc* sd, const SCall* sc, const uint32_t* tileoff, CompTable ct,
                                   const int8_t* mv, SResult* out);
 __global__ void k_dec_parse_b(const SDesc* sd, const SCall* sc, const SResult* enc, CompTable ct,
                               uint32_t* comp_tok, SResult* out);
-__global__ void k_dec_base_b(const SDesc* sd, int nstreams, const SResult* rs, uint32_t* tok_base);
-__global__ void k_dec_contrib_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tok_base,
-                                int nstreams, const uint32_t* comp_tok, CompTable ct, uint32_t* contrib,
-                                SResult* out);
-__global__ void k_dec_check_b(const SDesc* sd, const SResult* rs, const uint32_t* tok_base, const uint32_t* comp_tok,
-                              const uint32_t* pos, CompTable ct, SResult* out);
-__global__ void k_dec_scatter_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tok_base,
-                                int nstreams, const uint32_t* comp_tok, CompTable ct, const uint32_t* pos,
-                                int16_t* res);
+__global__ void k_dec_base_b(const SDesc* sd, int nstreams, const SResult* rs, uint32_t* tok_base, uint32_t* tile_base);
+// the decoder's token tiles: DEC_TILE tokens of one stream each, DEC_THREADS threads of
+// DEC_PER_THREAD consecutive tokens; grid-stride loops over the call's tiles
+constexpr int DEC_THREADS = 256, DEC_PER_THREAD = 8, DEC_TILE = DEC_THREADS * DEC_PER_THREAD;
+constexpr int DEC_MAX_COMP = 3 * (1 + CVC_MAX_LEVELS * 64);   // components of a stream, at most
+__global__ void k_dec_count_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tile_base,
+                              int nstreams, const uint32_t* comp_tok, CompTable ct, uint32_t* tile_sum, SResult* out);
+__global__ void k_dec_scatter_b(const SDesc* sd, const SCall* sc, const SResult* rs, const uint32_t* tile_base,
+                                int nstreams, const uint32_t* comp_tok, CompTable ct, const uint32_t* tile_pre,
+                                uint32_t* comp_codes, int16_t* res);
+__global__ void k_dec_check_b(const SDesc* sd, const SResult* rs, const uint32_t* comp_codes, CompTable ct,
+                              SResult* out);
 
 // exclusive scan of n values into out[0..n] (out[n] = total); tmp holds
 // ceil(n / 2048) + 1 values.

@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     dfb_a_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, smem_a);
 }
 
-// one row-split stage, one block per (job, tile)
-template <bool SYN, int NT>
+// one row-split stage, one block per (job, tile); FO: the first target coset is odd
+template <bool SYN, int NT, bool FO>
 __global__ void __launch_bounds__(DFBB_THREADS, NT == 8 ? 7 : 8) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
                                                Bases B, PassParams pp) {
     using G = BGeo<NT>;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(DFBB_THREADS, NT == 8 ? 7 : 8) k_dfb_b(const D
     __shared__ __align__(16) float sO[G::SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    dfb_b_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, sE, sO);
+    dfb_b_tile<SYN, NT, FO, false>(J, blockIdx.x - J.first_block, B, pp, sE, sO);
 }
 
 // ============================================================ launches
@@ -99,16 +99,23 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
         }
     } else {
         const DfbBJob* j = static_cast<const DfbBJob*>(L.d_jobs);
+        const bool fo = pp.first_odd != 0;
+#define CVC_DFBB(S, N)                                                                                   \
+    do {                                                                                                 \
+        if (fo) k_dfb_b<S, N, true><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);     \
+        else k_dfb_b<S, N, false><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);      \
+    } while (0)
         if (L.ntaps == 6) {
-            if (syn) k_dfb_b<true, 6><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 6><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) CVC_DFBB(true, 6);
+            else CVC_DFBB(false, 6);
         } else if (L.ntaps == 8) {
-            if (syn) k_dfb_b<true, 8><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 8><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) CVC_DFBB(true, 8);
+            else CVC_DFBB(false, 8);
         } else {
-            if (syn) k_dfb_b<true, 4><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
-            else k_dfb_b<false, 4><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);
+            if (syn) CVC_DFBB(true, 4);
+            else CVC_DFBB(false, 4);
         }
+#undef CVC_DFBB
     }
     return cudaGetLastError();
 }
