@@ -36,14 +36,26 @@ METRIC = "1080p encode+decode frames/s"
 UNIT = "frames/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
-# Counters of one ncu capture of a batched 1080p step (8 streams), per frame:
+# Counters of one ncu capture of a batched 1080p step (4 streams), per frame:
 # the DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# transform stage's launches and the warp instructions (smsp__inst_executed.sum)
+# stage's launches and the warp instructions (smsp__inst_executed.sum)
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": None, "dram_per_frame": {}, "warp_inst_per_frame": None,
-           "profile": None}
+CAPTURE = {"sources_sha256": "6e0b604a2e1ec35b70ec42a9270a3ea59ac980d63be63a9024518dea38911a37",
+           "dram_per_frame": {"colour_fwd": 6657408,
+                              "lp_analysis": 20803648,
+                              "dfb_analysis": 81467008,
+                              "quantise_kp": 33428160,
+                              "rle_stream": 17116608,
+                              "parse_unrle": 3694080,
+                              "unquantise_kp": 28919424,
+                              "dfb_synthesis": 82215168,
+                              "lp_synthesis": 29273216,
+                              "colour_inv": 12537920,
+                              "step": 316115968},
+           "warp_inst_per_frame": 187919516,
+           "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
 SMSP_PER_SM, N_SM = 4, 148
 
