@@ -466,8 +466,10 @@ cvc_status cvc_batch_step_async(cvc_batch* batch, int what, const cvc_batch_io* 
 /* as cvc_get_error for stream i of a batch */
 cvc_status cvc_batch_get_error(cvc_batch* batch, int i, cvc_stream_t stream, cvc_status* status);
 
-/* Launch shapes (they change no result): rows per block of the run-length
- * kernels (1..32) and blocks of the decoder's token kernels (1..65535).
+/* Launch shapes (they change no result): rows per block of the row kernels
+ * of motion-compensated frames, one warp per row (1..32; `rle_rows` names it
+ * for the row kernels it once set), and blocks of the decoder's grid-stride
+ * token-tile kernels (1..65535).
  * Fusion depth (changes no result either): the most coarse pyramid levels of
  * each plane that run in its pyramid tail, one block per plane with the
  * levels' images resident in shared memory (§2.1: the LP iterated on the

@@ -879,7 +879,7 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
     LaunchShape best = c->shape;
     float best_ms = 0.f;
     cvc_status s = measure(best, &best_ms);
-    // one coordinate at a time: token grid, then RLE rows per block
+    // one coordinate at a time: token grid, then rows per block of the motion row kernels
     for (int t : tok_cand) {
         if (s != CVC_OK) break;
         LaunchShape sh{best.rle_rows, t};

@@ -28,8 +28,8 @@ enum StepMode { STEP_ENC = 1, STEP_DEC = 2, STEP_ENCDEC = 3 };
 
 // launch shapes the autotuner may change (they change no result)
 struct LaunchShape {
-    int rle_rows;    // rows per block of the RLE kernels (one warp per row)
-    int tok_blocks;  // blocks of the grid-stride token kernels of the decoder
+    int rle_rows;    // rows per block of the motion-compensation row kernels (one warp per row)
+    int tok_blocks;  // blocks of the decoder's grid-stride token-tile kernels
 };
 
 // The decoder's back end at one pyramid scale s (§3.3: every LP scale can

@@ -469,6 +469,7 @@ struct BGeo {
     static constexpr int D = NT == 4 ? 2 : 0;
 };
 constexpr int DFBB_THREADS = 128;    // four warps: one run of rows each in the ladder passes
+constexpr int DFBB_THREADS_WIDE = 256;   // eight warps: for launches smaller than a wave (latency)
 static_assert(BGeo<4>::COLS == DFBB_COLS && dfbb_cols(4) == BGeo<4>::COLS && dfbb_cols(6) == BGeo<6>::COLS &&
                   dfbb_cols(8) == BGeo<8>::COLS,
               "host and device tile widths");
@@ -551,9 +552,9 @@ __device__ __forceinline__ void quad_rowsums(const QWin<NT, M>& w, float2& h01, 
 // target in registers, forming one new row sum per target.  Every sum is
 // accumulated in the order of the scalar definition (taps in index order, the
 // first a product), so each element rounds as a plain loop would round it.
-template <int NT, int R0, int R1, int X, int NQ, int DB, int M>
+template <int NT, int R0, int R1, int X, int NQ, int DB, int M, int TH>
 __device__ __forceinline__ void ladder_quads(float* T, const float* S, float alpha, float gamma) {
-    constexpr int CBS = BGeo<NT>::CBS, NWARPS = DFBB_THREADS / 32;
+    constexpr int CBS = BGeo<NT>::CBS, NWARPS = TH / 32;
     constexpr int NR = R1 - R0, KC = (NR + NWARPS - 1) / NWARPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = R0 + warp * KC;
@@ -608,21 +609,21 @@ __device__ __forceinline__ int wrap_fast(int v, int C) {
     return v < C ? v : (C >= CB ? v - C : v % C);
 }
 
-template <int NT, bool FO>
+template <int NT, bool FO, int TH>
 __device__ __forceinline__ void dfb_b_passes(float* F, float* Sx, const PassParams& pp) {
     using P = BPass<NT, FO>;
     constexpr int R = BGeo<NT>::R;
-    ladder_quads<NT, P::R10, P::R11, P::X1, P::NQ1, P::DB1, P::M1>(F, Sx, pp.a1, pp.g1);
+    ladder_quads<NT, P::R10, P::R11, P::X1, P::NQ1, P::DB1, P::M1, TH>(F, Sx, pp.a1, pp.g1);
     __syncthreads();
-    ladder_quads<NT, R, R + DFBB_ROWS, P::X2, P::NQ2, P::DB2, P::M2>(Sx, F, pp.a2, pp.g2);
+    ladder_quads<NT, R, R + DFBB_ROWS, P::X2, P::NQ2, P::DB2, P::M2, TH>(Sx, F, pp.a2, pp.g2);
 }
 
 // One tile of a row-split stage (sE, sO: BGeo<NT>::SMB floats of shared memory
 // each, 16-byte aligned), first target coset odd (FO = pp.first_odd) or even;
 // RESIDENT: the channel arrays may live in shared memory (the tail kernel).
-// The first DFBB_THREADS threads of the block do the work; every thread of
-// the block must call it (it holds barriers).
-template <bool SYN, int NT, bool FO, bool RESIDENT>
+// The first TH threads of the block (a multiple of 128) do the work; every
+// thread of the block must call it (it holds barriers).
+template <bool SYN, int NT, bool FO, bool RESIDENT, int TH>
 __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bases& B, const PassParams& pp,
                                            float* sE, float* sO) {
     using G = BGeo<NT>;
@@ -630,9 +631,10 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int t0 = ty * DFBB_ROWS, c0 = tx * COLS;
     const int R2 = J.R2, C = J.C, i = J.i;
-    constexpr int NW = DFBB_THREADS / 32;   // working warps
+    static_assert(TH % 128 == 0 && TH <= 256, "four or eight working warps");
+    constexpr int NW = TH / 32;   // working warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool worker = threadIdx.x < DFBB_THREADS;
+    const bool worker = threadIdx.x < TH;
     constexpr bool fo = FO;
     // the first target coset's array at the margin, the other D floats further
     float* const arrE = sE + G::MARGIN + (fo ? G::D : 0);
@@ -714,8 +716,8 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
     }
     cp_async_wait_all();
     __syncthreads();
-    if (FO) dfb_b_passes<NT, true>(arrO, arrE, pp);
-    else dfb_b_passes<NT, false>(arrE, arrO, pp);
+    if (FO) dfb_b_passes<NT, true, TH>(arrO, arrE, pp);
+    else dfb_b_passes<NT, false, TH>(arrE, arrO, pp);
     __syncthreads();
     if (!worker) return;
     // outputs: analysis writes the children, synthesis the parent's cosets.  Output

@@ -44,16 +44,16 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
     dfb_a_tile<SYN, NT>(J, blockIdx.x - J.first_block, B, pp, smem_a);
 }
 
-// one row-split stage, one block per (job, tile); FO: the first target coset is odd
-template <bool SYN, int NT, bool FO>
-__global__ void __launch_bounds__(DFBB_THREADS, NT == 8 ? 7 : 8) k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job,
-                                               Bases B, PassParams pp) {
+// one row-split stage, one block of TH threads per (job, tile); FO: the first target coset is odd
+template <bool SYN, int NT, bool FO, int TH>
+__global__ void __launch_bounds__(TH, TH == DFBB_THREADS ? (NT == 8 ? 7 : 8) : (NT == 8 ? 3 : 4))
+    k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job, Bases B, PassParams pp) {
     using G = BGeo<NT>;
     __shared__ __align__(16) float sE[G::SMB];
     __shared__ __align__(16) float sO[G::SMB];
     const DfbBJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    dfb_b_tile<SYN, NT, FO, false>(J, blockIdx.x - J.first_block, B, pp, sE, sO);
+    dfb_b_tile<SYN, NT, FO, false, TH>(J, blockIdx.x - J.first_block, B, pp, sE, sO);
 }
 
 // ============================================================ launches
@@ -100,10 +100,18 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
     } else {
         const DfbBJob* j = static_cast<const DfbBJob*>(L.d_jobs);
         const bool fo = pp.first_odd != 0;
-#define CVC_DFBB(S, N)                                                                                   \
-    do {                                                                                                 \
-        if (fo) k_dfb_b<S, N, true><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);     \
-        else k_dfb_b<S, N, false><<<L.nblocks, DFBB_THREADS, 0, st>>>(j, L.d_block_job, bases, pp);      \
+        // a launch of less than a wave of 128-thread blocks waits on each block's latency:
+        // eight warps per tile finish it sooner
+        const bool wide = L.nblocks < 148 * 8;
+#define CVC_DFBB_T(S, N, TH)                                                                            \
+    do {                                                                                                \
+        if (fo) k_dfb_b<S, N, true, TH><<<L.nblocks, TH, 0, st>>>(j, L.d_block_job, bases, pp);          \
+        else k_dfb_b<S, N, false, TH><<<L.nblocks, TH, 0, st>>>(j, L.d_block_job, bases, pp);           \
+    } while (0)
+#define CVC_DFBB(S, N)                                   \
+    do {                                                 \
+        if (wide) CVC_DFBB_T(S, N, DFBB_THREADS_WIDE);    \
+        else CVC_DFBB_T(S, N, DFBB_THREADS);             \
     } while (0)
         if (L.ntaps == 6) {
             if (syn) CVC_DFBB(true, 6);
@@ -116,6 +124,7 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
             else CVC_DFBB(false, 4);
         }
 #undef CVC_DFBB
+#undef CVC_DFBB_T
     }
     return cudaGetLastError();
 }

@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(256, 1) k_pyr_tail(const TailPlane* __restrict
             const int n = b_tiles(J);
             for (int tile = 0; tile < n; tile++) {
                 __syncthreads();
-                if (pp.first_odd) dfb_b_tile<SYN, NT, true, true>(J, tile, Bt, pp, sm, sm + BA);
-                else dfb_b_tile<SYN, NT, false, true>(J, tile, Bt, pp, sm, sm + BA);
+                if (pp.first_odd) dfb_b_tile<SYN, NT, true, true, 256>(J, tile, Bt, pp, sm, sm + BA);
+                else dfb_b_tile<SYN, NT, false, true, 256>(J, tile, Bt, pp, sm, sm + BA);
             }
         }
         __syncthreads();   // the step's resident outputs are complete before the next step reads them

@@ -78,8 +78,9 @@ def test_tile_kernels_keep_their_residency():
         return min(by_smem, by_regs)
 
     dfb = _ptxas("k_dfb.cu")
-    b4 = [v for k, v in dfb.items() if "k_dfb_b" in k and "Li4EE" in k]
-    assert len(b4) == 2 and all(blocks(v["smem"], v["regs"], threads=128) >= 8 for v in b4), b4
+    # 128-thread blocks (the launches of a wave or more), both first-target parities and directions
+    b4 = [v for k, v in dfb.items() if "k_dfb_b" in k and "Li4ELb" in k and "Li128EE" in k]
+    assert len(b4) == 4 and all(blocks(v["smem"], v["regs"], threads=128) >= 8 for v in b4), b4
     # k_dfb_a: 4 polyphase planes and 2 scratch planes of 44 x 45 floats, dynamic
     a4 = [v for k, v in dfb.items() if "k_dfb_a" in k and "Li4EE" in k]
     assert len(a4) == 2 and all(blocks(v["smem"] + 6 * 44 * 45 * 4, v["regs"]) >= 4 for v in a4), a4
