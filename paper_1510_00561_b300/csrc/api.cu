@@ -944,7 +944,7 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
         }
     };
     // pyramid-tail launches (kind 3): u32 nplanes, u32 ntaps; per plane i32 resident floats, i32 stream,
-    // u32 nsteps, u32 0, then per step u32 kind (0 LP, 1 DFB stages 1-2, 2 DFB stage >= 3), u32 0 and
+    // u32 nsteps, u32 0, then per step u32 kind (0 LP, 1 DFB stages 1-2, 2 DFB stage >= 3), u32 centred and
     // the job record; item size = blob bytes
     std::vector<std::vector<uint8_t>> blobs;
     for (const TailTables& T : e.h_tail[mode]) {
@@ -959,7 +959,7 @@ static cvc_status dump_tables(const CtEngine& e, int mode, const unsigned long l
             put(ph, 16);
             for (int k = 0; k < P.nsteps; k++) {
                 const TailStep& st = T.steps[(size_t)P.first_step + k];
-                uint32_t sh[2] = {(uint32_t)st.kind, 0};
+                uint32_t sh[2] = {(uint32_t)st.kind, (uint32_t)st.centred};
                 put(sh, 8);
                 if (st.kind == 0) put(&T.lp[st.job], sizeof(LpJob));
                 else if (st.kind == 1) put(&T.a[st.job], sizeof(DfbAJob));

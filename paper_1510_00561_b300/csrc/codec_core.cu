@@ -295,6 +295,8 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.qp.low_scale = ldexpf(1.0f, -L);
         D.qp.qpl_denorm = ldexpf((float)P.qpl, L);
         D.qp.st8 = P.storage8;
+        D.qp.rqph = (P.qph & (P.qph - 1)) == 0 ? 1.0f / (float)P.qph : 0.0f;
+        D.qp.rqpl = (P.qpl & (P.qpl - 1)) == 0 ? 1.0f / (float)P.qpl : 0.0f;
         D.hdr.levels = L;
         D.hdr.height = g.H;
         D.hdr.width = g.W;

@@ -375,18 +375,18 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 dfb_jobs(hj, wj, kj, nt, P.stream, B_SMEM, sd[j], sq[j], slots, la, lb);
                 std::vector<TailStep>& st = level_steps[j];
                 auto step_lp = [&]() {
-                    st.push_back({0, (int)T.lp.size()});
+                    st.push_back({0, (int)T.lp.size(), m == FWD && j == 1});
                     T.lp.push_back(J);
                 };
                 auto step_a = [&]() {
                     for (DfbAJob& A : la) {
-                        st.push_back({1, (int)T.a.size()});
+                        st.push_back({1, (int)T.a.size(), 0});
                         T.a.push_back(A);
                     }
                 };
                 auto step_b = [&](int s) {
                     for (DfbBJob& Bj : lb[s]) {
-                        st.push_back({2, (int)T.b.size()});
+                        st.push_back({2, (int)T.b.size(), 0});
                         T.b.push_back(Bj);
                     }
                 };
@@ -414,8 +414,10 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         e->h_lp[m].clear();
         e->h_dfb[m].clear();
         e->h_tail[m].clear();
-        auto add_lp = [&](std::vector<LpJob>& v) {
+        // the forward transform's first level runs centred in single precision (k_lp.cu)
+        auto add_lp = [&](std::vector<LpJob>& v, bool centred) {
             LaunchLp L{};
+            L.centred = centred;
             void* dj = nullptr;
             if (!upload<LpJob>(v, to_device, e, &dj, &L.d_block_job, &L.nblocks, count_lp)) return false;
             L.d_jobs = static_cast<LpJob*>(dj);
@@ -455,7 +457,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         }
         if (analysis) {
             for (int j = 1; j <= Lmax; j++)
-                if (!add_lp(lpj[j])) return false;
+                if (!add_lp(lpj[j], m == FWD && j == 1)) return false;
             for (int n = 0; n < 3; n++)
                 if (!aj[n].empty() && !add_a(aj[n])) return false;
             for (int s = 3; s <= kmax; s++)
@@ -468,7 +470,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
             for (int n = 0; n < 3; n++)
                 if (!aj[n].empty() && !add_a(aj[n])) return false;
             for (int j = Lmax; j >= 1; j--)
-                if (!add_lp(lpj[j])) return false;
+                if (!add_lp(lpj[j], false)) return false;
         }
     }
     return true;

@@ -146,6 +146,7 @@ struct LaunchLp {
     int njobs, nblocks;
     LpJob* d_jobs;
     int* d_block_job;
+    int centred;   // forward analysis in single precision on the tile minus its mean (level 1)
 };
 struct LaunchDfb {
     int kind;  // 0: DfbAJob, 1: DfbBJob
@@ -163,8 +164,9 @@ struct LaunchDfb {
 // the level's input lowpass (analysis) or output lowpass (synthesis) and the
 // coefficients go through global memory.
 struct TailStep {
-    int kind;  // 0: LpJob, 1: DfbAJob, 2: DfbBJob
-    int job;   // index into the launch's table of that kind
+    int kind;     // 0: LpJob, 1: DfbAJob, 2: DfbBJob
+    int job;      // index into the launch's table of that kind
+    int centred;  // an LP step of the forward transform's first level: centred single precision
 };
 struct TailPlane {
     int first_step, nsteps;

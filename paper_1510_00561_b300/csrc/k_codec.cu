@@ -299,7 +299,10 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
     float t;
     if (low) t = c * q.low_scale;                    // exact power-of-two normalisation
     else t = (fabsf(c) >= q.threshold) ? c : 0.0f;
-    float v = roundf(t / (low ? q.qpl : q.qph));     // IEEE division, ties away from zero
+    // the IEEE quotient t / QP, ties away from zero; for a power-of-two QP the product with
+    // its exact reciprocal is that same correctly rounded quotient
+    const float r = low ? q.rqpl : q.rqph;
+    float v = roundf(r != 0.0f ? t * r : t / (low ? q.qpl : q.qph));
     // 8-bit storage (§3.6): the rounded code is kept in a byte
     if (q.st8) v = low ? fminf(fmaxf(v, 0.0f), 255.0f) : fminf(fmaxf(v, -128.0f), 127.0f);
     if (!(fabsf(v) <= 32767.0f)) {

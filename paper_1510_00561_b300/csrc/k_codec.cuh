@@ -18,6 +18,9 @@ struct QuantParams {
     float low_scale;    // 2^-L (exact)
     float qpl_denorm;   // qpl * 2^L (exact)
     int st8;            // 8-bit storage (§3.6): codes clamped to a byte
+    // 1/qph, 1/qpl where the step is a power of two (exact, so t * (1/qp) is the
+    // correctly rounded t / qp, bit for bit); 0 where the quotient needs a division
+    float rqph, rqpl;
 };
 
 struct StreamHeader {

@@ -29,6 +29,7 @@ template <int NT>
 constexpr int b_array_floats() { return (BGeo<NT>::SMB + 3) & ~3; }
 template <int NT>
 constexpr int scratch_floats() {
+    static_assert(LevelGeo<4, 3>::FLOATS <= (int)(ff_smem<4, 3>() / 4), "the single-precision tile fits the scratch");
     constexpr int lp = (int)(ff_smem<4, 3>() / 4);
     constexpr int a = AGeo<NT>::SMEM / 4;
     constexpr int b = 2 * b_array_floats<NT>();
@@ -58,7 +59,14 @@ __global__ void __launch_bounds__(256, 1) k_pyr_tail(const TailPlane* __restrict
             const int n = lp_tiles(J);
             for (int tile = 0; tile < n; tile++) {
                 __syncthreads();   // the previous tile is done with the scratch
-                lp_ff_tile<4, 3, !SYN>(J, tile, Bt, sm);
+                if (!SYN && st.centred) {
+                    // the forward first level: centred single precision, as its own launches run it
+                    using LG = LevelGeo<4, 3>;
+                    float* s_a = sm + ((LG::MN * LG::MNS + 3) & ~3);
+                    lp_level_tile<4, 3, true>(J, tile, Bt, sm, s_a, s_a + ((LG::NA + 3) & ~3));
+                } else {
+                    lp_ff_tile<4, 3, !SYN>(J, tile, Bt, sm);
+                }
             }
         } else if (st.kind == 1) {
             const DfbAJob& J = da[st.job];

@@ -353,6 +353,146 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
     }
 }
 
+// single-precision analysis tile: cout = down(main, fa); out = main - up(cout, fs)
+// CENTRED: the tile's staged input is first replaced by x - mu, mu the nearest integer
+// to its mean (exact for integer samples, else one rounding of a number no larger
+// than x), and the lowpass output gets 2 mu back, exactly the lowpass of the constant
+// mu (the 9/7 lowpass has DC gain sqrt(2) per dimension), while the detail of a
+// constant is zero.  Rounding errors then scale with the tile's deviation from its
+// mean rather than with its values; this is what lets the forward transform's first
+// level, three quarters of its LP work, run in plain single precision.
+template <int RA, int RS>
+struct LevelGeo {
+    static constexpr int T = LP_TILE;
+    static constexpr int MLO = -(RS / 2);
+    static constexpr int MHI = (T - 1 + RS) / 2;
+    static constexpr int VN = MHI - MLO + 1;
+    static constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
+    static constexpr int Y0 = 2 * MLO - RA;  // main tile origin relative to the output tile origin
+    static constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
+    static constexpr int MNS = MN + (MN & 1);   // even row stride: the row pass reads its windows in pairs
+    // shared memory of one tile, in floats, each array 16-byte aligned
+    static constexpr int FLOATS = ((MN * MNS + 3) & ~3) + ((NA + 3) & ~3) + VN * VN;
+};
+
+// s_main: MN x MNS floats, s_a: NA, s_v: VN x VN (16-byte aligned); any number of
+// threads that is a multiple of 32 (at least 256 for the centring's warp sums: at most
+// VN * VN warps)
+template <int RA, int RS, bool CENTRED>
+__device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Bases& B, float* s_main, float* s_a,
+                                              float* s_v) {
+    using G = LevelGeo<RA, RS>;
+    constexpr int T = G::T, MLO = G::MLO, VN = G::VN, MN = G::MN, Y0 = G::Y0, MNS = G::MNS;
+    const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
+    const int y0 = ty * T, x0 = tx * T;
+    const int m0 = y0 / 2, n0 = x0 / 2;
+    const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
+    const float* mainp = base_ptr(B, J.main.b) + J.main.off;
+    const int mrs = J.main.rs;
+
+    lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
+    lp_cp_async_wait_all();
+    __syncthreads();
+    float mu = 0.f;
+    if (CENTRED) {
+        // mu: the staged tile's mean, rounded to an integer (fixed-order block sum)
+        float sum = 0.f;
+        for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
+            const int r = i / MN;
+            sum += s_main[r * MNS + (i - r * MN)];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        float tot = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_v[w];
+        mu = rintf(tot / (float)(MN * MN));
+        __syncthreads();   // s_v is reused below
+        for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
+            const int r = i / MN, k = r * MNS + (i - r * MN);
+            s_main[k] = s_main[k] - mu;
+        }
+        __syncthreads();
+    }
+    // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]; the window
+    // main[r][2n' + j], j = 0 .. 2 RA, starts at an even offset: RA pairs and one more
+    for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
+        int r = i / VN, n = i - r * VN;
+        const float* w = s_main + r * MNS + 2 * n;
+        float x[2 * RA + 1];
+#pragma unroll
+        for (int j = 0; j < RA; j++) {
+            const float2 pr = *reinterpret_cast<const float2*>(w + 2 * j);
+            x[2 * j] = pr.x;
+            x[2 * j + 1] = pr.y;
+        }
+        x[2 * RA] = w[2 * RA];
+        float acc = 0.f;
+#pragma unroll
+        for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), x[RA - b], acc);
+        s_a[i] = acc;
+    }
+    __syncthreads();
+    // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI]
+    for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
+        int m = i / VN, n = i - m * VN;
+        float acc = 0.f;
+#pragma unroll
+        for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), s_a[(2 * m + RA - a) * VN + n], acc);
+        s_v[i] = acc;
+    }
+    __syncthreads();
+    {
+        // interior 32 x 32 of v is this tile's share of the lowpass output
+        float* coutp = base_ptr(B, J.cout.b) + J.cout.off;
+        for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
+            int m = i / (T / 2), n = i - m * (T / 2);
+            int gm = m0 + m, gn = n0 + n;
+            if (gm < Hh && gn < Wh)
+                coutp[(long long)gm * J.cout.rs + gn] = CENTRED ? s_v[(m - MLO) * VN + (n - MLO)] + 2.f * mu
+                                                                : s_v[(m - MLO) * VN + (n - MLO)];
+        }
+    }
+    // expanding row pass, by output pairs (x = 2p, 2p + 1):
+    //   s_a[m][x] = sum_{t : x - t even} fs[t] v[m][(x - t)/2 - MLO]
+    for (int i = threadIdx.x; i < VN * (T / 2); i += blockDim.x) {
+        const int m = i / (T / 2), p = i - m * (T / 2);
+        const float* vr = s_v + m * VN + p - MLO;
+        float ev = 0.f, od = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), vr[-(t / 2)], ev);               // x = 2p
+            else od = fmaf(tap_s<RS>(t), vr[(1 - t) / 2], od);                           // x = 2p + 1
+        }
+        *reinterpret_cast<float2*>(s_a + m * T + 2 * p) = make_float2(ev, od);
+    }
+    __syncthreads();
+    // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main input
+    float* outp = base_ptr(B, J.out.b) + J.out.off;
+    for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
+        const int p = i / T, x = i - p * T;
+        const float* ar = s_a + (p - MLO) * T + x;
+        float ev = 0.f, od = 0.f;
+#pragma unroll
+        for (int t = -RS; t <= RS; t++) {
+            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), ar[-(t / 2) * T], ev);
+            else od = fmaf(tap_s<RS>(t), ar[((1 - t) / 2) * T], od);
+        }
+        const int gx = x0 + x;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int y = 2 * p + h, gy = y0 + y;
+            if (gy < H && gx < W) {
+                const float acc = h ? od : ev;
+                const float mv = s_main[(y - Y0) * MNS + (x - Y0)];
+                outp[(long long)gy * J.out.rs + gx] = mv - acc;
+            }
+        }
+    }
+}
+
+
 template <int RA, int RS>
 constexpr size_t ff_smem() {
     constexpr int T = LP_TILE;

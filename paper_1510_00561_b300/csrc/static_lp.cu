@@ -114,6 +114,7 @@ extern "C" cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int
         const int hj = h >> (j - 1);
         LaunchLp L;
         L.njobs = 1;
+        L.centred = j == 1;   // as the plan's forward first level
         L.nblocks = ((hj + LP_TILE - 1) / LP_TILE) * jobs.job[j - 1].tiles_x;
         L.d_jobs = reinterpret_cast<LpJob*>(base + (j - 1) * kJobSlotFloats);
         L.d_block_job = block_job;
