@@ -640,7 +640,7 @@ cvc_status cvc_lp_pyramid_forward_static(const float* d_x, int h, int w, int lev
  *   u32 kind 3, u32 byte count, and the tail's tables: u32 planes, u32
  *   prototype length, then per plane i32 shared-memory floats, i32 stream,
  *   u32 steps, u32 0, and per step u32 kind (0, 1 or 2 as above), u32 1 for an LP
- *   step computed centred in single precision (the forward first level) else 0
+ *   step computed centred in single precision (the first level) else 0
  *   and the job record; the tail's own images are base 4.
  * Lets a test check, before any GPU run, that every access of every job
  * stays inside its buffer and that the tables compute the transform.

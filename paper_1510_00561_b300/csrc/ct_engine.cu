@@ -375,7 +375,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
                 dfb_jobs(hj, wj, kj, nt, P.stream, B_SMEM, sd[j], sq[j], slots, la, lb);
                 std::vector<TailStep>& st = level_steps[j];
                 auto step_lp = [&]() {
-                    st.push_back({0, (int)T.lp.size(), m == FWD && j == 1});
+                    st.push_back({0, (int)T.lp.size(), (m == FWD || m == INV) && j == 1});
                     T.lp.push_back(J);
                 };
                 auto step_a = [&]() {
@@ -414,7 +414,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
         e->h_lp[m].clear();
         e->h_dfb[m].clear();
         e->h_tail[m].clear();
-        // the forward transform's first level runs centred in single precision (k_lp.cu)
+        // the first level of the forward transform and the inverse runs centred in single precision (k_lp.cu)
         auto add_lp = [&](std::vector<LpJob>& v, bool centred) {
             LaunchLp L{};
             L.centred = centred;
@@ -470,7 +470,7 @@ bool engine_build(CtEngine* e, const std::vector<PlaneRef>& planes_in, bool to_d
             for (int n = 0; n < 3; n++)
                 if (!aj[n].empty() && !add_a(aj[n])) return false;
             for (int j = Lmax; j >= 1; j--)
-                if (!add_lp(lpj[j], false)) return false;
+                if (!add_lp(lpj[j], m == INV && j == 1)) return false;
         }
     }
     return true;

@@ -146,7 +146,7 @@ struct LaunchLp {
     int njobs, nblocks;
     LpJob* d_jobs;
     int* d_block_job;
-    int centred;   // forward analysis in single precision on the tile minus its mean (level 1)
+    int centred;   // level 1 of the forward transform or the inverse: centred single precision
 };
 struct LaunchDfb {
     int kind;  // 0: DfbAJob, 1: DfbBJob
@@ -166,7 +166,7 @@ struct LaunchDfb {
 struct TailStep {
     int kind;     // 0: LpJob, 1: DfbAJob, 2: DfbBJob
     int job;      // index into the launch's table of that kind
-    int centred;  // an LP step of the forward transform's first level: centred single precision
+    int centred;  // an LP step of the first level (forward or inverse): centred single precision
 };
 struct TailPlane {
     int first_step, nsteps;

@@ -15,11 +15,11 @@
 // with halo, and the expanded row pass; every input element is read from
 // global memory once per tile plus the halo.
 //
-// The forward transform's first level runs in single precision on each tile
-// minus its mean (k_lp_level, CENTRED; see lp_level_tile): its numbers are
-// pixels, and centring makes its rounding scale with a tile's deviation from
-// its mean.  The other levels of the forward transform and the inverse
-// accumulate in float-float (k_lp_ff:
+// The first level of the forward transform and of the inverse runs in single
+// precision, centred on a per-tile constant (k_lp_level, CENTRED; see
+// lp_level_tile): its numbers are pixels, and centring makes its rounding
+// scale with a tile's deviation from its mean.  The other levels accumulate
+// in float-float (k_lp_ff:
 // error-free TwoSum / FMA-based TwoProd transformations, Dekker 1971 /
 // Knuth): the pyramid's DC gain of 2 per level makes coarse levels carry
 // numbers up to 2^L * 255, and single-precision roundings of such numbers
@@ -36,8 +36,8 @@
 
 namespace cvc {
 
-// single-precision analysis tile kernel (lp_level_tile): one block per (job, tile)
-template <int RA, int RS, bool CENTRED>
+// single-precision tile kernel (lp_level_tile): one block per (job, tile)
+template <int RA, int RS, bool CENTRED, bool SYN = false>
 __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs,
                                                   const int* __restrict__ block_job, Bases B) {
     using G = LevelGeo<RA, RS>;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
     __shared__ float s_v[G::VN * G::VN];
     const LpJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;
-    lp_level_tile<RA, RS, CENTRED>(J, blockIdx.x - J.first_block, B, s_main, s_a, s_v);
+    lp_level_tile<RA, RS, CENTRED, SYN>(J, blockIdx.x - J.first_block, B, s_main, s_a, s_v);
 }
 
 // float-float tile kernel: one block per (job, tile); blocks of streams that take no part return
@@ -84,6 +84,8 @@ cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st) {
     if (!synth && !swap && L.centred)
         k_lp_level<4, 3, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
     else if (!synth && !swap) k_lp_ff<4, 3, true><<<grid, block, ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
+    else if (synth && !swap && L.centred)
+        k_lp_level<4, 3, true, true><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);
     else if (synth && !swap)
         k_lp_ff<4, 3, false><<<grid, block, ff_smem<4, 3>(), st>>>(L.d_jobs, L.d_block_job, bases);
     else if (!synth && swap) k_lp_level<3, 4, false><<<grid, block, 0, st>>>(L.d_jobs, L.d_block_job, bases);

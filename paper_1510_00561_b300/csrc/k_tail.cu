@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(256, 1) k_pyr_tail(const TailPlane* __restrict
             const int n = lp_tiles(J);
             for (int tile = 0; tile < n; tile++) {
                 __syncthreads();   // the previous tile is done with the scratch
-                if (!SYN && st.centred) {
-                    // the forward first level: centred single precision, as its own launches run it
+                if (st.centred) {
+                    // the first level: centred single precision, as its own launches run it
                     using LG = LevelGeo<4, 3>;
                     float* s_a = sm + ((LG::MN * LG::MNS + 3) & ~3);
-                    lp_level_tile<4, 3, true>(J, tile, Bt, sm, s_a, s_a + ((LG::NA + 3) & ~3));
+                    lp_level_tile<4, 3, true, SYN>(J, tile, Bt, sm, s_a, s_a + ((LG::NA + 3) & ~3));
                 } else {
                     lp_ff_tile<4, 3, !SYN>(J, tile, Bt, sm);
                 }

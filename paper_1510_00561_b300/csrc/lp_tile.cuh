@@ -378,9 +378,14 @@ struct LevelGeo {
 // s_main: MN x MNS floats, s_a: NA, s_v: VN x VN (16-byte aligned); any number of
 // threads that is a multiple of 32 (at least 256 for the centring's warp sums: at most
 // VN * VN warps)
-template <int RA, int RS, bool CENTRED>
+// SYN: the synthesis tile instead, x = d + up(cin - down(d)) (main = d; cin with its
+// low-order part cin_lo where the job has one), CENTRED on mu = half the rounded
+// mean of the tile's cin window: e' = (cin - 2 mu) - down(d), x = d + up(e') + mu,
+// exact for the real filters because up(2 mu) = mu.
+template <int RA, int RS, bool CENTRED, bool SYN = false>
 __device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Bases& B, float* s_main, float* s_a,
                                               float* s_v) {
+    static_assert(!SYN || CENTRED, "the single-precision synthesis tile is centred");
     using G = LevelGeo<RA, RS>;
     constexpr int T = G::T, MLO = G::MLO, VN = G::VN, MN = G::MN, Y0 = G::Y0, MNS = G::MNS;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
@@ -391,10 +396,32 @@ __device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Ba
     const int mrs = J.main.rs;
 
     lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
-    lp_cp_async_wait_all();
-    __syncthreads();
+    const float* cinp = SYN ? base_ptr(B, J.cin.b) + J.cin.off : nullptr;
     float mu = 0.f;
-    if (CENTRED) {
+    if (SYN) {
+        // the tile's cin window (half resolution, periodic) into s_v while the detail stages;
+        // mu from its fixed-order block sum
+        float sum = 0.f;
+        for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
+            const int m = i / VN, n = i - m * VN;
+            const float c = cinp[(long long)wrap_idx(m0 + MLO + m, Hh) * J.cin.rs + wrap_idx(n0 + MLO + n, Wh)];
+            s_v[i] = c;
+            sum += c;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) s_a[threadIdx.x >> 5] = sum;
+        lp_cp_async_wait_all();
+        __syncthreads();
+        float tot = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_a[w];
+        mu = rintf(tot / (float)(2 * VN * VN));
+        __syncthreads();   // s_a is reused below
+    } else {
+        lp_cp_async_wait_all();
+        __syncthreads();
+    }
+    if (CENTRED && !SYN) {
         // mu: the staged tile's mean, rounded to an integer (fixed-order block sum)
         float sum = 0.f;
         for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
@@ -440,10 +467,20 @@ __device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Ba
         float acc = 0.f;
 #pragma unroll
         for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), s_a[(2 * m + RA - a) * VN + n], acc);
-        s_v[i] = acc;
+        if (SYN) {
+            // e' = (cin - 2 mu) + cin_lo - down(d)
+            float e = s_v[i] - 2.f * mu;
+            if (J.cin_lo.b >= 0) {
+                const float* cinlp = base_ptr(B, J.cin_lo.b) + J.cin_lo.off;
+                e = e + cinlp[(long long)wrap_idx(m0 + MLO + m, Hh) * J.cin_lo.rs + wrap_idx(n0 + MLO + n, Wh)];
+            }
+            s_v[i] = e - acc;
+        } else {
+            s_v[i] = acc;
+        }
     }
     __syncthreads();
-    {
+    if (!SYN) {
         // interior 32 x 32 of v is this tile's share of the lowpass output
         float* coutp = base_ptr(B, J.cout.b) + J.cout.off;
         for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
@@ -486,7 +523,7 @@ __device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Ba
             if (gy < H && gx < W) {
                 const float acc = h ? od : ev;
                 const float mv = s_main[(y - Y0) * MNS + (x - Y0)];
-                outp[(long long)gy * J.out.rs + gx] = mv - acc;
+                outp[(long long)gy * J.out.rs + gx] = SYN ? (mv + acc) + mu : mv - acc;
             }
         }
     }
