@@ -42,19 +42,19 @@ CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": "6e0b604a2e1ec35b70ec42a9270a3ea59ac980d63be63a9024518dea38911a37",
-           "dram_per_frame": {"colour_fwd": 6657408,
-                              "lp_analysis": 20803648,
-                              "dfb_analysis": 81467008,
-                              "quantise_kp": 33428160,
-                              "rle_stream": 17116608,
-                              "parse_unrle": 3694080,
-                              "unquantise_kp": 28919424,
-                              "dfb_synthesis": 82215168,
-                              "lp_synthesis": 29273216,
-                              "colour_inv": 12537920,
-                              "step": 316115968},
-           "warp_inst_per_frame": 187919516,
+CAPTURE = {"sources_sha256": "ae117dff5f33b9ff64da7cda8618c8da7000c3219cdbf0204b484ba60b0adecc",
+           "dram_per_frame": {"colour_fwd": 6652032,
+                              "lp_analysis": 21057152,
+                              "dfb_analysis": 81437184,
+                              "quantise_kp": 33489024,
+                              "rle_stream": 17114752,
+                              "parse_unrle": 3733056,
+                              "unquantise_kp": 28959936,
+                              "dfb_synthesis": 82376384,
+                              "lp_synthesis": 29172672,
+                              "colour_inv": 12542976,
+                              "step": 316538560},
+           "warp_inst_per_frame": 173377112,
            "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
 SMSP_PER_SM, N_SM = 4, 148

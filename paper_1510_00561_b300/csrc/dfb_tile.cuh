@@ -570,11 +570,11 @@ __device__ __forceinline__ void ladder_quads(float* T, const float* S, float alp
         w.load(s + ia * CBS);
         quad_rowsums<NT, M>(w, g01[ia], g23[ia]);
     }
-    // a rolled loop: the whole pass stays a few hundred instructions, so the
-    // blocks of an SM in their different phases share the instruction cache
+    // a loop unrolled twice at most: the whole pass stays a few hundred instructions,
+    // so the blocks of an SM in their different phases share the instruction cache
     const int steps = min(KC, R1 - r0);
     s += (NT - 1) * CBS;
-#pragma unroll 1
+#pragma unroll 2
     for (int k = 0; k < steps; k++, s += CBS, t += CBS) {
         {
             QWin<NT, M> w;

@@ -755,8 +755,10 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_count_b(const int16_t* __re
 __global__ void __launch_bounds__(RLE_THREADS) k_rle_write_b(const int16_t* __restrict__ res, RleTiles tt,
                                                               const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                                               const uint32_t* __restrict__ tileoff, SResult* out) {
-    __shared__ uint32_t s_sum[RLE_THREADS / 32];
-    __shared__ int s_max[RLE_THREADS / 32];
+    // warp totals of a chunk, double-buffered: chunk c + 1 writes the other half, so one
+    // barrier per chunk separates every write from the reads of the same half
+    __shared__ uint32_t s_sum[2][RLE_THREADS / 32];
+    __shared__ int s_max[2][RLE_THREADS / 32];
     const int tile = blockIdx.x;
     const int s = tt.stream[tile];
     const SCall& C = sc[s];
@@ -782,7 +784,8 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_write_b(const int16_t* __re
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         uint32_t carry = 0;     // tokens of the tile's earlier chunks
         int carry_s = -1;       // latest zero-run start among them (tile index)
-        for (long long gb = e0 & ~7LL; gb < e1; gb += RLE_CHUNK) {
+        int half = 0;
+        for (long long gb = e0 & ~7LL; gb < e1; gb += RLE_CHUNK, half ^= 1) {
             const long long g = gb + 8LL * threadIdx.x;
             RleChunk k;
             if (g < e1) k = rle_chunk(res, g, e0, e1, w);
@@ -805,16 +808,16 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_write_b(const int16_t* __re
             int mprev = __shfl_up_sync(0xffffffffu, mx, 1);
             if (lane == 0) mprev = -1;
             if (lane == 31) {
-                s_sum[warp] = x;
-                s_max[warp] = mx;
+                s_sum[half][warp] = x;
+                s_max[half][warp] = mx;
             }
             __syncthreads();
             uint32_t wpre = 0, tot = 0;
             int wmax = -1, bmax = -1;
 #pragma unroll
             for (int i = 0; i < RLE_THREADS / 32; i++) {
-                const uint32_t a = s_sum[i];
-                const int b = s_max[i];
+                const uint32_t a = s_sum[half][i];
+                const int b = s_max[half][i];
                 if (i < warp) {
                     wpre += a;
                     wmax = max(wmax, b);
@@ -853,7 +856,6 @@ __global__ void __launch_bounds__(RLE_THREADS) k_rle_write_b(const int16_t* __re
             }
             carry += tot;
             carry_s = max(carry_s, bmax);
-            __syncthreads();    // the scan arrays are reused by the next chunk
         }
     }
     if (over) atomicOr(&out[s].enc_err, EF_CAPACITY);

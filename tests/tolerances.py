@@ -6,11 +6,12 @@ the lowpass), the scale on which that level's numbers are pixels.
 
 INVERSE = 1e-4: the inverse transform and the decoder's reconstructed planes
 against the oracle's inverse of the same coefficients, max abs on the 0-255
-scale.  The LP synthesis computes in float-float, with the CDF 9/7 taps held
-as float-float and the lowpass images between levels stored as (hi, lo)
-pairs, so what remains is the single-precision DFB synthesis of the detail
-images and the final rounding of the output plane (measured below 6e-5 at
-1080p, 5 levels, uniform-noise planes).
+scale.  The LP synthesis of levels 2..L computes in float-float, with the
+CDF 9/7 taps held as float-float and the lowpass images between levels
+stored as (hi, lo) pairs; level 1 runs in single precision centred on a
+per-tile constant, which keeps its rounding at the scale of a tile's
+deviation from its mean.  Measured 4.9e-5 (uniform noise), 5.9e-5 (integer
+noise) and 2.1e-5 (smooth planes) at 1080p, 5 levels.
 
 ROUND_TRIP = FORWARD + INVERSE: the GPU's inverse of its own forward
 coefficients against the input carries both errors.
