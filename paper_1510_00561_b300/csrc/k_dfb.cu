@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_dfb_a(const DfbAJob* __restrict__ jobs,
 
 // one row-split stage, one block of TH threads per (job, tile); FO: the first target coset is odd
 template <bool SYN, int NT, bool FO, int TH>
-__global__ void __launch_bounds__(TH, TH == DFBB_THREADS ? (NT == 8 ? 7 : 8) : (NT == 8 ? 3 : 4))
+__global__ void __launch_bounds__(TH, TH == DFBB_THREADS ? (NT == 8 ? 6 : 8) : (NT == 8 ? 3 : 4))
     k_dfb_b(const DfbBJob* __restrict__ jobs, const int* __restrict__ block_job, Bases B, PassParams pp) {
     using G = BGeo<NT>;
     __shared__ __align__(16) float sE[G::SMB];
