@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_lp_level(const LpJob* __restrict__ jobs
                                                   const int* __restrict__ block_job, Bases B) {
     using G = LevelGeo<RA, RS>;
     __shared__ __align__(16) float s_main[G::MN * G::MNS];
-    __shared__ __align__(16) float s_a[G::NA];   // row pass (MN x VN), later expanded rows (VN x T)
+    __shared__ __align__(16) float s_a[G::NA];   // row pass (MN x VN), later expanded rows (VN x TS)
     __shared__ float s_v[G::VN * G::VN];
     const LpJob& J = jobs[block_job[blockIdx.x]];
     if (job_idle(B, J.stream)) return;

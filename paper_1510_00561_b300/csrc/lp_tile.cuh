@@ -354,13 +354,21 @@ __device__ __forceinline__ void lp_ff_tile(const LpJob& J, int tile, const Bases
 }
 
 // single-precision analysis tile: cout = down(main, fa); out = main - up(cout, fs)
-// CENTRED: the tile's staged input is first replaced by x - mu, mu the nearest integer
-// to its mean (exact for integer samples, else one rounding of a number no larger
-// than x), and the lowpass output gets 2 mu back, exactly the lowpass of the constant
-// mu (the 9/7 lowpass has DC gain sqrt(2) per dimension), while the detail of a
-// constant is zero.  Rounding errors then scale with the tile's deviation from its
-// mean rather than with its values; this is what lets the forward transform's first
-// level, three quarters of its LP work, run in plain single precision.
+// CENTRED: the tile's staged input is read as x - mu, mu the nearest integer to its
+// mean (exact for integer samples, else one rounding of a number no larger than x),
+// and the lowpass output gets 2 mu back, exactly the lowpass of the constant mu (the
+// 9/7 lowpass has DC gain sqrt(2) per dimension), while the detail of a constant is
+// zero.  Rounding errors then scale with the tile's deviation from its mean rather
+// than with its values; this is what lets the forward transform's first level, three
+// quarters of its LP work, run in plain single precision.
+//
+// Each of the four passes gives a thread a run of outputs along the filtered
+// direction and reads the run's input window once into registers; every output
+// still accumulates its taps in the same order as the one-output-per-thread form.
+
+// outputs per thread of a decimating pass over n outputs: the largest of 7, 6, 5 that divides n
+constexpr int lp_run_len(int n) { return n % 7 == 0 ? 7 : n % 6 == 0 ? 6 : 5; }
+
 template <int RA, int RS>
 struct LevelGeo {
     static constexpr int T = LP_TILE;
@@ -369,8 +377,15 @@ struct LevelGeo {
     static constexpr int VN = MHI - MLO + 1;
     static constexpr int MN = 2 * (VN - 1) + 2 * RA + 1;
     static constexpr int Y0 = 2 * MLO - RA;  // main tile origin relative to the output tile origin
-    static constexpr int NA = (MN * VN > VN * T) ? MN * VN : VN * T;
     static constexpr int MNS = MN + (MN & 1);   // even row stride: the row pass reads its windows in pairs
+    static constexpr int TS = T + 2;            // expanded-row stride: pair stores of 16 rows hit 32 banks
+    static constexpr int NA = (MN * VN > VN * TS) ? MN * VN : VN * TS;
+    static constexpr int KR = lp_run_len(VN);   // row-pass outputs per thread
+    static constexpr int KC = lp_run_len(VN);   // column-pass outputs per thread
+    static constexpr int KP = 8;                // expanding passes: output pairs per thread
+    static constexpr int SLO = RS / 2, SHI = (RS + 1) / 2;   // an expanded pair reads v[p - SLO .. p + SHI]
+    static_assert(VN % KR == 0 && VN % KC == 0 && (T / 2) % KP == 0, "runs tile the passes");
+    static_assert(((VN * VN + 3) & ~3) + 32 <= NA, "the synthesis stages cin_lo and the warp sums in s_a");
     // shared memory of one tile, in floats, each array 16-byte aligned
     static constexpr int FLOATS = ((MN * MNS + 3) & ~3) + ((NA + 3) & ~3) + VN * VN;
 };
@@ -380,150 +395,199 @@ struct LevelGeo {
 // VN * VN warps)
 // SYN: the synthesis tile instead, x = d + up(cin - down(d)) (main = d; cin with its
 // low-order part cin_lo where the job has one), CENTRED on mu = half the rounded
-// mean of the tile's cin window: e' = (cin - 2 mu) - down(d), x = d + up(e') + mu,
+// mean of the tile's cin window: e' = (cin - 2 mu) + cin_lo - down(d), x = d + up(e') + mu,
 // exact for the real filters because up(2 mu) = mu.
 template <int RA, int RS, bool CENTRED, bool SYN = false>
 __device__ __forceinline__ void lp_level_tile(const LpJob& J, int tile, const Bases& B, float* s_main, float* s_a,
                                               float* s_v) {
     static_assert(!SYN || CENTRED, "the single-precision synthesis tile is centred");
     using G = LevelGeo<RA, RS>;
-    constexpr int T = G::T, MLO = G::MLO, VN = G::VN, MN = G::MN, Y0 = G::Y0, MNS = G::MNS;
+    constexpr int T = G::T, MLO = G::MLO, VN = G::VN, MN = G::MN, Y0 = G::Y0, MNS = G::MNS, TS = G::TS;
     const int ty = tile / J.tiles_x, tx = tile - ty * J.tiles_x;
     const int y0 = ty * T, x0 = tx * T;
     const int m0 = y0 / 2, n0 = x0 / 2;
     const int H = J.H, W = J.W, Hh = H / 2, Wh = W / 2;
     const float* mainp = base_ptr(B, J.main.b) + J.main.off;
     const int mrs = J.main.rs;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
 
     lp_stage<MN, MNS>(s_main, mainp, mrs, y0 + Y0, x0 + Y0, H, W);
-    const float* cinp = SYN ? base_ptr(B, J.cin.b) + J.cin.off : nullptr;
     float mu = 0.f;
     if (SYN) {
-        // the tile's cin window (half resolution, periodic) into s_v while the detail stages;
-        // mu from its fixed-order block sum
-        float sum = 0.f;
-        for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
-            const int m = i / VN, n = i - m * VN;
-            const float c = cinp[(long long)wrap_idx(m0 + MLO + m, Hh) * J.cin.rs + wrap_idx(n0 + MLO + n, Wh)];
-            s_v[i] = c;
-            sum += c;
+        // the tile's cin window (half resolution, periodic) into s_v and its low-order part
+        // into s_a, a warp per row: copied asynchronously with the detail, or plainly where
+        // they are a tail kernel's resident images; mu from the block sum of the window
+        const float* cinp = base_ptr(B, J.cin.b) + J.cin.off;
+        const float* cinlp = J.cin_lo.b >= 0 ? base_ptr(B, J.cin_lo.b) + J.cin_lo.off : nullptr;
+        const bool cin_sh = __isShared(cinp), lo_sh = cinlp && __isShared(cinlp);
+        const int c0 = n0 + MLO;
+        const bool inner = c0 >= 0 && c0 + VN <= Wh;
+        for (int m = warp; m < VN; m += nwarp) {
+            const int gm = wrap_idx(m0 + MLO + m, Hh);
+            const float* rowp = cinp + (long long)gm * J.cin.rs;
+            const float* lrow = cinlp ? cinlp + (long long)gm * J.cin_lo.rs : nullptr;
+            for (int n = lane; n < VN; n += 32) {
+                const int gn = inner ? c0 + n : wrap_idx(c0 + n, Wh);
+                if (cin_sh) s_v[m * VN + n] = rowp[gn];
+                else lp_cp_async4(s_v + m * VN + n, rowp + gn);
+                if (lo_sh) s_a[m * VN + n] = lrow[gn];
+                else if (cinlp) lp_cp_async4(s_a + m * VN + n, lrow + gn);
+            }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if ((threadIdx.x & 31) == 0) s_a[threadIdx.x >> 5] = sum;
         lp_cp_async_wait_all();
         __syncthreads();
+        float* s_part = s_a + ((VN * VN + 3) & ~3);   // after the low-order window
+        float sum = 0.f;
+        for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) sum += s_v[i];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) s_part[warp] = sum;
+        __syncthreads();
         float tot = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_a[w];
+        for (int w = 0; w < nwarp; w++) tot += s_part[w];
         mu = rintf(tot / (float)(2 * VN * VN));
+        // e' = (cin - 2 mu) + cin_lo, less down(d) in the column pass
+        for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
+            float e = s_v[i] - 2.f * mu;
+            if (cinlp) e = e + s_a[i];
+            s_v[i] = e;
+        }
         __syncthreads();   // s_a is reused below
     } else {
         lp_cp_async_wait_all();
         __syncthreads();
     }
     if (CENTRED && !SYN) {
-        // mu: the staged tile's mean, rounded to an integer (fixed-order block sum)
+        // mu: the staged tile's mean, rounded to an integer (a warp per row)
         float sum = 0.f;
-        for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
-            const int r = i / MN;
-            sum += s_main[r * MNS + (i - r * MN)];
+        for (int r = warp; r < MN; r += nwarp) {
+            const float* row = s_main + r * MNS;
+            for (int c = lane; c < MN; c += 32) sum += row[c];
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = sum;
+        if (lane == 0) s_v[warp] = sum;
         __syncthreads();
         float tot = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_v[w];
+        for (int w = 0; w < nwarp; w++) tot += s_v[w];
         mu = rintf(tot / (float)(MN * MN));
-        __syncthreads();   // s_v is reused below
-        for (int i = threadIdx.x; i < MN * MN; i += blockDim.x) {
-            const int r = i / MN, k = r * MNS + (i - r * MN);
-            s_main[k] = s_main[k] - mu;
-        }
-        __syncthreads();
+        // s_v is next written in the column pass, after the row pass's barrier
     }
-    // decimating row pass: s_a[r][n'] = sum_b fa[b] main[r][2n' + RA - b]; the window
-    // main[r][2n' + j], j = 0 .. 2 RA, starts at an even offset: RA pairs and one more
-    for (int i = threadIdx.x; i < MN * VN; i += blockDim.x) {
-        int r = i / VN, n = i - r * VN;
-        const float* w = s_main + r * MNS + 2 * n;
-        float x[2 * RA + 1];
+    constexpr bool SUB = CENTRED && !SYN;   // the analysis reads its input as x - mu
+    // decimating row pass: s_a[r][n] = sum_b fa[b] main[r][2n + RA - b]; a thread takes KR
+    // outputs of one row, whose window main[r][2 n0 .. 2 n0 + 2 KR + 2 RA - 2] starts at an
+    // even offset (pairs and one more); lanes on consecutive rows
+    {
+        constexpr int KR = G::KR, NWIN = 2 * KR + 2 * RA - 1;
+        for (int i = threadIdx.x; i < MN * (VN / KR); i += blockDim.x) {
+            const int run = i / MN, r = i - run * MN;
+            const float* w = s_main + r * MNS + 2 * KR * run;
+            float x[NWIN];
 #pragma unroll
-        for (int j = 0; j < RA; j++) {
-            const float2 pr = *reinterpret_cast<const float2*>(w + 2 * j);
-            x[2 * j] = pr.x;
-            x[2 * j + 1] = pr.y;
-        }
-        x[2 * RA] = w[2 * RA];
-        float acc = 0.f;
-#pragma unroll
-        for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), x[RA - b], acc);
-        s_a[i] = acc;
-    }
-    __syncthreads();
-    // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI]
-    for (int i = threadIdx.x; i < VN * VN; i += blockDim.x) {
-        int m = i / VN, n = i - m * VN;
-        float acc = 0.f;
-#pragma unroll
-        for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), s_a[(2 * m + RA - a) * VN + n], acc);
-        if (SYN) {
-            // e' = (cin - 2 mu) + cin_lo - down(d)
-            float e = s_v[i] - 2.f * mu;
-            if (J.cin_lo.b >= 0) {
-                const float* cinlp = base_ptr(B, J.cin_lo.b) + J.cin_lo.off;
-                e = e + cinlp[(long long)wrap_idx(m0 + MLO + m, Hh) * J.cin_lo.rs + wrap_idx(n0 + MLO + n, Wh)];
+            for (int j = 0; j < NWIN / 2; j++) {
+                const float2 pr = *reinterpret_cast<const float2*>(w + 2 * j);
+                x[2 * j] = SUB ? pr.x - mu : pr.x;
+                x[2 * j + 1] = SUB ? pr.y - mu : pr.y;
             }
-            s_v[i] = e - acc;
-        } else {
-            s_v[i] = acc;
+            x[NWIN - 1] = SUB ? w[NWIN - 1] - mu : w[NWIN - 1];
+            float* dst = s_a + r * VN + KR * run;
+#pragma unroll
+            for (int k = 0; k < KR; k++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int b = -RA; b <= RA; b++) acc = fmaf(tap_a<RA>(b), x[2 * k + RA - b], acc);
+                dst[k] = acc;
+            }
         }
     }
     __syncthreads();
-    if (!SYN) {
-        // interior 32 x 32 of v is this tile's share of the lowpass output
-        float* coutp = base_ptr(B, J.cout.b) + J.cout.off;
-        for (int i = threadIdx.x; i < (T / 2) * (T / 2); i += blockDim.x) {
-            int m = i / (T / 2), n = i - m * (T / 2);
-            int gm = m0 + m, gn = n0 + n;
-            if (gm < Hh && gn < Wh)
-                coutp[(long long)gm * J.cout.rs + gn] = CENTRED ? s_v[(m - MLO) * VN + (n - MLO)] + 2.f * mu
-                                                                : s_v[(m - MLO) * VN + (n - MLO)];
+    // decimating column pass -> half-resolution values v on [m0+MLO, m0+MHI] x [n0+MLO, n0+MHI];
+    // a thread takes KC outputs of one column, lanes on consecutive columns.  The analysis
+    // stores the interior 32 x 32 of v, this tile's share of the lowpass output, from here.
+    {
+        constexpr int KC = G::KC, NWIN = 2 * KC + 2 * RA - 1;
+        float* coutp = SYN ? nullptr : base_ptr(B, J.cout.b) + J.cout.off;
+        for (int i = threadIdx.x; i < VN * (VN / KC); i += blockDim.x) {
+            const int run = i / VN, n = i - run * VN;
+            const int mr = KC * run;
+            const float* col = s_a + 2 * mr * VN + n;
+            float y[NWIN];
+#pragma unroll
+            for (int j = 0; j < NWIN; j++) y[j] = col[j * VN];
+            const int gn = n0 + n + MLO;
+            const bool ncol = !SYN && n + MLO >= 0 && n + MLO < T / 2 && gn < Wh;
+#pragma unroll
+            for (int k = 0; k < KC; k++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int a = -RA; a <= RA; a++) acc = fmaf(tap_a<RA>(a), y[2 * k + RA - a], acc);
+                const int m = mr + k;
+                if (SYN) {
+                    s_v[m * VN + n] = s_v[m * VN + n] - acc;
+                } else {
+                    s_v[m * VN + n] = acc;
+                    const int gm = m0 + m + MLO;
+                    if (ncol && m + MLO >= 0 && m + MLO < T / 2 && gm < Hh)
+                        coutp[(long long)gm * J.cout.rs + gn] = CENTRED ? acc + 2.f * mu : acc;
+                }
+            }
         }
     }
+    __syncthreads();
     // expanding row pass, by output pairs (x = 2p, 2p + 1):
     //   s_a[m][x] = sum_{t : x - t even} fs[t] v[m][(x - t)/2 - MLO]
-    for (int i = threadIdx.x; i < VN * (T / 2); i += blockDim.x) {
-        const int m = i / (T / 2), p = i - m * (T / 2);
-        const float* vr = s_v + m * VN + p - MLO;
-        float ev = 0.f, od = 0.f;
+    // a thread takes KP pairs of one row (window v[m][p0 - SLO - MLO .. p0 + KP - 1 + SHI - MLO]),
+    // lanes on consecutive rows
+    constexpr int KP = G::KP, SLO = G::SLO, NWE = KP + G::SLO + G::SHI;
+    for (int i = threadIdx.x; i < VN * (T / 2 / KP); i += blockDim.x) {
+        const int run = i / VN, m = i - run * VN;
+        const int p0 = KP * run;
+        const float* vr = s_v + m * VN + p0 - MLO - SLO;
+        float z[NWE];
 #pragma unroll
-        for (int t = -RS; t <= RS; t++) {
-            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), vr[-(t / 2)], ev);               // x = 2p
-            else od = fmaf(tap_s<RS>(t), vr[(1 - t) / 2], od);                           // x = 2p + 1
+        for (int j = 0; j < NWE; j++) z[j] = vr[j];
+        float* dst = s_a + m * TS + 2 * p0;
+#pragma unroll
+        for (int k = 0; k < KP; k++) {
+            float ev = 0.f, od = 0.f;
+#pragma unroll
+            for (int t = -RS; t <= RS; t++) {
+                if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), z[k + SLO - t / 2], ev);        // x = 2p
+                else od = fmaf(tap_s<RS>(t), z[k + SLO + (1 - t) / 2], od);                // x = 2p + 1
+            }
+            *reinterpret_cast<float2*>(dst + 2 * k) = make_float2(ev, od);
         }
-        *reinterpret_cast<float2*>(s_a + m * T + 2 * p) = make_float2(ev, od);
     }
     __syncthreads();
-    // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main input
+    // expanding column pass by output pairs (y = 2p, 2p + 1) and the combination with the main
+    // input; a thread takes KP pairs of one column, lanes on consecutive columns
     float* outp = base_ptr(B, J.out.b) + J.out.off;
-    for (int i = threadIdx.x; i < (T / 2) * T; i += blockDim.x) {
-        const int p = i / T, x = i - p * T;
-        const float* ar = s_a + (p - MLO) * T + x;
-        float ev = 0.f, od = 0.f;
+    for (int i = threadIdx.x; i < T * (T / 2 / KP); i += blockDim.x) {
+        const int run = i / T, x = i - run * T;
+        const int p0 = KP * run;
+        const float* ac = s_a + (p0 - MLO - SLO) * TS + x;
+        float z[NWE];
 #pragma unroll
-        for (int t = -RS; t <= RS; t++) {
-            if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), ar[-(t / 2) * T], ev);
-            else od = fmaf(tap_s<RS>(t), ar[((1 - t) / 2) * T], od);
-        }
+        for (int j = 0; j < NWE; j++) z[j] = ac[j * TS];
         const int gx = x0 + x;
+        const float* mcol = s_main + (2 * p0 - Y0) * MNS + (x - Y0);
+        float* ocol = outp + gx;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int y = 2 * p + h, gy = y0 + y;
-            if (gy < H && gx < W) {
-                const float acc = h ? od : ev;
-                const float mv = s_main[(y - Y0) * MNS + (x - Y0)];
-                outp[(long long)gy * J.out.rs + gx] = SYN ? (mv + acc) + mu : mv - acc;
+        for (int k = 0; k < KP; k++) {
+            float ev = 0.f, od = 0.f;
+#pragma unroll
+            for (int t = -RS; t <= RS; t++) {
+                if ((t & 1) == 0) ev = fmaf(tap_s<RS>(t), z[k + SLO - t / 2], ev);
+                else od = fmaf(tap_s<RS>(t), z[k + SLO + (1 - t) / 2], od);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int y = 2 * (p0 + k) + h, gy = y0 + y;
+                if (gy < H && gx < W) {
+                    const float acc = h ? od : ev;
+                    const float mv = mcol[(2 * k + h) * MNS];
+                    ocol[(long long)gy * J.out.rs] = SYN ? (mv + acc) + mu : (SUB ? mv - mu : mv) - acc;
+                }
             }
         }
     }
