@@ -313,7 +313,29 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
 }
 
 // codes q (the next coder state) and residuals r of one frame per stream;
-// a block covers ELEM_BLOCK elements of one plane, ELEM_PER_THREAD per thread
+// a block covers ELEM_BLOCK elements of one plane, ELEM_PER_THREAD per thread.
+// Planes whose coefficients start on a 4-element boundary (all but odd layouts)
+// move runs of 4 consecutive elements with 16-byte float and 8-byte code
+// accesses: thread t takes elements 4t .. 4t + 3 and 4(t + ELEM_THREADS) ..
+// of its block; a ragged tail and a key frame's lowpass predictions go element
+// by element.  Every element takes the same operations either way.
+constexpr int ELEM_VEC = ELEM_PER_THREAD / 4;
+static_assert(ELEM_PER_THREAD % 4 == 0, "runs of four");
+
+__device__ __forceinline__ void unpack4(uint2 w, int* v) {
+    v[0] = (int16_t)(w.x & 0xFFFF);
+    v[1] = (int16_t)(w.x >> 16);
+    v[2] = (int16_t)(w.y & 0xFFFF);
+    v[3] = (int16_t)(w.y >> 16);
+}
+__device__ __forceinline__ uint2 pack4(const int* v) {
+    return make_uint2((uint32_t)(v[0] & 0xFFFF) | ((uint32_t)v[1] << 16), (uint32_t)(v[2] & 0xFFFF) | ((uint32_t)v[3] << 16));
+}
+__device__ __forceinline__ bool vec_ok(long long e0, const void* a, const void* b, const void* c, const void* d) {
+    return (e0 & 3) == 0 && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                              reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15) == 0;
+}
+
 __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restrict__ coef, int16_t* est0,
                                                           int16_t* est1, const PDesc* __restrict__ pd,
                                                           const int* __restrict__ blk_plane,
@@ -329,8 +351,60 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
     const QuantParams qp = sd[P.stream].qp;
     uint32_t* err = &out[P.stream].enc_err;
     const int total = (int)P.total, low_n = (int)P.low_n, low_w = P.low_w;
-    const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
     const float* cp = coef + P.coef_off;
+    if (vec_ok(P.coef_off, coef, est0, est1, res)) {
+        const int blk0 = (blockIdx.x - P.first_block) * ELEM_BLOCK;
+        // every load of the thread first, so that they are in flight together
+        float4 cv[ELEM_VEC];
+        uint2 pv[ELEM_VEC];
+#pragma unroll
+        for (int k = 0; k < ELEM_VEC; k++) {
+            const int le = blk0 + 4 * (threadIdx.x + k * ELEM_THREADS);
+            cv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pv[k] = make_uint2(0u, 0u);
+            if (le + 4 > total) continue;
+            cv[k] = *reinterpret_cast<const float4*>(cp + le);
+            if (!key) pv[k] = *reinterpret_cast<const uint2*>(cur + P.coef_off + le);
+        }
+#pragma unroll
+        for (int k = 0; k < ELEM_VEC; k++) {
+            const int le = blk0 + 4 * (threadIdx.x + k * ELEM_THREADS);
+            if (le >= total) break;
+            const bool whole = le + 4 <= total;
+            float c[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+            int pr[4], q[4], r[4];
+            unpack4(pv[k], pr);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int lj = le + j;
+                q[j] = r[j] = 0;
+                if (lj >= total) continue;
+                if (!whole) {
+                    c[j] = cp[lj];
+                    if (!key) pr[j] = cur[P.coef_off + lj];
+                }
+                const bool low = lj < low_n;
+                q[j] = quant(c[j], low, qp, err);
+                if (!key) r[j] = q[j] - pr[j];
+                else if (low && lj >= low_w) r[j] = q[j] - quant(cp[lj - low_w], true, qp, err);
+                else r[j] = q[j];
+            }
+            const long long e = P.coef_off + le;
+            if (whole) {
+                *reinterpret_cast<uint2*>(nxt + e) = pack4(q);
+                if (!mc) *reinterpret_cast<uint2*>(res + e) = pack4(r);   // wrapping 16-bit differences
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (le + j >= total) break;
+                    nxt[e + j] = (int16_t)q[j];
+                    if (!mc) res[e + j] = (int16_t)(uint16_t)(r[j] & 0xFFFF);
+                }
+            }
+        }
+        return;
+    }
+    const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
     // every load of the thread first, so that they are in flight together
     float cv[ELEM_PER_THREAD], ca[ELEM_PER_THREAD];
     int pv[ELEM_PER_THREAD];
@@ -360,7 +434,8 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
     }
 }
 
-// decoder side: codes from residuals, then dequantised coefficients
+// decoder side: codes from residuals, then dequantised coefficients (runs of four
+// elements as in k_quant_b where the plane's layout allows)
 __global__ void __launch_bounds__(ELEM_THREADS) k_unquant_b(const int16_t* __restrict__ res, int16_t* dst0,
                                                             int16_t* dst1, const PDesc* __restrict__ pd,
                                                             const int* __restrict__ blk_plane,
@@ -376,6 +451,50 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_unquant_b(const int16_t* __res
     int16_t* nxt = C.dcur ? dst0 : dst1;
     const QuantParams qp = sd[P.stream].qp;
     const int total = (int)P.total, low_n = (int)P.low_n;
+    if (vec_ok(P.coef_off, res, dst0, dst1, coef)) {
+        const int blk0 = (blockIdx.x - P.first_block) * ELEM_BLOCK;
+        uint2 rv[ELEM_VEC], cv[ELEM_VEC];
+#pragma unroll
+        for (int k = 0; k < ELEM_VEC; k++) {
+            const int le = blk0 + 4 * (threadIdx.x + k * ELEM_THREADS);
+            rv[k] = cv[k] = make_uint2(0u, 0u);
+            if (le + 4 > total || (key && le < low_n)) continue;
+            rv[k] = *reinterpret_cast<const uint2*>(res + P.coef_off + le);
+            if (!key) cv[k] = *reinterpret_cast<const uint2*>(cur + P.coef_off + le);
+        }
+#pragma unroll
+        for (int k = 0; k < ELEM_VEC; k++) {
+            const int le = blk0 + 4 * (threadIdx.x + k * ELEM_THREADS);
+            if (le >= total) break;
+            const long long e = P.coef_off + le;
+            if (le + 4 > total || (key && le < low_n)) {
+                // a ragged tail, or a run touching a key frame's lowpass (k_unquant_keylow_b's)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int lj = le + j;
+                    if (lj >= total) break;
+                    const bool low = lj < low_n;
+                    if (key && low) continue;
+                    const int q = key ? res[e + j] : (int16_t)(uint16_t)((res[e + j] + cur[e + j]) & 0xFFFF);
+                    nxt[e + j] = (int16_t)q;
+                    coef[e + j] = (float)q * (low ? qp.qpl_denorm : qp.qph);
+                }
+                continue;
+            }
+            int r[4], c[4], q[4];
+            unpack4(rv[k], r);
+            unpack4(cv[k], c);
+            float f[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                q[j] = key ? r[j] : (int16_t)(uint16_t)((r[j] + c[j]) & 0xFFFF);
+                f[j] = (float)q[j] * (le + j < low_n ? qp.qpl_denorm : qp.qph);
+            }
+            *reinterpret_cast<uint2*>(nxt + e) = pack4(q);
+            *reinterpret_cast<float4*>(coef + e) = make_float4(f[0], f[1], f[2], f[3]);
+        }
+        return;
+    }
     const int base = (blockIdx.x - P.first_block) * ELEM_BLOCK + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < ELEM_PER_THREAD; k++) {
