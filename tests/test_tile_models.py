@@ -1,14 +1,16 @@
-"""CPU checks of the index arithmetic of the tiled row-split DFB stage and the
-tiled RLE (tests/tile_models.py restates their indexing): in bounds, every
-output once, and equal to the plain definitions -- the row-split stencil of
-the plan emulator (§2.1) and a row-by-row run-length coder (§3.8)."""
+"""CPU checks of the index arithmetic of the tiled row-split DFB stage, the
+tiled RLE and the single-precision LP level tile (tests/tile_models.py
+restates their indexing): in bounds, every output once, and equal to the plain
+definitions -- the row-split stencil of the plan emulator (§2.1), a row-by-row
+run-length coder (§3.8) and the periodic down / up filtering of one pyramid
+level (§2.1, Fig. 1)."""
 import itertools
 
 import numpy as np
 import pytest
 
-from plan_emulator import _rowsplit_stencil
-from tile_models import geometry, passes, rle_tile, row_split_stage
+from plan_emulator import _down, _rowsplit_stencil, _up
+from tile_models import geometry, lp_level_tile, passes, rle_tile, row_split_stage
 
 # (R2, C, slope index i): ragged and periodic-wrapping arrays, arrays narrower than one
 # staged window, negative slopes (the tree's first channels), long shears
@@ -76,3 +78,39 @@ def test_rle_tiles():
             live = rng.random(res.size) < dens
             res[live] = rng.integers(-50, 50, int(live.sum()))
         assert rle_tile(res, pre, w * rows, w) == _rle_rows(res[pre:pre + w * rows], w), (w, rows, pre)
+
+
+def _dc_taps(rng, n, phases):
+    """random asymmetric taps (a mirrored index fails the check) with the 9/7 pair's DC gains, which
+    the tile's centring relies on: sum sqrt(2) for the decimating filter, 1/sqrt(2) per phase for the
+    expanding one"""
+    f = rng.uniform(0.2, 1.0, n)
+    for p in range(phases):
+        f[p::phases] *= (np.sqrt(2) / phases) / f[p::phases].sum()
+    return f
+
+
+@pytest.mark.parametrize("RA, RS, syn", [(4, 3, False), (4, 3, True), (3, 4, False)])
+def test_lp_level_tile(RA, RS, syn):
+    """the forward level's geometry (9 analysis taps, 7 synthesis taps), its synthesis and the
+    adjoint's (7, 9) on corner and interior tiles of a 192 x 128 periodic image with pixel-scale
+    values, against the whole-image definitions c = down(x), d = x - up(c) and
+    x = d + up(c - down(d))"""
+    rng = np.random.default_rng(RA * 10 + syn)
+    fa, fs = _dc_taps(rng, 2 * RA + 1, 1), _dc_taps(rng, 2 * RS + 1, 2)
+    H, W = 192, 128
+    main = rng.integers(0, 256, (H, W)).astype(np.float64) if not syn else rng.standard_normal((H, W))
+    cin = 500 * rng.random((H // 2, W // 2)) if syn else None
+    lo = 1e-6 * rng.standard_normal((H // 2, W // 2)) if syn else None
+    if syn:
+        want_out = main + _up(cin + lo - _down(main, fa), fs)
+    else:
+        want_c = _down(main, fa)
+        want_out = main - _up(want_c, fs)
+    for ty, tx in ((0, 0), (1, 1), (2, 1)):
+        out, cout = lp_level_tile(RA, RS, syn, fa, fs, main, ty, tx, cin, lo)
+        ys, xs = slice(64 * ty, 64 * ty + 64), slice(64 * tx, 64 * tx + 64)
+        assert np.abs(out - want_out[ys, xs]).max() < 1e-9, (ty, tx)
+        if not syn:
+            cs, cx = slice(32 * ty, 32 * ty + 32), slice(32 * tx, 32 * tx + 32)
+            assert np.abs(cout - want_c[cs, cx]).max() < 1e-9, (ty, tx)

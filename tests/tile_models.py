@@ -15,6 +15,11 @@ row_split_stage: `dfb_b_tile` (csrc/dfb_tile.cuh), one row-split stage s >= 3
   both store paths.
 rle_tile: `k_rle_count_b` / `k_rle_write_b` (csrc/k_codec.cu), the tokens of
   one tile of whole rows (§3.8) from the per-chunk bit masks and block scans.
+lp_level_tile: `lp_level_tile` (csrc/lp_tile.cuh), one 64 x 64 tile of a
+  single-precision Laplacian-pyramid level (§2.1, Fig. 1), analysis or
+  synthesis, centred on the tile's rounded mean: the staged window, the four
+  passes with a run of outputs per thread read from one window, the lowpass
+  share stored from the column pass.
 """
 import numpy as np
 
@@ -223,3 +228,116 @@ def rle_tile(res, e0, n, w):
         carry_s = max(carry_s, max(ls))
     assert sorted(tok) == list(range(count)), "token positions fill the tile's count exactly"
     return [tok[i] for i in range(count)]
+
+
+# ------------------------------------------------------------------ LP level tile
+LP_T = 64
+
+
+def lp_geometry(RA, RS):
+    """LevelGeo<RA, RS>: half-resolution window, staged window, strides, runs per thread"""
+    MLO = -(RS // 2)
+    VN = (LP_T - 1 + RS) // 2 - MLO + 1
+    MN = 2 * (VN - 1) + 2 * RA + 1
+    run = 7 if VN % 7 == 0 else 6 if VN % 6 == 0 else 5
+    return dict(MLO=MLO, VN=VN, MN=MN, Y0=2 * MLO - RA, MNS=MN + (MN & 1), TS=LP_T + 2,
+                NA=max(MN * VN, VN * (LP_T + 2)), KR=run, KC=run, KP=8, SLO=RS // 2, SHI=(RS + 1) // 2)
+
+
+def _rd(buf, i):
+    assert 0 <= i < buf.size, ("shared read out of its array", i, buf.size)
+    assert not np.isnan(buf[i]), ("shared read before write", i)
+    return buf[i]
+
+
+def lp_level_tile(RA, RS, syn, fa, fs, main, ty, tx, cin=None, cin_lo=None):
+    """one tile (ty, tx) of a level: analysis (cout, out) of the periodic image main, or synthesis out
+    from the detail main and the coarse lowpass cin (+ cin_lo); returns (out 64 x 64, cout 32 x 32 or
+    None) with the kernel's indexing, every shared access checked in bounds and initialised"""
+    g = lp_geometry(RA, RS)
+    MLO, VN, MN, Y0, MNS, TS, NA = (g[k] for k in ("MLO", "VN", "MN", "Y0", "MNS", "TS", "NA"))
+    H, W = main.shape
+    y0, x0 = ty * LP_T, tx * LP_T
+    m0, n0 = y0 // 2, x0 // 2
+    ta = lambda b: fa[b + RA]
+    ts = lambda t: fs[t + RS]
+    s_main = np.full(MN * MNS, np.nan)
+    for r in range(MN):
+        for c in range(MN):
+            s_main[r * MNS + c] = main[(y0 + Y0 + r) % H, (x0 + Y0 + c) % W]
+    s_v = np.full(VN * VN, np.nan)
+    if syn:
+        for m in range(VN):
+            for n in range(VN):
+                s_v[m * VN + n] = cin[(m0 + MLO + m) % (H // 2), (n0 + MLO + n) % (W // 2)]
+        mu = float(np.rint(s_v.sum() / (2 * VN * VN)))
+        for m in range(VN):
+            for n in range(VN):
+                e = s_v[m * VN + n] - 2 * mu
+                if cin_lo is not None:
+                    e += cin_lo[(m0 + MLO + m) % (H // 2), (n0 + MLO + n) % (W // 2)]
+                s_v[m * VN + n] = e
+    else:
+        mu = float(np.rint(np.nansum(s_main[:MN * MNS]) / (MN * MN)))
+    sub = mu if not syn else 0.0
+    # decimating row pass
+    s_a = np.full(NA, np.nan)
+    KR = g["KR"]
+    for i in range(MN * (VN // KR)):
+        run, r = divmod(i, MN)
+        w = r * MNS + 2 * KR * run
+        assert w % 2 == 0, "pair loads"
+        x = [_rd(s_main, w + j) - sub for j in range(2 * KR + 2 * RA - 1)]
+        for k in range(KR):
+            s_a[r * VN + KR * run + k] = sum(ta(b) * x[2 * k + RA - b] for b in range(-RA, RA + 1))
+    # decimating column pass, the lowpass share
+    KC = g["KC"]
+    cout = None if syn else np.full((LP_T // 2, LP_T // 2), np.nan)
+    for i in range(VN * (VN // KC)):
+        run, n = divmod(i, VN)
+        mr = KC * run
+        y = [_rd(s_a, (2 * mr + j) * VN + n) for j in range(2 * KC + 2 * RA - 1)]
+        for k in range(KC):
+            acc = sum(ta(a) * y[2 * k + RA - a] for a in range(-RA, RA + 1))
+            m = mr + k
+            if syn:
+                s_v[m * VN + n] = _rd(s_v, m * VN + n) - acc
+            else:
+                s_v[m * VN + n] = acc
+                if 0 <= m + MLO < LP_T // 2 and 0 <= n + MLO < LP_T // 2:
+                    assert np.isnan(cout[m + MLO, n + MLO])
+                    cout[m + MLO, n + MLO] = acc + 2 * mu
+    # expanding passes, pairs of outputs, runs of KP pairs
+    KP, SLO, SHI = g["KP"], g["SLO"], g["SHI"]
+    NWE = KP + SLO + SHI
+
+    def pairs(z, k):
+        ev = sum(ts(t) * z[k + SLO - t // 2] for t in range(-RS, RS + 1) if t % 2 == 0)
+        od = sum(ts(t) * z[k + SLO + (1 - t) // 2] for t in range(-RS, RS + 1) if t % 2)
+        return ev, od
+
+    s_a = np.full(NA, np.nan)
+    for i in range(VN * (LP_T // 2 // KP)):
+        run, m = divmod(i, VN)
+        p0 = KP * run
+        vb = m * VN + p0 - MLO - SLO
+        assert vb >= m * VN and vb + NWE <= (m + 1) * VN, "a window inside its row"
+        z = [_rd(s_v, vb + j) for j in range(NWE)]
+        for k in range(KP):
+            d = m * TS + 2 * (p0 + k)
+            assert d + 1 < NA
+            s_a[d], s_a[d + 1] = pairs(z, k)
+    out = np.full((LP_T, LP_T), np.nan)
+    for i in range(LP_T * (LP_T // 2 // KP)):
+        run, x = divmod(i, LP_T)
+        p0 = KP * run
+        z = [_rd(s_a, (p0 - MLO - SLO + j) * TS + x) for j in range(NWE)]
+        for k in range(KP):
+            ev, od = pairs(z, k)
+            for h, acc in ((0, ev), (1, od)):
+                yy = 2 * (p0 + k) + h
+                mv = _rd(s_main, (2 * p0 - Y0) * MNS + (x - Y0) + (2 * k + h) * MNS)
+                assert np.isnan(out[yy, x]), "an output written twice"
+                out[yy, x] = (mv + acc) + mu if syn else (mv - sub) - acc
+    assert not np.isnan(out).any()
+    return out, cout
