@@ -297,6 +297,7 @@ cvc_status core_plan(Core* c, const cvc_params* params, int n) {
         D.qp.st8 = P.storage8;
         D.qp.rqph = (P.qph & (P.qph - 1)) == 0 ? 1.0f / (float)P.qph : 0.0f;
         D.qp.rqpl = (P.qpl & (P.qpl - 1)) == 0 ? 1.0f / (float)P.qpl : 0.0f;
+        if (D.qp.rqph == 0.0f || D.qp.rqpl == 0.0f) c->quant_pow2 = false;
         D.hdr.levels = L;
         D.hdr.height = g.H;
         D.hdr.width = g.W;
@@ -641,8 +642,8 @@ cudaError_t enqueue_direct(Core* c, int mode, int scale, cudaStream_t st, bool t
         k += 1 + engine_part_launches(&c->eng, FWD, 0) + engine_part_launches(&c->eng, FWD, 1) + ntail;
         // S6-S8: normalise, threshold, quantise, K/P differencing
         clk.begin(3);
-        k_quant_b<<<(int)c->h_blk_plane.size(), ELEM_THREADS, 0, st>>>(
-            c->d_coef, c->d_est_buf[0], c->d_est_buf[1], c->d_pd, c->d_blk_plane, c->d_sd, c->d_sc, c->d_res, c->d_rs);
+        launch_quant_b(c->quant_pow2, (int)c->h_blk_plane.size(), st, c->d_coef, c->d_est_buf[0], c->d_est_buf[1],
+                       c->d_pd, c->d_blk_plane, c->d_sd, c->d_sc, c->d_res, c->d_rs);
         CK(cudaGetLastError());
         if (motion) {
             // §3.2 motion search, then the residuals of the motion-compensated P-frames

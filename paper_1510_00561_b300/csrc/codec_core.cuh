@@ -120,6 +120,7 @@ struct Core {
     std::vector<uint8_t> pend_reset;
     // CUDA graphs of the step modes: one set per decoding scale (in ScalePlan)
     bool use_graphs = true;
+    bool quant_pow2 = true;   // every stream's quantiser steps are powers of two
     cudaStream_t cap_stream = nullptr;
     // the pyramid tails run on a side stream, beside the DFB launches of the other levels
     // (fork / join events: [0] analysis, [1] synthesis)

@@ -295,6 +295,8 @@ __global__ void k_colour_inv_b(const ScaleDesc* __restrict__ sdesc, const SCall*
 }
 
 // ------------------------------------------------------ quantisation + K/P
+// POW2: every step of the launch is a power of two (no division in the kernel)
+template <bool POW2 = false>
 __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, uint32_t* err) {
     float t;
     if (low) t = c * q.low_scale;                    // exact power-of-two normalisation
@@ -302,7 +304,7 @@ __device__ __forceinline__ int quant(float c, bool low, const QuantParams& q, ui
     // the IEEE quotient t / QP, ties away from zero; for a power-of-two QP the product with
     // its exact reciprocal is that same correctly rounded quotient
     const float r = low ? q.rqpl : q.rqph;
-    float v = roundf(r != 0.0f ? t * r : t / (low ? q.qpl : q.qph));
+    float v = roundf(POW2 || r != 0.0f ? t * r : t / (low ? q.qpl : q.qph));
     // 8-bit storage (§3.6): the rounded code is kept in a byte
     if (q.st8) v = low ? fminf(fmaxf(v, 0.0f), 255.0f) : fminf(fmaxf(v, -128.0f), 127.0f);
     if (!(fabsf(v) <= 32767.0f)) {
@@ -336,6 +338,7 @@ __device__ __forceinline__ bool vec_ok(long long e0, const void* a, const void* 
                               reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15) == 0;
 }
 
+template <bool POW2>
 __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restrict__ coef, int16_t* est0,
                                                           int16_t* est1, const PDesc* __restrict__ pd,
                                                           const int* __restrict__ blk_plane,
@@ -384,9 +387,9 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
                     if (!key) pr[j] = cur[P.coef_off + lj];
                 }
                 const bool low = lj < low_n;
-                q[j] = quant(c[j], low, qp, err);
+                q[j] = quant<POW2>(c[j], low, qp, err);
                 if (!key) r[j] = q[j] - pr[j];
-                else if (low && lj >= low_w) r[j] = q[j] - quant(cp[lj - low_w], true, qp, err);
+                else if (low && lj >= low_w) r[j] = q[j] - quant<POW2>(cp[lj - low_w], true, qp, err);
                 else r[j] = q[j];
             }
             const long long e = P.coef_off + le;
@@ -424,10 +427,10 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_quant_b(const float* __restric
         if (le >= total) break;
         const long long e = P.coef_off + le;
         const bool low = le < low_n;
-        const int q = quant(cv[k], low, qp, err);
+        const int q = quant<POW2>(cv[k], low, qp, err);
         int r;
         if (!key) r = q - pv[k];
-        else if (low && le >= low_w) r = q - quant(ca[k], true, qp, err);
+        else if (low && le >= low_w) r = q - quant<POW2>(ca[k], true, qp, err);
         else r = q;
         nxt[e] = (int16_t)q;
         if (!mc) res[e] = (int16_t)(uint16_t)(r & 0xFFFF);   // wrapping 16-bit difference
@@ -1521,6 +1524,13 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, const uint32_t* d_n, uint32_t
     k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
     k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, 0, d_n, tmp, out);
     return cudaGetLastError();
+}
+
+void launch_quant_b(bool pow2, int nblocks, cudaStream_t st, const float* coef, int16_t* est0, int16_t* est1,
+                    const PDesc* pd, const int* blk_plane, const SDesc* sd, const SCall* sc, int16_t* res,
+                    SResult* out) {
+    if (pow2) k_quant_b<true><<<nblocks, ELEM_THREADS, 0, st>>>(coef, est0, est1, pd, blk_plane, sd, sc, res, out);
+    else k_quant_b<false><<<nblocks, ELEM_THREADS, 0, st>>>(coef, est0, est1, pd, blk_plane, sd, sc, res, out);
 }
 
 }  // namespace cvc

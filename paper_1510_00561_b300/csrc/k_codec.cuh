@@ -198,8 +198,11 @@ __global__ void k_mc_recon_b(const int16_t* res, int16_t* dst0, int16_t* dst1, R
                              const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
 __global__ void k_colour_inv_b(const ScaleDesc* sdesc, const SCall* sc, const SResult* rs, const int* blk_stream,
                                const float* rplanes, const float* dcoef);
-__global__ void k_quant_b(const float* coef, int16_t* est0, int16_t* est1, const PDesc* pd, const int* blk_plane,
-                          const SDesc* sd, const SCall* sc, int16_t* res, SResult* out);
+// k_quant_b<POW2> over nblocks element blocks; pow2: every stream's steps are powers of two
+// (the quotients are products; the kernel carries no division code)
+void launch_quant_b(bool pow2, int nblocks, cudaStream_t st, const float* coef, int16_t* est0, int16_t* est1,
+                    const PDesc* pd, const int* blk_plane, const SDesc* sd, const SCall* sc, int16_t* res,
+                    SResult* out);
 __global__ void k_unquant_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, const int* blk_plane,
                             const SDesc* sd, const SCall* sc, const SResult* rs, float* coef);
 __global__ void k_unquant_keylow_b(const int16_t* res, int16_t* dst0, int16_t* dst1, const PDesc* pd, int nplanes,
