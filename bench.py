@@ -42,19 +42,19 @@ CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": "ae117dff5f33b9ff64da7cda8618c8da7000c3219cdbf0204b484ba60b0adecc",
-           "dram_per_frame": {"colour_fwd": 6652032,
-                              "lp_analysis": 21057152,
-                              "dfb_analysis": 81437184,
-                              "quantise_kp": 33489024,
-                              "rle_stream": 17114752,
-                              "parse_unrle": 3733056,
-                              "unquantise_kp": 28959936,
-                              "dfb_synthesis": 82376384,
-                              "lp_synthesis": 29172672,
-                              "colour_inv": 12542976,
-                              "step": 316538560},
-           "warp_inst_per_frame": 173377112,
+CAPTURE = {"sources_sha256": "0059fef9443845cf2bac0aa551b3c027e50bc35a68b33c73f00acb2b8a22b244",
+           "dram_per_frame": {"colour_fwd": 6652736,
+                              "lp_analysis": 21055296,
+                              "dfb_analysis": 81370624,
+                              "quantise_kp": 33340480,
+                              "rle_stream": 17114624,
+                              "parse_unrle": 3705728,
+                              "unquantise_kp": 28105088,
+                              "dfb_synthesis": 82351552,
+                              "lp_synthesis": 29116480,
+                              "colour_inv": 12571200,
+                              "step": 315387200},
+           "warp_inst_per_frame": 166782336,
            "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
 SMSP_PER_SM, N_SM = 4, 148
