@@ -1037,7 +1037,7 @@ def main():
     def frames_at(i):
         return [d_frames[(i + 3 * j) % F] for j in range(B)]
 
-    shape = (8, 148 * 8, 6) if args.no_autotune else batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
+    shape = (8, 148 * 8, 0, 0) if args.no_autotune else batch.autotune(3, rgb=frames_at(0), rgb_out=outs_rgb, reps=3)
     info0 = batch.info[0]
     batch_bytes = [0]
 
@@ -1140,6 +1140,7 @@ def main():
                              key_interval=KINT)] * B)
         dbatch.set_shape(*shape[:2])
         dbatch.set_fusion(shape[2])
+        dbatch.set_dfb_threads(shape[3])
         sc_steps = max(KINT, min(args.steps, 2 * KINT))
         scales = []
         for sc in range(LEVELS + 1):
@@ -1170,6 +1171,7 @@ def main():
                          key_interval=KINT, motion_range=args.motion_range)] * B)
         mb.set_shape(*shape[:2])
         mb.set_fusion(shape[2])
+        mb.set_dfb_threads(shape[3])
         m_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
         m_bytes = [0, 0]
 
@@ -1205,6 +1207,7 @@ def main():
                              key_interval=KINT, dfb_taps=nt)] * B)
             tb.set_shape(*shape[:2])
             tb.set_fusion(shape[2])
+            tb.set_dfb_threads(shape[3])
             t_outs = [torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)]
 
             def taps_step(i, tb=tb, t_outs=t_outs):

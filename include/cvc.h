@@ -479,13 +479,20 @@ cvc_status cvc_batch_get_error(cvc_batch* batch, int i, cvc_stream_t stream, cvc
  * launches, the default (one block per plane runs the coarse levels' tiles
  * one after the other, which on a 1080p frame is slower than their own
  * launches; the autotuner tries tails of 1, 2 and CVC_MAX_LEVELS levels).
- * cvc_batch_autotune times candidate shapes and fusion depths on steps over
- * `io` (the outputs of io are written; no coder state changes), keeps the
- * fastest and returns it in shape[3] = {rle_rows, tok_blocks, fusion depth}
- * (may be NULL).  Graph replay can be switched off (on = 0) to run the same
- * launches one by one.                                                      */
+ * Row-split DFB block width (changes no result either): threads per block of
+ * the launches of DFB stages 3 and later (§2.1), 128 (four warps, each a run
+ * of the tile's rows) or 256 (eight warps, shorter runs: sooner done where a
+ * launch has fewer blocks than the GPU holds); 0, the default, takes 256 for
+ * a launch of less than a wave of 128-thread blocks, else 128.  Anything
+ * else is INVALID_ARG.
+ * cvc_batch_autotune times candidate shapes, fusion depths and block widths
+ * on steps over `io` (the outputs of io are written; no coder state
+ * changes), keeps the fastest and returns it in shape[4] = {rle_rows,
+ * tok_blocks, fusion depth, row-split block width} (may be NULL).  Graph
+ * replay can be switched off (on = 0) to run the same launches one by one. */
 cvc_status cvc_batch_set_shape(cvc_batch* batch, int rle_rows, int tok_blocks);
 cvc_status cvc_batch_set_fusion(cvc_batch* batch, int levels);
+cvc_status cvc_batch_set_dfb_threads(cvc_batch* batch, int threads);
 cvc_status cvc_batch_autotune(cvc_batch* batch, int what, const cvc_batch_io* io, int reps, int* shape,
                               cvc_stream_t stream);
 cvc_status cvc_batch_set_graphs(cvc_batch* batch, int on);

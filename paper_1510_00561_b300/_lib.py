@@ -156,6 +156,7 @@ def lib():
         L.cvc_batch_get_error.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
         L.cvc_batch_set_shape.argtypes = [_P, _I, _I]
         L.cvc_batch_set_fusion.argtypes = [_P, _I]
+        L.cvc_batch_set_dfb_threads.argtypes = [_P, _I]
         L.cvc_batch_autotune.argtypes = [_P, _I, ctypes.POINTER(BatchIo), _I, ctypes.POINTER(_I), _P]
         L.cvc_batch_set_graphs.argtypes = [_P, _I]
         L.cvc_batch_set_timing.argtypes = [_P, _I]

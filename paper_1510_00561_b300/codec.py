@@ -491,17 +491,22 @@ class Batch:
         return {name: (ms[i], n[i]) for i, name in enumerate(_L.STAGE_NAMES)}
 
     def autotune(self, what, rgb=None, streams_in=None, rgb_out=None, reps=5, stream=None):
-        """Time candidate launch shapes and fusion depths on these inputs, keep the fastest;
-        returns (rle_rows, tok_blocks, fusion depth)."""
+        """Time candidate launch shapes, fusion depths and row-split DFB block widths on these
+        inputs, keep the fastest; returns (rle_rows, tok_blocks, fusion depth, block width)."""
         self._fill(rgb, streams_in, rgb_out, None)
-        shape = (ctypes.c_int * 3)()
+        shape = (ctypes.c_int * 4)()
         _L.check(_L.lib().cvc_batch_autotune(self._h, what, self._io, reps, shape, _stream(stream)),
                  "cvc_batch_autotune")
-        return shape[0], shape[1], shape[2]
+        return shape[0], shape[1], shape[2], shape[3]
 
     def set_fusion(self, levels):
         """cvc_batch_set_fusion: the most coarse levels of each plane in its pyramid tail (0: none)"""
         _L.check(_L.lib().cvc_batch_set_fusion(self._h, int(levels)), "cvc_batch_set_fusion")
+
+    def set_dfb_threads(self, threads):
+        """cvc_batch_set_dfb_threads: threads per block of the row-split DFB launches (0: by
+        launch size, 128 or 256)"""
+        _L.check(_L.lib().cvc_batch_set_dfb_threads(self._h, int(threads)), "cvc_batch_set_dfb_threads")
 
 
 class Server:

@@ -907,6 +907,18 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
         if (s == CVC_OK && ms < best_ms) best_fuse = f, best_ms = ms;
     }
     if (s == CVC_OK && c->eng.tail_levels != best_fuse) s = core_set_fusion(c, best_fuse);
+    // then the block width of the row-split DFB launches: by launch size, 128 or 256 threads
+    const int dfbb_cand[] = {0, DFBB_THREADS, DFBB_THREADS_WIDE};
+    int best_dfbb = c->eng.dfbb_threads;
+    for (int t : dfbb_cand) {
+        if (s != CVC_OK) break;
+        if (t == best_dfbb) continue;
+        s = core_set_dfb_threads(c, t);
+        float ms = 0.f;
+        if (s == CVC_OK) s = measure(best, &ms);
+        if (s == CVC_OK && ms < best_ms) best_dfbb = t, best_ms = ms;
+    }
+    if (s == CVC_OK && c->eng.dfbb_threads != best_dfbb) s = core_set_dfb_threads(c, best_dfbb);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->shape = best;
@@ -915,8 +927,14 @@ cvc_status cvc_batch_autotune(cvc_batch* b, int what, const cvc_batch_io* io, in
         shape[0] = best.rle_rows;
         shape[1] = best.tok_blocks;
         shape[2] = best_fuse;
+        shape[3] = best_dfbb;
     }
     return s;
+}
+
+cvc_status cvc_batch_set_dfb_threads(cvc_batch* b, int threads) {
+    if (!b) return CVC_ERR_INVALID_ARG;
+    return core_set_dfb_threads(&b->core, threads);
 }
 
 cvc_status cvc_batch_set_fusion(cvc_batch* b, int levels) {

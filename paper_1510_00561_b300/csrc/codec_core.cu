@@ -560,6 +560,19 @@ cvc_status core_set_fusion(Core* c, int levels) {
     return CVC_OK;
 }
 
+cvc_status core_set_dfb_threads(Core* c, int threads) {
+    if (threads != 0 && threads != DFBB_THREADS && threads != DFBB_THREADS_WIDE) return CVC_ERR_INVALID_ARG;
+    // captured graphs hold the old launches: nothing may still be running on them
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CVC_ERR_CUDA;
+    }
+    core_drop_graphs(c);
+    c->eng.dfbb_threads = threads;
+    for (size_t sc = 1; sc < c->scale.size(); sc++) c->scale[sc]->eng.dfbb_threads = threads;
+    return CVC_OK;
+}
+
 void core_scaled_size(const Core* c, int s, int scale, int* h, int* w) {
     const ColourGeom& g = c->sd[s].cg;
     const int f = 1 << scale;

@@ -166,6 +166,8 @@ void core_drop_graphs(Core* c);
 // the most coarse levels of each plane in its pyramid tail (0..CVC_MAX_LEVELS); rebuilds
 // the transform tables of every scale and drops the graphs
 cvc_status core_set_fusion(Core* c, int levels);
+// threads per block of the row-split DFB launches: 0 (by launch size), 128 or 256
+cvc_status core_set_dfb_threads(Core* c, int threads);
 
 // fill the call record of stream s for a step (after core_begin); returns false on bad arguments
 struct StreamIo {

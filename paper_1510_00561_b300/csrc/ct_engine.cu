@@ -483,7 +483,7 @@ cudaError_t engine_run_part(const CtEngine* e, Mode m, int part, Bases bases, cu
             if ((err = launch_lp(L, m, bases, st)) != cudaSuccess) return err;
     } else if (part == 1) {
         for (const LaunchDfb& L : e->dfb[m])
-            if ((err = launch_dfb(L, m, bases, st)) != cudaSuccess) return err;
+            if ((err = launch_dfb(L, m, bases, st, e->dfbb_threads)) != cudaSuccess) return err;
     } else {
         for (const LaunchTail& L : e->tail[m])
             if ((err = launch_tail(L, m, bases, st)) != cudaSuccess) return err;

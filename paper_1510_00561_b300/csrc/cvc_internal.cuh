@@ -98,6 +98,8 @@ struct DfbBJob {
 constexpr int DFBA_TILE = 64, DFBA_HALO = 12;   // the halo of the 4-tap prototype (4 (NT - 1) in general)
 constexpr int DFBB_ROWS = 16, DFBB_COLS = 120;  // columns of the 4-tap prototype ((128 - 2 (NT - 1)) & ~3 in general)
 constexpr int dfbb_cols(int ntaps) { return (128 - 2 * (ntaps - 1)) & ~3; }
+constexpr int DFBB_THREADS = 128;        // row-split blocks: four warps, one run of rows each in the ladder passes
+constexpr int DFBB_THREADS_WIDE = 256;   // eight warps: for launches smaller than a wave (latency)
 
 // One Laplacian-pyramid tile job (one level of one plane):
 //   analysis:  cout = down(main, fa);           out = main - up(cout, fs)
@@ -211,6 +213,7 @@ struct CtEngine {
     // for 1080p planes; the autotuner tries the others); a plane's tail takes as many of
     // them as fit the shared-memory budget
     int tail_levels = 0;
+    int dfbb_threads = 0;   // threads per block of the row-split DFB launches (launch_dfb's bthreads)
     std::vector<void*> allocs;
     ~CtEngine();
 };
@@ -235,7 +238,9 @@ void note_launches(long long n);
 cudaError_t launch_lp(const LaunchLp& L, Mode m, Bases bases, cudaStream_t st);
 // one-time kernel attributes of the LP kernels (call before any stream capture)
 cudaError_t lp_prepare();
-cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st);
+// bthreads: threads per block of the row-split launches (128 or 256; 0: 256 for a launch of
+// less than a wave of 128-thread blocks, else 128); it changes no result
+cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st, int bthreads = 0);
 // one-time kernel attributes of the DFB kernels (call before any stream capture)
 cudaError_t dfb_prepare();
 PassParams pass_params(Mode m);

@@ -468,8 +468,6 @@ struct BGeo {
     static constexpr int SMB = RB * CBS + 2 * MARGIN;   // floats per tile array
     static constexpr int D = NT == 4 ? 2 : 0;
 };
-constexpr int DFBB_THREADS = 128;    // four warps: one run of rows each in the ladder passes
-constexpr int DFBB_THREADS_WIDE = 256;   // eight warps: for launches smaller than a wave (latency)
 static_assert(BGeo<4>::COLS == DFBB_COLS && dfbb_cols(4) == BGeo<4>::COLS && dfbb_cols(6) == BGeo<6>::COLS &&
                   dfbb_cols(8) == BGeo<8>::COLS,
               "host and device tile widths");

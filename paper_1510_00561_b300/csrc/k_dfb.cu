@@ -81,7 +81,7 @@ PassParams pass_params(Mode m) {
     }
 }
 
-cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st) {
+cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st, int bthreads) {
     if (L.nblocks == 0) return cudaSuccess;
     const bool syn = (m == INV || m == FWD_ADJ);
     const PassParams pp = pass_params(m);
@@ -101,8 +101,8 @@ cudaError_t launch_dfb(const LaunchDfb& L, Mode m, Bases bases, cudaStream_t st)
         const DfbBJob* j = static_cast<const DfbBJob*>(L.d_jobs);
         const bool fo = pp.first_odd != 0;
         // a launch of less than a wave of 128-thread blocks waits on each block's latency:
-        // eight warps per tile finish it sooner
-        const bool wide = L.nblocks < 148 * 8;
+        // eight warps per tile finish it sooner (unless the caller chose the width)
+        const bool wide = bthreads ? bthreads == DFBB_THREADS_WIDE : L.nblocks < 148 * 8;
 #define CVC_DFBB_T(S, N, TH)                                                                            \
     do {                                                                                                \
         if (fo) k_dfb_b<S, N, true, TH><<<L.nblocks, TH, 0, st>>>(j, L.d_block_job, bases, pp);          \

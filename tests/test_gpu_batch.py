@@ -108,19 +108,22 @@ def test_encode_and_decode_steps_with_idle_streams():
 
 
 def test_launch_shapes_fusion_depths_and_graph_replay_change_nothing():
-    """Launch shapes, graph replay and the pyramid tail's fusion depth (0: every level its own
+    """Launch shapes, graph replay, the pyramid tail's fusion depth (0: every level its own
     launches, the default; 1, 2: tails of at most that many levels; 6: as many levels as fit)
-    give bit-identical bitstreams and reconstructions: a tail runs the same tile computations."""
+    and the row-split DFB block width (0: by launch size; 128; 256) give bit-identical
+    bitstreams and reconstructions: every variant runs the same tile computations."""
     streams = _streams(1)
     frames = _inputs(1, 3)
     ref = None
-    for graphs, rows, tok, fuse in [(True, 8, 1184, 0), (False, 8, 1184, 0), (True, 1, 1, 0), (True, 32, 65535, 0),
-                                    (True, 3, 7, 0), (True, 8, 1184, 6), (False, 8, 1184, 6), (True, 8, 1184, 1),
-                                    (True, 8, 1184, 2)]:
+    for graphs, rows, tok, fuse, bt in [(True, 8, 1184, 0, 0), (False, 8, 1184, 0, 0), (True, 1, 1, 0, 0),
+                                        (True, 32, 65535, 0, 0), (True, 3, 7, 0, 0), (True, 8, 1184, 6, 0),
+                                        (False, 8, 1184, 6, 0), (True, 8, 1184, 1, 0), (True, 8, 1184, 2, 0),
+                                        (True, 8, 1184, 0, 128), (True, 8, 1184, 0, 256), (False, 8, 1184, 2, 256)]:
         b = Batch(streams)
         b.set_graphs(graphs)
         b.set_shape(rows, tok)
         b.set_fusion(fuse)
+        b.set_dfb_threads(bt)
         outs = _rgb_buffers(streams)
         got = []
         for t in range(3):
@@ -131,7 +134,7 @@ def test_launch_shapes_fusion_depths_and_graph_replay_change_nothing():
             continue
         for a, c in zip(ref, got):
             for x, y in zip(a, c):
-                assert torch.equal(x, y), (graphs, rows, tok, fuse)
+                assert torch.equal(x, y), (graphs, rows, tok, fuse, bt)
 
 
 def test_autotune_keeps_state_and_output():
@@ -140,8 +143,8 @@ def test_autotune_keeps_state_and_output():
     b = Batch(streams)
     plain = [Codec(**s) for s in streams]
     outs = _rgb_buffers(streams)
-    rows, tok, fuse = b.autotune(3, rgb=[f[0] for f in frames], rgb_out=outs, reps=2)
-    assert 1 <= rows <= 32 and 1 <= tok <= 65535 and fuse in (0, 1, 2, 6)
+    rows, tok, fuse, bt = b.autotune(3, rgb=[f[0] for f in frames], rgb_out=outs, reps=2)
+    assert 1 <= rows <= 32 and 1 <= tok <= 65535 and fuse in (0, 1, 2, 6) and bt in (0, 128, 256)
     for t in range(3):
         res = b.step(3, rgb=[f[t] for f in frames], rgb_out=outs)
         for i, c in enumerate(plain):
