@@ -1071,9 +1071,13 @@ def main():
 
     # batched end to end through the public API: every step uploads its B frames
     # from pinned memory and downloads its B bitstreams and B reconstructed
-    # frames.  Double-buffered, so step t+1's upload and step t-1's download run
-    # on a copy stream while step t computes.
-    copy_st = torch.cuda.Stream(dev)
+    # frames.  Double-buffered and asynchronous (cvc_batch_step_async): step t+1
+    # is queued before the host reads step t's lengths and queues its downloads,
+    # so the device never waits for the host; uploads and downloads run on copy
+    # streams of their own (the host-to-device and device-to-host copy engines
+    # work at once) while the steps compute.
+    copy_st = torch.cuda.Stream(dev)     # uploads
+    down_st = torch.cuda.Stream(dev)     # downloads
     d_ins = [[torch.empty((H_, W_, 3), dtype=torch.uint8, device=dev) for _ in range(B)] for _ in range(2)]
     d_outs = [[torch.empty(batch.info[j].max_stream_bytes, dtype=torch.uint8, device=dev) for j in range(B)]
               for _ in range(2)]
@@ -1081,8 +1085,11 @@ def main():
     h_outs = [[torch.empty(batch.info[j].max_stream_bytes, dtype=torch.uint8).pin_memory() for j in range(B)]
               for _ in range(2)]
     h_rgbs = [[torch.empty((H_, W_, 3), dtype=torch.uint8).pin_memory() for _ in range(B)] for _ in range(2)]
+    d_res = [batch.results_buffer(dev) for _ in range(2)]
+    h_res = [torch.empty(d_res[0].numel(), dtype=torch.uint8).pin_memory() for _ in range(2)]
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_res = [torch.cuda.Event() for _ in range(2)]
     io_bytes = [0, 0]
 
     def upload(t, k):
@@ -1092,30 +1099,47 @@ def main():
                 io_bytes[0] += d_ins[k][j].numel()
             ev_in[k].record(copy_st)
 
+    def download(k):
+        # the step in slot k has finished: its per-stream results are on the host
+        ev_res[k].synchronize()
+        res = batch.results_of(h_res[k])
+        with torch.cuda.stream(down_st):
+            down_st.wait_event(ev_res[k])
+            for j in range(B):
+                if res[j]["enc_status"] != 0 or res[j]["dec_status"] != 0:
+                    raise RuntimeError("end-to-end step failed on stream %d: %s" % (j, res[j]))
+                n = res[j]["out_len"]
+                h_outs[k][j][:n].copy_(d_outs[k][j][:n], non_blocking=True)
+                h_rgbs[k][j].copy_(d_rgbs[k][j], non_blocking=True)
+                io_bytes[1] += n + d_rgbs[k][j].numel()
+            ev_out[k].record(down_st)
+
     def e2e_run(nsteps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         for k in range(2):
             ev_out[k].record(stream)
+            ev_res[k].record(stream)
         e0.record(stream)
         copy_st.wait_event(e0)
+        down_st.wait_event(e0)
         upload(0, 0)
         for t in range(nsteps):
             k = t % 2
             if t + 1 < nsteps:
+                copy_st.wait_event(ev_res[1 - k])   # step t-1 has read its inputs (slot 1-k)
                 upload(t + 1, 1 - k)
             stream.wait_event(ev_in[k])
-            stream.wait_event(ev_out[k])        # buffers k downloaded two steps ago
-            res = batch.step(3, rgb=d_ins[k], rgb_out=d_rgbs[k], outs=d_outs[k])
-            with torch.cuda.stream(copy_st):
-                for j in range(B):
-                    n = res[j]["out_len"]
-                    h_outs[k][j][:n].copy_(d_outs[k][j][:n], non_blocking=True)
-                    h_rgbs[k][j].copy_(d_rgbs[k][j], non_blocking=True)
-                    io_bytes[1] += n + d_rgbs[k][j].numel()
-                ev_out[k].record(copy_st)
+            stream.wait_event(ev_out[k])        # slot k's outputs downloaded two steps ago
+            batch.step_async(3, rgb=d_ins[k], rgb_out=d_rgbs[k], outs=d_outs[k], results=d_res[k], stream=stream)
+            h_res[k].copy_(d_res[k], non_blocking=True)
+            ev_res[k].record(stream)
+            if t > 0:
+                download(1 - k)
+        download((nsteps - 1) % 2)
         stream.wait_stream(copy_st)
+        stream.wait_stream(down_st)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
