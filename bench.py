@@ -446,13 +446,14 @@ def plain_e2e_async(kw, h_frames, dev, steps, ring=4):
     goes back up (a sender's and a receiver's copies), is decoded, and the decoded frame comes
     down.  Coding runs on the compute stream, copies on a copy stream; the host reads each
     frame's length (8 bytes copied after its encode) while the next frame's encode is already
-    queued, so the device never waits for the host.  Returns (frames/s, H2D bytes/frame,
+    queued, so the device never waits for the host.  Uploads and downloads go on copy streams
+    of their own (the two copy engines work at once).  Returns (frames/s, H2D bytes/frame,
     D2H bytes/frame)."""
     import torch
     from paper_1510_00561_b300 import Codec
     enc, dec = Codec(**kw), Codec(**kw)
     H, W = kw["height"], kw["width"]
-    cs, cp = torch.cuda.current_stream(), torch.cuda.Stream(dev)
+    cs, cp, cd = torch.cuda.current_stream(), torch.cuda.Stream(dev), torch.cuda.Stream(dev)   # compute, up, down
     R = ring
     d_in = [torch.empty((H, W, 3), dtype=torch.uint8, device=dev) for _ in range(R)]
     d_out = [torch.empty(enc.max_stream, dtype=torch.uint8, device=dev) for _ in range(R)]
@@ -462,7 +463,7 @@ def plain_e2e_async(kw, h_frames, dev, steps, ring=4):
     h_rgb = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(R)]
     d_len = torch.zeros(R, dtype=torch.int64, device=dev)
     h_len = torch.zeros(R, dtype=torch.int64).pin_memory()
-    ev = {name: [torch.cuda.Event() for _ in range(R)] for name in ("in", "enc", "sin", "dec", "done")}
+    ev = {name: [torch.cuda.Event() for _ in range(R)] for name in ("in", "enc", "sdown", "sin", "dec", "done")}
     io = [0, 0]
 
     def upload_encode(t):
@@ -482,18 +483,21 @@ def plain_e2e_async(kw, h_frames, dev, steps, ring=4):
         k = t % R
         ev["enc"][k].synchronize()
         n = int(h_len[k])
-        with torch.cuda.stream(cp):
-            cp.wait_event(ev["enc"][k])
+        with torch.cuda.stream(cd):
+            cd.wait_event(ev["enc"][k])
             h_str[k][:n].copy_(d_out[k][:n], non_blocking=True)
+            ev["sdown"][k].record(cd)
+        with torch.cuda.stream(cp):
+            cp.wait_event(ev["sdown"][k])
             d_sin[k][:n].copy_(h_str[k][:n], non_blocking=True)
             ev["sin"][k].record(cp)
         cs.wait_event(ev["sin"][k])
         dec.decode_async(d_sin[k][:n], d_rgb[k], stream=cs)
         ev["dec"][k].record(cs)
-        with torch.cuda.stream(cp):
-            cp.wait_event(ev["dec"][k])
+        with torch.cuda.stream(cd):
+            cd.wait_event(ev["dec"][k])
             h_rgb[k].copy_(d_rgb[k], non_blocking=True)
-            ev["done"][k].record(cp)
+            ev["done"][k].record(cd)
         io[0] += n
         io[1] += n + d_rgb[k].numel() + 8
 
@@ -502,12 +506,14 @@ def plain_e2e_async(kw, h_frames, dev, steps, ring=4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(cs)
         cp.wait_event(e0)
+        cd.wait_event(e0)
         upload_encode(0)
         for t in range(1, nsteps):
             upload_encode(t)
             round_trip_decode(t - 1)
         round_trip_decode(nsteps - 1)
         cs.wait_stream(cp)
+        cs.wait_stream(cd)
         e1.record(cs)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
