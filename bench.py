@@ -42,18 +42,18 @@ CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": "0059fef9443845cf2bac0aa551b3c027e50bc35a68b33c73f00acb2b8a22b244",
-           "dram_per_frame": {"colour_fwd": 6652736,
-                              "lp_analysis": 21055296,
-                              "dfb_analysis": 81370624,
-                              "quantise_kp": 33340480,
-                              "rle_stream": 17114624,
-                              "parse_unrle": 3705728,
-                              "unquantise_kp": 28105088,
-                              "dfb_synthesis": 82351552,
-                              "lp_synthesis": 29116480,
-                              "colour_inv": 12571200,
-                              "step": 315387200},
+CAPTURE = {"sources_sha256": "3a98a340da3ef1e5f6de39a55fb44bc73b73d33f81be14e97cbba323b062dd52",
+           "dram_per_frame": {"colour_fwd": 6660544,
+                              "lp_analysis": 20864128,
+                              "dfb_analysis": 81350784,
+                              "quantise_kp": 33395648,
+                              "rle_stream": 17114688,
+                              "parse_unrle": 3713536,
+                              "unquantise_kp": 28127040,
+                              "dfb_synthesis": 82267456,
+                              "lp_synthesis": 29116288,
+                              "colour_inv": 12555136,
+                              "step": 315168640},
            "warp_inst_per_frame": 166782336,
            "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
