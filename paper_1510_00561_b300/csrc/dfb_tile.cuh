@@ -653,22 +653,26 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
         static_assert(2 * RPW <= 32, "one lane per (row, parity) of a warp");
         const int lp = lane & 1, rl0 = warp + NW * (lane >> 1), tl = t0 - R + rl0;
         const int vl = wrapd(c0 - rl0 - i * (2 * tl + lp), C);
-        const float* rl = (lp ? P1 : P0) + (long long)wrapd(tl, R2) * (lp ? V1.rs : V0.rs);
+        const int ul = wrapd(tl, R2);
+        const long long rs0 = V0.rs, rs1 = V1.rs;
 #pragma unroll 1
-        for (int k = 0; k < 2 * RPW; k++) {
-            const int r = warp + NW * (k >> 1);
+        for (int kk = 0; kk < RPW; kk++) {
+            const int r = warp + NW * kk;
             if (r >= RB) break;
-            const float* row = reinterpret_cast<const float*>(
-                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rl), k));
-            const int vs = __shfl_sync(0xffffffffu, vl, k);
-            const unsigned sb = smem_addr(((k & 1) ? arrO : arrE) + r * CBS);
-            if (vs + CB <= C) {                  // the window does not wrap: no per-element checks
-                const float* src = row + vs;
 #pragma unroll
-                for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
-            } else {
+            for (int par = 0; par < 2; par++) {
+                const int u = __shfl_sync(0xffffffffu, ul, 2 * kk + par);
+                const int vs = __shfl_sync(0xffffffffu, vl, 2 * kk + par);
+                const float* row = par ? P1 + u * rs1 : P0 + u * rs0;
+                const unsigned sb = smem_addr((par ? arrO : arrE) + r * CBS);
+                if (vs + CB <= C) {                  // the window does not wrap: no per-element checks
+                    const float* src = row + vs;
 #pragma unroll
-                for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
+                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, src + x);
+                } else {
+#pragma unroll
+                    for (int x = lane; x < CB; x += 32) cp_async4s(sb + 4u * x, row + wrap_fast<CB>(vs + x, C));
+                }
             }
         }
     } else {
@@ -731,23 +735,26 @@ __device__ __forceinline__ void dfb_b_tile(const DfbBJob& J, int tile, const Bas
         static_assert(DFBB_ROWS % NW == 0 && 2 * RPW <= 32, "one lane per (row, parity) of a warp");
         const int lp = lane & 1, rl = warp + NW * (lane >> 1), tl = t0 + rl;
         const int vl = wrapd(c0 - rl - i * (2 * tl + lp), C);
-        float* ql = (lp ? Q1 : Q0) + (long long)tl * (lp ? W1.rs : W0.rs);
+        const long long rs0 = W0.rs, rs1 = W1.rs;
 #pragma unroll 1
-        for (int k = 0; k < 2 * RPW; k++) {
-            const int rr = warp + NW * (k >> 1);
-            if (t0 + rr >= R2) break;
-            float* row = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ql), k));
-            const int vs = __shfl_sync(0xffffffffu, vl, k);
-            const float* srow = ((k & 1) ? arrO : arrE) + (R + rr) * CBS + R;
-            if (vs + ncol <= C) {
-                float* dst = row + vs;
+        for (int kk = 0; kk < RPW; kk++) {
+            const int rr = warp + NW * kk, t = t0 + rr;
+            if (t >= R2) break;
 #pragma unroll
-                for (int xx = lane; xx < COLS; xx += 32)
-                    if (xx < ncol) dst[xx] = srow[xx];
-            } else {
+            for (int par = 0; par < 2; par++) {
+                const int vs = __shfl_sync(0xffffffffu, vl, 2 * kk + par);
+                float* row = par ? Q1 + t * rs1 : Q0 + t * rs0;
+                const float* srow = (par ? arrO : arrE) + (R + rr) * CBS + R;
+                if (vs + ncol <= C) {
+                    float* dst = row + vs;
 #pragma unroll
-                for (int xx = lane; xx < COLS; xx += 32)
-                    if (xx < ncol) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
+                    for (int xx = lane; xx < COLS; xx += 32)
+                        if (xx < ncol) dst[xx] = srow[xx];
+                } else {
+#pragma unroll
+                    for (int xx = lane; xx < COLS; xx += 32)
+                        if (xx < ncol) row[wrap_fast<CB>(vs + xx, C)] = srow[xx];
+                }
             }
         }
     } else {
