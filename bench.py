@@ -42,19 +42,19 @@ CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": "3a98a340da3ef1e5f6de39a55fb44bc73b73d33f81be14e97cbba323b062dd52",
-           "dram_per_frame": {"colour_fwd": 6660544,
-                              "lp_analysis": 20864128,
-                              "dfb_analysis": 81350784,
-                              "quantise_kp": 33395648,
+CAPTURE = {"sources_sha256": "c72b34f6cd9143d553f7b862107d6a7f811fd430b97b6f07ccb32306f5efa2f4",
+           "dram_per_frame": {"colour_fwd": 6632704,
+                              "lp_analysis": 20928064,
+                              "dfb_analysis": 81912704,
+                              "quantise_kp": 33427136,
                               "rle_stream": 17114688,
-                              "parse_unrle": 3713536,
-                              "unquantise_kp": 28127040,
-                              "dfb_synthesis": 82267456,
-                              "lp_synthesis": 29116288,
-                              "colour_inv": 12555136,
-                              "step": 315168640},
-           "warp_inst_per_frame": 166782336,
+                              "parse_unrle": 3723968,
+                              "unquantise_kp": 28012864,
+                              "dfb_synthesis": 83081024,
+                              "lp_synthesis": 29116480,
+                              "colour_inv": 12572096,
+                              "step": 316525120},
+           "warp_inst_per_frame": 162015842,
            "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
 SMSP_PER_SM, N_SM = 4, 148
