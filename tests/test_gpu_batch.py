@@ -135,6 +135,10 @@ def test_launch_shapes_fusion_depths_and_graph_replay_change_nothing():
         for a, c in zip(ref, got):
             for x, y in zip(a, c):
                 assert torch.equal(x, y), (graphs, rows, tok, fuse, bt)
+    # block widths other than 0, 128 and 256 are refused
+    for bad in (-1, 64, 192, 512):
+        with pytest.raises(CvcError):
+            b.set_dfb_threads(bad)
 
 
 def test_autotune_keeps_state_and_output():
