@@ -127,7 +127,7 @@ __device__ __forceinline__ int luma_of(int R, int G, int B, bool st8) {
     return t + (cg >> 1);
 }
 
-__global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
+__global__ void __launch_bounds__(256, 8) k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __restrict__ sc,
                                const int* __restrict__ blk_stream, float* __restrict__ planes,
                                uint8_t* __restrict__ luma0, uint8_t* __restrict__ luma1) {
     const int s = blk_stream[blockIdx.x];
@@ -185,26 +185,55 @@ __global__ void k_colour_fwd_b(const SDesc* __restrict__ sd, const SCall* __rest
         const uint8_t* r1 = rgb + (long long)min(2 * sy + 1, g.H - 1) * pitch;
         float* oco = Y + (long long)g.Hp * g.Wp + (long long)cy * g.Wcp;
         float* ocg = oco + (long long)g.Hcp * g.Wcp;
-        for (int cx = threadIdx.x; cx < g.Wcp; cx += blockDim.x) {
-            const int sx = mirror_idx(cx, g.Wc);
-            const int c0 = 3 * (2 * sx), c1 = 3 * min(2 * sx + 1, g.W - 1);
-            int sco = 0, scg = 0;
-            const uint8_t* q[4] = {r0 + c0, r0 + c1, r1 + c0, r1 + c1};
+        // a thread takes two neighbouring chroma samples; where both average four whole source
+        // pixels of aligned rows (2cx .. 2cx + 3: twelve bytes), it reads them as three words per row
+        const bool rows4 = (((uintptr_t)r0 | (uintptr_t)r1) & 3) == 0;
+        for (int cx = 2 * threadIdx.x; cx < g.Wcp; cx += 2 * blockDim.x) {
+            uint32_t wd[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};   // source row: the bytes of pixels 2cx .. 2cx + 3
+            const bool fast = rows4 && cx + 1 < g.Wc && 2 * cx + 3 < g.W;
+            if (fast) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int R = q[k][0], G = q[k][1], Bv = q[k][2];
-                if (st8) {
-                    // Table I: Co = (R - B)/2, Cg = (2G - R - B)/4, rounded, +127, clamped to a byte
-                    sco += min(max(div_pow2_round(R - Bv, 1) + 127, 0), 255);
-                    scg += min(max(div_pow2_round(2 * G - R - Bv, 2) + 127, 0), 255);
-                } else {
-                    const int co = R - Bv, t = Bv + (co >> 1);
-                    sco += co;
-                    scg += G - t;
+                for (int r = 0; r < 2; r++) {
+                    const uint32_t* w = reinterpret_cast<const uint32_t*>((r ? r1 : r0) + 6 * cx);
+                    wd[r][0] = w[0];
+                    wd[r][1] = w[1];
+                    wd[r][2] = w[2];
                 }
             }
-            oco[cx] = (float)((sco + 2) >> 2);
-            ocg[cx] = (float)((scg + 2) >> 2);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int c = cx + h;
+                int sco = 0, scg = 0;
+                const int sx = mirror_idx(c, g.Wc);
+                const int c0 = 3 * (2 * sx), c1 = 3 * min(2 * sx + 1, g.W - 1);
+                const uint8_t* q[4] = {r0 + c0, r0 + c1, r1 + c0, r1 + c1};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    // pixel k: source row k >> 1, column 2c + (k & 1)
+                    const int o = 6 * h + 3 * (k & 1);
+                    int R, G, Bv;
+                    if (fast) {
+                        R = (int)((wd[k >> 1][o >> 2] >> (8 * (o & 3))) & 255u);
+                        G = (int)((wd[k >> 1][(o + 1) >> 2] >> (8 * ((o + 1) & 3))) & 255u);
+                        Bv = (int)((wd[k >> 1][(o + 2) >> 2] >> (8 * ((o + 2) & 3))) & 255u);
+                    } else {
+                        R = q[k][0];
+                        G = q[k][1];
+                        Bv = q[k][2];
+                    }
+                    if (st8) {
+                        // Table I: Co = (R - B)/2, Cg = (2G - R - B)/4, rounded, +127, clamped to a byte
+                        sco += min(max(div_pow2_round(R - Bv, 1) + 127, 0), 255);
+                        scg += min(max(div_pow2_round(2 * G - R - Bv, 2) + 127, 0), 255);
+                    } else {
+                        const int co = R - Bv, t = Bv + (co >> 1);
+                        sco += co;
+                        scg += G - t;
+                    }
+                }
+                oco[c] = (float)((sco + 2) >> 2);
+                ocg[c] = (float)((scg + 2) >> 2);
+            }
         }
     }
 }
