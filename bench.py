@@ -42,19 +42,19 @@ CSRC = os.path.join(ROOT, "paper_1510_00561_b300", "csrc")
 # of the whole step.  They hold only for the kernel sources they were taken on:
 # `sources_sha256` is kernel_sources_sha() of that build, and the bench reports
 # them (roofline.traffic, roofline.alu) only while the sources still match.
-CAPTURE = {"sources_sha256": "c72b34f6cd9143d553f7b862107d6a7f811fd430b97b6f07ccb32306f5efa2f4",
-           "dram_per_frame": {"colour_fwd": 6632704,
-                              "lp_analysis": 20928064,
-                              "dfb_analysis": 81912704,
-                              "quantise_kp": 33427136,
-                              "rle_stream": 17114688,
-                              "parse_unrle": 3723968,
-                              "unquantise_kp": 28012864,
-                              "dfb_synthesis": 83081024,
-                              "lp_synthesis": 29116480,
-                              "colour_inv": 12572096,
-                              "step": 316525120},
-           "warp_inst_per_frame": 162015842,
+CAPTURE = {"sources_sha256": "8651f8cdacce8d26db0683ad0cff24b3f0409375de767000e01eb64c5f1c21ef",
+           "dram_per_frame": {"colour_fwd": 6475392,
+                              "lp_analysis": 20901440,
+                              "dfb_analysis": 81866880,
+                              "quantise_kp": 33368576,
+                              "rle_stream": 17114624,
+                              "parse_unrle": 3723200,
+                              "unquantise_kp": 28115776,
+                              "dfb_synthesis": 82856192,
+                              "lp_synthesis": 29105856,
+                              "colour_inv": 12526336,
+                              "step": 316057600},
+           "warp_inst_per_frame": 162596834,
            "profile": "profiles/launches_1080p_batched.md (ncu, 4 streams, one batched step)"}
 # issue rate of one SM sub-partition: one warp instruction per cycle
 SMSP_PER_SM, N_SM = 4, 148
